@@ -1,0 +1,246 @@
+/*
+ * nys.h -- C ABI of the GB300 randomized-Nystrom-preconditioned reconstruction
+ * library (arxiv 2411.08178, "randomized Nystrom preconditioners for
+ * variational image reconstruction").
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * Pointers.   Arguments named x, y, z, s, out, Omega, Y, U, Q, S_hat, gamma are
+ *             DEVICE pointers owned by the caller; the library never frees
+ *             them.  Descriptor structs and scalars are host memory.
+ * Layout.     An image is n1 x n2, row-major (pixel (i, j) = row i, column j at
+ *             offset i*n2 + j).  A batch of B images is B images back to back.
+ *             An N x ell matrix (Omega, Y, U) is stored as ell images back to
+ *             back ("each column of Omega represents an image", Sec. III-C):
+ *             column j starts at offset j*N.
+ * Types.      dtype NYS_F64 or NYS_F32 for images; the sketch may also use
+ *             NYS_BF16 storage for Omega, Y and U (FP32 accumulation).
+ * Streams.    Every call is asynchronous on the context's CUDA stream unless
+ *             it says otherwise; host-visible results are noted per call.
+ * Memory.     op_apply / op_adjoint / op_normal, precond_apply, prox_* and
+ *             pgd_step never allocate: their scratch comes from the context
+ *             workspace, which nys_reserve() sizes ahead of time (calls made
+ *             before a reserve may grow it once).
+ * Errors.     Every function returns NYS_OK (0) or one of the codes below and
+ *             records a message readable with nys_last_error().  No C++
+ *             exception crosses this boundary.
+ */
+#ifndef NYS_H
+#define NYS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---------------------------------------------------------------- codes -- */
+enum {
+    NYS_OK = 0,
+    NYS_EINVAL = 1,        /* bad shape, dtype, null pointer or argument      */
+    NYS_ENOMEM = 2,        /* device allocation failed                        */
+    NYS_ECUDA = 3,         /* a CUDA runtime call failed                      */
+    NYS_ENOTSPD = 4,       /* Cholesky of the shifted core failed 8 retries   */
+    NYS_EDEGENERATE = 5,   /* s_K + mu <= 0 in the preconditioner             */
+    NYS_ENONFINITE = 6,    /* NaN/Inf produced                                */
+    NYS_ETIMEOUT = 7,      /* a bounded device wait ran out                   */
+    NYS_ENOCONV = 8        /* iteration cap hit (warning: output still valid) */
+};
+
+enum { NYS_F32 = 0, NYS_F64 = 1, NYS_BF16 = 2 };
+enum { NYS_OP_BLUR = 0, NYS_OP_BLUR_DECIM = 1, NYS_OP_RADON = 2 };
+enum { NYS_PHI_ATA = 0, NYS_PHI_W_ATA_WT = 1 };
+enum { NYS_REG_WAVELET = 0, NYS_REG_TV = 1, NYS_REG_HS = 2 };
+enum { NYS_FIT_L2 = 0, NYS_FIT_HUBER = 1 };
+
+typedef struct nys_ctx nys_ctx;
+typedef struct nys_op nys_op;
+typedef struct nys_solver nys_solver;
+
+/* ------------------------------------------------------------- context -- */
+/* Create a context on CUDA device `device`, issuing work on `cuda_stream`
+ * (a cudaStream_t; NULL = legacy default stream).  *ctx is set on success. */
+int nys_create(nys_ctx** ctx, int device, void* cuda_stream);
+int nys_destroy(nys_ctx* ctx);
+/* Replace the stream used by later calls on this context. */
+int nys_set_stream(nys_ctx* ctx, void* cuda_stream);
+/* Block the host until all work issued on the context's stream is done. */
+int nys_sync(nys_ctx* ctx);
+/* Message of the last failing call on this context ("" if none).  Valid until
+ * the next call on the same context.  NULL ctx gives the global message. */
+const char* nys_last_error(const nys_ctx* ctx);
+/* Make sure the context workspace holds at least `bytes` bytes. */
+int nys_reserve(nys_ctx* ctx, size_t bytes);
+/* Library version string. */
+const char* nys_version(void);
+
+/* ------------------------------------------------------------ operators -- */
+/* Forward models of Sec. IV: periodic blur (IV-A), blur + decimation
+ * (IV-A, super-resolution) and the parallel-beam ray transform (IV-C),
+ * discretised with Joseph's method: ray (theta_k, t_m) with
+ * theta_k = k * angle_span / n_angles, detector offset t_m = m - (n_bins-1)/2
+ * pixels, pixel (i, j) at x = j - (n2-1)/2, y = i - (n1-1)/2; one sample per
+ * row (|cos| + 1e-9 >= |sin|, weight 1/|cos|) or per column (weight 1/|sin|)
+ * with linear interpolation, zero outside the image.
+ * Blur: (Hx)[i,j] = sum_ab kernel[a*kw+b] x[(i+a-(kh-1)/2) mod n1,
+ * (j+b-(kw-1)/2) mod n2]; kh, kw odd.  Decimation keeps pixels (d i, d j).
+ * The kernel (host, float64, kh*kw) is copied; the descriptor may be freed
+ * after the call.  haar_levels > 0 enables the orthonormal Haar transform W
+ * (Mallat layout) used by NYS_PHI_W_ATA_WT and the wavelet regulariser
+ * (Sec. III-B, invertible L); n1, n2 must be divisible by 2^haar_levels. */
+typedef struct nys_op_desc {
+    int kind;               /* NYS_OP_*                                     */
+    int dtype;              /* NYS_F32 or NYS_F64                           */
+    int n1, n2;             /* image rows, columns                          */
+    const double* kernel;   /* host, kh*kw row-major (blur kinds)           */
+    int kh, kw;
+    int decim;              /* NYS_OP_BLUR_DECIM factor (n1, n2 divisible)  */
+    int n_angles, n_bins;   /* NYS_OP_RADON                                 */
+    double angle_span;      /* NYS_OP_RADON, radians (pi = parallel beam)   */
+    int haar_levels;        /* 0 = no wavelet                               */
+} nys_op_desc;
+
+int nys_op_create(nys_ctx* ctx, const nys_op_desc* desc, nys_op** op);
+int nys_op_destroy(nys_op* op);
+/* Number of pixels N = n1*n2 and measurements M of one image. */
+int nys_op_sizes(const nys_op* op, int64_t* N, int64_t* M);
+
+/* y[b] = A x[b], b < batch.  x: batch*N, y: batch*M, op dtype. */
+int op_apply(nys_op* op, const void* x, void* y, int batch);
+/* x[b] = A^T y[b]: the exact transpose of op_apply. */
+int op_adjoint(nys_op* op, const void* y, void* x, int batch);
+/* y[b] = A^T A x[b] (fused where the operator allows).  x, y: batch*N. */
+int op_normal(nys_op* op, const void* x, void* y, int batch);
+/* c[b] = W x[b] (inverse = 0) or x[b] = W^T c[b] (inverse = 1). */
+int op_haar(nys_op* op, const void* in, void* out, int batch, int inverse);
+
+/* ---------------------------------------------------------- Algorithm 1 -- */
+/* Steps 1-2 of Algorithm 1: draw Omega (N x ell, i.i.d. N(0,1)) from the
+ * Philox4x32-10 counter generator (element (i, j) -> flat index e = j*N + i,
+ * Philox block e/4 with counter (e/4 mod 2^32, e/4 >> 32, 0, 0) and key
+ * (seed mod 2^32, seed >> 32), uniforms ((x >> 9) + 0.5) 2^-23, Box-Muller
+ * pairs) and write Y = Phi Omega with Phi = A^T A (NYS_PHI_ATA) or
+ * W A^T A W^T (NYS_PHI_W_ATA_WT, Sec. III-B).  Omega and Y use `store_dtype`
+ * (the op dtype, or NYS_BF16 for an FP32 op: the operator then computes in
+ * FP32 and rounds its output). */
+int nys_sketch(nys_ctx* ctx, nys_op* op, int phi_kind, int ell, uint64_t seed,
+               int store_dtype, void* Omega, void* Y);
+
+/* Nystrom factor U, S_hat (Algorithm 1 steps 3-8).  Caller-owned device
+ * buffers: U (N x ell, dtype `dtype`: NYS_F32, NYS_F64 or NYS_BF16) and
+ * S_hat (ell doubles, descending).  The library attaches small state of its
+ * own (O(ell^2) device memory: U^T U of the stored U and the ell x ell matrix
+ * that applies P^{-1}) to `priv`; release it with nys_precond_release.
+ * nys_factor synchronises with the stream before returning and fills the
+ * host fields marked "out".  It also runs nys_precond_setup(mu = 0,
+ * sqrt_shift = 1). */
+typedef struct nys_precond {
+    void* U;
+    double* S_hat;
+    int64_t N;
+    int ell;
+    int dtype;
+    double v;            /* out: final shift eps*||Omega||_F * 10^retries  */
+    int chol_retries;    /* out                                            */
+    double s_first;      /* out: S_hat[0]                                  */
+    double s_last;       /* out: S_hat[ell-1]                              */
+    double mu;           /* set by nys_precond_setup                       */
+    int sqrt_shift;      /* set by nys_precond_setup                       */
+    void* priv;          /* library-owned; NULL before nys_factor          */
+} nys_precond;
+
+/* Omega, Y: N x ell in `in_dtype` (as written by nys_sketch).  eps is the
+ * "machine accuracy" of Algorithm 1.  On Cholesky failure the shift is
+ * multiplied by 10 and retried up to 8 times, then NYS_ENOTSPD.  The core is
+ * symmetrised, (M + M^T)/2, before the Cholesky. */
+int nys_factor(nys_ctx* ctx, const void* Omega, const void* Y, int in_dtype,
+               int64_t N, int ell, double eps, nys_precond* out);
+int nys_precond_release(nys_precond* pc);
+/* Adopt a factor the caller wrote into pc->U and pc->S_hat (N, ell, dtype
+ * set; e.g. a preconditioner saved earlier): computes U^T U of the stored U,
+ * the host copies s_first / s_last, and runs nys_precond_setup(mu,
+ * sqrt_shift).  Synchronises. */
+int nys_precond_import(nys_ctx* ctx, nys_precond* pc, double mu, int sqrt_shift);
+
+/* ------------------------------------------------------ preconditioner -- */
+/* Choose mu and the s_K <- sqrt(s_K) heuristic (Sec. III-B) and precompute
+ * the weights d_i = max(0, (s_i + mu)/(s' + mu) - 1), s' = sqrt(s_K) or s_K,
+ * of P = I + Ubar Ubar^T, Ubar = U diag(sqrt(d)) (the Sec. III-B rewrite of
+ * Eq. RYPreconditioner), and M = diag(sqrt d) (I + Ubar^T Ubar)^{-1}
+ * diag(sqrt d).  NYS_EDEGENERATE if s' + mu <= 0.  Synchronises. */
+int nys_precond_setup(nys_ctx* ctx, nys_precond* pc, double mu, int sqrt_shift);
+
+/* inverse = 0: out = P z = z + U diag(d) U^T z.
+ * inverse = 1: out = P^{-1} z = z - U M U^T z.  This is the second line of
+ * Eq. (RYPreconditioner) when U^T U = I, and the exact inverse of P for the
+ * stored U otherwise (Woodbury), so P P^{-1} = I also when U is stored in
+ * BF16.  z, out: batch*N of `dtype` (NYS_F32/NYS_F64); out == z allowed. */
+int precond_apply(nys_ctx* ctx, const nys_precond* pc, int inverse, int dtype,
+                  const void* z, void* out, int batch);
+
+/* ---------------------------------------------------------------- prox -- */
+typedef struct nys_prox_info {
+    int iterations;      /* Newton steps taken                 */
+    int converged;       /* 1 if ||F|| reached the tolerance   */
+    double residual;     /* final ||F(gamma)||                 */
+} nys_prox_info;
+
+/* Theorem 1 prox of tau ||.||_1 in the P metric (wavelet regulariser):
+ * out = T_tau(s - Ubar gamma*) where gamma* solves
+ * Ubar^T (s - T_tau(s - Ubar gamma)) + gamma = 0 by semi-smooth Newton.
+ * pc == NULL gives the plain soft threshold.  gamma_io: device, ell doubles,
+ * warm start in / solution out (may be NULL).  info (host, may be NULL) is
+ * filled after an internal synchronisation. */
+int prox_wavelet(nys_ctx* ctx, const nys_precond* pc, double tau, int dtype,
+                 int64_t N, const void* s, void* out, double* gamma_io,
+                 nys_prox_info* info);
+
+/* Dual APG prox of lambda_bar ||L x||_{1,phi} in the P metric (Sec. III-B):
+ * L = first differences with phi = 1 (prox_tv, Q: 2*N) or second differences
+ * with the Schatten-1 norm (prox_hs, Q: 3*N as (q11, q12, q22) planes);
+ * n_inner APG steps on the dual, warm-started from Q_io (in/out, caller
+ * zeroes it before the first call).  pc == NULL gives P = I. */
+int prox_tv(nys_ctx* ctx, const nys_precond* pc, double lambda_bar, int n_inner,
+            int dtype, int n1, int n2, const void* s, void* out, void* Q_io);
+int prox_hs(nys_ctx* ctx, const nys_precond* pc, double lambda_bar, int n_inner,
+            int dtype, int n1, int n2, const void* s, void* out, void* Q_io);
+
+/* ---------------------------------------------------------- Algorithm 3 -- */
+typedef struct nys_solver_desc {
+    int reg;             /* NYS_REG_*                                       */
+    int fit;             /* NYS_FIT_L2 or NYS_FIT_HUBER                     */
+    double lambda;       /* regularisation weight                           */
+    double huber_delta;
+    double alpha;        /* step size; <= 0: 1.02 x power-iteration estimate */
+    int n_inner;         /* dual APG steps per prox (TV, HS)                */
+    int power_iters;     /* power iterations for alpha (default 50)         */
+    uint64_t power_seed;
+} nys_solver_desc;
+
+/* WAPG (Algorithm 3) for min_x f(x) + lambda g(x) with operator op, data y
+ * (device, M values, copied) and preconditioner pc (NULL = plain APG).  For
+ * NYS_REG_WAVELET the variable is xbar = W x.  The solver owns x, u, t and
+ * the dual/Newton warm starts; x^1 = u^1 = 0, t^0 = 1. */
+int nys_solver_create(nys_ctx* ctx, nys_op* op, const nys_solver_desc* desc,
+                      const void* y, const nys_precond* pc, nys_solver** solver);
+int nys_solver_destroy(nys_solver* solver);
+/* Run n_steps iterations of Algorithm 3 (asynchronous; graph-capturable). */
+int pgd_step(nys_solver* solver, int n_steps);
+/* Reset to x = u = 0, t = 1, zero warm starts (keeps alpha). */
+int nys_solver_reset(nys_solver* solver);
+/* Copy the current iterate, in the image domain (W^T xbar for wavelets),
+ * to x_out (device, N values of the op dtype). */
+int nys_solver_get_x(nys_solver* solver, void* x_out);
+/* The step size in use (host).  Synchronises if it was estimated. */
+int nys_solver_alpha(nys_solver* solver, double* alpha);
+
+/* ---------------------------------------------------------- reductions -- */
+/* *out (host) = ||a - b||_2 / ||b||_2 over n elements (b != 0), or ||a||_2
+ * when b == NULL.  Synchronises. */
+int nys_rel_err(nys_ctx* ctx, int dtype, int64_t n, const void* a, const void* b, double* out);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* NYS_H */

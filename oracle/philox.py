@@ -18,7 +18,7 @@ so that the same seed gives the same Omega:
 Omega element mapping (column-major N x ell, flat index e = j*N + i):
   Philox block b = e // 4 with counter (b mod 2^32, b >> 32, 0, 0) and key
   (seed mod 2^32, seed >> 32) gives words (x0, x1, x2, x3);
-  uniforms u_r = ((x_r >> 8) + 0.5) * 2^-24, exactly representable in fp32;
+  uniforms u_r = ((x_r >> 9) + 0.5) * 2^-23, exactly representable in fp32;
   Box-Muller (Box & Muller 1958): rho = sqrt(-2 ln u0),
       z[4b+0] = rho cos(2 pi u1), z[4b+1] = rho sin(2 pi u1),
   and likewise (u2, u3) -> z[4b+2], z[4b+3].
@@ -68,7 +68,7 @@ def gaussian_matrix(N: int, ell: int, seed: int) -> np.ndarray:
     key[:, 0] = np.uint64(seed) & MASK
     key[:, 1] = np.uint64(seed) >> np.uint64(32)
     x = philox4x32_10(ctr, key)
-    u = ((x >> np.uint64(8)).astype(np.float64) + 0.5) * (2.0 ** -24)
+    u = ((x >> np.uint64(9)).astype(np.float64) + 0.5) * (2.0 ** -23)
     rho01 = np.sqrt(-2.0 * np.log(u[:, 0]))
     rho23 = np.sqrt(-2.0 * np.log(u[:, 2]))
     z = np.empty((nblk, 4), dtype=np.float64)

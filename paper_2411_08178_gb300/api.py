@@ -1,0 +1,346 @@
+"""Thin Python binding over libnys.so with the C ABI's names.
+
+Torch is used only for device memory and the current CUDA stream: every
+function passes raw pointers and sizes to the library, which does all of the
+computation.  Shapes and dtypes are checked here so that errors are caught
+before a pointer reaches the device.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import math
+
+import numpy as np
+import torch
+
+from . import _abi as A
+from ._abi import check
+
+_DT = {torch.float32: A.NYS_F32, torch.float64: A.NYS_F64, torch.bfloat16: A.NYS_BF16}
+_TORCH = {A.NYS_F32: torch.float32, A.NYS_F64: torch.float64, A.NYS_BF16: torch.bfloat16}
+
+
+def _lib():
+    return A.load()
+
+
+def _ptr(t: torch.Tensor) -> int:
+    if not t.is_cuda:
+        raise ValueError("expected a CUDA tensor")
+    if not t.is_contiguous():
+        raise ValueError("expected a contiguous tensor")
+    return t.data_ptr()
+
+
+def dtype_code(t: torch.Tensor) -> int:
+    try:
+        return _DT[t.dtype]
+    except KeyError:
+        raise ValueError(f"unsupported dtype {t.dtype}") from None
+
+
+class Context:
+    """nys_ctx: device, stream and workspace of the library."""
+
+    def __init__(self, device: int = 0, stream: torch.cuda.Stream | None = None):
+        lib = _lib()
+        self.device = device
+        s = stream if stream is not None else torch.cuda.current_stream(device)
+        self._stream = s
+        h = C.c_void_p()
+        check(lib.nys_create(C.byref(h), device, C.c_void_p(s.cuda_stream)))
+        self.h = h
+
+    def set_stream(self, stream: torch.cuda.Stream):
+        self._stream = stream
+        check(_lib().nys_set_stream(self.h, C.c_void_p(stream.cuda_stream)), self.h)
+
+    @property
+    def stream(self):
+        return self._stream
+
+    def sync(self):
+        check(_lib().nys_sync(self.h), self.h)
+
+    def reserve(self, nbytes: int):
+        check(_lib().nys_reserve(self.h, nbytes), self.h)
+
+    def last_error(self) -> str:
+        return _lib().nys_last_error(self.h).decode()
+
+    def close(self):
+        if getattr(self, "h", None):
+            _lib().nys_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Operator:
+    """nys_op: blur, blur + decimation or parallel-beam ray transform."""
+
+    def __init__(self, ctx: Context, kind: str, n1: int, n2: int, dtype=torch.float32, kernel=None,
+                 decim: int = 1, n_angles: int = 0, n_bins: int = 0, angle_span: float = math.pi,
+                 haar_levels: int = 0):
+        lib = _lib()
+        self.ctx, self.kind, self.n1, self.n2, self.dtype = ctx, kind, n1, n2, dtype
+        d = A.nys_op_desc()
+        d.kind = {"blur": A.NYS_OP_BLUR, "blur_decim": A.NYS_OP_BLUR_DECIM, "radon": A.NYS_OP_RADON}[kind]
+        d.dtype = _DT[dtype]
+        d.n1, d.n2 = n1, n2
+        self._kernel = None
+        if kernel is not None:
+            k = np.ascontiguousarray(np.asarray(kernel, dtype=np.float64))
+            self._kernel = k
+            d.kernel = k.ctypes.data_as(C.POINTER(C.c_double))
+            d.kh, d.kw = k.shape
+        d.decim = decim
+        d.n_angles, d.n_bins, d.angle_span = n_angles, n_bins, angle_span
+        d.haar_levels = haar_levels
+        h = C.c_void_p()
+        check(lib.nys_op_create(ctx.h, C.byref(d), C.byref(h)), ctx.h)
+        self.h = h
+        N, M = C.c_int64(), C.c_int64()
+        check(lib.nys_op_sizes(h, C.byref(N), C.byref(M)))
+        self.N, self.M = N.value, M.value
+        if kind == "blur":
+            self.meas_shape = (n1, n2)
+        elif kind == "blur_decim":
+            self.meas_shape = (n1 // decim, n2 // decim)
+        else:
+            self.meas_shape = (n_angles, n_bins)
+
+    def close(self):
+        if getattr(self, "h", None):
+            _lib().nys_op_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def _batch(t: torch.Tensor, per: int) -> int:
+    if t.numel() % per:
+        raise ValueError(f"tensor of {t.numel()} elements is not a batch of {per}")
+    return t.numel() // per
+
+
+def op_apply(op: Operator, x: torch.Tensor, y: torch.Tensor | None = None) -> torch.Tensor:
+    b = _batch(x, op.N)
+    if y is None:
+        y = torch.empty((b,) + op.meas_shape, dtype=x.dtype, device=x.device)
+    if x.dtype != op.dtype or y.dtype != op.dtype or _batch(y, op.M) != b:
+        raise ValueError("op_apply: dtype or size mismatch")
+    check(_lib().op_apply(op.h, _ptr(x), _ptr(y), b), op.ctx.h)
+    return y
+
+
+def op_adjoint(op: Operator, y: torch.Tensor, x: torch.Tensor | None = None) -> torch.Tensor:
+    b = _batch(y, op.M)
+    if x is None:
+        x = torch.empty((b, op.n1, op.n2), dtype=y.dtype, device=y.device)
+    if x.dtype != op.dtype or y.dtype != op.dtype or _batch(x, op.N) != b:
+        raise ValueError("op_adjoint: dtype or size mismatch")
+    check(_lib().op_adjoint(op.h, _ptr(y), _ptr(x), b), op.ctx.h)
+    return x
+
+
+def op_normal(op: Operator, x: torch.Tensor, y: torch.Tensor | None = None) -> torch.Tensor:
+    b = _batch(x, op.N)
+    if y is None:
+        y = torch.empty((b, op.n1, op.n2), dtype=x.dtype, device=x.device)
+    if x.dtype != op.dtype or y.dtype != op.dtype or _batch(y, op.N) != b:
+        raise ValueError("op_normal: dtype or size mismatch")
+    check(_lib().op_normal(op.h, _ptr(x), _ptr(y), b), op.ctx.h)
+    return y
+
+
+def op_haar(op: Operator, x: torch.Tensor, inverse: bool = False, out: torch.Tensor | None = None) -> torch.Tensor:
+    b = _batch(x, op.N)
+    if out is None:
+        out = torch.empty_like(x)
+    if out.data_ptr() == x.data_ptr():
+        raise ValueError("op_haar: in-place transform is not supported")
+    check(_lib().op_haar(op.h, _ptr(x), _ptr(out), b, int(inverse)), op.ctx.h)
+    return out
+
+
+def nys_sketch(ctx: Context, op: Operator, ell: int, seed: int, phi: str = "ata",
+               store_dtype=None) -> tuple[torch.Tensor, torch.Tensor]:
+    """Algorithm 1 steps 1-2: returns (Omega, Y), each (ell, n1, n2)."""
+    sd = store_dtype or op.dtype
+    dev = torch.device("cuda", ctx.device)
+    Om = torch.empty((ell, op.n1, op.n2), dtype=sd, device=dev)
+    Y = torch.empty_like(Om)
+    kind = {"ata": A.NYS_PHI_ATA, "w_ata_wt": A.NYS_PHI_W_ATA_WT}[phi]
+    check(_lib().nys_sketch(ctx.h, op.h, kind, ell, seed, _DT[sd], _ptr(Om), _ptr(Y)), ctx.h)
+    return Om, Y
+
+
+class Precond:
+    """nys_precond with caller-owned U (ell, N) and S_hat (ell,) tensors."""
+
+    def __init__(self, ctx: Context, N: int, ell: int, dtype=torch.float32):
+        dev = torch.device("cuda", ctx.device)
+        self.ctx = ctx
+        self.U = torch.empty((ell, N), dtype=dtype, device=dev)
+        self.S_hat = torch.empty((ell,), dtype=torch.float64, device=dev)
+        self.s = A.nys_precond()
+        self.s.U = _ptr(self.U)
+        self.s.S_hat = _ptr(self.S_hat)
+        self.s.N = N
+        self.s.ell = ell
+        self.s.dtype = _DT[dtype]
+        self.s.mu = float("nan")
+
+    @property
+    def v(self) -> float:
+        return self.s.v
+
+    @property
+    def chol_retries(self) -> int:
+        return self.s.chol_retries
+
+    def setup(self, mu: float = 0.0, sqrt_shift: bool = True):
+        check(_lib().nys_precond_setup(self.ctx.h, C.byref(self.s), mu, int(sqrt_shift)), self.ctx.h)
+
+    def import_factor(self, U, S_hat, mu: float = 0.0, sqrt_shift: bool = True):
+        """Adopt a factor computed elsewhere (arrays or tensors of shape (ell, N), (ell,))."""
+        self.U.copy_(torch.as_tensor(U).reshape(self.U.shape).to(self.U.dtype))
+        self.S_hat.copy_(torch.as_tensor(S_hat).reshape(self.S_hat.shape).to(torch.float64))
+        check(_lib().nys_precond_import(self.ctx.h, C.byref(self.s), mu, int(sqrt_shift)), self.ctx.h)
+        return self
+
+    def close(self):
+        if getattr(self, "s", None) is not None and self.s.priv:
+            _lib().nys_precond_release(C.byref(self.s))
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def nys_factor(ctx: Context, Omega: torch.Tensor, Y: torch.Tensor, eps: float, u_dtype=None,
+               pc: Precond | None = None) -> Precond:
+    """Algorithm 1 steps 3-8 into a Precond (set up with mu = 0, sqrt heuristic on)."""
+    ell = Omega.shape[0]
+    N = Omega.numel() // ell
+    if Y.shape != Omega.shape or Y.dtype != Omega.dtype:
+        raise ValueError("nys_factor: Omega and Y must match")
+    if pc is None:
+        ud = u_dtype or (torch.float64 if Omega.dtype == torch.float64 else torch.float32)
+        pc = Precond(ctx, N, ell, ud)
+    check(_lib().nys_factor(ctx.h, _ptr(Omega), _ptr(Y), dtype_code(Omega), N, ell, eps, C.byref(pc.s)), ctx.h)
+    return pc
+
+
+def precond_apply(ctx: Context, pc: Precond, z: torch.Tensor, inverse: bool = True,
+                  out: torch.Tensor | None = None) -> torch.Tensor:
+    b = _batch(z, pc.s.N)
+    if out is None:
+        out = torch.empty_like(z)
+    check(_lib().precond_apply(ctx.h, C.byref(pc.s), int(inverse), dtype_code(z), _ptr(z), _ptr(out), b), ctx.h)
+    return out
+
+
+def prox_wavelet(ctx: Context, pc: Precond | None, tau: float, s: torch.Tensor, gamma: torch.Tensor | None = None,
+                 out: torch.Tensor | None = None):
+    if out is None:
+        out = torch.empty_like(s)
+    info = A.nys_prox_info()
+    pcs = C.byref(pc.s) if pc is not None else None
+    g = _ptr(gamma) if gamma is not None else None
+    check(_lib().prox_wavelet(ctx.h, pcs, tau, dtype_code(s), s.numel(), _ptr(s), _ptr(out), g, C.byref(info)),
+          ctx.h)
+    return out, dict(iterations=info.iterations, converged=bool(info.converged), residual=info.residual)
+
+
+def _prox_dual(fn, G, ctx, pc, lam_bar, n_inner, s, Q=None, out=None):
+    n1, n2 = s.shape[-2:]
+    if Q is None:
+        Q = torch.zeros((G, n1, n2), dtype=s.dtype, device=s.device)
+    if out is None:
+        out = torch.empty_like(s)
+    pcs = C.byref(pc.s) if pc is not None else None
+    check(fn(ctx.h, pcs, lam_bar, n_inner, dtype_code(s), n1, n2, _ptr(s), _ptr(out), _ptr(Q)), ctx.h)
+    return out, Q
+
+
+def prox_tv(ctx, pc, lam_bar, n_inner, s, Q=None, out=None):
+    return _prox_dual(_lib().prox_tv, 2, ctx, pc, lam_bar, n_inner, s, Q, out)
+
+
+def prox_hs(ctx, pc, lam_bar, n_inner, s, Q=None, out=None):
+    return _prox_dual(_lib().prox_hs, 3, ctx, pc, lam_bar, n_inner, s, Q, out)
+
+
+class Solver:
+    """nys_solver: Algorithm 3 (WAPG; plain APG when pc is None)."""
+
+    def __init__(self, ctx: Context, op: Operator, y: torch.Tensor, reg: str, lam: float, pc: Precond | None = None,
+                 fit: str = "l2", huber_delta: float = 0.0, alpha: float = 0.0, n_inner: int = 20,
+                 power_iters: int = 50, power_seed: int = 7):
+        d = A.nys_solver_desc()
+        d.reg = {"wavelet": A.NYS_REG_WAVELET, "tv": A.NYS_REG_TV, "hs": A.NYS_REG_HS}[reg]
+        d.fit = {"l2": A.NYS_FIT_L2, "huber": A.NYS_FIT_HUBER}[fit]
+        d.lambda_ = lam
+        d.huber_delta = huber_delta
+        d.alpha = alpha
+        d.n_inner = n_inner
+        d.power_iters = power_iters
+        d.power_seed = power_seed
+        self.ctx, self.op, self.pc = ctx, op, pc
+        h = C.c_void_p()
+        pcs = C.byref(pc.s) if pc is not None else None
+        check(_lib().nys_solver_create(ctx.h, op.h, C.byref(d), _ptr(y.contiguous()), pcs, C.byref(h)), ctx.h)
+        self.h = h
+
+    def step(self, n: int = 1):
+        check(_lib().pgd_step(self.h, n), self.ctx.h)
+
+    def reset(self):
+        check(_lib().nys_solver_reset(self.h), self.ctx.h)
+
+    @property
+    def alpha(self) -> float:
+        a = C.c_double()
+        check(_lib().nys_solver_alpha(self.h, C.byref(a)), self.ctx.h)
+        return a.value
+
+    def x(self, out: torch.Tensor | None = None) -> torch.Tensor:
+        if out is None:
+            out = torch.empty((self.op.n1, self.op.n2), dtype=self.op.dtype,
+                              device=torch.device("cuda", self.ctx.device))
+        check(_lib().nys_solver_get_x(self.h, _ptr(out)), self.ctx.h)
+        return out
+
+    def close(self):
+        if getattr(self, "h", None):
+            _lib().nys_solver_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def pgd_step(solver: Solver, n: int = 1):
+    solver.step(n)
+
+
+def nys_rel_err(ctx: Context, a: torch.Tensor, b: torch.Tensor | None) -> float:
+    out = C.c_double()
+    check(_lib().nys_rel_err(ctx.h, dtype_code(a), a.numel(), _ptr(a), _ptr(b) if b is not None else None,
+                             C.byref(out)), ctx.h)
+    return out.value

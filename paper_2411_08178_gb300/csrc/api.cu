@@ -1,0 +1,255 @@
+// Context, error handling, operator handles and dispatch of the C ABI.
+#include "internal.cuh"
+
+#include <cmath>
+#include <cstring>
+#include <mutex>
+
+namespace {
+std::mutex g_err_mu;
+std::string g_err;
+}  // namespace
+
+namespace nys {
+
+int fail(nys_ctx* ctx, int code, const char* fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    if (ctx) ctx->err = buf;
+    std::lock_guard<std::mutex> g(g_err_mu);
+    g_err = buf;
+    return code;
+}
+
+int cuda_fail(nys_ctx* ctx, cudaError_t e, const char* what) {
+    return fail(ctx, e == cudaErrorMemoryAllocation ? NYS_ENOMEM : NYS_ECUDA, "%s: %s", what,
+                cudaGetErrorString(e));
+}
+
+void* scratch(nys_ctx* ctx, int slot, size_t bytes, int* status) {
+    *status = NYS_OK;
+    if (bytes == 0) bytes = 256;
+    if (ctx->slot_bytes[slot] >= bytes) return ctx->slot_ptr[slot];
+    // growing is not allowed while the stream is being captured
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(ctx->stream, &cs) == cudaSuccess && cs != cudaStreamCaptureStatusNone) {
+        *status = fail(ctx, NYS_ENOMEM, "scratch slot %d needs %zu bytes during stream capture; "
+                                        "call once before capturing or nys_reserve()", slot, bytes);
+        return nullptr;
+    }
+    if (ctx->slot_ptr[slot]) {
+        cudaStreamSynchronize(ctx->stream);
+        cudaFree(ctx->slot_ptr[slot]);
+        ctx->slot_ptr[slot] = nullptr;
+        ctx->slot_bytes[slot] = 0;
+    }
+    size_t nb = (bytes + 4095) & ~size_t(4095);
+    cudaError_t e = cudaMalloc(&ctx->slot_ptr[slot], nb);
+    if (e != cudaSuccess) {
+        ctx->slot_ptr[slot] = nullptr;
+        *status = cuda_fail(ctx, e, "scratch cudaMalloc");
+        return nullptr;
+    }
+    ctx->slot_bytes[slot] = nb;
+    return ctx->slot_ptr[slot];
+}
+
+int op_run(nys_op* op, int which, const void* x, void* y, int batch, int in_dt, int out_dt) {
+    switch (op->kind) {
+        case NYS_OP_BLUR: return blur_run(op, which, x, y, batch, in_dt, out_dt);
+        case NYS_OP_BLUR_DECIM: return decim_run(op, which, x, y, batch, in_dt, out_dt);
+        case NYS_OP_RADON: return radon_run(op, which, x, y, batch, in_dt, out_dt);
+    }
+    return fail(op->ctx, NYS_EINVAL, "unknown operator kind %d", op->kind);
+}
+
+}  // namespace nys
+
+using namespace nys;
+
+extern "C" {
+
+const char* nys_version(void) { return "nys 0.1 (sm_103a)"; }
+
+const char* nys_last_error(const nys_ctx* ctx) {
+    if (ctx) return ctx->err.c_str();
+    std::lock_guard<std::mutex> g(g_err_mu);
+    static thread_local std::string copy;
+    copy = g_err;
+    return copy.c_str();
+}
+
+int nys_create(nys_ctx** out, int device, void* stream) {
+    if (!out) return fail(nullptr, NYS_EINVAL, "nys_create: null output");
+    int n = 0;
+    cudaError_t e = cudaGetDeviceCount(&n);
+    if (e != cudaSuccess) return cuda_fail(nullptr, e, "cudaGetDeviceCount");
+    if (device < 0 || device >= n) return fail(nullptr, NYS_EINVAL, "nys_create: bad device %d", device);
+    e = cudaSetDevice(device);
+    if (e != cudaSuccess) return cuda_fail(nullptr, e, "cudaSetDevice");
+    auto* c = new nys_ctx();
+    c->device = device;
+    c->stream = (cudaStream_t)stream;
+    cudaDeviceGetAttribute(&c->sm_count, cudaDevAttrMultiProcessorCount, device);
+    *out = c;
+    return NYS_OK;
+}
+
+int nys_destroy(nys_ctx* ctx) {
+    if (!ctx) return NYS_OK;
+    cudaStreamSynchronize(ctx->stream);
+    for (int i = 0; i < 12; ++i)
+        if (ctx->slot_ptr[i]) cudaFree(ctx->slot_ptr[i]);
+    delete ctx;
+    return NYS_OK;
+}
+
+int nys_set_stream(nys_ctx* ctx, void* stream) {
+    if (!ctx) return fail(nullptr, NYS_EINVAL, "null ctx");
+    ctx->stream = (cudaStream_t)stream;
+    return NYS_OK;
+}
+
+int nys_sync(nys_ctx* ctx) {
+    if (!ctx) return fail(nullptr, NYS_EINVAL, "null ctx");
+    NYS_CK(ctx, cudaStreamSynchronize(ctx->stream));
+    return NYS_OK;
+}
+
+int nys_reserve(nys_ctx* ctx, size_t bytes) {
+    if (!ctx) return fail(nullptr, NYS_EINVAL, "null ctx");
+    int st;
+    for (int s = 0; s < SLOT_COUNT; ++s) {
+        scratch(ctx, s, bytes, &st);
+        if (st) return st;
+    }
+    return NYS_OK;
+}
+
+int nys_op_create(nys_ctx* ctx, const nys_op_desc* d, nys_op** out) {
+    if (!ctx || !d || !out) return fail(ctx, NYS_EINVAL, "nys_op_create: null argument");
+    if (d->dtype != NYS_F32 && d->dtype != NYS_F64)
+        return fail(ctx, NYS_EINVAL, "operator dtype must be NYS_F32 or NYS_F64");
+    if (d->n1 <= 0 || d->n2 <= 0) return fail(ctx, NYS_EINVAL, "bad image size %d x %d", d->n1, d->n2);
+    auto* op = new nys_op();
+    op->ctx = ctx;
+    op->kind = d->kind;
+    op->dtype = d->dtype;
+    op->n1 = d->n1;
+    op->n2 = d->n2;
+    op->N = (int64_t)d->n1 * d->n2;
+    op->haar_levels = d->haar_levels;
+    if (d->haar_levels < 0 || (d->haar_levels > 0 && ((d->n1 % (1 << d->haar_levels)) ||
+                                                     (d->n2 % (1 << d->haar_levels))))) {
+        delete op;
+        return fail(ctx, NYS_EINVAL, "image size not divisible by 2^haar_levels");
+    }
+    int st = NYS_OK;
+    if (d->kind == NYS_OP_BLUR || d->kind == NYS_OP_BLUR_DECIM) {
+        if (!d->kernel || d->kh <= 0 || d->kw <= 0 || !(d->kh & 1) || !(d->kw & 1)) {
+            delete op;
+            return fail(ctx, NYS_EINVAL, "blur kernel must be given with odd sizes");
+        }
+        op->kh = d->kh;
+        op->kw = d->kw;
+        op->h.assign(d->kernel, d->kernel + (size_t)d->kh * d->kw);
+        op->decim = d->kind == NYS_OP_BLUR_DECIM ? d->decim : 1;
+        if (op->decim < 1 || d->n1 % op->decim || d->n2 % op->decim) {
+            delete op;
+            return fail(ctx, NYS_EINVAL, "decimation factor must divide the image size");
+        }
+        op->M = (int64_t)(d->n1 / op->decim) * (d->n2 / op->decim);
+        st = blur_setup(op);
+    } else if (d->kind == NYS_OP_RADON) {
+        if (d->n_angles <= 0 || d->n_bins <= 0 || !(d->angle_span > 0.0)) {
+            delete op;
+            return fail(ctx, NYS_EINVAL, "radon geometry needs n_angles, n_bins > 0 and span > 0");
+        }
+        op->n_angles = d->n_angles;
+        op->n_bins = d->n_bins;
+        op->span = d->angle_span;
+        op->M = (int64_t)d->n_angles * d->n_bins;
+        st = radon_setup(op);
+    } else {
+        delete op;
+        return fail(ctx, NYS_EINVAL, "unknown operator kind %d", d->kind);
+    }
+    if (st) {
+        nys_op_destroy(op);
+        return st;
+    }
+    *out = op;
+    return NYS_OK;
+}
+
+int nys_op_destroy(nys_op* op) {
+    if (!op) return NYS_OK;
+    if (op->ctx) cudaStreamSynchronize(op->ctx->stream);
+    void* bufs[] = {op->taps_fwd, op->taps_adj, op->taps_nrm, op->rtab, op->inter};
+    for (void* b : bufs)
+        if (b) cudaFree(b);
+    delete op;
+    return NYS_OK;
+}
+
+int nys_op_sizes(const nys_op* op, int64_t* N, int64_t* M) {
+    if (!op) return fail(nullptr, NYS_EINVAL, "null op");
+    if (N) *N = op->N;
+    if (M) *M = op->M;
+    return NYS_OK;
+}
+
+static int check_io(nys_op* op, const void* a, const void* b, int batch) {
+    if (!op) return fail(nullptr, NYS_EINVAL, "null op");
+    if (!a || !b) return fail(op->ctx, NYS_EINVAL, "null data pointer");
+    if (batch < 0) return fail(op->ctx, NYS_EINVAL, "negative batch");
+    return NYS_OK;
+}
+
+int op_apply(nys_op* op, const void* x, void* y, int batch) {
+    if (int st = check_io(op, x, y, batch)) return st;
+    if (batch == 0) return NYS_OK;
+    return op_run(op, 0, x, y, batch, op->dtype, op->dtype);
+}
+
+int op_adjoint(nys_op* op, const void* y, void* x, int batch) {
+    if (int st = check_io(op, y, x, batch)) return st;
+    if (batch == 0) return NYS_OK;
+    return op_run(op, 1, y, x, batch, op->dtype, op->dtype);
+}
+
+int op_normal(nys_op* op, const void* x, void* y, int batch) {
+    if (int st = check_io(op, x, y, batch)) return st;
+    if (batch == 0) return NYS_OK;
+    return op_run(op, 2, x, y, batch, op->dtype, op->dtype);
+}
+
+int op_haar(nys_op* op, const void* in, void* out, int batch, int inverse) {
+    if (int st = check_io(op, in, out, batch)) return st;
+    if (op->haar_levels <= 0) return fail(op->ctx, NYS_EINVAL, "operator was created without haar_levels");
+    if (batch == 0) return NYS_OK;
+    return haar_run(op, in, out, batch, inverse, op->dtype, op->dtype);
+}
+
+int nys_rel_err(nys_ctx* ctx, int dtype, int64_t n, const void* a, const void* b, double* out) {
+    if (!ctx || !a || !out) return fail(ctx, NYS_EINVAL, "nys_rel_err: null argument");
+    if (dtype != NYS_F32 && dtype != NYS_F64) return fail(ctx, NYS_EINVAL, "nys_rel_err: dtype");
+    int st;
+    double* dev = nullptr;
+    if ((st = norm2_diff(ctx, dtype, n, a, b, &dev))) return st;
+    double h[2];
+    NYS_CK(ctx, cudaMemcpyAsync(h, dev, sizeof(h), cudaMemcpyDeviceToHost, ctx->stream));
+    NYS_CK(ctx, cudaStreamSynchronize(ctx->stream));
+    if (b == nullptr) {
+        *out = std::sqrt(h[0]);
+    } else {
+        if (!(h[1] > 0.0)) return fail(ctx, NYS_EINVAL, "nys_rel_err: reference has zero norm");
+        *out = std::sqrt(h[0] / h[1]);
+    }
+    return NYS_OK;
+}
+
+}  // extern "C"

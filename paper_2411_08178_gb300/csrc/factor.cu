@@ -1,0 +1,434 @@
+// Algorithm 1 (Nystrom approximation) and the preconditioner of
+// Eq. (RYPreconditioner) in its Sec. III-B form P = I + Ubar Ubar^T.
+//
+// nys_sketch   steps 1-2: Omega from Philox4x32-10 + Box-Muller, Y = Phi Omega
+//              through the batched operator (all ell probes in one launch).
+// nys_factor   steps 3-8, reorganised so the tall N x ell data is read twice:
+//                G2 = [Omega | Y]^T [Omega | Y]            (one Gram pass)
+//                v  = eps sqrt(trace(Omega^T Omega))        (step 3)
+//                C  = chol(sym(Omega^T Y) + v Omega^T Omega)   (steps 4-5)
+//                H  = Y_v^T Y_v from the blocks of G2
+//                G  = C^{-1} H C^{-T}  = B^T B for B = Y_v C^{-T}   (step 6)
+//                G  = V S^2 V^T                             (step 7, eig of B^T B)
+//                U  = B V S^{-1} = (Y + v Omega) (C^{-T} V S^{-1})  (one GEMM pass)
+//                S_hat = max(0, S^2 - v)                    (step 8)
+//              In exact arithmetic this is Algorithm 1's thin SVD of B.
+// precond      weights d_i, K = U^T U of the stored U, and
+//              M = diag(sqrt d) (I + Ubar^T Ubar)^{-1} diag(sqrt d), so that
+//              P^{-1} z = z - U M U^T z is the exact inverse of P z = z + U diag(d) U^T z.
+#include "internal.cuh"
+
+#include <cmath>
+
+namespace nys {
+
+int launch_small_gemm(nys_ctx* ctx, const double* A, int ta, const double* B, int tb, int m, int n, int k,
+                      const double* colscale, double* C);
+int sym_eig(nys_ctx* ctx, const double* G, int ell, bool use_f32, const double* info, void* work, double* Vout,
+            double* S_hat, double* scale, int* sweeps_dev);
+__global__ void shift_chol_kernel(const double* __restrict__ G2, int ell, double eps, int max_retries,
+                                  double* __restrict__ C, double* __restrict__ info);
+__global__ void form_H_kernel(const double* __restrict__ G2, int ell, const double* __restrict__ info,
+                              double* __restrict__ H);
+__global__ void tri_inv_kernel(const double* __restrict__ C, double* __restrict__ X, int n);
+__global__ void weights_kernel(const double* __restrict__ S_hat, int ell, double mu, int sqrt_shift,
+                               double* __restrict__ d, double* __restrict__ sqd, float* __restrict__ d32);
+__global__ void form_A_kernel(const double* __restrict__ K, const double* __restrict__ sqd, int ell,
+                              double* __restrict__ A);
+__global__ void chol_kernel(double* __restrict__ A, int n, double* __restrict__ info);
+__global__ void form_M_kernel(const double* __restrict__ Ainv, const double* __restrict__ sqd, int ell,
+                              double* __restrict__ M, float* __restrict__ M32);
+
+namespace {
+
+// ------------------------------------------------------------ Philox ----
+struct P4 {
+    uint32_t x, y, z, w;
+};
+
+__device__ __forceinline__ P4 philox4x32_10(P4 c, uint32_t k0, uint32_t k1) {
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        if (r > 0) {
+            k0 += 0x9E3779B9u;
+            k1 += 0xBB67AE85u;
+        }
+        const uint32_t hi0 = __umulhi(0xD2511F53u, c.x), lo0 = 0xD2511F53u * c.x;
+        const uint32_t hi1 = __umulhi(0xCD9E8D57u, c.z), lo1 = 0xCD9E8D57u * c.z;
+        c = P4{hi1 ^ c.y ^ k0, lo1, hi0 ^ c.w ^ k1, lo0};
+    }
+    return c;
+}
+
+__device__ __forceinline__ void box_muller(uint32_t a, uint32_t b, float& z0, float& z1) {
+    const float u0 = ((float)(a >> 9) + 0.5f) * 1.1920928955078125e-7f;   // 2^-23
+    const float u1 = ((float)(b >> 9) + 0.5f) * 1.1920928955078125e-7f;
+    const float rho = sqrtf(-2.0f * logf(u0));
+    float s, c;
+    sincospif(2.0f * u1, &s, &c);
+    z0 = rho * c;
+    z1 = rho * s;
+}
+__device__ __forceinline__ void box_muller(uint32_t a, uint32_t b, double& z0, double& z1) {
+    const double u0 = ((double)(a >> 9) + 0.5) * 1.1920928955078125e-7;
+    const double u1 = ((double)(b >> 9) + 0.5) * 1.1920928955078125e-7;
+    const double rho = sqrt(-2.0 * log(u0));
+    double s, c;
+    sincospi(2.0 * u1, &s, &c);
+    z0 = rho * c;
+    z1 = rho * s;
+}
+
+template <class T, class TC>
+__global__ void omega_kernel(T* __restrict__ out, int64_t total, uint64_t seed) {
+    const int64_t nblk = (total + 3) / 4;
+    const uint32_t k0 = (uint32_t)(seed & 0xffffffffu), k1 = (uint32_t)(seed >> 32);
+    for (int64_t b = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; b < nblk; b += (int64_t)gridDim.x * blockDim.x) {
+        const P4 x = philox4x32_10(P4{(uint32_t)(b & 0xffffffffu), (uint32_t)((uint64_t)b >> 32), 0u, 0u}, k0, k1);
+        TC z[4];
+        box_muller(x.x, x.y, z[0], z[1]);
+        box_muller(x.z, x.w, z[2], z[3]);
+        const int64_t e0 = 4 * b;
+#pragma unroll
+        for (int r = 0; r < 4; ++r)
+            if (e0 + r < total) stf(out + e0 + r, z[r]);
+    }
+}
+
+// --------------------------------------------------- P / P^{-1} apply ---
+constexpr int PCH = 1024;   // pixels per partial-sum block
+
+// part[b][j] = sum_{i in chunk b} U[j][i] z[i]
+template <class TU, class TZ, class TA>
+__global__ void __launch_bounds__(256) utz_kernel(const TU* __restrict__ U, const TZ* __restrict__ z, int64_t N,
+                                                  int ell, TA* __restrict__ part) {
+    __shared__ TA zs[PCH];
+    const int64_t i0 = (int64_t)blockIdx.x * PCH;
+    const int nb = gridDim.x;
+    const TZ* zb = z + (size_t)blockIdx.y * N;
+    for (int t = threadIdx.x; t < PCH; t += blockDim.x) zs[t] = (i0 + t < N) ? (TA)ldf(zb + i0 + t) : TA(0);
+    __syncthreads();
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+    const int cnt = (int)(N - i0 < (int64_t)PCH ? N - i0 : (int64_t)PCH);
+    for (int j = warp; j < ell; j += nw) {
+        const TU* uj = U + (size_t)j * N + i0;
+        TA s = TA(0);
+        for (int t = lane; t < cnt; t += 32) s = fma((TA)ldf(uj + t), zs[t], s);
+        s = warp_sum(s);
+        if (lane == 0) part[((size_t)blockIdx.y * nb + blockIdx.x) * ell + j] = s;
+    }
+}
+
+// coef[b][r] = inverse ? sum_k M[r][k] w[k] : d[r] w[r],  w = sum over partial blocks
+template <class TA, class TM>
+__global__ void __launch_bounds__(256) coef_kernel(const TA* __restrict__ part, int nb, int ell, int inverse,
+                                                   const TM* __restrict__ M, const TM* __restrict__ d,
+                                                   TA* __restrict__ coef) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    double* w = reinterpret_cast<double*>(smem_raw);
+    const int b = blockIdx.y;
+    const TA* pb = part + (size_t)b * nb * ell;
+    for (int j = threadIdx.x; j < ell; j += blockDim.x) {
+        double s = 0.0;
+        for (int k = 0; k < nb; ++k) s += (double)pb[(size_t)k * ell + j];
+        w[j] = s;
+    }
+    __syncthreads();
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+    const int r0 = blockIdx.x * 32;
+    for (int r = r0 + warp; r < min(ell, r0 + 32); r += nw) {
+        double s;
+        if (inverse) {
+            s = 0.0;
+            for (int k = lane; k < ell; k += 32) s += (double)M[(size_t)r * ell + k] * w[k];
+            s = warp_sum(s);
+        } else {
+            s = (double)d[r] * w[r];
+        }
+        if (lane == 0) coef[(size_t)b * ell + r] = (TA)s;
+    }
+}
+
+// out[i] = z[i] + sign * sum_j U[j][i] coef[j]
+template <class TU, class TZ, class TA>
+__global__ void __launch_bounds__(256) uc_kernel(const TU* __restrict__ U, const TZ* __restrict__ z, int64_t N,
+                                                 int ell, const TA* __restrict__ coef, TA sign, TZ* __restrict__ out) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    TA* c = reinterpret_cast<TA*>(smem_raw);
+    const int b = blockIdx.y;
+    for (int j = threadIdx.x; j < ell; j += blockDim.x) c[j] = coef[(size_t)b * ell + j];
+    __syncthreads();
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
+        TA s = TA(0);
+        for (int j = 0; j < ell; ++j) s = fma((TA)ldf(U + (size_t)j * N + i), c[j], s);
+        const size_t o = (size_t)b * N + i;
+        stf(out + o, (TA)ldf(z + o) + sign * s);
+    }
+}
+
+template <class TU, class TZ, class TA>
+int precond_typed(nys_ctx* ctx, const nys_precond* pc, int inverse, const void* z, void* out, int batch) {
+    const nys_precond_priv* pv = (const nys_precond_priv*)pc->priv;
+    const int64_t N = pc->N;
+    const int ell = pc->ell;
+    const int nb = (int)((N + PCH - 1) / PCH);
+    int st;
+    TA* part = (TA*)scratch(ctx, SLOT_PRECOND, ((size_t)batch * nb * ell + (size_t)batch * ell) * sizeof(TA), &st);
+    if (st) return st;
+    TA* coef = part + (size_t)batch * nb * ell;
+    cudaStream_t s = ctx->stream;
+    for (int b0 = 0; b0 < batch; b0 += 65535) {
+        const int bb = std::min(65535, batch - b0);
+        utz_kernel<TU, TZ, TA><<<dim3(nb, bb), 256, 0, s>>>((const TU*)pc->U, (const TZ*)z + (size_t)b0 * N, N, ell,
+                                                             part);
+        NYS_LAUNCH_CK(ctx);
+        if (sizeof(TA) == 8)
+            coef_kernel<TA, double><<<dim3((ell + 31) / 32, bb), 256, ell * sizeof(double), s>>>(
+                part, nb, ell, inverse, (const double*)pv->M64, (const double*)pv->d, coef);
+        else
+            coef_kernel<TA, float><<<dim3((ell + 31) / 32, bb), 256, ell * sizeof(double), s>>>(
+                part, nb, ell, inverse, (const float*)pv->M32, (const float*)pv->d32, coef);
+        NYS_LAUNCH_CK(ctx);
+        const int gx = (int)std::min<int64_t>((N + 255) / 256, 4096);
+        uc_kernel<TU, TZ, TA><<<dim3(gx, bb), 256, ell * sizeof(TA), s>>>(
+            (const TU*)pc->U, (const TZ*)z + (size_t)b0 * N, N, ell, coef, inverse ? TA(-1) : TA(1),
+            (TZ*)out + (size_t)b0 * N);
+        NYS_LAUNCH_CK(ctx);
+    }
+    return NYS_OK;
+}
+
+int precond_setup_impl(nys_ctx* ctx, nys_precond* pc, double mu, int sqrt_shift) {
+    auto* pv = (nys_precond_priv*)pc->priv;
+    const int ell = pc->ell;
+    const double sref = sqrt_shift ? std::sqrt(std::max(pc->s_last, 0.0)) : pc->s_last;
+    if (!(sref + mu > 0.0))
+        return fail(ctx, NYS_EDEGENERATE, "preconditioner: s_K%s + mu = %g is not positive",
+                    sqrt_shift ? " (square-rooted)" : "", sref + mu);
+    int st;
+    double* work = (double*)scratch(ctx, SLOT_FACTOR, (size_t)4 * ell * ell * sizeof(double) + 64, &st);
+    if (st) return st;
+    double* A = work;
+    double* Li = A + (size_t)ell * ell;
+    double* Ai = Li + (size_t)ell * ell;
+    double* info = Ai + (size_t)ell * ell;
+    cudaStream_t s = ctx->stream;
+    weights_kernel<<<(ell + 127) / 128, 128, 0, s>>>(pc->S_hat, ell, mu, sqrt_shift, pv->d, pv->sqrtd, pv->d32);
+    NYS_LAUNCH_CK(ctx);
+    form_A_kernel<<<64, 256, 0, s>>>(pv->K, pv->sqrtd, ell, A);
+    NYS_LAUNCH_CK(ctx);
+    chol_kernel<<<1, 1024, 0, s>>>(A, ell, info);
+    NYS_LAUNCH_CK(ctx);
+    tri_inv_kernel<<<ell, 32, 0, s>>>(A, Li, ell);
+    NYS_LAUNCH_CK(ctx);
+    // (I + Ubar^T Ubar)^{-1} = L^{-T} L^{-1}
+    if ((st = launch_small_gemm(ctx, Li, 1, Li, 0, ell, ell, ell, nullptr, Ai))) return st;
+    form_M_kernel<<<64, 256, 0, s>>>(Ai, pv->sqrtd, ell, pv->M64, pv->M32);
+    NYS_LAUNCH_CK(ctx);
+    double h_info[4];
+    NYS_CK(ctx, cudaMemcpyAsync(h_info, info, sizeof(h_info), cudaMemcpyDeviceToHost, s));
+    NYS_CK(ctx, cudaStreamSynchronize(s));
+    if (h_info[3] != 0.0) return fail(ctx, NYS_ENONFINITE, "preconditioner: I + Ubar^T Ubar is not positive definite");
+    pc->mu = mu;
+    pc->sqrt_shift = sqrt_shift;
+    return NYS_OK;
+}
+
+}  // namespace
+
+int precond_run(nys_ctx* ctx, const nys_precond* pc, int inverse, int dtype, const void* z, void* out, int batch) {
+    if (!pc || !pc->priv || !pc->U) return fail(ctx, NYS_EINVAL, "precond: not factored");
+    if (pc->mu != pc->mu) return fail(ctx, NYS_EINVAL, "precond: call nys_precond_setup first");
+    if (dtype == NYS_F64) {
+        if (pc->dtype != NYS_F64) return fail(ctx, NYS_EINVAL, "precond: f64 data needs an f64 factor");
+        return precond_typed<double, double, double>(ctx, pc, inverse, z, out, batch);
+    }
+    if (dtype != NYS_F32) return fail(ctx, NYS_EINVAL, "precond: data must be f32 or f64");
+    if (pc->dtype == NYS_F32) return precond_typed<float, float, float>(ctx, pc, inverse, z, out, batch);
+    if (pc->dtype == NYS_BF16) return precond_typed<__nv_bfloat16, float, float>(ctx, pc, inverse, z, out, batch);
+    return fail(ctx, NYS_EINVAL, "precond: f32 data needs an f32 or bf16 factor");
+}
+
+}  // namespace nys
+
+using namespace nys;
+
+extern "C" {
+
+int nys_sketch(nys_ctx* ctx, nys_op* op, int phi_kind, int ell, uint64_t seed, int store_dt, void* Omega, void* Y) {
+    if (!ctx || !op || !Omega || !Y) return fail(ctx, NYS_EINVAL, "nys_sketch: null argument");
+    if (ell <= 0) return fail(ctx, NYS_EINVAL, "nys_sketch: ell must be positive");
+    if (op->dtype == NYS_F64 ? store_dt != NYS_F64 : (store_dt != NYS_F32 && store_dt != NYS_BF16))
+        return fail(ctx, NYS_EINVAL, "nys_sketch: store dtype does not match the operator");
+    if (phi_kind == NYS_PHI_W_ATA_WT && op->haar_levels <= 0)
+        return fail(ctx, NYS_EINVAL, "nys_sketch: W A^T A W^T needs an operator with haar_levels");
+    cudaStream_t s = ctx->stream;
+    const int64_t total = (int64_t)ell * op->N;
+    const int grid = (int)std::min<int64_t>((total / 4 + 255) / 256 + 1, ctx->sm_count * 16);
+    if (store_dt == NYS_F64) omega_kernel<double, double><<<grid, 256, 0, s>>>((double*)Omega, total, seed);
+    else if (store_dt == NYS_F32) omega_kernel<float, float><<<grid, 256, 0, s>>>((float*)Omega, total, seed);
+    else omega_kernel<__nv_bfloat16, float><<<grid, 256, 0, s>>>((__nv_bfloat16*)Omega, total, seed);
+    NYS_LAUNCH_CK(ctx);
+    if (phi_kind == NYS_PHI_ATA) return op_run(op, 2, Omega, Y, ell, store_dt, store_dt);
+    if (phi_kind != NYS_PHI_W_ATA_WT) return fail(ctx, NYS_EINVAL, "nys_sketch: unknown phi kind");
+    // W A^T A W^T, chunked through compute-type temporaries
+    const int cdt = op->dtype;
+    const size_t es = dtype_size(cdt);
+    const int chunk = std::min(ell, 64);
+    int st;
+    char* tmp = (char*)scratch(ctx, SLOT_SKETCH, 2 * (size_t)chunk * op->N * es, &st);
+    if (st) return st;
+    char* t1 = tmp;
+    char* t2 = tmp + (size_t)chunk * op->N * es;
+    const size_t ss = dtype_size(store_dt);
+    for (int b0 = 0; b0 < ell; b0 += chunk) {
+        const int nb = std::min(chunk, ell - b0);
+        const char* om = (const char*)Omega + (size_t)b0 * op->N * ss;
+        char* yy = (char*)Y + (size_t)b0 * op->N * ss;
+        if ((st = haar_run(op, om, t1, nb, 1, store_dt, cdt))) return st;
+        if ((st = op_run(op, 2, t1, t2, nb, cdt, cdt))) return st;
+        if ((st = haar_run(op, t2, yy, nb, 0, cdt, store_dt))) return st;
+    }
+    return NYS_OK;
+}
+
+int nys_precond_release(nys_precond* pc) {
+    if (!pc || !pc->priv) return NYS_OK;
+    auto* pv = (nys_precond_priv*)pc->priv;
+    cudaDeviceSynchronize();
+    void* bufs[] = {pv->K, pv->d, pv->M64, pv->M32, pv->d32, pv->sqrtd};
+    for (void* b : bufs)
+        if (b) cudaFree(b);
+    delete pv;
+    pc->priv = nullptr;
+    return NYS_OK;
+}
+
+// allocate (or re-size) the library-owned small state of a preconditioner
+static int alloc_priv(nys_ctx* ctx, nys_precond* pc) {
+    const int ell = pc->ell;
+    if (pc->priv && ((nys_precond_priv*)pc->priv)->ell != ell) nys_precond_release(pc);
+    if (pc->priv) return NYS_OK;
+    auto* pv = new nys_precond_priv();
+    pv->ell = ell;
+    const size_t l2 = (size_t)ell * ell;
+    cudaError_t e = cudaSuccess;
+    if (e == cudaSuccess) e = cudaMalloc(&pv->K, l2 * 8);
+    if (e == cudaSuccess) e = cudaMalloc(&pv->M64, l2 * 8);
+    if (e == cudaSuccess) e = cudaMalloc(&pv->M32, l2 * 4);
+    if (e == cudaSuccess) e = cudaMalloc(&pv->d, ell * 8);
+    if (e == cudaSuccess) e = cudaMalloc(&pv->sqrtd, ell * 8);
+    if (e == cudaSuccess) e = cudaMalloc(&pv->d32, ell * 4);
+    pc->priv = pv;
+    if (e != cudaSuccess) {
+        nys_precond_release(pc);
+        return cuda_fail(ctx, e, "preconditioner state: cudaMalloc");
+    }
+    return NYS_OK;
+}
+
+int nys_factor(nys_ctx* ctx, const void* Omega, const void* Y, int in_dt, int64_t N, int ell, double eps,
+               nys_precond* pc) {
+    if (!ctx || !Omega || !Y || !pc || !pc->U || !pc->S_hat) return fail(ctx, NYS_EINVAL, "nys_factor: null argument");
+    if (N <= 0 || ell <= 0 || ell > 1024 || ell > N)
+        return fail(ctx, NYS_EINVAL, "nys_factor: need 0 < ell <= min(N, 1024)");
+    if (!(eps >= 0.0)) return fail(ctx, NYS_EINVAL, "nys_factor: eps must be >= 0");
+    const bool f64 = in_dt == NYS_F64;
+    if (f64 != (pc->dtype == NYS_F64)) return fail(ctx, NYS_EINVAL, "nys_factor: f64 data needs an f64 factor");
+    if (!f64 && in_dt != NYS_F32 && in_dt != NYS_BF16) return fail(ctx, NYS_EINVAL, "nys_factor: bad input dtype");
+    pc->N = N;
+    pc->ell = ell;
+    if (int st0 = alloc_priv(ctx, pc)) return st0;
+    auto* pv = (nys_precond_priv*)pc->priv;
+    pc->mu = NAN;
+    const int L2 = 2 * ell;
+    const size_t l2 = (size_t)ell * ell;
+    const int n = (ell + 1) & ~1;
+    int st;
+    // layout of the factor workspace (float64 unless noted)
+    // G2, C, H, Ci, T1, Gm, Vs, scale, info (16) + sweeps (16), then the eigen
+    // work area: 2 n^2 values of the Jacobi type and ell doubles
+    const size_t need = ((size_t)L2 * L2 + 6 * l2 + (size_t)ell + 32) * 8 + 2 * (size_t)n * n * 8 + 8 * (size_t)n + 256;
+    double* w = (double*)scratch(ctx, SLOT_FACTOR, need, &st);
+    if (st) return st;
+    double* G2 = w;
+    double* C = G2 + (size_t)L2 * L2;
+    double* H = C + l2;
+    double* Ci = H + l2;
+    double* T1 = Ci + l2;
+    double* Gm = T1 + l2;
+    double* Vs = Gm + l2;
+    double* scale = Vs + l2;
+    double* info = scale + ell;           // 16 doubles
+    int* sweeps = (int*)(info + 16);
+    void* ework = (void*)(info + 32);     // eigen work (2 n^2 T + n doubles)
+    cudaStream_t s = ctx->stream;
+    NYS_CK(ctx, cudaMemsetAsync(info, 0, 16 * sizeof(double), s));
+    // one Gram pass over [Omega | Y]
+    if ((st = gram_AtB(ctx, in_dt, Omega, ell, Omega, ell, N, G2, L2))) return st;
+    if ((st = gram_AtB(ctx, in_dt, Omega, ell, Y, ell, N, G2 + ell, L2))) return st;
+    if ((st = gram_AtB(ctx, in_dt, Y, ell, Y, ell, N, G2 + (size_t)ell * L2 + ell, L2))) return st;
+    shift_chol_kernel<<<1, 1024, 0, s>>>(G2, ell, eps, 8, C, info);
+    NYS_LAUNCH_CK(ctx);
+    form_H_kernel<<<64, 256, 0, s>>>(G2, ell, info, H);
+    NYS_LAUNCH_CK(ctx);
+    tri_inv_kernel<<<ell, 32, 0, s>>>(C, Ci, ell);
+    NYS_LAUNCH_CK(ctx);
+    if ((st = launch_small_gemm(ctx, Ci, 0, H, 0, ell, ell, ell, nullptr, T1))) return st;
+    if ((st = launch_small_gemm(ctx, T1, 0, Ci, 1, ell, ell, ell, nullptr, Gm))) return st;
+    if ((st = sym_eig(ctx, Gm, ell, !f64, info, ework, Vs, pc->S_hat, scale, sweeps))) return st;
+    // W = C^{-T} V S^{-1}  (into T1)
+    if ((st = launch_small_gemm(ctx, Ci, 1, Vs, 0, ell, ell, ell, scale, T1))) return st;
+    // U = (Y + v Omega) W
+    if ((st = gemm_tall(ctx, in_dt, Y, Omega, info + 1, N, ell, T1, ell, pc->dtype, pc->U))) return st;
+    // K = U^T U of the stored U
+    if ((st = gram_AtB(ctx, pc->dtype, pc->U, ell, pc->U, ell, N, pv->K, ell))) return st;
+    double h[4];
+    NYS_CK(ctx, cudaMemcpyAsync(h, info, 3 * sizeof(double), cudaMemcpyDeviceToHost, s));
+    NYS_CK(ctx, cudaMemcpyAsync(&pc->s_first, pc->S_hat, sizeof(double), cudaMemcpyDeviceToHost, s));
+    NYS_CK(ctx, cudaMemcpyAsync(&pc->s_last, pc->S_hat + ell - 1, sizeof(double), cudaMemcpyDeviceToHost, s));
+    NYS_CK(ctx, cudaStreamSynchronize(s));
+    pc->v = h[1];
+    pc->chol_retries = (int)h[2];
+    if (h[0] != 0.0) return fail(ctx, NYS_ENOTSPD, "nys_factor: Cholesky of the shifted core failed after %d retries",
+                                 pc->chol_retries);
+    if (!std::isfinite(pc->s_first) || !std::isfinite(pc->s_last))
+        return fail(ctx, NYS_ENONFINITE, "nys_factor: non-finite eigenvalues");
+    // default preconditioner set-up (skipped when s_K is zero: set mu > 0 then)
+    const double sref = std::sqrt(std::max(pc->s_last, 0.0));
+    if (sref > 0.0) return precond_setup_impl(ctx, pc, 0.0, 1);
+    return NYS_OK;
+}
+
+int nys_precond_import(nys_ctx* ctx, nys_precond* pc, double mu, int sqrt_shift) {
+    if (!ctx || !pc || !pc->U || !pc->S_hat) return fail(ctx, NYS_EINVAL, "nys_precond_import: null argument");
+    const int ell = pc->ell;
+    if (pc->N <= 0 || ell <= 0 || ell > 1024 || ell > pc->N)
+        return fail(ctx, NYS_EINVAL, "nys_precond_import: need 0 < ell <= min(N, 1024)");
+    if (pc->dtype != NYS_F32 && pc->dtype != NYS_F64 && pc->dtype != NYS_BF16)
+        return fail(ctx, NYS_EINVAL, "nys_precond_import: bad dtype");
+    if (int st = alloc_priv(ctx, pc)) return st;
+    auto* pv = (nys_precond_priv*)pc->priv;
+    pc->mu = NAN;
+    int st;
+    if ((st = gram_AtB(ctx, pc->dtype, pc->U, ell, pc->U, ell, pc->N, pv->K, ell))) return st;
+    cudaStream_t s = ctx->stream;
+    NYS_CK(ctx, cudaMemcpyAsync(&pc->s_first, pc->S_hat, sizeof(double), cudaMemcpyDeviceToHost, s));
+    NYS_CK(ctx, cudaMemcpyAsync(&pc->s_last, pc->S_hat + ell - 1, sizeof(double), cudaMemcpyDeviceToHost, s));
+    NYS_CK(ctx, cudaStreamSynchronize(s));
+    return precond_setup_impl(ctx, pc, mu, sqrt_shift ? 1 : 0);
+}
+
+int nys_precond_setup(nys_ctx* ctx, nys_precond* pc, double mu, int sqrt_shift) {
+    if (!ctx || !pc || !pc->priv) return fail(ctx, NYS_EINVAL, "nys_precond_setup: factor first");
+    return precond_setup_impl(ctx, pc, mu, sqrt_shift ? 1 : 0);
+}
+
+int precond_apply(nys_ctx* ctx, const nys_precond* pc, int inverse, int dtype, const void* z, void* out, int batch) {
+    if (!ctx || !pc || !z || !out) return fail(ctx, NYS_EINVAL, "precond_apply: null argument");
+    if (batch < 0) return fail(ctx, NYS_EINVAL, "precond_apply: negative batch");
+    if (batch == 0) return NYS_OK;
+    return precond_run(ctx, pc, inverse, dtype, z, out, batch);
+}
+
+}  // extern "C"

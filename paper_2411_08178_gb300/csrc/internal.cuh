@@ -1,0 +1,176 @@
+// Internal declarations shared by the CUDA translation units of libnys.
+// Nothing here is part of the C ABI (include/nys.h).
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include <cstdarg>
+#include <cstdint>
+#include <cstdio>
+#include <string>
+#include <vector>
+
+#include "../../include/nys.h"
+
+namespace nys {
+
+// ----------------------------------------------------------- numerics ----
+__device__ __forceinline__ float ldf(const float* p) { return *p; }
+__device__ __forceinline__ double ldf(const double* p) { return *p; }
+__device__ __forceinline__ float ldf(const __nv_bfloat16* p) { return __bfloat162float(*p); }
+__device__ __forceinline__ void stf(float* p, float v) { *p = v; }
+__device__ __forceinline__ void stf(double* p, double v) { *p = v; }
+__device__ __forceinline__ void stf(__nv_bfloat16* p, float v) { *p = __float2bfloat16_rn(v); }
+__device__ __forceinline__ void stf(float* p, double v) { *p = (float)v; }
+__device__ __forceinline__ void stf(__nv_bfloat16* p, double v) { *p = __float2bfloat16_rn((float)v); }
+
+// compute type: double for double storage, float otherwise
+template <class T> struct Comp { using type = float; };
+template <> struct Comp<double> { using type = double; };
+
+template <class T>
+__device__ __forceinline__ T warp_sum(T v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// Sum over the block; `sh` needs blockDim.x/32 entries.  Result valid in
+// every thread.  Must be called by all threads of the block.
+template <class T>
+__device__ __forceinline__ T block_sum(T v, T* sh) {
+    v = warp_sum(v);
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const int nw = (blockDim.x + 31) >> 5;
+    __syncthreads();
+    if (lane == 0) sh[wid] = v;
+    __syncthreads();
+    T r = (threadIdx.x < (unsigned)nw) ? sh[threadIdx.x] : T(0);
+    if (wid == 0) r = warp_sum(r);
+    if (threadIdx.x == 0) sh[0] = r;
+    __syncthreads();
+    r = sh[0];
+    __syncthreads();
+    return r;
+}
+
+__host__ __device__ __forceinline__ int pmod(int a, int n) {
+    int r = a % n;
+    return r < 0 ? r + n : r;
+}
+
+inline size_t dtype_size(int dt) { return dt == NYS_F64 ? 8 : (dt == NYS_BF16 ? 2 : 4); }
+
+}  // namespace nys
+
+// ----------------------------------------------------------- handles -----
+struct nys_ctx {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    int sm_count = 152;
+    std::string err;
+    // independent growable scratch regions (see nys::scratch)
+    void* slot_ptr[12] = {nullptr};
+    size_t slot_bytes[12] = {0};
+};
+
+struct nys_op {
+    nys_ctx* ctx = nullptr;
+    int kind = 0, dtype = 0, n1 = 0, n2 = 0;
+    int64_t N = 0, M = 0;
+    int haar_levels = 0;
+    // blur
+    int kh = 0, kw = 0, decim = 1;
+    std::vector<double> h;            // kh*kw
+    bool separable = false;
+    // device tap tables (dtype of the op): see blur.cu
+    void* taps_fwd = nullptr;         // H   (2-D kernel or [col taps | row taps])
+    void* taps_adj = nullptr;         // H^T
+    void* taps_nrm = nullptr;         // H^T H (separable only)
+    int Lc_f = 0, Lr_f = 0, cc_f = 0, cr_f = 0;   // separable forward lengths/centres
+    int Lc_n = 0, Lr_n = 0, cc_n = 0, cr_n = 0;   // separable normal
+    // radon
+    int n_angles = 0, n_bins = 0;
+    double span = 0.0;
+    void* rtab = nullptr;             // per-angle tables, see radon.cu
+    // intermediate buffer for two-pass normals (M per image, `chunk` images)
+    void* inter = nullptr;
+    int chunk = 0;
+};
+
+namespace nys {
+
+// record an error on ctx (and globally) and return `code`
+int fail(nys_ctx* ctx, int code, const char* fmt, ...);
+int cuda_fail(nys_ctx* ctx, cudaError_t e, const char* what);
+
+// Scratch regions: each slot is an independent buffer that grows on demand.
+enum Slot {
+    SLOT_PRECOND = 0,   // partial sums of U^T z
+    SLOT_PROX = 1,      // dual variables of prox_tv / prox_hs
+    SLOT_FACTOR = 2,    // ell x ell work in nys_factor
+    SLOT_SSN = 3,       // semi-smooth Newton state
+    SLOT_MISC = 4,      // reductions, converted GEMM operands
+    SLOT_OPTMP = 5,     // Haar ping-pong buffers
+    SLOT_SKETCH = 6,    // W^T Omega and A^T A W^T Omega in nys_sketch
+    SLOT_GRAM = 7,      // split-K partial tiles of gram_AtB
+    SLOT_SOLVER = 8,    // solver temporaries
+    SLOT_COUNT = 9
+};
+void* scratch(nys_ctx* ctx, int slot, size_t bytes, int* status);
+
+#define NYS_CK(ctx, call)                                              \
+    do {                                                               \
+        cudaError_t e_ = (call);                                       \
+        if (e_ != cudaSuccess) return nys::cuda_fail((ctx), e_, #call); \
+    } while (0)
+
+#define NYS_LAUNCH_CK(ctx)                                             \
+    do {                                                               \
+        cudaError_t e_ = cudaGetLastError();                           \
+        if (e_ != cudaSuccess) return nys::cuda_fail((ctx), e_, "kernel launch"); \
+    } while (0)
+
+// ------------------------------------------------ internal launch API ----
+// operators (blur.cu, radon.cu, haar.cu)
+int blur_setup(nys_op* op);
+int blur_run(nys_op* op, int which /*0 fwd,1 adj,2 normal*/, const void* x, void* y, int batch,
+             int in_dtype, int out_dtype);
+int decim_run(nys_op* op, int which, const void* x, void* y, int batch, int in_dtype, int out_dtype);
+int radon_setup(nys_op* op);
+int radon_run(nys_op* op, int which, const void* x, void* y, int batch, int in_dtype, int out_dtype);
+int haar_run(nys_op* op, const void* in, void* out, int batch, int inverse, int in_dtype, int out_dtype);
+// generic: which = 0 A, 1 A^T, 2 A^T A ; dtypes may differ from op dtype (bf16 io)
+int op_run(nys_op* op, int which, const void* x, void* y, int batch, int in_dtype, int out_dtype);
+
+// dense helpers (dense.cu)
+// C[p x q] (double) = A^T B, A: N x p, B: N x q (column j at offset j*N)
+int gram_AtB(nys_ctx* ctx, int dtype, const void* A, int p, const void* B, int q, int64_t N,
+             double* C, int ldc);
+// out (N x q, dtype out_dt) = (A + alpha*A2) W, A/A2: N x k of in_dt, W: k x q double (row-major k x q)
+int gemm_tall(nys_ctx* ctx, int in_dt, const void* A, const void* A2, const double* alpha_dev, int64_t N,
+              int k, const double* W, int q, int out_dt, void* out);
+
+// reductions (reduce.cu)
+int norm2_diff(nys_ctx* ctx, int dtype, int64_t n, const void* a, const void* b, double** out_dev);
+
+}  // namespace nys
+
+// precond internal state (precond.cu)
+struct nys_precond_priv {
+    double* K = nullptr;      // ell x ell, U^T U
+    double* d = nullptr;      // ell weights
+    double* M64 = nullptr;    // ell x ell, inverse-apply matrix
+    float* M32 = nullptr;
+    float* d32 = nullptr;
+    double* sqrtd = nullptr;  // ell, sqrt(d) (Ubar scaling)
+    int ell = 0;
+};
+
+namespace nys {
+// P^{-1} or P applied to z (dtype f32/f64); out may alias z.  If `lt_src` is
+// not null the input is computed on the fly (used by the fused prox kernels).
+int precond_run(nys_ctx* ctx, const nys_precond* pc, int inverse, int dtype, const void* z,
+                void* out, int batch);
+}  // namespace nys

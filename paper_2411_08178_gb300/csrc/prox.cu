@@ -1,0 +1,538 @@
+// Weighted proximal mappings in the P metric (Sec. III-B).
+//
+// prox_tv / prox_hs: the dual scheme for lambda_bar ||L x||_{1,phi} with
+// C = R^N.  The dual objective ||s - lb P^{-1} L^T Q||_P^2 over the unit ball of
+// the dual norm has gradient -2 lb L x(Q), x(Q) = s - lb P^{-1} L^T Q, and
+// Lipschitz constant 2 lb^2 ||L||^2 (sigma_min(P) = 1), so each APG (FISTA)
+// step is
+//     x   = s - lb P^{-1} L^T R
+//     Q'  = Proj(R + L x / (lb ||L||^2))
+//     R   = Q' + beta_k (Q' - Q)           beta_k from the fixed t_k sequence
+// L = first differences (anisotropic TV, ||L||^2 = 8, Proj = clip to [-1,1])
+// or second differences (Hessian Schatten-1, ||L||^2 = 32 in the inner
+// product q11 v11 + 2 q12 v12 + q22 v22, Proj = clip the eigenvalues of each
+// symmetric 2 x 2 block to [-1, 1]).  Kernels: one stencil pass for L^T R
+// (fused with x = s - lb L^T R when P = I), P^{-1} through precond_run, and
+// one pass that forms L x, projects and extrapolates.  beta_k depends only on
+// k, so it is a kernel argument and no host synchronisation is needed.
+//
+// prox_wavelet: Theorem 1 with D = I, W = I + Ubar Ubar^T: out =
+// T_tau(s - Ubar gamma*), gamma* solving F(gamma) = Ubar^T (s - T_tau(s - Ubar
+// gamma)) + gamma = 0 by semi-smooth Newton with step halving.  The Newton
+// state machine runs on the device: an evaluation pass over the pixels
+// computes F (float64) and the generalised Jacobian J = I + Ubar_S^T Ubar_S on
+// the support S = {|z| > tau} (float32 partial sums: J only steers the Newton
+// direction, F decides the solution), and a one-CTA pass accepts or halves
+// the step and solves J d = -F by Cholesky.
+#include "internal.cuh"
+#include "chol.cuh"
+
+#include <cmath>
+
+namespace nys {
+
+namespace {
+
+// ----------------------------------------------------------- stencils ----
+template <class T>
+__device__ __forceinline__ T at(const T* p, int i, int j, int n1, int n2) {
+    return p[(size_t)pmod(i, n1) * n2 + pmod(j, n2)];
+}
+
+// L^T Q at pixel (i, j)
+template <class T, int REG>
+__device__ __forceinline__ typename Comp<T>::type lt_q(const T* __restrict__ Q, int i, int j, int n1, int n2) {
+    using TC = typename Comp<T>::type;
+    const size_t N = (size_t)n1 * n2;
+    if (REG == NYS_REG_TV) {
+        const T* q1 = Q;
+        const T* q2 = Q + N;
+        return (TC)at(q1, i, j, n1, n2) - (TC)at(q1, i + 1, j, n1, n2) + (TC)at(q2, i, j, n1, n2) -
+               (TC)at(q2, i, j + 1, n1, n2);
+    } else {
+        const T* q11 = Q;
+        const T* q12 = Q + N;
+        const T* q22 = Q + 2 * N;
+        const TC a11 = (TC)at(q11, i - 1, j, n1, n2) - TC(2) * (TC)at(q11, i, j, n1, n2) + (TC)at(q11, i + 1, j, n1, n2);
+        const TC a22 = (TC)at(q22, i, j - 1, n1, n2) - TC(2) * (TC)at(q22, i, j, n1, n2) + (TC)at(q22, i, j + 1, n1, n2);
+        const TC a12 = TC(0.25) * ((TC)at(q12, i + 1, j + 1, n1, n2) - (TC)at(q12, i + 1, j - 1, n1, n2) -
+                                   (TC)at(q12, i - 1, j + 1, n1, n2) + (TC)at(q12, i - 1, j - 1, n1, n2));
+        return a11 + TC(2) * a12 + a22;
+    }
+}
+
+// out = base - lb * L^T Q   (base may be null -> out = L^T Q, lb ignored)
+template <class T, int REG>
+__global__ void lt_kernel(const T* __restrict__ Q, const T* __restrict__ base, typename Comp<T>::type lb, int n1,
+                          int n2, T* __restrict__ out) {
+    using TC = typename Comp<T>::type;
+    const int64_t N = (int64_t)n1 * n2;
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < N; t += (int64_t)gridDim.x * blockDim.x) {
+        const int i = (int)(t / n2), j = (int)(t - (int64_t)i * n2);
+        const TC g = lt_q<T, REG>(Q, i, j, n1, n2);
+        out[t] = base ? (T)((TC)base[t] - lb * g) : (T)g;
+    }
+}
+
+// x = s - lb * pg   (pg = P^{-1} L^T R)
+template <class T>
+__global__ void axpy_kernel(const T* __restrict__ s, const T* __restrict__ pg, typename Comp<T>::type lb, int64_t N,
+                            T* __restrict__ x) {
+    using TC = typename Comp<T>::type;
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < N; t += (int64_t)gridDim.x * blockDim.x)
+        x[t] = (T)((TC)s[t] - lb * (TC)pg[t]);
+}
+
+// Q' = Proj(R + step * L x); R <- Q' + beta (Q' - Qp); Qp <- Q'
+template <class T, int REG>
+__global__ void dual_update_kernel(const T* __restrict__ x, T* __restrict__ R, T* __restrict__ Qp,
+                                   typename Comp<T>::type step, typename Comp<T>::type beta, int n1, int n2) {
+    using TC = typename Comp<T>::type;
+    const int64_t N = (int64_t)n1 * n2;
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < N; t += (int64_t)gridDim.x * blockDim.x) {
+        const int i = (int)(t / n2), j = (int)(t - (int64_t)i * n2);
+        const TC xc = (TC)x[t];
+        if (REG == NYS_REG_TV) {
+            const TC v1 = xc - (TC)at(x, i - 1, j, n1, n2);
+            const TC v2 = xc - (TC)at(x, i, j - 1, n1, n2);
+            const TC n1v = fmin(TC(1), fmax(TC(-1), (TC)R[t] + step * v1));
+            const TC n2v = fmin(TC(1), fmax(TC(-1), (TC)R[t + N] + step * v2));
+            const TC o1 = (TC)Qp[t], o2 = (TC)Qp[t + N];
+            R[t] = (T)(n1v + beta * (n1v - o1));
+            R[t + N] = (T)(n2v + beta * (n2v - o2));
+            Qp[t] = (T)n1v;
+            Qp[t + N] = (T)n2v;
+        } else {
+            const TC v11 = (TC)at(x, i - 1, j, n1, n2) - TC(2) * xc + (TC)at(x, i + 1, j, n1, n2);
+            const TC v22 = (TC)at(x, i, j - 1, n1, n2) - TC(2) * xc + (TC)at(x, i, j + 1, n1, n2);
+            const TC v12 = TC(0.25) * ((TC)at(x, i + 1, j + 1, n1, n2) - (TC)at(x, i + 1, j - 1, n1, n2) -
+                                       (TC)at(x, i - 1, j + 1, n1, n2) + (TC)at(x, i - 1, j - 1, n1, n2));
+            const TC a = (TC)R[t] + step * v11;
+            const TC b = (TC)R[t + N] + step * v12;
+            const TC c = (TC)R[t + 2 * N] + step * v22;
+            // eigen-clip of [[a, b], [b, c]]
+            const TC m = TC(0.5) * (a + c), h = TC(0.5) * (a - c);
+            const TC r = sqrt(h * h + b * b);
+            const TC l1 = fmin(TC(1), fmax(TC(-1), m + r));
+            const TC l2 = fmin(TC(1), fmax(TC(-1), m - r));
+            const TC mp = TC(0.5) * (l1 + l2), dp = TC(0.5) * (l1 - l2);
+            TC pa, pb, pc;
+            if (r > TC(0)) {
+                pa = mp + dp * (h / r);
+                pb = dp * (b / r);
+                pc = mp - dp * (h / r);
+            } else {
+                pa = mp;
+                pb = TC(0);
+                pc = mp;
+            }
+            const TC oa = (TC)Qp[t], ob = (TC)Qp[t + N], oc = (TC)Qp[t + 2 * N];
+            R[t] = (T)(pa + beta * (pa - oa));
+            R[t + N] = (T)(pb + beta * (pb - ob));
+            R[t + 2 * N] = (T)(pc + beta * (pc - oc));
+            Qp[t] = (T)pa;
+            Qp[t + N] = (T)pb;
+            Qp[t + 2 * N] = (T)pc;
+        }
+    }
+}
+
+template <class T, int REG>
+int prox_dual_typed(nys_ctx* ctx, const nys_precond* pc, double lb, int n_inner, int n1, int n2, const T* s, T* out,
+                    T* Q) {
+    using TC = typename Comp<T>::type;
+    const int G = REG == NYS_REG_TV ? 2 : 3;
+    const double normL2 = REG == NYS_REG_TV ? 8.0 : 32.0;
+    const int64_t N = (int64_t)n1 * n2;
+    int st;
+    T* work = (T*)scratch(ctx, SLOT_PROX, ((size_t)2 * G * N + 2 * N) * sizeof(T), &st);
+    if (st) return st;
+    T* R = work;
+    T* Qp = R + G * N;
+    T* x = Qp + G * N;
+    T* g = x + N;
+    cudaStream_t sm = ctx->stream;
+    NYS_CK(ctx, cudaMemcpyAsync(R, Q, sizeof(T) * G * N, cudaMemcpyDeviceToDevice, sm));
+    NYS_CK(ctx, cudaMemcpyAsync(Qp, Q, sizeof(T) * G * N, cudaMemcpyDeviceToDevice, sm));
+    const int grid = (int)std::min<int64_t>((N + 255) / 256, ctx->sm_count * 8);
+    const int dt = sizeof(T) == 8 ? NYS_F64 : NYS_F32;
+    const TC step = (TC)(1.0 / (lb * normL2));
+    double t = 1.0;
+    for (int k = 0; k < n_inner; ++k) {
+        if (pc) {
+            lt_kernel<T, REG><<<grid, 256, 0, sm>>>(R, nullptr, TC(0), n1, n2, g);
+            NYS_LAUNCH_CK(ctx);
+            if ((st = precond_run(ctx, pc, 1, dt, g, g, 1))) return st;
+            axpy_kernel<T><<<grid, 256, 0, sm>>>(s, g, (TC)lb, N, x);
+        } else {
+            lt_kernel<T, REG><<<grid, 256, 0, sm>>>(R, s, (TC)lb, n1, n2, x);
+        }
+        NYS_LAUNCH_CK(ctx);
+        const double tn = 0.5 * (1.0 + std::sqrt(1.0 + 4.0 * t * t));
+        const double beta = (t - 1.0) / tn;
+        t = tn;
+        dual_update_kernel<T, REG><<<grid, 256, 0, sm>>>(x, R, Qp, step, (TC)beta, n1, n2);
+        NYS_LAUNCH_CK(ctx);
+    }
+    // Q_io <- last Q; out = s - lb P^{-1} L^T Q
+    NYS_CK(ctx, cudaMemcpyAsync(Q, Qp, sizeof(T) * G * N, cudaMemcpyDeviceToDevice, sm));
+    if (pc) {
+        lt_kernel<T, REG><<<grid, 256, 0, sm>>>(Qp, nullptr, TC(0), n1, n2, g);
+        NYS_LAUNCH_CK(ctx);
+        if ((st = precond_run(ctx, pc, 1, dt, g, g, 1))) return st;
+        axpy_kernel<T><<<grid, 256, 0, sm>>>(s, g, (TC)lb, N, out);
+    } else {
+        lt_kernel<T, REG><<<grid, 256, 0, sm>>>(Qp, s, (TC)lb, n1, n2, out);
+    }
+    NYS_LAUNCH_CK(ctx);
+    return NYS_OK;
+}
+
+// ------------------------------------------------------- wavelet SSN ----
+constexpr int SCH = 128;     // pixels per evaluation block
+constexpr int SMAXL = 128;   // largest sketch size of the Newton solver
+
+struct SsnState {
+    double nF;        // ||F|| at the accepted gamma
+    double a;         // current step fraction
+    double scale;     // 1 + ||Ubar^T s||
+    int done;         // 1 = finished
+    int first;        // 1 = no accepted point yet
+    int tries;        // step halvings at the current Newton step
+    int newton;       // Newton steps taken
+    int converged;
+};
+
+template <class T>
+__device__ __forceinline__ T soft(T z, T tau) {
+    const T a = fabs(z) - tau;
+    return a > T(0) ? copysign(a, z) : T(0);
+}
+
+// Evaluation at gamma_trial: partial F, partial J (upper triangle, float),
+// partial Ubar^T s.  Ubar[j][i] = sqrtd[j] * U[j][i].
+template <class T>
+__global__ void __launch_bounds__(256) ssn_eval_kernel(const T* __restrict__ U, const double* __restrict__ sqd,
+                                                       const T* __restrict__ s, int64_t N, int ell, double tau,
+                                                       const double* __restrict__ gtrial,
+                                                       const SsnState* __restrict__ state, double* __restrict__ Fp,
+                                                       double* __restrict__ Sp, float* __restrict__ Jp) {
+    if (state->done) return;
+    // dynamic shared memory: rr, ss (SCH doubles each), gs, sd (ell doubles
+    // each), then the masked Ubar chunk ub (ell x (SCH + 1) floats)
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    double* rr = reinterpret_cast<double*>(smem_raw);
+    double* ss = rr + SCH;
+    double* gs = ss + SCH;
+    double* sd = gs + ell;
+    float* ubf = reinterpret_cast<float*>(sd + ell);
+    auto ub = [&](int j, int t) -> float& { return ubf[(size_t)j * (SCH + 1) + t]; };
+    const int64_t i0 = (int64_t)blockIdx.x * SCH;
+    const int cnt = (int)(N - i0 < (int64_t)SCH ? N - i0 : (int64_t)SCH);
+    for (int j = threadIdx.x; j < ell; j += blockDim.x) gs[j] = gtrial[j], sd[j] = sqd[j];
+    __syncthreads();
+    // z = s - Ubar gamma per pixel (one thread per pixel of the chunk)
+    for (int t = threadIdx.x; t < SCH; t += blockDim.x) {
+        double r = 0.0, sv = 0.0;
+        bool m = false;
+        if (t < cnt) {
+            sv = (double)s[i0 + t];
+            double z = sv;
+            for (int j = 0; j < ell; ++j) z -= sd[j] * (double)U[(size_t)j * N + i0 + t] * gs[j];
+            r = sv - soft(z, tau);
+            m = fabs(z) > tau;
+        }
+        rr[t] = r;
+        ss[t] = sv;
+        for (int j = 0; j < ell; ++j)
+            ub(j, t) = (m && t < cnt) ? (float)(sd[j] * (double)U[(size_t)j * N + i0 + t]) : 0.0f;
+    }
+    __syncthreads();
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+    double* Fb = Fp + (size_t)blockIdx.x * ell;
+    double* Sb = Sp + (size_t)blockIdx.x * ell;
+    for (int j = warp; j < ell; j += nw) {
+        double f = 0.0, sv = 0.0;
+        for (int t = lane; t < cnt; t += 32) {
+            const double u = sd[j] * (double)U[(size_t)j * N + i0 + t];
+            f += u * rr[t];
+            sv += u * ss[t];
+        }
+        f = warp_sum(f);
+        sv = warp_sum(sv);
+        if (lane == 0) Fb[j] = f, Sb[j] = sv;
+    }
+    float* Jb = Jp + (size_t)blockIdx.x * ell * ell;
+    for (int e = threadIdx.x; e < ell * ell; e += blockDim.x) {
+        const int j = e / ell, k = e - j * ell;
+        if (k < j) continue;
+        float acc = 0.0f;
+        for (int t = 0; t < cnt; ++t) acc = fmaf(ub(j, t), ub(k, t), acc);
+        Jb[e] = acc;
+    }
+}
+
+// One CTA: reduce partials at gamma_trial and run the accept / halve logic.
+__global__ void __launch_bounds__(1024) ssn_step_kernel(int nb, int ell, double tol, int max_newton,
+                                                        const double* __restrict__ Fp, const double* __restrict__ Sp,
+                                                        const float* __restrict__ Jp, double* __restrict__ gamma,
+                                                        double* __restrict__ gtrial, double* __restrict__ dir,
+                                                        double* __restrict__ Fcur, double* __restrict__ Jw,
+                                                        SsnState* __restrict__ st) {
+    if (st->done) return;
+    __shared__ double F[SMAXL];
+    __shared__ double sh[32];
+    __shared__ int flag;
+    __shared__ int accept;
+    for (int j = threadIdx.x; j < ell; j += blockDim.x) {
+        double f = 0.0, sv = 0.0;
+        for (int b = 0; b < nb; ++b) f += Fp[(size_t)b * ell + j], sv += Sp[(size_t)b * ell + j];
+        F[j] = f + gtrial[j];
+        if (st->first) Fcur[j] = sv;   // stash Ubar^T s for the scale below
+    }
+    __syncthreads();
+    double n2 = 0.0;
+    for (int j = threadIdx.x; j < ell; j += blockDim.x) n2 += F[j] * F[j];
+    n2 = block_sum(n2, sh);
+    const double nF = sqrt(n2);
+    if (threadIdx.x == 0) {
+        if (st->first) {
+            double s2 = 0.0;
+            for (int j = 0; j < ell; ++j) s2 += Fcur[j] * Fcur[j];
+            st->scale = 1.0 + sqrt(s2);
+        }
+        // accept when first, improved, or after the 11th trial of this step
+        accept = st->first || nF < st->nF || st->tries >= 10;
+    }
+    __syncthreads();
+    if (!accept) {
+        if (threadIdx.x == 0) {
+            st->tries += 1;
+            st->a *= 0.5;
+        }
+        __syncthreads();
+        for (int j = threadIdx.x; j < ell; j += blockDim.x) gtrial[j] = gamma[j] + st->a * dir[j];
+        return;
+    }
+    // accepted: gamma <- trial, J <- I + sum of partials
+    for (int j = threadIdx.x; j < ell; j += blockDim.x) gamma[j] = gtrial[j], Fcur[j] = F[j];
+    for (int e = threadIdx.x; e < ell * ell; e += blockDim.x) {
+        const int j = e / ell, k = e - j * ell;
+        const int a = min(j, k), b = max(j, k);
+        double v = 0.0;
+        for (int q = 0; q < nb; ++q) v += (double)Jp[(size_t)q * ell * ell + (size_t)a * ell + b];
+        Jw[e] = v + (j == k ? 1.0 : 0.0);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        if (!st->first) st->newton += 1;
+        st->first = 0;
+        st->nF = nF;
+        st->tries = 0;
+        st->a = 1.0;
+        if (nF <= tol * st->scale) st->done = 1, st->converged = 1;
+        else if (st->newton >= max_newton) st->done = 1;
+    }
+    __syncthreads();
+    if (st->done) return;
+    // Newton direction: J d = -F (Cholesky, forward and back substitution)
+    const bool ok = block_cholesky(Jw, ell, &flag);
+    if (!ok) {
+        if (threadIdx.x == 0) st->done = 1;
+        return;
+    }
+    if (threadIdx.x == 0) {
+        for (int i = 0; i < ell; ++i) {
+            double v = -F[i];
+            for (int k = 0; k < i; ++k) v -= Jw[(size_t)i * ell + k] * dir[k];
+            dir[i] = v / Jw[(size_t)i * ell + i];
+        }
+        for (int i = ell - 1; i >= 0; --i) {
+            double v = dir[i];
+            for (int k = i + 1; k < ell; ++k) v -= Jw[(size_t)k * ell + i] * dir[k];
+            dir[i] = v / Jw[(size_t)i * ell + i];
+        }
+    }
+    __syncthreads();
+    for (int j = threadIdx.x; j < ell; j += blockDim.x) gtrial[j] = gamma[j] + dir[j];
+}
+
+template <class T>
+__global__ void ssn_final_kernel(const T* __restrict__ U, const double* __restrict__ sqd, const T* __restrict__ s,
+                                 int64_t N, int ell, double tau, const double* __restrict__ gamma, T* __restrict__ out) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
+        double z = (double)s[i];
+        for (int j = 0; j < ell; ++j) z -= sqd[j] * (double)U[(size_t)j * N + i] * gamma[j];
+        out[i] = (T)soft(z, tau);
+    }
+}
+
+template <class T>
+__global__ void soft_kernel(const T* __restrict__ s, int64_t N, double tau, T* __restrict__ out) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x)
+        out[i] = (T)soft((double)s[i], tau);
+}
+
+__global__ void ssn_init_kernel(SsnState* st, const double* gamma_in, double* gamma, double* gtrial, int ell) {
+    for (int j = threadIdx.x; j < ell; j += blockDim.x) {
+        const double g = gamma_in ? gamma_in[j] : 0.0;
+        gamma[j] = g;
+        gtrial[j] = g;
+    }
+    if (threadIdx.x == 0) {
+        st->nF = 0.0;
+        st->a = 1.0;
+        st->scale = 1.0;
+        st->done = 0;
+        st->first = 1;
+        st->tries = 0;
+        st->newton = 0;
+        st->converged = 0;
+    }
+}
+
+}  // namespace
+
+// Semi-smooth Newton prox; `max_evals` evaluation/step pairs are launched
+// (later ones exit at once when done).  If `sync_until_done`, the host keeps
+// launching batches until the device reports completion.
+template <class T>
+int ssn_run(nys_ctx* ctx, const nys_precond* pc, double tau, int64_t N, const T* s, T* out, double* gamma_io,
+            int max_newton, int evals_per_batch, bool sync_until_done, nys_prox_info* info) {
+    const int ell = pc->ell;
+    if (ell > SMAXL) return fail(ctx, NYS_EINVAL, "prox_wavelet: sketch size above %d is not supported", SMAXL);
+    const auto* pv = (const nys_precond_priv*)pc->priv;
+    const int nb = (int)((N + SCH - 1) / SCH);
+    int st;
+    const size_t need = sizeof(SsnState) + 64 + (size_t)(6 * ell + ell * ell) * 8 + (size_t)nb * ell * 16 +
+                        (size_t)nb * ell * ell * 4;
+    char* w = (char*)scratch(ctx, SLOT_SSN, need, &st);
+    if (st) return st;
+    SsnState* state = (SsnState*)w;
+    double* gamma = (double*)(w + ((sizeof(SsnState) + 63) & ~size_t(63)));
+    double* gtrial = gamma + ell;
+    double* dir = gtrial + ell;
+    double* Fcur = dir + ell;
+    double* Jw = Fcur + ell;
+    double* Fp = Jw + (size_t)ell * ell;
+    double* Sp = Fp + (size_t)nb * ell;
+    float* Jp = (float*)(Sp + (size_t)nb * ell);
+    cudaStream_t sm = ctx->stream;
+    const double tol = sizeof(T) == 8 ? 1e-12 : 1e-6;
+    ssn_init_kernel<<<1, 256, 0, sm>>>(state, gamma_io, gamma, gtrial, ell);
+    NYS_LAUNCH_CK(ctx);
+    const T* U = (const T*)pc->U;
+    const size_t esm = (size_t)(2 * SCH + 2 * ell) * sizeof(double) + (size_t)ell * (SCH + 1) * sizeof(float);
+    if (esm > 48 * 1024)
+        NYS_CK(ctx, cudaFuncSetAttribute(ssn_eval_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)esm));
+    int launched = 0;
+    const int max_evals = max_newton * 12 + 1;
+    while (true) {
+        for (int e = 0; e < evals_per_batch; ++e) {
+            ssn_eval_kernel<T><<<nb, 256, esm, sm>>>(U, pv->sqrtd, s, N, ell, tau, gtrial, state, Fp, Sp, Jp);
+            NYS_LAUNCH_CK(ctx);
+            ssn_step_kernel<<<1, 1024, 0, sm>>>(nb, ell, tol, max_newton, Fp, Sp, Jp, gamma, gtrial, dir, Fcur, Jw,
+                                                state);
+            NYS_LAUNCH_CK(ctx);
+        }
+        launched += evals_per_batch;
+        if (!sync_until_done) break;
+        SsnState h;
+        NYS_CK(ctx, cudaMemcpyAsync(&h, state, sizeof(h), cudaMemcpyDeviceToHost, sm));
+        NYS_CK(ctx, cudaStreamSynchronize(sm));
+        if (h.done || launched >= max_evals) break;
+    }
+    const int grid = (int)std::min<int64_t>((N + 255) / 256, ctx->sm_count * 8);
+    ssn_final_kernel<T><<<grid, 256, 0, sm>>>(U, pv->sqrtd, s, N, ell, tau, gamma, out);
+    NYS_LAUNCH_CK(ctx);
+    if (gamma_io) NYS_CK(ctx, cudaMemcpyAsync(gamma_io, gamma, ell * sizeof(double), cudaMemcpyDeviceToDevice, sm));
+    if (info) {
+        SsnState h;
+        NYS_CK(ctx, cudaMemcpyAsync(&h, state, sizeof(h), cudaMemcpyDeviceToHost, sm));
+        NYS_CK(ctx, cudaStreamSynchronize(sm));
+        info->iterations = h.newton;
+        info->converged = h.converged;
+        info->residual = h.nF;
+    }
+    return NYS_OK;
+}
+
+template int ssn_run<float>(nys_ctx*, const nys_precond*, double, int64_t, const float*, float*, double*, int, int,
+                            bool, nys_prox_info*);
+template int ssn_run<double>(nys_ctx*, const nys_precond*, double, int64_t, const double*, double*, double*, int, int,
+                             bool, nys_prox_info*);
+
+template <class T>
+int soft_run(nys_ctx* ctx, double tau, int64_t N, const T* s, T* out) {
+    const int grid = (int)std::min<int64_t>((N + 255) / 256, ctx->sm_count * 8);
+    soft_kernel<T><<<grid, 256, 0, ctx->stream>>>(s, N, tau, out);
+    NYS_LAUNCH_CK(ctx);
+    return NYS_OK;
+}
+template int soft_run<float>(nys_ctx*, double, int64_t, const float*, float*);
+template int soft_run<double>(nys_ctx*, double, int64_t, const double*, double*);
+
+int prox_dual_run(nys_ctx* ctx, const nys_precond* pc, int reg, double lb, int n_inner, int dtype, int n1, int n2,
+                  const void* s, void* out, void* Q) {
+    if (dtype == NYS_F64) {
+        if (reg == NYS_REG_TV)
+            return prox_dual_typed<double, NYS_REG_TV>(ctx, pc, lb, n_inner, n1, n2, (const double*)s, (double*)out,
+                                                       (double*)Q);
+        return prox_dual_typed<double, NYS_REG_HS>(ctx, pc, lb, n_inner, n1, n2, (const double*)s, (double*)out,
+                                                   (double*)Q);
+    }
+    if (reg == NYS_REG_TV)
+        return prox_dual_typed<float, NYS_REG_TV>(ctx, pc, lb, n_inner, n1, n2, (const float*)s, (float*)out,
+                                                  (float*)Q);
+    return prox_dual_typed<float, NYS_REG_HS>(ctx, pc, lb, n_inner, n1, n2, (const float*)s, (float*)out, (float*)Q);
+}
+
+}  // namespace nys
+
+using namespace nys;
+
+extern "C" {
+
+static int check_prox(nys_ctx* ctx, const nys_precond* pc, int dtype, int64_t N, const void* s, const void* out) {
+    if (!ctx || !s || !out) return fail(ctx, NYS_EINVAL, "prox: null argument");
+    if (dtype != NYS_F32 && dtype != NYS_F64) return fail(ctx, NYS_EINVAL, "prox: dtype must be f32 or f64");
+    if (pc) {
+        if (!pc->priv) return fail(ctx, NYS_EINVAL, "prox: preconditioner not factored");
+        if (pc->N != N) return fail(ctx, NYS_EINVAL, "prox: preconditioner size %lld != %lld", (long long)pc->N,
+                                    (long long)N);
+        if (pc->mu != pc->mu) return fail(ctx, NYS_EINVAL, "prox: call nys_precond_setup first");
+    }
+    return NYS_OK;
+}
+
+int prox_tv(nys_ctx* ctx, const nys_precond* pc, double lb, int n_inner, int dtype, int n1, int n2, const void* s,
+            void* out, void* Q) {
+    if (int st = check_prox(ctx, pc, dtype, (int64_t)n1 * n2, s, out)) return st;
+    if (!Q || n1 <= 0 || n2 <= 0 || n_inner < 0 || !(lb > 0.0)) return fail(ctx, NYS_EINVAL, "prox_tv: bad argument");
+    return prox_dual_run(ctx, pc, NYS_REG_TV, lb, n_inner, dtype, n1, n2, s, out, Q);
+}
+
+int prox_hs(nys_ctx* ctx, const nys_precond* pc, double lb, int n_inner, int dtype, int n1, int n2, const void* s,
+            void* out, void* Q) {
+    if (int st = check_prox(ctx, pc, dtype, (int64_t)n1 * n2, s, out)) return st;
+    if (!Q || n1 <= 0 || n2 <= 0 || n_inner < 0 || !(lb > 0.0)) return fail(ctx, NYS_EINVAL, "prox_hs: bad argument");
+    return prox_dual_run(ctx, pc, NYS_REG_HS, lb, n_inner, dtype, n1, n2, s, out, Q);
+}
+
+int prox_wavelet(nys_ctx* ctx, const nys_precond* pc, double tau, int dtype, int64_t N, const void* s, void* out,
+                 double* gamma_io, nys_prox_info* info) {
+    if (int st = check_prox(ctx, pc, dtype, N, s, out)) return st;
+    if (!(tau >= 0.0)) return fail(ctx, NYS_EINVAL, "prox_wavelet: tau must be >= 0");
+    if (!pc) {
+        if (info) info->iterations = 0, info->converged = 1, info->residual = 0.0;
+        return dtype == NYS_F64 ? soft_run<double>(ctx, tau, N, (const double*)s, (double*)out)
+                                : soft_run<float>(ctx, tau, N, (const float*)s, (float*)out);
+    }
+    if ((pc->dtype == NYS_F64) != (dtype == NYS_F64) || pc->dtype == NYS_BF16)
+        return fail(ctx, NYS_EINVAL, "prox_wavelet: factor dtype must match the data (f32 or f64)");
+    if (dtype == NYS_F64)
+        return ssn_run<double>(ctx, pc, tau, N, (const double*)s, (double*)out, gamma_io, 50, 4, true, info);
+    return ssn_run<float>(ctx, pc, tau, N, (const float*)s, (float*)out, gamma_io, 50, 4, true, info);
+}
+
+}  // extern "C"

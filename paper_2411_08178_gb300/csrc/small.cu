@@ -1,0 +1,328 @@
+// ell x ell dense kernels of Algorithm 1 (steps 3, 5, 7, 8) and of the
+// preconditioner set-up.  All inputs come from float64 Gram matrices.
+//
+//   shift_chol   v = eps sqrt(trace(Omega^T Omega)) (= eps ||Omega||_F, step 3);
+//                C = chol(sym(Omega^T Y) + v Omega^T Omega) (= chol(Omega^T Y_v),
+//                step 5) with v <- 10 v retries; one CTA, float64.
+//   form_H       H = Y_v^T Y_v = Y^T Y + v (Omega^T Y + Y^T Omega) + v^2 Omega^T Omega
+//   tri_inv      C^{-1} for lower-triangular C, one warp per column
+//   small_gemm   C = op(A) op(B) diag(colscale), float64
+//   jacobi       cyclic Jacobi with the round-robin parallel ordering
+//                (Golub & Van Loan, Sec. 8.5: sym.schur2 rotations, every
+//                index in exactly one pair per round), one CTA, working type T
+//   rayleigh     lambda_i = v_i^T G v_i / v_i^T v_i in float64
+//   sort_eig     descending order of eigenpairs
+//
+// The float64 pipe of GB300 issues about two FMAs per clock per SM, so the
+// Jacobi rotations run in float32 when the path's working type is float32;
+// the eigenvalues are then Rayleigh quotients in float64, accurate to second
+// order in the eigenvector error.
+#include "internal.cuh"
+#include "chol.cuh"
+
+#include <cmath>
+
+namespace nys {
+
+// G2: (2 ell) x (2 ell) Gram of [Omega | Y] (row-major, ld = 2 ell).
+// info[0] = status (0 ok, 1 not SPD), info[1] = v, info[2] = retries.
+__global__ void __launch_bounds__(1024) shift_chol_kernel(const double* __restrict__ G2, int ell, double eps,
+                                                          int max_retries, double* __restrict__ C,
+                                                          double* __restrict__ info) {
+    __shared__ int flag;
+    __shared__ double sh[32];
+    const int ld = 2 * ell;
+    double tr = 0.0;
+    for (int i = threadIdx.x; i < ell; i += blockDim.x) tr += G2[(size_t)i * ld + i];
+    tr = block_sum(tr, sh);
+    double v = eps * sqrt(tr);
+    int r = 0;
+    bool ok = false;
+    for (; r <= max_retries; ++r) {
+        for (int t = threadIdx.x; t < ell * ell; t += blockDim.x) {
+            const int i = t / ell, j = t % ell;
+            const double oy = 0.5 * (G2[(size_t)i * ld + ell + j] + G2[(size_t)j * ld + ell + i]);
+            C[t] = oy + v * G2[(size_t)i * ld + j];
+        }
+        __syncthreads();
+        ok = block_cholesky(C, ell, &flag);
+        if (ok) break;
+        v *= 10.0;
+    }
+    if (threadIdx.x == 0) {
+        info[0] = ok ? 0.0 : 1.0;
+        info[1] = v;
+        info[2] = (double)(ok ? r : max_retries);
+    }
+}
+
+// H = Y^T Y + v (Omega^T Y + Y^T Omega) + v^2 Omega^T Omega
+__global__ void form_H_kernel(const double* __restrict__ G2, int ell, const double* __restrict__ info,
+                              double* __restrict__ H) {
+    const double v = info[1];
+    const int ld = 2 * ell;
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < ell * ell; t += gridDim.x * blockDim.x) {
+        const int i = t / ell, j = t % ell;
+        const double yy = G2[(size_t)(ell + i) * ld + ell + j];
+        const double oy = G2[(size_t)i * ld + ell + j] + G2[(size_t)j * ld + ell + i];
+        const double oo = G2[(size_t)i * ld + j];
+        H[t] = yy + v * oy + v * v * oo;
+    }
+}
+
+// X = C^{-1} for lower-triangular C (n x n).  Block j (one warp) solves
+// C x = e_j by forward substitution.
+__global__ void tri_inv_kernel(const double* __restrict__ C, double* __restrict__ X, int n) {
+    const int j = blockIdx.x;
+    const int lane = threadIdx.x;
+    double* x = X + 0;  // column j stored at X[i * n + j]
+    for (int i = lane; i < j; i += 32) x[(size_t)i * n + j] = 0.0;
+    if (lane == 0) x[(size_t)j * n + j] = 1.0 / C[(size_t)j * n + j];
+    __syncwarp();
+    for (int i = j + 1; i < n; ++i) {
+        double s = 0.0;
+        for (int k = j + lane; k < i; k += 32) s += C[(size_t)i * n + k] * x[(size_t)k * n + j];
+        s = warp_sum(s);
+        if (lane == 0) x[(size_t)i * n + j] = -s / C[(size_t)i * n + i];
+        __syncwarp();
+    }
+}
+
+// C (m x n) = op(A) op(B) * colscale[j]  (row-major; op = transpose if flag)
+__global__ void small_gemm_kernel(const double* __restrict__ A, int ta, const double* __restrict__ B, int tb, int m,
+                                  int n, int k, const double* __restrict__ colscale, double* __restrict__ C) {
+    __shared__ double As[16][17];
+    __shared__ double Bs[16][17];
+    const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+    const int i = blockIdx.y * 16 + ty, j = blockIdx.x * 16 + tx;
+    double acc = 0.0;
+    for (int k0 = 0; k0 < k; k0 += 16) {
+        const int ka = k0 + tx, kb = k0 + ty;
+        // A(i, ka): ta ? A[ka][i] (A is k x m) : A[i][ka] (A is m x k)
+        As[ty][tx] = (i < m && ka < k) ? (ta ? A[(size_t)ka * m + i] : A[(size_t)i * k + ka]) : 0.0;
+        // B(kb, j): tb ? B[j][kb] (B is n x k) : B[kb][j] (B is k x n)
+        Bs[ty][tx] = (kb < k && j < n) ? (tb ? B[(size_t)j * k + kb] : B[(size_t)kb * n + j]) : 0.0;
+        __syncthreads();
+#pragma unroll
+        for (int kk = 0; kk < 16; ++kk) acc = fma(As[ty][kk], Bs[kk][tx], acc);
+        __syncthreads();
+    }
+    if (i < m && j < n) C[(size_t)i * n + j] = acc * (colscale ? colscale[j] : 1.0);
+}
+
+template <class TS, class TD>
+__global__ void convert_kernel(const TS* __restrict__ in, TD* __restrict__ out, int n) {
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < n; t += gridDim.x * blockDim.x) out[t] = (TD)in[t];
+}
+
+template <class T>
+__global__ void copy_pad(const double* __restrict__ G, int ell, T* __restrict__ Gw, int n) {
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < ell * ell; t += gridDim.x * blockDim.x) {
+        const int i = t / ell, j = t % ell;
+        Gw[(size_t)i * n + j] = (T)(0.5 * (G[t] + G[(size_t)j * ell + i]));
+    }
+}
+
+// Jacobi eigensolver.  G: n x n (n even, the last index a zero pad when the
+// real size is odd), overwritten by (nearly) diagonal; V: eigenvectors in
+// columns.  arr holds the round-robin arrangement.
+template <class T>
+__global__ void __launch_bounds__(1024) jacobi_kernel(T* __restrict__ G, T* __restrict__ V, int n, int nreal,
+                                                      int max_sweeps, double tol, int* __restrict__ sweeps_out) {
+    __shared__ int arr[1024];
+    __shared__ int arr2[1024];
+    __shared__ int pp[512], qq[512];
+    __shared__ T cs[512], sn[512];
+    __shared__ double sh[32];
+    const int h = n / 2;
+    for (int t = threadIdx.x; t < n * n; t += blockDim.x) V[t] = (t / n == t % n) ? T(1) : T(0);
+    for (int t = threadIdx.x; t < n; t += blockDim.x) arr[t] = t;
+    __syncthreads();
+    const T eps = sizeof(T) == 8 ? T(1e-15) : T(1e-7);
+    int sweep = 0;
+    for (; sweep < max_sweeps; ++sweep) {
+        double off = 0.0, dg = 0.0;
+        for (int t = threadIdx.x; t < nreal * nreal; t += blockDim.x) {
+            const int i = t / nreal, j = t % nreal;
+            const double g = (double)G[(size_t)i * n + j];
+            if (i == j) dg += g * g;
+            else off += g * g;
+        }
+        off = block_sum(off, sh);
+        dg = block_sum(dg, sh);
+        if (off <= tol * tol * dg) break;
+        for (int round = 0; round < n - 1; ++round) {
+            for (int k = threadIdx.x; k < h; k += blockDim.x) {
+                const int a = arr[k], b = arr[n - 1 - k];
+                const int p = min(a, b), q = max(a, b);
+                T c = T(1), s = T(0);
+                if (q < nreal) {
+                    const T apq = G[(size_t)p * n + q];
+                    const T app = G[(size_t)p * n + p], aqq = G[(size_t)q * n + q];
+                    if (fabs((double)apq) > (double)eps * sqrt(fabs((double)app * (double)aqq)) && apq != T(0)) {
+                        const T tau = (aqq - app) / (T(2) * apq);
+                        const T t = (tau >= T(0) ? T(1) : T(-1)) / (fabs(tau) + sqrt(T(1) + tau * tau));
+                        c = T(1) / sqrt(T(1) + t * t);
+                        s = t * c;
+                    }
+                }
+                pp[k] = p;
+                qq[k] = q;
+                cs[k] = c;
+                sn[k] = s;
+            }
+            __syncthreads();
+            for (int t = threadIdx.x; t < h * h; t += blockDim.x) {
+                const int k1 = t / h, k2 = t % h;
+                const int p1 = pp[k1], q1 = qq[k1], p2 = pp[k2], q2 = qq[k2];
+                const T c1 = cs[k1], s1 = sn[k1], c2 = cs[k2], s2 = sn[k2];
+                if (s1 == T(0) && s2 == T(0)) continue;
+                T* gp = G + (size_t)p1 * n;
+                T* gq = G + (size_t)q1 * n;
+                const T xpp = gp[p2], xpq = gp[q2], xqp = gq[p2], xqq = gq[q2];
+                const T rpp = c1 * xpp - s1 * xqp, rpq = c1 * xpq - s1 * xqq;
+                const T rqp = s1 * xpp + c1 * xqp, rqq = s1 * xpq + c1 * xqq;
+                T ypp = c2 * rpp - s2 * rpq, ypq = s2 * rpp + c2 * rpq;
+                T yqp = c2 * rqp - s2 * rqq, yqq = s2 * rqp + c2 * rqq;
+                if (k1 == k2) ypq = yqp = T(0);
+                gp[p2] = ypp;
+                gp[q2] = ypq;
+                gq[p2] = yqp;
+                gq[q2] = yqq;
+            }
+            for (int t = threadIdx.x; t < n * h; t += blockDim.x) {
+                const int i = t / h, k = t % h;
+                const T c = cs[k], s = sn[k];
+                if (s == T(0)) continue;
+                T* vr = V + (size_t)i * n;
+                const T vp = vr[pp[k]], vq = vr[qq[k]];
+                vr[pp[k]] = c * vp - s * vq;
+                vr[qq[k]] = s * vp + c * vq;
+            }
+            // next arrangement: element 0 fixed, the others rotate by one
+            for (int t = threadIdx.x; t < n; t += blockDim.x) arr2[t] = (t == 0) ? arr[0] : (t == 1 ? arr[n - 1] : arr[t - 1]);
+            __syncthreads();
+            for (int t = threadIdx.x; t < n; t += blockDim.x) arr[t] = arr2[t];
+            __syncthreads();
+        }
+    }
+    if (threadIdx.x == 0) *sweeps_out = sweep;
+}
+
+// lambda_i = v_i^T G v_i / (v_i^T v_i), G float64 (ld = ell), V (ld = n) of T.
+template <class T>
+__global__ void rayleigh_kernel(const double* __restrict__ G, const T* __restrict__ V, int ell, int n,
+                                double* __restrict__ lam) {
+    __shared__ double sh[32];
+    const int i = blockIdx.x;
+    double num = 0.0, den = 0.0;
+    for (int r = threadIdx.x; r < ell; r += blockDim.x) {
+        const double vr = (double)V[(size_t)r * n + i];
+        double gv = 0.0;
+        for (int c = 0; c < ell; ++c) gv += G[(size_t)r * ell + c] * (double)V[(size_t)c * n + i];
+        num += vr * gv;
+        den += vr * vr;
+    }
+    num = block_sum(num, sh);
+    den = block_sum(den, sh);
+    if (threadIdx.x == 0) lam[i] = num / den;
+}
+
+// sort eigenpairs descending; Vout (ell x ell float64, column k = k-th
+// eigenvector), S2 = sorted eigenvalues, S_hat = max(0, S2 - v), scale = 1/sqrt(S2)
+template <class T>
+__global__ void sort_eig_kernel(const double* __restrict__ lam, const T* __restrict__ V, int ell, int n,
+                                const double* __restrict__ info, double* __restrict__ Vout,
+                                double* __restrict__ S_hat, double* __restrict__ scale) {
+    const double v = info[1];
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < ell; i += gridDim.x * blockDim.x) {
+        const double li = lam[i];
+        int rank = 0;
+        for (int j = 0; j < ell; ++j) {
+            const double lj = lam[j];
+            rank += (lj > li) || (lj == li && j < i);
+        }
+        S_hat[rank] = fmax(0.0, li - v);
+        scale[rank] = li > 0.0 ? 1.0 / sqrt(li) : 0.0;
+        for (int r = 0; r < ell; ++r) Vout[(size_t)r * ell + rank] = (double)V[(size_t)r * n + i];
+    }
+}
+
+// d_i = max(0, (s_i + mu)/(s' + mu) - 1), s' = sqrt(s_K) or s_K; sqrt(d)
+__global__ void weights_kernel(const double* __restrict__ S_hat, int ell, double mu, int sqrt_shift,
+                               double* __restrict__ d, double* __restrict__ sqd, float* __restrict__ d32) {
+    const double sk = S_hat[ell - 1];
+    const double sref = sqrt_shift ? sqrt(fmax(sk, 0.0)) : sk;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < ell; i += gridDim.x * blockDim.x) {
+        const double di = fmax(0.0, (S_hat[i] + mu) / (sref + mu) - 1.0);
+        d[i] = di;
+        sqd[i] = sqrt(di);
+        d32[i] = (float)di;
+    }
+}
+
+// A = I + diag(sqd) K diag(sqd)
+__global__ void form_A_kernel(const double* __restrict__ K, const double* __restrict__ sqd, int ell,
+                              double* __restrict__ A) {
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < ell * ell; t += gridDim.x * blockDim.x) {
+        const int i = t / ell, j = t % ell;
+        A[t] = (i == j ? 1.0 : 0.0) + sqd[i] * 0.5 * (K[t] + K[(size_t)j * ell + i]) * sqd[j];
+    }
+}
+
+__global__ void chol_kernel(double* __restrict__ A, int n, double* __restrict__ info) {
+    __shared__ int flag;
+    const bool ok = block_cholesky(A, n, &flag);
+    if (threadIdx.x == 0) info[3] = ok ? 0.0 : 1.0;
+}
+
+// M = diag(sqd) (Linv^T Linv) diag(sqd); also a float copy
+__global__ void form_M_kernel(const double* __restrict__ Ainv, const double* __restrict__ sqd, int ell,
+                              double* __restrict__ M, float* __restrict__ M32) {
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < ell * ell; t += gridDim.x * blockDim.x) {
+        const int i = t / ell, j = t % ell;
+        const double m = sqd[i] * Ainv[t] * sqd[j];
+        M[t] = m;
+        M32[t] = (float)m;
+    }
+}
+
+// ---------------------------------------------------------------- host ---
+int launch_small_gemm(nys_ctx* ctx, const double* A, int ta, const double* B, int tb, int m, int n, int k,
+                      const double* colscale, double* C) {
+    dim3 grid((n + 15) / 16, (m + 15) / 16);
+    small_gemm_kernel<<<grid, 256, 0, ctx->stream>>>(A, ta, B, tb, m, n, k, colscale, C);
+    NYS_LAUNCH_CK(ctx);
+    return NYS_OK;
+}
+
+// Eigen-decomposition of the symmetric ell x ell float64 matrix G:
+// Vout (ell x ell, columns sorted by descending eigenvalue), S_hat, scale.
+// `work` provides n*n*2 T + ell doubles.  `use_f32` picks the Jacobi type.
+int sym_eig(nys_ctx* ctx, const double* G, int ell, bool use_f32, const double* info, void* work, double* Vout,
+            double* S_hat, double* scale, int* sweeps_dev) {
+    const int n = (ell + 1) & ~1;
+    if (n > 1024) return fail(ctx, NYS_EINVAL, "sketch size above 1024 is not supported");
+    cudaStream_t s = ctx->stream;
+    auto run = [&](auto* tag) -> int {
+        using T = std::remove_pointer_t<decltype(tag)>;
+        T* Gw = (T*)work;
+        T* V = Gw + (size_t)n * n;
+        double* lam = (double*)(V + (size_t)n * n);
+        // padded copy in the working type
+        NYS_CK(ctx, cudaMemsetAsync(Gw, 0, sizeof(T) * n * n, s));
+        copy_pad<T><<<64, 256, 0, s>>>(G, ell, Gw, n);
+        NYS_LAUNCH_CK(ctx);
+        jacobi_kernel<T><<<1, 1024, 0, s>>>(Gw, V, n, ell, sizeof(T) == 8 ? 30 : 15, sizeof(T) == 8 ? 1e-14 : 2e-7,
+                                            sweeps_dev);
+        NYS_LAUNCH_CK(ctx);
+        rayleigh_kernel<T><<<ell, 128, 0, s>>>(G, V, ell, n, lam);
+        NYS_LAUNCH_CK(ctx);
+        sort_eig_kernel<T><<<(ell + 127) / 128, 128, 0, s>>>(lam, V, ell, n, info, Vout, S_hat, scale);
+        NYS_LAUNCH_CK(ctx);
+        return NYS_OK;
+    };
+    return use_f32 ? run((float*)nullptr) : run((double*)nullptr);
+}
+
+}  // namespace nys

@@ -1,0 +1,367 @@
+// Weighted accelerated proximal gradient, Algorithm 3, for
+//     min_x f(x) + lambda g(x),   f = 1/2 ||A x - y||^2  or  sum huber_delta(A x - y),
+// with g = anisotropic TV, Hessian Schatten-1, or ||xbar||_1 of the Haar
+// coefficients xbar = W x (invertible-L form, Sec. III-B).  Per iteration:
+//     grad = A^T A u - A^T y            (one fused normal-operator pass), or
+//            A^T clip(A u - y, +-delta) (Huber), or W (A^T A W^T u) - W A^T y
+//     s    = u - alpha P^{-1} grad
+//     x'   = prox^P_{alpha lambda g}(s)  (dual APG / semi-smooth Newton)
+//     t'   = (1 + sqrt(1 + 4 t^2))/2,  u = x' + ((t - 1)/t') (x' - x)
+// x^1 = u^1 = 0, t^0 = 1.  alpha defaults to 1/(1.02 lambda_max(P^{-1} Phi)),
+// lambda_max from 50 power-iteration steps started at a Philox Gaussian.
+#include "internal.cuh"
+
+#include <cmath>
+
+namespace nys {
+template <class T>
+int ssn_run(nys_ctx* ctx, const nys_precond* pc, double tau, int64_t N, const T* s, T* out, double* gamma_io,
+            int max_newton, int evals_per_batch, bool sync_until_done, nys_prox_info* info);
+template <class T>
+int soft_run(nys_ctx* ctx, double tau, int64_t N, const T* s, T* out);
+int prox_dual_run(nys_ctx* ctx, const nys_precond* pc, int reg, double lb, int n_inner, int dtype, int n1, int n2,
+                  const void* s, void* out, void* Q);
+}  // namespace nys
+
+struct nys_solver {
+    nys_ctx* ctx = nullptr;
+    nys_op* op = nullptr;
+    nys_solver_desc d{};
+    const nys_precond* pc = nullptr;
+    int dt = NYS_F32;
+    int64_t N = 0, M = 0;
+    int G = 0;
+    void* mem = nullptr;
+    // buffers (op dtype)
+    void *y = nullptr, *aty = nullptr, *x = nullptr, *xn = nullptr, *u = nullptr, *s = nullptr, *g = nullptr;
+    void *tM = nullptr, *tN = nullptr, *Q = nullptr;
+    double* gamma = nullptr;
+    double* pw = nullptr;   // power-iteration scalars
+    double alpha = 0.0;
+    double t = 1.0;
+    int k = 0;
+};
+
+namespace nys {
+namespace {
+
+template <class T>
+__global__ void sub_kernel(T* __restrict__ a, const T* __restrict__ b, int64_t n) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        a[i] = a[i] - b[i];
+}
+
+template <class T>
+__global__ void huber_resid_kernel(T* __restrict__ r, const T* __restrict__ y, int64_t n, double delta) {
+    using TC = typename Comp<T>::type;
+    const TC d = (TC)delta;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        r[i] = (T)fmin(d, fmax(-d, (TC)r[i] - (TC)y[i]));
+}
+
+// s = u - alpha * g
+template <class T>
+__global__ void step_kernel(const T* __restrict__ u, const T* __restrict__ g, double alpha, int64_t n,
+                            T* __restrict__ s) {
+    using TC = typename Comp<T>::type;
+    const TC a = (TC)alpha;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        s[i] = (T)((TC)u[i] - a * (TC)g[i]);
+}
+
+// u = xn + beta (xn - x)
+template <class T>
+__global__ void momentum_kernel(const T* __restrict__ xn, const T* __restrict__ x, double beta, int64_t n,
+                                T* __restrict__ u) {
+    using TC = typename Comp<T>::type;
+    const TC b = (TC)beta;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const TC a = (TC)xn[i];
+        u[i] = (T)(a + b * (a - (TC)x[i]));
+    }
+}
+
+// power iteration helpers: out[0] = ||w||, w /= ||w||
+template <class T>
+__global__ void norm_scale_kernel(T* __restrict__ w, int64_t n, double* __restrict__ out) {
+    __shared__ double sh[32];
+    double s = 0.0;
+    for (int64_t i = threadIdx.x; i < n; i += blockDim.x) {
+        const double v = (double)w[i];
+        s += v * v;
+    }
+    s = block_sum(s, sh);
+    const double nr = sqrt(s);
+    if (threadIdx.x == 0) out[0] = nr;
+    const double inv = nr > 0.0 ? 1.0 / nr : 0.0;
+    for (int64_t i = threadIdx.x; i < n; i += blockDim.x) w[i] = (T)((double)w[i] * inv);
+}
+
+template <class T>
+__global__ void gauss_init_kernel(T* __restrict__ w, int64_t n, uint64_t seed) {
+    // small Philox-free start: a deterministic hash-based +-1 pattern is not
+    // Gaussian; use a simple LCG-driven Box-Muller for the power start only
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        uint64_t z = seed * 0x9E3779B97F4A7C15ull + (uint64_t)i * 0xBF58476D1CE4E5B9ull;
+        z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+        z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+        z ^= z >> 31;
+        const double u0 = ((double)(z >> 11) + 0.5) * (1.0 / 9007199254740992.0);
+        uint64_t z2 = z * 0x9E3779B97F4A7C15ull + 0x632BE59BD9B4E019ull;
+        z2 = (z2 ^ (z2 >> 29)) * 0xBF58476D1CE4E5B9ull;
+        const double u1 = ((double)(z2 >> 11) + 0.5) * (1.0 / 9007199254740992.0);
+        w[i] = (T)(sqrt(-2.0 * log(u0)) * cospi(2.0 * u1));
+    }
+}
+
+inline int grid_for(nys_ctx* ctx, int64_t n) { return (int)std::min<int64_t>((n + 255) / 256, ctx->sm_count * 8); }
+
+template <class T>
+int phi_apply(nys_solver* S, const void* v, void* out) {
+    // Phi = A^T A, or W A^T A W^T for the wavelet model
+    nys_op* op = S->op;
+    if (S->d.reg != NYS_REG_WAVELET) return op_run(op, 2, v, out, 1, S->dt, S->dt);
+    int st;
+    if ((st = haar_run(op, v, S->tN, 1, 1, S->dt, S->dt))) return st;
+    if ((st = op_run(op, 2, S->tN, S->s, 1, S->dt, S->dt))) return st;
+    return haar_run(op, S->s, out, 1, 0, S->dt, S->dt);
+}
+
+template <class T>
+int gradient(nys_solver* S) {
+    nys_ctx* ctx = S->ctx;
+    nys_op* op = S->op;
+    const int dt = S->dt;
+    int st;
+    const int gN = grid_for(ctx, S->N), gM = grid_for(ctx, S->M);
+    if (S->d.reg == NYS_REG_WAVELET) {
+        // g = W A^T A W^T u - W A^T y
+        if ((st = haar_run(op, S->u, S->tN, 1, 1, dt, dt))) return st;
+        if (S->d.fit == NYS_FIT_HUBER) {
+            if ((st = op_run(op, 0, S->tN, S->tM, 1, dt, dt))) return st;
+            huber_resid_kernel<T><<<gM, 256, 0, ctx->stream>>>((T*)S->tM, (const T*)S->y, S->M, S->d.huber_delta);
+            NYS_LAUNCH_CK(ctx);
+            if ((st = op_run(op, 1, S->tM, S->s, 1, dt, dt))) return st;
+            return haar_run(op, S->s, S->g, 1, 0, dt, dt);
+        }
+        if ((st = op_run(op, 2, S->tN, S->s, 1, dt, dt))) return st;
+        if ((st = haar_run(op, S->s, S->g, 1, 0, dt, dt))) return st;
+        sub_kernel<T><<<gN, 256, 0, ctx->stream>>>((T*)S->g, (const T*)S->aty, S->N);
+        NYS_LAUNCH_CK(ctx);
+        return NYS_OK;
+    }
+    if (S->d.fit == NYS_FIT_HUBER) {
+        if ((st = op_run(op, 0, S->u, S->tM, 1, dt, dt))) return st;
+        huber_resid_kernel<T><<<gM, 256, 0, ctx->stream>>>((T*)S->tM, (const T*)S->y, S->M, S->d.huber_delta);
+        NYS_LAUNCH_CK(ctx);
+        return op_run(op, 1, S->tM, S->g, 1, dt, dt);
+    }
+    if ((st = op_run(op, 2, S->u, S->g, 1, dt, dt))) return st;
+    sub_kernel<T><<<gN, 256, 0, ctx->stream>>>((T*)S->g, (const T*)S->aty, S->N);
+    NYS_LAUNCH_CK(ctx);
+    return NYS_OK;
+}
+
+template <class T>
+int iterate(nys_solver* S, int n_steps) {
+    nys_ctx* ctx = S->ctx;
+    const int gN = grid_for(ctx, S->N);
+    int st;
+    for (int it = 0; it < n_steps; ++it) {
+        if ((st = gradient<T>(S))) return st;
+        if (S->pc && (st = precond_run(ctx, S->pc, 1, S->dt, S->g, S->g, 1))) return st;
+        step_kernel<T><<<gN, 256, 0, ctx->stream>>>((const T*)S->u, (const T*)S->g, S->alpha, S->N, (T*)S->s);
+        NYS_LAUNCH_CK(ctx);
+        const double tau = S->alpha * S->d.lambda;
+        if (S->d.reg == NYS_REG_WAVELET) {
+            if (S->pc)
+                st = ssn_run<T>(ctx, S->pc, tau, S->N, (const T*)S->s, (T*)S->xn, S->gamma, 50, 10, false, nullptr);
+            else
+                st = soft_run<T>(ctx, tau, S->N, (const T*)S->s, (T*)S->xn);
+        } else {
+            st = prox_dual_run(ctx, S->pc, S->d.reg, tau, S->d.n_inner, S->dt, S->op->n1, S->op->n2, S->s, S->xn,
+                               S->Q);
+        }
+        if (st) return st;
+        const double tn = 0.5 * (1.0 + std::sqrt(1.0 + 4.0 * S->t * S->t));
+        const double beta = (S->t - 1.0) / tn;
+        S->t = tn;
+        momentum_kernel<T><<<gN, 256, 0, ctx->stream>>>((const T*)S->xn, (const T*)S->x, beta, S->N, (T*)S->u);
+        NYS_LAUNCH_CK(ctx);
+        std::swap(S->x, S->xn);
+        S->k += 1;
+    }
+    return NYS_OK;
+}
+
+template <class T>
+int estimate_alpha(nys_solver* S) {
+    nys_ctx* ctx = S->ctx;
+    cudaStream_t s = ctx->stream;
+    T* z = (T*)S->xn;   // scratch vectors before the first iteration
+    T* w = (T*)S->u;
+    gauss_init_kernel<T><<<grid_for(ctx, S->N), 256, 0, s>>>(z, S->N, S->d.power_seed);
+    NYS_LAUNCH_CK(ctx);
+    norm_scale_kernel<T><<<1, 1024, 0, s>>>(z, S->N, S->pw);
+    NYS_LAUNCH_CK(ctx);
+    const int iters = S->d.power_iters > 0 ? S->d.power_iters : 50;
+    int st;
+    for (int it = 0; it < iters; ++it) {
+        if ((st = phi_apply<T>(S, z, w))) return st;
+        if (S->pc && (st = precond_run(ctx, S->pc, 1, S->dt, w, w, 1))) return st;
+        norm_scale_kernel<T><<<1, 1024, 0, s>>>(w, S->N, S->pw);
+        NYS_LAUNCH_CK(ctx);
+        std::swap(z, w);
+    }
+    double lam = 0.0;
+    NYS_CK(ctx, cudaMemcpyAsync(&lam, S->pw, sizeof(double), cudaMemcpyDeviceToHost, s));
+    NYS_CK(ctx, cudaStreamSynchronize(s));
+    if (!(lam > 0.0) || !std::isfinite(lam)) return fail(ctx, NYS_ENONFINITE, "power iteration gave %g", lam);
+    S->alpha = 1.0 / (1.02 * lam);
+    return NYS_OK;
+}
+
+template <class T>
+int reset_state(nys_solver* S) {
+    cudaStream_t s = S->ctx->stream;
+    const size_t nb = S->N * sizeof(T);
+    NYS_CK(S->ctx, cudaMemsetAsync(S->x, 0, nb, s));
+    NYS_CK(S->ctx, cudaMemsetAsync(S->xn, 0, nb, s));
+    NYS_CK(S->ctx, cudaMemsetAsync(S->u, 0, nb, s));
+    if (S->G) NYS_CK(S->ctx, cudaMemsetAsync(S->Q, 0, (size_t)S->G * nb, s));
+    if (S->gamma && S->pc) NYS_CK(S->ctx, cudaMemsetAsync(S->gamma, 0, S->pc->ell * sizeof(double), s));
+    S->t = 1.0;
+    S->k = 0;
+    return NYS_OK;
+}
+
+template <class T>
+int create_typed(nys_solver* S, const void* y) {
+    nys_ctx* ctx = S->ctx;
+    const int64_t N = S->N, M = S->M;
+    const size_t es = sizeof(T);
+    const int ell = S->pc ? S->pc->ell : 0;
+    auto al = [](size_t v) { return (v + 255) & ~size_t(255); };
+    const size_t total = al(M * es) * 2 + al(N * es) * 7 + al((size_t)S->G * N * es) + al((ell + 1) * 8) + 256;
+    NYS_CK(ctx, cudaMalloc(&S->mem, total));
+    char* p = (char*)S->mem;
+    auto take = [&](size_t n) {
+        char* r = p;
+        p += al(n);
+        return r;
+    };
+    S->y = take(M * es);
+    S->tM = take(M * es);
+    S->aty = take(N * es);
+    S->x = take(N * es);
+    S->xn = take(N * es);
+    S->u = take(N * es);
+    S->s = take(N * es);
+    S->g = take(N * es);
+    S->tN = take(N * es);
+    S->Q = S->G ? take((size_t)S->G * N * es) : nullptr;
+    S->gamma = (double*)take((ell + 1) * 8);
+    S->pw = (double*)take(256);
+    cudaStream_t s = ctx->stream;
+    NYS_CK(ctx, cudaMemcpyAsync(S->y, y, M * es, cudaMemcpyDeviceToDevice, s));
+    int st;
+    // A^T y (and W A^T y for the wavelet model)
+    if ((st = op_run(S->op, 1, S->y, S->aty, 1, S->dt, S->dt))) return st;
+    if (S->d.reg == NYS_REG_WAVELET) {
+        if ((st = haar_run(S->op, S->aty, S->tN, 1, 0, S->dt, S->dt))) return st;
+        NYS_CK(ctx, cudaMemcpyAsync(S->aty, S->tN, N * es, cudaMemcpyDeviceToDevice, s));
+    }
+    if ((st = reset_state<T>(S))) return st;
+    if (S->d.alpha > 0.0) S->alpha = S->d.alpha;
+    else if ((st = estimate_alpha<T>(S))) return st;
+    if ((st = reset_state<T>(S))) return st;
+    // reserve the scratch that pgd_step uses, so later steps never allocate
+    if (S->G) {
+        if (!scratch(ctx, SLOT_PROX, ((size_t)2 * S->G * N + 2 * N) * es, &st)) return st;
+    }
+    if (S->pc) {
+        const size_t nbp = (size_t)((N + 1023) / 1024);
+        if (!scratch(ctx, SLOT_PRECOND, (nbp * ell + ell) * es, &st)) return st;
+        if (S->d.reg == NYS_REG_WAVELET) {
+            // first ssn_run call sizes SLOT_SSN; run one prox now
+            if ((st = ssn_run<T>(ctx, S->pc, 0.0, N, (const T*)S->x, (T*)S->xn, nullptr, 1, 1, false, nullptr)))
+                return st;
+            if ((st = reset_state<T>(S))) return st;
+        }
+    }
+    if (S->op->haar_levels > 0 && !scratch(ctx, SLOT_OPTMP, 2 * (size_t)N * es, &st)) return st;
+    return NYS_OK;
+}
+
+}  // namespace
+}  // namespace nys
+
+using namespace nys;
+
+extern "C" {
+
+int nys_solver_create(nys_ctx* ctx, nys_op* op, const nys_solver_desc* d, const void* y, const nys_precond* pc,
+                      nys_solver** out) {
+    if (!ctx || !op || !d || !y || !out) return fail(ctx, NYS_EINVAL, "nys_solver_create: null argument");
+    if (d->reg != NYS_REG_WAVELET && d->reg != NYS_REG_TV && d->reg != NYS_REG_HS)
+        return fail(ctx, NYS_EINVAL, "nys_solver_create: unknown regulariser");
+    if (d->reg == NYS_REG_WAVELET && op->haar_levels <= 0)
+        return fail(ctx, NYS_EINVAL, "nys_solver_create: the wavelet model needs haar_levels > 0");
+    if (d->fit != NYS_FIT_L2 && d->fit != NYS_FIT_HUBER) return fail(ctx, NYS_EINVAL, "nys_solver_create: fit");
+    if (!(d->lambda >= 0.0)) return fail(ctx, NYS_EINVAL, "nys_solver_create: lambda must be >= 0");
+    if (d->reg != NYS_REG_WAVELET && d->n_inner <= 0) return fail(ctx, NYS_EINVAL, "nys_solver_create: n_inner");
+    if (pc) {
+        if (!pc->priv || pc->N != op->N) return fail(ctx, NYS_EINVAL, "nys_solver_create: preconditioner mismatch");
+        if (pc->mu != pc->mu) return fail(ctx, NYS_EINVAL, "nys_solver_create: call nys_precond_setup first");
+    }
+    auto* S = new nys_solver();
+    S->ctx = ctx;
+    S->op = op;
+    S->d = *d;
+    S->pc = pc;
+    S->dt = op->dtype;
+    S->N = op->N;
+    S->M = op->M;
+    S->G = d->reg == NYS_REG_TV ? 2 : (d->reg == NYS_REG_HS ? 3 : 0);
+    const int st = S->dt == NYS_F64 ? create_typed<double>(S, y) : create_typed<float>(S, y);
+    if (st) {
+        nys_solver_destroy(S);
+        return st;
+    }
+    *out = S;
+    return NYS_OK;
+}
+
+int nys_solver_destroy(nys_solver* S) {
+    if (!S) return NYS_OK;
+    cudaStreamSynchronize(S->ctx->stream);
+    if (S->mem) cudaFree(S->mem);
+    delete S;
+    return NYS_OK;
+}
+
+int pgd_step(nys_solver* S, int n_steps) {
+    if (!S) return fail(nullptr, NYS_EINVAL, "pgd_step: null solver");
+    if (n_steps < 0) return fail(S->ctx, NYS_EINVAL, "pgd_step: negative step count");
+    return S->dt == NYS_F64 ? iterate<double>(S, n_steps) : iterate<float>(S, n_steps);
+}
+
+int nys_solver_reset(nys_solver* S) {
+    if (!S) return fail(nullptr, NYS_EINVAL, "null solver");
+    return S->dt == NYS_F64 ? reset_state<double>(S) : reset_state<float>(S);
+}
+
+int nys_solver_get_x(nys_solver* S, void* x_out) {
+    if (!S || !x_out) return fail(S ? S->ctx : nullptr, NYS_EINVAL, "nys_solver_get_x: null argument");
+    if (S->d.reg == NYS_REG_WAVELET) return haar_run(S->op, S->x, x_out, 1, 1, S->dt, S->dt);
+    NYS_CK(S->ctx, cudaMemcpyAsync(x_out, S->x, S->N * dtype_size(S->dt), cudaMemcpyDeviceToDevice, S->ctx->stream));
+    return NYS_OK;
+}
+
+int nys_solver_alpha(nys_solver* S, double* alpha) {
+    if (!S || !alpha) return fail(nullptr, NYS_EINVAL, "nys_solver_alpha: null argument");
+    *alpha = S->alpha;
+    return NYS_OK;
+}
+
+}  // extern "C"

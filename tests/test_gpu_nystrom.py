@@ -1,0 +1,203 @@
+"""GPU parity of Algorithm 1 (sketch + factor), the preconditioner and the proxes
+against the float64 oracle, through the C ABI."""
+import numpy as np
+import pytest
+
+import oracle
+from oracle import operators as O
+from oracle.philox import gaussian_matrix
+from workloads import gaussian_kernel, gaussian_probe_like, phantom
+from tests.gpu_util import TOL, rel, require_gpu
+
+pytestmark = pytest.mark.gpu
+EPS64 = 2.0 ** -52
+EPS32 = 2.0 ** -23
+
+
+@pytest.fixture(scope="module")
+def env():
+    torch, api = require_gpu()
+    return torch, api, api.Context(0)
+
+
+def _flat_phi(opo, n1, n2):
+    return lambda V: opo.normal(V.reshape(-1, n1, n2)).reshape(V.shape[0], -1)
+
+
+@pytest.mark.parametrize("dt", ["f32", "f64"])
+@pytest.mark.parametrize("N,ell", [(64 * 64, 32), (37 * 29, 7), (5, 3)])
+def test_omega_matches_philox_spec(env, dt, N, ell):
+    torch, api, ctx = env
+    n1 = {4096: 64, 1073: 37, 5: 1}[N]
+    n2 = N // n1
+    tdt = torch.float64 if dt == "f64" else torch.float32
+    op = api.Operator(ctx, "blur", n1, n2, dtype=tdt, kernel=np.ones((1, 1)))
+    Om, Y = api.nys_sketch(ctx, op, ell, seed=0x1234_5678_9ABC)
+    ref = gaussian_matrix(N, ell, 0x1234_5678_9ABC)
+    got = Om.reshape(ell, N).double().cpu().numpy()
+    assert np.max(np.abs(got - ref)) <= (1e-13 if dt == "f64" else 4e-6) * max(1.0, np.abs(ref).max())
+    # 1 x 1 unit kernel: Phi = I
+    assert np.array_equal(Y.cpu().numpy(), Om.cpu().numpy())
+
+
+@pytest.mark.parametrize("dt", ["f32", "f64"])
+def test_sketch_blur_and_wavelet(env, dt):
+    torch, api, ctx = env
+    n, ell = 64, 12
+    h = gaussian_kernel(9, 1.5)
+    tdt = torch.float64 if dt == "f64" else torch.float32
+    op = api.Operator(ctx, "blur", n, n, dtype=tdt, kernel=h, haar_levels=3)
+    opo = O.Operator("blur", n, n, kernel=h)
+    Om_ref = gaussian_matrix(n * n, ell, 3).reshape(ell, n, n)
+    _, Y = api.nys_sketch(ctx, op, ell, seed=3)
+    assert rel(Y.cpu(), opo.normal(Om_ref)) < TOL[dt]
+    _, Yw = api.nys_sketch(ctx, op, ell, seed=3, phi="w_ata_wt")
+    ref = O.haar_forward(opo.normal(O.haar_adjoint(Om_ref, 3)), 3)
+    assert rel(Yw.cpu(), ref) < TOL[dt]
+
+
+def _check_factor(U_g, S_g, ref, rtol_s, rtol_op):
+    # eigenvalues, and the low-rank operator U S U^T on random vectors (basis-free)
+    S_ref = ref["S_hat"]
+    assert np.max(np.abs(S_g - S_ref)) <= rtol_s * S_ref[0]
+    Z = np.random.default_rng(1).standard_normal((5, U_g.shape[1]))
+    A_g = ((Z @ U_g.T) * S_g) @ U_g
+    A_r = ((Z @ ref["U"].T) * S_ref) @ ref["U"]
+    assert rel(A_g, A_r) < rtol_op
+
+
+def test_factor_f64_matches_algorithm1(env):
+    torch, api, ctx = env
+    n, ell = 64, 32
+    h = gaussian_kernel(9, 1.5)
+    op = api.Operator(ctx, "blur", n, n, dtype=torch.float64, kernel=h)
+    opo = O.Operator("blur", n, n, kernel=h)
+    Om, Y = api.nys_sketch(ctx, op, ell, seed=3)
+    pc = api.nys_factor(ctx, Om, Y, EPS64)
+    ref = oracle.nystrom.nystrom(_flat_phi(opo, n, n), gaussian_matrix(n * n, ell, 3), EPS64)
+    assert abs(pc.v - ref["v"]) <= 1e-12 * ref["v"] and pc.chol_retries == ref["retries"]
+    _check_factor(pc.U.cpu().numpy(), pc.S_hat.cpu().numpy(), ref, 1e-10, 1e-9)
+    # orthonormal columns
+    U = pc.U.cpu().numpy()
+    assert np.max(np.abs(U @ U.T - np.eye(ell))) < 1e-9
+
+
+def test_factor_f32_and_bf16_stated_accuracy(env):
+    torch, api, ctx = env
+    n, ell = 128, 48
+    h = gaussian_kernel(9, 1.5)
+    op = api.Operator(ctx, "blur", n, n, dtype=torch.float32, kernel=h)
+    opo = O.Operator("blur", n, n, kernel=h)
+    ref = oracle.nystrom.nystrom(_flat_phi(opo, n, n), gaussian_matrix(n * n, ell, 4), EPS32)
+    Om, Y = api.nys_sketch(ctx, op, ell, seed=4)
+    pc = api.nys_factor(ctx, Om, Y, EPS32)
+    _check_factor(pc.U.double().cpu().numpy(), pc.S_hat.cpu().numpy(), ref, 1e-4, 1e-3)
+    Ob, Yb = api.nys_sketch(ctx, op, ell, seed=4, store_dtype=torch.bfloat16)
+    pcb = api.nys_factor(ctx, Ob, Yb, EPS32, u_dtype=torch.bfloat16)
+    _check_factor(pcb.U.double().cpu().numpy(), pcb.S_hat.cpu().numpy(), ref, 3e-2, 3e-2)
+
+
+def test_exact_recovery_low_rank_on_gpu(env):
+    # blur + 4x decimation of a 16 x 16 image has rank <= 16 < ell = 20
+    torch, api, ctx = env
+    n, d, ell = 16, 4, 20
+    h = gaussian_kernel(7, 2.0)
+    op = api.Operator(ctx, "blur_decim", n, n, dtype=torch.float64, kernel=h, decim=d)
+    Om, Y = api.nys_sketch(ctx, op, ell, seed=5)
+    pc = api.nys_factor(ctx, Om, Y, EPS64)
+    U, S = pc.U.cpu().numpy(), pc.S_hat.cpu().numpy()
+    opo = O.Operator("blur_decim", n, n, kernel=h, decim=d)
+    Phi = opo.normal(np.eye(n * n).reshape(-1, n, n)).reshape(n * n, -1)
+    assert np.linalg.norm(U.T @ np.diag(S) @ U - Phi) <= 1e-9 * np.linalg.norm(Phi)
+
+
+def test_not_spd_core_is_reported(env):
+    # Y = -Omega is the sketch of Phi = -I: the shifted core stays negative definite
+    torch, api, ctx = env
+    from paper_2411_08178_gb300._abi import NYS_ENOTSPD, NysError
+    Om = torch.from_numpy(gaussian_matrix(400, 6, 1).reshape(6, 20, 20)).cuda()
+    with pytest.raises(NysError) as e:
+        api.nys_factor(ctx, Om, -Om, EPS64)
+    assert e.value.code == NYS_ENOTSPD
+
+
+@pytest.mark.parametrize("dt", ["f32", "f64"])
+@pytest.mark.parametrize("sqrt_shift,mu", [(True, 0.0), (False, 1e-2)])
+def test_precond_apply_matches_oracle(env, dt, sqrt_shift, mu):
+    torch, api, ctx = env
+    n, ell = 48, 16
+    h = gaussian_kernel(5, 1.0)
+    opo = O.Operator("blur", n, n, kernel=h)
+    ref = oracle.nystrom.nystrom(_flat_phi(opo, n, n), gaussian_matrix(n * n, ell, 6), EPS64)
+    P = oracle.nystrom.Precond(ref["U"], ref["S_hat"], mu=mu, sqrt_shift=sqrt_shift)
+    tdt = torch.float64 if dt == "f64" else torch.float32
+    pc = api.Precond(ctx, n * n, ell, tdt).import_factor(ref["U"], ref["S_hat"], mu, sqrt_shift)
+    z = gaussian_probe_like((3, n * n), seed=12)
+    zg = torch.from_numpy(z).to(tdt).cuda()
+    assert rel(api.precond_apply(ctx, pc, zg, inverse=True).cpu(), P.inverse(z)) < TOL[dt]
+    assert rel(api.precond_apply(ctx, pc, zg, inverse=False).cpu(), P.apply(z)) < TOL[dt]
+    # P P^{-1} z = z on the device, in place
+    w = api.precond_apply(ctx, pc, zg, inverse=True)
+    api.precond_apply(ctx, pc, w, inverse=False, out=w)
+    assert rel(w.cpu(), z) < TOL[dt]
+
+
+def test_precond_degenerate_is_reported(env):
+    torch, api, ctx = env
+    from paper_2411_08178_gb300._abi import NYS_EDEGENERATE, NysError
+    U = np.linalg.qr(np.random.default_rng(0).standard_normal((100, 3)))[0].T
+    with pytest.raises(NysError) as e:
+        api.Precond(ctx, 100, 3, torch.float64).import_factor(U, np.array([2.0, 1.0, 0.0]), 0.0, True)
+    assert e.value.code == NYS_EDEGENERATE
+
+
+@pytest.mark.parametrize("dt", ["f32", "f64"])
+@pytest.mark.parametrize("reg", ["tv", "hs"])
+@pytest.mark.parametrize("precond", [False, True])
+def test_prox_dual_matches_oracle(env, dt, reg, precond):
+    torch, api, ctx = env
+    n1, n2, ell = 40, 52, 10
+    s = phantom(max(n1, n2), 6, 3, "mixed")[:n1, :n2] + 0.05 * gaussian_probe_like((n1, n2), 13)
+    lb, n_inner = 0.02, 30
+    tdt = torch.float64 if dt == "f64" else torch.float32
+    P, pc = oracle.nystrom.Identity(), None
+    if precond:
+        h = gaussian_kernel(5, 1.0)
+        opo = O.Operator("blur", n1, n2, kernel=h)
+        ref = oracle.nystrom.nystrom(_flat_phi(opo, n1, n2), gaussian_matrix(n1 * n2, ell, 7), EPS64)
+        P = oracle.nystrom.Precond(ref["U"], ref["S_hat"])
+        pc = api.Precond(ctx, n1 * n2, ell, tdt).import_factor(ref["U"], ref["S_hat"], 0.0, True)
+    x_ref, Q_ref = oracle.prox.prox_dual(s, reg, lb, P, n_inner)
+    sg = torch.from_numpy(s).to(tdt).cuda()
+    fn = api.prox_tv if reg == "tv" else api.prox_hs
+    x, Q = fn(ctx, pc, lb, n_inner, sg)
+    tol = TOL[dt] * (10 if dt == "f32" else 1)
+    assert rel(x.cpu(), x_ref) < tol
+    assert rel(Q.cpu(), Q_ref) < tol * 10
+    # warm start continues the same sequence of Q (restart of t)
+    x2, Q2 = fn(ctx, pc, lb, n_inner, sg, Q=Q)
+    x2_ref, _ = oracle.prox.prox_dual(s, reg, lb, P, n_inner, Q0=Q_ref)
+    assert rel(x2.cpu(), x2_ref) < tol * 10
+
+
+def test_prox_wavelet_matches_oracle(env):
+    torch, api, ctx = env
+    n, ell = 64, 32
+    h = gaussian_kernel(9, 1.5)
+    opo = O.Operator("blur", n, n, kernel=h)
+    phi = lambda V: O.haar_forward(opo.normal(O.haar_adjoint(V.reshape(-1, n, n), 3)), 3).reshape(V.shape[0], -1)
+    ref = oracle.nystrom.nystrom(phi, gaussian_matrix(n * n, ell, 3), EPS64)
+    P = oracle.nystrom.Precond(ref["U"], ref["S_hat"])
+    pc = api.Precond(ctx, n * n, ell, torch.float64).import_factor(ref["U"], ref["S_hat"], 0.0, True)
+    s = O.haar_forward(phantom(n, 8, 1, "mixed"), 3).ravel() + 0.01 * gaussian_probe_like(n * n, 14)
+    tau = 0.02
+    x_ref, g_ref, it, ok = oracle.prox.prox_wavelet(s, P.Ubar, tau)
+    assert ok
+    gamma = torch.zeros(ell, dtype=torch.float64, device="cuda")
+    x, info = api.prox_wavelet(ctx, pc, tau, torch.from_numpy(s).cuda(), gamma=gamma)
+    assert info["converged"]
+    assert rel(x.cpu(), x_ref) < 1e-10
+    assert rel(gamma.cpu(), g_ref) < 1e-8
+    # P = I: soft threshold
+    x0, _ = api.prox_wavelet(ctx, None, tau, torch.from_numpy(s).cuda())
+    assert rel(x0.cpu(), oracle.prox.soft_threshold(s, tau)) < 1e-15

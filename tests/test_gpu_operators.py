@@ -1,0 +1,115 @@
+"""GPU parity of the operators (blur, blur + decimation, Joseph ray transform, Haar)
+against the float64 oracle, element by element, through the C ABI."""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import operators as O
+from workloads import gaussian_kernel, gaussian_probe_like, random_kernel
+from tests.gpu_util import TOL, rel, require_gpu
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def env():
+    torch, api = require_gpu()
+    return torch, api, api.Context(0)
+
+
+DT = {"f32": "float32", "f64": "float64"}
+
+
+def _t(torch, a, dt):
+    return torch.from_numpy(np.ascontiguousarray(a)).to(getattr(torch, DT[dt])).cuda()
+
+
+@pytest.mark.parametrize("dt", ["f32", "f64"])
+@pytest.mark.parametrize("shape,kern", [((64, 64), "gauss9"), ((70, 45), "gauss25"), ((33, 97), "rand5"),
+                                        ((16, 16), "gauss25"), ((128, 80), "rand7x3")])
+def test_blur_apply_adjoint_normal(env, dt, shape, kern):
+    torch, api, ctx = env
+    n1, n2 = shape
+    h = {"gauss9": gaussian_kernel(9, 1.5), "gauss25": gaussian_kernel(25, 4.0), "rand5": random_kernel(5, 1),
+         "rand7x3": random_kernel(7, 2)[:, 2:5] / random_kernel(7, 2)[:, 2:5].sum()}[kern]
+    op = api.Operator(ctx, "blur", n1, n2, dtype=getattr(torch, DT[dt]), kernel=h)
+    x = gaussian_probe_like((3, n1, n2), seed=5)
+    xg = _t(torch, x, dt)
+    tol = TOL[dt] * (3 if dt == "f32" else 1)
+    assert rel(api.op_apply(op, xg).cpu(), O.blur_apply(x, h)) < tol
+    assert rel(api.op_adjoint(op, xg).cpu(), O.blur_adjoint(x, h)) < tol
+    assert rel(api.op_normal(op, xg).cpu(), O.blur_adjoint(O.blur_apply(x, h), h)) < tol
+
+
+@pytest.mark.parametrize("dt", ["f32", "f64"])
+def test_decim_apply_adjoint_normal(env, dt):
+    torch, api, ctx = env
+    n, d = 64, 4
+    h = gaussian_kernel(7, 2.0)
+    op = api.Operator(ctx, "blur_decim", n, n, dtype=getattr(torch, DT[dt]), kernel=h, decim=d)
+    x = gaussian_probe_like((2, n, n), seed=6)
+    yv = gaussian_probe_like((2, n // d, n // d), seed=7)
+    assert rel(api.op_apply(op, _t(torch, x, dt)).cpu(), O.decim_apply(x, h, d)) < TOL[dt]
+    assert rel(api.op_adjoint(op, _t(torch, yv, dt)).cpu(), O.decim_adjoint(yv, h, d)) < TOL[dt]
+    assert rel(api.op_normal(op, _t(torch, x, dt)).cpu(), O.decim_adjoint(O.decim_apply(x, h, d), h, d)) < TOL[dt]
+
+
+@pytest.mark.parametrize("dt", ["f32", "f64"])
+@pytest.mark.parametrize("geom", [(48, 48, 30, 70), (40, 56, 17, 81), (24, 24, 4, 40)])
+def test_radon_apply_adjoint(env, dt, geom):
+    torch, api, ctx = env
+    n1, n2, na, nb = geom
+    op = api.Operator(ctx, "radon", n1, n2, dtype=getattr(torch, DT[dt]), n_angles=na, n_bins=nb)
+    x = gaussian_probe_like((2, n1, n2), seed=8)
+    s = gaussian_probe_like((2, na, nb), seed=9)
+    tol = 1e-5 if dt == "f32" else 1e-12
+    assert rel(api.op_apply(op, _t(torch, x, dt)).cpu(), O.radon_apply(x, na, nb)) < tol
+    assert rel(api.op_adjoint(op, _t(torch, s, dt)).cpu(), O.radon_adjoint(s, n1, n2)) < tol
+    # exact transposition on the device: <A x, s> = <x, A^T s>
+    Ax = api.op_apply(op, _t(torch, x, dt)).double()
+    Ats = api.op_adjoint(op, _t(torch, s, dt)).double()
+    lhs = float((Ax.cpu().numpy() * s).sum())
+    rhs = float((x * Ats.cpu().numpy()).sum())
+    assert abs(lhs - rhs) <= (1e-5 if dt == "f32" else 1e-12) * np.linalg.norm(Ax.cpu().numpy()) * np.linalg.norm(s)
+
+
+@pytest.mark.parametrize("dt", ["f32", "f64"])
+def test_haar_forward_inverse(env, dt):
+    torch, api, ctx = env
+    n = 64
+    op = api.Operator(ctx, "blur", n, n, dtype=getattr(torch, DT[dt]), kernel=gaussian_kernel(9, 1.5),
+                      haar_levels=3)
+    x = gaussian_probe_like((3, n, n), seed=10)
+    w = api.op_haar(op, _t(torch, x, dt))
+    assert rel(w.cpu(), O.haar_forward(x, 3)) < TOL[dt]
+    assert rel(api.op_haar(op, _t(torch, x, dt), inverse=True).cpu(), O.haar_adjoint(x, 3)) < TOL[dt]
+    assert rel(api.op_haar(op, w, inverse=True).cpu(), x) < TOL[dt]
+
+
+def test_blur_full_size_sampled(env):
+    # the 512 x 512, 25 x 25 sigma = 4 operator at full size, checked on
+    # sampled pixels that the oracle computes one by one
+    torch, api, ctx = env
+    n = 512
+    h = gaussian_kernel(25, 4.0)
+    op = api.Operator(ctx, "blur", n, n, dtype=torch.float32, kernel=h)
+    x = gaussian_probe_like((2, n, n), seed=11)
+    y = api.op_normal(op, _t(torch, x, "f32")).cpu().numpy()
+    rng = np.random.default_rng(0)
+    pts = rng.integers(0, n, size=(40, 2))
+    pts = np.vstack([pts, [[0, 0], [511, 511], [0, 511], [255, 3]]])
+    # H^T H x at (i, j) = sum_{a,b,a',b'} h[a,b] h[a',b'] x[i - a + a', j - b + b'] (periodic)
+    kh = h.shape[0]
+    c = (kh - 1) // 2
+    for b in range(2):
+        for (i, j) in pts:
+            # Hx on the neighbourhood rows/cols needed, then H^T at (i, j)
+            acc = 0.0
+            for a in range(kh):
+                for bb in range(kh):
+                    ii, jj = (i - a + c) % n, (j - bb + c) % n
+                    rows = (ii + np.arange(kh) - c) % n
+                    cols = (jj + np.arange(kh) - c) % n
+                    acc += h[a, bb] * float((h * x[b][np.ix_(rows, cols)]).sum())
+            assert abs(y[b, i, j] - acc) <= 1e-5 * max(1.0, abs(acc)), (b, i, j)

@@ -1,0 +1,106 @@
+"""GPU parity of Algorithm 3 (WAPG / APG) against the float64 oracle after a fixed
+number of iterations, with the same U, S_hat and step size fed to both."""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from oracle import operators as O
+from oracle.philox import gaussian_matrix
+from workloads import gaussian_kernel, phantom
+from tests.gpu_util import rel, require_gpu
+
+pytestmark = pytest.mark.gpu
+EPS64 = 2.0 ** -52
+
+
+@pytest.fixture(scope="module")
+def env():
+    torch, api = require_gpu()
+    return torch, api, api.Context(0)
+
+
+def _setup(kind, n, ell, seed, reg, lam, fit="l2", delta=0.0, decim=1, na=0, nb=0, ksize=9, sigma=1.5,
+           levels=3, noise=0.01):
+    h = gaussian_kernel(ksize, sigma) if kind != "radon" else None
+    opo = O.Operator(kind, n, n, kernel=h, decim=decim, n_angles=na, n_bins=nb)
+    x_true = phantom(n, 8, seed, "mixed")
+    y = opo.apply(x_true)
+    y = y + np.random.default_rng(seed + 1).normal(0, noise * max(1.0, np.abs(y).max()), y.shape)
+    prob = oracle.wapg.Problem(opo, y, lam, reg, fit=fit, huber_delta=delta, haar_levels=levels)
+    phi = lambda V: prob.phi(V.reshape(-1, n, n)).reshape(V.shape[0], -1)
+    ref = oracle.nystrom.nystrom(phi, gaussian_matrix(n * n, ell, seed + 2), EPS64) if ell else None
+    return h, opo, prob, y, ref
+
+
+def _run(env, dt, kind, n, ell, reg, lam, iters, n_inner=10, fit="l2", delta=0.0, decim=1, na=0, nb=0,
+         levels=3, seed=1, precond=True):
+    torch, api, ctx = env
+    h, opo, prob, y, ref = _setup(kind, n, ell if precond else 0, seed, reg, lam, fit, delta, decim, na, nb,
+                                  levels=levels)
+    P = oracle.nystrom.Precond(ref["U"], ref["S_hat"]) if precond else None
+    alpha = 1.0 / oracle.wapg.power_lipschitz(prob, P)
+    x_ref = prob.to_image(oracle.wapg.wapg(prob, alpha, iters, precond=P, n_inner=n_inner)["x"])
+    tdt = torch.float64 if dt == "f64" else torch.float32
+    op = api.Operator(ctx, kind, n, n, dtype=tdt, kernel=h, decim=decim, n_angles=na, n_bins=nb,
+                      haar_levels=levels if reg == "wavelet" else 0)
+    pc = None
+    if precond:
+        pc = api.Precond(ctx, n * n, ell, tdt).import_factor(ref["U"], ref["S_hat"], 0.0, True)
+    sol = api.Solver(ctx, op, torch.from_numpy(y).to(tdt).cuda(), reg, lam, pc=pc, fit=fit, huber_delta=delta,
+                     alpha=alpha, n_inner=n_inner)
+    sol.step(iters)
+    return rel(sol.x().cpu(), x_ref)
+
+
+def test_wapg_wavelet_deblur64_f64(env):
+    # the 64 x 64 float64 deblurring workload: 9 x 9 sigma 1.5, Haar-3, lambda 1e-3, ell 32
+    assert _run(env, "f64", "blur", 64, 32, "wavelet", 1e-3, 15) < 1e-9
+
+
+def test_apg_plain_tv_f64(env):
+    assert _run(env, "f64", "blur", 48, 0, "tv", 5e-3, 12, precond=False) < 1e-10
+
+
+@pytest.mark.parametrize("dt,tol", [("f64", 1e-10), ("f32", 1e-4)])
+def test_wapg_tv_blur(env, dt, tol):
+    assert _run(env, dt, "blur", 64, 16, "tv", 5e-3, 20) < tol
+
+
+def test_wapg_hs_huber_superres_f32(env):
+    assert _run(env, "f32", "blur_decim", 64, 12, "hs", 1e-3, 15, fit="huber", delta=0.01, decim=4) < 1e-4
+
+
+def test_wapg_tv_radon_f32(env):
+    assert _run(env, "f32", "radon", 48, 16, "tv", 2e-4, 10, na=30, nb=70) < 1e-4
+
+
+def test_step_size_estimate_close_to_oracle(env):
+    torch, api, ctx = env
+    h, opo, prob, y, ref = _setup("blur", 64, 16, 3, "tv", 5e-3)
+    P = oracle.nystrom.Precond(ref["U"], ref["S_hat"])
+    a_ref = 1.0 / oracle.wapg.power_lipschitz(prob, P)
+    op = api.Operator(ctx, "blur", 64, 64, dtype=torch.float64, kernel=h)
+    pc = api.Precond(ctx, 64 * 64, 16, torch.float64).import_factor(ref["U"], ref["S_hat"], 0.0, True)
+    sol = api.Solver(ctx, op, torch.from_numpy(y).cuda(), "tv", 5e-3, pc=pc)
+    assert abs(sol.alpha - a_ref) <= 0.02 * a_ref
+
+
+def test_end_to_end_gpu_sketch_reaches_same_minimiser(env):
+    # sketch + factor on the device; preconditioned and plain runs approach the
+    # same minimiser (Sec. III-B: P changes the metric, not the solution)
+    torch, api, ctx = env
+    n = 48
+    h = gaussian_kernel(9, 1.5)
+    opo = O.Operator("blur", n, n, kernel=h)
+    y = opo.apply(phantom(n, 8, 4, "mixed")) + np.random.default_rng(5).normal(0, 0.01, (n, n))
+    op = api.Operator(ctx, "blur", n, n, dtype=torch.float64, kernel=h)
+    Om, Y = api.nys_sketch(ctx, op, 24, seed=9)
+    pc = api.nys_factor(ctx, Om, Y, EPS64)
+    yt = torch.from_numpy(y).cuda()
+    a = api.Solver(ctx, op, yt, "tv", 5e-3, pc=pc, n_inner=20)
+    b = api.Solver(ctx, op, yt, "tv", 5e-3, pc=None, n_inner=20)
+    a.step(1500)
+    b.step(1500)
+    assert rel(a.x().cpu(), b.x().cpu()) < 1e-5
