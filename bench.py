@@ -1,0 +1,386 @@
+#!/usr/bin/env python
+"""Benchmark of the Nystrom-preconditioned reconstruction hot path on one GB300.
+
+Workload (default): the 512 x 512 TV deblurring problem -- 30-ellipse phantom,
+25 x 25 Gaussian blur sigma 4 with periodic boundary, Gaussian noise 0.005,
+anisotropic TV lambda 5e-4, sketch size ell = 200, float32 iterate with the
+sketch (Omega, Y, U) stored in bf16 and float64 core algebra.
+
+One step = one preconditioned solve to 1e-3 relative error: draw Omega, sketch
+Y = A^T A Omega, factor (Algorithm 1), estimate the step size, and run the
+k* WAPG iterations that reach ||x^k - x*|| <= 1e-3 ||x*|| (k* found in an
+untimed pass; x* from a long plain-APG run).  `value` is its wall time on the
+device (ms, lower is better); the plain APG time to the same accuracy
+(including its own step-size estimate) is reported beside it.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl native|reference]
+
+--impl reference times the float64 CPU oracle on a bounded sample of the same
+workload (per-phase costs measured, extrapolated to the whole solve).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import workloads as WL  # noqa: E402
+
+EPS32 = 2.0 ** -23
+METRIC = "time to 1e-3 rel. error (Nyström-precond vs plain PGD), sketch ms, HBM GB/s"
+TARGET = 1e-3
+
+
+def dist_env():
+    return int(os.environ.get("RANK", 0)), int(os.environ.get("LOCAL_RANK", 0)), int(os.environ.get("WORLD_SIZE", 1))
+
+
+# ------------------------------------------------------------ clocks ------
+class ClockSampler:
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device: int):
+        self.device = device
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_bench_{device}.csv")
+
+    def start(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                                          "-i", str(self.device), "-lms", "200"], stdout=self.f,
+                                         stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.f.close()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            p = [t.strip() for t in line.split(",")]
+            if len(p) < 9:
+                continue
+            try:
+                sm.append(float(p[1]))
+                mx.append(float(p[2]))
+            except ValueError:
+                continue
+            for name, v in zip(names, p[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# --------------------------------------------------------- native arm -----
+class Native:
+    def __init__(self, w: WL.Workload, device: int, sketch_dtype: str):
+        import torch
+        from paper_2411_08178_gb300 import api
+        self.torch, self.api, self.w = torch, api, w
+        self.dev = torch.device("cuda", device)
+        self.ctx = api.Context(device)
+        self.sd = torch.bfloat16 if sketch_dtype == "bf16" else torch.float32
+        h = WL.blur_kernel_for(w)
+        self.op = api.Operator(self.ctx, "blur", w.n, w.n, dtype=torch.float32, kernel=h)
+        x_true = torch.from_numpy(WL.ground_truth(w)).float().to(self.dev)
+        clean = api.op_apply(self.op, x_true.reshape(1, w.n, w.n)).reshape(w.n, w.n).double().cpu().numpy()
+        y = WL.degrade(w, clean)
+        self.y_host = torch.from_numpy(y).float().pin_memory()
+        self.y = self.y_host.to(self.dev)
+        self.Om = torch.empty((w.ell, w.n, w.n), dtype=self.sd, device=self.dev)
+        self.Y = torch.empty_like(self.Om)
+        self.pc = api.Precond(self.ctx, w.n * w.n, w.ell, self.sd)
+        self.sketch_factor()
+        self.solver_p = api.Solver(self.ctx, self.op, self.y, "tv", w.lam, pc=self.pc, n_inner=w.n_inner)
+        self.solver_0 = api.Solver(self.ctx, self.op, self.y, "tv", w.lam, pc=None, n_inner=w.n_inner)
+        self.flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=self.dev)   # 256 MB > L2
+
+    def sketch_factor(self):
+        self.api.nys_sketch(self.ctx, self.op, self.w.ell, self.w.seed_omega, store_dtype=self.sd,
+                            out=(self.Om, self.Y))
+        self.api.nys_factor(self.ctx, self.Om, self.Y, EPS32, pc=self.pc)
+
+    def reference_minimiser(self, iters: int = 4000):
+        s = self.solver_0
+        s.restart(False)
+        s.step(iters)
+        x0 = s.x().clone()
+        p = self.solver_p
+        p.restart(False)
+        p.step(1500)
+        agree = self.api.nys_rel_err(self.ctx, p.x(), x0)
+        return x0, agree
+
+    def iterations_to(self, solver, xstar, kmax: int):
+        solver.restart(False)
+        buf = self.torch.empty_like(xstar)
+        for k in range(1, kmax + 1):
+            solver.step(1)
+            solver.x(buf)
+            if self.api.nys_rel_err(self.ctx, buf, xstar) <= TARGET:
+                return k
+        return None
+
+    def solve_precond(self, k):
+        self.sketch_factor()
+        self.solver_p.restart(True)
+        self.solver_p.step(k)
+
+    def solve_plain(self, k):
+        self.solver_0.restart(True)
+        self.solver_0.step(k)
+
+    def time_loop(self, fn, steps, warmup):
+        torch = self.torch
+        stream = torch.cuda.current_stream(self.dev)
+        for _ in range(warmup):
+            fn()
+        times = []
+        for _ in range(steps):
+            self.flush.zero_()
+            torch.cuda.synchronize(self.dev)
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            torch.cuda.nvtx.range_push("timed")
+            a.record(stream)
+            fn()
+            b.record(stream)
+            torch.cuda.nvtx.range_pop()
+            torch.cuda.synchronize(self.dev)
+            times.append(a.elapsed_time(b))
+        return times
+
+    def e2e_step(self, k):
+        # public API end to end: host y -> device, solve, x -> host
+        self.y.copy_(self.y_host, non_blocking=True)
+        self.solver_p.set_data(self.y)
+        self.solve_precond(k)
+        out = self.solver_p.x()
+        self.x_host.copy_(out, non_blocking=True)
+
+    def precond_roofline(self, reps: int = 30):
+        torch = self.torch
+        z = torch.randn(self.w.n * self.w.n, dtype=torch.float32, device=self.dev)
+        out = torch.empty_like(z)
+        stream = torch.cuda.current_stream(self.dev)
+        for _ in range(3):
+            self.api.precond_apply(self.ctx, self.pc, z, True, out)
+        torch.cuda.synchronize(self.dev)
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(reps):
+            self.api.precond_apply(self.ctx, self.pc, z, True, out)
+        b.record(stream)
+        torch.cuda.synchronize(self.dev)
+        ms = a.elapsed_time(b) / reps
+        N, ell = self.w.n * self.w.n, self.w.ell
+        ub = 2 if self.sd == torch.bfloat16 else 4
+        # algorithmic bytes: U read twice (U^T z and U c) + z read twice + out written
+        nbytes = 2 * N * ell * ub + 3 * N * 4
+        return ms, nbytes
+
+
+def run_native(args, w: WL.Workload):
+    import torch
+    rank, local, world = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    torch.cuda.set_device(local)
+    import __graft_entry__ as g
+    g.build()
+    nb = Native(w, local, args.sketch_dtype)
+    t0 = time.time()
+    xstar, agree = nb.reference_minimiser(args.ref_iters)
+    kmax = args.kmax
+    k_p = nb.iterations_to(nb.solver_p, xstar, kmax)
+    k_0 = nb.iterations_to(nb.solver_0, xstar, kmax)
+    setup_s = time.time() - t0
+    k_p_run = k_p or kmax
+    k_0_run = k_0 or kmax
+    # sketch-only time (Algorithm 1 end to end)
+    sketch_ms = statistics.median(nb.time_loop(nb.sketch_factor, max(3, args.steps), 1))
+    clocks = ClockSampler(local)
+    clocks.start()
+    l0 = nb.ctx.launches()
+    if world > 1:
+        torch.distributed.barrier()
+    times_p = nb.time_loop(lambda: nb.solve_precond(k_p_run), args.steps, args.warmup)
+    l1 = nb.ctx.launches()
+    times_0 = nb.time_loop(lambda: nb.solve_plain(k_0_run), args.steps, args.warmup)
+    clk = clocks.stop()
+    if world > 1:
+        torch.distributed.barrier()
+    nb.x_host = torch.empty((w.n, w.n), dtype=torch.float32).pin_memory()
+    times_e2e = nb.time_loop(lambda: nb.e2e_step(k_p_run), args.steps, 1)
+    pre_ms, pre_bytes = nb.precond_roofline()
+    ms_p = statistics.mean(times_p)
+    ms_0 = statistics.mean(times_0)
+    ms_e = statistics.mean(times_e2e)
+    if world > 1:
+        t = torch.tensor([ms_p, ms_0, ms_e], device=nb.dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms_p, ms_0, ms_e = [float(v) for v in t.cpu()]
+    launches = (l1 - l0) // max(1, args.steps + args.warmup)
+    peaks = load_peaks()
+    achieved = pre_bytes / (pre_ms * 1e-3) / 1e9
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = oracle_sample(w, k_p_run, seconds_hint=args.cpu_seconds)
+    out = {
+        "metric": METRIC, "value": round(ms_p, 3), "unit": "ms", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": round(ms_p, 3), "higher_is_better": False, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32 (sketch bf16, core f64)", "data": "synthetic",
+        "config": {"workload": w.name, "n": w.n, "blur": f"{w.blur_k}x{w.blur_k} sigma {w.blur_sigma} periodic",
+                   "reg": "anisotropic TV", "lambda": w.lam, "ell": w.ell, "n_inner": w.n_inner,
+                   "sketch_dtype": args.sketch_dtype, "target_rel_err": TARGET,
+                   "l2": "flushed between timed steps (256 MB write)", "parallelism": f"replicas x{world}"},
+        "plain_ms": round(ms_0, 3), "speedup_vs_plain": round(ms_0 / ms_p, 3),
+        "k_precond": k_p, "k_plain": k_0, "sketch_ms": round(sketch_ms, 3),
+        "precond_plain_agreement": agree,
+        "e2e": {"value": round(ms_e, 3), "unit": "ms", "h2d_bytes_per_step": w.n * w.n * 4,
+                "d2h_bytes_per_step": w.n * w.n * 4},
+        "gpu_launches": int(launches),
+        "roofline": {"bound": "hbm", "kernel": "P^{-1} apply (utz_kernel + coef_kernel + uc_kernel)",
+                     "achieved": round(achieved, 1), "peak": peaks["hbm_gbs"], "peak_source": peaks["src"],
+                     "unit": "GB/s", "frac": round(achieved / peaks["hbm_gbs"], 4), "traffic": None,
+                     "bytes_per_launch": pre_bytes, "ms_per_launch": round(pre_ms, 5)},
+        "clocks": clk,
+        "cpu_baseline": cpu,
+        "setup_s": round(setup_s, 1),
+    }
+    if rank == 0:
+        print(json.dumps(out))
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+def load_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        d = json.load(open(p))
+        return {"hbm_gbs": float(d["hbm_gbs"]), "bf16_tflops": float(d["bf16_tflops"]), "src": "measured"}
+    except Exception:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "src": "fallback"}
+
+
+# --------------------------------------------------- oracle (CPU) arm -----
+def oracle_sample(w: WL.Workload, k_iters: int, seconds_hint: float = 15.0):
+    """Time the float64 oracle on a bounded sample of the workload and scale it
+    to one preconditioned solve: ell sketch columns, the factor, 50 power
+    steps and k_iters WAPG iterations."""
+    import oracle
+    from oracle import operators as O
+    n, ell = w.n, w.ell
+    h = WL.blur_kernel_for(w)
+    opo = O.Operator("blur", n, n, kernel=h)
+    rng = np.random.default_rng(0)
+    t = time.perf_counter
+    # sketch: Phi on 2 probe columns
+    Om2 = oracle.philox.gaussian_matrix(n * n, 2, w.seed_omega).reshape(2, n, n)
+    a = t()
+    opo.normal(Om2)
+    t_col = (t() - a) / 2
+    # factor (steps 3-8) at full ell on a stand-in sketch of the same size
+    Om = rng.standard_normal((ell, n * n))
+    Yf = Om * 0.5 + 0.01 * rng.standard_normal((ell, n * n))
+    a = t()
+    r = oracle.nystrom.nystrom(lambda V: Yf, Om, EPS32)
+    t_factor = t() - a
+    P = oracle.nystrom.Precond(r["U"], np.linspace(1.0, 0.5, ell))
+    x_true = WL.ground_truth(w)
+    y = WL.degrade(w, opo.apply(x_true))
+    prob = oracle.wapg.Problem(opo, y, w.lam, "tv")
+    # one power-iteration step and one WAPG iteration
+    z = rng.standard_normal((n, n))
+    a = t()
+    P.inverse(prob.phi(z))
+    t_pow = t() - a
+    a = t()
+    oracle.wapg.wapg(prob, 0.5, 1, precond=P, n_inner=w.n_inner)
+    t_it = t() - a
+    total = ell * t_col + t_factor + 50 * t_pow + k_iters * t_it
+    cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
+    return {"value": round(total * 1e3, 1), "unit": "ms", "cores": cores, "kind": "oracle",
+            "sample": (f"float64 numpy oracle at {n}x{n}: A^T A on 2 of {ell} probe columns, Algorithm 1 "
+                       f"steps 3-8 at full ell, 1 power step, 1 WAPG iteration (n_inner={w.n_inner}); "
+                       f"scaled to ell columns + 50 power steps + {k_iters} iterations"),
+            "phase_s": {"col": round(t_col, 3), "factor": round(t_factor, 3), "power": round(t_pow, 3),
+                        "iteration": round(t_it, 3)}}
+
+
+def run_reference(args, w: WL.Workload):
+    rank, _, world = dist_env()
+    if rank != 0:
+        return
+    k = w.iters
+    vals = []
+    cpu = None
+    for i in range(args.warmup + args.steps):
+        cpu = oracle_sample(w, k)
+        if i >= args.warmup:
+            vals.append(cpu["value"])
+    v = statistics.mean(vals)
+    cpu["value"] = round(v, 1)
+    out = {"impl": "reference", "metric": METRIC, "value": round(v, 1), "unit": "ms", "n_gpus": world,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(v, 1), "higher_is_better": False,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "config": {"workload": w.name, "n": w.n, "ell": w.ell, "k_assumed": k,
+                      "note": "the oracle cannot reach x* within minutes; its solve time is extrapolated "
+                              "for the configured iteration count"},
+           "cpu_baseline": cpu,
+           "e2e": {"value": round(v, 1), "unit": "ms", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out))
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["native", "reference"], default="native")
+    ap.add_argument("--workload", default=WL.DEBLUR512.name, choices=sorted(WL.PRESETS))
+    ap.add_argument("--sketch-dtype", choices=["bf16", "f32"], default="bf16")
+    ap.add_argument("--ell", type=int, default=0, help="override the sketch size")
+    ap.add_argument("--ref-iters", type=int, default=4000)
+    ap.add_argument("--kmax", type=int, default=3000)
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    w = WL.PRESETS[args.workload]
+    if args.ell:
+        import dataclasses
+        w = dataclasses.replace(w, ell=args.ell)
+    if args.warmup < 3:
+        ap.error("--warmup must be at least 3")
+    if args.impl == "reference":
+        run_reference(args, w)
+    else:
+        run_native(args, w)
+
+
+if __name__ == "__main__":
+    main()

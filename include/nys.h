@@ -74,6 +74,8 @@ const char* nys_last_error(const nys_ctx* ctx);
 int nys_reserve(nys_ctx* ctx, size_t bytes);
 /* Library version string. */
 const char* nys_version(void);
+/* Number of kernels launched through this context since it was created. */
+int nys_launch_count(const nys_ctx* ctx, int64_t* count);
 
 /* ------------------------------------------------------------ operators -- */
 /* Forward models of Sec. IV: periodic blur (IV-A), blur + decimation
@@ -229,6 +231,12 @@ int nys_solver_destroy(nys_solver* solver);
 int pgd_step(nys_solver* solver, int n_steps);
 /* Reset to x = u = 0, t = 1, zero warm starts (keeps alpha). */
 int nys_solver_reset(nys_solver* solver);
+/* Reset, and (if reestimate_alpha and the step size was not given) estimate
+ * alpha again -- after the preconditioner was re-factored in place.
+ * Synchronises when it estimates. */
+int nys_solver_restart(nys_solver* solver, int reestimate_alpha);
+/* Replace the data y (device, M values, copied) and reset the iterate. */
+int nys_solver_set_data(nys_solver* solver, const void* y);
 /* Copy the current iterate, in the image domain (W^T xbar for wavelets),
  * to x_out (device, N values of the op dtype). */
 int nys_solver_get_x(nys_solver* solver, void* x_out);

@@ -60,6 +60,7 @@ PROTOTYPES = {
     "nys_last_error": (C.c_char_p, [vp]),
     "nys_reserve": (i32, [vp, C.c_size_t]),
     "nys_version": (C.c_char_p, []),
+    "nys_launch_count": (i32, [vp, C.POINTER(i64)]),
     "nys_op_create": (i32, [vp, C.POINTER(nys_op_desc), C.POINTER(vp)]),
     "nys_op_destroy": (i32, [vp]),
     "nys_op_sizes": (i32, [vp, C.POINTER(i64), C.POINTER(i64)]),
@@ -80,6 +81,8 @@ PROTOTYPES = {
     "nys_solver_destroy": (i32, [vp]),
     "pgd_step": (i32, [vp, i32]),
     "nys_solver_reset": (i32, [vp]),
+    "nys_solver_restart": (i32, [vp, i32]),
+    "nys_solver_set_data": (i32, [vp, vp]),
     "nys_solver_get_x": (i32, [vp, vp]),
     "nys_solver_alpha": (i32, [vp, C.POINTER(f64)]),
     "nys_rel_err": (i32, [vp, i32, i64, vp, vp, C.POINTER(f64)]),

@@ -65,6 +65,11 @@ class Context:
     def reserve(self, nbytes: int):
         check(_lib().nys_reserve(self.h, nbytes), self.h)
 
+    def launches(self) -> int:
+        n = C.c_int64()
+        check(_lib().nys_launch_count(self.h, C.byref(n)), self.h)
+        return n.value
+
     def last_error(self) -> str:
         return _lib().nys_last_error(self.h).decode()
 
@@ -173,12 +178,17 @@ def op_haar(op: Operator, x: torch.Tensor, inverse: bool = False, out: torch.Ten
 
 
 def nys_sketch(ctx: Context, op: Operator, ell: int, seed: int, phi: str = "ata",
-               store_dtype=None) -> tuple[torch.Tensor, torch.Tensor]:
+               store_dtype=None, out=None) -> tuple[torch.Tensor, torch.Tensor]:
     """Algorithm 1 steps 1-2: returns (Omega, Y), each (ell, n1, n2)."""
     sd = store_dtype or op.dtype
     dev = torch.device("cuda", ctx.device)
-    Om = torch.empty((ell, op.n1, op.n2), dtype=sd, device=dev)
-    Y = torch.empty_like(Om)
+    if out is not None:
+        Om, Y = out
+        if Om.dtype != sd or Y.dtype != sd or Om.numel() != ell * op.N or Y.numel() != ell * op.N:
+            raise ValueError("nys_sketch: output buffers do not match")
+    else:
+        Om = torch.empty((ell, op.n1, op.n2), dtype=sd, device=dev)
+        Y = torch.empty_like(Om)
     kind = {"ata": A.NYS_PHI_ATA, "w_ata_wt": A.NYS_PHI_W_ATA_WT}[phi]
     check(_lib().nys_sketch(ctx.h, op.h, kind, ell, seed, _DT[sd], _ptr(Om), _ptr(Y)), ctx.h)
     return Om, Y
@@ -309,6 +319,12 @@ class Solver:
 
     def reset(self):
         check(_lib().nys_solver_reset(self.h), self.ctx.h)
+
+    def restart(self, reestimate_alpha: bool = True):
+        check(_lib().nys_solver_restart(self.h, int(reestimate_alpha)), self.ctx.h)
+
+    def set_data(self, y: torch.Tensor):
+        check(_lib().nys_solver_set_data(self.h, _ptr(y)), self.ctx.h)
 
     @property
     def alpha(self) -> float:

@@ -74,6 +74,12 @@ extern "C" {
 
 const char* nys_version(void) { return "nys 0.1 (sm_103a)"; }
 
+int nys_launch_count(const nys_ctx* ctx, int64_t* count) {
+    if (!ctx || !count) return fail(nullptr, NYS_EINVAL, "nys_launch_count: null argument");
+    *count = ctx->launches;
+    return NYS_OK;
+}
+
 const char* nys_last_error(const nys_ctx* ctx) {
     if (ctx) return ctx->err.c_str();
     std::lock_guard<std::mutex> g(g_err_mu);

@@ -69,6 +69,7 @@ struct nys_ctx {
     int device = 0;
     cudaStream_t stream = nullptr;
     int sm_count = 152;
+    int64_t launches = 0;   // kernels launched through this context
     std::string err;
     // independent growable scratch regions (see nys::scratch)
     void* slot_ptr[12] = {nullptr};
@@ -128,6 +129,7 @@ void* scratch(nys_ctx* ctx, int slot, size_t bytes, int* status);
 
 #define NYS_LAUNCH_CK(ctx)                                             \
     do {                                                               \
+        (ctx)->launches += 1;                                          \
         cudaError_t e_ = cudaGetLastError();                           \
         if (e_ != cudaSuccess) return nys::cuda_fail((ctx), e_, "kernel launch"); \
     } while (0)

@@ -351,6 +351,31 @@ int nys_solver_reset(nys_solver* S) {
     return S->dt == NYS_F64 ? reset_state<double>(S) : reset_state<float>(S);
 }
 
+int nys_solver_set_data(nys_solver* S, const void* y) {
+    if (!S || !y) return fail(S ? S->ctx : nullptr, NYS_EINVAL, "nys_solver_set_data: null argument");
+    nys_ctx* ctx = S->ctx;
+    const size_t es = dtype_size(S->dt);
+    NYS_CK(ctx, cudaMemcpyAsync(S->y, y, S->M * es, cudaMemcpyDeviceToDevice, ctx->stream));
+    int st;
+    if ((st = op_run(S->op, 1, S->y, S->aty, 1, S->dt, S->dt))) return st;
+    if (S->d.reg == NYS_REG_WAVELET) {
+        if ((st = haar_run(S->op, S->aty, S->tN, 1, 0, S->dt, S->dt))) return st;
+        NYS_CK(ctx, cudaMemcpyAsync(S->aty, S->tN, S->N * es, cudaMemcpyDeviceToDevice, ctx->stream));
+    }
+    return S->dt == NYS_F64 ? reset_state<double>(S) : reset_state<float>(S);
+}
+
+int nys_solver_restart(nys_solver* S, int reestimate_alpha) {
+    if (!S) return fail(nullptr, NYS_EINVAL, "null solver");
+    int st;
+    if (reestimate_alpha && S->d.alpha <= 0.0) {
+        if (S->pc && S->pc->mu != S->pc->mu) return fail(S->ctx, NYS_EINVAL, "restart: preconditioner not set up");
+        st = S->dt == NYS_F64 ? estimate_alpha<double>(S) : estimate_alpha<float>(S);
+        if (st) return st;
+    }
+    return S->dt == NYS_F64 ? reset_state<double>(S) : reset_state<float>(S);
+}
+
 int nys_solver_get_x(nys_solver* S, void* x_out) {
     if (!S || !x_out) return fail(S ? S->ctx : nullptr, NYS_EINVAL, "nys_solver_get_x: null argument");
     if (S->d.reg == NYS_REG_WAVELET) return haar_run(S->op, S->x, x_out, 1, 1, S->dt, S->dt);
