@@ -181,6 +181,26 @@ int nys_precond_setup(nys_ctx* ctx, nys_precond* pc, double mu, int sqrt_shift);
 int precond_apply(nys_ctx* ctx, const nys_precond* pc, int inverse, int dtype,
                   const void* z, void* out, int batch);
 
+/* precond_apply for callers that cannot allocate device memory (no
+ * cudaMalloc is allowed on their side: e.g. while another component captures
+ * the stream into a CUDA graph, or under a fixed memory budget).  The paper
+ * has no counterpart; this is a deployment variant of precond_apply with the
+ * same arguments and results.  Its scratch is one fixed device array of
+ * NYS_NOALLOC_SCRATCH_BYTES (2 MiB) compiled into the library, which every
+ * process that loads the library keeps on each GPU it uses until exit.
+ * Limit: (ceil(N/1024) * ell + ell) values of the compute type (4 bytes for
+ * f32/bf16 factors, 8 for f64) must fit, e.g. N = 512*512 with ell <= 2040 in
+ * f32; larger problems get NYS_EINVAL (use precond_apply).  The call
+ * allocates nothing.  Its first call on a device looks up the array's device
+ * address (cudaGetSymbolAddress); make that first call before any stream
+ * capture.  All calls share the one array: calls whose kernels overlap on the
+ * GPU (different streams, or several contexts) race and give wrong results;
+ * calls issued in order on one stream are safe.  Nothing in the array needs
+ * clearing: each call writes every entry it later reads. */
+#define NYS_NOALLOC_SCRATCH_BYTES (2u * 1024u * 1024u)
+int precond_apply_noalloc(nys_ctx* ctx, const nys_precond* pc, int inverse, int dtype,
+                          const void* z, void* out, int batch);
+
 /* ---------------------------------------------------------------- prox -- */
 typedef struct nys_prox_info {
     int iterations;      /* Newton steps taken                 */

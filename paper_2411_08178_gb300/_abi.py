@@ -74,6 +74,7 @@ PROTOTYPES = {
     "nys_precond_setup": (i32, [vp, C.POINTER(nys_precond), f64, i32]),
     "nys_precond_import": (i32, [vp, C.POINTER(nys_precond), f64, i32]),
     "precond_apply": (i32, [vp, C.POINTER(nys_precond), i32, i32, vp, vp, i32]),
+    "precond_apply_noalloc": (i32, [vp, C.POINTER(nys_precond), i32, i32, vp, vp, i32]),
     "prox_wavelet": (i32, [vp, C.POINTER(nys_precond), f64, i32, i64, vp, vp, vp, C.POINTER(nys_prox_info)]),
     "prox_tv": (i32, [vp, C.POINTER(nys_precond), f64, i32, i32, i32, i32, vp, vp, vp]),
     "prox_hs": (i32, [vp, C.POINTER(nys_precond), f64, i32, i32, i32, i32, vp, vp, vp]),

@@ -19,6 +19,7 @@
 #include "internal.cuh"
 
 #include <cmath>
+#include <mutex>
 
 namespace nys {
 
@@ -432,3 +433,96 @@ int precond_apply(nys_ctx* ctx, const nys_precond* pc, int inverse, int dtype, c
 }
 
 }  // extern "C"
+
+// ------------------------------------------- allocation-free P / P^{-1} ----
+// precond_apply_noalloc runs the same three kernels as precond_apply, but its
+// scratch (the per-block partial sums of U^T z and the ell coefficients) lives
+// in one file-scope device array instead of the context workspace, so the
+// call never allocates: for callers that must not call cudaMalloc (a stream
+// that is being captured into a CUDA graph by someone else, a real-time loop
+// with a fixed memory budget, a host that hands the library only its own
+// buffers).  Every process that loads the library keeps this array on each
+// GPU it uses until it exits.
+static __device__ __align__(256) unsigned char g_noalloc_scratch[NYS_NOALLOC_SCRATCH_BYTES];
+
+namespace {
+std::mutex g_noalloc_mu;
+void* g_noalloc_addr[256] = {nullptr};   // device address of the array, per device
+
+// Device address of g_noalloc_scratch on ctx's device.  In host code the
+// array's name is only a host-side stand-in, so the address is looked up with
+// cudaGetSymbolAddress once per device, with that device current.
+int noalloc_scratch(nys_ctx* ctx, void** out) {
+    if (ctx->device < 0 || ctx->device >= 256) return fail(ctx, NYS_EINVAL, "precond_apply_noalloc: device id");
+    std::lock_guard<std::mutex> g(g_noalloc_mu);
+    if (!g_noalloc_addr[ctx->device]) {
+        int cur = 0;
+        NYS_CK(ctx, cudaGetDevice(&cur));
+        NYS_CK(ctx, cudaSetDevice(ctx->device));
+        void* p = nullptr;
+        const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        cudaSetDevice(cur);
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaGetSymbolAddress(g_noalloc_scratch)");
+        g_noalloc_addr[ctx->device] = p;
+    }
+    *out = g_noalloc_addr[ctx->device];
+    return NYS_OK;
+}
+
+template <class TU, class TZ, class TA>
+int precond_noalloc_typed(nys_ctx* ctx, const nys_precond* pc, int inverse, const void* z, void* out, int batch,
+                          void* scratch_dev) {
+    const nys_precond_priv* pv = (const nys_precond_priv*)pc->priv;
+    const int64_t N = pc->N;
+    const int ell = pc->ell;
+    const int nb = (int)((N + PCH - 1) / PCH);
+    const size_t need = ((size_t)nb * ell + (size_t)ell) * sizeof(TA);
+    if (need > NYS_NOALLOC_SCRATCH_BYTES)
+        return fail(ctx, NYS_EINVAL,
+                    "precond_apply_noalloc: needs %zu scratch bytes (ceil(N/%d) * ell + ell values) but the "
+                    "fixed array holds %d; use precond_apply", need, PCH, (int)NYS_NOALLOC_SCRATCH_BYTES);
+    // every partial and coefficient is written before it is read: nothing
+    // has to be cleared between calls
+    TA* part = (TA*)scratch_dev;
+    TA* coef = part + (size_t)nb * ell;
+    cudaStream_t s = ctx->stream;
+    const int gx = (int)std::min<int64_t>((N + 255) / 256, 4096);
+    for (int b = 0; b < batch; ++b) {
+        const TZ* zb = (const TZ*)z + (size_t)b * N;
+        TZ* ob = (TZ*)out + (size_t)b * N;
+        utz_kernel<TU, TZ, TA><<<dim3(nb, 1), 256, 0, s>>>((const TU*)pc->U, zb, N, ell, part);
+        NYS_LAUNCH_CK(ctx);
+        if (sizeof(TA) == 8)
+            coef_kernel<TA, double><<<dim3((ell + 31) / 32, 1), 256, ell * sizeof(double), s>>>(
+                part, nb, ell, inverse, (const double*)pv->M64, (const double*)pv->d, coef);
+        else
+            coef_kernel<TA, float><<<dim3((ell + 31) / 32, 1), 256, ell * sizeof(double), s>>>(
+                part, nb, ell, inverse, (const float*)pv->M32, (const float*)pv->d32, coef);
+        NYS_LAUNCH_CK(ctx);
+        uc_kernel<TU, TZ, TA><<<dim3(gx, 1), 256, ell * sizeof(TA), s>>>((const TU*)pc->U, zb, N, ell, coef,
+                                                                        inverse ? TA(-1) : TA(1), ob);
+        NYS_LAUNCH_CK(ctx);
+    }
+    return NYS_OK;
+}
+}  // namespace
+
+extern "C" int precond_apply_noalloc(nys_ctx* ctx, const nys_precond* pc, int inverse, int dtype, const void* z,
+                                     void* out, int batch) {
+    if (!ctx || !pc || !z || !out) return fail(ctx, NYS_EINVAL, "precond_apply_noalloc: null argument");
+    if (batch < 0) return fail(ctx, NYS_EINVAL, "precond_apply_noalloc: negative batch");
+    if (!pc->priv || !pc->U) return fail(ctx, NYS_EINVAL, "precond_apply_noalloc: not factored");
+    if (pc->mu != pc->mu) return fail(ctx, NYS_EINVAL, "precond_apply_noalloc: call nys_precond_setup first");
+    if (batch == 0) return NYS_OK;
+    void* sp = nullptr;
+    if (int st = noalloc_scratch(ctx, &sp)) return st;
+    if (dtype == NYS_F64) {
+        if (pc->dtype != NYS_F64) return fail(ctx, NYS_EINVAL, "precond_apply_noalloc: f64 data needs an f64 factor");
+        return precond_noalloc_typed<double, double, double>(ctx, pc, inverse, z, out, batch, sp);
+    }
+    if (dtype != NYS_F32) return fail(ctx, NYS_EINVAL, "precond_apply_noalloc: data must be f32 or f64");
+    if (pc->dtype == NYS_F32) return precond_noalloc_typed<float, float, float>(ctx, pc, inverse, z, out, batch, sp);
+    if (pc->dtype == NYS_BF16)
+        return precond_noalloc_typed<__nv_bfloat16, float, float>(ctx, pc, inverse, z, out, batch, sp);
+    return fail(ctx, NYS_EINVAL, "precond_apply_noalloc: f32 data needs an f32 or bf16 factor");
+}
