@@ -122,26 +122,43 @@ class Native:
                             out=(self.Om, self.Y))
         self.api.nys_factor(self.ctx, self.Om, self.Y, EPS32, pc=self.pc)
 
-    def reference_minimiser(self, iters: int = 4000):
-        s = self.solver_0
-        s.restart(False)
-        s.step(iters)
-        x0 = s.x().clone()
-        p = self.solver_p
-        p.restart(False)
-        p.step(1500)
-        agree = self.api.nys_rel_err(self.ctx, p.x(), x0)
-        return x0, agree
+    def reference_minimiser(self, iters: int = 20000):
+        """x* from a long float64 plain-APG run of the same problem (the float32
+        iterates stall about 6e-4 away from their own limit, so x* must come
+        from float64).  Returns (x* as float32, drift of the last quarter)."""
+        torch, api, w = self.torch, self.api, self.w
+        op64 = api.Operator(self.ctx, "blur", w.n, w.n, dtype=torch.float64, kernel=WL.blur_kernel_for(w))
+        s64 = api.Solver(self.ctx, op64, self.y.double(), "tv", w.lam, pc=None, n_inner=w.n_inner)
+        s64.step(iters * 3 // 4)
+        xa = s64.x().clone()
+        Fa = s64.objective()
+        s64.step(iters - iters * 3 // 4)
+        xb = s64.x().clone()
+        Fb = s64.objective()
+        drift = api.nys_rel_err(self.ctx, xa, xb)
+        s64.close()
+        op64.close()
+        return xb.float(), Fb, {"drift_last_quarter": drift, "F_drift_last_quarter": abs(Fa - Fb) / abs(Fb)}
 
-    def iterations_to(self, solver, xstar, kmax: int):
+    def iterations_to(self, solver, xstar, Fstar, kmax: int):
+        """First k with (F(x^k) - F*)/|F*| <= 1e-3, and first k with
+        ||x^k - x*||/||x*|| <= 1e-3 (None if not reached by kmax; then the
+        error at kmax is returned too)."""
         solver.restart(False)
         buf = self.torch.empty_like(xstar)
+        k_obj = k_it = None
+        err = None
         for k in range(1, kmax + 1):
             solver.step(1)
+            if k_obj is None and (solver.objective() - Fstar) / abs(Fstar) <= TARGET:
+                k_obj = k
             solver.x(buf)
-            if self.api.nys_rel_err(self.ctx, buf, xstar) <= TARGET:
-                return k
-        return None
+            err = self.api.nys_rel_err(self.ctx, buf, xstar)
+            if k_it is None and err <= TARGET:
+                k_it = k
+            if k_obj is not None and (k_it is not None or k >= 4 * k_obj + 200):
+                break
+        return k_obj, k_it, err, k
 
     def solve_precond(self, k):
         self.sketch_factor()
@@ -214,10 +231,10 @@ def run_native(args, w: WL.Workload):
     g.build()
     nb = Native(w, local, args.sketch_dtype)
     t0 = time.time()
-    xstar, agree = nb.reference_minimiser(args.ref_iters)
+    xstar, Fstar, xs_info = nb.reference_minimiser(args.ref_iters)
     kmax = args.kmax
-    k_p = nb.iterations_to(nb.solver_p, xstar, kmax)
-    k_0 = nb.iterations_to(nb.solver_0, xstar, kmax)
+    k_p, kit_p, err_p, kend_p = nb.iterations_to(nb.solver_p, xstar, Fstar, kmax)
+    k_0, kit_0, err_0, kend_0 = nb.iterations_to(nb.solver_0, xstar, Fstar, kmax)
     setup_s = time.time() - t0
     k_p_run = k_p or kmax
     k_0_run = k_0 or kmax
@@ -259,8 +276,13 @@ def run_native(args, w: WL.Workload):
                    "sketch_dtype": args.sketch_dtype, "target_rel_err": TARGET,
                    "l2": "flushed between timed steps (256 MB write)", "parallelism": f"replicas x{world}"},
         "plain_ms": round(ms_0, 3), "speedup_vs_plain": round(ms_0 / ms_p, 3),
+        "criterion": "objective gap (F(x^k) - F*)/|F*| <= 1e-3, F* from the float64 run; the iterate error "
+                     "||x^k - x*||/||x*|| is reported beside it (x* is not resolved to 1e-3 within the run, see "
+                     "xstar.drift_last_quarter)",
         "k_precond": k_p, "k_plain": k_0, "sketch_ms": round(sketch_ms, 3),
-        "precond_plain_agreement": agree,
+        "iterate_err": {"k_precond_1e-3": kit_p, "k_plain_1e-3": kit_0, "precond_err_at_k": [kend_p, err_p],
+                        "plain_err_at_k": [kend_0, err_0]},
+        "xstar": {"from": "float64 plain APG", "iters": args.ref_iters, "F_star": Fstar, **xs_info},
         "e2e": {"value": round(ms_e, 3), "unit": "ms", "h2d_bytes_per_step": w.n * w.n * 4,
                 "d2h_bytes_per_step": w.n * w.n * 4},
         "gpu_launches": int(launches),
@@ -365,8 +387,8 @@ def main():
     ap.add_argument("--workload", default=WL.DEBLUR512.name, choices=sorted(WL.PRESETS))
     ap.add_argument("--sketch-dtype", choices=["bf16", "f32"], default="bf16")
     ap.add_argument("--ell", type=int, default=0, help="override the sketch size")
-    ap.add_argument("--ref-iters", type=int, default=4000)
-    ap.add_argument("--kmax", type=int, default=3000)
+    ap.add_argument("--ref-iters", type=int, default=20000)
+    ap.add_argument("--kmax", type=int, default=8000)
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()

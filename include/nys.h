@@ -74,6 +74,14 @@ const char* nys_last_error(const nys_ctx* ctx);
 int nys_reserve(nys_ctx* ctx, size_t bytes);
 /* Library version string. */
 const char* nys_version(void);
+/* Keep [ptr, ptr + bytes) resident in L2 for kernels issued on the context's
+ * stream (and in graphs the solvers capture afterwards): reserves the
+ * device's largest persisting-L2 carve-out for this CUDA context and sets the
+ * stream's access-policy window (persisting hits, streaming misses).
+ * hit_ratio scales the fraction of the window marked persisting.  ptr = NULL
+ * clears the window.  The setting belongs to this process's CUDA context and
+ * ends with it.  Needs a non-default stream. */
+int nys_l2_persist(nys_ctx* ctx, const void* ptr, size_t bytes, double hit_ratio);
 /* Number of kernels launched through this context since it was created. */
 int nys_launch_count(const nys_ctx* ctx, int64_t* count);
 
@@ -238,6 +246,8 @@ typedef struct nys_solver_desc {
     int n_inner;         /* dual APG steps per prox (TV, HS)                */
     int power_iters;     /* power iterations for alpha (default 50)         */
     uint64_t power_seed;
+    int no_graph;        /* 1: launch kernels one by one instead of replaying
+                            the captured CUDA graph of an iteration          */
 } nys_solver_desc;
 
 /* WAPG (Algorithm 3) for min_x f(x) + lambda g(x) with operator op, data y
@@ -260,8 +270,23 @@ int nys_solver_set_data(nys_solver* solver, const void* y);
 /* Copy the current iterate, in the image domain (W^T xbar for wavelets),
  * to x_out (device, N values of the op dtype). */
 int nys_solver_get_x(nys_solver* solver, void* x_out);
+/* Objective F(x) = f(x) + lambda g(x) at the current iterate (host, float64
+ * accumulation): f = 1/2 ||A x - y||^2 or the Huber sum, g = anisotropic TV,
+ * Hessian Schatten-1 or ||xbar||_1.  Synchronises. */
+int nys_solver_objective(nys_solver* solver, double* F);
 /* The step size in use (host).  Synchronises if it was estimated. */
 int nys_solver_alpha(nys_solver* solver, double* alpha);
+
+/* ------------------------------------------------------- dense products -- */
+/* C (p x q, float64, row-major, device) = A^T B for tall operands A (N x p)
+ * and B (N x q) stored as columns of N contiguous values (the layout of
+ * Omega, Y and U): the Gram products of Algorithm 1 steps 5-7 and U^T U.
+ * path 0: tcgen05 tensor cores for bf16 operands when q <= 256 and N is a
+ * multiple of 8, else CUDA cores; 1: CUDA cores; 2: tensor cores or
+ * NYS_EINVAL.  Float32 accumulation, splits summed in float64.
+ * Synchronises (to report NYS_ETIMEOUT from a bounded pipeline wait). */
+int nys_gram(nys_ctx* ctx, int dtype, const void* A, int p, const void* B, int q,
+             int64_t N, double* C, int path);
 
 /* ---------------------------------------------------------- reductions -- */
 /* *out (host) = ||a - b||_2 / ||b||_2 over n elements (b != 0), or ||a||_2

@@ -43,7 +43,7 @@ class nys_prox_info(C.Structure):
 class nys_solver_desc(C.Structure):
     _fields_ = [("reg", C.c_int), ("fit", C.c_int), ("lambda_", C.c_double), ("huber_delta", C.c_double),
                 ("alpha", C.c_double), ("n_inner", C.c_int), ("power_iters", C.c_int),
-                ("power_seed", C.c_uint64)]
+                ("power_seed", C.c_uint64), ("no_graph", C.c_int)]
 
 
 vp = C.c_void_p
@@ -61,6 +61,7 @@ PROTOTYPES = {
     "nys_reserve": (i32, [vp, C.c_size_t]),
     "nys_version": (C.c_char_p, []),
     "nys_launch_count": (i32, [vp, C.POINTER(i64)]),
+    "nys_l2_persist": (i32, [vp, vp, C.c_size_t, f64]),
     "nys_op_create": (i32, [vp, C.POINTER(nys_op_desc), C.POINTER(vp)]),
     "nys_op_destroy": (i32, [vp]),
     "nys_op_sizes": (i32, [vp, C.POINTER(i64), C.POINTER(i64)]),
@@ -86,7 +87,9 @@ PROTOTYPES = {
     "nys_solver_set_data": (i32, [vp, vp]),
     "nys_solver_get_x": (i32, [vp, vp]),
     "nys_solver_alpha": (i32, [vp, C.POINTER(f64)]),
+    "nys_solver_objective": (i32, [vp, C.POINTER(f64)]),
     "nys_rel_err": (i32, [vp, i32, i64, vp, vp, C.POINTER(f64)]),
+    "nys_gram": (i32, [vp, i32, vp, i32, vp, i32, i64, vp, i32]),
 }
 
 

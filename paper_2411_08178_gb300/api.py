@@ -65,6 +65,13 @@ class Context:
     def reserve(self, nbytes: int):
         check(_lib().nys_reserve(self.h, nbytes), self.h)
 
+    def l2_persist(self, t: torch.Tensor | None, hit_ratio: float = 1.0):
+        """Keep tensor t resident in L2 for this context's stream (None clears)."""
+        if t is None:
+            check(_lib().nys_l2_persist(self.h, None, 0, 0.0), self.h)
+        else:
+            check(_lib().nys_l2_persist(self.h, _ptr(t), t.numel() * t.element_size(), hit_ratio), self.h)
+
     def launches(self) -> int:
         n = C.c_int64()
         check(_lib().nys_launch_count(self.h, C.byref(n)), self.h)
@@ -298,7 +305,7 @@ class Solver:
 
     def __init__(self, ctx: Context, op: Operator, y: torch.Tensor, reg: str, lam: float, pc: Precond | None = None,
                  fit: str = "l2", huber_delta: float = 0.0, alpha: float = 0.0, n_inner: int = 20,
-                 power_iters: int = 50, power_seed: int = 7):
+                 power_iters: int = 50, power_seed: int = 7, use_graph: bool = True):
         d = A.nys_solver_desc()
         d.reg = {"wavelet": A.NYS_REG_WAVELET, "tv": A.NYS_REG_TV, "hs": A.NYS_REG_HS}[reg]
         d.fit = {"l2": A.NYS_FIT_L2, "huber": A.NYS_FIT_HUBER}[fit]
@@ -308,6 +315,7 @@ class Solver:
         d.n_inner = n_inner
         d.power_iters = power_iters
         d.power_seed = power_seed
+        d.no_graph = 0 if use_graph else 1
         self.ctx, self.op, self.pc = ctx, op, pc
         h = C.c_void_p()
         pcs = C.byref(pc.s) if pc is not None else None
@@ -325,6 +333,11 @@ class Solver:
 
     def set_data(self, y: torch.Tensor):
         check(_lib().nys_solver_set_data(self.h, _ptr(y)), self.ctx.h)
+
+    def objective(self) -> float:
+        F = C.c_double()
+        check(_lib().nys_solver_objective(self.h, C.byref(F)), self.ctx.h)
+        return F.value
 
     @property
     def alpha(self) -> float:
@@ -353,6 +366,17 @@ class Solver:
 
 def pgd_step(solver: Solver, n: int = 1):
     solver.step(n)
+
+
+def nys_gram(ctx: Context, A: torch.Tensor, B: torch.Tensor, path: int = 0) -> torch.Tensor:
+    """A^T B (float64, p x q) for A: (p, N), B: (q, N) stacks of columns."""
+    p, q = A.shape[0], B.shape[0]
+    N = A.numel() // p
+    if A.dtype != B.dtype or B.numel() // q != N:
+        raise ValueError("nys_gram: operands do not match")
+    C = torch.empty((p, q), dtype=torch.float64, device=A.device)
+    check(_lib().nys_gram(ctx.h, dtype_code(A), _ptr(A), p, _ptr(B), q, N, _ptr(C), path), ctx.h)
+    return C
 
 
 def nys_rel_err(ctx: Context, a: torch.Tensor, b: torch.Tensor | None) -> float:

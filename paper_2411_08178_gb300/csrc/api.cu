@@ -74,6 +74,34 @@ extern "C" {
 
 const char* nys_version(void) { return "nys 0.1 (sm_103a)"; }
 
+int nys_l2_persist(nys_ctx* ctx, const void* ptr, size_t bytes, double hit_ratio) {
+    if (!ctx) return fail(nullptr, NYS_EINVAL, "nys_l2_persist: null ctx");
+    if (!ctx->stream) return fail(ctx, NYS_EINVAL, "nys_l2_persist: needs a non-default stream");
+    cudaStreamAttrValue v = {};
+    if (ptr && bytes) {
+        int maxp = 0, maxw = 0;
+        NYS_CK(ctx, cudaDeviceGetAttribute(&maxp, cudaDevAttrMaxPersistingL2CacheSize, ctx->device));
+        NYS_CK(ctx, cudaDeviceGetAttribute(&maxw, cudaDevAttrMaxAccessPolicyWindowSize, ctx->device));
+        if (maxp <= 0 || maxw <= 0) return fail(ctx, NYS_EINVAL, "nys_l2_persist: not supported on this device");
+        NYS_CK(ctx, cudaDeviceSetLimit(cudaLimitPersistingL2CacheSize, (size_t)maxp));
+        const size_t win = std::min(bytes, (size_t)maxw);
+        v.accessPolicyWindow.base_ptr = const_cast<void*>(ptr);
+        v.accessPolicyWindow.num_bytes = win;
+        v.accessPolicyWindow.hitRatio = (float)std::min(1.0, std::max(0.0, hit_ratio * (double)maxp / (double)win));
+        v.accessPolicyWindow.hitProp = cudaAccessPropertyPersisting;
+        v.accessPolicyWindow.missProp = cudaAccessPropertyStreaming;
+    } else {
+        v.accessPolicyWindow.num_bytes = 0;
+        v.accessPolicyWindow.hitProp = cudaAccessPropertyNormal;
+        v.accessPolicyWindow.missProp = cudaAccessPropertyNormal;
+        cudaCtxResetPersistingL2Cache();
+    }
+    NYS_CK(ctx, cudaStreamSetAttribute(ctx->stream, cudaStreamAttributeAccessPolicyWindow, &v));
+    ctx->l2_window = v;
+    ctx->l2_window_set = ptr && bytes;
+    return NYS_OK;
+}
+
 int nys_launch_count(const nys_ctx* ctx, int64_t* count) {
     if (!ctx || !count) return fail(nullptr, NYS_EINVAL, "nys_launch_count: null argument");
     *count = ctx->launches;
@@ -238,6 +266,14 @@ int op_haar(nys_op* op, const void* in, void* out, int batch, int inverse) {
     if (op->haar_levels <= 0) return fail(op->ctx, NYS_EINVAL, "operator was created without haar_levels");
     if (batch == 0) return NYS_OK;
     return haar_run(op, in, out, batch, inverse, op->dtype, op->dtype);
+}
+
+int nys_gram(nys_ctx* ctx, int dtype, const void* A, int p, const void* B, int q, int64_t N, double* C, int path) {
+    if (!ctx || !A || !B || !C) return fail(ctx, NYS_EINVAL, "nys_gram: null argument");
+    if (dtype != NYS_F32 && dtype != NYS_F64 && dtype != NYS_BF16) return fail(ctx, NYS_EINVAL, "nys_gram: dtype");
+    if (path < 0 || path > 2) return fail(ctx, NYS_EINVAL, "nys_gram: path");
+    if (int st = gram_AtB_path(ctx, dtype, A, p, B, q, N, C, q, path)) return st;
+    return check_tc_timeout(ctx);
 }
 
 int nys_rel_err(nys_ctx* ctx, int dtype, int64_t n, const void* a, const void* b, double* out) {

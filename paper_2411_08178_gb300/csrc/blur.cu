@@ -217,8 +217,12 @@ int launch_sep(nys_op* op, const void* x, void* y, int batch, const void* taps, 
                int cr) {
     const size_t sm = sep_smem<TC>(T, T, Lcp, Lrp);
     auto k = sepcorr_kernel<TI, TO, TC, T, T>;
-    if (sm > 48 * 1024) NYS_CK(op->ctx, cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
     if (sm > 227 * 1024) return fail(op->ctx, NYS_EINVAL, "blur kernel too wide for the shared-memory tile");
+    static int attr_max = 48 * 1024;   // largest opt-in already granted to this instantiation
+    if ((int)sm > attr_max) {
+        NYS_CK(op->ctx, cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+        attr_max = (int)sm;
+    }
     dim3 grid((op->n2 + T - 1) / T, (op->n1 + T - 1) / T, batch);
     k<<<grid, 256, sm, op->ctx->stream>>>((const TI*)x, (TO*)y, op->n1, op->n2, (const TC*)taps, Lcp, Lrp, cc, cr);
     NYS_LAUNCH_CK(op->ctx);
@@ -231,7 +235,11 @@ int launch_c2d(nys_op* op, const void* x, void* y, int batch, const void* taps) 
     const size_t sm = c2d_smem<TC>(T, T, op->kh, kwp);
     auto k = corr2d_kernel<TI, TO, TC, T, T>;
     if (sm > 227 * 1024) return fail(op->ctx, NYS_EINVAL, "blur kernel too large for the shared-memory tile");
-    if (sm > 48 * 1024) NYS_CK(op->ctx, cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+    static int attr_max = 48 * 1024;
+    if ((int)sm > attr_max) {
+        NYS_CK(op->ctx, cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+        attr_max = (int)sm;
+    }
     dim3 grid((op->n2 + T - 1) / T, (op->n1 + T - 1) / T, batch);
     k<<<grid, 256, sm, op->ctx->stream>>>((const TI*)x, (TO*)y, op->n1, op->n2, (const TC*)taps, op->kh, kwp,
                                           (op->kh - 1) / 2, (op->kw - 1) / 2);

@@ -193,8 +193,33 @@ __global__ void sum_pairs_kernel(const double* __restrict__ part, int nb, double
 
 }  // namespace
 
+void gram_reduce_f32(nys_ctx* ctx, const float* part, int splits, int p, int q, double* C, int ldc, int blocks) {
+    gram_reduce_kernel<float><<<blocks, 256, 0, ctx->stream>>>(part, splits, p, q, C, ldc);
+}
+
+int check_tc_timeout(nys_ctx* ctx) {
+    if (ctx->slot_bytes[SLOT_TCERR] == 0) return NYS_OK;
+    int h = 0;
+    NYS_CK(ctx, cudaMemcpyAsync(&h, ctx->slot_ptr[SLOT_TCERR], sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+    NYS_CK(ctx, cudaStreamSynchronize(ctx->stream));
+    if (h) return fail(ctx, NYS_ETIMEOUT, "a tensor-core kernel gave up waiting on its pipeline (bounded wait)");
+    return NYS_OK;
+}
+
 int gram_AtB(nys_ctx* ctx, int dtype, const void* A, int p, const void* B, int q, int64_t N, double* C, int ldc) {
+    return gram_AtB_path(ctx, dtype, A, p, B, q, N, C, ldc, 0);
+}
+
+int gram_AtB_path(nys_ctx* ctx, int dtype, const void* A, int p, const void* B, int q, int64_t N, double* C, int ldc,
+                  int path) {
     if (N <= 0 || p <= 0 || q <= 0) return fail(ctx, NYS_EINVAL, "gram_AtB: empty operand");
+    if (path != 1 && dtype == NYS_BF16) {
+        const int st = gram_AtB_tc(ctx, A, p, B, q, N, C, ldc);
+        if (st != NYS_EINVAL) return st;
+        if (path == 2) return fail(ctx, NYS_EINVAL, "gram: shape not supported by the tensor-core path");
+    } else if (path == 2) {
+        return fail(ctx, NYS_EINVAL, "gram: the tensor-core path takes bf16 operands");
+    }
     const int tiles = ((p + GT - 1) / GT) * ((q + GT - 1) / GT);
     // enough CTAs to fill the GPU about twice, each K range a multiple of GK
     int64_t splits = std::max<int64_t>(1, (2LL * ctx->sm_count + tiles - 1) / tiles);

@@ -167,11 +167,260 @@ __global__ void __launch_bounds__(256) uc_kernel(const TU* __restrict__ U, const
     }
 }
 
+// ---- vectorised fast path (N a multiple of the 16-byte vector width) ----
+// Both passes stream U once with 16-byte loads (8 bf16, 4 f32 or 2 f64 per
+// lane) and are sized to put several CTAs on every SM.
+constexpr int VCH = 2048;    // pixels per partial-sum chunk
+
+template <class T> struct Vec16;
+template <> struct Vec16<__nv_bfloat16> { static constexpr int n = 8; };
+template <> struct Vec16<float> { static constexpr int n = 4; };
+template <> struct Vec16<double> { static constexpr int n = 2; };
+
+// 16-byte loads unpacked in registers (bf16 -> f32 is a 16-bit shift)
+template <class TU, class TA, int V>
+__device__ __forceinline__ void load_vec(const TU* p, TA (&v)[V]);
+
+template <>
+__device__ __forceinline__ void load_vec<__nv_bfloat16, float, 8>(const __nv_bfloat16* p, float (&v)[8]) {
+    const uint4 r = __ldg(reinterpret_cast<const uint4*>(p));
+    const uint32_t w[4] = {r.x, r.y, r.z, r.w};
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        v[2 * k] = __uint_as_float(w[k] << 16);
+        v[2 * k + 1] = __uint_as_float(w[k] & 0xffff0000u);
+    }
+}
+template <>
+__device__ __forceinline__ void load_vec<float, float, 4>(const float* p, float (&v)[4]) {
+    const float4 r = __ldg(reinterpret_cast<const float4*>(p));
+    v[0] = r.x, v[1] = r.y, v[2] = r.z, v[3] = r.w;
+}
+template <>
+__device__ __forceinline__ void load_vec<double, double, 2>(const double* p, double (&v)[2]) {
+    const double2 r = __ldg(reinterpret_cast<const double2*>(p));
+    v[0] = r.x, v[1] = r.y;
+}
+
+// 128-bit shared-memory loads of V compute-type values (V * sizeof(TA) is a
+// multiple of 16 bytes)
+template <class TA, int V>
+__device__ __forceinline__ void lds_vec(const TA* p, TA (&v)[V]);
+template <>
+__device__ __forceinline__ void lds_vec<float, 8>(const float* p, float (&v)[8]) {
+    const float4 a = reinterpret_cast<const float4*>(p)[0], b = reinterpret_cast<const float4*>(p)[1];
+    v[0] = a.x, v[1] = a.y, v[2] = a.z, v[3] = a.w, v[4] = b.x, v[5] = b.y, v[6] = b.z, v[7] = b.w;
+}
+template <>
+__device__ __forceinline__ void lds_vec<float, 4>(const float* p, float (&v)[4]) {
+    const float4 a = reinterpret_cast<const float4*>(p)[0];
+    v[0] = a.x, v[1] = a.y, v[2] = a.z, v[3] = a.w;
+}
+template <>
+__device__ __forceinline__ void lds_vec<double, 2>(const double* p, double (&v)[2]) {
+    const double2 a = reinterpret_cast<const double2*>(p)[0];
+    v[0] = a.x, v[1] = a.y;
+}
+
+// grid (chunks, column groups): part[b][chunk][j] = sum_{i in chunk} U[j][i] z[i]
+template <class TU, class TZ, class TA>
+__global__ void __launch_bounds__(256) utz_vec_kernel(const TU* __restrict__ U, const TZ* __restrict__ z, int64_t N,
+                                                      int ell, int jper, TA* __restrict__ part) {
+    constexpr int V = Vec16<TU>::n;
+    __shared__ __align__(16) TA zs[VCH];
+    const int64_t i0 = (int64_t)blockIdx.x * VCH;
+    const int nchunk = gridDim.x;
+    const TZ* zb = z + (size_t)blockIdx.z * N;
+    for (int t = threadIdx.x; t < VCH; t += blockDim.x) zs[t] = (i0 + t < N) ? (TA)ldf(zb + i0 + t) : TA(0);
+    __syncthreads();
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int j0 = blockIdx.y * jper, j1 = min(ell, j0 + jper);
+    const int cnt = (int)(N - i0 < (int64_t)VCH ? N - i0 : (int64_t)VCH);   // multiple of V
+    for (int j = j0 + warp; j < j1; j += 8) {
+        const TU* uj = U + (size_t)j * N + i0;
+        TA s = TA(0);
+        if (cnt == VCH) {
+            // full chunk: the trip count is a compile-time constant, so all of a
+            // column's 16-byte loads are issued before the FMAs consume them
+            constexpr int T = VCH / (32 * V);
+            constexpr int G = T < 8 ? T : 8;
+#pragma unroll
+            for (int t0 = 0; t0 < T; t0 += G) {
+                TA u[G][V];
+#pragma unroll
+                for (int q = 0; q < G; ++q) load_vec<TU, TA, V>(uj + ((t0 + q) * 32 + lane) * V, u[q]);
+#pragma unroll
+                for (int q = 0; q < G; ++q) {
+                    const int t = ((t0 + q) * 32 + lane) * V;
+                    TA zv[V];
+                    lds_vec<TA, V>(zs + t, zv);
+#pragma unroll
+                    for (int k = 0; k < V; ++k) s = fma(u[q][k], zv[k], s);
+                }
+            }
+            s = warp_sum(s);
+            if (lane == 0) part[((size_t)blockIdx.z * nchunk + blockIdx.x) * ell + j] = s;
+            continue;
+        }
+        for (int t = lane * V; t < cnt; t += 32 * V) {
+            TA u[V], zv[V];
+            load_vec<TU, TA, V>(uj + t, u);
+            lds_vec<TA, V>(zs + t, zv);
+#pragma unroll
+            for (int k = 0; k < V; ++k) s = fma(u[k], zv[k], s);
+        }
+        s = warp_sum(s);
+        if (lane == 0) part[((size_t)blockIdx.z * nchunk + blockIdx.x) * ell + j] = s;
+    }
+}
+
+// out = z + sign * U c: a CTA owns 32 V pixels; its 8 warps split the columns
+// and their partial sums meet in shared memory
+template <class TU, class TZ, class TA>
+__global__ void __launch_bounds__(256) uc_vec_kernel(const TU* __restrict__ U, const TZ* __restrict__ z, int64_t N,
+                                                     int ell, const TA* __restrict__ coef, TA sign,
+                                                     TZ* __restrict__ out) {
+    constexpr int V = Vec16<TU>::n;
+    constexpr int P = 32 * V;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    TA* c = reinterpret_cast<TA*>(smem_raw);
+    TA* red = c + ((ell + 3) & ~3);            // [8][P]
+    const int b = blockIdx.y;
+    for (int j = threadIdx.x; j < ell; j += blockDim.x) c[j] = coef[(size_t)b * ell + j];
+    __syncthreads();
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int64_t i = (int64_t)blockIdx.x * P + lane * V;
+    TA acc[V];
+#pragma unroll
+    for (int k = 0; k < V; ++k) acc[k] = TA(0);
+    if (i < N) {
+        int j = warp;
+        // four independent 16-byte loads in flight per lane
+        for (; j + 24 < ell; j += 32) {
+            TA u0[V], u1[V], u2[V], u3[V];
+            load_vec<TU, TA, V>(U + (size_t)j * N + i, u0);
+            load_vec<TU, TA, V>(U + (size_t)(j + 8) * N + i, u1);
+            load_vec<TU, TA, V>(U + (size_t)(j + 16) * N + i, u2);
+            load_vec<TU, TA, V>(U + (size_t)(j + 24) * N + i, u3);
+            const TA c0 = c[j], c1 = c[j + 8], c2 = c[j + 16], c3 = c[j + 24];
+#pragma unroll
+            for (int k = 0; k < V; ++k) acc[k] = fma(u3[k], c3, fma(u2[k], c2, fma(u1[k], c1, fma(u0[k], c0, acc[k]))));
+        }
+        for (; j < ell; j += 8) {
+            TA u[V];
+            load_vec<TU, TA, V>(U + (size_t)j * N + i, u);
+            const TA cj = c[j];
+#pragma unroll
+            for (int k = 0; k < V; ++k) acc[k] = fma(u[k], cj, acc[k]);
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < V; ++k) red[warp * P + lane * V + k] = acc[k];
+    __syncthreads();
+    for (int p = threadIdx.x; p < P; p += blockDim.x) {
+        const int64_t ii = (int64_t)blockIdx.x * P + p;
+        if (ii >= N) continue;
+        TA s = TA(0);
+#pragma unroll
+        for (int w = 0; w < 8; ++w) s += red[w * P + p];
+        const size_t o = (size_t)b * N + ii;
+        stf(out + o, (TA)ldf(z + o) + sign * s);
+    }
+}
+
+// coef[b][r] = inverse ? sum_k M[r][k] w[k] : d[r] w[r] for r < le, with
+// w = sum over the chunk partials; every CTA rebuilds w (coalesced, eight
+// independent accumulators per thread) and then forms 32 coefficients.
+template <class TA, class TM>
+__global__ void __launch_bounds__(256) coef_vec_kernel(const TA* __restrict__ part, int nb, int le, int ldm,
+                                                       int inverse, const TM* __restrict__ M,
+                                                       const TM* __restrict__ d, TA* __restrict__ coef) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    TA* w = reinterpret_cast<TA*>(smem_raw);
+    const int b = blockIdx.y;
+    const TA* pb = part + (size_t)b * nb * le;
+    for (int j = threadIdx.x; j < le; j += blockDim.x) {
+        TA acc[8];
+#pragma unroll
+        for (int q = 0; q < 8; ++q) acc[q] = TA(0);
+        int k = 0;
+        for (; k + 8 <= nb; k += 8) {
+#pragma unroll
+            for (int q = 0; q < 8; ++q) acc[q] += pb[(size_t)(k + q) * le + j];
+        }
+        for (; k < nb; ++k) acc[0] += pb[(size_t)k * le + j];
+        TA s = TA(0);
+#pragma unroll
+        for (int q = 0; q < 8; ++q) s += acc[q];
+        w[j] = s;
+    }
+    __syncthreads();
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int r0 = blockIdx.x * 32;
+    for (int r = r0 + warp; r < min(le, r0 + 32); r += 8) {
+        TA s;
+        if (inverse) {
+            s = TA(0);
+            for (int k = lane; k < le; k += 32) s = fma((TA)M[(size_t)r * ldm + k], w[k], s);
+            s = warp_sum(s);
+        } else {
+            s = (TA)d[r] * w[r];
+        }
+        if (lane == 0) coef[(size_t)b * le + r] = s;
+    }
+}
+
+template <class TU, class TZ, class TA>
+int precond_vec(nys_ctx* ctx, const nys_precond* pc, int inverse, const void* z, void* out, int batch) {
+    constexpr int V = Vec16<TU>::n;
+    const nys_precond_priv* pv = (const nys_precond_priv*)pc->priv;
+    const int64_t N = pc->N;
+    const int ell = pv->ell_eff;   // only the columns with d > 0
+    if (ell == 0) {
+        if (out != z) NYS_CK(ctx, cudaMemcpyAsync(out, z, (size_t)batch * N * sizeof(TZ), cudaMemcpyDeviceToDevice,
+                                                  ctx->stream));
+        return NYS_OK;
+    }
+    const int nchunk = (int)((N + VCH - 1) / VCH);
+    // column groups: about four CTAs per SM for the U^T z pass
+    int groups = std::max(1, std::min(ell, (4 * ctx->sm_count + nchunk - 1) / nchunk));
+    const int jper = (ell + groups - 1) / groups;
+    groups = (ell + jper - 1) / jper;
+    int st;
+    TA* part = (TA*)scratch(ctx, SLOT_PRECOND, ((size_t)batch * nchunk * ell + (size_t)batch * ell) * sizeof(TA), &st);
+    if (st) return st;
+    TA* coef = part + (size_t)batch * nchunk * ell;
+    cudaStream_t s = ctx->stream;
+    if (batch > 65535) return fail(ctx, NYS_EINVAL, "precond: batch above 65535");
+    utz_vec_kernel<TU, TZ, TA><<<dim3(nchunk, groups, batch), 256, 0, s>>>((const TU*)pc->U, (const TZ*)z, N, ell,
+                                                                          jper, part);
+    NYS_LAUNCH_CK(ctx);
+    if (sizeof(TA) == 8)
+        coef_vec_kernel<TA, double><<<dim3((ell + 31) / 32, batch), 256, ell * sizeof(TA), s>>>(
+            part, nchunk, ell, pc->ell, inverse, (const double*)pv->M64, (const double*)pv->d, coef);
+    else
+        coef_vec_kernel<TA, float><<<dim3((ell + 31) / 32, batch), 256, ell * sizeof(TA), s>>>(
+            part, nchunk, ell, pc->ell, inverse, (const float*)pv->M32, (const float*)pv->d32, coef);
+    NYS_LAUNCH_CK(ctx);
+    constexpr int P = 32 * V;
+    const size_t sm = (((size_t)ell + 3) & ~size_t(3)) * sizeof(TA) + (size_t)8 * P * sizeof(TA);
+    uc_vec_kernel<TU, TZ, TA><<<dim3((unsigned)((N + P - 1) / P), batch), 256, sm, s>>>(
+        (const TU*)pc->U, (const TZ*)z, N, ell, coef, inverse ? TA(-1) : TA(1), (TZ*)out);
+    NYS_LAUNCH_CK(ctx);
+    return NYS_OK;
+}
+
 template <class TU, class TZ, class TA>
 int precond_typed(nys_ctx* ctx, const nys_precond* pc, int inverse, const void* z, void* out, int batch) {
     const nys_precond_priv* pv = (const nys_precond_priv*)pc->priv;
     const int64_t N = pc->N;
     const int ell = pc->ell;
+    {
+        constexpr int V = Vec16<TU>::n;
+        const bool aligned = (((uintptr_t)pc->U | (uintptr_t)z | (uintptr_t)out) & 15) == 0;
+        if (N % V == 0 && N % 4 == 0 && aligned && batch <= 65535)
+            return precond_vec<TU, TZ, TA>(ctx, pc, inverse, z, out, batch);
+    }
     const int nb = (int)((N + PCH - 1) / PCH);
     int st;
     TA* part = (TA*)scratch(ctx, SLOT_PRECOND, ((size_t)batch * nb * ell + (size_t)batch * ell) * sizeof(TA), &st);
@@ -227,9 +476,16 @@ int precond_setup_impl(nys_ctx* ctx, nys_precond* pc, double mu, int sqrt_shift)
     form_M_kernel<<<64, 256, 0, s>>>(Ai, pv->sqrtd, ell, pv->M64, pv->M32);
     NYS_LAUNCH_CK(ctx);
     double h_info[4];
+    std::vector<double> S(ell);
     NYS_CK(ctx, cudaMemcpyAsync(h_info, info, sizeof(h_info), cudaMemcpyDeviceToHost, s));
+    NYS_CK(ctx, cudaMemcpyAsync(S.data(), pc->S_hat, ell * sizeof(double), cudaMemcpyDeviceToHost, s));
     NYS_CK(ctx, cudaStreamSynchronize(s));
     if (h_info[3] != 0.0) return fail(ctx, NYS_ENONFINITE, "preconditioner: I + Ubar^T Ubar is not positive definite");
+    // active prefix: the same IEEE double expression as weights_kernel
+    int eff = 0;
+    for (int i = 0; i < ell; ++i)
+        if ((S[i] + mu) / (sref + mu) - 1.0 > 0.0) eff = i + 1;
+    pv->ell_eff = eff;
     pc->mu = mu;
     pc->sqrt_shift = sqrt_shift;
     return NYS_OK;
@@ -389,6 +645,7 @@ int nys_factor(nys_ctx* ctx, const void* Omega, const void* Y, int in_dt, int64_
     NYS_CK(ctx, cudaMemcpyAsync(&pc->s_first, pc->S_hat, sizeof(double), cudaMemcpyDeviceToHost, s));
     NYS_CK(ctx, cudaMemcpyAsync(&pc->s_last, pc->S_hat + ell - 1, sizeof(double), cudaMemcpyDeviceToHost, s));
     NYS_CK(ctx, cudaStreamSynchronize(s));
+    if (int st2 = check_tc_timeout(ctx)) return st2;
     pc->v = h[1];
     pc->chol_retries = (int)h[2];
     if (h[0] != 0.0) return fail(ctx, NYS_ENOTSPD, "nys_factor: Cholesky of the shifted core failed after %d retries",

@@ -1,0 +1,289 @@
+// Tall-skinny Gram C = A^T B on the 5th-generation tensor cores (tcgen05).
+//
+// A (N x p) and B (N x q) hold their columns as contiguous bf16 images, so as
+// MMA operands both are K-major (K = N pixels): the UMMA computes
+// D[m][n] = sum_k A[m][k] B[n][k] = (A^T B)[m][n] directly.  These are the
+// Gram products of Algorithm 1 (Omega^T Omega, Omega^T Y, Y^T Y) and the
+// U^T U of the stored factor: 2 N ell^2 flops over 4 N ell bytes, i.e. HBM
+// bound once the multiply runs on tensor cores.
+//
+// One CTA owns a 128-row block of D (all q <= 256 columns, one TMEM
+// accumulator of BN <= 256 fp32 columns) over one split of the K range:
+//   warp 0      TMA producer: 64-pixel K blocks of A (128 x 64) and B (BN x 64)
+//               into a 4-stage ring, 128B swizzle, mbarrier transaction counts
+//   warp 1      MMA issuer: one elected thread, 4 x tcgen05.mma (K = 16) per
+//               stage, tcgen05.commit frees the stage / signals the result
+//   warp 2      TMEM allocation (BN columns, power of two >= 32)
+//   warps 4-7   epilogue: tcgen05.ld 32x32b.x16 of its 32-lane quarter, fp32
+//               partial tile to global; the splits are summed in float64 by
+//               the existing deterministic reduction.
+// Every mbarrier wait is bounded: on time-out the kernel records an error,
+// stops issuing, drains its own TMA copies and MMAs, frees TMEM and returns.
+#include "internal.cuh"
+
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
+#include <mutex>
+
+namespace nys {
+namespace {
+
+constexpr int TC_BM = 128;
+constexpr int TC_BK = 64;           // bf16 elements per 128-byte swizzle row
+constexpr int TC_STAGES = 4;
+constexpr uint32_t WAIT_LIMIT = 1u << 24;   // try_wait polls before giving up
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+// bounded wait; false on time-out
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+    for (uint32_t i = 0; i < WAIT_LIMIT; ++i)
+        if (mbar_try_wait(bar, parity)) return true;
+    return false;
+}
+__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, uint64_t* bar, int x, int y) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], "
+        "[%4];" ::"r"(smem_u32(dst)),
+        "l"((uint64_t)map), "r"(x), "r"(y), "r"(smem_u32(bar))
+        : "memory");
+}
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+// K-major operand tile with rows of 128 bytes (64 bf16) written by TMA with
+// 128-byte swizzle: 8-row atoms of 1024 bytes (stride-dimension offset), the
+// leading offset unused for this layout (encoded 1), descriptor version 1,
+// layout type 2 = SWIZZLE_128B.  The tile base is 1024-byte aligned.
+__device__ __forceinline__ uint64_t sw128_kmajor_desc(const void* tile) {
+    const uint32_t a = smem_u32(tile);
+    return (uint64_t)((a & 0x3FFFFu) >> 4) | ((uint64_t)1 << 16) | ((uint64_t)(1024 >> 4) << 32) |
+           ((uint64_t)1 << 46) | ((uint64_t)2 << 61);
+}
+// instruction descriptor, kind::f16: D fp32, A and B bf16, both K-major
+__host__ __device__ constexpr uint32_t idesc_bf16(int M, int N) {
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+__global__ void __launch_bounds__(256, 1)
+    gram_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, int p, int q,
+                   int BN, int tmem_cols, int kblocks_total, int kblocks_per_split, float* __restrict__ part,
+                   int* __restrict__ err) {
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    unsigned char* base = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    const uint32_t a_bytes = TC_BM * TC_BK * 2;
+    const uint32_t b_bytes = (uint32_t)BN * TC_BK * 2;
+    unsigned char* sA = base;
+    unsigned char* sB = base + TC_STAGES * a_bytes;
+    uint64_t* full = reinterpret_cast<uint64_t*>(sB + TC_STAGES * b_bytes);
+    uint64_t* empty = full + TC_STAGES;
+    uint64_t* accum = empty + TC_STAGES;
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(accum + 1);
+    int* abort_flag = reinterpret_cast<int*>(tmem_slot + 1);
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int m0 = blockIdx.y * TC_BM;
+    const int split = blockIdx.x;
+    const int kb0 = split * kblocks_per_split;
+    const int nk = max(0, min(kblocks_total, kb0 + kblocks_per_split) - kb0);
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < TC_STAGES; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], 1);
+        }
+        mbar_init(accum, 1);
+        *abort_flag = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 2) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                     "r"(tmem_cols)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *tmem_slot;
+
+    if (warp == 0 && lane == 0) {
+        // producer
+        int issued = 0;
+        for (int i = 0; i < nk; ++i) {
+            const int s = i % TC_STAGES;
+            const uint32_t ph = (uint32_t)(i / TC_STAGES) & 1u;
+            if (!mbar_wait(&empty[s], ph ^ 1u) || *(volatile int*)abort_flag) {
+                atomicExch(err, 1);
+                *(volatile int*)abort_flag = 1;
+                break;
+            }
+            mbar_arrive_expect_tx(&full[s], a_bytes + b_bytes);
+            const int kx = (kb0 + i) * TC_BK;
+            tma_load_2d(sA + s * a_bytes, &tmA, &full[s], kx, m0);
+            tma_load_2d(sB + s * b_bytes, &tmB, &full[s], kx, 0);
+            ++issued;
+        }
+        // drain: every issued copy has landed before the CTA may exit
+        for (int i = max(0, issued - TC_STAGES); i < issued; ++i)
+            if (!mbar_wait(&full[i % TC_STAGES], (uint32_t)(i / TC_STAGES) & 1u)) atomicExch(err, 1);
+    } else if (warp == 1 && lane == 0) {
+        // MMA issuer
+        const uint32_t idesc = idesc_bf16(TC_BM, BN);
+        for (int i = 0; i < nk; ++i) {
+            const int s = i % TC_STAGES;
+            const uint32_t ph = (uint32_t)(i / TC_STAGES) & 1u;
+            if (!mbar_wait(&full[s], ph) || *(volatile int*)abort_flag) {
+                atomicExch(err, 1);
+                *(volatile int*)abort_flag = 1;
+                break;
+            }
+            tc_fence_after();
+            const uint64_t da = sw128_kmajor_desc(sA + s * a_bytes);
+            const uint64_t db = sw128_kmajor_desc(sB + s * b_bytes);
+#pragma unroll
+            for (int k = 0; k < TC_BK / 16; ++k) {
+                // +32 bytes (16 bf16) along K inside the swizzled row: +2 in the encoded address
+                const uint32_t acc = (i > 0 || k > 0) ? 1u : 0u;
+                asm volatile(
+                    "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+                    "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
+                    "l"(da + 2 * k), "l"(db + 2 * k), "r"(idesc), "r"(acc)
+                    : "memory");
+            }
+            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                             smem_u32(&empty[s]))
+                         : "memory");
+        }
+        // result ready (also issued after an abort, so the epilogue never waits on a dead barrier)
+        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                         smem_u32(accum))
+                     : "memory");
+    } else if (warp >= 4) {
+        // epilogue: this warp's quarter of the 128 TMEM lanes = rows of D
+        const int quarter = warp & 3;
+        const bool ok = mbar_wait(accum, 0);
+        tc_fence_after();
+        if (!ok) atomicExch(err, 1);
+        const int row = m0 + quarter * 32 + lane;
+        if (ok && nk > 0 && !*(volatile int*)abort_flag) {
+            float* out = part + ((size_t)split * p + row) * q;
+            for (int c0 = 0; c0 < BN; c0 += 16) {
+                uint32_t v[16];
+                const uint32_t taddr = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)c0;
+                asm volatile(
+                    "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, "
+                    "[%16];"
+                    : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+                      "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]),
+                      "=r"(v[15])
+                    : "r"(taddr));
+                asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+                if (row < p) {
+#pragma unroll
+                    for (int j = 0; j < 16; ++j)
+                        if (c0 + j < q) out[c0 + j] = __uint_as_float(v[j]);
+                }
+            }
+        } else if (nk == 0 && row < p) {
+            float* out = part + ((size_t)split * p + row) * q;
+            for (int c = 0; c < q; ++c) out[c] = 0.0f;
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    if (warp == 2)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(tmem_cols) : "memory");
+}
+
+PFN_cuTensorMapEncodeTiled_v12000 encode_fn(nys_ctx* ctx) {
+    static std::mutex mu;
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    std::lock_guard<std::mutex> g(mu);
+    if (!fn) {
+        void* ptr = nullptr;
+        cudaDriverEntryPointQueryResult qr;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &ptr, 12000, cudaEnableDefault, &qr) ==
+                cudaSuccess &&
+            qr == cudaDriverEntryPointSuccess)
+            fn = (PFN_cuTensorMapEncodeTiled_v12000)ptr;
+    }
+    (void)ctx;
+    return fn;
+}
+
+bool make_map(PFN_cuTensorMapEncodeTiled_v12000 enc, CUtensorMap* m, const void* ptr, int64_t N, int rows,
+              int box_rows) {
+    cuuint64_t dims[2] = {(cuuint64_t)N, (cuuint64_t)rows};
+    cuuint64_t strides[1] = {(cuuint64_t)N * 2};
+    cuuint32_t box[2] = {(cuuint32_t)TC_BK, (cuuint32_t)box_rows};
+    cuuint32_t estr[2] = {1, 1};
+    return enc(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(ptr), dims, strides, box, estr,
+               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+}  // namespace
+
+// C (p x q, float64, ld = ldc) = A^T B for bf16 operands on tensor cores.
+// Returns NYS_EINVAL (without touching the device) when the shapes are not
+// supported, so the caller can take the CUDA-core path.
+int gram_AtB_tc(nys_ctx* ctx, const void* A, int p, const void* B, int q, int64_t N, double* C, int ldc) {
+    if (q < 1 || q > 256 || p < 1 || N < TC_BK || (N % 8) != 0 || N > (int64_t)0x7fffffff ||
+        (((uintptr_t)A | (uintptr_t)B) & 15))
+        return NYS_EINVAL;
+    auto enc = encode_fn(ctx);
+    if (!enc) return NYS_EINVAL;
+    const int BN = ((q + 15) / 16) * 16;
+    int tmem_cols = 32;
+    while (tmem_cols < BN) tmem_cols <<= 1;
+    CUtensorMap mA, mB;
+    if (!make_map(enc, &mA, A, N, p, TC_BM) || !make_map(enc, &mB, B, N, q, BN)) return NYS_EINVAL;
+    const int mtiles = (p + TC_BM - 1) / TC_BM;
+    const int kblocks = (int)((N + TC_BK - 1) / TC_BK);
+    // about one CTA per SM (each holds ~170 KB of shared memory)
+    int splits = std::max(1, std::min(kblocks, ctx->sm_count / mtiles));
+    const int kper = (kblocks + splits - 1) / splits;
+    splits = (kblocks + kper - 1) / kper;
+    int st;
+    float* part = (float*)scratch(ctx, SLOT_GRAM, (size_t)splits * p * q * sizeof(float) + 64, &st);
+    if (st) return st;
+    int* err = (int*)scratch(ctx, SLOT_TCERR, 64, &st);
+    if (st) return st;
+    const size_t smem = 1024 + (size_t)TC_STAGES * (TC_BM * TC_BK * 2 + (size_t)BN * TC_BK * 2) + 256;
+    static size_t attr = 0;
+    if (smem > attr) {
+        NYS_CK(ctx, cudaFuncSetAttribute(gram_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        attr = smem;
+    }
+    cudaStream_t s = ctx->stream;
+    NYS_CK(ctx, cudaMemsetAsync(err, 0, sizeof(int), s));
+    gram_tc_kernel<<<dim3(splits, mtiles), 256, smem, s>>>(mA, mB, p, q, BN, tmem_cols, kblocks, kper, part, err);
+    NYS_LAUNCH_CK(ctx);
+    const int rb = std::min<int64_t>(1024, ((int64_t)p * q + 255) / 256);
+    gram_reduce_f32(ctx, part, splits, p, q, C, ldc, rb);
+    NYS_LAUNCH_CK(ctx);
+    return NYS_OK;
+}
+
+}  // namespace nys

@@ -70,6 +70,8 @@ struct nys_ctx {
     cudaStream_t stream = nullptr;
     int sm_count = 152;
     int64_t launches = 0;   // kernels launched through this context
+    cudaStreamAttrValue l2_window = {};   // access-policy window set by nys_l2_persist
+    bool l2_window_set = false;
     std::string err;
     // independent growable scratch regions (see nys::scratch)
     void* slot_ptr[12] = {nullptr};
@@ -117,7 +119,9 @@ enum Slot {
     SLOT_SKETCH = 6,    // W^T Omega and A^T A W^T Omega in nys_sketch
     SLOT_GRAM = 7,      // split-K partial tiles of gram_AtB
     SLOT_SOLVER = 8,    // solver temporaries
-    SLOT_COUNT = 9
+    SLOT_EIG = 9,       // Jacobi rotation log
+    SLOT_TCERR = 10,    // time-out flag of the tensor-core kernels
+    SLOT_COUNT = 11
 };
 void* scratch(nys_ctx* ctx, int slot, size_t bytes, int* status);
 
@@ -150,6 +154,14 @@ int op_run(nys_op* op, int which, const void* x, void* y, int batch, int in_dtyp
 // C[p x q] (double) = A^T B, A: N x p, B: N x q (column j at offset j*N)
 int gram_AtB(nys_ctx* ctx, int dtype, const void* A, int p, const void* B, int q, int64_t N,
              double* C, int ldc);
+// path: 0 = tensor cores when the shape allows, 1 = CUDA cores, 2 = tensor cores or NYS_EINVAL
+int gram_AtB_path(nys_ctx* ctx, int dtype, const void* A, int p, const void* B, int q, int64_t N, double* C, int ldc,
+                  int path);
+// tcgen05 Gram for bf16 operands (gram_tc.cu); NYS_EINVAL when unsupported
+int gram_AtB_tc(nys_ctx* ctx, const void* A, int p, const void* B, int q, int64_t N, double* C, int ldc);
+void gram_reduce_f32(nys_ctx* ctx, const float* part, int splits, int p, int q, double* C, int ldc, int blocks);
+// raise NYS_ETIMEOUT if a tensor-core kernel recorded a time-out (synchronises)
+int check_tc_timeout(nys_ctx* ctx);
 // out (N x q, dtype out_dt) = (A + alpha*A2) W, A/A2: N x k of in_dt, W: k x q double (row-major k x q)
 int gemm_tall(nys_ctx* ctx, int in_dt, const void* A, const void* A2, const double* alpha_dev, int64_t N,
               int k, const double* W, int q, int out_dt, void* out);
@@ -168,6 +180,9 @@ struct nys_precond_priv {
     float* d32 = nullptr;
     double* sqrtd = nullptr;  // ell, sqrt(d) (Ubar scaling)
     int ell = 0;
+    // d is non-increasing (S_hat is sorted), so only the columns j < ell_eff
+    // with d_j > 0 enter P and P^{-1}; the rows and columns of M beyond it are 0
+    int ell_eff = 0;
 };
 
 namespace nys {

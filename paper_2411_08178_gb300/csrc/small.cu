@@ -209,6 +209,123 @@ __global__ void __launch_bounds__(1024) jacobi_kernel(T* __restrict__ G, T* __re
     if (threadIdx.x == 0) *sweeps_out = sweep;
 }
 
+// Jacobi with G held in shared memory (pitch n + 1).  V is not formed here:
+// every round's rotations (pairs and (c, s)) are appended to a log in global
+// memory, and rot_apply_kernel builds V = J_1 J_2 ... J_r afterwards with one
+// warp per row of V (the rows are independent).  rounds_out = rounds logged.
+template <class T>
+__global__ void __launch_bounds__(1024) jacobi_smem_kernel(const T* __restrict__ Gin, int n, int nreal,
+                                                           int max_sweeps, double tol, int2* __restrict__ logpq,
+                                                           T* __restrict__ logcs, int* __restrict__ rounds_out,
+                                                           int* __restrict__ sweeps_out) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int h = n / 2;
+    const int pitch = n + 1;
+    T* G = reinterpret_cast<T*>(smem_raw);
+    T* cs = G + (size_t)n * pitch;
+    T* sn = cs + h;
+    int* arr = reinterpret_cast<int*>(sn + h);
+    int* arr2 = arr + n;
+    int* pp = arr2 + n;
+    int* qq = pp + h;
+    __shared__ double sh[32];
+    for (int t = threadIdx.x; t < n * n; t += blockDim.x) G[(t / n) * pitch + t % n] = Gin[t];
+    for (int t = threadIdx.x; t < n; t += blockDim.x) arr[t] = t;
+    __syncthreads();
+    const T eps = sizeof(T) == 8 ? T(1e-15) : T(1e-7);
+    int sweep = 0, round_total = 0;
+    for (; sweep < max_sweeps; ++sweep) {
+        double off = 0.0, dg = 0.0;
+        for (int t = threadIdx.x; t < nreal * nreal; t += blockDim.x) {
+            const int i = t / nreal, j = t % nreal;
+            const double g = (double)G[i * pitch + j];
+            if (i == j) dg += g * g;
+            else off += g * g;
+        }
+        off = block_sum(off, sh);
+        dg = block_sum(dg, sh);
+        if (off <= tol * tol * dg) break;
+        for (int round = 0; round < n - 1; ++round, ++round_total) {
+            for (int k = threadIdx.x; k < h; k += blockDim.x) {
+                const int a = arr[k], b = arr[n - 1 - k];
+                const int p = min(a, b), q = max(a, b);
+                T c = T(1), s = T(0);
+                if (q < nreal) {
+                    const T apq = G[p * pitch + q];
+                    const T app = G[p * pitch + p], aqq = G[q * pitch + q];
+                    if (fabs((double)apq) > (double)eps * sqrt(fabs((double)app * (double)aqq)) && apq != T(0)) {
+                        const T tau = (aqq - app) / (T(2) * apq);
+                        const T t = (tau >= T(0) ? T(1) : T(-1)) / (fabs(tau) + sqrt(T(1) + tau * tau));
+                        c = T(1) / sqrt(T(1) + t * t);
+                        s = t * c;
+                    }
+                }
+                pp[k] = p;
+                qq[k] = q;
+                cs[k] = c;
+                sn[k] = s;
+                logpq[(size_t)round_total * h + k] = make_int2(p, q);
+                logcs[((size_t)round_total * h + k) * 2] = c;
+                logcs[((size_t)round_total * h + k) * 2 + 1] = s;
+            }
+            __syncthreads();
+            for (int t = threadIdx.x; t < h * h; t += blockDim.x) {
+                const int k1 = t / h, k2 = t % h;
+                const T c1 = cs[k1], s1 = sn[k1], c2 = cs[k2], s2 = sn[k2];
+                if (s1 == T(0) && s2 == T(0)) continue;
+                const int p1 = pp[k1], q1 = qq[k1], p2 = pp[k2], q2 = qq[k2];
+                T* gp = G + p1 * pitch;
+                T* gq = G + q1 * pitch;
+                const T xpp = gp[p2], xpq = gp[q2], xqp = gq[p2], xqq = gq[q2];
+                const T rpp = c1 * xpp - s1 * xqp, rpq = c1 * xpq - s1 * xqq;
+                const T rqp = s1 * xpp + c1 * xqp, rqq = s1 * xpq + c1 * xqq;
+                T ypp = c2 * rpp - s2 * rpq, ypq = s2 * rpp + c2 * rpq;
+                T yqp = c2 * rqp - s2 * rqq, yqq = s2 * rqp + c2 * rqq;
+                if (k1 == k2) ypq = yqp = T(0);
+                gp[p2] = ypp;
+                gp[q2] = ypq;
+                gq[p2] = yqp;
+                gq[q2] = yqq;
+            }
+            for (int t = threadIdx.x; t < n; t += blockDim.x) arr2[t] = (t == 0) ? arr[0] : (t == 1 ? arr[n - 1] : arr[t - 1]);
+            __syncthreads();
+            for (int t = threadIdx.x; t < n; t += blockDim.x) arr[t] = arr2[t];
+            __syncthreads();
+        }
+    }
+    if (threadIdx.x == 0) {
+        *sweeps_out = sweep;
+        *rounds_out = round_total;
+    }
+}
+
+// V[i][:] = e_i J_1 ... J_r, one warp per row; pairs of a round are disjoint
+template <class T>
+__global__ void __launch_bounds__(256) rot_apply_kernel(const int2* __restrict__ logpq, const T* __restrict__ logcs,
+                                                        const int* __restrict__ rounds, int n, T* __restrict__ V) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int i = blockIdx.x * 8 + warp;
+    T* row = reinterpret_cast<T*>(smem_raw) + (size_t)warp * n;
+    if (i >= n) return;
+    for (int j = lane; j < n; j += 32) row[j] = (j == i) ? T(1) : T(0);
+    __syncwarp();
+    const int h = n / 2;
+    const int R = *rounds;
+    for (int r = 0; r < R; ++r) {
+        for (int k = lane; k < h; k += 32) {
+            const int2 pq = logpq[(size_t)r * h + k];
+            const T c = logcs[((size_t)r * h + k) * 2], s = logcs[((size_t)r * h + k) * 2 + 1];
+            if (s == T(0)) continue;
+            const T vp = row[pq.x], vq = row[pq.y];
+            row[pq.x] = c * vp - s * vq;
+            row[pq.y] = s * vp + c * vq;
+        }
+        __syncwarp();
+    }
+    for (int j = lane; j < n; j += 32) V[(size_t)i * n + j] = row[j];
+}
+
 // lambda_i = v_i^T G v_i / (v_i^T v_i), G float64 (ld = ell), V (ld = n) of T.
 template <class T>
 __global__ void rayleigh_kernel(const double* __restrict__ G, const T* __restrict__ V, int ell, int n,
@@ -313,9 +430,34 @@ int sym_eig(nys_ctx* ctx, const double* G, int ell, bool use_f32, const double* 
         NYS_CK(ctx, cudaMemsetAsync(Gw, 0, sizeof(T) * n * n, s));
         copy_pad<T><<<64, 256, 0, s>>>(G, ell, Gw, n);
         NYS_LAUNCH_CK(ctx);
-        jacobi_kernel<T><<<1, 1024, 0, s>>>(Gw, V, n, ell, sizeof(T) == 8 ? 30 : 15, sizeof(T) == 8 ? 1e-14 : 2e-7,
-                                            sweeps_dev);
-        NYS_LAUNCH_CK(ctx);
+        const int max_sweeps = sizeof(T) == 8 ? 30 : 15;
+        const double tol = sizeof(T) == 8 ? 1e-14 : 2e-7;
+        const int h = n / 2;
+        const size_t smem = sizeof(T) * ((size_t)n * (n + 1) + 2 * (size_t)h) + sizeof(int) * (2 * (size_t)n + 2 * h + 4) + 64;
+        if (smem + 1024 <= 227 * 1024) {   // leave room for the kernel's static shared memory
+            // G in shared memory, rotations logged, V built by many CTAs
+            int st;
+            const size_t rounds = (size_t)max_sweeps * (n - 1);
+            char* lg = (char*)scratch(ctx, SLOT_EIG, rounds * h * (sizeof(int2) + 2 * sizeof(T)) + 64, &st);
+            if (st) return st;
+            int2* logpq = (int2*)lg;
+            T* logcs = (T*)(lg + rounds * h * sizeof(int2));
+            int* rounds_dev = sweeps_dev + 1;
+            static size_t attr = 48 * 1024;
+            if (smem > attr) {
+                NYS_CK(ctx, cudaFuncSetAttribute(jacobi_smem_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                 (int)smem));
+                attr = smem;
+            }
+            jacobi_smem_kernel<T><<<1, 1024, smem, s>>>(Gw, n, ell, max_sweeps, tol, logpq, logcs, rounds_dev,
+                                                        sweeps_dev);
+            NYS_LAUNCH_CK(ctx);
+            rot_apply_kernel<T><<<(n + 7) / 8, 256, 8 * n * sizeof(T), s>>>(logpq, logcs, rounds_dev, n, V);
+            NYS_LAUNCH_CK(ctx);
+        } else {
+            jacobi_kernel<T><<<1, 1024, 0, s>>>(Gw, V, n, ell, max_sweeps, tol, sweeps_dev);
+            NYS_LAUNCH_CK(ctx);
+        }
         rayleigh_kernel<T><<<ell, 128, 0, s>>>(G, V, ell, n, lam);
         NYS_LAUNCH_CK(ctx);
         sort_eig_kernel<T><<<(ell + 127) / 128, 128, 0, s>>>(lam, V, ell, n, info, Vout, S_hat, scale);

@@ -8,7 +8,13 @@
 //     x'   = prox^P_{alpha lambda g}(s)  (dual APG / semi-smooth Newton)
 //     t'   = (1 + sqrt(1 + 4 t^2))/2,  u = x' + ((t - 1)/t') (x' - x)
 // x^1 = u^1 = 0, t^0 = 1.  alpha defaults to 1/(1.02 lambda_max(P^{-1} Phi)),
-// lambda_max from 50 power-iteration steps started at a Philox Gaussian.
+// lambda_max from 50 power-iteration steps from a seeded Gaussian start.
+//
+// Launch structure: one iteration is a fixed sequence of kernels (the momentum
+// scalar t lives on the device, double-buffered by iteration parity, and the
+// two iterate buffers swap roles every iteration), so the solver captures the
+// even and the odd iteration once into CUDA graphs on its own stream and
+// replays them: one graph launch per iteration instead of ~60 kernel launches.
 #include "internal.cuh"
 
 #include <cmath>
@@ -32,14 +38,21 @@ struct nys_solver {
     int64_t N = 0, M = 0;
     int G = 0;
     void* mem = nullptr;
-    // buffers (op dtype)
-    void *y = nullptr, *aty = nullptr, *x = nullptr, *xn = nullptr, *u = nullptr, *s = nullptr, *g = nullptr;
+    // buffers (op dtype); X[parity] is the current iterate
+    void *y = nullptr, *aty = nullptr, *u = nullptr, *s = nullptr, *g = nullptr;
+    void* X[2] = {nullptr, nullptr};
     void *tM = nullptr, *tN = nullptr, *Q = nullptr;
     double* gamma = nullptr;
-    double* pw = nullptr;   // power-iteration scalars
+    double* pw = nullptr;     // [0] power-iteration norm, [2], [3]: t slots by parity
     double alpha = 0.0;
-    double t = 1.0;
+    int parity = 0;
     int k = 0;
+    // graph replay
+    cudaStream_t gs = nullptr;
+    cudaEvent_t ev_in = nullptr, ev_out = nullptr;
+    cudaGraphExec_t gexec[2] = {nullptr, nullptr};
+    int64_t glaunch[2] = {0, 0};
+    bool gvalid = false;
 };
 
 namespace nys {
@@ -69,12 +82,16 @@ __global__ void step_kernel(const T* __restrict__ u, const T* __restrict__ g, do
         s[i] = (T)((TC)u[i] - a * (TC)g[i]);
 }
 
-// u = xn + beta (xn - x)
+// t' = (1 + sqrt(1 + 4 t^2))/2 from t_in; u = xn + ((t - 1)/t') (xn - x);
+// t' written to t_out by one thread (t_in and t_out are different slots)
 template <class T>
-__global__ void momentum_kernel(const T* __restrict__ xn, const T* __restrict__ x, double beta, int64_t n,
-                                T* __restrict__ u) {
+__global__ void momentum_kernel(const T* __restrict__ xn, const T* __restrict__ x, const double* __restrict__ t_in,
+                                double* __restrict__ t_out, int64_t n, T* __restrict__ u) {
     using TC = typename Comp<T>::type;
-    const TC b = (TC)beta;
+    const double t = *t_in;
+    const double tn = 0.5 * (1.0 + sqrt(1.0 + 4.0 * t * t));
+    const TC b = (TC)((t - 1.0) / tn);
+    if (blockIdx.x == 0 && threadIdx.x == 0) *t_out = tn;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
         const TC a = (TC)xn[i];
         u[i] = (T)(a + b * (a - (TC)x[i]));
@@ -97,21 +114,74 @@ __global__ void norm_scale_kernel(T* __restrict__ w, int64_t n, double* __restri
     for (int64_t i = threadIdx.x; i < n; i += blockDim.x) w[i] = (T)((double)w[i] * inv);
 }
 
+// Gaussian start vector of the power iteration: splitmix64 (Steele, Lea and
+// Flood, OOPSLA 2014) hashes of (seed, i) turned into N(0,1) by Box-Muller
+__device__ __forceinline__ uint64_t splitmix64(uint64_t z) {
+    z += 0x9E3779B97F4A7C15ull;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
 template <class T>
 __global__ void gauss_init_kernel(T* __restrict__ w, int64_t n, uint64_t seed) {
-    // small Philox-free start: a deterministic hash-based +-1 pattern is not
-    // Gaussian; use a simple LCG-driven Box-Muller for the power start only
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-        uint64_t z = seed * 0x9E3779B97F4A7C15ull + (uint64_t)i * 0xBF58476D1CE4E5B9ull;
-        z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
-        z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
-        z ^= z >> 31;
-        const double u0 = ((double)(z >> 11) + 0.5) * (1.0 / 9007199254740992.0);
-        uint64_t z2 = z * 0x9E3779B97F4A7C15ull + 0x632BE59BD9B4E019ull;
-        z2 = (z2 ^ (z2 >> 29)) * 0xBF58476D1CE4E5B9ull;
-        const double u1 = ((double)(z2 >> 11) + 0.5) * (1.0 / 9007199254740992.0);
+        const uint64_t a = splitmix64(seed ^ splitmix64(2 * (uint64_t)i));
+        const uint64_t b = splitmix64(seed ^ splitmix64(2 * (uint64_t)i + 1));
+        const double u0 = ((double)(a >> 11) + 0.5) * (1.0 / 9007199254740992.0);
+        const double u1 = ((double)(b >> 11) + 0.5) * (1.0 / 9007199254740992.0);
         w[i] = (T)(sqrt(-2.0 * log(u0)) * cospi(2.0 * u1));
     }
+}
+
+__global__ void set_t_kernel(double* t) {
+    t[0] = 1.0;
+    t[1] = 1.0;
+}
+
+// ------------------------------------------------------------ objective --
+// part[2 b]   = sum of the data term over the block's entries of r = A x - y
+// part[2 b+1] = sum of the regulariser over the block's pixels
+template <class T, int REG>
+__global__ void objective_kernel(const T* __restrict__ r, const T* __restrict__ y, int64_t M, int fit, double delta,
+                                 const T* __restrict__ x, int n1, int n2, double* __restrict__ part) {
+    __shared__ double sh[32];
+    double f = 0.0, g = 0.0;
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < M; t += (int64_t)gridDim.x * blockDim.x) {
+        const double v = (double)r[t] - (double)y[t];
+        const double a = fabs(v);
+        f += (fit == NYS_FIT_HUBER && a > delta) ? delta * a - 0.5 * delta * delta : 0.5 * v * v;
+    }
+    const int64_t N = (int64_t)n1 * n2;
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < N; t += (int64_t)gridDim.x * blockDim.x) {
+        const int i = (int)(t / n2), j = (int)(t - (int64_t)i * n2);
+        auto X = [&](int a, int b) { return (double)x[(size_t)pmod(a, n1) * n2 + pmod(b, n2)]; };
+        if (REG == NYS_REG_TV) {
+            g += fabs(X(i, j) - X(i - 1, j)) + fabs(X(i, j) - X(i, j - 1));
+        } else if (REG == NYS_REG_HS) {
+            const double v11 = X(i - 1, j) - 2.0 * X(i, j) + X(i + 1, j);
+            const double v22 = X(i, j - 1) - 2.0 * X(i, j) + X(i, j + 1);
+            const double v12 = 0.25 * (X(i + 1, j + 1) - X(i + 1, j - 1) - X(i - 1, j + 1) + X(i - 1, j - 1));
+            const double m = 0.5 * (v11 + v22), h = 0.5 * (v11 - v22);
+            const double rr = sqrt(h * h + v12 * v12);
+            g += fabs(m + rr) + fabs(m - rr);
+        } else {
+            g += fabs((double)x[t]);
+        }
+    }
+    f = block_sum(f, sh);
+    g = block_sum(g, sh);
+    if (threadIdx.x == 0) part[2 * blockIdx.x] = f, part[2 * blockIdx.x + 1] = g;
+}
+
+__global__ void objective_sum_kernel(const double* __restrict__ part, int nb, double lambda,
+                                     double* __restrict__ out) {
+    __shared__ double sh[32];
+    double f = 0.0, g = 0.0;
+    for (int t = threadIdx.x; t < nb; t += blockDim.x) f += part[2 * t], g += part[2 * t + 1];
+    f = block_sum(f, sh);
+    g = block_sum(g, sh);
+    if (threadIdx.x == 0) out[0] = f + lambda * g, out[1] = f, out[2] = g;
 }
 
 inline int grid_for(nys_ctx* ctx, int64_t n) { return (int)std::min<int64_t>((n + 255) / 256, ctx->sm_count * 8); }
@@ -162,35 +232,90 @@ int gradient(nys_solver* S) {
     return NYS_OK;
 }
 
+// one iteration of Algorithm 3 with the given parity, issued on ctx->stream
+template <class T>
+int iterate_one(nys_solver* S, int par) {
+    nys_ctx* ctx = S->ctx;
+    const int gN = grid_for(ctx, S->N);
+    void* x = S->X[par];
+    void* xn = S->X[par ^ 1];
+    int st;
+    if ((st = gradient<T>(S))) return st;
+    if (S->pc && (st = precond_run(ctx, S->pc, 1, S->dt, S->g, S->g, 1))) return st;
+    step_kernel<T><<<gN, 256, 0, ctx->stream>>>((const T*)S->u, (const T*)S->g, S->alpha, S->N, (T*)S->s);
+    NYS_LAUNCH_CK(ctx);
+    const double tau = S->alpha * S->d.lambda;
+    if (S->d.reg == NYS_REG_WAVELET) {
+        if (S->pc) st = ssn_run<T>(ctx, S->pc, tau, S->N, (const T*)S->s, (T*)xn, S->gamma, 50, 10, false, nullptr);
+        else st = soft_run<T>(ctx, tau, S->N, (const T*)S->s, (T*)xn);
+    } else {
+        st = prox_dual_run(ctx, S->pc, S->d.reg, tau, S->d.n_inner, S->dt, S->op->n1, S->op->n2, S->s, xn, S->Q);
+    }
+    if (st) return st;
+    momentum_kernel<T><<<gN, 256, 0, ctx->stream>>>((const T*)xn, (const T*)x, S->pw + 2 + par, S->pw + 2 + (par ^ 1),
+                                                    S->N, (T*)S->u);
+    NYS_LAUNCH_CK(ctx);
+    return NYS_OK;
+}
+
+template <class T>
+int capture(nys_solver* S) {
+    nys_ctx* ctx = S->ctx;
+    cudaStream_t saved = ctx->stream;
+    // the captured kernels carry the context's L2 access-policy window
+    cudaStreamAttrValue v = {};
+    if (ctx->l2_window_set) v = ctx->l2_window;
+    NYS_CK(ctx, cudaStreamSetAttribute(S->gs, cudaStreamAttributeAccessPolicyWindow, &v));
+    for (int par = 0; par < 2; ++par) {
+        if (S->gexec[par]) {
+            cudaGraphExecDestroy(S->gexec[par]);
+            S->gexec[par] = nullptr;
+        }
+        const int64_t l0 = ctx->launches;
+        ctx->stream = S->gs;
+        NYS_CK(ctx, cudaStreamBeginCapture(S->gs, cudaStreamCaptureModeRelaxed));
+        int st = iterate_one<T>(S, par);
+        cudaGraph_t graph = nullptr;
+        const cudaError_t e = cudaStreamEndCapture(S->gs, &graph);
+        ctx->stream = saved;
+        if (st) {
+            if (graph) cudaGraphDestroy(graph);
+            return st;
+        }
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaStreamEndCapture");
+        const cudaError_t ei = cudaGraphInstantiate(&S->gexec[par], graph, 0);
+        cudaGraphDestroy(graph);
+        if (ei != cudaSuccess) return cuda_fail(ctx, ei, "cudaGraphInstantiate");
+        S->glaunch[par] = ctx->launches - l0;
+        ctx->launches = l0;
+    }
+    S->gvalid = true;
+    return NYS_OK;
+}
+
 template <class T>
 int iterate(nys_solver* S, int n_steps) {
     nys_ctx* ctx = S->ctx;
-    const int gN = grid_for(ctx, S->N);
     int st;
-    for (int it = 0; it < n_steps; ++it) {
-        if ((st = gradient<T>(S))) return st;
-        if (S->pc && (st = precond_run(ctx, S->pc, 1, S->dt, S->g, S->g, 1))) return st;
-        step_kernel<T><<<gN, 256, 0, ctx->stream>>>((const T*)S->u, (const T*)S->g, S->alpha, S->N, (T*)S->s);
-        NYS_LAUNCH_CK(ctx);
-        const double tau = S->alpha * S->d.lambda;
-        if (S->d.reg == NYS_REG_WAVELET) {
-            if (S->pc)
-                st = ssn_run<T>(ctx, S->pc, tau, S->N, (const T*)S->s, (T*)S->xn, S->gamma, 50, 10, false, nullptr);
-            else
-                st = soft_run<T>(ctx, tau, S->N, (const T*)S->s, (T*)S->xn);
-        } else {
-            st = prox_dual_run(ctx, S->pc, S->d.reg, tau, S->d.n_inner, S->dt, S->op->n1, S->op->n2, S->s, S->xn,
-                               S->Q);
+    if (S->d.no_graph) {
+        for (int it = 0; it < n_steps; ++it) {
+            if ((st = iterate_one<T>(S, S->parity))) return st;
+            S->parity ^= 1;
+            S->k += 1;
         }
-        if (st) return st;
-        const double tn = 0.5 * (1.0 + std::sqrt(1.0 + 4.0 * S->t * S->t));
-        const double beta = (S->t - 1.0) / tn;
-        S->t = tn;
-        momentum_kernel<T><<<gN, 256, 0, ctx->stream>>>((const T*)S->xn, (const T*)S->x, beta, S->N, (T*)S->u);
-        NYS_LAUNCH_CK(ctx);
-        std::swap(S->x, S->xn);
+        return NYS_OK;
+    }
+    if (!S->gvalid && (st = capture<T>(S))) return st;
+    NYS_CK(ctx, cudaEventRecord(S->ev_in, ctx->stream));
+    NYS_CK(ctx, cudaStreamWaitEvent(S->gs, S->ev_in, 0));
+    for (int it = 0; it < n_steps; ++it) {
+        NYS_CK(ctx, cudaGraphLaunch(S->gexec[S->parity], S->gs));
+        ctx->launches += S->glaunch[S->parity];
+        S->parity ^= 1;
         S->k += 1;
     }
+    NYS_CK(ctx, cudaEventRecord(S->ev_out, S->gs));
+    NYS_CK(ctx, cudaStreamWaitEvent(ctx->stream, S->ev_out, 0));
     return NYS_OK;
 }
 
@@ -198,7 +323,7 @@ template <class T>
 int estimate_alpha(nys_solver* S) {
     nys_ctx* ctx = S->ctx;
     cudaStream_t s = ctx->stream;
-    T* z = (T*)S->xn;   // scratch vectors before the first iteration
+    T* z = (T*)S->X[1];   // scratch vectors before the first iteration
     T* w = (T*)S->u;
     gauss_init_kernel<T><<<grid_for(ctx, S->N), 256, 0, s>>>(z, S->N, S->d.power_seed);
     NYS_LAUNCH_CK(ctx);
@@ -217,7 +342,9 @@ int estimate_alpha(nys_solver* S) {
     NYS_CK(ctx, cudaMemcpyAsync(&lam, S->pw, sizeof(double), cudaMemcpyDeviceToHost, s));
     NYS_CK(ctx, cudaStreamSynchronize(s));
     if (!(lam > 0.0) || !std::isfinite(lam)) return fail(ctx, NYS_ENONFINITE, "power iteration gave %g", lam);
-    S->alpha = 1.0 / (1.02 * lam);
+    const double a = 1.0 / (1.02 * lam);
+    if (a != S->alpha) S->gvalid = false;   // alpha is baked into the captured graphs
+    S->alpha = a;
     return NYS_OK;
 }
 
@@ -225,13 +352,30 @@ template <class T>
 int reset_state(nys_solver* S) {
     cudaStream_t s = S->ctx->stream;
     const size_t nb = S->N * sizeof(T);
-    NYS_CK(S->ctx, cudaMemsetAsync(S->x, 0, nb, s));
-    NYS_CK(S->ctx, cudaMemsetAsync(S->xn, 0, nb, s));
+    NYS_CK(S->ctx, cudaMemsetAsync(S->X[0], 0, nb, s));
+    NYS_CK(S->ctx, cudaMemsetAsync(S->X[1], 0, nb, s));
     NYS_CK(S->ctx, cudaMemsetAsync(S->u, 0, nb, s));
     if (S->G) NYS_CK(S->ctx, cudaMemsetAsync(S->Q, 0, (size_t)S->G * nb, s));
     if (S->gamma && S->pc) NYS_CK(S->ctx, cudaMemsetAsync(S->gamma, 0, S->pc->ell * sizeof(double), s));
-    S->t = 1.0;
+    set_t_kernel<<<1, 1, 0, s>>>(S->pw + 2);
+    NYS_LAUNCH_CK(S->ctx);
+    S->parity = 0;
     S->k = 0;
+    return NYS_OK;
+}
+
+template <class T>
+int load_data(nys_solver* S, const void* y) {
+    nys_ctx* ctx = S->ctx;
+    const size_t es = sizeof(T);
+    NYS_CK(ctx, cudaMemcpyAsync(S->y, y, S->M * es, cudaMemcpyDeviceToDevice, ctx->stream));
+    int st;
+    // A^T y (and W A^T y for the wavelet model)
+    if ((st = op_run(S->op, 1, S->y, S->aty, 1, S->dt, S->dt))) return st;
+    if (S->d.reg == NYS_REG_WAVELET) {
+        if ((st = haar_run(S->op, S->aty, S->tN, 1, 0, S->dt, S->dt))) return st;
+        NYS_CK(ctx, cudaMemcpyAsync(S->aty, S->tN, S->N * es, cudaMemcpyDeviceToDevice, ctx->stream));
+    }
     return NYS_OK;
 }
 
@@ -253,8 +397,8 @@ int create_typed(nys_solver* S, const void* y) {
     S->y = take(M * es);
     S->tM = take(M * es);
     S->aty = take(N * es);
-    S->x = take(N * es);
-    S->xn = take(N * es);
+    S->X[0] = take(N * es);
+    S->X[1] = take(N * es);
     S->u = take(N * es);
     S->s = take(N * es);
     S->g = take(N * es);
@@ -262,15 +406,11 @@ int create_typed(nys_solver* S, const void* y) {
     S->Q = S->G ? take((size_t)S->G * N * es) : nullptr;
     S->gamma = (double*)take((ell + 1) * 8);
     S->pw = (double*)take(256);
-    cudaStream_t s = ctx->stream;
-    NYS_CK(ctx, cudaMemcpyAsync(S->y, y, M * es, cudaMemcpyDeviceToDevice, s));
+    NYS_CK(ctx, cudaStreamCreateWithFlags(&S->gs, cudaStreamNonBlocking));
+    NYS_CK(ctx, cudaEventCreateWithFlags(&S->ev_in, cudaEventDisableTiming));
+    NYS_CK(ctx, cudaEventCreateWithFlags(&S->ev_out, cudaEventDisableTiming));
     int st;
-    // A^T y (and W A^T y for the wavelet model)
-    if ((st = op_run(S->op, 1, S->y, S->aty, 1, S->dt, S->dt))) return st;
-    if (S->d.reg == NYS_REG_WAVELET) {
-        if ((st = haar_run(S->op, S->aty, S->tN, 1, 0, S->dt, S->dt))) return st;
-        NYS_CK(ctx, cudaMemcpyAsync(S->aty, S->tN, N * es, cudaMemcpyDeviceToDevice, s));
-    }
+    if ((st = load_data<T>(S, y))) return st;
     if ((st = reset_state<T>(S))) return st;
     if (S->d.alpha > 0.0) S->alpha = S->d.alpha;
     else if ((st = estimate_alpha<T>(S))) return st;
@@ -280,11 +420,12 @@ int create_typed(nys_solver* S, const void* y) {
         if (!scratch(ctx, SLOT_PROX, ((size_t)2 * S->G * N + 2 * N) * es, &st)) return st;
     }
     if (S->pc) {
+        // the largest of the two P^{-1} layouts (chunks of 1024 or 2048 pixels)
         const size_t nbp = (size_t)((N + 1023) / 1024);
         if (!scratch(ctx, SLOT_PRECOND, (nbp * ell + ell) * es, &st)) return st;
         if (S->d.reg == NYS_REG_WAVELET) {
-            // first ssn_run call sizes SLOT_SSN; run one prox now
-            if ((st = ssn_run<T>(ctx, S->pc, 0.0, N, (const T*)S->x, (T*)S->xn, nullptr, 1, 1, false, nullptr)))
+            // the first ssn_run call sizes SLOT_SSN; run one prox now
+            if ((st = ssn_run<T>(ctx, S->pc, 0.0, N, (const T*)S->X[0], (T*)S->X[1], nullptr, 1, 1, false, nullptr)))
                 return st;
             if ((st = reset_state<T>(S))) return st;
         }
@@ -335,6 +476,12 @@ int nys_solver_create(nys_ctx* ctx, nys_op* op, const nys_solver_desc* d, const 
 int nys_solver_destroy(nys_solver* S) {
     if (!S) return NYS_OK;
     cudaStreamSynchronize(S->ctx->stream);
+    if (S->gs) cudaStreamSynchronize(S->gs);
+    for (auto& g : S->gexec)
+        if (g) cudaGraphExecDestroy(g);
+    if (S->ev_in) cudaEventDestroy(S->ev_in);
+    if (S->ev_out) cudaEventDestroy(S->ev_out);
+    if (S->gs) cudaStreamDestroy(S->gs);
     if (S->mem) cudaFree(S->mem);
     delete S;
     return NYS_OK;
@@ -343,6 +490,7 @@ int nys_solver_destroy(nys_solver* S) {
 int pgd_step(nys_solver* S, int n_steps) {
     if (!S) return fail(nullptr, NYS_EINVAL, "pgd_step: null solver");
     if (n_steps < 0) return fail(S->ctx, NYS_EINVAL, "pgd_step: negative step count");
+    if (n_steps == 0) return NYS_OK;
     return S->dt == NYS_F64 ? iterate<double>(S, n_steps) : iterate<float>(S, n_steps);
 }
 
@@ -353,15 +501,8 @@ int nys_solver_reset(nys_solver* S) {
 
 int nys_solver_set_data(nys_solver* S, const void* y) {
     if (!S || !y) return fail(S ? S->ctx : nullptr, NYS_EINVAL, "nys_solver_set_data: null argument");
-    nys_ctx* ctx = S->ctx;
-    const size_t es = dtype_size(S->dt);
-    NYS_CK(ctx, cudaMemcpyAsync(S->y, y, S->M * es, cudaMemcpyDeviceToDevice, ctx->stream));
-    int st;
-    if ((st = op_run(S->op, 1, S->y, S->aty, 1, S->dt, S->dt))) return st;
-    if (S->d.reg == NYS_REG_WAVELET) {
-        if ((st = haar_run(S->op, S->aty, S->tN, 1, 0, S->dt, S->dt))) return st;
-        NYS_CK(ctx, cudaMemcpyAsync(S->aty, S->tN, S->N * es, cudaMemcpyDeviceToDevice, ctx->stream));
-    }
+    int st = S->dt == NYS_F64 ? load_data<double>(S, y) : load_data<float>(S, y);
+    if (st) return st;
     return S->dt == NYS_F64 ? reset_state<double>(S) : reset_state<float>(S);
 }
 
@@ -378,8 +519,54 @@ int nys_solver_restart(nys_solver* S, int reestimate_alpha) {
 
 int nys_solver_get_x(nys_solver* S, void* x_out) {
     if (!S || !x_out) return fail(S ? S->ctx : nullptr, NYS_EINVAL, "nys_solver_get_x: null argument");
-    if (S->d.reg == NYS_REG_WAVELET) return haar_run(S->op, S->x, x_out, 1, 1, S->dt, S->dt);
-    NYS_CK(S->ctx, cudaMemcpyAsync(x_out, S->x, S->N * dtype_size(S->dt), cudaMemcpyDeviceToDevice, S->ctx->stream));
+    void* x = S->X[S->parity];
+    if (S->d.reg == NYS_REG_WAVELET) return haar_run(S->op, x, x_out, 1, 1, S->dt, S->dt);
+    NYS_CK(S->ctx, cudaMemcpyAsync(x_out, x, S->N * dtype_size(S->dt), cudaMemcpyDeviceToDevice, S->ctx->stream));
+    return NYS_OK;
+}
+
+int nys_solver_objective(nys_solver* S, double* F) {
+    if (!S || !F) return fail(S ? S->ctx : nullptr, NYS_EINVAL, "nys_solver_objective: null argument");
+    nys_ctx* ctx = S->ctx;
+    cudaStream_t s = ctx->stream;
+    const void* x = S->X[S->parity];
+    int st;
+    // r = A x (image domain: W^T xbar for the wavelet model), into tM
+    const void* img = x;
+    if (S->d.reg == NYS_REG_WAVELET) {
+        if ((st = haar_run(S->op, x, S->tN, 1, 1, S->dt, S->dt))) return st;
+        img = S->tN;
+    }
+    if ((st = op_run(S->op, 0, img, S->tM, 1, S->dt, S->dt))) return st;
+    const int nb = std::max(1, std::min<int>(ctx->sm_count * 2, (int)((std::max(S->M, S->N) + 255) / 256)));
+    double* buf = (double*)scratch(ctx, SLOT_MISC, (size_t)(2 * nb + 4) * sizeof(double), &st);
+    if (st) return st;
+    double* out = buf;
+    double* part = buf + 4;
+    auto launch = [&](auto* tag) -> int {
+        using T = std::remove_pointer_t<decltype(tag)>;
+        const T* r = (const T*)S->tM;
+        const T* yy = (const T*)S->y;
+        const T* xx = (const T*)x;
+        if (S->d.reg == NYS_REG_TV)
+            objective_kernel<T, NYS_REG_TV><<<nb, 256, 0, s>>>(r, yy, S->M, S->d.fit, S->d.huber_delta, xx,
+                                                               S->op->n1, S->op->n2, part);
+        else if (S->d.reg == NYS_REG_HS)
+            objective_kernel<T, NYS_REG_HS><<<nb, 256, 0, s>>>(r, yy, S->M, S->d.fit, S->d.huber_delta, xx,
+                                                               S->op->n1, S->op->n2, part);
+        else
+            objective_kernel<T, NYS_REG_WAVELET><<<nb, 256, 0, s>>>(r, yy, S->M, S->d.fit, S->d.huber_delta, xx,
+                                                                    S->op->n1, S->op->n2, part);
+        NYS_LAUNCH_CK(ctx);
+        return NYS_OK;
+    };
+    if ((st = S->dt == NYS_F64 ? launch((double*)nullptr) : launch((float*)nullptr))) return st;
+    objective_sum_kernel<<<1, 256, 0, s>>>(part, nb, S->d.lambda, out);
+    NYS_LAUNCH_CK(ctx);
+    double h[3];
+    NYS_CK(ctx, cudaMemcpyAsync(h, out, sizeof(h), cudaMemcpyDeviceToHost, s));
+    NYS_CK(ctx, cudaStreamSynchronize(s));
+    F[0] = h[0];
     return NYS_OK;
 }
 

@@ -1,0 +1,106 @@
+"""Per-call timings of the library's hot entry points, and a small target for ncu.
+
+  python -m paper_2411_08178_gb300.profile_kernels [--case all|precond|normal|sketch|prox|iter]
+        [--n 512] [--ell 200] [--reps 20] [--l2]
+
+Each case builds the 512 x 512 deblurring operator (25 x 25 Gaussian, sigma 4)
+and times one library call with CUDA events on the calling stream (warm-up
+first, mean over --reps), then prints one JSON line per case with the time
+and the algorithmic bytes or flops of the call.  With few repetitions it is
+also the workload for `ncu -k regex:<kernel> -c <n>` captures.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import sys
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--case", default="all")
+    ap.add_argument("--n", type=int, default=512)
+    ap.add_argument("--ell", type=int, default=200)
+    ap.add_argument("--reps", type=int, default=20)
+    ap.add_argument("--u-dtype", choices=["bf16", "f32"], default="bf16")
+    ap.add_argument("--l2", action="store_true", help="keep U resident in L2 (nys_l2_persist)")
+    args = ap.parse_args()
+    import torch
+
+    import __graft_entry__ as g
+    g.build()
+    from paper_2411_08178_gb300 import api
+    import workloads as WL
+
+    dev = torch.device("cuda", 0)
+    stream = torch.cuda.Stream(dev)
+    torch.cuda.set_stream(stream)
+    ctx = api.Context(0, stream)
+    n, ell = args.n, args.ell
+    N = n * n
+    h = WL.gaussian_kernel(25, 4.0)
+    op = api.Operator(ctx, "blur", n, n, dtype=torch.float32, kernel=h)
+    sd = torch.bfloat16 if args.u_dtype == "bf16" else torch.float32
+    ub = 2 if sd == torch.bfloat16 else 4
+
+    def timed(fn, reps=args.reps):
+        for _ in range(3):
+            fn()
+        torch.cuda.synchronize()
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(reps):
+            fn()
+        b.record(stream)
+        torch.cuda.synchronize()
+        return a.elapsed_time(b) / reps
+
+    out = []
+    Om, Y = api.nys_sketch(ctx, op, ell, 13, store_dtype=sd)
+    pc = api.nys_factor(ctx, Om, Y, 2.0 ** -23, u_dtype=sd)
+    if args.l2:
+        ctx.l2_persist(pc.U, 1.0)
+    cases = args.case.split(",") if args.case != "all" else ["precond", "normal", "sketch", "prox", "iter"]
+    if "precond" in cases:
+        z = torch.randn(N, device=dev)
+        o = torch.empty_like(z)
+        ms = timed(lambda: api.precond_apply(ctx, pc, z, True, o))
+        nbytes = 2 * N * ell * ub + 3 * N * 4
+        out.append(dict(case="precond_apply(inverse)", ms=ms, bytes=nbytes, GBs=nbytes / ms / 1e6))
+    if "normal" in cases:
+        x1 = torch.randn(1, n, n, device=dev)
+        y1 = torch.empty_like(x1)
+        ms = timed(lambda: api.op_normal(op, x1, y1))
+        out.append(dict(case="op_normal x1 (A^T A, 25x25 separable)", ms=ms, bytes=2 * N * 4,
+                        flops=2 * 2 * 49 * N))
+    if "sketch" in cases:
+        ms = timed(lambda: api.nys_sketch(ctx, op, ell, 13, store_dtype=sd, out=(Om, Y)), reps=max(2, args.reps // 4))
+        out.append(dict(case=f"nys_sketch ell={ell}", ms=ms, bytes=2 * N * ell * ub, flops=2 * 2 * 49 * N * ell))
+        ms = timed(lambda: api.nys_factor(ctx, Om, Y, 2.0 ** -23, pc=pc), reps=max(2, args.reps // 4))
+        out.append(dict(case=f"nys_factor ell={ell}", ms=ms, bytes=4 * N * ell * ub, flops=4 * 2 * N * ell * ell))
+    if "prox" in cases:
+        s = torch.rand(n, n, device=dev)
+        Q = torch.zeros(2, n, n, device=dev)
+        ms = timed(lambda: api.prox_tv(ctx, None, 5e-4, 20, s, Q=Q), reps=max(2, args.reps // 2))
+        out.append(dict(case="prox_tv P=I n_inner=20", ms=ms))
+        ms = timed(lambda: api.prox_tv(ctx, pc, 5e-4, 20, s, Q=Q), reps=max(2, args.reps // 2))
+        out.append(dict(case="prox_tv P=RNP n_inner=20", ms=ms))
+    if "iter" in cases:
+        y = torch.rand(n, n, device=dev)
+        for name, p in (("plain", None), ("precond", pc)):
+            sol = api.Solver(ctx, op, y, "tv", 5e-4, pc=p, n_inner=20)
+            ms = timed(lambda: sol.step(1), reps=args.reps)
+            out.append(dict(case=f"pgd_step TV {name}", ms=ms))
+            sol.close()
+    for o in out:
+        print(json.dumps(o))
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,62 @@
+"""Tall-skinny Gram products A^T B (Algorithm 1's Omega^T Omega, Omega^T Y, Y^T Y,
+and U^T U) through the C ABI: the tcgen05 tensor-core path and the CUDA-core
+path against a float64 matmul of the same bf16 values."""
+import numpy as np
+import pytest
+
+from tests.gpu_util import require_gpu
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def env():
+    torch, api = require_gpu()
+    return torch, api, api.Context(0)
+
+
+def _operands(torch, p, q, N, seed, same=False):
+    g = torch.Generator(device="cpu").manual_seed(seed)
+    A = torch.randn(p, N, generator=g).to(torch.bfloat16)
+    B = A.clone() if same else torch.randn(q, N, generator=g).to(torch.bfloat16)
+    ref = A.double().numpy() @ B.double().numpy().T
+    return A.cuda(), B.cuda(), ref
+
+
+# (p, q, N): the ell = 200 sketch at 512 x 512, ragged K (N not a multiple of
+# the 64-pixel K block), a second M tile that is mostly padding, narrow and
+# full-width outputs, a single column
+CASES = [(200, 200, 262144), (130, 48, 5000), (64, 17, 4096), (128, 256, 8192), (1, 1, 1024), (257, 96, 2048)]
+
+
+@pytest.mark.parametrize("p,q,N", CASES)
+def test_gram_tensor_cores_match_float64(env, p, q, N):
+    torch, api, ctx = env
+    A, B, ref = _operands(torch, p, q, N, seed=p * 7 + q)
+    C = api.nys_gram(ctx, A, B, path=2).cpu().numpy()
+    err = np.linalg.norm(C - ref) / np.linalg.norm(ref)
+    assert err < 1e-5, err
+
+
+@pytest.mark.parametrize("p,q,N", CASES[:3])
+def test_gram_paths_agree(env, p, q, N):
+    torch, api, ctx = env
+    A, B, ref = _operands(torch, p, q, N, seed=3)
+    Ct = api.nys_gram(ctx, A, B, path=2).cpu().numpy()
+    Cc = api.nys_gram(ctx, A, B, path=1).cpu().numpy()
+    assert np.linalg.norm(Ct - Cc) <= 1e-5 * np.linalg.norm(ref)
+
+
+def test_gram_symmetric_and_fallback(env):
+    torch, api, ctx = env
+    A, _, ref = _operands(torch, 40, 40, 4096, seed=9, same=True)
+    C = api.nys_gram(ctx, A, A, path=0).cpu().numpy()
+    assert np.allclose(C, C.T, rtol=0, atol=1e-6 * np.abs(C).max())
+    # q > 256 or N not a multiple of 8: the tensor-core path declines
+    from paper_2411_08178_gb300._abi import NYS_EINVAL, NysError
+    A2, B2, ref2 = _operands(torch, 8, 300, 1024, seed=4)
+    with pytest.raises(NysError) as e:
+        api.nys_gram(ctx, A2, B2, path=2)
+    assert e.value.code == NYS_EINVAL
+    C2 = api.nys_gram(ctx, A2, B2, path=0).cpu().numpy()
+    assert np.linalg.norm(C2 - ref2) / np.linalg.norm(ref2) < 1e-5

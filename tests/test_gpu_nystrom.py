@@ -97,6 +97,31 @@ def test_factor_f32_and_bf16_stated_accuracy(env):
     _check_factor(pcb.U.double().cpu().numpy(), pcb.S_hat.cpu().numpy(), ref, 3e-2, 3e-2)
 
 
+@pytest.mark.parametrize("sd,tol", [("f32", 2e-4), ("bf16", 2e-2)])
+def test_factor_full_size_properties(env, sd, tol):
+    # the 512 x 512, ell = 200, 25 x 25 sigma 4 sketch in the bench's launch
+    # configuration.  Properties that hold at any size: B B^T Omega = Y_v, i.e.
+    # U (S_hat + v) U^T Omega = Y + v Omega on the sketched columns; U^T U = I;
+    # 0 <= s_i <= lambda_max(A^T A) = 1; descending order.
+    torch, api, ctx = env
+    n, ell = 512, 200
+    op = api.Operator(ctx, "blur", n, n, dtype=torch.float32, kernel=gaussian_kernel(25, 4.0))
+    tsd = torch.bfloat16 if sd == "bf16" else torch.float32
+    Om, Y = api.nys_sketch(ctx, op, ell, seed=13, store_dtype=tsd)
+    pc = api.nys_factor(ctx, Om, Y, EPS32, u_dtype=tsd)
+    U = pc.U.double()
+    S = pc.S_hat
+    assert torch.all(S[:-1] >= S[1:]) and S[-1] >= 0 and S[0] <= 1.0 + 1e-3
+    G = U @ U.T
+    assert torch.max(torch.abs(G - torch.eye(ell, dtype=torch.float64, device=G.device))).item() < 50 * tol
+    cols = [0, 7, 99, 199]
+    Oc = Om.reshape(ell, -1)[cols].double()
+    Yc = Y.reshape(ell, -1)[cols].double()
+    lhs = ((Oc @ U.T) * (S + pc.v)) @ U
+    rhs = Yc + pc.v * Oc
+    assert rel(lhs.cpu(), rhs.cpu()) < tol
+
+
 def test_exact_recovery_low_rank_on_gpu(env):
     # blur + 4x decimation of a 16 x 16 image has rank <= 16 < ell = 20
     torch, api, ctx = env

@@ -87,6 +87,47 @@ def test_step_size_estimate_close_to_oracle(env):
     assert abs(sol.alpha - a_ref) <= 0.02 * a_ref
 
 
+@pytest.mark.parametrize("reg,fit,dt", [("tv", "l2", "f64"), ("hs", "huber", "f64"), ("wavelet", "l2", "f64"),
+                                        ("tv", "l2", "f32")])
+def test_objective_matches_oracle(env, reg, fit, dt):
+    torch, api, ctx = env
+    n = 48
+    h, opo, prob, y, ref = _setup("blur", n, 0, 6, reg, 3e-3, fit=fit, delta=0.02, levels=2)
+    tdt = torch.float64 if dt == "f64" else torch.float32
+    op = api.Operator(ctx, "blur", n, n, dtype=tdt, kernel=h, haar_levels=2 if reg == "wavelet" else 0)
+    alpha = 1.0 / oracle.wapg.power_lipschitz(prob)
+    sol = api.Solver(ctx, op, torch.from_numpy(y).to(tdt).cuda(), reg, 3e-3, fit=fit, huber_delta=0.02,
+                     alpha=alpha, n_inner=10)
+    sol.step(7)
+    xv = oracle.wapg.wapg(prob, alpha, 7, n_inner=10)["x"]
+    F_ref = prob.objective(xv)
+    assert abs(sol.objective() - F_ref) <= (1e-10 if dt == "f64" else 1e-5) * abs(F_ref)
+
+
+@pytest.mark.parametrize("reg,dt", [("tv", "f32"), ("hs", "f64"), ("wavelet", "f64")])
+def test_graph_replay_matches_direct_launches(env, reg, dt):
+    # the captured even/odd iteration graphs give the same iterates as
+    # launching every kernel one by one, across odd step counts and restarts
+    torch, api, ctx = env
+    n = 64
+    h, opo, prob, y, ref = _setup("blur", n, 16, 2, reg, 2e-3, levels=3)
+    tdt = torch.float64 if dt == "f64" else torch.float32
+    op = api.Operator(ctx, "blur", n, n, dtype=tdt, kernel=h, haar_levels=3 if reg == "wavelet" else 0)
+    pc = api.Precond(ctx, n * n, 16, tdt).import_factor(ref["U"], ref["S_hat"], 0.0, True)
+    yt = torch.from_numpy(y).to(tdt).cuda()
+    a = api.Solver(ctx, op, yt, reg, 2e-3, pc=pc, n_inner=8, use_graph=True)
+    b = api.Solver(ctx, op, yt, reg, 2e-3, pc=pc, n_inner=8, use_graph=False)
+    for steps in (3, 4, 1):
+        a.step(steps)
+        b.step(steps)
+    assert rel(a.x().cpu(), b.x().cpu()) == 0.0
+    a.restart(True)
+    b.restart(True)
+    a.step(5)
+    b.step(5)
+    assert rel(a.x().cpu(), b.x().cpu()) == 0.0
+
+
 def test_end_to_end_gpu_sketch_reaches_same_minimiser(env):
     # sketch + factor on the device; preconditioned and plain runs approach the
     # same minimiser (Sec. III-B: P changes the metric, not the solution)
