@@ -288,6 +288,15 @@ int nys_solver_alpha(nys_solver* solver, double* alpha);
 int nys_gram(nys_ctx* ctx, int dtype, const void* A, int p, const void* B, int q,
              int64_t N, double* C, int path);
 
+/* out (q columns of N, out_dtype) = (A + alpha A2) W for tall A, A2 (k
+ * columns of N, in_dtype; A2 may be NULL) and W (k x q float64, row-major,
+ * device): with A = Y, A2 = Omega, alpha = v this is U = Y_v (C^{-T} V S^{-1})
+ * of Algorithm 1 steps 6-7.  path as in nys_gram (tensor cores need bf16
+ * inputs, A2 given, k = q <= 256, N a multiple of 8 and >= 128).
+ * Synchronises. */
+int nys_tall_gemm(nys_ctx* ctx, int in_dtype, const void* A, const void* A2, double alpha,
+                  int64_t N, int k, const double* W, int q, int out_dtype, void* out, int path);
+
 /* ---------------------------------------------------------- reductions -- */
 /* *out (host) = ||a - b||_2 / ||b||_2 over n elements (b != 0), or ||a||_2
  * when b == NULL.  Synchronises. */

@@ -90,6 +90,7 @@ PROTOTYPES = {
     "nys_solver_objective": (i32, [vp, C.POINTER(f64)]),
     "nys_rel_err": (i32, [vp, i32, i64, vp, vp, C.POINTER(f64)]),
     "nys_gram": (i32, [vp, i32, vp, i32, vp, i32, i64, vp, i32]),
+    "nys_tall_gemm": (i32, [vp, i32, vp, vp, f64, i64, i32, vp, i32, i32, vp, i32]),
 }
 
 

@@ -379,6 +379,20 @@ def nys_gram(ctx: Context, A: torch.Tensor, B: torch.Tensor, path: int = 0) -> t
     return C
 
 
+def nys_tall_gemm(ctx: Context, A: torch.Tensor, A2: torch.Tensor | None, alpha: float, W: torch.Tensor,
+                  out_dtype=None, path: int = 0) -> torch.Tensor:
+    """(A + alpha A2) W for A, A2: (k, N) stacks of columns, W: (k, q) float64 -> (q, N)."""
+    k = A.shape[0]
+    N = A.numel() // k
+    q = W.shape[1]
+    od = out_dtype or A.dtype
+    out = torch.empty((q, N), dtype=od, device=A.device)
+    Wd = W.to(torch.float64).contiguous()
+    check(_lib().nys_tall_gemm(ctx.h, dtype_code(A), _ptr(A), _ptr(A2) if A2 is not None else None, alpha, N, k,
+                               _ptr(Wd), q, _DT[od], _ptr(out), path), ctx.h)
+    return out
+
+
 def nys_rel_err(ctx: Context, a: torch.Tensor, b: torch.Tensor | None) -> float:
     out = C.c_double()
     check(_lib().nys_rel_err(ctx.h, dtype_code(a), a.numel(), _ptr(a), _ptr(b) if b is not None else None,

@@ -25,6 +25,9 @@ int fail(nys_ctx* ctx, int code, const char* fmt, ...) {
 }
 
 int cuda_fail(nys_ctx* ctx, cudaError_t e, const char* what) {
+    // reset the runtime's last-error state so that a later, unrelated launch
+    // check does not report this (non-sticky) error again
+    cudaGetLastError();
     return fail(ctx, e == cudaErrorMemoryAllocation ? NYS_ENOMEM : NYS_ECUDA, "%s: %s", what,
                 cudaGetErrorString(e));
 }
@@ -273,6 +276,18 @@ int nys_gram(nys_ctx* ctx, int dtype, const void* A, int p, const void* B, int q
     if (dtype != NYS_F32 && dtype != NYS_F64 && dtype != NYS_BF16) return fail(ctx, NYS_EINVAL, "nys_gram: dtype");
     if (path < 0 || path > 2) return fail(ctx, NYS_EINVAL, "nys_gram: path");
     if (int st = gram_AtB_path(ctx, dtype, A, p, B, q, N, C, q, path)) return st;
+    return check_tc_timeout(ctx);
+}
+
+int nys_tall_gemm(nys_ctx* ctx, int in_dtype, const void* A, const void* A2, double alpha, int64_t N, int k,
+                  const double* W, int q, int out_dtype, void* out, int path) {
+    if (!ctx || !A || !W || !out) return fail(ctx, NYS_EINVAL, "nys_tall_gemm: null argument");
+    if (N <= 0 || k <= 0 || q <= 0 || path < 0 || path > 2) return fail(ctx, NYS_EINVAL, "nys_tall_gemm: sizes");
+    int st;
+    double* a_dev = (double*)scratch(ctx, SLOT_TCERR + 1, 64, &st);
+    if (st) return st;
+    NYS_CK(ctx, cudaMemcpyAsync(a_dev, &alpha, sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
+    if ((st = gemm_tall_path(ctx, in_dtype, A, A2, a_dev, N, k, W, q, out_dtype, out, path))) return st;
     return check_tc_timeout(ctx);
 }
 

@@ -253,6 +253,16 @@ int gram_AtB_path(nys_ctx* ctx, int dtype, const void* A, int p, const void* B, 
 
 int gemm_tall(nys_ctx* ctx, int in_dt, const void* A, const void* A2, const double* alpha, int64_t N, int k,
               const double* W, int q, int out_dt, void* out) {
+    return gemm_tall_path(ctx, in_dt, A, A2, alpha, N, k, W, q, out_dt, out, 0);
+}
+
+int gemm_tall_path(nys_ctx* ctx, int in_dt, const void* A, const void* A2, const double* alpha, int64_t N, int k,
+                   const double* W, int q, int out_dt, void* out, int path) {
+    if (path != 1 && in_dt == NYS_BF16 && A2 && k == q) {
+        const int st = gemm_tall_tc(ctx, A, A2, alpha, N, k, W, out_dt, out);
+        if (st != NYS_EINVAL) return st;
+    }
+    if (path == 2) return fail(ctx, NYS_EINVAL, "tall gemm: shape or dtype not supported by the tensor-core path");
     int st;
     const bool f64 = in_dt == NYS_F64;
     void* Wc = scratch(ctx, SLOT_MISC, (size_t)k * q * (f64 ? 8 : 4), &st);

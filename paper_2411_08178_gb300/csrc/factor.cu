@@ -34,10 +34,10 @@ __global__ void form_H_kernel(const double* __restrict__ G2, int ell, const doub
 __global__ void tri_inv_kernel(const double* __restrict__ C, double* __restrict__ X, int n);
 __global__ void weights_kernel(const double* __restrict__ S_hat, int ell, double mu, int sqrt_shift,
                                double* __restrict__ d, double* __restrict__ sqd, float* __restrict__ d32);
-__global__ void form_A_kernel(const double* __restrict__ K, const double* __restrict__ sqd, int ell,
+__global__ void form_A_kernel(const double* __restrict__ K, int ldk, const double* __restrict__ sqd, int eff,
                               double* __restrict__ A);
 __global__ void chol_kernel(double* __restrict__ A, int n, double* __restrict__ info);
-__global__ void form_M_kernel(const double* __restrict__ Ainv, const double* __restrict__ sqd, int ell,
+__global__ void form_M_kernel(const double* __restrict__ Ainv, const double* __restrict__ sqd, int ell, int eff,
                               double* __restrict__ M, float* __restrict__ M32);
 
 namespace {
@@ -455,36 +455,42 @@ int precond_setup_impl(nys_ctx* ctx, nys_precond* pc, double mu, int sqrt_shift)
     if (!(sref + mu > 0.0))
         return fail(ctx, NYS_EDEGENERATE, "preconditioner: s_K%s + mu = %g is not positive",
                     sqrt_shift ? " (square-rooted)" : "", sref + mu);
+    cudaStream_t s = ctx->stream;
+    // active prefix: the same IEEE double expression as weights_kernel; d is
+    // non-increasing, so d_i > 0 exactly for i < eff
+    std::vector<double> S(ell);
+    NYS_CK(ctx, cudaMemcpyAsync(S.data(), pc->S_hat, ell * sizeof(double), cudaMemcpyDeviceToHost, s));
+    NYS_CK(ctx, cudaStreamSynchronize(s));
+    int eff = 0;
+    for (int i = 0; i < ell; ++i)
+        if ((S[i] + mu) / (sref + mu) - 1.0 > 0.0) eff = i + 1;
     int st;
-    double* work = (double*)scratch(ctx, SLOT_FACTOR, (size_t)4 * ell * ell * sizeof(double) + 64, &st);
+    double* work = (double*)scratch(ctx, SLOT_FACTOR, (size_t)3 * ell * ell * sizeof(double) + 256, &st);
     if (st) return st;
     double* A = work;
     double* Li = A + (size_t)ell * ell;
     double* Ai = Li + (size_t)ell * ell;
     double* info = Ai + (size_t)ell * ell;
-    cudaStream_t s = ctx->stream;
+    NYS_CK(ctx, cudaMemsetAsync(info, 0, 4 * sizeof(double), s));
     weights_kernel<<<(ell + 127) / 128, 128, 0, s>>>(pc->S_hat, ell, mu, sqrt_shift, pv->d, pv->sqrtd, pv->d32);
     NYS_LAUNCH_CK(ctx);
-    form_A_kernel<<<64, 256, 0, s>>>(pv->K, pv->sqrtd, ell, A);
-    NYS_LAUNCH_CK(ctx);
-    chol_kernel<<<1, 1024, 0, s>>>(A, ell, info);
-    NYS_LAUNCH_CK(ctx);
-    tri_inv_kernel<<<ell, 32, 0, s>>>(A, Li, ell);
-    NYS_LAUNCH_CK(ctx);
-    // (I + Ubar^T Ubar)^{-1} = L^{-T} L^{-1}
-    if ((st = launch_small_gemm(ctx, Li, 1, Li, 0, ell, ell, ell, nullptr, Ai))) return st;
-    form_M_kernel<<<64, 256, 0, s>>>(Ai, pv->sqrtd, ell, pv->M64, pv->M32);
+    if (eff > 0) {
+        // (I + Ubar^T Ubar)^{-1} on the active block only (Ubar's other columns are 0)
+        form_A_kernel<<<64, 256, 0, s>>>(pv->K, ell, pv->sqrtd, eff, A);
+        NYS_LAUNCH_CK(ctx);
+        chol_kernel<<<1, 1024, 0, s>>>(A, eff, info);
+        NYS_LAUNCH_CK(ctx);
+        tri_inv_kernel<<<eff, 32, 0, s>>>(A, Li, eff);
+        NYS_LAUNCH_CK(ctx);
+        // (I + Ubar^T Ubar)^{-1} = L^{-T} L^{-1}
+        if ((st = launch_small_gemm(ctx, Li, 1, Li, 0, eff, eff, eff, nullptr, Ai))) return st;
+    }
+    form_M_kernel<<<64, 256, 0, s>>>(Ai, pv->sqrtd, ell, eff, pv->M64, pv->M32);
     NYS_LAUNCH_CK(ctx);
     double h_info[4];
-    std::vector<double> S(ell);
     NYS_CK(ctx, cudaMemcpyAsync(h_info, info, sizeof(h_info), cudaMemcpyDeviceToHost, s));
-    NYS_CK(ctx, cudaMemcpyAsync(S.data(), pc->S_hat, ell * sizeof(double), cudaMemcpyDeviceToHost, s));
     NYS_CK(ctx, cudaStreamSynchronize(s));
     if (h_info[3] != 0.0) return fail(ctx, NYS_ENONFINITE, "preconditioner: I + Ubar^T Ubar is not positive definite");
-    // active prefix: the same IEEE double expression as weights_kernel
-    int eff = 0;
-    for (int i = 0; i < ell; ++i)
-        if ((S[i] + mu) / (sref + mu) - 1.0 > 0.0) eff = i + 1;
     pv->ell_eff = eff;
     pc->mu = mu;
     pc->sqrt_shift = sqrt_shift;

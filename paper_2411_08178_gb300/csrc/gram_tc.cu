@@ -287,3 +287,251 @@ int gram_AtB_tc(nys_ctx* ctx, const void* A, int p, const void* B, int q, int64_
 }
 
 }  // namespace nys
+
+// ---------------------------------------------------------------------------
+// U = (Y + v Omega) W on tcgen05, as the plain product U = [Y | Omega] W' with
+// W' = [W; v W] (no elementwise pass over the tall data).  Per CTA one
+// 128-pixel tile of U and all q <= 256 columns:
+//   A (128 pixels x 64 k) comes from Y or Omega, whose rows are images, so the
+//     operand is MN-major: two 64-pixel TMA boxes (128B swizzle) side by side,
+//     the second at LBO = 8 KB, 8-row K groups 1 KB apart (SBO)
+//   B (q x 64 k) from W'^T, K-major, as in the Gram kernel
+//   D in TMEM: lane = pixel, column = output column j; the epilogue writes
+//     U[j][pixel] with 32 consecutive pixels per warp store.
+namespace nys {
+namespace {
+
+constexpr uint32_t idesc_bf16_amn(int M, int N) { return idesc_bf16(M, N) | (1u << 15); }
+
+__device__ __forceinline__ uint64_t sw128_mnmajor_desc(const void* tile, uint32_t lbo_bytes) {
+    const uint32_t a = smem_u32(tile);
+    return (uint64_t)((a & 0x3FFFFu) >> 4) | ((uint64_t)(lbo_bytes >> 4) << 16) | ((uint64_t)(1024 >> 4) << 32) |
+           ((uint64_t)1 << 46) | ((uint64_t)2 << 61);
+}
+
+// W' = [W; v W] as a bf16 pair W' = hi + lo (error ~2^-16 relative), stored
+// K-major: Wt[j][k] = hi, Wt[j][Kpad + k] = lo, for k < L1 from W[k][j]
+// (k < ell) and for L1 <= k < 2 L1 from v W[k - L1][j]; zero padding.
+constexpr int TALL_STAGES = 3;
+__global__ void wt_kernel(const double* __restrict__ W, int ell, const double* __restrict__ v_dev, int L1,
+                          __nv_bfloat16* __restrict__ Wt) {
+    const int Kpad = 2 * L1;
+    const double v = v_dev ? *v_dev : 0.0;
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < ell * Kpad; t += gridDim.x * blockDim.x) {
+        const int j = t / Kpad, k = t - j * Kpad;
+        double w = 0.0;
+        if (k < L1) w = (k < ell) ? W[(size_t)k * ell + j] : 0.0;
+        else w = (k - L1 < ell) ? v * W[(size_t)(k - L1) * ell + j] : 0.0;
+        const __nv_bfloat16 hi = __float2bfloat16_rn((float)w);
+        const __nv_bfloat16 lo = __float2bfloat16_rn((float)(w - (double)__bfloat162float(hi)));
+        Wt[(size_t)j * 2 * Kpad + k] = hi;
+        Wt[(size_t)j * 2 * Kpad + Kpad + k] = lo;
+    }
+}
+
+template <class TO>
+__global__ void __launch_bounds__(256, 1)
+    tall_tc_kernel(const __grid_constant__ CUtensorMap tmY, const __grid_constant__ CUtensorMap tmO,
+                   const __grid_constant__ CUtensorMap tmW, int64_t N, int q, int BN, int tmem_cols, int kb_half, int kpad, int nst,
+                   TO* __restrict__ U, int* __restrict__ err) {
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    unsigned char* base = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    const uint32_t half_bytes = 64 * TC_BK * 2;          // one 64-pixel x 64-k box
+    const uint32_t a_bytes = 2 * half_bytes;
+    const uint32_t bh_bytes = (uint32_t)BN * TC_BK * 2;   // one of the hi / lo tiles
+    const uint32_t b_bytes = 2 * bh_bytes;
+    unsigned char* sA = base;
+    unsigned char* sB = base + nst * a_bytes;
+    uint64_t* full = reinterpret_cast<uint64_t*>(sB + nst * b_bytes);
+    uint64_t* empty = full + nst;
+    uint64_t* accum = empty + nst;
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(accum + 1);
+    int* abort_flag = reinterpret_cast<int*>(tmem_slot + 1);
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int64_t m0 = (int64_t)blockIdx.x * TC_BM;
+    const int nk = 2 * kb_half;
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < nst; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], 1);
+        }
+        mbar_init(accum, 1);
+        *abort_flag = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 2) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                     "r"(tmem_cols)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *tmem_slot;
+
+    if (warp == 0 && lane == 0) {
+        int issued = 0;
+        for (int i = 0; i < nk; ++i) {
+            const int s = i % nst;
+            const uint32_t ph = (uint32_t)(i / nst) & 1u;
+            if (!mbar_wait(&empty[s], ph ^ 1u) || *(volatile int*)abort_flag) {
+                atomicExch(err, 1);
+                *(volatile int*)abort_flag = 1;
+                break;
+            }
+            mbar_arrive_expect_tx(&full[s], a_bytes + b_bytes);
+            const CUtensorMap* mx = (i < kb_half) ? &tmY : &tmO;
+            const int krow = (i < kb_half ? i : i - kb_half) * TC_BK;
+            tma_load_2d(sA + s * a_bytes, mx, &full[s], (int)m0, krow);
+            tma_load_2d(sA + s * a_bytes + half_bytes, mx, &full[s], (int)m0 + 64, krow);
+            tma_load_2d(sB + s * b_bytes, &tmW, &full[s], i * TC_BK, 0);
+            tma_load_2d(sB + s * b_bytes + bh_bytes, &tmW, &full[s], kpad + i * TC_BK, 0);
+            ++issued;
+        }
+        for (int i = max(0, issued - nst); i < issued; ++i)
+            if (!mbar_wait(&full[i % nst], (uint32_t)(i / nst) & 1u)) atomicExch(err, 1);
+    } else if (warp == 1 && lane == 0) {
+        const uint32_t idesc = idesc_bf16_amn(TC_BM, BN);
+        for (int i = 0; i < nk; ++i) {
+            const int s = i % nst;
+            const uint32_t ph = (uint32_t)(i / nst) & 1u;
+            if (!mbar_wait(&full[s], ph) || *(volatile int*)abort_flag) {
+                atomicExch(err, 1);
+                *(volatile int*)abort_flag = 1;
+                break;
+            }
+            tc_fence_after();
+            const uint64_t da = sw128_mnmajor_desc(sA + s * a_bytes, half_bytes);
+            const uint64_t dbh = sw128_kmajor_desc(sB + s * b_bytes);
+            const uint64_t dbl = sw128_kmajor_desc(sB + s * b_bytes + bh_bytes);
+#pragma unroll
+            for (int k = 0; k < TC_BK / 16; ++k) {
+                // A: +16 K rows = 2048 bytes (2 swizzle atoms); B: +32 bytes inside the row.
+                // Two MMAs per K step: the hi and the lo part of W'.
+                const uint32_t acc = (i > 0 || k > 0) ? 1u : 0u;
+                const uint64_t dak = da + (uint64_t)(k * (2048 >> 4));
+                asm volatile(
+                    "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+                    "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
+                    "l"(dak), "l"(dbh + 2 * k), "r"(idesc), "r"(acc)
+                    : "memory");
+                asm volatile(
+                    "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+                    "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
+                    "l"(dak), "l"(dbl + 2 * k), "r"(idesc), "r"(1u)
+                    : "memory");
+            }
+            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                             smem_u32(&empty[s]))
+                         : "memory");
+        }
+        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                         smem_u32(accum))
+                     : "memory");
+    } else if (warp >= 4) {
+        const int quarter = warp & 3;
+        const bool ok = mbar_wait(accum, 0);
+        tc_fence_after();
+        if (!ok) atomicExch(err, 1);
+        const int64_t pix = m0 + quarter * 32 + lane;
+        if (ok && !*(volatile int*)abort_flag) {
+            for (int c0 = 0; c0 < BN; c0 += 16) {
+                uint32_t v[16];
+                const uint32_t taddr = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)c0;
+                asm volatile(
+                    "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, "
+                    "[%16];"
+                    : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+                      "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]),
+                      "=r"(v[15])
+                    : "r"(taddr));
+                asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+                if (pix < N) {
+#pragma unroll
+                    for (int j = 0; j < 16; ++j)
+                        if (c0 + j < q) stf(U + (size_t)(c0 + j) * N + pix, __uint_as_float(v[j]));
+                }
+            }
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    if (warp == 2)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(tmem_cols) : "memory");
+}
+
+bool make_map_box(PFN_cuTensorMapEncodeTiled_v12000 enc, CUtensorMap* m, const void* ptr, int64_t inner,
+                  int64_t rows, int box_inner, int box_rows) {
+    cuuint64_t dims[2] = {(cuuint64_t)inner, (cuuint64_t)rows};
+    cuuint64_t strides[1] = {(cuuint64_t)inner * 2};
+    cuuint32_t box[2] = {(cuuint32_t)box_inner, (cuuint32_t)box_rows};
+    cuuint32_t estr[2] = {1, 1};
+    return enc(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(ptr), dims, strides, box, estr,
+               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+}  // namespace
+
+// out (q = ell columns of N, dtype out_dt) = (Y + v Omega) W for bf16 Y, Omega;
+// W is ell x ell float64 (row-major), v read from v_dev.  NYS_EINVAL when the
+// shape is not supported (caller falls back to CUDA cores).
+int gemm_tall_tc(nys_ctx* ctx, const void* Y, const void* Om, const double* v_dev, int64_t N, int ell,
+                 const double* W, int out_dt, void* out) {
+    if (ell < 1 || ell > 256 || N < 128 || (N % 8) != 0 || N > (int64_t)0x7fffffff ||
+        (((uintptr_t)Y | (uintptr_t)Om) & 15) || (out_dt != NYS_BF16 && out_dt != NYS_F32))
+        return NYS_EINVAL;
+    auto enc = encode_fn(ctx);
+    if (!enc) return NYS_EINVAL;
+    const int q = ell;
+    const int BN = ((q + 15) / 16) * 16;
+    int tmem_cols = 32;
+    while (tmem_cols < BN) tmem_cols <<= 1;
+    const int L1 = ((ell + TC_BK - 1) / TC_BK) * TC_BK;
+    const int Kpad = 2 * L1;
+    int st;
+    __nv_bfloat16* Wt = (__nv_bfloat16*)scratch(ctx, SLOT_MISC, (size_t)q * 2 * Kpad * 2 + 256, &st);
+    if (st) return st;
+    int* err = (int*)scratch(ctx, SLOT_TCERR, 64, &st);
+    if (st) return st;
+    CUtensorMap mY, mO, mW;
+    if (!make_map_box(enc, &mY, Y, N, ell, 64, TC_BK) || !make_map_box(enc, &mO, Om, N, ell, 64, TC_BK) ||
+        !make_map_box(enc, &mW, Wt, 2 * Kpad, q, TC_BK, BN))
+        return NYS_EINVAL;
+    cudaStream_t s = ctx->stream;
+    wt_kernel<<<64, 256, 0, s>>>(W, ell, v_dev, L1, Wt);
+    NYS_LAUNCH_CK(ctx);
+    // as many stages (2 or 3) as fit in the 227 KB shared-memory budget
+    const size_t stage_bytes = 2 * 64 * TC_BK * 2 + 2 * (size_t)BN * TC_BK * 2;
+    const int nst = (int)std::min<size_t>(TALL_STAGES, (227 * 1024 - 2048) / stage_bytes);
+    if (nst < 2) return NYS_EINVAL;
+    const size_t smem = 1024 + (size_t)nst * stage_bytes + 256;
+    const unsigned mtiles = (unsigned)((N + TC_BM - 1) / TC_BM);
+    if (out_dt == NYS_BF16) {
+        static size_t attr = 0;
+        if (smem > attr) {
+            NYS_CK(ctx, cudaFuncSetAttribute(tall_tc_kernel<__nv_bfloat16>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+            attr = smem;
+        }
+        tall_tc_kernel<__nv_bfloat16><<<mtiles, 256, smem, s>>>(mY, mO, mW, N, q, BN, tmem_cols, L1 / TC_BK,
+                                                                 Kpad, nst, (__nv_bfloat16*)out, err);
+    } else {
+        static size_t attr = 0;
+        if (smem > attr) {
+            NYS_CK(ctx, cudaFuncSetAttribute(tall_tc_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)smem));
+            attr = smem;
+        }
+        tall_tc_kernel<float><<<mtiles, 256, smem, s>>>(mY, mO, mW, N, q, BN, tmem_cols, L1 / TC_BK, Kpad, nst, (float*)out,
+                                                       err);
+    }
+    NYS_LAUNCH_CK(ctx);
+    return NYS_OK;
+}
+
+}  // namespace nys

@@ -160,6 +160,12 @@ int gram_AtB_path(nys_ctx* ctx, int dtype, const void* A, int p, const void* B, 
 // tcgen05 Gram for bf16 operands (gram_tc.cu); NYS_EINVAL when unsupported
 int gram_AtB_tc(nys_ctx* ctx, const void* A, int p, const void* B, int q, int64_t N, double* C, int ldc);
 void gram_reduce_f32(nys_ctx* ctx, const float* part, int splits, int p, int q, double* C, int ldc, int blocks);
+// tcgen05 U = (Y + v Omega) W for bf16 Y, Omega, ell <= 256 (gram_tc.cu); NYS_EINVAL when unsupported
+int gemm_tall_tc(nys_ctx* ctx, const void* Y, const void* Om, const double* v_dev, int64_t N, int ell,
+                 const double* W, int out_dt, void* out);
+// path: 0 = tensor cores when possible, 1 = CUDA cores, 2 = tensor cores or NYS_EINVAL
+int gemm_tall_path(nys_ctx* ctx, int in_dt, const void* A, const void* A2, const double* alpha_dev, int64_t N,
+                   int k, const double* W, int q, int out_dt, void* out, int path);
 // raise NYS_ETIMEOUT if a tensor-core kernel recorded a time-out (synchronises)
 int check_tc_timeout(nys_ctx* ctx);
 // out (N x q, dtype out_dt) = (A + alpha*A2) W, A/A2: N x k of in_dt, W: k x q double (row-major k x q)

@@ -234,6 +234,7 @@ __global__ void __launch_bounds__(1024) jacobi_smem_kernel(const T* __restrict__
     __syncthreads();
     const T eps = sizeof(T) == 8 ? T(1e-15) : T(1e-7);
     int sweep = 0, round_total = 0;
+    __shared__ int nrot;   // rotations applied in the current sweep
     for (; sweep < max_sweeps; ++sweep) {
         double off = 0.0, dg = 0.0;
         for (int t = threadIdx.x; t < nreal * nreal; t += blockDim.x) {
@@ -245,6 +246,8 @@ __global__ void __launch_bounds__(1024) jacobi_smem_kernel(const T* __restrict__
         off = block_sum(off, sh);
         dg = block_sum(dg, sh);
         if (off <= tol * tol * dg) break;
+        if (threadIdx.x == 0) nrot = 0;
+        __syncthreads();
         for (int round = 0; round < n - 1; ++round, ++round_total) {
             for (int k = threadIdx.x; k < h; k += blockDim.x) {
                 const int a = arr[k], b = arr[n - 1 - k];
@@ -264,6 +267,7 @@ __global__ void __launch_bounds__(1024) jacobi_smem_kernel(const T* __restrict__
                 qq[k] = q;
                 cs[k] = c;
                 sn[k] = s;
+                if (s != T(0)) atomicAdd(&nrot, 1);
                 logpq[(size_t)round_total * h + k] = make_int2(p, q);
                 logcs[((size_t)round_total * h + k) * 2] = c;
                 logcs[((size_t)round_total * h + k) * 2 + 1] = s;
@@ -292,6 +296,12 @@ __global__ void __launch_bounds__(1024) jacobi_smem_kernel(const T* __restrict__
             for (int t = threadIdx.x; t < n; t += blockDim.x) arr[t] = arr2[t];
             __syncthreads();
         }
+        // threshold criterion: a sweep without a single rotation has converged
+        // to the working precision
+        if (nrot == 0) {
+            ++sweep;
+            break;
+        }
     }
     if (threadIdx.x == 0) {
         *sweeps_out = sweep;
@@ -299,31 +309,50 @@ __global__ void __launch_bounds__(1024) jacobi_smem_kernel(const T* __restrict__
     }
 }
 
-// V[i][:] = e_i J_1 ... J_r, one warp per row; pairs of a round are disjoint
+// V[i][:] = e_i J_1 ... J_r, one warp per row (eight rows per CTA); pairs of
+// a round are disjoint.  The log is staged through shared memory RCH rounds
+// at a time by the whole CTA, so the sequential rounds wait on shared-memory
+// latency instead of global-memory latency.
+constexpr int RCH = 32;
 template <class T>
 __global__ void __launch_bounds__(256) rot_apply_kernel(const int2* __restrict__ logpq, const T* __restrict__ logcs,
                                                         const int* __restrict__ rounds, int n, T* __restrict__ V) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int i = blockIdx.x * 8 + warp;
-    T* row = reinterpret_cast<T*>(smem_raw) + (size_t)warp * n;
-    if (i >= n) return;
-    for (int j = lane; j < n; j += 32) row[j] = (j == i) ? T(1) : T(0);
-    __syncwarp();
     const int h = n / 2;
+    const int i = blockIdx.x * 8 + warp;
+    T* rows = reinterpret_cast<T*>(smem_raw);              // 8 x n
+    T* scs = rows + 8 * (size_t)n;                         // RCH x h x 2
+    int2* spq = reinterpret_cast<int2*>(scs + (size_t)RCH * h * 2);   // RCH x h
+    T* row = rows + (size_t)warp * n;
+    for (int j = lane; j < n; j += 32) row[j] = (j == i) ? T(1) : T(0);
     const int R = *rounds;
-    for (int r = 0; r < R; ++r) {
-        for (int k = lane; k < h; k += 32) {
-            const int2 pq = logpq[(size_t)r * h + k];
-            const T c = logcs[((size_t)r * h + k) * 2], s = logcs[((size_t)r * h + k) * 2 + 1];
-            if (s == T(0)) continue;
-            const T vp = row[pq.x], vq = row[pq.y];
-            row[pq.x] = c * vp - s * vq;
-            row[pq.y] = s * vp + c * vq;
+    for (int r0 = 0; r0 < R; r0 += RCH) {
+        const int nr = min(RCH, R - r0);
+        __syncthreads();
+        for (int t = threadIdx.x; t < nr * h; t += blockDim.x) {
+            spq[t] = logpq[(size_t)r0 * h + t];
+            scs[2 * t] = logcs[((size_t)r0 * h + t) * 2];
+            scs[2 * t + 1] = logcs[((size_t)r0 * h + t) * 2 + 1];
         }
-        __syncwarp();
+        __syncthreads();
+        if (i < n) {
+            for (int r = 0; r < nr; ++r) {
+                for (int k = lane; k < h; k += 32) {
+                    const T s = scs[2 * (r * h + k) + 1];
+                    if (s == T(0)) continue;
+                    const T c = scs[2 * (r * h + k)];
+                    const int2 pq = spq[r * h + k];
+                    const T vp = row[pq.x], vq = row[pq.y];
+                    row[pq.x] = c * vp - s * vq;
+                    row[pq.y] = s * vp + c * vq;
+                }
+                __syncwarp();
+            }
+        }
     }
-    for (int j = lane; j < n; j += 32) V[(size_t)i * n + j] = row[j];
+    if (i < n)
+        for (int j = lane; j < n; j += 32) V[(size_t)i * n + j] = row[j];
 }
 
 // lambda_i = v_i^T G v_i / (v_i^T v_i), G float64 (ld = ell), V (ld = n) of T.
@@ -378,12 +407,12 @@ __global__ void weights_kernel(const double* __restrict__ S_hat, int ell, double
     }
 }
 
-// A = I + diag(sqd) K diag(sqd)
-__global__ void form_A_kernel(const double* __restrict__ K, const double* __restrict__ sqd, int ell,
+// A (eff x eff) = I + diag(sqd) K diag(sqd) on the leading eff x eff block of K (ld = ldk)
+__global__ void form_A_kernel(const double* __restrict__ K, int ldk, const double* __restrict__ sqd, int eff,
                               double* __restrict__ A) {
-    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < ell * ell; t += gridDim.x * blockDim.x) {
-        const int i = t / ell, j = t % ell;
-        A[t] = (i == j ? 1.0 : 0.0) + sqd[i] * 0.5 * (K[t] + K[(size_t)j * ell + i]) * sqd[j];
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < eff * eff; t += gridDim.x * blockDim.x) {
+        const int i = t / eff, j = t % eff;
+        A[t] = (i == j ? 1.0 : 0.0) + sqd[i] * 0.5 * (K[(size_t)i * ldk + j] + K[(size_t)j * ldk + i]) * sqd[j];
     }
 }
 
@@ -393,12 +422,13 @@ __global__ void chol_kernel(double* __restrict__ A, int n, double* __restrict__ 
     if (threadIdx.x == 0) info[3] = ok ? 0.0 : 1.0;
 }
 
-// M = diag(sqd) (Linv^T Linv) diag(sqd); also a float copy
-__global__ void form_M_kernel(const double* __restrict__ Ainv, const double* __restrict__ sqd, int ell,
+// M (ell x ell) = diag(sqd) Ainv diag(sqd) on the leading eff x eff block
+// (Ainv has ld = eff), zero elsewhere; also a float copy
+__global__ void form_M_kernel(const double* __restrict__ Ainv, const double* __restrict__ sqd, int ell, int eff,
                               double* __restrict__ M, float* __restrict__ M32) {
     for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < ell * ell; t += gridDim.x * blockDim.x) {
         const int i = t / ell, j = t % ell;
-        const double m = sqd[i] * Ainv[t] * sqd[j];
+        const double m = (i < eff && j < eff) ? sqd[i] * Ainv[(size_t)i * eff + j] * sqd[j] : 0.0;
         M[t] = m;
         M32[t] = (float)m;
     }
@@ -452,7 +482,14 @@ int sym_eig(nys_ctx* ctx, const double* G, int ell, bool use_f32, const double* 
             jacobi_smem_kernel<T><<<1, 1024, smem, s>>>(Gw, n, ell, max_sweeps, tol, logpq, logcs, rounds_dev,
                                                         sweeps_dev);
             NYS_LAUNCH_CK(ctx);
-            rot_apply_kernel<T><<<(n + 7) / 8, 256, 8 * n * sizeof(T), s>>>(logpq, logcs, rounds_dev, n, V);
+            const size_t rsm = (8 * (size_t)n + (size_t)RCH * h * 2) * sizeof(T) + (size_t)RCH * h * sizeof(int2);
+            static size_t rattr = 48 * 1024;
+            if (rsm > rattr) {
+                NYS_CK(ctx, cudaFuncSetAttribute(rot_apply_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                 (int)rsm));
+                rattr = rsm;
+            }
+            rot_apply_kernel<T><<<(n + 7) / 8, 256, rsm, s>>>(logpq, logcs, rounds_dev, n, V);
             NYS_LAUNCH_CK(ctx);
         } else {
             jacobi_kernel<T><<<1, 1024, 0, s>>>(Gw, V, n, ell, max_sweeps, tol, sweeps_dev);

@@ -47,6 +47,26 @@ def test_gram_paths_agree(env, p, q, N):
     assert np.linalg.norm(Ct - Cc) <= 1e-5 * np.linalg.norm(ref)
 
 
+@pytest.mark.parametrize("k,N,out", [(200, 262144, "bf16"), (48, 5000, "f32"), (17, 1024, "f32"), (256, 2048, "bf16"),
+                                     (1, 128, "f32")])
+def test_tall_gemm_tensor_cores_match_float64(env, k, N, out):
+    # U = (Y + v Omega) W: the MN-major A operand (columns are images)
+    torch, api, ctx = env
+    g = torch.Generator(device="cpu").manual_seed(k + N)
+    Y = torch.randn(k, N, generator=g).to(torch.bfloat16)
+    Om = torch.randn(k, N, generator=g).to(torch.bfloat16)
+    W = torch.randn(k, k, generator=g, dtype=torch.float64) / np.sqrt(k)
+    v = 0.37
+    ref = ((Y.double() + v * Om.double()).T.numpy() @ W.numpy()).T       # (q, N)
+    od = torch.bfloat16 if out == "bf16" else torch.float32
+    U = api.nys_tall_gemm(ctx, Y.cuda(), Om.cuda(), v, W.cuda(), out_dtype=od, path=2).double().cpu().numpy()
+    # bf16 output rounding (2^-9) / W split into bf16 hi + lo (about 2^-17)
+    tol = 8e-3 if out == "bf16" else 1e-4
+    assert np.linalg.norm(U - ref) / np.linalg.norm(ref) < tol
+    Uc = api.nys_tall_gemm(ctx, Y.cuda(), Om.cuda(), v, W.cuda(), out_dtype=od, path=1).double().cpu().numpy()
+    assert np.linalg.norm(U - Uc) / np.linalg.norm(ref) < tol
+
+
 def test_gram_symmetric_and_fallback(env):
     torch, api, ctx = env
     A, _, ref = _operands(torch, 40, 40, 4096, seed=9, same=True)
