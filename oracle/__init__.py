@@ -14,8 +14,10 @@ slowly and obviously, one step at a time:
   nystrom   -- Algorithm 1 and the preconditioner of Eq. (RYPreconditioner)
   prox      -- Theorem 1 prox (semi-smooth Newton) and the dual APG prox (Sec. III-B)
   wapg      -- Algorithm 3 (WAPG / APG), power-iteration step size, objectives
+  unroll    -- K unrolled Algorithm 3 iterations (TV) and their hand-derived
+               reverse-mode gradient with respect to lambda and the blur kernel
 Every function is pinned by a `-m "not gpu"` test against something other than
 itself (closed forms, invariants, brute force, published test vectors); see
 the tests named test_oracle_*.
 """
-from . import operators, philox, nystrom, prox, wapg  # noqa: F401
+from . import operators, philox, nystrom, prox, wapg, unroll  # noqa: F401

@@ -217,7 +217,10 @@ template <class T>
 __global__ void __launch_bounds__(1024) jacobi_smem_kernel(const T* __restrict__ Gin, int n, int nreal,
                                                            int max_sweeps, double tol, int2* __restrict__ logpq,
                                                            T* __restrict__ logcs, int* __restrict__ rounds_out,
-                                                           int* __restrict__ sweeps_out) {
+                                                           int* __restrict__ sweeps_out,
+                                                           const int* __restrict__ only_if_failed) {
+    // runs only when the one-sided kernel reported a failed Cholesky
+    if (only_if_failed && *only_if_failed == 0) return;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int h = n / 2;
     const int pitch = n + 1;
@@ -306,6 +309,138 @@ __global__ void __launch_bounds__(1024) jacobi_smem_kernel(const T* __restrict__
     if (threadIdx.x == 0) {
         *sweeps_out = sweep;
         *rounds_out = round_total;
+    }
+}
+
+// One-sided (Hestenes) Jacobi for the same eigenproblem: G = R^T R by an
+// in-shared-memory Cholesky (upper R, column j at R + j * (n + 1)), then plane
+// rotations of column pairs of R until all columns are mutually orthogonal;
+// the accumulated rotation V holds the eigenvectors of G (R V has orthogonal
+// columns, so V^T G V is diagonal).  Columns are contiguous in shared memory,
+// so a pair's inner products and its update are stride-1.  The rotation log
+// has the two-sided kernel's format.  status_out = 1 (and nothing logged) if
+// the Cholesky meets a non-positive pivot, so that the two-sided kernel runs.
+template <class T>
+__global__ void __launch_bounds__(1024) jacobi_1s_kernel(const T* __restrict__ Gin, int n, int nreal, int max_sweeps,
+                                                         int2* __restrict__ logpq, T* __restrict__ logcs,
+                                                         int* __restrict__ rounds_out, int* __restrict__ sweeps_out,
+                                                         int* __restrict__ status_out) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int h = n / 2;
+    const int pitch = n + 1;   // column j at R + j * pitch
+    T* R = reinterpret_cast<T*>(smem_raw);
+    __shared__ int bad;
+    // load G (symmetric) into R as column-major, pad index -> identity
+    for (int t = threadIdx.x; t < n * n; t += blockDim.x) {
+        const int i = t / n, j = t % n;
+        T g = Gin[t];
+        if (i >= nreal || j >= nreal) g = (i == j) ? T(1) : T(0);
+        R[j * pitch + i] = g;
+    }
+    if (threadIdx.x == 0) bad = 0;
+    __syncthreads();
+    // in-place Cholesky, upper factor: R[k][j] for j >= k (column j holds rows 0..j)
+    for (int k = 0; k < n; ++k) {
+        if (threadIdx.x == 0) {
+            const T d = R[k * pitch + k];
+            if (!(d > T(0))) bad = 1;
+            else R[k * pitch + k] = sqrt(d);
+        }
+        __syncthreads();
+        if (bad) break;
+        const T rkk = R[k * pitch + k];
+        for (int j = k + 1 + threadIdx.x; j < n; j += blockDim.x) R[j * pitch + k] /= rkk;   // row k, columns j > k
+        __syncthreads();
+        const int m = n - k - 1;
+        for (int t = threadIdx.x; t < m * m; t += blockDim.x) {
+            const int i = k + 1 + t / m, j = k + 1 + t % m;
+            if (i <= j) R[j * pitch + i] -= R[i * pitch + k] * R[j * pitch + k];
+        }
+        __syncthreads();
+    }
+    if (bad) {
+        if (threadIdx.x == 0) *status_out = 1;
+        return;
+    }
+    for (int t = threadIdx.x; t < n * n; t += blockDim.x) {
+        const int i = t % n, j = t / n;   // zero the strict lower part
+        if (i > j) R[j * pitch + i] = T(0);
+    }
+    __syncthreads();
+    // Threshold: a pair counts as orthogonal once |x.y| <= tol sqrt(|x|^2 |y|^2)
+    // with tol = sqrt(n) eps; eigenvalues are recomputed afterwards in FP64 from
+    // Rayleigh quotients, so this bounds only the eigenvector accuracy.
+    const T tol = (sizeof(T) == 8 ? T(2.2e-16) : T(1.2e-7)) * sqrt(T(n));
+    // gs threads per column pair (a power of two <= 32), every pair of a round
+    // in flight at once; pairs by the circle method: player n-1 is fixed,
+    // players 0..n-2 rotate, round r pairs (n-1, r) and (r+k, r-k) mod (n-1)
+    int gs = 32;
+    while (gs > 1 && gs * h > (int)blockDim.x) gs >>= 1;
+    const int ngroups = blockDim.x / gs;
+    const int g = threadIdx.x / gs, gl = threadIdx.x % gs;
+    const int m1 = n - 1;
+    int sweep = 0, round_total = 0;
+    for (; sweep < max_sweeps; ++sweep) {
+        int rotated = 0;
+        for (int round = 0; round < m1; ++round, ++round_total) {
+            for (int k0 = 0; k0 < h; k0 += ngroups) {
+                const int k = k0 + g;
+                const bool active = k < h;
+                int p = 0, q = 1;
+                if (active) {
+                    const int u = (k == 0) ? m1 : (round + k) % m1;
+                    const int w = (k == 0) ? round : (round - k + m1) % m1;
+                    p = min(u, w);
+                    q = max(u, w);
+                }
+                T* wp = R + p * pitch;
+                T* wq = R + q * pitch;
+                T a = T(0), b = T(0), c = T(0);
+                if (active) {
+                    for (int i = gl; i < n; i += gs) {
+                        const T x = wp[i], y = wq[i];
+                        a = fma(x, x, a);
+                        b = fma(y, y, b);
+                        c = fma(x, y, c);
+                    }
+                }
+                for (int o = gs >> 1; o > 0; o >>= 1) {
+                    a += __shfl_xor_sync(0xffffffffu, a, o);
+                    b += __shfl_xor_sync(0xffffffffu, b, o);
+                    c += __shfl_xor_sync(0xffffffffu, c, o);
+                }
+                if (!active) continue;
+                T cs = T(1), sn = T(0);
+                if (q < nreal && c != T(0) && fabs(c) > tol * sqrt(a * b)) {
+                    const T zeta = (b - a) / (T(2) * c);
+                    const T t = (zeta >= T(0) ? T(1) : T(-1)) / (fabs(zeta) + sqrt(T(1) + zeta * zeta));
+                    cs = T(1) / sqrt(T(1) + t * t);
+                    sn = t * cs;
+                    for (int i = gl; i < n; i += gs) {
+                        const T x = wp[i], y = wq[i];
+                        wp[i] = cs * x - sn * y;
+                        wq[i] = sn * x + cs * y;
+                    }
+                    rotated = 1;
+                }
+                if (gl == 0) {
+                    const size_t e = (size_t)round_total * h + k;
+                    logpq[e] = make_int2(p, q);
+                    logcs[e * 2] = cs;
+                    logcs[e * 2 + 1] = sn;
+                }
+            }
+            __syncthreads();
+        }
+        if (!__syncthreads_or(rotated)) {
+            ++sweep;
+            break;
+        }
+    }
+    if (threadIdx.x == 0) {
+        *sweeps_out = sweep;
+        *rounds_out = round_total;
+        *status_out = 0;
     }
 }
 
@@ -479,8 +614,21 @@ int sym_eig(nys_ctx* ctx, const double* G, int ell, bool use_f32, const double* 
                                                  (int)smem));
                 attr = smem;
             }
+            // one-sided Jacobi on the Cholesky factor; the two-sided kernel
+            // runs instead (decided on the device) if that Cholesky fails
+            int* status_dev = sweeps_dev + 2;
+            const size_t smem1 = sizeof(T) * (size_t)n * (n + 1) + 64;
+            static size_t attr1 = 48 * 1024;
+            if (smem1 > attr1) {
+                NYS_CK(ctx, cudaFuncSetAttribute(jacobi_1s_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                 (int)smem1));
+                attr1 = smem1;
+            }
+            jacobi_1s_kernel<T><<<1, 1024, smem1, s>>>(Gw, n, ell, max_sweeps, logpq, logcs, rounds_dev, sweeps_dev,
+                                                       status_dev);
+            NYS_LAUNCH_CK(ctx);
             jacobi_smem_kernel<T><<<1, 1024, smem, s>>>(Gw, n, ell, max_sweeps, tol, logpq, logcs, rounds_dev,
-                                                        sweeps_dev);
+                                                        sweeps_dev, status_dev);
             NYS_LAUNCH_CK(ctx);
             const size_t rsm = (8 * (size_t)n + (size_t)RCH * h * 2) * sizeof(T) + (size_t)RCH * h * sizeof(int2);
             static size_t rattr = 48 * 1024;
