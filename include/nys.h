@@ -115,6 +115,10 @@ int nys_op_create(nys_ctx* ctx, const nys_op_desc* desc, nys_op** op);
 int nys_op_destroy(nys_op* op);
 /* Number of pixels N = n1*n2 and measurements M of one image. */
 int nys_op_sizes(const nys_op* op, int64_t* N, int64_t* M);
+/* Replace the blur kernel (host, float64, kh*kw with the op's kh, kw; copied)
+ * of a blur or blur + decimation op.  Synchronises the ctx stream; not
+ * capturable.  NYS_EINVAL for other kinds or another kernel shape. */
+int nys_op_set_kernel(nys_op* op, const double* kernel, int kh, int kw);
 
 /* y[b] = A x[b], b < batch.  x: batch*N, y: batch*M, op dtype. */
 int op_apply(nys_op* op, const void* x, void* y, int batch);
@@ -276,6 +280,42 @@ int nys_solver_get_x(nys_solver* solver, void* x_out);
 int nys_solver_objective(nys_solver* solver, double* F);
 /* The step size in use (host).  Synchronises if it was estimated. */
 int nys_solver_alpha(nys_solver* solver, double* alpha);
+
+/* ------------------------------------------ differentiated unrolled solve -- */
+/* Not in the paper: gradients of a truncated solve for learning lambda and
+ * the blur kernel.  The map is K iterations of Algorithm 3 with the
+ * anisotropic TV regulariser (quadratic data term), each prox the dual APG of
+ * Sec. III-B with n_inner steps warm-started from the previous iteration's
+ * dual, x^1 = u^1 = 0.  P and alpha are constants of the map. */
+typedef struct nys_unroll nys_unroll;
+typedef struct nys_unroll_desc {
+    double lambda;       /* TV weight, > 0                                   */
+    double alpha;        /* step size, > 0                                   */
+    int K;               /* outer iterations, >= 1                           */
+    int n_inner;         /* dual APG steps per prox, >= 0                    */
+    int ckpt_every;      /* keep (x, u, Q) every ckpt_every iterations and
+                            re-run each segment in the backward pass (0 = K) */
+} nys_unroll_desc;
+
+/* Allocates all device memory the forward and backward passes use: about
+ * (5 + 4 ceil(K / ckpt_every) + 18) N + 2 M values plus ckpt_every (N + M +
+ * 2 (n_inner + 1) N) for the segment record.  op must be f32 or f64 (the
+ * dtype of every buffer below); pc (may be NULL: P = I) must stay alive and
+ * unchanged while the handle is used. */
+int nys_unroll_create(nys_ctx* ctx, nys_op* op, const nys_precond* pc,
+                      const nys_unroll_desc* desc, nys_unroll** out);
+int nys_unroll_destroy(nys_unroll* u);
+/* x_out (device, N values; may be NULL) = x^{K+1} for data y (device, M
+ * values, copied).  Keeps the checkpoints for nys_unroll_backward. */
+int nys_unroll_forward(nys_unroll* u, const void* y, void* x_out);
+/* Reverse pass of the last forward: for the cotangent xbar (device, N values)
+ * of x^{K+1}, writes grads[0] = <xbar, d x / d lambda> and, for a blur
+ * operator, grads[1 + a kw + b] = <xbar, d x / d h[a][b]> (grads: device,
+ * float64, 1 + kh kw values).  NYS_EINVAL if no forward ran since the handle
+ * was created or lambda changed. */
+int nys_unroll_backward(nys_unroll* u, const void* xbar, double* grads);
+/* Change lambda (invalidates the last forward). */
+int nys_unroll_set_lambda(nys_unroll* u, double lambda);
 
 /* ------------------------------------------------------- dense products -- */
 /* C (p x q, float64, row-major, device) = A^T B for tall operands A (N x p)

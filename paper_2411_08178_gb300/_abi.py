@@ -46,6 +46,11 @@ class nys_solver_desc(C.Structure):
                 ("power_seed", C.c_uint64), ("no_graph", C.c_int)]
 
 
+class nys_unroll_desc(C.Structure):
+    _fields_ = [("lambda_", C.c_double), ("alpha", C.c_double), ("K", C.c_int), ("n_inner", C.c_int),
+                ("ckpt_every", C.c_int)]
+
+
 vp = C.c_void_p
 i32 = C.c_int
 i64 = C.c_int64
@@ -65,6 +70,7 @@ PROTOTYPES = {
     "nys_op_create": (i32, [vp, C.POINTER(nys_op_desc), C.POINTER(vp)]),
     "nys_op_destroy": (i32, [vp]),
     "nys_op_sizes": (i32, [vp, C.POINTER(i64), C.POINTER(i64)]),
+    "nys_op_set_kernel": (i32, [vp, C.POINTER(C.c_double), i32, i32]),
     "op_apply": (i32, [vp, vp, vp, i32]),
     "op_adjoint": (i32, [vp, vp, vp, i32]),
     "op_normal": (i32, [vp, vp, vp, i32]),
@@ -88,6 +94,11 @@ PROTOTYPES = {
     "nys_solver_get_x": (i32, [vp, vp]),
     "nys_solver_alpha": (i32, [vp, C.POINTER(f64)]),
     "nys_solver_objective": (i32, [vp, C.POINTER(f64)]),
+    "nys_unroll_create": (i32, [vp, vp, C.POINTER(nys_precond), C.POINTER(nys_unroll_desc), C.POINTER(vp)]),
+    "nys_unroll_destroy": (i32, [vp]),
+    "nys_unroll_forward": (i32, [vp, vp, vp]),
+    "nys_unroll_backward": (i32, [vp, vp, vp]),
+    "nys_unroll_set_lambda": (i32, [vp, f64]),
     "nys_rel_err": (i32, [vp, i32, i64, vp, vp, C.POINTER(f64)]),
     "nys_gram": (i32, [vp, i32, vp, i32, vp, i32, i64, vp, i32]),
     "nys_tall_gemm": (i32, [vp, i32, vp, vp, f64, i64, i32, vp, i32, i32, vp, i32]),

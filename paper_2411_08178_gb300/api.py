@@ -126,6 +126,13 @@ class Operator:
         else:
             self.meas_shape = (n_angles, n_bins)
 
+    def set_kernel(self, kernel):
+        """Replace the blur kernel (same shape; host copy, synchronises)."""
+        k = np.ascontiguousarray(np.asarray(kernel, dtype=np.float64))
+        check(_lib().nys_op_set_kernel(self.h, k.ctypes.data_as(C.POINTER(C.c_double)), k.shape[0], k.shape[1]),
+              self.ctx.h)
+        self._kernel = k
+
     def close(self):
         if getattr(self, "h", None):
             _lib().nys_op_destroy(self.h)
@@ -366,6 +373,52 @@ class Solver:
 
 def pgd_step(solver: Solver, n: int = 1):
     solver.step(n)
+
+
+class Unroll:
+    """nys_unroll: K unrolled TV-regularised Algorithm 3 iterations with a
+    hand-written reverse pass (gradients with respect to lambda and the blur
+    kernel; P and alpha fixed)."""
+
+    def __init__(self, ctx: Context, op: Operator, lam: float, alpha: float, K: int, n_inner: int = 20,
+                 ckpt_every: int = 10, pc: Precond | None = None):
+        d = A.nys_unroll_desc()
+        d.lambda_, d.alpha, d.K, d.n_inner, d.ckpt_every = lam, alpha, K, n_inner, ckpt_every
+        self.ctx, self.op, self.pc, self.lam = ctx, op, pc, lam
+        h = C.c_void_p()
+        pcs = C.byref(pc.s) if pc is not None else None
+        check(_lib().nys_unroll_create(ctx.h, op.h, pcs, C.byref(d), C.byref(h)), ctx.h)
+        self.h = h
+        self.ntaps = op._kernel.size if op.kind == "blur" else 0
+
+    def set_lambda(self, lam: float):
+        check(_lib().nys_unroll_set_lambda(self.h, lam), self.ctx.h)
+        self.lam = lam
+
+    def forward(self, y: torch.Tensor, out: torch.Tensor | None = None) -> torch.Tensor:
+        if out is None:
+            out = torch.empty((self.op.n1, self.op.n2), dtype=self.op.dtype, device=y.device)
+        check(_lib().nys_unroll_forward(self.h, _ptr(y.contiguous()), _ptr(out)), self.ctx.h)
+        return out
+
+    def backward(self, xbar: torch.Tensor):
+        """(d<xbar, x>/d lambda as a float64 0-d tensor, d<xbar, x>/dh as a
+        float64 (kh, kw) tensor or None) on the device."""
+        g = torch.empty(1 + self.ntaps, dtype=torch.float64, device=xbar.device)
+        check(_lib().nys_unroll_backward(self.h, _ptr(xbar.contiguous()), _ptr(g)), self.ctx.h)
+        dh = g[1:].reshape(self.op._kernel.shape) if self.ntaps else None
+        return g[0], dh
+
+    def close(self):
+        if getattr(self, "h", None):
+            _lib().nys_unroll_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def nys_gram(ctx: Context, A: torch.Tensor, B: torch.Tensor, path: int = 0) -> torch.Tensor:

@@ -232,6 +232,21 @@ int nys_op_destroy(nys_op* op) {
     return NYS_OK;
 }
 
+int nys_op_set_kernel(nys_op* op, const double* kernel, int kh, int kw) {
+    if (!op || !kernel) return fail(op ? op->ctx : nullptr, NYS_EINVAL, "null argument");
+    if (op->kind != NYS_OP_BLUR && op->kind != NYS_OP_BLUR_DECIM)
+        return fail(op->ctx, NYS_EINVAL, "nys_op_set_kernel needs a blur operator");
+    if (kh != op->kh || kw != op->kw) return fail(op->ctx, NYS_EINVAL, "kernel shape differs from the op's");
+    NYS_CK(op->ctx, cudaStreamSynchronize(op->ctx->stream));
+    void* bufs[] = {op->taps_fwd, op->taps_adj, op->taps_nrm, op->inter};
+    for (void* b : bufs)
+        if (b) cudaFree(b);
+    op->taps_fwd = op->taps_adj = op->taps_nrm = op->inter = nullptr;
+    op->chunk = 0;
+    op->h.assign(kernel, kernel + (size_t)kh * kw);
+    return blur_setup(op);
+}
+
 int nys_op_sizes(const nys_op* op, int64_t* N, int64_t* M) {
     if (!op) return fail(nullptr, NYS_EINVAL, "null op");
     if (N) *N = op->N;

@@ -1,6 +1,6 @@
 """Per-call timings of the library's hot entry points, and a small target for ncu.
 
-  python -m paper_2411_08178_gb300.profile_kernels [--case all|precond|normal|sketch|prox|iter]
+  python -m paper_2411_08178_gb300.profile_kernels [--case all|precond|normal|sketch|prox|iter|unroll]
         [--n 512] [--ell 200] [--reps 20] [--l2]
 
 Each case builds the 512 x 512 deblurring operator (25 x 25 Gaussian, sigma 4)
@@ -98,6 +98,17 @@ def main():
             ms = timed(lambda: sol.step(1), reps=args.reps)
             out.append(dict(case=f"pgd_step TV {name}", ms=ms))
             sol.close()
+    if "unroll" in cases:
+        # 50 unrolled preconditioned iterations (n_inner 20), checkpoint every 10:
+        # forward alone and forward + reverse pass (d/d lambda, d/d 25x25 kernel)
+        y = torch.rand(n, n, device=dev)
+        un = api.Unroll(ctx, op, 5e-4, 0.9, 50, n_inner=20, ckpt_every=10, pc=pc)
+        xb = torch.randn(n, n, device=dev)
+        ms_f = timed(lambda: un.forward(y), reps=2)
+        ms_fb = timed(lambda: (un.forward(y), un.backward(xb)), reps=2)
+        out.append(dict(case="unroll K=50 n_inner=20 ckpt=10 forward", ms=ms_f))
+        out.append(dict(case="unroll K=50 n_inner=20 ckpt=10 forward+backward", ms=ms_fb))
+        un.close()
     for o in out:
         print(json.dumps(o))
 
