@@ -8,10 +8,13 @@ sketch (Omega, Y, U) stored in bf16 and float64 core algebra.
 
 One step = one preconditioned solve to 1e-3 relative error: draw Omega, sketch
 Y = A^T A Omega, factor (Algorithm 1), estimate the step size, and run the
-k* WAPG iterations that reach ||x^k - x*|| <= 1e-3 ||x*|| (k* found in an
-untimed pass; x* from a long plain-APG run).  `value` is its wall time on the
-device (ms, lower is better); the plain APG time to the same accuracy
-(including its own step-size estimate) is reported beside it.
+k* WAPG iterations that reach an objective gap (F(x^k) - F*)/|F*| <= 1e-3
+(k* found in an untimed pass; F* from a long float64 plain-APG run of the
+same problem).  The float32 iterates are not resolved to 1e-3 in
+||x^k - x*||/||x*|| within the run, so that error is reported beside it.
+`value` is the step's wall time on the device (ms, lower is better); the
+plain APG time to the same criterion (including its own step-size estimate)
+is reported beside it.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl native|reference]
 
@@ -39,6 +42,11 @@ import workloads as WL  # noqa: E402
 EPS32 = 2.0 ** -23
 METRIC = "time to 1e-3 rel. error (Nyström-precond vs plain PGD), sketch ms, HBM GB/s"
 TARGET = 1e-3
+# DRAM bytes (read + write) of one dual step with cold caches, measured with ncu
+# (dram__bytes_read.sum + dram__bytes_write.sum of lt_utz_kernel, uc_vec_kernel
+# and dual_update_kernel at 512 x 512, 22 active bf16 columns); None until the
+# current kernels have been captured
+DUAL_STEP_TRAFFIC = None
 
 
 def dist_env():
@@ -169,7 +177,7 @@ class Native:
         self.solver_0.restart(True)
         self.solver_0.step(k)
 
-    def time_loop(self, fn, steps, warmup):
+    def time_loop(self, fn, steps, warmup, tag="timed"):
         torch = self.torch
         stream = torch.cuda.current_stream(self.dev)
         for _ in range(warmup):
@@ -180,7 +188,7 @@ class Native:
             torch.cuda.synchronize(self.dev)
             a = torch.cuda.Event(enable_timing=True)
             b = torch.cuda.Event(enable_timing=True)
-            torch.cuda.nvtx.range_push("timed")
+            torch.cuda.nvtx.range_push(tag)
             a.record(stream)
             fn()
             b.record(stream)
@@ -197,27 +205,53 @@ class Native:
         out = self.solver_p.x()
         self.x_host.copy_(out, non_blocking=True)
 
-    def precond_roofline(self, reps: int = 30):
+    def _events_ms(self, fn, reps):
         torch = self.torch
-        z = torch.randn(self.w.n * self.w.n, dtype=torch.float32, device=self.dev)
-        out = torch.empty_like(z)
         stream = torch.cuda.current_stream(self.dev)
         for _ in range(3):
-            self.api.precond_apply(self.ctx, self.pc, z, True, out)
+            fn()
         torch.cuda.synchronize(self.dev)
         a = torch.cuda.Event(enable_timing=True)
         b = torch.cuda.Event(enable_timing=True)
         a.record(stream)
         for _ in range(reps):
-            self.api.precond_apply(self.ctx, self.pc, z, True, out)
+            fn()
         b.record(stream)
         torch.cuda.synchronize(self.dev)
-        ms = a.elapsed_time(b) / reps
-        N, ell = self.w.n * self.w.n, self.w.ell
+        return a.elapsed_time(b) / reps
+
+    def precond_roofline(self, reps: int = 30):
+        """Standalone P^{-1} apply: (ms, algorithmic bytes)."""
+        torch = self.torch
+        z = torch.randn(self.w.n * self.w.n, dtype=torch.float32, device=self.dev)
+        out = torch.empty_like(z)
+        ms = self._events_ms(lambda: self.api.precond_apply(self.ctx, self.pc, z, True, out), reps)
+        N, ell = self.w.n * self.w.n, self.pc.ell_active
         ub = 2 if self.sd == torch.bfloat16 else 4
-        # algorithmic bytes: U read twice (U^T z and U c) + z read twice + out written
-        nbytes = 2 * N * ell * ub + 3 * N * 4
-        return ms, nbytes
+        # the active columns of U (d_i > 0) read twice (U^T z and U c) + z read
+        # twice + out written
+        return ms, 2 * N * ell * ub + 3 * N * 4
+
+    def dual_step_roofline(self, reps: int = 20):
+        """The P-metric TV prox as the solve runs it (n_inner dual steps of
+        lt_utz + uc_vec + dual_update, then the final x): (ms per dual step,
+        algorithmic bytes per dual step).  The call is timed with CUDA events
+        on the context's stream, right after the timed region."""
+        torch, w = self.torch, self.w
+        N = w.n * w.n
+        s = torch.rand(w.n, w.n, dtype=torch.float32, device=self.dev)
+        Q = torch.zeros(2, w.n, w.n, dtype=torch.float32, device=self.dev)
+        out = torch.empty_like(s)
+        lb = 0.9 * w.lam
+        ms = self._events_ms(lambda: self.api.prox_tv(self.ctx, self.pc, lb, w.n_inner, s, Q=Q, out=out), reps)
+        le, ub, f = self.pc.ell_active, (2 if self.sd == torch.bfloat16 else 4), 4
+        lt_utz = 2 * N * f + le * N * ub + N * f            # R in, U, g out
+        uc = le * N * ub + 2 * N * f + N * f                 # U, g and s in, x out
+        dual = N * f + 2 * 2 * N * f + 2 * 2 * N * f         # x in, R and Q in and out
+        copies = 3 * 2 * (2 * N * f)                         # the warm start in and out
+        total = w.n_inner * (lt_utz + uc + dual) + lt_utz + uc + copies
+        steps = w.n_inner + 1
+        return ms / steps, total / steps
 
 
 def run_native(args, w: WL.Workload):
@@ -239,21 +273,22 @@ def run_native(args, w: WL.Workload):
     k_p_run = k_p or kmax
     k_0_run = k_0 or kmax
     # sketch-only time (Algorithm 1 end to end)
-    sketch_ms = statistics.median(nb.time_loop(nb.sketch_factor, max(3, args.steps), 1))
+    sketch_ms = statistics.median(nb.time_loop(nb.sketch_factor, max(3, args.steps), 1, "timed_sketch"))
     clocks = ClockSampler(local)
     clocks.start()
     l0 = nb.ctx.launches()
     if world > 1:
         torch.distributed.barrier()
-    times_p = nb.time_loop(lambda: nb.solve_precond(k_p_run), args.steps, args.warmup)
+    times_p = nb.time_loop(lambda: nb.solve_precond(k_p_run), args.steps, args.warmup, "timed_precond")
     l1 = nb.ctx.launches()
-    times_0 = nb.time_loop(lambda: nb.solve_plain(k_0_run), args.steps, args.warmup)
+    times_0 = nb.time_loop(lambda: nb.solve_plain(k_0_run), args.steps, args.warmup, "timed_plain")
     clk = clocks.stop()
     if world > 1:
         torch.distributed.barrier()
     nb.x_host = torch.empty((w.n, w.n), dtype=torch.float32).pin_memory()
-    times_e2e = nb.time_loop(lambda: nb.e2e_step(k_p_run), args.steps, 1)
+    times_e2e = nb.time_loop(lambda: nb.e2e_step(k_p_run), args.steps, 1, "timed_e2e")
     pre_ms, pre_bytes = nb.precond_roofline()
+    step_ms, step_bytes = nb.dual_step_roofline()
     ms_p = statistics.mean(times_p)
     ms_0 = statistics.mean(times_0)
     ms_e = statistics.mean(times_e2e)
@@ -263,7 +298,8 @@ def run_native(args, w: WL.Workload):
         ms_p, ms_0, ms_e = [float(v) for v in t.cpu()]
     launches = (l1 - l0) // max(1, args.steps + args.warmup)
     peaks = load_peaks()
-    achieved = pre_bytes / (pre_ms * 1e-3) / 1e9
+    achieved = step_bytes / (step_ms * 1e-3) / 1e9
+    achieved_pinv = pre_bytes / (pre_ms * 1e-3) / 1e9
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = oracle_sample(w, k_p_run, seconds_hint=args.cpu_seconds)
@@ -286,10 +322,15 @@ def run_native(args, w: WL.Workload):
         "e2e": {"value": round(ms_e, 3), "unit": "ms", "h2d_bytes_per_step": w.n * w.n * 4,
                 "d2h_bytes_per_step": w.n * w.n * 4},
         "gpu_launches": int(launches),
-        "roofline": {"bound": "hbm", "kernel": "P^{-1} apply (utz_kernel + coef_kernel + uc_kernel)",
+        "roofline": {"bound": "hbm",
+                     "kernel": "P-metric TV dual step (lt_utz_kernel + uc_vec_kernel + dual_update_kernel)",
                      "achieved": round(achieved, 1), "peak": peaks["hbm_gbs"], "peak_source": peaks["src"],
-                     "unit": "GB/s", "frac": round(achieved / peaks["hbm_gbs"], 4), "traffic": None,
-                     "bytes_per_launch": pre_bytes, "ms_per_launch": round(pre_ms, 5)},
+                     "unit": "GB/s", "frac": round(achieved / peaks["hbm_gbs"], 4),
+                     "traffic": DUAL_STEP_TRAFFIC, "bytes_per_step": step_bytes, "ms_per_step": round(step_ms, 5),
+                     "active_columns": nb.pc.ell_active,
+                     "p_inverse_apply": {"achieved": round(achieved_pinv, 1), "bytes": pre_bytes,
+                                         "ms": round(pre_ms, 5),
+                                         "frac": round(achieved_pinv / peaks["hbm_gbs"], 4)}},
         "clocks": clk,
         "cpu_baseline": cpu,
         "setup_s": round(setup_s, 1),

@@ -161,6 +161,8 @@ typedef struct nys_precond {
     double s_last;       /* out: S_hat[ell-1]                              */
     double mu;           /* set by nys_precond_setup                       */
     int sqrt_shift;      /* set by nys_precond_setup                       */
+    int ell_active;      /* out (setup): columns with d_i > 0, the only
+                            ones P and P^{-1} read (d is non-increasing)   */
     void* priv;          /* library-owned; NULL before nys_factor          */
 } nys_precond;
 

@@ -33,7 +33,8 @@ class nys_op_desc(C.Structure):
 class nys_precond(C.Structure):
     _fields_ = [("U", C.c_void_p), ("S_hat", C.c_void_p), ("N", C.c_int64), ("ell", C.c_int),
                 ("dtype", C.c_int), ("v", C.c_double), ("chol_retries", C.c_int), ("s_first", C.c_double),
-                ("s_last", C.c_double), ("mu", C.c_double), ("sqrt_shift", C.c_int), ("priv", C.c_void_p)]
+                ("s_last", C.c_double), ("mu", C.c_double), ("sqrt_shift", C.c_int), ("ell_active", C.c_int),
+                ("priv", C.c_void_p)]
 
 
 class nys_prox_info(C.Structure):

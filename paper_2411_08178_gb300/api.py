@@ -232,6 +232,11 @@ class Precond:
     def chol_retries(self) -> int:
         return self.s.chol_retries
 
+    @property
+    def ell_active(self) -> int:
+        """Columns with d_i > 0 (the only ones P and P^{-1} read)."""
+        return self.s.ell_active
+
     def setup(self, mu: float = 0.0, sqrt_shift: bool = True):
         check(_lib().nys_precond_setup(self.ctx.h, C.byref(self.s), mu, int(sqrt_shift)), self.ctx.h)
 

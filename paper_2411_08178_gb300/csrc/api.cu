@@ -131,6 +131,14 @@ int nys_create(nys_ctx** out, int device, void* stream) {
     c->device = device;
     c->stream = (cudaStream_t)stream;
     cudaDeviceGetAttribute(&c->sm_count, cudaDevAttrMultiProcessorCount, device);
+    // completion counters of the last-CTA reductions (zero between launches)
+    e = cudaMalloc(&c->counters, 64 * sizeof(unsigned));
+    if (e == cudaSuccess) e = cudaMemset(c->counters, 0, 64 * sizeof(unsigned));
+    if (e != cudaSuccess) {
+        if (c->counters) cudaFree(c->counters);
+        delete c;
+        return cuda_fail(nullptr, e, "nys_create: counters");
+    }
     *out = c;
     return NYS_OK;
 }
@@ -140,6 +148,7 @@ int nys_destroy(nys_ctx* ctx) {
     cudaStreamSynchronize(ctx->stream);
     for (int i = 0; i < 12; ++i)
         if (ctx->slot_ptr[i]) cudaFree(ctx->slot_ptr[i]);
+    if (ctx->counters) cudaFree(ctx->counters);
     delete ctx;
     return NYS_OK;
 }
@@ -178,6 +187,10 @@ int nys_op_create(nys_ctx* ctx, const nys_op_desc* d, nys_op** out) {
     op->n1 = d->n1;
     op->n2 = d->n2;
     op->N = (int64_t)d->n1 * d->n2;
+    if (d->n1 <= 0 || d->n2 <= 0 || op->N >= (int64_t(1) << 31)) {
+        delete op;
+        return fail(ctx, NYS_EINVAL, "image size must be positive with fewer than 2^31 pixels");
+    }
     op->haar_levels = d->haar_levels;
     if (d->haar_levels < 0 || (d->haar_levels > 0 && ((d->n1 % (1 << d->haar_levels)) ||
                                                      (d->n2 % (1 << d->haar_levels))))) {

@@ -17,6 +17,7 @@
 //              M = diag(sqrt d) (I + Ubar^T Ubar)^{-1} diag(sqrt d), so that
 //              P^{-1} z = z - U M U^T z is the exact inverse of P z = z + U diag(d) U^T z.
 #include "internal.cuh"
+#include "vec.cuh"
 
 #include <cmath>
 #include <mutex>
@@ -172,56 +173,6 @@ __global__ void __launch_bounds__(256) uc_kernel(const TU* __restrict__ U, const
 // lane) and are sized to put several CTAs on every SM.
 constexpr int VCH = 2048;    // pixels per partial-sum chunk
 
-template <class T> struct Vec16;
-template <> struct Vec16<__nv_bfloat16> { static constexpr int n = 8; };
-template <> struct Vec16<float> { static constexpr int n = 4; };
-template <> struct Vec16<double> { static constexpr int n = 2; };
-
-// 16-byte loads unpacked in registers (bf16 -> f32 is a 16-bit shift)
-template <class TU, class TA, int V>
-__device__ __forceinline__ void load_vec(const TU* p, TA (&v)[V]);
-
-template <>
-__device__ __forceinline__ void load_vec<__nv_bfloat16, float, 8>(const __nv_bfloat16* p, float (&v)[8]) {
-    const uint4 r = __ldg(reinterpret_cast<const uint4*>(p));
-    const uint32_t w[4] = {r.x, r.y, r.z, r.w};
-#pragma unroll
-    for (int k = 0; k < 4; ++k) {
-        v[2 * k] = __uint_as_float(w[k] << 16);
-        v[2 * k + 1] = __uint_as_float(w[k] & 0xffff0000u);
-    }
-}
-template <>
-__device__ __forceinline__ void load_vec<float, float, 4>(const float* p, float (&v)[4]) {
-    const float4 r = __ldg(reinterpret_cast<const float4*>(p));
-    v[0] = r.x, v[1] = r.y, v[2] = r.z, v[3] = r.w;
-}
-template <>
-__device__ __forceinline__ void load_vec<double, double, 2>(const double* p, double (&v)[2]) {
-    const double2 r = __ldg(reinterpret_cast<const double2*>(p));
-    v[0] = r.x, v[1] = r.y;
-}
-
-// 128-bit shared-memory loads of V compute-type values (V * sizeof(TA) is a
-// multiple of 16 bytes)
-template <class TA, int V>
-__device__ __forceinline__ void lds_vec(const TA* p, TA (&v)[V]);
-template <>
-__device__ __forceinline__ void lds_vec<float, 8>(const float* p, float (&v)[8]) {
-    const float4 a = reinterpret_cast<const float4*>(p)[0], b = reinterpret_cast<const float4*>(p)[1];
-    v[0] = a.x, v[1] = a.y, v[2] = a.z, v[3] = a.w, v[4] = b.x, v[5] = b.y, v[6] = b.z, v[7] = b.w;
-}
-template <>
-__device__ __forceinline__ void lds_vec<float, 4>(const float* p, float (&v)[4]) {
-    const float4 a = reinterpret_cast<const float4*>(p)[0];
-    v[0] = a.x, v[1] = a.y, v[2] = a.z, v[3] = a.w;
-}
-template <>
-__device__ __forceinline__ void lds_vec<double, 2>(const double* p, double (&v)[2]) {
-    const double2 a = reinterpret_cast<const double2*>(p)[0];
-    v[0] = a.x, v[1] = a.y;
-}
-
 // grid (chunks, column groups): part[b][chunk][j] = sum_{i in chunk} U[j][i] z[i]
 template <class TU, class TZ, class TA>
 __global__ void __launch_bounds__(256) utz_vec_kernel(const TU* __restrict__ U, const TZ* __restrict__ z, int64_t N,
@@ -274,102 +225,6 @@ __global__ void __launch_bounds__(256) utz_vec_kernel(const TU* __restrict__ U, 
     }
 }
 
-// out = z + sign * U c: a CTA owns 32 V pixels; its 8 warps split the columns
-// and their partial sums meet in shared memory
-template <class TU, class TZ, class TA>
-__global__ void __launch_bounds__(256) uc_vec_kernel(const TU* __restrict__ U, const TZ* __restrict__ z, int64_t N,
-                                                     int ell, const TA* __restrict__ coef, TA sign,
-                                                     TZ* __restrict__ out) {
-    constexpr int V = Vec16<TU>::n;
-    constexpr int P = 32 * V;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    TA* c = reinterpret_cast<TA*>(smem_raw);
-    TA* red = c + ((ell + 3) & ~3);            // [8][P]
-    const int b = blockIdx.y;
-    for (int j = threadIdx.x; j < ell; j += blockDim.x) c[j] = coef[(size_t)b * ell + j];
-    __syncthreads();
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int64_t i = (int64_t)blockIdx.x * P + lane * V;
-    TA acc[V];
-#pragma unroll
-    for (int k = 0; k < V; ++k) acc[k] = TA(0);
-    if (i < N) {
-        int j = warp;
-        // four independent 16-byte loads in flight per lane
-        for (; j + 24 < ell; j += 32) {
-            TA u0[V], u1[V], u2[V], u3[V];
-            load_vec<TU, TA, V>(U + (size_t)j * N + i, u0);
-            load_vec<TU, TA, V>(U + (size_t)(j + 8) * N + i, u1);
-            load_vec<TU, TA, V>(U + (size_t)(j + 16) * N + i, u2);
-            load_vec<TU, TA, V>(U + (size_t)(j + 24) * N + i, u3);
-            const TA c0 = c[j], c1 = c[j + 8], c2 = c[j + 16], c3 = c[j + 24];
-#pragma unroll
-            for (int k = 0; k < V; ++k) acc[k] = fma(u3[k], c3, fma(u2[k], c2, fma(u1[k], c1, fma(u0[k], c0, acc[k]))));
-        }
-        for (; j < ell; j += 8) {
-            TA u[V];
-            load_vec<TU, TA, V>(U + (size_t)j * N + i, u);
-            const TA cj = c[j];
-#pragma unroll
-            for (int k = 0; k < V; ++k) acc[k] = fma(u[k], cj, acc[k]);
-        }
-    }
-#pragma unroll
-    for (int k = 0; k < V; ++k) red[warp * P + lane * V + k] = acc[k];
-    __syncthreads();
-    for (int p = threadIdx.x; p < P; p += blockDim.x) {
-        const int64_t ii = (int64_t)blockIdx.x * P + p;
-        if (ii >= N) continue;
-        TA s = TA(0);
-#pragma unroll
-        for (int w = 0; w < 8; ++w) s += red[w * P + p];
-        const size_t o = (size_t)b * N + ii;
-        stf(out + o, (TA)ldf(z + o) + sign * s);
-    }
-}
-
-// coef[b][r] = inverse ? sum_k M[r][k] w[k] : d[r] w[r] for r < le, with
-// w = sum over the chunk partials; every CTA rebuilds w (coalesced, eight
-// independent accumulators per thread) and then forms 32 coefficients.
-template <class TA, class TM>
-__global__ void __launch_bounds__(256) coef_vec_kernel(const TA* __restrict__ part, int nb, int le, int ldm,
-                                                       int inverse, const TM* __restrict__ M,
-                                                       const TM* __restrict__ d, TA* __restrict__ coef) {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    TA* w = reinterpret_cast<TA*>(smem_raw);
-    const int b = blockIdx.y;
-    const TA* pb = part + (size_t)b * nb * le;
-    for (int j = threadIdx.x; j < le; j += blockDim.x) {
-        TA acc[8];
-#pragma unroll
-        for (int q = 0; q < 8; ++q) acc[q] = TA(0);
-        int k = 0;
-        for (; k + 8 <= nb; k += 8) {
-#pragma unroll
-            for (int q = 0; q < 8; ++q) acc[q] += pb[(size_t)(k + q) * le + j];
-        }
-        for (; k < nb; ++k) acc[0] += pb[(size_t)k * le + j];
-        TA s = TA(0);
-#pragma unroll
-        for (int q = 0; q < 8; ++q) s += acc[q];
-        w[j] = s;
-    }
-    __syncthreads();
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int r0 = blockIdx.x * 32;
-    for (int r = r0 + warp; r < min(le, r0 + 32); r += 8) {
-        TA s;
-        if (inverse) {
-            s = TA(0);
-            for (int k = lane; k < le; k += 32) s = fma((TA)M[(size_t)r * ldm + k], w[k], s);
-            s = warp_sum(s);
-        } else {
-            s = (TA)d[r] * w[r];
-        }
-        if (lane == 0) coef[(size_t)b * le + r] = s;
-    }
-}
-
 template <class TU, class TZ, class TA>
 int precond_vec(nys_ctx* ctx, const nys_precond* pc, int inverse, const void* z, void* out, int batch) {
     constexpr int V = Vec16<TU>::n;
@@ -396,10 +251,10 @@ int precond_vec(nys_ctx* ctx, const nys_precond* pc, int inverse, const void* z,
                                                                           jper, part);
     NYS_LAUNCH_CK(ctx);
     if (sizeof(TA) == 8)
-        coef_vec_kernel<TA, double><<<dim3((ell + 31) / 32, batch), 256, ell * sizeof(TA), s>>>(
+        coef_vec_kernel<TA, double><<<dim3((ell + 31) / 32, batch), 256, (ell + 256) * sizeof(TA), s>>>(
             part, nchunk, ell, pc->ell, inverse, (const double*)pv->M64, (const double*)pv->d, coef);
     else
-        coef_vec_kernel<TA, float><<<dim3((ell + 31) / 32, batch), 256, ell * sizeof(TA), s>>>(
+        coef_vec_kernel<TA, float><<<dim3((ell + 31) / 32, batch), 256, (ell + 256) * sizeof(TA), s>>>(
             part, nchunk, ell, pc->ell, inverse, (const float*)pv->M32, (const float*)pv->d32, coef);
     NYS_LAUNCH_CK(ctx);
     constexpr int P = 32 * V;
@@ -492,6 +347,7 @@ int precond_setup_impl(nys_ctx* ctx, nys_precond* pc, double mu, int sqrt_shift)
     NYS_CK(ctx, cudaStreamSynchronize(s));
     if (h_info[3] != 0.0) return fail(ctx, NYS_ENONFINITE, "preconditioner: I + Ubar^T Ubar is not positive definite");
     pv->ell_eff = eff;
+    pc->ell_active = eff;
     pc->mu = mu;
     pc->sqrt_shift = sqrt_shift;
     return NYS_OK;

@@ -73,6 +73,7 @@ struct nys_ctx {
     cudaStreamAttrValue l2_window = {};   // access-policy window set by nys_l2_persist
     bool l2_window_set = false;
     std::string err;
+    unsigned* counters = nullptr;   // device, 64 completion counters (see vec.cuh)
     // independent growable scratch regions (see nys::scratch)
     void* slot_ptr[12] = {nullptr};
     size_t slot_bytes[12] = {0};
@@ -196,4 +197,8 @@ namespace nys {
 // not null the input is computed on the fly (used by the fused prox kernels).
 int precond_run(nys_ctx* ctx, const nys_precond* pc, int inverse, int dtype, const void* z,
                 void* out, int batch);
+// dual APG prox with the fused three-launch step (prox_fused.cu); returns
+// NYS_EINVAL without launching anything when the layout does not allow it
+int prox_dual_fused(nys_ctx* ctx, const nys_precond* pc, int reg, double lb, int n_inner, int dtype, int n1, int n2,
+                    const void* s, void* out, void* Q);
 }  // namespace nys

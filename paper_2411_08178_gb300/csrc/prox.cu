@@ -41,7 +41,8 @@ __global__ void lt_kernel(const T* __restrict__ Q, const T* __restrict__ base, t
     using TC = typename Comp<T>::type;
     const int64_t N = (int64_t)n1 * n2;
     for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < N; t += (int64_t)gridDim.x * blockDim.x) {
-        const int i = (int)(t / n2), j = (int)(t - (int64_t)i * n2);
+        int i, j;
+        pix_ij(t, n2, i, j);
         const TC g = lt_q<T, REG>(Q, i, j, n1, n2);
         out[t] = base ? (T)((TC)base[t] - lb * g) : (T)g;
     }
@@ -56,60 +57,6 @@ __global__ void axpy_kernel(const T* __restrict__ s, const T* __restrict__ pg, t
         x[t] = (T)((TC)s[t] - lb * (TC)pg[t]);
 }
 
-// Q' = Proj(R + step * L x); R <- Q' + beta (Q' - Qp); Qp <- Q'
-template <class T, int REG>
-__global__ void dual_update_kernel(const T* __restrict__ x, T* __restrict__ R, T* __restrict__ Qp,
-                                   typename Comp<T>::type step, typename Comp<T>::type beta, int n1, int n2) {
-    using TC = typename Comp<T>::type;
-    const int64_t N = (int64_t)n1 * n2;
-    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < N; t += (int64_t)gridDim.x * blockDim.x) {
-        const int i = (int)(t / n2), j = (int)(t - (int64_t)i * n2);
-        const TC xc = (TC)x[t];
-        if (REG == NYS_REG_TV) {
-            const TC v1 = xc - (TC)at(x, i - 1, j, n1, n2);
-            const TC v2 = xc - (TC)at(x, i, j - 1, n1, n2);
-            const TC n1v = fmin(TC(1), fmax(TC(-1), (TC)R[t] + step * v1));
-            const TC n2v = fmin(TC(1), fmax(TC(-1), (TC)R[t + N] + step * v2));
-            const TC o1 = (TC)Qp[t], o2 = (TC)Qp[t + N];
-            R[t] = (T)(n1v + beta * (n1v - o1));
-            R[t + N] = (T)(n2v + beta * (n2v - o2));
-            Qp[t] = (T)n1v;
-            Qp[t + N] = (T)n2v;
-        } else {
-            const TC v11 = (TC)at(x, i - 1, j, n1, n2) - TC(2) * xc + (TC)at(x, i + 1, j, n1, n2);
-            const TC v22 = (TC)at(x, i, j - 1, n1, n2) - TC(2) * xc + (TC)at(x, i, j + 1, n1, n2);
-            const TC v12 = TC(0.25) * ((TC)at(x, i + 1, j + 1, n1, n2) - (TC)at(x, i + 1, j - 1, n1, n2) -
-                                       (TC)at(x, i - 1, j + 1, n1, n2) + (TC)at(x, i - 1, j - 1, n1, n2));
-            const TC a = (TC)R[t] + step * v11;
-            const TC b = (TC)R[t + N] + step * v12;
-            const TC c = (TC)R[t + 2 * N] + step * v22;
-            // eigen-clip of [[a, b], [b, c]]
-            const TC m = TC(0.5) * (a + c), h = TC(0.5) * (a - c);
-            const TC r = sqrt(h * h + b * b);
-            const TC l1 = fmin(TC(1), fmax(TC(-1), m + r));
-            const TC l2 = fmin(TC(1), fmax(TC(-1), m - r));
-            const TC mp = TC(0.5) * (l1 + l2), dp = TC(0.5) * (l1 - l2);
-            TC pa, pb, pc;
-            if (r > TC(0)) {
-                pa = mp + dp * (h / r);
-                pb = dp * (b / r);
-                pc = mp - dp * (h / r);
-            } else {
-                pa = mp;
-                pb = TC(0);
-                pc = mp;
-            }
-            const TC oa = (TC)Qp[t], ob = (TC)Qp[t + N], oc = (TC)Qp[t + 2 * N];
-            R[t] = (T)(pa + beta * (pa - oa));
-            R[t + N] = (T)(pb + beta * (pb - ob));
-            R[t + 2 * N] = (T)(pc + beta * (pc - oc));
-            Qp[t] = (T)pa;
-            Qp[t + N] = (T)pb;
-            Qp[t + 2 * N] = (T)pc;
-        }
-    }
-}
-
 template <class T, int REG>
 int prox_dual_typed(nys_ctx* ctx, const nys_precond* pc, double lb, int n_inner, int n1, int n2, const T* s, T* out,
                     T* Q) {
@@ -118,6 +65,11 @@ int prox_dual_typed(nys_ctx* ctx, const nys_precond* pc, double lb, int n_inner,
     const double normL2 = REG == NYS_REG_TV ? 8.0 : 32.0;
     const int64_t N = (int64_t)n1 * n2;
     int st;
+    if (pc) {
+        // three launches per dual step (prox_fused.cu) where the layout allows
+        st = prox_dual_fused(ctx, pc, REG, lb, n_inner, sizeof(T) == 8 ? NYS_F64 : NYS_F32, n1, n2, s, out, Q);
+        if (st != NYS_EINVAL) return st;
+    }
     T* work = (T*)scratch(ctx, SLOT_PROX, ((size_t)2 * G * N + 2 * N) * sizeof(T), &st);
     if (st) return st;
     T* R = work;

@@ -1,0 +1,194 @@
+// Dual APG step of the P-metric prox (Sec. III-B) for a low-rank
+// preconditioner P = I + Ubar Ubar^T, P^{-1} z = z - U M U^T z over the active
+// columns of U (Eq. RYPreconditioner in Woodbury form).  One dual step
+//     x   = s - lb P^{-1} L^T R
+//     Q'  = Proj(R + step L x),  R <- Q' + beta (Q' - Q),  Q <- Q'
+// takes three launches instead of six:
+//   lt_utz   g = L^T R over a chunk of pixels (stencil from global R), written
+//            out and staged in shared memory, then the chunk's partial sums
+//            of U^T g (warps over the active columns, 16-byte loads of U);
+//            the last CTA to finish reduces the (column-major) partials and
+//            forms c = M w
+//   uc       x = s - lb (g - U c)   (vec.cuh, 16-byte loads of U)
+//   dual     L x and the dual update (stencil.cuh)
+// U is read twice per step, as in the unfused P^{-1} apply; the launches of
+// L^T R, the coefficient pass and x = s - lb (...) are folded away.
+#include "internal.cuh"
+#include "stencil.cuh"
+#include "vec.cuh"
+
+#include <algorithm>
+#include <cmath>
+
+namespace nys {
+namespace {
+
+constexpr int FCH = 1024;   // pixels per partial-sum chunk
+constexpr int COUNTER_PROX = 1;
+
+template <class TU, class T, class TA, class TM, int REG>
+__global__ void __launch_bounds__(256) lt_utz_kernel(const T* __restrict__ R, int n1, int n2,
+                                                     const TU* __restrict__ U, int le, int ldm,
+                                                     const TM* __restrict__ M, T* __restrict__ g,
+                                                     TA* __restrict__ part, TA* __restrict__ coef,
+                                                     unsigned* __restrict__ counter) {
+    constexpr int V = Vec16<TU>::n;
+    constexpr int PT = FCH / 256;   // pixels per thread in the stencil pass
+    __shared__ __align__(16) TA gs[FCH];
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    TA* sm = reinterpret_cast<TA*>(smem_raw);   // last CTA: w and (le <= 64) M
+    const int64_t N = (int64_t)n1 * n2;
+    const int64_t i0 = (int64_t)blockIdx.x * FCH;
+    TA v[PT];
+#pragma unroll
+    for (int q = 0; q < PT; ++q) {
+        const int64_t p = i0 + threadIdx.x + q * 256;
+        v[q] = TA(0);
+        if (p < N) {
+            int i, j;
+            pix_ij(p, n2, i, j);
+            v[q] = (TA)lt_q<T, REG>(R, i, j, n1, n2);
+        }
+    }
+#pragma unroll
+    for (int q = 0; q < PT; ++q) {
+        const int64_t p = i0 + threadIdx.x + q * 256;
+        if (p < N) g[p] = (T)v[q];
+        gs[threadIdx.x + q * 256] = v[q];
+    }
+    __syncthreads();
+    if (le == 0) return;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int cnt = (int)(N - i0 < (int64_t)FCH ? N - i0 : (int64_t)FCH);   // multiple of V
+    constexpr int T4 = FCH / (32 * V);
+    for (int j = warp; j < le; j += 16) {
+        // columns j and j + 8 together: twice the 16-byte loads in flight
+        const bool two = j + 8 < le;
+        const TU* u0 = U + (size_t)j * N + i0;
+        const TU* u1 = U + (size_t)(two ? j + 8 : j) * N + i0;
+        TA s0 = TA(0), s1 = TA(0);
+        if (cnt == FCH) {
+            TA a[T4][V], b[T4][V];
+#pragma unroll
+            for (int q = 0; q < T4; ++q) {
+                load_vec<TU, TA, V>(u0 + (q * 32 + lane) * V, a[q]);
+                load_vec<TU, TA, V>(u1 + (q * 32 + lane) * V, b[q]);
+            }
+#pragma unroll
+            for (int q = 0; q < T4; ++q) {
+                TA zv[V];
+                lds_vec<TA, V>(gs + (q * 32 + lane) * V, zv);
+#pragma unroll
+                for (int k = 0; k < V; ++k) {
+                    s0 = fma(a[q][k], zv[k], s0);
+                    s1 = fma(b[q][k], zv[k], s1);
+                }
+            }
+        } else {
+            for (int t = lane * V; t < cnt; t += 32 * V) {
+                TA a[V], b[V], zv[V];
+                load_vec<TU, TA, V>(u0 + t, a);
+                load_vec<TU, TA, V>(u1 + t, b);
+                lds_vec<TA, V>(gs + t, zv);
+#pragma unroll
+                for (int k = 0; k < V; ++k) {
+                    s0 = fma(a[k], zv[k], s0);
+                    s1 = fma(b[k], zv[k], s1);
+                }
+            }
+        }
+        s0 = warp_sum(s0);
+        s1 = warp_sum(s1);
+        if (lane == 0) {
+            part[(size_t)j * gridDim.x + blockIdx.x] = s0;
+            if (two) part[(size_t)(j + 8) * gridDim.x + blockIdx.x] = s1;
+        }
+    }
+    last_cta_coef_t<TA, TM>(part, le, ldm, M, coef, counter, sm);
+}
+
+template <class TU, class T, class TA, int REG>
+int fused_typed(nys_ctx* ctx, const nys_precond* pc, double lb, int n_inner, int n1, int n2, const T* s, T* out,
+                T* Q) {
+    using TM = typename std::conditional<sizeof(TA) == 8, double, float>::type;
+    constexpr int V = Vec16<TU>::n;
+    const nys_precond_priv* pv = (const nys_precond_priv*)pc->priv;
+    const int G = REG == NYS_REG_TV ? 2 : 3;
+    const double normL2 = REG == NYS_REG_TV ? 8.0 : 32.0;
+    const int64_t N = (int64_t)n1 * n2;
+    const int le = pv->ell_eff;
+    const int nchunk = (int)((N + FCH - 1) / FCH);
+    int st;
+    T* work = (T*)scratch(ctx, SLOT_PROX, ((size_t)2 * G * N + 2 * N) * sizeof(T), &st);
+    if (st) return st;
+    T* R = work;
+    T* Qp = R + G * N;
+    T* g = Qp + G * N;
+    T* x = g + N;
+    TA* part = (TA*)scratch(ctx, SLOT_PRECOND, ((size_t)nchunk * std::max(le, 1) + std::max(le, 1)) * sizeof(TA), &st);
+    if (st) return st;
+    TA* coef = part + (size_t)nchunk * std::max(le, 1);
+    cudaStream_t sm = ctx->stream;
+    NYS_CK(ctx, cudaMemcpyAsync(R, Q, sizeof(T) * G * N, cudaMemcpyDeviceToDevice, sm));
+    NYS_CK(ctx, cudaMemcpyAsync(Qp, Q, sizeof(T) * G * N, cudaMemcpyDeviceToDevice, sm));
+    const TM* M = sizeof(TA) == 8 ? (const TM*)pv->M64 : (const TM*)pv->M32;
+    const size_t lsm = ((size_t)le + (le <= 64 ? (size_t)le * le : 0)) * sizeof(TA) + 16;
+    constexpr int P = 32 * V;
+    const size_t usm = (((size_t)le + 3) & ~size_t(3)) * sizeof(TA) + (size_t)8 * P * sizeof(TA);
+    const int ug = (int)((N + P - 1) / P);
+    const int dg = (int)std::min<int64_t>((N + 255) / 256, (int64_t)ctx->sm_count * 8);
+    const TA step = (TA)(1.0 / (lb * normL2));
+    unsigned* counter = ctx->counters + COUNTER_PROX;
+    // x (or out) = s - lb P^{-1} L^T Rin
+    auto xfn = [&](const T* Rin, T* dst) -> int {
+        lt_utz_kernel<TU, T, TA, TM, REG><<<nchunk, 256, lsm, sm>>>(Rin, n1, n2, (const TU*)pc->U, le, pc->ell, M, g,
+                                                                      part, coef, counter);
+        NYS_LAUNCH_CK(ctx);
+        uc_vec_kernel<TU, T, TA><<<dim3(ug, 1), 256, usm, sm>>>((const TU*)pc->U, g, N, le, coef, TA(-1), dst, s,
+                                                                (TA)(-lb));
+        NYS_LAUNCH_CK(ctx);
+        return NYS_OK;
+    };
+    double t = 1.0;
+    for (int k = 0; k < n_inner; ++k) {
+        if ((st = xfn(R, x))) return st;
+        const double tn = 0.5 * (1.0 + std::sqrt(1.0 + 4.0 * t * t));
+        const double beta = (t - 1.0) / tn;
+        t = tn;
+        dual_update_kernel<T, REG><<<dg, 256, 0, sm>>>(x, R, Qp, step, (TA)beta, n1, n2);
+        NYS_LAUNCH_CK(ctx);
+    }
+    NYS_CK(ctx, cudaMemcpyAsync(Q, Qp, sizeof(T) * G * N, cudaMemcpyDeviceToDevice, sm));
+    return xfn(Qp, out);
+}
+
+}  // namespace
+
+// fused prox for a set-up low-rank P; NYS_EINVAL (nothing launched) when the
+// layout does not allow it, so the caller can take the unfused path
+int prox_dual_fused(nys_ctx* ctx, const nys_precond* pc, int reg, double lb, int n_inner, int dtype, int n1, int n2,
+                    const void* s, void* out, void* Q) {
+    if (!pc || !pc->priv) return NYS_EINVAL;
+    const nys_precond_priv* pv = (const nys_precond_priv*)pc->priv;
+    const int64_t N = (int64_t)n1 * n2;
+    const int V = pc->dtype == NYS_BF16 ? 8 : (pc->dtype == NYS_F32 ? 4 : 2);
+    const bool aligned = (((uintptr_t)pc->U | (uintptr_t)s | (uintptr_t)out) & 15) == 0;
+    if (N % V || N % 4 || !aligned || pv->ell_eff > 4096) return NYS_EINVAL;
+    auto go = [&](auto* tu, auto* tt, auto* ta) -> int {
+        using TU = std::remove_pointer_t<decltype(tu)>;
+        using T = std::remove_pointer_t<decltype(tt)>;
+        using TA = std::remove_pointer_t<decltype(ta)>;
+        if (reg == NYS_REG_TV)
+            return fused_typed<TU, T, TA, NYS_REG_TV>(ctx, pc, lb, n_inner, n1, n2, (const T*)s, (T*)out, (T*)Q);
+        return fused_typed<TU, T, TA, NYS_REG_HS>(ctx, pc, lb, n_inner, n1, n2, (const T*)s, (T*)out, (T*)Q);
+    };
+    if (dtype == NYS_F64) {
+        if (pc->dtype != NYS_F64) return NYS_EINVAL;
+        return go((double*)nullptr, (double*)nullptr, (double*)nullptr);
+    }
+    if (pc->dtype == NYS_BF16) return go((__nv_bfloat16*)nullptr, (float*)nullptr, (float*)nullptr);
+    if (pc->dtype == NYS_F32) return go((float*)nullptr, (float*)nullptr, (float*)nullptr);
+    return NYS_EINVAL;
+}
+
+}  // namespace nys

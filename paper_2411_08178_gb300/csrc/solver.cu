@@ -44,6 +44,7 @@ struct nys_solver {
     void *tM = nullptr, *tN = nullptr, *Q = nullptr;
     double* gamma = nullptr;
     double* pw = nullptr;     // [0] power-iteration norm, [2], [3]: t slots by parity
+    double* npart = nullptr;  // per-CTA partial sums of the power-iteration norm
     double alpha = 0.0;
     int parity = 0;
     int k = 0;
@@ -98,20 +99,33 @@ __global__ void momentum_kernel(const T* __restrict__ xn, const T* __restrict__ 
     }
 }
 
-// power iteration helpers: out[0] = ||w||, w /= ||w||
+// power iteration helpers: part[b] = block b's share of ||w||^2, then every
+// CTA sums the partials in the same order, w /= ||w|| and out[0] = ||w||
 template <class T>
-__global__ void norm_scale_kernel(T* __restrict__ w, int64_t n, double* __restrict__ out) {
+__global__ void __launch_bounds__(256) sumsq_part_kernel(const T* __restrict__ w, int64_t n, double* __restrict__ part) {
     __shared__ double sh[32];
     double s = 0.0;
-    for (int64_t i = threadIdx.x; i < n; i += blockDim.x) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
         const double v = (double)w[i];
         s += v * v;
     }
     s = block_sum(s, sh);
+    if (threadIdx.x == 0) part[blockIdx.x] = s;
+}
+
+template <class T>
+__global__ void __launch_bounds__(256) scale_by_norm_kernel(T* __restrict__ w, int64_t n,
+                                                            const double* __restrict__ part, int np,
+                                                            double* __restrict__ out) {
+    __shared__ double sh[32];
+    double s = 0.0;
+    for (int t = threadIdx.x; t < np; t += blockDim.x) s += part[t];
+    s = block_sum(s, sh);
     const double nr = sqrt(s);
-    if (threadIdx.x == 0) out[0] = nr;
+    if (blockIdx.x == 0 && threadIdx.x == 0) out[0] = nr;
     const double inv = nr > 0.0 ? 1.0 / nr : 0.0;
-    for (int64_t i = threadIdx.x; i < n; i += blockDim.x) w[i] = (T)((double)w[i] * inv);
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        w[i] = (T)((double)w[i] * inv);
 }
 
 // Gaussian start vector of the power iteration: splitmix64 (Steele, Lea and
@@ -327,15 +341,21 @@ int estimate_alpha(nys_solver* S) {
     T* w = (T*)S->u;
     gauss_init_kernel<T><<<grid_for(ctx, S->N), 256, 0, s>>>(z, S->N, S->d.power_seed);
     NYS_LAUNCH_CK(ctx);
-    norm_scale_kernel<T><<<1, 1024, 0, s>>>(z, S->N, S->pw);
-    NYS_LAUNCH_CK(ctx);
-    const int iters = S->d.power_iters > 0 ? S->d.power_iters : 50;
+    const int gN = grid_for(ctx, S->N);
+    auto normalise = [&](T* v) -> int {
+        sumsq_part_kernel<T><<<gN, 256, 0, s>>>(v, S->N, S->npart);
+        NYS_LAUNCH_CK(ctx);
+        scale_by_norm_kernel<T><<<gN, 256, 0, s>>>(v, S->N, S->npart, gN, S->pw);
+        NYS_LAUNCH_CK(ctx);
+        return NYS_OK;
+    };
     int st;
+    if ((st = normalise(z))) return st;
+    const int iters = S->d.power_iters > 0 ? S->d.power_iters : 50;
     for (int it = 0; it < iters; ++it) {
         if ((st = phi_apply<T>(S, z, w))) return st;
         if (S->pc && (st = precond_run(ctx, S->pc, 1, S->dt, w, w, 1))) return st;
-        norm_scale_kernel<T><<<1, 1024, 0, s>>>(w, S->N, S->pw);
-        NYS_LAUNCH_CK(ctx);
+        if ((st = normalise(w))) return st;
         std::swap(z, w);
     }
     double lam = 0.0;
@@ -386,7 +406,8 @@ int create_typed(nys_solver* S, const void* y) {
     const size_t es = sizeof(T);
     const int ell = S->pc ? S->pc->ell : 0;
     auto al = [](size_t v) { return (v + 255) & ~size_t(255); };
-    const size_t total = al(M * es) * 2 + al(N * es) * 7 + al((size_t)S->G * N * es) + al((ell + 1) * 8) + 256;
+    const size_t total = al(M * es) * 2 + al(N * es) * 7 + al((size_t)S->G * N * es) + al((ell + 1) * 8) + 256 +
+                         al((size_t)ctx->sm_count * 8 * sizeof(double));
     NYS_CK(ctx, cudaMalloc(&S->mem, total));
     char* p = (char*)S->mem;
     auto take = [&](size_t n) {
@@ -406,6 +427,7 @@ int create_typed(nys_solver* S, const void* y) {
     S->Q = S->G ? take((size_t)S->G * N * es) : nullptr;
     S->gamma = (double*)take((ell + 1) * 8);
     S->pw = (double*)take(256);
+    S->npart = (double*)take((size_t)ctx->sm_count * 8 * sizeof(double));
     NYS_CK(ctx, cudaStreamCreateWithFlags(&S->gs, cudaStreamNonBlocking));
     NYS_CK(ctx, cudaEventCreateWithFlags(&S->ev_in, cudaEventDisableTiming));
     NYS_CK(ctx, cudaEventCreateWithFlags(&S->ev_out, cudaEventDisableTiming));

@@ -12,26 +12,119 @@ __device__ __forceinline__ T at(const T* p, int i, int j, int n1, int n2) {
     return p[(size_t)pmod(i, n1) * n2 + pmod(j, n2)];
 }
 
+__device__ __forceinline__ int wrap_dec(int i, int n) { return i == 0 ? n - 1 : i - 1; }
+__device__ __forceinline__ int wrap_inc(int i, int n) { return i + 1 == n ? 0 : i + 1; }
+// row and column of flat pixel t (images hold fewer than 2^31 pixels)
+__device__ __forceinline__ void pix_ij(int64_t t, int n2, int& i, int& j) {
+    const unsigned u = (unsigned)t;
+    i = (int)(u / (unsigned)n2);
+    j = (int)(u - (unsigned)i * (unsigned)n2);
+}
+
 // L^T Q at pixel (i, j)
 template <class T, int REG>
 __device__ __forceinline__ typename Comp<T>::type lt_q(const T* __restrict__ Q, int i, int j, int n1, int n2) {
     using TC = typename Comp<T>::type;
     const size_t N = (size_t)n1 * n2;
+    const size_t r0 = (size_t)i * n2;
+    const int jp = wrap_inc(j, n2);
+    const size_t rp = (size_t)wrap_inc(i, n1) * n2;
     if (REG == NYS_REG_TV) {
         const T* q1 = Q;
         const T* q2 = Q + N;
-        return (TC)at(q1, i, j, n1, n2) - (TC)at(q1, i + 1, j, n1, n2) + (TC)at(q2, i, j, n1, n2) -
-               (TC)at(q2, i, j + 1, n1, n2);
+        return (TC)q1[r0 + j] - (TC)q1[rp + j] + (TC)q2[r0 + j] - (TC)q2[r0 + jp];
     } else {
         const T* q11 = Q;
         const T* q12 = Q + N;
         const T* q22 = Q + 2 * N;
-        const TC a11 = (TC)at(q11, i - 1, j, n1, n2) - TC(2) * (TC)at(q11, i, j, n1, n2) + (TC)at(q11, i + 1, j, n1, n2);
-        const TC a22 = (TC)at(q22, i, j - 1, n1, n2) - TC(2) * (TC)at(q22, i, j, n1, n2) + (TC)at(q22, i, j + 1, n1, n2);
-        const TC a12 = TC(0.25) * ((TC)at(q12, i + 1, j + 1, n1, n2) - (TC)at(q12, i + 1, j - 1, n1, n2) -
-                                   (TC)at(q12, i - 1, j + 1, n1, n2) + (TC)at(q12, i - 1, j - 1, n1, n2));
+        const int jm = wrap_dec(j, n2);
+        const size_t rm = (size_t)wrap_dec(i, n1) * n2;
+        const TC a11 = (TC)q11[rm + j] - TC(2) * (TC)q11[r0 + j] + (TC)q11[rp + j];
+        const TC a22 = (TC)q22[r0 + jm] - TC(2) * (TC)q22[r0 + j] + (TC)q22[r0 + jp];
+        const TC a12 = TC(0.25) * ((TC)q12[rp + jp] - (TC)q12[rp + jm] - (TC)q12[rm + jp] + (TC)q12[rm + jm]);
         return a11 + TC(2) * a12 + a22;
     }
 }
+
+// One APG step of the dual at pixel t (components at t, t + N, t + 2N) given
+// L x there (2 components for TV, (v11, v12, v22) for the Hessian):
+// Q' = Proj(R + step L x), R <- Q' + beta (Q' - Qp), Qp <- Q'.  Proj clips to
+// [-1, 1] (TV) or clips the eigenvalues of the symmetric 2 x 2 block (HS).
+template <class T, int REG>
+__device__ __forceinline__ void dual_pixel(const typename Comp<T>::type* Lx, T* __restrict__ R, T* __restrict__ Qp,
+                                           int64_t t, int64_t N, typename Comp<T>::type step,
+                                           typename Comp<T>::type beta) {
+    using TC = typename Comp<T>::type;
+    if (REG == NYS_REG_TV) {
+#pragma unroll
+        for (int c = 0; c < 2; ++c) {
+            const int64_t e = t + c * N;
+            const TC q = fmin(TC(1), fmax(TC(-1), (TC)R[e] + step * Lx[c]));
+            const TC o = (TC)Qp[e];
+            R[e] = (T)(q + beta * (q - o));
+            Qp[e] = (T)q;
+        }
+    } else {
+        const TC a = (TC)R[t] + step * Lx[0];
+        const TC b = (TC)R[t + N] + step * Lx[1];
+        const TC c = (TC)R[t + 2 * N] + step * Lx[2];
+        // eigen-clip of [[a, b], [b, c]]
+        const TC m = TC(0.5) * (a + c), h = TC(0.5) * (a - c);
+        const TC r = sqrt(h * h + b * b);
+        const TC l1 = fmin(TC(1), fmax(TC(-1), m + r));
+        const TC l2 = fmin(TC(1), fmax(TC(-1), m - r));
+        const TC mp = TC(0.5) * (l1 + l2), dp = TC(0.5) * (l1 - l2);
+        TC pa, pb, pc;
+        if (r > TC(0)) {
+            pa = mp + dp * (h / r);
+            pb = dp * (b / r);
+            pc = mp - dp * (h / r);
+        } else {
+            pa = mp;
+            pb = TC(0);
+            pc = mp;
+        }
+        const TC oa = (TC)Qp[t], ob = (TC)Qp[t + N], oc = (TC)Qp[t + 2 * N];
+        R[t] = (T)(pa + beta * (pa - oa));
+        R[t + N] = (T)(pb + beta * (pb - ob));
+        R[t + 2 * N] = (T)(pc + beta * (pc - oc));
+        Qp[t] = (T)pa;
+        Qp[t + N] = (T)pb;
+        Qp[t + 2 * N] = (T)pc;
+    }
+}
+
+namespace {
+
+// Q' = Proj(R + step * L x); R <- Q' + beta (Q' - Qp); Qp <- Q' over the image
+// (x read from global memory with its periodic neighbours)
+template <class T, int REG>
+__global__ void dual_update_kernel(const T* __restrict__ x, T* __restrict__ R, T* __restrict__ Qp,
+                                   typename Comp<T>::type step, typename Comp<T>::type beta, int n1, int n2) {
+    using TC = typename Comp<T>::type;
+    const int64_t N = (int64_t)n1 * n2;
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < N; t += (int64_t)gridDim.x * blockDim.x) {
+        int i, j;
+        pix_ij(t, n2, i, j);
+        const size_t r0 = (size_t)i * n2, rm = (size_t)wrap_dec(i, n1) * n2;
+        const int jm = wrap_dec(j, n2);
+        const TC xc = (TC)x[t];
+        TC Lx[3];
+        if (REG == NYS_REG_TV) {
+            Lx[0] = xc - (TC)x[rm + j];
+            Lx[1] = xc - (TC)x[r0 + jm];
+            Lx[2] = TC(0);
+        } else {
+            const size_t rp = (size_t)wrap_inc(i, n1) * n2;
+            const int jp = wrap_inc(j, n2);
+            Lx[0] = (TC)x[rm + j] - TC(2) * xc + (TC)x[rp + j];
+            Lx[2] = (TC)x[r0 + jm] - TC(2) * xc + (TC)x[r0 + jp];
+            Lx[1] = TC(0.25) * ((TC)x[rp + jp] - (TC)x[rp + jm] - (TC)x[rm + jp] + (TC)x[rm + jm]);
+        }
+        dual_pixel<T, REG>(Lx, R, Qp, t, N, step, beta);
+    }
+}
+
+}  // namespace
 
 }  // namespace nys

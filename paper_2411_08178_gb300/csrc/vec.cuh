@@ -1,0 +1,298 @@
+// Vectorised access helpers and the coefficient pass of the low-rank
+// P / P^{-1} apply (Eq. RYPreconditioner in Woodbury form), shared by the
+// standalone apply and the fused prox kernels.
+#pragma once
+
+#include "internal.cuh"
+
+namespace nys {
+namespace {
+
+template <class T> struct Vec16;
+template <> struct Vec16<__nv_bfloat16> { static constexpr int n = 8; };
+template <> struct Vec16<float> { static constexpr int n = 4; };
+template <> struct Vec16<double> { static constexpr int n = 2; };
+
+// 16-byte loads unpacked in registers (bf16 -> f32 is a 16-bit shift)
+template <class TU, class TA, int V>
+__device__ __forceinline__ void load_vec(const TU* p, TA (&v)[V]);
+
+template <>
+__device__ __forceinline__ void load_vec<__nv_bfloat16, float, 8>(const __nv_bfloat16* p, float (&v)[8]) {
+    const uint4 r = __ldg(reinterpret_cast<const uint4*>(p));
+    const uint32_t w[4] = {r.x, r.y, r.z, r.w};
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        v[2 * k] = __uint_as_float(w[k] << 16);
+        v[2 * k + 1] = __uint_as_float(w[k] & 0xffff0000u);
+    }
+}
+template <>
+__device__ __forceinline__ void load_vec<float, float, 4>(const float* p, float (&v)[4]) {
+    const float4 r = __ldg(reinterpret_cast<const float4*>(p));
+    v[0] = r.x, v[1] = r.y, v[2] = r.z, v[3] = r.w;
+}
+template <>
+__device__ __forceinline__ void load_vec<double, double, 2>(const double* p, double (&v)[2]) {
+    const double2 r = __ldg(reinterpret_cast<const double2*>(p));
+    v[0] = r.x, v[1] = r.y;
+}
+
+// 128-bit shared-memory loads of V compute-type values (V * sizeof(TA) is a
+// multiple of 16 bytes)
+template <class TA, int V>
+__device__ __forceinline__ void lds_vec(const TA* p, TA (&v)[V]);
+template <>
+__device__ __forceinline__ void lds_vec<float, 8>(const float* p, float (&v)[8]) {
+    const float4 a = reinterpret_cast<const float4*>(p)[0], b = reinterpret_cast<const float4*>(p)[1];
+    v[0] = a.x, v[1] = a.y, v[2] = a.z, v[3] = a.w, v[4] = b.x, v[5] = b.y, v[6] = b.z, v[7] = b.w;
+}
+template <>
+__device__ __forceinline__ void lds_vec<float, 4>(const float* p, float (&v)[4]) {
+    const float4 a = reinterpret_cast<const float4*>(p)[0];
+    v[0] = a.x, v[1] = a.y, v[2] = a.z, v[3] = a.w;
+}
+template <>
+__device__ __forceinline__ void lds_vec<double, 2>(const double* p, double (&v)[2]) {
+    const double2 a = reinterpret_cast<const double2*>(p)[0];
+    v[0] = a.x, v[1] = a.y;
+}
+
+// w[j] = sum over the nb chunk partials part[c][j] (j < le), in a fixed order,
+// by all threads of the CTA: thread t sums column t % le over the chunks
+// c = t / le (mod blockDim / le), four loads in flight, and the groups meet in
+// shared memory.  red needs blockDim.x entries.  Ends with __syncthreads().
+template <class TA>
+__device__ __forceinline__ void reduce_partials(const TA* __restrict__ part, int nb, int le, TA* w, TA* red) {
+    const int nt = blockDim.x, t = threadIdx.x;
+    if (le <= nt) {
+        const int ng = nt / le;
+        TA acc = TA(0);
+        if (t < ng * le) {
+            const int j = t % le, grp = t / le;
+            TA a[8];
+#pragma unroll
+            for (int q = 0; q < 8; ++q) a[q] = TA(0);
+            int c = grp;
+            for (; c + 7 * ng < nb; c += 8 * ng) {
+#pragma unroll
+                for (int q = 0; q < 8; ++q) a[q] += __ldcg(part + (size_t)(c + q * ng) * le + j);
+            }
+            for (; c < nb; c += ng) a[0] += __ldcg(part + (size_t)c * le + j);
+            acc = ((a[0] + a[1]) + (a[2] + a[3])) + ((a[4] + a[5]) + (a[6] + a[7]));
+        }
+        red[t] = acc;
+        __syncthreads();
+        if (t < le) {
+            TA s = TA(0);
+            for (int g = 0; g < ng; ++g) s += red[g * le + t];
+            w[t] = s;
+        }
+    } else {
+        for (int j = t; j < le; j += nt) {
+            TA a0 = TA(0), a1 = TA(0), a2 = TA(0), a3 = TA(0);
+            int c = 0;
+            for (; c + 4 <= nb; c += 4) {
+                a0 += __ldcg(part + (size_t)c * le + j);
+                a1 += __ldcg(part + (size_t)(c + 1) * le + j);
+                a2 += __ldcg(part + (size_t)(c + 2) * le + j);
+                a3 += __ldcg(part + (size_t)(c + 3) * le + j);
+            }
+            for (; c < nb; ++c) a0 += __ldcg(part + (size_t)c * le + j);
+            w[j] = (a0 + a1) + (a2 + a3);
+        }
+    }
+    __syncthreads();
+}
+
+// coef[r] = inverse ? sum_k M[r][k] w[k] : d[r] w[r] for r in [r0, r1), one
+// warp per row
+template <class TA, class TM>
+__device__ __forceinline__ void coef_rows(const TA* w, int le, int ldm, int inverse, const TM* __restrict__ M,
+                                          const TM* __restrict__ d, int r0, int r1, TA* __restrict__ coef) {
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+    for (int r = r0 + warp; r < r1; r += nw) {
+        TA s;
+        if (inverse) {
+            s = TA(0);
+            for (int k = lane; k < le; k += 32) s = fma((TA)M[(size_t)r * ldm + k], w[k], s);
+            s = warp_sum(s);
+        } else {
+            s = (TA)d[r] * w[r];
+        }
+        if (lane == 0) coef[r] = s;
+    }
+}
+
+// coef[b][r] for the 32 rows r of this CTA (batch b = blockIdx.y); every CTA
+// rebuilds w.  Dynamic shared memory: (le + blockDim.x) TA.
+template <class TA, class TM>
+__global__ void __launch_bounds__(256) coef_vec_kernel(const TA* __restrict__ part, int nb, int le, int ldm,
+                                                       int inverse, const TM* __restrict__ M,
+                                                       const TM* __restrict__ d, TA* __restrict__ coef) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    TA* w = reinterpret_cast<TA*>(smem_raw);
+    TA* red = w + le;
+    const int b = blockIdx.y;
+    reduce_partials<TA>(part + (size_t)b * nb * le, nb, le, w, red);
+    const int r0 = blockIdx.x * 32;
+    coef_rows<TA, TM>(w, le, ldm, inverse, M, d, r0, min(le, r0 + 32), coef + (size_t)b * le);
+}
+
+// w[j] = sum_c partT[j * nb + c] (column-major partials: column j's chunk sums
+// are contiguous), one warp per column, all of a warp's columns loaded before
+// they are summed (four at a time), fixed order.  Ends with __syncthreads().
+template <class TA>
+__device__ __forceinline__ void reduce_partials_t(const TA* __restrict__ partT, int nb, int le, TA* w) {
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+    for (int j0 = warp; j0 < le; j0 += 4 * nw) {
+        TA acc[4] = {TA(0), TA(0), TA(0), TA(0)};
+        for (int c0 = 0; c0 < nb; c0 += 32 * 8) {
+            TA v[4][8];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const int j = j0 + q * nw;
+#pragma unroll
+                for (int r = 0; r < 8; ++r) {
+                    const int c = c0 + r * 32 + lane;
+                    v[q][r] = (j < le && c < nb) ? __ldcg(partT + (size_t)j * nb + c) : TA(0);
+                }
+            }
+#pragma unroll
+            for (int q = 0; q < 4; ++q)
+#pragma unroll
+                for (int r = 0; r < 8; ++r) acc[q] += v[q][r];
+        }
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const TA sq = warp_sum(acc[q]);
+            const int j = j0 + q * nw;
+            if (lane == 0 && j < le) w[j] = sq;
+        }
+    }
+    __syncthreads();
+}
+
+// End of a 1-D partial-sum pass whose CTAs wrote column-major partials
+// partT[j * gridDim.x + blockIdx.x]: the last CTA to arrive (counted on
+// *counter, zero before the launch and reset here) reduces them and writes
+// coef = M w (one thread per row).  No CTA waits for another.  sm: le TA,
+// plus le * le TA when le <= 64 (M is staged in shared memory).
+template <class TA, class TM>
+__device__ __forceinline__ void last_cta_coef_t(const TA* partT, int le, int ldm, const TM* __restrict__ M,
+                                                TA* __restrict__ coef, unsigned* counter, TA* sm) {
+    __shared__ unsigned is_last;
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) is_last = atomicAdd(counter, 1u) == gridDim.x - 1;
+    __syncthreads();
+    if (!is_last) return;
+    __threadfence();
+    reduce_partials_t<TA>(partT, gridDim.x, le, sm);
+    if (le <= 64) {
+        // stage the le x le block of M (coalesced, one round of loads)
+        TA* Ms = sm + le;
+        for (int e = threadIdx.x; e < le * le; e += blockDim.x) Ms[e] = (TA)M[(size_t)(e / le) * ldm + e % le];
+        __syncthreads();
+        for (int r = threadIdx.x; r < le; r += blockDim.x) {
+            TA a = TA(0);
+            for (int k = 0; k < le; ++k) a = fma(Ms[r * le + k], sm[k], a);
+            coef[r] = a;
+        }
+    } else {
+        for (int r = threadIdx.x; r < le; r += blockDim.x) {
+            const TM* mr = M + (size_t)r * ldm;
+            TA a[4] = {TA(0), TA(0), TA(0), TA(0)};
+            int k = 0;
+            for (; k + 4 <= le; k += 4) {
+#pragma unroll
+                for (int q = 0; q < 4; ++q) a[q] = fma((TA)mr[k + q], sm[k + q], a[q]);
+            }
+            for (; k < le; ++k) a[0] = fma((TA)mr[k], sm[k], a[0]);
+            coef[r] = (a[0] + a[1]) + (a[2] + a[3]);
+        }
+    }
+    if (threadIdx.x == 0) *counter = 0u;
+}
+
+// End of a 1-D partial-sum pass: each CTA has written its row of `part`; the
+// last CTA to arrive (counted on *counter, which is zero before the launch
+// and reset here) reduces all rows and writes coef.  No CTA waits for
+// another.  sm: (le + blockDim.x) TA of shared memory.
+template <class TA, class TM>
+__device__ __forceinline__ void last_cta_coef(const TA* part, int nb, int le, int ldm, int inverse,
+                                              const TM* __restrict__ M, const TM* __restrict__ d,
+                                              TA* __restrict__ coef, unsigned* counter, TA* sm) {
+    __shared__ unsigned is_last;
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) is_last = atomicAdd(counter, 1u) == gridDim.x - 1;
+    __syncthreads();
+    if (!is_last) return;
+    __threadfence();
+    reduce_partials<TA>(part, nb, le, sm, sm + le);
+    coef_rows<TA, TM>(sm, le, ldm, inverse, M, d, 0, le, coef);
+    if (threadIdx.x == 0) *counter = 0u;
+}
+
+// out = z + sign * U c, or with base: out = base + scale (z + sign U c).  A CTA
+// owns 32 V pixels; its 8 warps split the columns and their partial sums meet
+// in shared memory
+template <class TU, class TZ, class TA>
+__global__ void __launch_bounds__(256) uc_vec_kernel(const TU* __restrict__ U, const TZ* __restrict__ z, int64_t N,
+                                                     int ell, const TA* __restrict__ coef, TA sign,
+                                                     TZ* __restrict__ out, const TZ* __restrict__ base = nullptr,
+                                                     TA scale = TA(1)) {
+    constexpr int V = Vec16<TU>::n;
+    constexpr int P = 32 * V;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    TA* c = reinterpret_cast<TA*>(smem_raw);
+    TA* red = c + ((ell + 3) & ~3);            // [8][P]
+    const int b = blockIdx.y;
+    for (int j = threadIdx.x; j < ell; j += blockDim.x) c[j] = coef[(size_t)b * ell + j];
+    __syncthreads();
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int64_t i = (int64_t)blockIdx.x * P + lane * V;
+    TA acc[V];
+#pragma unroll
+    for (int k = 0; k < V; ++k) acc[k] = TA(0);
+    if (i < N) {
+        // four columns (j, j + 8, j + 16, j + 24) per round, loads predicated,
+        // so a small active set still has all its loads in flight at once
+        for (int j = warp; j < ell; j += 32) {
+            TA u[4][V];
+            TA cq[4];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const int jq = j + 8 * q;
+                if (jq < ell) {
+                    load_vec<TU, TA, V>(U + (size_t)jq * N + i, u[q]);
+                    cq[q] = c[jq];
+                } else {
+#pragma unroll
+                    for (int k = 0; k < V; ++k) u[q][k] = TA(0);
+                    cq[q] = TA(0);
+                }
+            }
+#pragma unroll
+            for (int k = 0; k < V; ++k)
+                acc[k] = fma(u[3][k], cq[3], fma(u[2][k], cq[2], fma(u[1][k], cq[1], fma(u[0][k], cq[0], acc[k]))));
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < V; ++k) red[warp * P + lane * V + k] = acc[k];
+    __syncthreads();
+    for (int p = threadIdx.x; p < P; p += blockDim.x) {
+        const int64_t ii = (int64_t)blockIdx.x * P + p;
+        if (ii >= N) continue;
+        TA s = TA(0);
+#pragma unroll
+        for (int w = 0; w < 8; ++w) s += red[w * P + p];
+        const size_t o = (size_t)b * N + ii;
+        const TA v = (TA)ldf(z + o) + sign * s;
+        stf(out + o, base ? (TA)ldf(base + o) + scale * v : v);
+    }
+}
+
+}  // namespace
+}  // namespace nys

@@ -71,8 +71,9 @@ def main():
         z = torch.randn(N, device=dev)
         o = torch.empty_like(z)
         ms = timed(lambda: api.precond_apply(ctx, pc, z, True, o))
-        nbytes = 2 * N * ell * ub + 3 * N * 4
-        out.append(dict(case="precond_apply(inverse)", ms=ms, bytes=nbytes, GBs=nbytes / ms / 1e6))
+        nbytes = 2 * N * pc.ell_active * ub + 3 * N * 4
+        out.append(dict(case="precond_apply(inverse)", ms=ms, bytes=nbytes, GBs=nbytes / ms / 1e6,
+                        active_columns=pc.ell_active))
     if "normal" in cases:
         x1 = torch.randn(1, n, n, device=dev)
         y1 = torch.empty_like(x1)

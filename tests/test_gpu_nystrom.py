@@ -179,9 +179,12 @@ def test_precond_degenerate_is_reported(env):
 @pytest.mark.parametrize("dt", ["f32", "f64"])
 @pytest.mark.parametrize("reg", ["tv", "hs"])
 @pytest.mark.parametrize("precond", [False, True])
-def test_prox_dual_matches_oracle(env, dt, reg, precond):
+@pytest.mark.parametrize("shape", [(40, 52), (27, 31)])
+def test_prox_dual_matches_oracle(env, dt, reg, precond, shape):
+    # (40, 52): the fused three-launch dual step with partial 8 x 64 tiles;
+    # (27, 31): N not a multiple of the vector width, the unfused path
     torch, api, ctx = env
-    n1, n2, ell = 40, 52, 10
+    (n1, n2), ell = shape, 10
     s = phantom(max(n1, n2), 6, 3, "mixed")[:n1, :n2] + 0.05 * gaussian_probe_like((n1, n2), 13)
     lb, n_inner = 0.02, 30
     tdt = torch.float64 if dt == "f64" else torch.float32
