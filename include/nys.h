@@ -120,6 +120,15 @@ int nys_op_sizes(const nys_op* op, int64_t* N, int64_t* M);
  * capturable.  NYS_EINVAL for other kinds or another kernel shape. */
 int nys_op_set_kernel(nys_op* op, const double* kernel, int kh, int kw);
 
+/* Project autotuner: times the operator's launch variants on scratch data
+ * of `batch` images (batch >= 1) on the ctx stream and keeps the fastest for
+ * this op -- the blur output tile (32 or 64 pixels square, float32 ops) or the
+ * number of angles the Radon adjoint stages per round (4, 8 or 16; at most 8
+ * for float64).  *choice (may be NULL) receives the value kept.  Allocates
+ * and frees scratch and synchronises; not capturable.  Results are the same
+ * for every variant up to float summation order. */
+int nys_op_autotune(nys_op* op, int batch, int* choice);
+
 /* y[b] = A x[b], b < batch.  x: batch*N, y: batch*M, op dtype. */
 int op_apply(nys_op* op, const void* x, void* y, int batch);
 /* x[b] = A^T y[b]: the exact transpose of op_apply. */
@@ -318,6 +327,27 @@ int nys_unroll_forward(nys_unroll* u, const void* y, void* x_out);
 int nys_unroll_backward(nys_unroll* u, const void* xbar, double* grads);
 /* Change lambda (invalidates the last forward). */
 int nys_unroll_set_lambda(nys_unroll* u, double lambda);
+
+/* -------------------------------------------------- batched unrolled solves -- */
+/* Not in the paper: many unrolled solves (mixed sizes, operators and sketch
+ * sizes) replayed as one CUDA graph.  items[i] and its operator must have
+ * been created on item_ctx[i], whose stream must be its own (not ctx's);
+ * ys[i] (M_i values), xs[i] (N_i), xbars[i] (N_i) are device buffers of the
+ * item's dtype and grads[i] a device float64 buffer of 1 + kh kw values (as
+ * nys_unroll_backward), all fixed for the life of the batch.  Creation runs
+ * every item forward and backward once (synchronising), then captures the
+ * two graphs: the batch stream forks to the item streams, which run
+ * concurrently as branches of the graph, and joins them.  Not thread-safe. */
+typedef struct nys_batch nys_batch;
+int nys_batch_create(nys_ctx* ctx, int n, nys_unroll* const* items, nys_ctx* const* item_ctx,
+                     const void* const* ys, void* const* xs, const void* const* xbars,
+                     double* const* grads, nys_batch** out);
+/* One graph launch on ctx's stream: every item's forward (xs <- x^{K+1}). */
+int nys_batch_forward(nys_batch* b);
+/* One graph launch: every item's reverse pass for its xbars (grads <- ...).
+ * NYS_EINVAL before the first nys_batch_forward. */
+int nys_batch_backward(nys_batch* b);
+int nys_batch_destroy(nys_batch* b);
 
 /* ------------------------------------------------------- dense products -- */
 /* C (p x q, float64, row-major, device) = A^T B for tall operands A (N x p)

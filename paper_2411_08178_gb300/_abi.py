@@ -72,6 +72,7 @@ PROTOTYPES = {
     "nys_op_destroy": (i32, [vp]),
     "nys_op_sizes": (i32, [vp, C.POINTER(i64), C.POINTER(i64)]),
     "nys_op_set_kernel": (i32, [vp, C.POINTER(C.c_double), i32, i32]),
+    "nys_op_autotune": (i32, [vp, i32, C.POINTER(i32)]),
     "op_apply": (i32, [vp, vp, vp, i32]),
     "op_adjoint": (i32, [vp, vp, vp, i32]),
     "op_normal": (i32, [vp, vp, vp, i32]),
@@ -100,6 +101,11 @@ PROTOTYPES = {
     "nys_unroll_forward": (i32, [vp, vp, vp]),
     "nys_unroll_backward": (i32, [vp, vp, vp]),
     "nys_unroll_set_lambda": (i32, [vp, f64]),
+    "nys_batch_create": (i32, [vp, i32, C.POINTER(vp), C.POINTER(vp), C.POINTER(vp), C.POINTER(vp), C.POINTER(vp),
+                               C.POINTER(vp), C.POINTER(vp)]),
+    "nys_batch_forward": (i32, [vp]),
+    "nys_batch_backward": (i32, [vp]),
+    "nys_batch_destroy": (i32, [vp]),
     "nys_rel_err": (i32, [vp, i32, i64, vp, vp, C.POINTER(f64)]),
     "nys_gram": (i32, [vp, i32, vp, i32, vp, i32, i64, vp, i32]),
     "nys_tall_gemm": (i32, [vp, i32, vp, vp, f64, i64, i32, vp, i32, i32, vp, i32]),

@@ -126,6 +126,12 @@ class Operator:
         else:
             self.meas_shape = (n_angles, n_bins)
 
+    def autotune(self, batch: int = 1) -> int:
+        """Pick the fastest launch variant for `batch` images (synchronises)."""
+        c = C.c_int()
+        check(_lib().nys_op_autotune(self.h, batch, C.byref(c)), self.ctx.h)
+        return c.value
+
     def set_kernel(self, kernel):
         """Replace the blur kernel (same shape; host copy, synchronises)."""
         k = np.ascontiguousarray(np.asarray(kernel, dtype=np.float64))
@@ -456,3 +462,41 @@ def nys_rel_err(ctx: Context, a: torch.Tensor, b: torch.Tensor | None) -> float:
     check(_lib().nys_rel_err(ctx.h, dtype_code(a), a.numel(), _ptr(a), _ptr(b) if b is not None else None,
                              C.byref(out)), ctx.h)
     return out.value
+
+
+class Batch:
+    """nys_batch: several Unroll handles (each on its own Context with its own
+    stream) replayed as one CUDA graph for the forward and one for the
+    reverse pass.  ys, xs, xbars are per-item device tensors fixed for the
+    life of the batch; grads are allocated here (float64, 1 + kh kw each)."""
+
+    def __init__(self, ctx: Context, unrolls: list, ys: list, xs: list, xbars: list):
+        n = len(unrolls)
+        self.ctx, self.unrolls = ctx, unrolls
+        self.ys, self.xs, self.xbars = ys, xs, xbars
+        self.grads = [torch.zeros(1 + u.ntaps, dtype=torch.float64, device=torch.device("cuda", ctx.device))
+                      for u in unrolls]
+        arr = lambda vals: (C.c_void_p * n)(*vals)
+        h = C.c_void_p()
+        check(_lib().nys_batch_create(ctx.h, n, arr([u.h.value for u in unrolls]),
+                                      arr([u.ctx.h.value for u in unrolls]), arr([_ptr(t) for t in ys]),
+                                      arr([_ptr(t) for t in xs]), arr([_ptr(t) for t in xbars]),
+                                      arr([_ptr(t) for t in self.grads]), C.byref(h)), ctx.h)
+        self.h = h
+
+    def forward(self):
+        check(_lib().nys_batch_forward(self.h), self.ctx.h)
+
+    def backward(self):
+        check(_lib().nys_batch_backward(self.h), self.ctx.h)
+
+    def close(self):
+        if getattr(self, "h", None):
+            _lib().nys_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -12,6 +12,19 @@ std::string g_err;
 
 namespace nys {
 
+void ctx_retain(nys_ctx* ctx) {
+    if (ctx) ++ctx->refs;
+}
+
+void ctx_release(nys_ctx* ctx) {
+    if (!ctx || --ctx->refs > 0) return;
+    cudaStreamSynchronize(ctx->stream);
+    for (int i = 0; i < 12; ++i)
+        if (ctx->slot_ptr[i]) cudaFree(ctx->slot_ptr[i]);
+    if (ctx->counters) cudaFree(ctx->counters);
+    delete ctx;
+}
+
 int fail(nys_ctx* ctx, int code, const char* fmt, ...) {
     char buf[512];
     va_list ap;
@@ -146,10 +159,7 @@ int nys_create(nys_ctx** out, int device, void* stream) {
 int nys_destroy(nys_ctx* ctx) {
     if (!ctx) return NYS_OK;
     cudaStreamSynchronize(ctx->stream);
-    for (int i = 0; i < 12; ++i)
-        if (ctx->slot_ptr[i]) cudaFree(ctx->slot_ptr[i]);
-    if (ctx->counters) cudaFree(ctx->counters);
-    delete ctx;
+    ctx_release(ctx);
     return NYS_OK;
 }
 
@@ -182,25 +192,26 @@ int nys_op_create(nys_ctx* ctx, const nys_op_desc* d, nys_op** out) {
     if (d->n1 <= 0 || d->n2 <= 0) return fail(ctx, NYS_EINVAL, "bad image size %d x %d", d->n1, d->n2);
     auto* op = new nys_op();
     op->ctx = ctx;
+    ctx_retain(ctx);
     op->kind = d->kind;
     op->dtype = d->dtype;
     op->n1 = d->n1;
     op->n2 = d->n2;
     op->N = (int64_t)d->n1 * d->n2;
     if (d->n1 <= 0 || d->n2 <= 0 || op->N >= (int64_t(1) << 31)) {
-        delete op;
+        nys_op_destroy(op);
         return fail(ctx, NYS_EINVAL, "image size must be positive with fewer than 2^31 pixels");
     }
     op->haar_levels = d->haar_levels;
     if (d->haar_levels < 0 || (d->haar_levels > 0 && ((d->n1 % (1 << d->haar_levels)) ||
                                                      (d->n2 % (1 << d->haar_levels))))) {
-        delete op;
+        nys_op_destroy(op);
         return fail(ctx, NYS_EINVAL, "image size not divisible by 2^haar_levels");
     }
     int st = NYS_OK;
     if (d->kind == NYS_OP_BLUR || d->kind == NYS_OP_BLUR_DECIM) {
         if (!d->kernel || d->kh <= 0 || d->kw <= 0 || !(d->kh & 1) || !(d->kw & 1)) {
-            delete op;
+            nys_op_destroy(op);
             return fail(ctx, NYS_EINVAL, "blur kernel must be given with odd sizes");
         }
         op->kh = d->kh;
@@ -208,14 +219,14 @@ int nys_op_create(nys_ctx* ctx, const nys_op_desc* d, nys_op** out) {
         op->h.assign(d->kernel, d->kernel + (size_t)d->kh * d->kw);
         op->decim = d->kind == NYS_OP_BLUR_DECIM ? d->decim : 1;
         if (op->decim < 1 || d->n1 % op->decim || d->n2 % op->decim) {
-            delete op;
+            nys_op_destroy(op);
             return fail(ctx, NYS_EINVAL, "decimation factor must divide the image size");
         }
         op->M = (int64_t)(d->n1 / op->decim) * (d->n2 / op->decim);
         st = blur_setup(op);
     } else if (d->kind == NYS_OP_RADON) {
         if (d->n_angles <= 0 || d->n_bins <= 0 || !(d->angle_span > 0.0)) {
-            delete op;
+            nys_op_destroy(op);
             return fail(ctx, NYS_EINVAL, "radon geometry needs n_angles, n_bins > 0 and span > 0");
         }
         op->n_angles = d->n_angles;
@@ -224,7 +235,7 @@ int nys_op_create(nys_ctx* ctx, const nys_op_desc* d, nys_op** out) {
         op->M = (int64_t)d->n_angles * d->n_bins;
         st = radon_setup(op);
     } else {
-        delete op;
+        nys_op_destroy(op);
         return fail(ctx, NYS_EINVAL, "unknown operator kind %d", d->kind);
     }
     if (st) {
@@ -238,10 +249,12 @@ int nys_op_create(nys_ctx* ctx, const nys_op_desc* d, nys_op** out) {
 int nys_op_destroy(nys_op* op) {
     if (!op) return NYS_OK;
     if (op->ctx) cudaStreamSynchronize(op->ctx->stream);
-    void* bufs[] = {op->taps_fwd, op->taps_adj, op->taps_nrm, op->rtab, op->inter};
+    void* bufs[] = {op->taps_fwd, op->taps_adj, op->taps_nrm, op->rtab, op->inter, op->lines};
     for (void* b : bufs)
         if (b) cudaFree(b);
+    nys_ctx* ctx = op->ctx;
     delete op;
+    ctx_release(ctx);
     return NYS_OK;
 }
 
@@ -258,6 +271,70 @@ int nys_op_set_kernel(nys_op* op, const double* kernel, int kh, int kw) {
     op->chunk = 0;
     op->h.assign(kernel, kernel + (size_t)kh * kw);
     return blur_setup(op);
+}
+
+int nys_op_autotune(nys_op* op, int batch, int* choice) {
+    if (!op || batch < 1) return fail(op ? op->ctx : nullptr, NYS_EINVAL, "nys_op_autotune: null op or batch < 1");
+    nys_ctx* ctx = op->ctx;
+    const size_t es = dtype_size(op->dtype);
+    void* x = nullptr;
+    void* y = nullptr;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    int st = NYS_OK;
+    auto cleanup = [&]() {
+        if (x) cudaFree(x);
+        if (y) cudaFree(y);
+        if (e0) cudaEventDestroy(e0);
+        if (e1) cudaEventDestroy(e1);
+    };
+    cudaError_t e = cudaMalloc(&x, (size_t)batch * std::max(op->N, op->M) * es);
+    if (e == cudaSuccess) e = cudaMalloc(&y, (size_t)batch * std::max(op->N, op->M) * es);
+    if (e == cudaSuccess) e = cudaMemsetAsync(x, 0, (size_t)batch * std::max(op->N, op->M) * es, ctx->stream);
+    if (e == cudaSuccess) e = cudaEventCreate(&e0);
+    if (e == cudaSuccess) e = cudaEventCreate(&e1);
+    if (e != cudaSuccess) {
+        cleanup();
+        return cuda_fail(ctx, e, "nys_op_autotune scratch");
+    }
+    // candidates: the variant knob and the operator pass it affects
+    std::vector<int> cand;
+    int which = 2;
+    int* knob = nullptr;
+    if (op->kind == NYS_OP_RADON) {
+        knob = &op->radon_adj_ak;
+        cand = op->dtype == NYS_F64 ? std::vector<int>{4, 8} : std::vector<int>{4, 8, 16};
+        which = 1;
+    } else if (op->kind == NYS_OP_BLUR && op->dtype != NYS_F64) {
+        knob = &op->blur_tile;
+        cand = {32, 64};
+    }
+    if (knob) {
+        float best = 1e30f;
+        int best_v = *knob;
+        for (int v : cand) {
+            *knob = v;
+            if ((st = op_run(op, which, x, y, batch, op->dtype, op->dtype))) break;   // warm-up
+            cudaEventRecord(e0, ctx->stream);
+            for (int r = 0; r < 3 && !st; ++r) st = op_run(op, which, x, y, batch, op->dtype, op->dtype);
+            cudaEventRecord(e1, ctx->stream);
+            if (st) break;
+            if ((e = cudaEventSynchronize(e1)) != cudaSuccess) {
+                st = cuda_fail(ctx, e, "nys_op_autotune timing");
+                break;
+            }
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, e0, e1);
+            if (ms < best) {
+                best = ms;
+                best_v = v;
+            }
+        }
+        *knob = best_v;
+    }
+    cudaStreamSynchronize(ctx->stream);
+    cleanup();
+    if (choice) *choice = knob ? *knob : 0;
+    return st;
 }
 
 int nys_op_sizes(const nys_op* op, int64_t* N, int64_t* M) {

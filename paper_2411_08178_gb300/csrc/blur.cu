@@ -247,9 +247,8 @@ int launch_c2d(nys_op* op, const void* x, void* y, int batch, const void* taps) 
     return NYS_OK;
 }
 
-template <class TI, class TO, class TC>
-int blur_typed(nys_op* op, int which, const void* x, void* y, int batch) {
-    constexpr int T = sizeof(TC) == 8 ? 32 : 64;
+template <class TI, class TO, class TC, int T>
+int blur_typed_t(nys_op* op, int which, const void* x, void* y, int batch) {
     if (op->separable) {
         if (which == 2)
             return launch_sep<TI, TO, TC, T>(op, x, y, batch, op->taps_nrm, op->Lc_n, op->Lr_n, op->cc_n, op->cr_n);
@@ -265,6 +264,13 @@ int blur_typed(nys_op* op, int which, const void* x, void* y, int batch) {
         if (int st = launch_c2d<TC, TO, TC, T>(op, op->inter, (char*)y + out_off, nb, op->taps_adj)) return st;
     }
     return NYS_OK;
+}
+
+// output tile: 32 x 32 in float64; 32 or 64 in float32 (nys_op_autotune picks)
+template <class TI, class TO, class TC>
+int blur_typed(nys_op* op, int which, const void* x, void* y, int batch) {
+    if (sizeof(TC) == 8 || op->blur_tile == 32) return blur_typed_t<TI, TO, TC, 32>(op, which, x, y, batch);
+    return blur_typed_t<TI, TO, TC, 64>(op, which, x, y, batch);
 }
 
 template <class TI, class TO, class TC>

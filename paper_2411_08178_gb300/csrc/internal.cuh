@@ -74,6 +74,10 @@ struct nys_ctx {
     bool l2_window_set = false;
     std::string err;
     unsigned* counters = nullptr;   // device, 64 completion counters (see vec.cuh)
+    // the context is freed when its owner (nys_destroy) and every object
+    // created on it (operators, solvers, unrolled solves, batches) are gone,
+    // in whatever order they are destroyed
+    int refs = 1;
     // independent growable scratch regions (see nys::scratch)
     void* slot_ptr[12] = {nullptr};
     size_t slot_bytes[12] = {0};
@@ -98,6 +102,9 @@ struct nys_op {
     int n_angles = 0, n_bins = 0;
     double span = 0.0;
     void* rtab = nullptr;             // per-angle tables, see radon.cu
+    void* lines = nullptr;            // radon: `chunk` images as line-major copies (row-major and transposed)
+    int radon_adj_ak = 8;             // radon adjoint: angles staged per round (chosen by nys_op_autotune)
+    int blur_tile = 64;               // blur: output tile side, 32 or 64 (float32; chosen by nys_op_autotune)
     // intermediate buffer for two-pass normals (M per image, `chunk` images)
     void* inter = nullptr;
     int chunk = 0;
@@ -105,6 +112,9 @@ struct nys_op {
 
 namespace nys {
 
+// reference counting of a context by the objects created on it
+void ctx_retain(nys_ctx* ctx);
+void ctx_release(nys_ctx* ctx);
 // record an error on ctx (and globally) and return `code`
 int fail(nys_ctx* ctx, int code, const char* fmt, ...);
 int cuda_fail(nys_ctx* ctx, cudaError_t e, const char* what);
@@ -197,6 +207,8 @@ namespace nys {
 // not null the input is computed on the fly (used by the fused prox kernels).
 int precond_run(nys_ctx* ctx, const nys_precond* pc, int inverse, int dtype, const void* z,
                 void* out, int batch);
+// the contexts an unrolled-solve handle launches on (unroll.cu)
+void unroll_contexts(const nys_unroll* U, nys_ctx** ctx, nys_ctx** op_ctx);
 // dual APG prox with the fused three-launch step (prox_fused.cu); returns
 // NYS_EINVAL without launching anything when the layout does not allow it
 int prox_dual_fused(nys_ctx* ctx, const nys_precond* pc, int reg, double lb, int n_inner, int dtype, int n1, int n2,

@@ -128,7 +128,10 @@ __global__ void copy_pad(const double* __restrict__ G, int ell, T* __restrict__ 
 // columns.  arr holds the round-robin arrangement.
 template <class T>
 __global__ void __launch_bounds__(1024) jacobi_kernel(T* __restrict__ G, T* __restrict__ V, int n, int nreal,
-                                                      int max_sweeps, double tol, int* __restrict__ sweeps_out) {
+                                                      int max_sweeps, double tol, int* __restrict__ sweeps_out,
+                                                      const int* __restrict__ only_if_failed) {
+    // runs only when the one-sided kernel reported a failed Cholesky
+    if (only_if_failed && *only_if_failed == 0) return;
     __shared__ int arr[1024];
     __shared__ int arr2[1024];
     __shared__ int pp[512], qq[512];
@@ -320,16 +323,22 @@ __global__ void __launch_bounds__(1024) jacobi_smem_kernel(const T* __restrict__
 // so a pair's inner products and its update are stride-1.  The rotation log
 // has the two-sided kernel's format.  status_out = 1 (and nothing logged) if
 // the Cholesky meets a non-positive pivot, so that the two-sided kernel runs.
-template <class T>
-__global__ void __launch_bounds__(1024) jacobi_1s_kernel(const T* __restrict__ Gin, int n, int nreal, int max_sweeps,
-                                                         int2* __restrict__ logpq, T* __restrict__ logcs,
-                                                         int* __restrict__ rounds_out, int* __restrict__ sweeps_out,
-                                                         int* __restrict__ status_out) {
+template <class T, bool GLOBAL>
+__global__ void __launch_bounds__(1024) jacobi_1s_kernel(const T* __restrict__ Gin, T* __restrict__ Rg, int n, int nreal,
+                                                         int max_sweeps, int2* __restrict__ logpq,
+                                                         T* __restrict__ logcs, int* __restrict__ rounds_out,
+                                                         int* __restrict__ sweeps_out, int* __restrict__ status_out) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int h = n / 2;
-    const int pitch = n + 1;   // column j at R + j * pitch
-    T* R = reinterpret_cast<T*>(smem_raw);
+    // column j at R + j * pitch: shared memory (pitch n + 1) with the Cholesky
+    // done here, or global memory (pitch n) holding the factor written by
+    // chol_upper_kernel, which also set *status_out
+    const int pitch = GLOBAL ? n : n + 1;
+    T* R = GLOBAL ? Rg : reinterpret_cast<T*>(smem_raw);
     __shared__ int bad;
+    if (GLOBAL) {
+        if (*status_out != 0) return;
+    } else {
     // load G (symmetric) into R as column-major, pad index -> identity
     for (int t = threadIdx.x; t < n * n; t += blockDim.x) {
         const int i = t / n, j = t % n;
@@ -366,6 +375,7 @@ __global__ void __launch_bounds__(1024) jacobi_1s_kernel(const T* __restrict__ G
         const int i = t % n, j = t / n;   // zero the strict lower part
         if (i > j) R[j * pitch + i] = T(0);
     }
+    }   // shared-memory set-up
     __syncthreads();
     // Threshold: a pair counts as orthogonal once |x.y| <= tol sqrt(|x|^2 |y|^2)
     // with tol = sqrt(n) eps; eigenvalues are recomputed afterwards in FP64 from
@@ -397,6 +407,7 @@ __global__ void __launch_bounds__(1024) jacobi_1s_kernel(const T* __restrict__ G
                 T* wq = R + q * pitch;
                 T a = T(0), b = T(0), c = T(0);
                 if (active) {
+#pragma unroll 8
                     for (int i = gl; i < n; i += gs) {
                         const T x = wp[i], y = wq[i];
                         a = fma(x, x, a);
@@ -416,6 +427,7 @@ __global__ void __launch_bounds__(1024) jacobi_1s_kernel(const T* __restrict__ G
                     const T t = (zeta >= T(0) ? T(1) : T(-1)) / (fabs(zeta) + sqrt(T(1) + zeta * zeta));
                     cs = T(1) / sqrt(T(1) + t * t);
                     sn = t * cs;
+#pragma unroll 8
                     for (int i = gl; i < n; i += gs) {
                         const T x = wp[i], y = wq[i];
                         wp[i] = cs * x - sn * y;
@@ -444,14 +456,38 @@ __global__ void __launch_bounds__(1024) jacobi_1s_kernel(const T* __restrict__ G
     }
 }
 
+// Set-up of the global-memory one-sided Jacobi: work (n x n float64) = G
+// padded with the identity, its float64 Cholesky L (one CTA), and R = L^T in
+// the working type, column-major with pitch n (column j of R is row j of L).
+// *status = 1 if a pivot is not positive; *rounds = 0 until the sweeps log.
+template <class T>
+__global__ void __launch_bounds__(1024) chol_upper_kernel(const double* __restrict__ G, int ell, int n,
+                                                          double* __restrict__ work, T* __restrict__ R,
+                                                          int* __restrict__ status, int* __restrict__ rounds) {
+    __shared__ int flag;
+    for (int t = threadIdx.x; t < n * n; t += blockDim.x) {
+        const int i = t / n, j = t % n;
+        work[t] = (i < ell && j < ell) ? G[(size_t)i * ell + j] : (i == j ? 1.0 : 0.0);
+    }
+    if (threadIdx.x == 0) *rounds = 0;
+    __syncthreads();
+    const bool ok = block_cholesky(work, n, &flag);
+    if (threadIdx.x == 0) *status = ok ? 0 : 1;
+    if (!ok) return;
+    for (int t = threadIdx.x; t < n * n; t += blockDim.x) {
+        const int j = t / n, i = t % n;
+        R[t] = (i <= j) ? (T)work[(size_t)j * n + i] : T(0);
+    }
+}
+
 // V[i][:] = e_i J_1 ... J_r, one warp per row (eight rows per CTA); pairs of
-// a round are disjoint.  The log is staged through shared memory RCH rounds
+// a round are disjoint.  The log is staged through shared memory rch rounds
 // at a time by the whole CTA, so the sequential rounds wait on shared-memory
 // latency instead of global-memory latency.
-constexpr int RCH = 32;
 template <class T>
 __global__ void __launch_bounds__(256) rot_apply_kernel(const int2* __restrict__ logpq, const T* __restrict__ logcs,
-                                                        const int* __restrict__ rounds, int n, T* __restrict__ V) {
+                                                        const int* __restrict__ rounds, int n, int RCH,
+                                                        T* __restrict__ V) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int h = n / 2;
@@ -599,48 +635,67 @@ int sym_eig(nys_ctx* ctx, const double* G, int ell, bool use_f32, const double* 
         const double tol = sizeof(T) == 8 ? 1e-14 : 2e-7;
         const int h = n / 2;
         const size_t smem = sizeof(T) * ((size_t)n * (n + 1) + 2 * (size_t)h) + sizeof(int) * (2 * (size_t)n + 2 * h + 4) + 64;
-        if (smem + 1024 <= 227 * 1024) {   // leave room for the kernel's static shared memory
-            // G in shared memory, rotations logged, V built by many CTAs
-            int st;
-            const size_t rounds = (size_t)max_sweeps * (n - 1);
-            char* lg = (char*)scratch(ctx, SLOT_EIG, rounds * h * (sizeof(int2) + 2 * sizeof(T)) + 64, &st);
-            if (st) return st;
-            int2* logpq = (int2*)lg;
-            T* logcs = (T*)(lg + rounds * h * sizeof(int2));
-            int* rounds_dev = sweeps_dev + 1;
+        const bool in_smem = smem + 1024 <= 227 * 1024;   // leave room for the kernels' static shared memory
+        // rotations are logged and V is built by many CTAs (rot_apply)
+        int st;
+        const size_t rounds = (size_t)max_sweeps * (n - 1);
+        auto al = [](size_t v) { return (v + 255) & ~size_t(255); };
+        const size_t logb = al(rounds * h * (sizeof(int2) + 2 * sizeof(T)));
+        const size_t extra = in_smem ? 0 : al((size_t)n * n * sizeof(double)) + al((size_t)n * n * sizeof(T));
+        char* lg = (char*)scratch(ctx, SLOT_EIG, logb + extra + 64, &st);
+        if (st) return st;
+        int2* logpq = (int2*)lg;
+        T* logcs = (T*)(lg + rounds * h * sizeof(int2));
+        int* rounds_dev = sweeps_dev + 1;
+        // one-sided Jacobi on the Cholesky factor of G; the two-sided kernel runs
+        // instead (decided on the device) if that Cholesky fails
+        int* status_dev = sweeps_dev + 2;
+        if (in_smem) {
             static size_t attr = 48 * 1024;
             if (smem > attr) {
                 NYS_CK(ctx, cudaFuncSetAttribute(jacobi_smem_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                                  (int)smem));
                 attr = smem;
             }
-            // one-sided Jacobi on the Cholesky factor; the two-sided kernel
-            // runs instead (decided on the device) if that Cholesky fails
-            int* status_dev = sweeps_dev + 2;
             const size_t smem1 = sizeof(T) * (size_t)n * (n + 1) + 64;
             static size_t attr1 = 48 * 1024;
             if (smem1 > attr1) {
-                NYS_CK(ctx, cudaFuncSetAttribute(jacobi_1s_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                 (int)smem1));
+                NYS_CK(ctx, cudaFuncSetAttribute(jacobi_1s_kernel<T, false>,
+                                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem1));
                 attr1 = smem1;
             }
-            jacobi_1s_kernel<T><<<1, 1024, smem1, s>>>(Gw, n, ell, max_sweeps, logpq, logcs, rounds_dev, sweeps_dev,
-                                                       status_dev);
+            jacobi_1s_kernel<T, false><<<1, 1024, smem1, s>>>(Gw, nullptr, n, ell, max_sweeps, logpq, logcs,
+                                                              rounds_dev, sweeps_dev, status_dev);
             NYS_LAUNCH_CK(ctx);
             jacobi_smem_kernel<T><<<1, 1024, smem, s>>>(Gw, n, ell, max_sweeps, tol, logpq, logcs, rounds_dev,
                                                         sweeps_dev, status_dev);
             NYS_LAUNCH_CK(ctx);
-            const size_t rsm = (8 * (size_t)n + (size_t)RCH * h * 2) * sizeof(T) + (size_t)RCH * h * sizeof(int2);
-            static size_t rattr = 48 * 1024;
-            if (rsm > rattr) {
-                NYS_CK(ctx, cudaFuncSetAttribute(rot_apply_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                 (int)rsm));
-                rattr = rsm;
-            }
-            rot_apply_kernel<T><<<(n + 7) / 8, 256, rsm, s>>>(logpq, logcs, rounds_dev, n, V);
-            NYS_LAUNCH_CK(ctx);
         } else {
-            jacobi_kernel<T><<<1, 1024, 0, s>>>(Gw, V, n, ell, max_sweeps, tol, sweeps_dev);
+            // too large for shared memory: float64 Cholesky of G, then the
+            // one-sided sweeps on R held in global memory (L2-resident)
+            double* w64 = (double*)(lg + logb);
+            T* Rg = (T*)(lg + logb + al((size_t)n * n * sizeof(double)));
+            chol_upper_kernel<T><<<1, 1024, 0, s>>>(G, ell, n, w64, Rg, status_dev, rounds_dev);
+            NYS_LAUNCH_CK(ctx);
+            jacobi_1s_kernel<T, true><<<1, 1024, 0, s>>>(nullptr, Rg, n, ell, max_sweeps, logpq, logcs, rounds_dev,
+                                                         sweeps_dev, status_dev);
+            NYS_LAUNCH_CK(ctx);
+        }
+        // staged rounds per pass of rot_apply: as many as fit in 96 KB
+        const size_t per_round = (size_t)h * (2 * sizeof(T) + sizeof(int2));
+        const int rch = (int)std::max<size_t>(1, std::min<size_t>(32, (96 * 1024) / per_round));
+        const size_t rsm = 8 * (size_t)n * sizeof(T) + (size_t)rch * per_round;
+        static size_t rattr = 48 * 1024;
+        if (rsm > rattr) {
+            NYS_CK(ctx, cudaFuncSetAttribute(rot_apply_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)rsm));
+            rattr = rsm;
+        }
+        rot_apply_kernel<T><<<(n + 7) / 8, 256, rsm, s>>>(logpq, logcs, rounds_dev, n, rch, V);
+        NYS_LAUNCH_CK(ctx);
+        if (!in_smem) {
+            // two-sided fallback in global memory (overwrites V) if the Cholesky failed
+            jacobi_kernel<T><<<1, 1024, 0, s>>>(Gw, V, n, ell, max_sweeps, tol, sweeps_dev, status_dev);
             NYS_LAUNCH_CK(ctx);
         }
         rayleigh_kernel<T><<<ell, 128, 0, s>>>(G, V, ell, n, lam);

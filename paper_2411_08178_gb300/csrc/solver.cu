@@ -479,6 +479,7 @@ int nys_solver_create(nys_ctx* ctx, nys_op* op, const nys_solver_desc* d, const 
     }
     auto* S = new nys_solver();
     S->ctx = ctx;
+    ctx_retain(ctx);
     S->op = op;
     S->d = *d;
     S->pc = pc;
@@ -505,7 +506,9 @@ int nys_solver_destroy(nys_solver* S) {
     if (S->ev_out) cudaEventDestroy(S->ev_out);
     if (S->gs) cudaStreamDestroy(S->gs);
     if (S->mem) cudaFree(S->mem);
+    nys_ctx* ctx = S->ctx;
     delete S;
+    ctx_release(ctx);
     return NYS_OK;
 }
 

@@ -465,6 +465,14 @@ std::vector<double> tseq(int count) {
 }  // namespace
 }  // namespace nys
 
+namespace nys {
+// the contexts an unrolled-solve handle launches on (its own and its op's)
+void unroll_contexts(const nys_unroll* U, nys_ctx** ctx, nys_ctx** op_ctx) {
+    *ctx = U->ctx;
+    *op_ctx = U->op->ctx;
+}
+}  // namespace nys
+
 using namespace nys;
 
 extern "C" {
@@ -478,6 +486,7 @@ int nys_unroll_create(nys_ctx* ctx, nys_op* op, const nys_precond* pc, const nys
     if (pc && (pc->N != op->N || !pc->priv)) return fail(ctx, NYS_EINVAL, "preconditioner size mismatch or not set up");
     nys_unroll* U = new nys_unroll();
     U->ctx = ctx;
+    ctx_retain(ctx);
     U->op = op;
     U->pc = pc;
     U->dtype = op->dtype;
@@ -534,7 +543,9 @@ int nys_unroll_destroy(nys_unroll* U) {
     void* bufs_[] = {U->y, U->st, U->ckpt, U->rec, U->tmp, U->acc};
     for (void* p : bufs_)
         if (p) cudaFree(p);
+    nys_ctx* ctx = U->ctx;
     delete U;
+    ctx_release(ctx);
     return NYS_OK;
 }
 

@@ -1,6 +1,6 @@
 """Per-call timings of the library's hot entry points, and a small target for ncu.
 
-  python -m paper_2411_08178_gb300.profile_kernels [--case all|precond|normal|sketch|prox|iter|unroll]
+  python -m paper_2411_08178_gb300.profile_kernels [--case all|precond|normal|sketch|prox|iter|unroll|batch]
         [--n 512] [--ell 200] [--reps 20] [--l2]
 
 Each case builds the 512 x 512 deblurring operator (25 x 25 Gaussian, sigma 4)
@@ -29,6 +29,10 @@ def main():
     ap.add_argument("--reps", type=int, default=20)
     ap.add_argument("--u-dtype", choices=["bf16", "f32"], default="bf16")
     ap.add_argument("--l2", action="store_true", help="keep U resident in L2 (nys_l2_persist)")
+    ap.add_argument("--batch-count", type=int, default=64)
+    ap.add_argument("--batch-inner", type=int, default=20)
+    ap.add_argument("--op", choices=["blur", "radon"], default="blur",
+                    help="blur: 25 x 25 Gaussian sigma 4; radon: 720 angles x 736 bins")
     args = ap.parse_args()
     import torch
 
@@ -43,8 +47,10 @@ def main():
     ctx = api.Context(0, stream)
     n, ell = args.n, args.ell
     N = n * n
-    h = WL.gaussian_kernel(25, 4.0)
-    op = api.Operator(ctx, "blur", n, n, dtype=torch.float32, kernel=h)
+    if args.op == "blur":
+        op = api.Operator(ctx, "blur", n, n, dtype=torch.float32, kernel=WL.gaussian_kernel(25, 4.0))
+    else:
+        op = api.Operator(ctx, "radon", n, n, dtype=torch.float32, n_angles=720, n_bins=736)
     sd = torch.bfloat16 if args.u_dtype == "bf16" else torch.float32
     ub = 2 if sd == torch.bfloat16 else 4
 
@@ -78,11 +84,10 @@ def main():
         x1 = torch.randn(1, n, n, device=dev)
         y1 = torch.empty_like(x1)
         ms = timed(lambda: api.op_normal(op, x1, y1))
-        out.append(dict(case="op_normal x1 (A^T A, 25x25 separable)", ms=ms, bytes=2 * N * 4,
-                        flops=2 * 2 * 49 * N))
+        out.append(dict(case=f"op_normal x1 ({args.op})", ms=ms, bytes=2 * N * 4))
     if "sketch" in cases:
         ms = timed(lambda: api.nys_sketch(ctx, op, ell, 13, store_dtype=sd, out=(Om, Y)), reps=max(2, args.reps // 4))
-        out.append(dict(case=f"nys_sketch ell={ell}", ms=ms, bytes=2 * N * ell * ub, flops=2 * 2 * 49 * N * ell))
+        out.append(dict(case=f"nys_sketch ell={ell} ({args.op})", ms=ms, bytes=2 * N * ell * ub))
         ms = timed(lambda: api.nys_factor(ctx, Om, Y, 2.0 ** -23, pc=pc), reps=max(2, args.reps // 4))
         out.append(dict(case=f"nys_factor ell={ell}", ms=ms, bytes=4 * N * ell * ub, flops=4 * 2 * N * ell * ell))
     if "prox" in cases:
@@ -93,7 +98,7 @@ def main():
         ms = timed(lambda: api.prox_tv(ctx, pc, 5e-4, 20, s, Q=Q), reps=max(2, args.reps // 2))
         out.append(dict(case="prox_tv P=RNP n_inner=20", ms=ms))
     if "iter" in cases:
-        y = torch.rand(n, n, device=dev)
+        y = torch.rand(op.meas_shape, device=dev)
         for name, p in (("plain", None), ("precond", pc)):
             sol = api.Solver(ctx, op, y, "tv", 5e-4, pc=p, n_inner=20)
             ms = timed(lambda: sol.step(1), reps=args.reps)
@@ -102,7 +107,7 @@ def main():
     if "unroll" in cases:
         # 50 unrolled preconditioned iterations (n_inner 20), checkpoint every 10:
         # forward alone and forward + reverse pass (d/d lambda, d/d 25x25 kernel)
-        y = torch.rand(n, n, device=dev)
+        y = torch.rand(op.meas_shape, device=dev)
         un = api.Unroll(ctx, op, 5e-4, 0.9, 50, n_inner=20, ckpt_every=10, pc=pc)
         xb = torch.randn(n, n, device=dev)
         ms_f = timed(lambda: un.forward(y), reps=2)
@@ -110,6 +115,50 @@ def main():
         out.append(dict(case="unroll K=50 n_inner=20 ckpt=10 forward", ms=ms_f))
         out.append(dict(case="unroll K=50 n_inner=20 ckpt=10 forward+backward", ms=ms_fb))
         un.close()
+    if "batch" in cases:
+        # the batched, differentiated workload: 64 instances (128^2 .. 512^2,
+        # blur / CT, ell in {64, 128, 256}), 50 unrolled iterations, checkpoint
+        # every 10, one graph launch forward and one backward
+        import time
+        from paper_2411_08178_gb300.batched import BatchedUnroll
+        specs = []
+        for inst in WL.batch_instances(args.batch_count):
+            sp = dict(inst)
+            ctx_i = api.Context(0)
+            if inst["op"] == "blur":
+                sp["kernel"] = WL.gaussian_kernel(inst["k"], inst["sigma"])
+                opi = api.Operator(ctx_i, "blur", inst["n"], inst["n"], dtype=torch.float32, kernel=sp["kernel"])
+            else:
+                opi = api.Operator(ctx_i, "radon", inst["n"], inst["n"], dtype=torch.float32,
+                                   n_angles=inst["n_angles"], n_bins=inst["n_bins"])
+            sp["x_true"], sp["y"] = WL.batch_instance_data(
+                inst, lambda xt: api.op_apply(opi, torch.from_numpy(xt).float().to(dev)[None]).cpu().numpy()[0])
+            opi.close()
+            specs.append(sp)
+        t0 = time.time()
+        B = BatchedUnroll(specs, K=50, n_inner=args.batch_inner, ckpt_every=10)
+        setup_s = time.time() - t0
+        bs = B.stream
+
+        def timed_on(fn, reps=3):
+            fn()
+            torch.cuda.synchronize()
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record(bs)
+            for _ in range(reps):
+                fn()
+            b.record(bs)
+            torch.cuda.synchronize()
+            return a.elapsed_time(b) / reps
+
+        ms_f = timed_on(B.forward)
+        ms_b = timed_on(B.backward)
+        pix = sum(sp["n"] ** 2 for sp in specs)
+        out.append(dict(case=f"batch {len(specs)} instances K=50 n_inner={args.batch_inner} forward (one graph)",
+                        ms=ms_f, pixels=pix, setup_s=round(setup_s, 1)))
+        out.append(dict(case=f"batch {len(specs)} instances backward (one graph)", ms=ms_b,
+                        tuned=[it["tuned"] for it in B.items]))
     for o in out:
         print(json.dumps(o))
 

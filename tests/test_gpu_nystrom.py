@@ -97,6 +97,25 @@ def test_factor_f32_and_bf16_stated_accuracy(env):
     _check_factor(pcb.U.double().cpu().numpy(), pcb.S_hat.cpu().numpy(), ref, 3e-2, 3e-2)
 
 
+@pytest.mark.parametrize("dt,ell", [("f32", 300), ("f64", 200)])
+def test_factor_large_ell_global_jacobi(env, dt, ell):
+    # sketch sizes whose ell x ell core does not fit in shared memory (float32
+    # above 236, float64 above 166): float64 Cholesky of the core, one-sided
+    # Jacobi with R in global memory
+    torch, api, ctx = env
+    n = 64
+    h = gaussian_kernel(9, 1.5)
+    tdt = torch.float64 if dt == "f64" else torch.float32
+    eps = EPS64 if dt == "f64" else EPS32
+    op = api.Operator(ctx, "blur", n, n, dtype=tdt, kernel=h)
+    opo = O.Operator("blur", n, n, kernel=h)
+    ref = oracle.nystrom.nystrom(_flat_phi(opo, n, n), gaussian_matrix(n * n, ell, 5), eps)
+    Om, Y = api.nys_sketch(ctx, op, ell, seed=5)
+    pc = api.nys_factor(ctx, Om, Y, eps)
+    tol = (1e-9, 1e-8) if dt == "f64" else (1e-4, 1e-3)
+    _check_factor(pc.U.double().cpu().numpy(), pc.S_hat.cpu().numpy(), ref, *tol)
+
+
 @pytest.mark.parametrize("sd,tol", [("f32", 2e-4), ("bf16", 2e-2)])
 def test_factor_full_size_properties(env, sd, tol):
     # the 512 x 512, ell = 200, 25 x 25 sigma 4 sketch in the bench's launch

@@ -75,6 +75,39 @@ def test_radon_apply_adjoint(env, dt, geom):
 
 
 @pytest.mark.parametrize("dt", ["f32", "f64"])
+def test_radon_batch_groups(env, dt):
+    # five images: one group of four (the IB = 4 kernels) and a remainder
+    torch, api, ctx = env
+    n1, n2, na, nb = 40, 56, 17, 81
+    op = api.Operator(ctx, "radon", n1, n2, dtype=getattr(torch, DT[dt]), n_angles=na, n_bins=nb)
+    x = gaussian_probe_like((5, n1, n2), seed=18)
+    s = gaussian_probe_like((5, na, nb), seed=19)
+    tol = 1e-5 if dt == "f32" else 1e-12
+    assert rel(api.op_apply(op, _t(torch, x, dt)).cpu(), O.radon_apply(x, na, nb)) < tol
+    assert rel(api.op_adjoint(op, _t(torch, s, dt)).cpu(), O.radon_adjoint(s, n1, n2)) < tol
+    assert rel(api.op_normal(op, _t(torch, x, dt)).cpu(), O.radon_adjoint(O.radon_apply(x, na, nb), n1, n2)) < tol
+
+
+def test_radon_full_size_properties(env):
+    # the 512 x 512, 720 x 736 geometry: at theta = 0 each bin is a column sum
+    # (u = m - 112 is an integer, so Joseph's weights are exactly 0 and 1), and
+    # <A x, s> = <x, A^T s> in float64 on the host
+    torch, api, ctx = env
+    n, na, nb = 512, 720, 736
+    op = api.Operator(ctx, "radon", n, n, dtype=torch.float32, n_angles=na, n_bins=nb)
+    x = gaussian_probe_like((3, n, n), seed=20).astype(np.float32)
+    s = gaussian_probe_like((3, na, nb), seed=21).astype(np.float32)
+    Ax = api.op_apply(op, torch.from_numpy(x).cuda()).double().cpu().numpy()
+    Ats = api.op_adjoint(op, torch.from_numpy(s).cuda()).double().cpu().numpy()
+    cols = x.astype(np.float64).sum(axis=1)                  # (3, n)
+    assert np.abs(Ax[:, 0, 112:112 + n] - cols).max() <= 1e-4 * np.abs(cols).max()
+    assert np.abs(Ax[:, 0, :112]).max() == 0.0 and np.abs(Ax[:, 0, 112 + n:]).max() == 0.0
+    lhs = float((Ax * s).sum())
+    rhs = float((x * Ats).sum())
+    assert abs(lhs - rhs) <= 1e-5 * np.linalg.norm(Ax) * np.linalg.norm(s)
+
+
+@pytest.mark.parametrize("dt", ["f32", "f64"])
 def test_haar_forward_inverse(env, dt):
     torch, api, ctx = env
     n = 64

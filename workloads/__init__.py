@@ -185,3 +185,38 @@ def degrade(w: Workload, clean_meas: np.ndarray) -> np.ndarray:
     if w.noise == "saltpepper":
         return salt_and_pepper(clean_meas, w.noise_level, w.seed_noise)
     raise ValueError(w.noise)
+
+
+def batch_instances(count: int = 64, seed: int = 51, sizes=(128, 256, 384, 512), ells=(64, 128, 256),
+                    angle_range=(180, 720)):
+    """The batched, differentiated workload: `count` instances, alternately blur (Gaussian sigma ~ U[1, 4], kernel side
+    2 ceil(3 sigma) + 1, noise 0.005, TV lambda 5e-4) and parallel-beam CT
+    (angles ~ U{180..720} over 180 degrees, ceil(sqrt(2) n) + 2 bins, noise 1%
+    of the sinogram maximum, TV lambda 2e-4), each kind cycling through the
+    image sizes, sketch size drawn from `ells`.
+    Returns plain dicts (seeded, no method arithmetic)."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for i in range(count):
+        n = sizes[(i // 2) % len(sizes)]
+        inst = dict(index=i, n=n, ell=int(ells[rng.integers(len(ells))]), seed_phantom=1000 + i,
+                    seed_noise=2000 + i, seed_omega=3000 + i)
+        if i % 2 == 0:
+            sigma = float(rng.uniform(1.0, 4.0))
+            inst.update(op="blur", sigma=sigma, k=2 * int(np.ceil(3 * sigma)) + 1, lam=5e-4, noise=0.005)
+        else:
+            inst.update(op="radon", n_angles=int(rng.integers(angle_range[0], angle_range[1] + 1)),
+                        n_bins=int(np.ceil(np.sqrt(2.0) * n)) + 2, lam=2e-4, noise=0.01)
+        out.append(inst)
+    return out
+
+
+def batch_instance_data(inst: dict, apply_fn) -> tuple:
+    """(x_true, y) of one batched instance: the phantom recipe at its size and
+    the noisy measurements, with apply_fn(x_true) -> A x_true supplied by the
+    caller's operator."""
+    x_true = phantom(inst["n"], 30, inst["seed_phantom"], "ellipse")
+    clean = np.asarray(apply_fn(x_true), dtype=np.float64)
+    scale = inst["noise"] * (float(np.max(np.abs(clean))) if inst["op"] == "radon" else 1.0)
+    return x_true, clean + gaussian_noise(clean.shape, scale, inst["seed_noise"])
+
