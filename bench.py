@@ -101,6 +101,26 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def make_op(api, ctx, w: WL.Workload, dtype):
+    """The workload's forward model through the C ABI."""
+    if w.op == "radon":
+        return api.Operator(ctx, "radon", w.n, w.n, dtype=dtype, n_angles=w.n_angles, n_bins=w.n_bins)
+    return api.Operator(ctx, w.op, w.n, w.n, dtype=dtype, kernel=WL.blur_kernel_for(w), decim=w.decim)
+
+
+def describe(w: WL.Workload) -> dict:
+    if w.op == "radon":
+        model = f"parallel-beam Radon (Joseph), {w.n_angles} angles over 180 deg, {w.n_bins} bins"
+    elif w.op == "blur_decim":
+        model = f"{w.blur_k}x{w.blur_k} Gaussian sigma {w.blur_sigma} periodic + x{w.decim} decimation"
+    else:
+        model = f"{w.blur_k}x{w.blur_k} Gaussian sigma {w.blur_sigma} periodic"
+    reg = {"tv": "anisotropic TV", "hs": "Hessian Schatten-1", "wavelet": "Haar l1"}[w.reg]
+    fit = "quadratic" if w.fit == "l2" else f"Huber delta {w.huber_delta}"
+    return {"workload": w.name, "n": w.n, "operator": model, "reg": reg, "fit": fit, "lambda": w.lam, "ell": w.ell,
+            "n_inner": w.n_inner}
+
+
 # --------------------------------------------------------- native arm -----
 class Native:
     def __init__(self, w: WL.Workload, device: int, sketch_dtype: str):
@@ -110,10 +130,9 @@ class Native:
         self.dev = torch.device("cuda", device)
         self.ctx = api.Context(device)
         self.sd = torch.bfloat16 if sketch_dtype == "bf16" else torch.float32
-        h = WL.blur_kernel_for(w)
-        self.op = api.Operator(self.ctx, "blur", w.n, w.n, dtype=torch.float32, kernel=h)
+        self.op = make_op(api, self.ctx, w, torch.float32)
         x_true = torch.from_numpy(WL.ground_truth(w)).float().to(self.dev)
-        clean = api.op_apply(self.op, x_true.reshape(1, w.n, w.n)).reshape(w.n, w.n).double().cpu().numpy()
+        clean = api.op_apply(self.op, x_true.reshape(1, w.n, w.n)).reshape(self.op.meas_shape).double().cpu().numpy()
         y = WL.degrade(w, clean)
         self.y_host = torch.from_numpy(y).float().pin_memory()
         self.y = self.y_host.to(self.dev)
@@ -121,8 +140,9 @@ class Native:
         self.Y = torch.empty_like(self.Om)
         self.pc = api.Precond(self.ctx, w.n * w.n, w.ell, self.sd)
         self.sketch_factor()
-        self.solver_p = api.Solver(self.ctx, self.op, self.y, "tv", w.lam, pc=self.pc, n_inner=w.n_inner)
-        self.solver_0 = api.Solver(self.ctx, self.op, self.y, "tv", w.lam, pc=None, n_inner=w.n_inner)
+        kw = dict(fit=w.fit, huber_delta=w.huber_delta, n_inner=w.n_inner)
+        self.solver_p = api.Solver(self.ctx, self.op, self.y, w.reg, w.lam, pc=self.pc, **kw)
+        self.solver_0 = api.Solver(self.ctx, self.op, self.y, w.reg, w.lam, pc=None, **kw)
         self.flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=self.dev)   # 256 MB > L2
 
     def sketch_factor(self):
@@ -135,8 +155,9 @@ class Native:
         iterates stall about 6e-4 away from their own limit, so x* must come
         from float64).  Returns (x* as float32, drift of the last quarter)."""
         torch, api, w = self.torch, self.api, self.w
-        op64 = api.Operator(self.ctx, "blur", w.n, w.n, dtype=torch.float64, kernel=WL.blur_kernel_for(w))
-        s64 = api.Solver(self.ctx, op64, self.y.double(), "tv", w.lam, pc=None, n_inner=w.n_inner)
+        op64 = make_op(api, self.ctx, w, torch.float64)
+        s64 = api.Solver(self.ctx, op64, self.y.double(), w.reg, w.lam, pc=None, fit=w.fit, huber_delta=w.huber_delta,
+                         n_inner=w.n_inner)
         s64.step(iters * 3 // 4)
         xa = s64.x().clone()
         Fa = s64.objective()
@@ -239,16 +260,18 @@ class Native:
         on the context's stream, right after the timed region."""
         torch, w = self.torch, self.w
         N = w.n * w.n
+        G = 3 if w.reg == "hs" else 2
         s = torch.rand(w.n, w.n, dtype=torch.float32, device=self.dev)
-        Q = torch.zeros(2, w.n, w.n, dtype=torch.float32, device=self.dev)
+        Q = torch.zeros(G, w.n, w.n, dtype=torch.float32, device=self.dev)
         out = torch.empty_like(s)
         lb = 0.9 * w.lam
-        ms = self._events_ms(lambda: self.api.prox_tv(self.ctx, self.pc, lb, w.n_inner, s, Q=Q, out=out), reps)
+        fn = self.api.prox_hs if w.reg == "hs" else self.api.prox_tv
+        ms = self._events_ms(lambda: fn(self.ctx, self.pc, lb, w.n_inner, s, Q=Q, out=out), reps)
         le, ub, f = self.pc.ell_active, (2 if self.sd == torch.bfloat16 else 4), 4
-        lt_utz = 2 * N * f + le * N * ub + N * f            # R in, U, g out
+        lt_utz = G * N * f + le * N * ub + N * f            # R in, U, g out
         uc = le * N * ub + 2 * N * f + N * f                 # U, g and s in, x out
-        dual = N * f + 2 * 2 * N * f + 2 * 2 * N * f         # x in, R and Q in and out
-        copies = 3 * 2 * (2 * N * f)                         # the warm start in and out
+        dual = N * f + 2 * G * N * f + 2 * G * N * f         # x in, R and Q in and out
+        copies = 3 * 2 * (G * N * f)                         # the warm start in and out
         total = w.n_inner * (lt_utz + uc + dual) + lt_utz + uc + copies
         steps = w.n_inner + 1
         return ms / steps, total / steps
@@ -307,9 +330,7 @@ def run_native(args, w: WL.Workload):
         "metric": METRIC, "value": round(ms_p, 3), "unit": "ms", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": round(ms_p, 3), "higher_is_better": False, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32 (sketch bf16, core f64)", "data": "synthetic",
-        "config": {"workload": w.name, "n": w.n, "blur": f"{w.blur_k}x{w.blur_k} sigma {w.blur_sigma} periodic",
-                   "reg": "anisotropic TV", "lambda": w.lam, "ell": w.ell, "n_inner": w.n_inner,
-                   "sketch_dtype": args.sketch_dtype, "target_rel_err": TARGET,
+        "config": {**describe(w), "sketch_dtype": args.sketch_dtype, "target_rel_err": TARGET,
                    "l2": "flushed between timed steps (256 MB write)", "parallelism": f"replicas x{world}"},
         "plain_ms": round(ms_0, 3), "speedup_vs_plain": round(ms_0 / ms_p, 3),
         "criterion": "objective gap (F(x^k) - F*)/|F*| <= 1e-3, F* from the float64 run; the iterate error "
@@ -323,7 +344,7 @@ def run_native(args, w: WL.Workload):
                 "d2h_bytes_per_step": w.n * w.n * 4},
         "gpu_launches": int(launches),
         "roofline": {"bound": "hbm",
-                     "kernel": "P-metric TV dual step (lt_utz_kernel + uc_vec_kernel + dual_update_kernel)",
+                     "kernel": f"P-metric {w.reg.upper()} dual step (lt_utz_kernel + uc_vec_kernel + dual_update_kernel)",
                      "achieved": round(achieved, 1), "peak": peaks["hbm_gbs"], "peak_source": peaks["src"],
                      "unit": "GB/s", "frac": round(achieved / peaks["hbm_gbs"], 4),
                      "traffic": DUAL_STEP_TRAFFIC, "bytes_per_step": step_bytes, "ms_per_step": round(step_ms, 5),
@@ -358,8 +379,10 @@ def oracle_sample(w: WL.Workload, k_iters: int, seconds_hint: float = 15.0):
     import oracle
     from oracle import operators as O
     n, ell = w.n, w.ell
-    h = WL.blur_kernel_for(w)
-    opo = O.Operator("blur", n, n, kernel=h)
+    if w.op == "radon":
+        opo = O.Operator("radon", n, n, n_angles=w.n_angles, n_bins=w.n_bins)
+    else:
+        opo = O.Operator(w.op, n, n, kernel=WL.blur_kernel_for(w), decim=w.decim)
     rng = np.random.default_rng(0)
     t = time.perf_counter
     # sketch: Phi on 2 probe columns
@@ -376,7 +399,7 @@ def oracle_sample(w: WL.Workload, k_iters: int, seconds_hint: float = 15.0):
     P = oracle.nystrom.Precond(r["U"], np.linspace(1.0, 0.5, ell))
     x_true = WL.ground_truth(w)
     y = WL.degrade(w, opo.apply(x_true))
-    prob = oracle.wapg.Problem(opo, y, w.lam, "tv")
+    prob = oracle.wapg.Problem(opo, y, w.lam, w.reg, fit=w.fit, huber_delta=w.huber_delta)
     # one power-iteration step and one WAPG iteration
     z = rng.standard_normal((n, n))
     a = t()
@@ -425,7 +448,8 @@ def main():
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["native", "reference"], default="native")
-    ap.add_argument("--workload", default=WL.DEBLUR512.name, choices=sorted(WL.PRESETS))
+    ap.add_argument("--workload", default=WL.DEBLUR512.name,
+                    choices=sorted(k for k, v in WL.PRESETS.items() if v.reg != "wavelet"))
     ap.add_argument("--sketch-dtype", choices=["bf16", "f32"], default="bf16")
     ap.add_argument("--ell", type=int, default=0, help="override the sketch size")
     ap.add_argument("--ref-iters", type=int, default=20000)
