@@ -20,6 +20,7 @@
 #include "vec.cuh"
 
 #include <cmath>
+#include <type_traits>
 #include <mutex>
 
 namespace nys {
@@ -173,7 +174,8 @@ __global__ void __launch_bounds__(256) uc_kernel(const TU* __restrict__ U, const
 // lane) and are sized to put several CTAs on every SM.
 constexpr int VCH = 2048;    // pixels per partial-sum chunk
 
-// grid (chunks, column groups): part[b][chunk][j] = sum_{i in chunk} U[j][i] z[i]
+// grid (chunks, column groups): part[b][j][chunk] = sum_{i in chunk} U[j][i] z[i]
+// (column-major per batch image: a column's chunk sums are contiguous)
 template <class TU, class TZ, class TA>
 __global__ void __launch_bounds__(256) utz_vec_kernel(const TU* __restrict__ U, const TZ* __restrict__ z, int64_t N,
                                                       int ell, int jper, TA* __restrict__ part) {
@@ -210,7 +212,7 @@ __global__ void __launch_bounds__(256) utz_vec_kernel(const TU* __restrict__ U, 
                 }
             }
             s = warp_sum(s);
-            if (lane == 0) part[((size_t)blockIdx.z * nchunk + blockIdx.x) * ell + j] = s;
+            if (lane == 0) part[((size_t)blockIdx.z * ell + j) * nchunk + blockIdx.x] = s;
             continue;
         }
         for (int t = lane * V; t < cnt; t += 32 * V) {
@@ -221,7 +223,7 @@ __global__ void __launch_bounds__(256) utz_vec_kernel(const TU* __restrict__ U, 
             for (int k = 0; k < V; ++k) s = fma(u[k], zv[k], s);
         }
         s = warp_sum(s);
-        if (lane == 0) part[((size_t)blockIdx.z * nchunk + blockIdx.x) * ell + j] = s;
+        if (lane == 0) part[((size_t)blockIdx.z * ell + j) * nchunk + blockIdx.x] = s;
     }
 }
 
@@ -242,21 +244,19 @@ int precond_vec(nys_ctx* ctx, const nys_precond* pc, int inverse, const void* z,
     const int jper = (ell + groups - 1) / groups;
     groups = (ell + jper - 1) / jper;
     int st;
-    TA* part = (TA*)scratch(ctx, SLOT_PRECOND, ((size_t)batch * nchunk * ell + (size_t)batch * ell) * sizeof(TA), &st);
+    TA* part = (TA*)scratch(ctx, SLOT_PRECOND, ((size_t)batch * nchunk * ell + 2 * (size_t)batch * ell) * sizeof(TA), &st);
     if (st) return st;
     TA* coef = part + (size_t)batch * nchunk * ell;
+    TA* wbuf = coef + (size_t)batch * ell;
     cudaStream_t s = ctx->stream;
     if (batch > 65535) return fail(ctx, NYS_EINVAL, "precond: batch above 65535");
     utz_vec_kernel<TU, TZ, TA><<<dim3(nchunk, groups, batch), 256, 0, s>>>((const TU*)pc->U, (const TZ*)z, N, ell,
                                                                           jper, part);
     NYS_LAUNCH_CK(ctx);
-    if (sizeof(TA) == 8)
-        coef_vec_kernel<TA, double><<<dim3((ell + 31) / 32, batch), 256, (ell + 256) * sizeof(TA), s>>>(
-            part, nchunk, ell, pc->ell, inverse, (const double*)pv->M64, (const double*)pv->d, coef);
-    else
-        coef_vec_kernel<TA, float><<<dim3((ell + 31) / 32, batch), 256, (ell + 256) * sizeof(TA), s>>>(
-            part, nchunk, ell, pc->ell, inverse, (const float*)pv->M32, (const float*)pv->d32, coef);
-    NYS_LAUNCH_CK(ctx);
+    using TM = typename std::conditional<sizeof(TA) == 8, double, float>::type;
+    const TM* Mp = sizeof(TA) == 8 ? (const TM*)pv->M64 : (const TM*)pv->M32;
+    const TM* dp = sizeof(TA) == 8 ? (const TM*)pv->d : (const TM*)pv->d32;
+    if ((st = coef_run<TA, TM>(ctx, part, nchunk, ell, pc->ell, inverse, Mp, dp, coef, batch, wbuf))) return st;
     constexpr int P = 32 * V;
     const size_t sm = (((size_t)ell + 3) & ~size_t(3)) * sizeof(TA) + (size_t)8 * P * sizeof(TA);
     uc_vec_kernel<TU, TZ, TA><<<dim3((unsigned)((N + P - 1) / P), batch), 256, sm, s>>>(

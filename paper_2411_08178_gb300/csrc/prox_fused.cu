@@ -26,7 +26,7 @@ namespace {
 constexpr int FCH = 1024;   // pixels per partial-sum chunk
 constexpr int COUNTER_PROX = 1;
 
-template <class TU, class T, class TA, class TM, int REG>
+template <class TU, class T, class TA, class TM, int REG, bool LAST>
 __global__ void __launch_bounds__(256) lt_utz_kernel(const T* __restrict__ R, int n1, int n2,
                                                      const TU* __restrict__ U, int le, int ldm,
                                                      const TM* __restrict__ M, T* __restrict__ g,
@@ -104,7 +104,7 @@ __global__ void __launch_bounds__(256) lt_utz_kernel(const T* __restrict__ R, in
             if (two) part[(size_t)(j + 8) * gridDim.x + blockIdx.x] = s1;
         }
     }
-    last_cta_coef_t<TA, TM>(part, le, ldm, M, coef, counter, sm);
+    if (LAST) last_cta_coef_t<TA, TM>(part, le, ldm, M, coef, counter, sm);
 }
 
 template <class TU, class T, class TA, int REG>
@@ -125,9 +125,13 @@ int fused_typed(nys_ctx* ctx, const nys_precond* pc, double lb, int n_inner, int
     T* Qp = R + G * N;
     T* g = Qp + G * N;
     T* x = g + N;
-    TA* part = (TA*)scratch(ctx, SLOT_PRECOND, ((size_t)nchunk * std::max(le, 1) + std::max(le, 1)) * sizeof(TA), &st);
+    TA* part = (TA*)scratch(ctx, SLOT_PRECOND, ((size_t)nchunk * std::max(le, 1) + 2 * std::max(le, 1)) * sizeof(TA), &st);
     if (st) return st;
     TA* coef = part + (size_t)nchunk * std::max(le, 1);
+    TA* wbuf = coef + std::max(le, 1);
+    // small active sets: the last CTA of lt_utz forms M w; large ones: two
+    // passes over many CTAs (reduce_cols, mw)
+    const bool last = le <= 64;
     cudaStream_t sm = ctx->stream;
     NYS_CK(ctx, cudaMemcpyAsync(R, Q, sizeof(T) * G * N, cudaMemcpyDeviceToDevice, sm));
     NYS_CK(ctx, cudaMemcpyAsync(Qp, Q, sizeof(T) * G * N, cudaMemcpyDeviceToDevice, sm));
@@ -141,9 +145,17 @@ int fused_typed(nys_ctx* ctx, const nys_precond* pc, double lb, int n_inner, int
     unsigned* counter = ctx->counters + COUNTER_PROX;
     // x (or out) = s - lb P^{-1} L^T Rin
     auto xfn = [&](const T* Rin, T* dst) -> int {
-        lt_utz_kernel<TU, T, TA, TM, REG><<<nchunk, 256, lsm, sm>>>(Rin, n1, n2, (const TU*)pc->U, le, pc->ell, M, g,
-                                                                      part, coef, counter);
-        NYS_LAUNCH_CK(ctx);
+        if (last) {
+            lt_utz_kernel<TU, T, TA, TM, REG, true><<<nchunk, 256, lsm, sm>>>(Rin, n1, n2, (const TU*)pc->U, le,
+                                                                                pc->ell, M, g, part, coef, counter);
+            NYS_LAUNCH_CK(ctx);
+        } else {
+            lt_utz_kernel<TU, T, TA, TM, REG, false><<<nchunk, 256, 16, sm>>>(Rin, n1, n2, (const TU*)pc->U, le,
+                                                                                pc->ell, M, g, part, coef, counter);
+            NYS_LAUNCH_CK(ctx);
+            int st2 = coef_run<TA, TM>(ctx, part, nchunk, le, pc->ell, 1, M, (const TM*)nullptr, coef, 1, wbuf);
+            if (st2) return st2;
+        }
         uc_vec_kernel<TU, T, TA><<<dim3(ug, 1), 256, usm, sm>>>((const TU*)pc->U, g, N, le, coef, TA(-1), dst, s,
                                                                 (TA)(-lb));
         NYS_LAUNCH_CK(ctx);

@@ -444,7 +444,7 @@ int create_typed(nys_solver* S, const void* y) {
     if (S->pc) {
         // the largest of the two P^{-1} layouts (chunks of 1024 or 2048 pixels)
         const size_t nbp = (size_t)((N + 1023) / 1024);
-        if (!scratch(ctx, SLOT_PRECOND, (nbp * ell + ell) * es, &st)) return st;
+        if (!scratch(ctx, SLOT_PRECOND, (nbp * ell + 2 * ell) * es, &st)) return st;
         if (S->d.reg == NYS_REG_WAVELET) {
             // the first ssn_run call sizes SLOT_SSN; run one prox now
             if ((st = ssn_run<T>(ctx, S->pc, 0.0, N, (const T*)S->X[0], (T*)S->X[1], nullptr, 1, 1, false, nullptr)))

@@ -58,87 +58,6 @@ __device__ __forceinline__ void lds_vec<double, 2>(const double* p, double (&v)[
     v[0] = a.x, v[1] = a.y;
 }
 
-// w[j] = sum over the nb chunk partials part[c][j] (j < le), in a fixed order,
-// by all threads of the CTA: thread t sums column t % le over the chunks
-// c = t / le (mod blockDim / le), four loads in flight, and the groups meet in
-// shared memory.  red needs blockDim.x entries.  Ends with __syncthreads().
-template <class TA>
-__device__ __forceinline__ void reduce_partials(const TA* __restrict__ part, int nb, int le, TA* w, TA* red) {
-    const int nt = blockDim.x, t = threadIdx.x;
-    if (le <= nt) {
-        const int ng = nt / le;
-        TA acc = TA(0);
-        if (t < ng * le) {
-            const int j = t % le, grp = t / le;
-            TA a[8];
-#pragma unroll
-            for (int q = 0; q < 8; ++q) a[q] = TA(0);
-            int c = grp;
-            for (; c + 7 * ng < nb; c += 8 * ng) {
-#pragma unroll
-                for (int q = 0; q < 8; ++q) a[q] += __ldcg(part + (size_t)(c + q * ng) * le + j);
-            }
-            for (; c < nb; c += ng) a[0] += __ldcg(part + (size_t)c * le + j);
-            acc = ((a[0] + a[1]) + (a[2] + a[3])) + ((a[4] + a[5]) + (a[6] + a[7]));
-        }
-        red[t] = acc;
-        __syncthreads();
-        if (t < le) {
-            TA s = TA(0);
-            for (int g = 0; g < ng; ++g) s += red[g * le + t];
-            w[t] = s;
-        }
-    } else {
-        for (int j = t; j < le; j += nt) {
-            TA a0 = TA(0), a1 = TA(0), a2 = TA(0), a3 = TA(0);
-            int c = 0;
-            for (; c + 4 <= nb; c += 4) {
-                a0 += __ldcg(part + (size_t)c * le + j);
-                a1 += __ldcg(part + (size_t)(c + 1) * le + j);
-                a2 += __ldcg(part + (size_t)(c + 2) * le + j);
-                a3 += __ldcg(part + (size_t)(c + 3) * le + j);
-            }
-            for (; c < nb; ++c) a0 += __ldcg(part + (size_t)c * le + j);
-            w[j] = (a0 + a1) + (a2 + a3);
-        }
-    }
-    __syncthreads();
-}
-
-// coef[r] = inverse ? sum_k M[r][k] w[k] : d[r] w[r] for r in [r0, r1), one
-// warp per row
-template <class TA, class TM>
-__device__ __forceinline__ void coef_rows(const TA* w, int le, int ldm, int inverse, const TM* __restrict__ M,
-                                          const TM* __restrict__ d, int r0, int r1, TA* __restrict__ coef) {
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
-    for (int r = r0 + warp; r < r1; r += nw) {
-        TA s;
-        if (inverse) {
-            s = TA(0);
-            for (int k = lane; k < le; k += 32) s = fma((TA)M[(size_t)r * ldm + k], w[k], s);
-            s = warp_sum(s);
-        } else {
-            s = (TA)d[r] * w[r];
-        }
-        if (lane == 0) coef[r] = s;
-    }
-}
-
-// coef[b][r] for the 32 rows r of this CTA (batch b = blockIdx.y); every CTA
-// rebuilds w.  Dynamic shared memory: (le + blockDim.x) TA.
-template <class TA, class TM>
-__global__ void __launch_bounds__(256) coef_vec_kernel(const TA* __restrict__ part, int nb, int le, int ldm,
-                                                       int inverse, const TM* __restrict__ M,
-                                                       const TM* __restrict__ d, TA* __restrict__ coef) {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    TA* w = reinterpret_cast<TA*>(smem_raw);
-    TA* red = w + le;
-    const int b = blockIdx.y;
-    reduce_partials<TA>(part + (size_t)b * nb * le, nb, le, w, red);
-    const int r0 = blockIdx.x * 32;
-    coef_rows<TA, TM>(w, le, ldm, inverse, M, d, r0, min(le, r0 + 32), coef + (size_t)b * le);
-}
-
 // w[j] = sum_c partT[j * nb + c] (column-major partials: column j's chunk sums
 // are contiguous), one warp per column, all of a warp's columns loaded before
 // they are summed (four at a time), fixed order.  Ends with __syncthreads().
@@ -171,6 +90,95 @@ __device__ __forceinline__ void reduce_partials_t(const TA* __restrict__ partT, 
         }
     }
     __syncthreads();
+}
+
+// coef[r] = inverse ? sum_k M[r][k] w[k] : d[r] w[r] for r in [r0, r1), one
+// warp per row
+template <class TA, class TM>
+__device__ __forceinline__ void coef_rows(const TA* w, int le, int ldm, int inverse, const TM* __restrict__ M,
+                                          const TM* __restrict__ d, int r0, int r1, TA* __restrict__ coef) {
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+    for (int r = r0 + warp; r < r1; r += nw) {
+        TA s;
+        if (inverse) {
+            s = TA(0);
+            for (int k = lane; k < le; k += 32) s = fma((TA)M[(size_t)r * ldm + k], w[k], s);
+            s = warp_sum(s);
+        } else {
+            s = (TA)d[r] * w[r];
+        }
+        if (lane == 0) coef[r] = s;
+    }
+}
+
+// coef[b][r] for the 32 rows r of this CTA (batch b = blockIdx.y); every CTA
+// rebuilds w from the column-major partials part[b][j][c].  Dynamic shared
+// memory: le TA.  For small le (the rebuild is le x nb loads per CTA).
+template <class TA, class TM>
+__global__ void __launch_bounds__(256) coef_vec_kernel(const TA* __restrict__ part, int nb, int le, int ldm,
+                                                       int inverse, const TM* __restrict__ M,
+                                                       const TM* __restrict__ d, TA* __restrict__ coef) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    TA* w = reinterpret_cast<TA*>(smem_raw);
+    const int b = blockIdx.y;
+    reduce_partials_t<TA>(part + (size_t)b * nb * le, nb, le, w);
+    const int r0 = blockIdx.x * 32;
+    coef_rows<TA, TM>(w, le, ldm, inverse, M, d, r0, min(le, r0 + 32), coef + (size_t)b * le);
+}
+
+// Large le, two passes spread over many CTAs.  reduce_cols: w[b][j] =
+// sum_c part[b][j][c], one warp per column (8 per CTA); mw: coef[b][r] =
+// inverse ? sum_k M[r][k] w[b][k] : d[r] w[b][r], one warp per row.
+template <class TA>
+__global__ void __launch_bounds__(256) reduce_cols_kernel(const TA* __restrict__ part, int nb, int le,
+                                                          TA* __restrict__ w) {
+    const int j = blockIdx.x * 8 + (threadIdx.x >> 5), lane = threadIdx.x & 31, b = blockIdx.y;
+    if (j >= le) return;
+    const TA* p = part + ((size_t)b * le + j) * nb;
+    TA a[8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) a[q] = TA(0);
+    for (int c0 = 0; c0 < nb; c0 += 256) {
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+            const int c = c0 + q * 32 + lane;
+            if (c < nb) a[q] += p[c];
+        }
+    }
+    TA s = ((a[0] + a[1]) + (a[2] + a[3])) + ((a[4] + a[5]) + (a[6] + a[7]));
+    s = warp_sum(s);
+    if (lane == 0) w[(size_t)b * le + j] = s;
+}
+
+template <class TA, class TM>
+__global__ void __launch_bounds__(256) mw_kernel(const TM* __restrict__ M, int ldm, int inverse,
+                                                 const TM* __restrict__ d, const TA* __restrict__ w, int le,
+                                                 TA* __restrict__ coef) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    TA* ws = reinterpret_cast<TA*>(smem_raw);
+    const int b = blockIdx.y;
+    for (int k = threadIdx.x; k < le; k += blockDim.x) ws[k] = w[(size_t)b * le + k];
+    __syncthreads();
+    coef_rows<TA, TM>(ws, le, ldm, inverse, M, d, blockIdx.x * 8, min(le, blockIdx.x * 8 + 8), coef + (size_t)b * le);
+}
+
+// c = M w (or d .* w) from column-major partials, choosing the one-kernel
+// path for small le and the two-kernel path otherwise
+template <class TA, class TM>
+int coef_run(nys_ctx* ctx, const TA* part, int nb, int le, int ldm, int inverse, const TM* M, const TM* d,
+             TA* coef, int batch, TA* wbuf = nullptr) {
+    cudaStream_t s = ctx->stream;
+    if (le <= 64 || !wbuf) {
+        coef_vec_kernel<TA, TM><<<dim3((le + 31) / 32, batch), 256, le * sizeof(TA), s>>>(part, nb, le, ldm, inverse,
+                                                                                         M, d, coef);
+        NYS_LAUNCH_CK(ctx);
+        return NYS_OK;
+    }
+    reduce_cols_kernel<TA><<<dim3((le + 7) / 8, batch), 256, 0, s>>>(part, nb, le, wbuf);
+    NYS_LAUNCH_CK(ctx);
+    mw_kernel<TA, TM><<<dim3((le + 7) / 8, batch), 256, le * sizeof(TA), s>>>(M, ldm, inverse, d, wbuf, le, coef);
+    NYS_LAUNCH_CK(ctx);
+    return NYS_OK;
 }
 
 // End of a 1-D partial-sum pass whose CTAs wrote column-major partials
@@ -212,26 +220,6 @@ __device__ __forceinline__ void last_cta_coef_t(const TA* partT, int le, int ldm
             coef[r] = (a[0] + a[1]) + (a[2] + a[3]);
         }
     }
-    if (threadIdx.x == 0) *counter = 0u;
-}
-
-// End of a 1-D partial-sum pass: each CTA has written its row of `part`; the
-// last CTA to arrive (counted on *counter, which is zero before the launch
-// and reset here) reduces all rows and writes coef.  No CTA waits for
-// another.  sm: (le + blockDim.x) TA of shared memory.
-template <class TA, class TM>
-__device__ __forceinline__ void last_cta_coef(const TA* part, int nb, int le, int ldm, int inverse,
-                                              const TM* __restrict__ M, const TM* __restrict__ d,
-                                              TA* __restrict__ coef, unsigned* counter, TA* sm) {
-    __shared__ unsigned is_last;
-    __threadfence();
-    __syncthreads();
-    if (threadIdx.x == 0) is_last = atomicAdd(counter, 1u) == gridDim.x - 1;
-    __syncthreads();
-    if (!is_last) return;
-    __threadfence();
-    reduce_partials<TA>(part, nb, le, sm, sm + le);
-    coef_rows<TA, TM>(sm, le, ldm, inverse, M, d, 0, le, coef);
     if (threadIdx.x == 0) *counter = 0u;
 }
 

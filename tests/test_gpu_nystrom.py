@@ -227,6 +227,71 @@ def test_prox_dual_matches_oracle(env, dt, reg, precond, shape):
     assert rel(x2.cpu(), x2_ref) < tol * 10
 
 
+@pytest.mark.parametrize("ell,reg", [(16, "tv"), (16, "hs"), (96, "tv")])
+def test_prox_fused_bf16_matches_composed(env, ell, reg):
+    # the fused dual step with a bf16 U (last-CTA coefficients for
+    # ell_active <= 64, two extra passes otherwise) against the same
+    # iteration composed from the standalone
+    # P^-1 apply and torch stencils, on the same stored U
+    torch, api, ctx = env
+    n = 64
+    h = gaussian_kernel(9, 1.5)
+    op = api.Operator(ctx, "blur", n, n, dtype=torch.float32, kernel=h)
+    Om, Y = api.nys_sketch(ctx, op, ell, seed=6, store_dtype=torch.bfloat16)
+    pc = api.nys_factor(ctx, Om, Y, EPS32, u_dtype=torch.bfloat16)
+    pc.setup(0.0, False)
+    s = torch.from_numpy(phantom(n, 6, 2, "mixed")).float().cuda()
+    lb, n_inner = 0.02, 12
+    fn = api.prox_tv if reg == "tv" else api.prox_hs
+    x, Q = fn(ctx, pc, lb, n_inner, s)
+    # composed reference
+    sh = lambda a, di, dj: torch.roll(a, shifts=(-di, -dj), dims=(-2, -1))
+    if reg == "tv":
+        L = lambda v: torch.stack([v - sh(v, -1, 0), v - sh(v, 0, -1)])
+        Lt = lambda q: (q[0] - sh(q[0], 1, 0)) + (q[1] - sh(q[1], 0, 1))
+        proj = lambda z: z.clamp(-1.0, 1.0)
+        normL2 = 8.0
+    else:
+        def L(v):
+            return torch.stack([sh(v, -1, 0) - 2 * v + sh(v, 1, 0),
+                                0.25 * (sh(v, 1, 1) - sh(v, 1, -1) - sh(v, -1, 1) + sh(v, -1, -1)),
+                                sh(v, 0, -1) - 2 * v + sh(v, 0, 1)])
+
+        def Lt(q):
+            a11 = sh(q[0], -1, 0) - 2 * q[0] + sh(q[0], 1, 0)
+            a22 = sh(q[2], 0, -1) - 2 * q[2] + sh(q[2], 0, 1)
+            a12 = 0.25 * (sh(q[1], 1, 1) - sh(q[1], 1, -1) - sh(q[1], -1, 1) + sh(q[1], -1, -1))
+            return a11 + 2 * a12 + a22
+
+        def proj(z):
+            a, b, c = z[0].double(), z[1].double(), z[2].double()
+            m, hh = 0.5 * (a + c), 0.5 * (a - c)
+            r = torch.sqrt(hh * hh + b * b)
+            l1, l2 = (m + r).clamp(-1, 1), (m - r).clamp(-1, 1)
+            mp, dp = 0.5 * (l1 + l2), 0.5 * (l1 - l2)
+            rs = torch.where(r > 0, r, torch.ones_like(r))
+            pa = torch.where(r > 0, mp + dp * hh / rs, mp)
+            pb = torch.where(r > 0, dp * b / rs, torch.zeros_like(r))
+            pc_ = torch.where(r > 0, mp - dp * hh / rs, mp)
+            return torch.stack([pa, pb, pc_]).float()
+        normL2 = 32.0
+    pinv = lambda z: api.precond_apply(ctx, pc, z.contiguous().reshape(-1), True).reshape(n, n)
+    G = 2 if reg == "tv" else 3
+    Qp = torch.zeros(G, n, n, device="cuda")
+    R = Qp.clone()
+    t = 1.0
+    for _ in range(n_inner):
+        xr = s - lb * pinv(Lt(R))
+        Qn = proj(R + L(xr) / (lb * normL2))
+        tn = 0.5 * (1.0 + (1.0 + 4.0 * t * t) ** 0.5)
+        R = Qn + ((t - 1.0) / tn) * (Qn - Qp)
+        Qp, t = Qn, tn
+    xr = s - lb * pinv(Lt(Qp))
+    assert ell - 2 <= pc.ell_active < ell      # the last column has d = 0 without the sqrt heuristic
+    assert rel(x.cpu(), xr.cpu()) < 1e-5
+    assert rel(Q.cpu(), Qp.cpu()) < 1e-4
+
+
 def test_prox_wavelet_matches_oracle(env):
     torch, api, ctx = env
     n, ell = 64, 32
