@@ -442,7 +442,8 @@ int create_typed(nys_solver* S, const void* y) {
         if (!scratch(ctx, SLOT_PROX, ((size_t)2 * S->G * N + 2 * N) * es, &st)) return st;
     }
     if (S->pc) {
-        // the largest of the two P^{-1} layouts (chunks of 1024 or 2048 pixels)
+        // the largest of the P^{-1} / prox partial-sum layouts (chunks of 1024 or
+        // 2048 pixels)
         const size_t nbp = (size_t)((N + 1023) / 1024);
         if (!scratch(ctx, SLOT_PRECOND, (nbp * ell + 2 * ell) * es, &st)) return st;
         if (S->d.reg == NYS_REG_WAVELET) {
