@@ -323,59 +323,88 @@ __global__ void __launch_bounds__(1024) jacobi_smem_kernel(const T* __restrict__
 // so a pair's inner products and its update are stride-1.  The rotation log
 // has the two-sided kernel's format.  status_out = 1 (and nothing logged) if
 // the Cholesky meets a non-positive pivot, so that the two-sided kernel runs.
+// 16-byte vectors of the working type (float4 / double2)
+template <class T> struct JV;
+template <> struct JV<float> { using type = float4; static constexpr int n = 4; };
+template <> struct JV<double> { using type = double2; static constexpr int n = 2; };
+__device__ __forceinline__ float vdot(float4 x, float4 y) { return x.x * y.x + x.y * y.y + x.z * y.z + x.w * y.w; }
+__device__ __forceinline__ double vdot(double2 x, double2 y) { return x.x * y.x + x.y * y.y; }
+__device__ __forceinline__ float4 vrot(float4 x, float4 y, float c, float s) {
+    return make_float4(c * x.x - s * y.x, c * x.y - s * y.y, c * x.z - s * y.z, c * x.w - s * y.w);
+}
+__device__ __forceinline__ double2 vrot(double2 x, double2 y, double c, double s) {
+    return make_double2(c * x.x - s * y.x, c * x.y - s * y.y);
+}
+
+// column pitch of R: a whole number of 16-byte vectors (the rows beyond n are
+// zero), plus one vector in shared memory to spread the columns over banks
+__host__ __device__ inline int jac_pitch(int n, bool global) { return ((n + 3) & ~3) + (global ? 0 : 4); }
+
 template <class T, bool GLOBAL>
 __global__ void __launch_bounds__(1024) jacobi_1s_kernel(const T* __restrict__ Gin, T* __restrict__ Rg, int n, int nreal,
                                                          int max_sweeps, int2* __restrict__ logpq,
                                                          T* __restrict__ logcs, int* __restrict__ rounds_out,
                                                          int* __restrict__ sweeps_out, int* __restrict__ status_out) {
+    using VT = typename JV<T>::type;
+    constexpr int VW = JV<T>::n;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int h = n / 2;
-    // column j at R + j * pitch: shared memory (pitch n + 1) with the Cholesky
-    // done here, or global memory (pitch n) holding the factor written by
-    // chol_upper_kernel, which also set *status_out
-    const int pitch = GLOBAL ? n : n + 1;
+    // column j at R + j * pitch: shared memory with the Cholesky done here, or
+    // global memory holding the factor written by chol_upper_kernel (which
+    // also set *status_out)
+    const int pitch = jac_pitch(n, GLOBAL);
     T* R = GLOBAL ? Rg : reinterpret_cast<T*>(smem_raw);
+    T* nrm = GLOBAL ? reinterpret_cast<T*>(smem_raw) : R + (size_t)n * pitch;   // n column norms
+    T* rowk = nrm + n;                                                          // n (Cholesky row)
     __shared__ int bad;
     if (GLOBAL) {
         if (*status_out != 0) return;
     } else {
-    // load G (symmetric) into R as column-major, pad index -> identity
-    for (int t = threadIdx.x; t < n * n; t += blockDim.x) {
-        const int i = t / n, j = t % n;
-        T g = Gin[t];
-        if (i >= nreal || j >= nreal) g = (i == j) ? T(1) : T(0);
-        R[j * pitch + i] = g;
-    }
-    if (threadIdx.x == 0) bad = 0;
-    __syncthreads();
-    // in-place Cholesky, upper factor: R[k][j] for j >= k (column j holds rows 0..j)
-    for (int k = 0; k < n; ++k) {
-        if (threadIdx.x == 0) {
-            const T d = R[k * pitch + k];
-            if (!(d > T(0))) bad = 1;
-            else R[k * pitch + k] = sqrt(d);
+        // load G (symmetric) into R as column-major, pad index -> identity, pad rows -> 0
+        for (int t = threadIdx.x; t < n * pitch; t += blockDim.x) {
+            const int j = t / pitch, i = t % pitch;
+            T g = T(0);
+            if (i < n) {
+                g = Gin[(size_t)i * n + j];
+                if (i >= nreal || j >= nreal) g = (i == j) ? T(1) : T(0);
+            }
+            R[t] = g;
         }
+        if (threadIdx.x == 0) bad = 0;
         __syncthreads();
-        if (bad) break;
-        const T rkk = R[k * pitch + k];
-        for (int j = k + 1 + threadIdx.x; j < n; j += blockDim.x) R[j * pitch + k] /= rkk;   // row k, columns j > k
-        __syncthreads();
-        const int m = n - k - 1;
-        for (int t = threadIdx.x; t < m * m; t += blockDim.x) {
-            const int i = k + 1 + t / m, j = k + 1 + t % m;
-            if (i <= j) R[j * pitch + i] -= R[i * pitch + k] * R[j * pitch + k];
+        // in-place Cholesky, upper factor: R(k, j) for j >= k (column j holds rows 0..j)
+        for (int k = 0; k < n; ++k) {
+            if (threadIdx.x == 0) {
+                const T d = R[k * pitch + k];
+                if (!(d > T(0))) bad = 1;
+                else R[k * pitch + k] = sqrt(d);
+            }
+            __syncthreads();
+            if (bad) break;
+            const T rkk = R[k * pitch + k];
+            for (int j = k + 1 + threadIdx.x; j < n; j += blockDim.x) {   // row k, columns j > k
+                const T v = R[j * pitch + k] / rkk;
+                R[j * pitch + k] = v;
+                rowk[j] = v;
+            }
+            __syncthreads();
+            // trailing update R(i, j) -= R(k, i) R(k, j), i <= j, rows fastest
+            const int m = n - k - 1;
+            for (int t = threadIdx.x; t < m * m; t += blockDim.x) {
+                const int j = k + 1 + t / m, i = k + 1 + t % m;
+                if (i <= j) R[j * pitch + i] -= rowk[i] * rowk[j];
+            }
+            __syncthreads();
         }
-        __syncthreads();
+        if (bad) {
+            if (threadIdx.x == 0) *status_out = 1;
+            return;
+        }
+        for (int t = threadIdx.x; t < n * n; t += blockDim.x) {
+            const int i = t % n, j = t / n;   // zero the strict lower part
+            if (i > j) R[j * pitch + i] = T(0);
+        }
     }
-    if (bad) {
-        if (threadIdx.x == 0) *status_out = 1;
-        return;
-    }
-    for (int t = threadIdx.x; t < n * n; t += blockDim.x) {
-        const int i = t % n, j = t / n;   // zero the strict lower part
-        if (i > j) R[j * pitch + i] = T(0);
-    }
-    }   // shared-memory set-up
     __syncthreads();
     // Threshold: a pair counts as orthogonal once |x.y| <= tol sqrt(|x|^2 |y|^2)
     // with tol = sqrt(n) eps; eigenvalues are recomputed afterwards in FP64 from
@@ -383,14 +412,30 @@ __global__ void __launch_bounds__(1024) jacobi_1s_kernel(const T* __restrict__ G
     const T tol = (sizeof(T) == 8 ? T(2.2e-16) : T(1.2e-7)) * sqrt(T(n));
     // gs threads per column pair (a power of two <= 32), every pair of a round
     // in flight at once; pairs by the circle method: player n-1 is fixed,
-    // players 0..n-2 rotate, round r pairs (n-1, r) and (r+k, r-k) mod (n-1)
+    // players 0..n-2 rotate, round r pairs (n-1, r) and (r+k, r-k) mod (n-1).
+    // Column norms are kept up to date (|x'|^2 = |x|^2 - t c, |y'|^2 =
+    // |y|^2 + t c for the rotation below) and recomputed at every sweep, so a
+    // pair needs one inner product; columns move as 16-byte vectors.
     int gs = 32;
     while (gs > 1 && gs * h > (int)blockDim.x) gs >>= 1;
     const int ngroups = blockDim.x / gs;
     const int g = threadIdx.x / gs, gl = threadIdx.x % gs;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarps = blockDim.x >> 5;
+    const int nv = pitch / VW;   // vectors per column (pad rows are zero)
     const int m1 = n - 1;
     int sweep = 0, round_total = 0;
     for (; sweep < max_sweeps; ++sweep) {
+        for (int j = warp; j < n; j += nwarps) {
+            const VT* wj = reinterpret_cast<const VT*>(R + (size_t)j * pitch);
+            T a = T(0);
+            for (int v = lane; v < nv; v += 32) {
+                const VT x = wj[v];
+                a += vdot(x, x);
+            }
+            a = warp_sum(a);
+            if (lane == 0) nrm[j] = a;
+        }
+        __syncthreads();
         int rotated = 0;
         for (int round = 0; round < m1; ++round, ++round_total) {
             for (int k0 = 0; k0 < h; k0 += ngroups) {
@@ -403,35 +448,31 @@ __global__ void __launch_bounds__(1024) jacobi_1s_kernel(const T* __restrict__ G
                     p = min(u, w);
                     q = max(u, w);
                 }
-                T* wp = R + p * pitch;
-                T* wq = R + q * pitch;
-                T a = T(0), b = T(0), c = T(0);
+                VT* wp = reinterpret_cast<VT*>(R + (size_t)p * pitch);
+                VT* wq = reinterpret_cast<VT*>(R + (size_t)q * pitch);
+                T c = T(0);
                 if (active) {
-#pragma unroll 8
-                    for (int i = gl; i < n; i += gs) {
-                        const T x = wp[i], y = wq[i];
-                        a = fma(x, x, a);
-                        b = fma(y, y, b);
-                        c = fma(x, y, c);
-                    }
+#pragma unroll 4
+                    for (int v = gl; v < nv; v += gs) c += vdot(wp[v], wq[v]);
                 }
-                for (int o = gs >> 1; o > 0; o >>= 1) {
-                    a += __shfl_xor_sync(0xffffffffu, a, o);
-                    b += __shfl_xor_sync(0xffffffffu, b, o);
-                    c += __shfl_xor_sync(0xffffffffu, c, o);
-                }
+                for (int o = gs >> 1; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
                 if (!active) continue;
+                const T a = nrm[p], b = nrm[q];
                 T cs = T(1), sn = T(0);
                 if (q < nreal && c != T(0) && fabs(c) > tol * sqrt(a * b)) {
                     const T zeta = (b - a) / (T(2) * c);
                     const T t = (zeta >= T(0) ? T(1) : T(-1)) / (fabs(zeta) + sqrt(T(1) + zeta * zeta));
                     cs = T(1) / sqrt(T(1) + t * t);
                     sn = t * cs;
-#pragma unroll 8
-                    for (int i = gl; i < n; i += gs) {
-                        const T x = wp[i], y = wq[i];
-                        wp[i] = cs * x - sn * y;
-                        wq[i] = sn * x + cs * y;
+#pragma unroll 4
+                    for (int v = gl; v < nv; v += gs) {
+                        const VT x = wp[v], y = wq[v];
+                        wp[v] = vrot(x, y, cs, sn);
+                        wq[v] = vrot(y, x, cs, -sn);   // sn x + cs y
+                    }
+                    if (gl == 0) {
+                        nrm[p] = a - t * c;
+                        nrm[q] = b + t * c;
                     }
                     rotated = 1;
                 }
@@ -458,7 +499,8 @@ __global__ void __launch_bounds__(1024) jacobi_1s_kernel(const T* __restrict__ G
 
 // Set-up of the global-memory one-sided Jacobi: work (n x n float64) = G
 // padded with the identity, its float64 Cholesky L (one CTA), and R = L^T in
-// the working type, column-major with pitch n (column j of R is row j of L).
+// the working type, column-major with pitch jac_pitch(n, true) (column j of R
+// is row j of L, zero-padded).
 // *status = 1 if a pivot is not positive; *rounds = 0 until the sweeps log.
 template <class T>
 __global__ void __launch_bounds__(1024) chol_upper_kernel(const double* __restrict__ G, int ell, int n,
@@ -474,9 +516,10 @@ __global__ void __launch_bounds__(1024) chol_upper_kernel(const double* __restri
     const bool ok = block_cholesky(work, n, &flag);
     if (threadIdx.x == 0) *status = ok ? 0 : 1;
     if (!ok) return;
-    for (int t = threadIdx.x; t < n * n; t += blockDim.x) {
-        const int j = t / n, i = t % n;
-        R[t] = (i <= j) ? (T)work[(size_t)j * n + i] : T(0);
+    const int pitch = jac_pitch(n, true);
+    for (int t = threadIdx.x; t < n * pitch; t += blockDim.x) {
+        const int j = t / pitch, i = t % pitch;
+        R[t] = (i <= j && i < n) ? (T)work[(size_t)j * n + i] : T(0);
     }
 }
 
@@ -635,13 +678,17 @@ int sym_eig(nys_ctx* ctx, const double* G, int ell, bool use_f32, const double* 
         const double tol = sizeof(T) == 8 ? 1e-14 : 2e-7;
         const int h = n / 2;
         const size_t smem = sizeof(T) * ((size_t)n * (n + 1) + 2 * (size_t)h) + sizeof(int) * (2 * (size_t)n + 2 * h + 4) + 64;
-        const bool in_smem = smem + 1024 <= 227 * 1024;   // leave room for the kernels' static shared memory
+        const size_t smem1 = sizeof(T) * ((size_t)n * jac_pitch(n, false) + 2 * (size_t)n) + 64;
+        // both kernels of the shared-memory path must fit (leaving room for
+        // their static shared memory)
+        const bool in_smem = smem + 1024 <= 227 * 1024 && smem1 + 1024 <= 227 * 1024;
         // rotations are logged and V is built by many CTAs (rot_apply)
         int st;
         const size_t rounds = (size_t)max_sweeps * (n - 1);
         auto al = [](size_t v) { return (v + 255) & ~size_t(255); };
         const size_t logb = al(rounds * h * (sizeof(int2) + 2 * sizeof(T)));
-        const size_t extra = in_smem ? 0 : al((size_t)n * n * sizeof(double)) + al((size_t)n * n * sizeof(T));
+        const size_t extra =
+            in_smem ? 0 : al((size_t)n * n * sizeof(double)) + al((size_t)n * jac_pitch(n, true) * sizeof(T));
         char* lg = (char*)scratch(ctx, SLOT_EIG, logb + extra + 64, &st);
         if (st) return st;
         int2* logpq = (int2*)lg;
@@ -657,7 +704,6 @@ int sym_eig(nys_ctx* ctx, const double* G, int ell, bool use_f32, const double* 
                                                  (int)smem));
                 attr = smem;
             }
-            const size_t smem1 = sizeof(T) * (size_t)n * (n + 1) + 64;
             static size_t attr1 = 48 * 1024;
             if (smem1 > attr1) {
                 NYS_CK(ctx, cudaFuncSetAttribute(jacobi_1s_kernel<T, false>,
@@ -677,8 +723,9 @@ int sym_eig(nys_ctx* ctx, const double* G, int ell, bool use_f32, const double* 
             T* Rg = (T*)(lg + logb + al((size_t)n * n * sizeof(double)));
             chol_upper_kernel<T><<<1, 1024, 0, s>>>(G, ell, n, w64, Rg, status_dev, rounds_dev);
             NYS_LAUNCH_CK(ctx);
-            jacobi_1s_kernel<T, true><<<1, 1024, 0, s>>>(nullptr, Rg, n, ell, max_sweeps, logpq, logcs, rounds_dev,
-                                                         sweeps_dev, status_dev);
+            jacobi_1s_kernel<T, true><<<1, 1024, 2 * (size_t)n * sizeof(T), s>>>(nullptr, Rg, n, ell, max_sweeps, logpq,
+                                                                                  logcs, rounds_dev, sweeps_dev,
+                                                                                  status_dev);
             NYS_LAUNCH_CK(ctx);
         }
         // staged rounds per pass of rot_apply: as many as fit in 96 KB
