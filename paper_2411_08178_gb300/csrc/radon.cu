@@ -160,7 +160,7 @@ __global__ void __launch_bounds__(256) radon_fwd2_kernel(const TC* __restrict__ 
 // adjoint: one CTA per (16 x 16 pixel tile, IB images), angles AK at a time.
 // For a pixel at position p on line l of angle k, the rays that sample it
 // are found from the continuous bin m* = c_b + slope (p - c - R_l) and the
-// four integer candidates around it are tested with the forward's exact test.
+// three integer candidates around it are tested with the forward's exact test.
 constexpr int ATS = 16;     // tile side
 constexpr int AWIN = 48;    // staged bins per angle
 template <class TI, class TO, class TC, int IB, int AK>
@@ -178,6 +178,7 @@ __global__ void __launch_bounds__(256) radon_adj2_kernel(const TI* __restrict__ 
     __shared__ TC ss[AK][IB][AWIN];
     __shared__ int sr_i[AK][ATS];
     __shared__ TC sr_f[AK][ATS];
+    __shared__ int s_mlo[AK];
     const int i0 = blockIdx.y * ATS, j0 = blockIdx.x * ATS;
     const int b0 = blockIdx.z * IB;
     const int ti = threadIdx.x / ATS, tj = threadIdx.x % ATS;
@@ -208,11 +209,13 @@ __global__ void __launch_bounds__(256) radon_adj2_kernel(const TI* __restrict__ 
     for (int q = 0; q < IB; ++q) acc[q] = TC(0);
     for (int k0 = 0; k0 < n_angles; k0 += AK) {
         __syncthreads();   // the previous round's shared tables are consumed
+        if (threadIdx.x < AK) s_mlo[threadIdx.x] = (k0 + threadIdx.x < n_angles) ? window(k0 + threadIdx.x) : 0;
+        __syncthreads();
         for (int e = threadIdx.x; e < AK * AWIN; e += blockDim.x) {
             const int a = e / AWIN, w = e % AWIN;
             const int k = k0 + a;
             bool ok = k < n_angles;
-            const int m = ok ? window(k) + w : 0;
+            const int m = ok ? s_mlo[a] + w : 0;
             ok = ok && m >= 0 && m < n_bins;
             sq_i[a][w] = ok ? tab.qi[(size_t)k * n_bins + m] : 0;
             sq_f[a][w] = ok ? tab.qf[(size_t)k * n_bins + m] : TC(0);
@@ -248,13 +251,16 @@ __global__ void __launch_bounds__(256) radon_adj2_kernel(const TI* __restrict__ 
             const int ri = sr_i[a][lq];
             const TC rf = sr_f[a][lq];
             const TC mstar = cb + g_slope[k] * ((TC)p - cpos - ((TC)ri + rf));
-            const int m0 = (int)floor(mstar) - 1;
-            const int mlo = window(k);
+            // a bin m samples this pixel only if |u(m) - p| < 1, i.e. |m - m*| <
+            // |slope| <= 1: the (at most three) integers in (m* - 1, m* + 1),
+            // with a margin for the rounding of m*
+            const int m0 = (int)ceil(mstar - TC(1) - TC(1e-4));
+            const int mlo = s_mlo[a];
             TC part[IB];
 #pragma unroll
             for (int q = 0; q < IB; ++q) part[q] = TC(0);
 #pragma unroll
-            for (int dm = 0; dm < 4; ++dm) {
+            for (int dm = 0; dm < 3; ++dm) {
                 const int m = m0 + dm;
                 if (m < 0 || m >= n_bins) continue;
                 const int w = m - mlo;
