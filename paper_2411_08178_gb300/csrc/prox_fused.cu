@@ -23,17 +23,18 @@
 namespace nys {
 namespace {
 
-constexpr int FCH = 1024;   // pixels per partial-sum chunk
+constexpr int FCH = 1024;        // pixels per partial-sum chunk (small active sets)
+constexpr int FCH_WIDE = 512;    // large active sets: twice the CTAs, more bytes of U in flight
 constexpr int COUNTER_PROX = 1;
 
-template <class TU, class T, class TA, class TM, int REG, bool LAST>
+template <class TU, class T, class TA, class TM, int REG, bool LAST, int FCH>
 __global__ void __launch_bounds__(256) lt_utz_kernel(const T* __restrict__ R, int n1, int n2,
                                                      const TU* __restrict__ U, int le, int ldm,
                                                      const TM* __restrict__ M, T* __restrict__ g,
                                                      TA* __restrict__ part, TA* __restrict__ coef,
                                                      unsigned* __restrict__ counter) {
     constexpr int V = Vec16<TU>::n;
-    constexpr int PT = FCH / 256;   // pixels per thread in the stencil pass
+    constexpr int PT = (FCH + 255) / 256;   // pixels per thread in the stencil pass
     __shared__ __align__(16) TA gs[FCH];
     extern __shared__ __align__(16) unsigned char smem_raw[];
     TA* sm = reinterpret_cast<TA*>(smem_raw);   // last CTA: w and (le <= 64) M
@@ -44,7 +45,7 @@ __global__ void __launch_bounds__(256) lt_utz_kernel(const T* __restrict__ R, in
     for (int q = 0; q < PT; ++q) {
         const int64_t p = i0 + threadIdx.x + q * 256;
         v[q] = TA(0);
-        if (p < N) {
+        if (threadIdx.x + q * 256 < FCH && p < N) {
             int i, j;
             pix_ij(p, n2, i, j);
             v[q] = (TA)lt_q<T, REG>(R, i, j, n1, n2);
@@ -53,6 +54,7 @@ __global__ void __launch_bounds__(256) lt_utz_kernel(const T* __restrict__ R, in
 #pragma unroll
     for (int q = 0; q < PT; ++q) {
         const int64_t p = i0 + threadIdx.x + q * 256;
+        if (threadIdx.x + q * 256 >= FCH) continue;
         if (p < N) g[p] = (T)v[q];
         gs[threadIdx.x + q * 256] = v[q];
     }
@@ -117,7 +119,12 @@ int fused_typed(nys_ctx* ctx, const nys_precond* pc, double lb, int n_inner, int
     const double normL2 = REG == NYS_REG_TV ? 8.0 : 32.0;
     const int64_t N = (int64_t)n1 * n2;
     const int le = pv->ell_eff;
-    const int nchunk = (int)((N + FCH - 1) / FCH);
+    // small active sets: the last CTA of lt_utz forms M w; large ones: two
+    // passes over many CTAs (reduce_cols, mw) and smaller pixel chunks (more
+    // CTAs, more bytes of U in flight)
+    const bool last = le <= 64;
+    const int fch = last ? FCH : FCH_WIDE;
+    const int nchunk = (int)((N + fch - 1) / fch);
     int st;
     T* work = (T*)scratch(ctx, SLOT_PROX, ((size_t)2 * G * N + 2 * N) * sizeof(T), &st);
     if (st) return st;
@@ -129,9 +136,6 @@ int fused_typed(nys_ctx* ctx, const nys_precond* pc, double lb, int n_inner, int
     if (st) return st;
     TA* coef = part + (size_t)nchunk * std::max(le, 1);
     TA* wbuf = coef + std::max(le, 1);
-    // small active sets: the last CTA of lt_utz forms M w; large ones: two
-    // passes over many CTAs (reduce_cols, mw)
-    const bool last = le <= 64;
     cudaStream_t sm = ctx->stream;
     NYS_CK(ctx, cudaMemcpyAsync(R, Q, sizeof(T) * G * N, cudaMemcpyDeviceToDevice, sm));
     NYS_CK(ctx, cudaMemcpyAsync(Qp, Q, sizeof(T) * G * N, cudaMemcpyDeviceToDevice, sm));
@@ -146,12 +150,12 @@ int fused_typed(nys_ctx* ctx, const nys_precond* pc, double lb, int n_inner, int
     // x (or out) = s - lb P^{-1} L^T Rin
     auto xfn = [&](const T* Rin, T* dst) -> int {
         if (last) {
-            lt_utz_kernel<TU, T, TA, TM, REG, true><<<nchunk, 256, lsm, sm>>>(Rin, n1, n2, (const TU*)pc->U, le,
-                                                                                pc->ell, M, g, part, coef, counter);
+            lt_utz_kernel<TU, T, TA, TM, REG, true, FCH><<<nchunk, 256, lsm, sm>>>(Rin, n1, n2, (const TU*)pc->U, le,
+                                                                                     pc->ell, M, g, part, coef, counter);
             NYS_LAUNCH_CK(ctx);
         } else {
-            lt_utz_kernel<TU, T, TA, TM, REG, false><<<nchunk, 256, 16, sm>>>(Rin, n1, n2, (const TU*)pc->U, le,
-                                                                                pc->ell, M, g, part, coef, counter);
+            lt_utz_kernel<TU, T, TA, TM, REG, false, FCH_WIDE><<<nchunk, 256, 16, sm>>>(
+                Rin, n1, n2, (const TU*)pc->U, le, pc->ell, M, g, part, coef, counter);
             NYS_LAUNCH_CK(ctx);
             int st2 = coef_run<TA, TM>(ctx, part, nchunk, le, pc->ell, 1, M, (const TM*)nullptr, coef, 1, wbuf);
             if (st2) return st2;

@@ -444,7 +444,7 @@ int create_typed(nys_solver* S, const void* y) {
     if (S->pc) {
         // the largest of the P^{-1} / prox partial-sum layouts (chunks of 1024 or
         // 2048 pixels)
-        const size_t nbp = (size_t)((N + 1023) / 1024);
+        const size_t nbp = (size_t)((N + 511) / 512);   // chunks of 512 .. 2048 pixels
         if (!scratch(ctx, SLOT_PRECOND, (nbp * ell + 2 * ell) * es, &st)) return st;
         if (S->d.reg == NYS_REG_WAVELET) {
             // the first ssn_run call sizes SLOT_SSN; run one prox now
