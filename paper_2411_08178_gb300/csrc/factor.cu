@@ -257,10 +257,18 @@ int precond_vec(nys_ctx* ctx, const nys_precond* pc, int inverse, const void* z,
     const TM* Mp = sizeof(TA) == 8 ? (const TM*)pv->M64 : (const TM*)pv->M32;
     const TM* dp = sizeof(TA) == 8 ? (const TM*)pv->d : (const TM*)pv->d32;
     if ((st = coef_run<TA, TM>(ctx, part, nchunk, ell, pc->ell, inverse, Mp, dp, coef, batch, wbuf))) return st;
-    constexpr int P = 32 * V;
+    // large active sets: two 16-byte vectors per lane and two columns per
+    // round (1 KB contiguous per column and warp, near the HBM rate)
+    const int pvx = ell <= 64 ? 1 : 2;
+    const int P = 32 * V * pvx;
     const size_t sm = (((size_t)ell + 3) & ~size_t(3)) * sizeof(TA) + (size_t)8 * P * sizeof(TA);
-    uc_vec_kernel<TU, TZ, TA><<<dim3((unsigned)((N + P - 1) / P), batch), 256, sm, s>>>(
-        (const TU*)pc->U, (const TZ*)z, N, ell, coef, inverse ? TA(-1) : TA(1), (TZ*)out);
+    const dim3 grid((unsigned)((N + P - 1) / P), batch);
+    if (pvx == 1)
+        uc_vec_kernel<TU, TZ, TA><<<grid, 256, sm, s>>>((const TU*)pc->U, (const TZ*)z, N, ell, coef,
+                                                        inverse ? TA(-1) : TA(1), (TZ*)out);
+    else
+        uc_vec_kernel<TU, TZ, TA, 2, 2><<<grid, 256, sm, s>>>((const TU*)pc->U, (const TZ*)z, N, ell, coef,
+                                                              inverse ? TA(-1) : TA(1), (TZ*)out);
     NYS_LAUNCH_CK(ctx);
     return NYS_OK;
 }

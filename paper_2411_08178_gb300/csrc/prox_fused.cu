@@ -141,7 +141,10 @@ int fused_typed(nys_ctx* ctx, const nys_precond* pc, double lb, int n_inner, int
     NYS_CK(ctx, cudaMemcpyAsync(Qp, Q, sizeof(T) * G * N, cudaMemcpyDeviceToDevice, sm));
     const TM* M = sizeof(TA) == 8 ? (const TM*)pv->M64 : (const TM*)pv->M32;
     const size_t lsm = ((size_t)le + (le <= 64 ? (size_t)le * le : 0)) * sizeof(TA) + 16;
-    constexpr int P = 32 * V;
+    // x pass: large active sets take two 16-byte vectors per lane and two
+    // columns per round (1 KB contiguous per column and warp)
+    const int pvx = last ? 1 : 2;
+    const int P = 32 * V * pvx;
     const size_t usm = (((size_t)le + 3) & ~size_t(3)) * sizeof(TA) + (size_t)8 * P * sizeof(TA);
     const int ug = (int)((N + P - 1) / P);
     const int dg = (int)std::min<int64_t>((N + 255) / 256, (int64_t)ctx->sm_count * 8);
@@ -160,8 +163,12 @@ int fused_typed(nys_ctx* ctx, const nys_precond* pc, double lb, int n_inner, int
             int st2 = coef_run<TA, TM>(ctx, part, nchunk, le, pc->ell, 1, M, (const TM*)nullptr, coef, 1, wbuf);
             if (st2) return st2;
         }
-        uc_vec_kernel<TU, T, TA><<<dim3(ug, 1), 256, usm, sm>>>((const TU*)pc->U, g, N, le, coef, TA(-1), dst, s,
-                                                                (TA)(-lb));
+        if (pvx == 1)
+            uc_vec_kernel<TU, T, TA><<<dim3(ug, 1), 256, usm, sm>>>((const TU*)pc->U, g, N, le, coef, TA(-1), dst, s,
+                                                                    (TA)(-lb));
+        else
+            uc_vec_kernel<TU, T, TA, 2, 2><<<dim3(ug, 1), 256, usm, sm>>>((const TU*)pc->U, g, N, le, coef, TA(-1), dst,
+                                                                          s, (TA)(-lb));
         NYS_LAUNCH_CK(ctx);
         return NYS_OK;
     };

@@ -224,15 +224,15 @@ __device__ __forceinline__ void last_cta_coef_t(const TA* partT, int le, int ldm
 }
 
 // out = z + sign * U c, or with base: out = base + scale (z + sign U c).  A CTA
-// owns 32 V pixels; its 8 warps split the columns and their partial sums meet
-// in shared memory
-template <class TU, class TZ, class TA>
+// owns 32 V PV pixels (PV 16-byte vectors per lane); its 8 warps split the
+// columns, NQ columns per round, and their partial sums meet in shared memory
+template <class TU, class TZ, class TA, int NQ = 4, int PV = 1>
 __global__ void __launch_bounds__(256) uc_vec_kernel(const TU* __restrict__ U, const TZ* __restrict__ z, int64_t N,
                                                      int ell, const TA* __restrict__ coef, TA sign,
                                                      TZ* __restrict__ out, const TZ* __restrict__ base = nullptr,
                                                      TA scale = TA(1)) {
     constexpr int V = Vec16<TU>::n;
-    constexpr int P = 32 * V;
+    constexpr int P = 32 * V * PV;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     TA* c = reinterpret_cast<TA*>(smem_raw);
     TA* red = c + ((ell + 3) & ~3);            // [8][P]
@@ -240,35 +240,40 @@ __global__ void __launch_bounds__(256) uc_vec_kernel(const TU* __restrict__ U, c
     for (int j = threadIdx.x; j < ell; j += blockDim.x) c[j] = coef[(size_t)b * ell + j];
     __syncthreads();
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int64_t i = (int64_t)blockIdx.x * P + lane * V;
-    TA acc[V];
+    TA acc[PV][V];
 #pragma unroll
-    for (int k = 0; k < V; ++k) acc[k] = TA(0);
-    if (i < N) {
-        // four columns (j, j + 8, j + 16, j + 24) per round, loads predicated,
-        // so a small active set still has all its loads in flight at once
-        for (int j = warp; j < ell; j += 32) {
-            TA u[4][V];
-            TA cq[4];
+    for (int v = 0; v < PV; ++v)
 #pragma unroll
-            for (int q = 0; q < 4; ++q) {
-                const int jq = j + 8 * q;
-                if (jq < ell) {
-                    load_vec<TU, TA, V>(U + (size_t)jq * N + i, u[q]);
-                    cq[q] = c[jq];
-                } else {
+        for (int k = 0; k < V; ++k) acc[v][k] = TA(0);
+    // NQ columns (j, j + 8, ...) per round, loads predicated, so a small
+    // active set still has all its loads in flight at once
+    for (int j = warp; j < ell; j += 8 * NQ) {
+        TA u[NQ][PV][V];
+        TA cq[NQ];
 #pragma unroll
-                    for (int k = 0; k < V; ++k) u[q][k] = TA(0);
-                    cq[q] = TA(0);
-                }
+        for (int q = 0; q < NQ; ++q) {
+            const int jq = j + 8 * q;
+            cq[q] = jq < ell ? c[jq] : TA(0);
+#pragma unroll
+            for (int v = 0; v < PV; ++v) {
+                const int64_t i = (int64_t)blockIdx.x * P + (v * 32 + lane) * V;
+                if (jq < ell && i < N) load_vec<TU, TA, V>(U + (size_t)jq * N + i, u[q][v]);
+                else
+#pragma unroll
+                    for (int k = 0; k < V; ++k) u[q][v][k] = TA(0);
             }
-#pragma unroll
-            for (int k = 0; k < V; ++k)
-                acc[k] = fma(u[3][k], cq[3], fma(u[2][k], cq[2], fma(u[1][k], cq[1], fma(u[0][k], cq[0], acc[k]))));
         }
+#pragma unroll
+        for (int q = 0; q < NQ; ++q)
+#pragma unroll
+            for (int v = 0; v < PV; ++v)
+#pragma unroll
+                for (int k = 0; k < V; ++k) acc[v][k] = fma(u[q][v][k], cq[q], acc[v][k]);
     }
 #pragma unroll
-    for (int k = 0; k < V; ++k) red[warp * P + lane * V + k] = acc[k];
+    for (int v = 0; v < PV; ++v)
+#pragma unroll
+        for (int k = 0; k < V; ++k) red[warp * P + (v * 32 + lane) * V + k] = acc[v][k];
     __syncthreads();
     for (int p = threadIdx.x; p < P; p += blockDim.x) {
         const int64_t ii = (int64_t)blockIdx.x * P + p;
