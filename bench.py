@@ -42,13 +42,13 @@ import workloads as WL  # noqa: E402
 EPS32 = 2.0 ** -23
 METRIC = "time to 1e-3 rel. error (Nyström-precond vs plain PGD), sketch ms, HBM GB/s"
 TARGET = 1e-3
-# DRAM bytes (read + write) of one dual step with cold caches, measured with ncu
-# (dram__bytes_read.sum + dram__bytes_write.sum of lt_utz_kernel 13.67 MB,
-# uc_vec_kernel 13.65 MB and dual_update_kernel 5.25 MB; no DRAM writes, the
+# DRAM bytes (read + write) per x evaluation of the P-metric TV prox with cold
+# caches, from one ncu capture of the current kernels (lt_utz_kernel with the
+# fused dual update 16.57 MB + uc_vec_kernel 13.65 MB, no DRAM writes: the
 # outputs stay in L2) on the 512 x 512 sigma-4 deblurring problem with 22
 # active bf16 columns; it applies to that configuration only
 DUAL_STEP_TRAFFIC = {"workload": "deblur512_tv_f32", "active_columns": 22, "sketch_dtype": "bf16",
-                     "bytes": 32.57e6}
+                     "bytes": 30.22e6}
 
 
 def dist_env():
@@ -216,6 +216,54 @@ class Native:
         self.solver_p.restart(True)
         self.solver_p.step(k)
 
+    def apg_constant(self, sol, pc, xstar, Fstar):
+        """C = L ||x^1 - x*||_P^2 with x^1 = 0 and L = 1/alpha (the step-size
+        estimate): the constant of the bound F(x^k) - F* <= 2 C / (k + 1)^2
+        that Algorithm 3 inherits from accelerated proximal gradient in the
+        P-metric.  A preconditioner pays when it lowers C: L drops with the
+        captured spectrum, ||x*||_P grows with d.  Also returns the k at which
+        the bound reaches the objective-gap target."""
+        torch = self.torch
+        z = xstar.reshape(-1).contiguous()
+        Pz = self.api.precond_apply(self.ctx, pc, z, False) if pc is not None else z
+        C = float(torch.dot(z.double(), Pz.double())) / sol.alpha
+        k_bound = max(1, math.ceil(math.sqrt(2.0 * C / (TARGET * abs(Fstar))) - 1.0))
+        return {"C": C, "k_bound": k_bound, "L": 1.0 / sol.alpha}
+
+    def ell_sweep(self, ells, xstar, Fstar, kmax, steps, warmup):
+        """Time to the same objective gap for other sketch sizes: for each ell a
+        fresh sketch, factor and preconditioned solver on the same data and F*;
+        the timed step is sketch + factor + step size + k iterations, as in
+        the main measurement."""
+        torch, api, w = self.torch, self.api, self.w
+        out = []
+        for ell in ells:
+            Om = torch.empty((ell, w.n, w.n), dtype=self.sd, device=self.dev)
+            Y = torch.empty_like(Om)
+            pc = api.Precond(self.ctx, w.n * w.n, ell, self.sd)
+
+            def sf():
+                api.nys_sketch(self.ctx, self.op, ell, w.seed_omega, store_dtype=self.sd, out=(Om, Y))
+                api.nys_factor(self.ctx, Om, Y, EPS32, pc=pc)
+            sf()
+            sol = api.Solver(self.ctx, self.op, self.y, w.reg, w.lam, pc=pc, fit=w.fit,
+                             huber_delta=w.huber_delta, n_inner=w.n_inner)
+            k, _, _, _ = self.iterations_to(sol, xstar, Fstar, kmax)
+            kr = k or kmax
+
+            def run():
+                sf()
+                sol.restart(True)
+                sol.step(kr)
+            sk = statistics.median(self.time_loop(sf, max(3, steps), 1, "sweep_sketch"))
+            ms = statistics.mean(self.time_loop(run, steps, warmup, "sweep_precond"))
+            out.append({"ell": ell, "active_columns": pc.ell_active, "k_precond": k, "ms": round(ms, 3),
+                        "sketch_ms": round(sk, 3), "apg_bound": self.apg_constant(sol, pc, xstar, Fstar)})
+            sol.close()
+            pc.close()
+            del Om, Y
+        return out
+
     def solve_plain(self, k):
         self.solver_0.restart(True)
         self.solver_0.step(k)
@@ -263,12 +311,30 @@ class Native:
         torch.cuda.synchronize(self.dev)
         return a.elapsed_time(b) / reps
 
+    def _graph_ms(self, fn, reps):
+        """fn captured once into a CUDA graph (as the solver runs its
+        iteration) and replayed reps times, timed with CUDA events on the
+        stream the replays are launched on; ms per replay."""
+        torch = self.torch
+        fn()                                   # eager once: scratch sized, attributes set
+        torch.cuda.synchronize(self.dev)
+        cap = torch.cuda.Stream(self.dev)
+        old = self.ctx.stream
+        g = torch.cuda.CUDAGraph()
+        self.ctx.set_stream(cap)
+        try:
+            with torch.cuda.graph(g, stream=cap):
+                fn()
+        finally:
+            self.ctx.set_stream(old)
+        return self._events_ms(g.replay, reps)
+
     def precond_roofline(self, reps: int = 30):
-        """Standalone P^{-1} apply: (ms, algorithmic bytes)."""
+        """Standalone P^{-1} apply, replayed from a CUDA graph: (ms, algorithmic bytes)."""
         torch = self.torch
         z = torch.randn(self.w.n * self.w.n, dtype=torch.float32, device=self.dev)
         out = torch.empty_like(z)
-        ms = self._events_ms(lambda: self.api.precond_apply(self.ctx, self.pc, z, True, out), reps)
+        ms = self._graph_ms(lambda: self.api.precond_apply(self.ctx, self.pc, z, True, out), reps)
         N, ell = self.w.n * self.w.n, self.pc.ell_active
         ub = 2 if self.sd == torch.bfloat16 else 4
         # the active columns of U (d_i > 0) read twice (U^T z and U c) + z read
@@ -276,10 +342,11 @@ class Native:
         return ms, 2 * N * ell * ub + 3 * N * 4
 
     def dual_step_roofline(self, reps: int = 20):
-        """The P-metric TV prox as the solve runs it (n_inner dual steps of
-        lt_utz + uc_vec + dual_update, then the final x): (ms per dual step,
-        algorithmic bytes per dual step).  The call is timed with CUDA events
-        on the context's stream, right after the timed region."""
+        """The P-metric prox as the solve runs it (replayed from a CUDA graph):
+        the first x, then n_inner dual steps, each one launch of the dual
+        update fused with L^T and the U^T g partial sums (TV; HS: L^T with
+        U^T g, then the dual update) and one of x = s - lb (g - U c).  Returns
+        (ms, algorithmic bytes), both per x evaluation (n_inner + 1 of them)."""
         torch, w = self.torch, self.w
         N = w.n * w.n
         G = 3 if w.reg == "hs" else 2
@@ -288,13 +355,18 @@ class Native:
         out = torch.empty_like(s)
         lb = 0.9 * w.lam
         fn = self.api.prox_hs if w.reg == "hs" else self.api.prox_tv
-        ms = self._events_ms(lambda: fn(self.ctx, self.pc, lb, w.n_inner, s, Q=Q, out=out), reps)
+        ms = self._graph_ms(lambda: fn(self.ctx, self.pc, lb, w.n_inner, s, Q=Q, out=out), reps)
         le, ub, f = self.pc.ell_active, (2 if self.sd == torch.bfloat16 else 4), 4
-        lt_utz = G * N * f + le * N * ub + N * f            # R in, U, g out
         uc = le * N * ub + 2 * N * f + N * f                 # U, g and s in, x out
-        dual = N * f + 2 * G * N * f + 2 * G * N * f         # x in, R and Q in and out
-        copies = 3 * 2 * (G * N * f)                         # the warm start in and out
-        total = w.n_inner * (lt_utz + uc + dual) + lt_utz + uc + copies
+        lt_utz = G * N * f + le * N * ub + N * f             # R (or Q) in, U, g out
+        if w.reg == "tv":
+            # x, (R, Q) old in, (R, Q) new out, g out, U (the last step writes no R)
+            fused = N * f + 4 * G * N * f + N * f + le * N * ub
+            total = lt_utz + uc + w.n_inner * (fused + uc) - G * N * f
+        else:
+            dual = N * f + 2 * G * N * f + 2 * G * N * f    # x in, R and Q in and out
+            copies = 3 * 2 * (G * N * f)                     # the warm start in and out
+            total = w.n_inner * (lt_utz + uc + dual) + lt_utz + uc + copies
         steps = w.n_inner + 1
         return ms / steps, total / steps
 
@@ -342,9 +414,17 @@ def run_native(args, w: WL.Workload):
     peaks = load_peaks()
     achieved = step_bytes / (step_ms * 1e-3) / 1e9
     tr = DUAL_STEP_TRAFFIC
-    traffic = (tr["bytes"] if (w.name == tr["workload"] and nb.pc.ell_active == tr["active_columns"]
-                               and args.sketch_dtype == tr["sketch_dtype"]) else None)
+    traffic = (tr["bytes"] if tr and (w.name == tr["workload"] and nb.pc.ell_active == tr["active_columns"]
+                                      and args.sketch_dtype == tr["sketch_dtype"]) else None)
     achieved_pinv = pre_bytes / (pre_ms * 1e-3) / 1e9
+    bound = {"precond": nb.apg_constant(nb.solver_p, nb.pc, xstar, Fstar),
+             "plain": nb.apg_constant(nb.solver_0, None, xstar, Fstar),
+             "what": "C = L ||x^1 - x*||_P^2 (x^1 = 0, L = 1/alpha); F(x^k) - F* <= 2C/(k+1)^2 reaches the target at "
+                     "k_bound"}
+    sweep = None
+    if args.ell_sweep:
+        sweep = nb.ell_sweep([int(e) for e in args.ell_sweep.split(",")], xstar, Fstar, kmax, args.steps,
+                             args.warmup)
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = oracle_sample(w, k_p_run, seconds_hint=args.cpu_seconds)
@@ -358,7 +438,7 @@ def run_native(args, w: WL.Workload):
         "criterion": "objective gap (F(x^k) - F*)/|F*| <= 1e-3, F* the best of the reference runs; the iterate error "
                      "||x^k - x*||/||x*|| is reported beside it (x* is not resolved to 1e-3 within the run, see "
                      "xstar.drift_last_quarter)",
-        "k_precond": k_p, "k_plain": k_0, "sketch_ms": round(sketch_ms, 3),
+        "k_precond": k_p, "k_plain": k_0, "sketch_ms": round(sketch_ms, 3), "apg_bound": bound,
         "iterate_err": {"k_precond_1e-3": kit_p, "k_plain_1e-3": kit_0, "precond_err_at_k": [kend_p, err_p],
                         "plain_err_at_k": [kend_0, err_0]},
         "xstar": {"from": "float64 plain APG (x*); F* = min(that, float32 WAPG with P)", "iters": args.ref_iters,
@@ -367,7 +447,9 @@ def run_native(args, w: WL.Workload):
                 "d2h_bytes_per_step": w.n * w.n * 4},
         "gpu_launches": int(launches),
         "roofline": {"bound": "hbm",
-                     "kernel": f"P-metric {w.reg.upper()} dual step (lt_utz_kernel + uc_vec_kernel + dual_update_kernel)",
+                     "kernel": (f"P-metric {w.reg.upper()} dual step, graph replay ("
+                                + ("lt_utz_kernel with the fused dual update + uc_vec_kernel)" if w.reg == "tv"
+                                   else "lt_utz_kernel + uc_vec_kernel + dual_update_kernel)")),
                      "achieved": round(achieved, 1), "peak": peaks["hbm_gbs"], "peak_source": peaks["src"],
                      "unit": "GB/s", "frac": round(achieved / peaks["hbm_gbs"], 4),
                      "traffic": traffic, "bytes_per_step": step_bytes, "ms_per_step": round(step_ms, 5),
@@ -379,6 +461,8 @@ def run_native(args, w: WL.Workload):
         "cpu_baseline": cpu,
         "setup_s": round(setup_s, 1),
     }
+    if sweep is not None:
+        out["ell_sweep"] = sweep
     if rank == 0:
         print(json.dumps(out))
     if world > 1:
@@ -475,6 +559,8 @@ def main():
                     choices=sorted(k for k, v in WL.PRESETS.items() if v.reg != "wavelet"))
     ap.add_argument("--sketch-dtype", choices=["bf16", "f32"], default="bf16")
     ap.add_argument("--ell", type=int, default=0, help="override the sketch size")
+    ap.add_argument("--ell-sweep", default="",
+                    help="comma-separated sketch sizes also timed to the same F* (adds 'ell_sweep' to the line)")
     ap.add_argument("--ref-iters", type=int, default=20000)
     ap.add_argument("--kmax", type=int, default=8000)
     ap.add_argument("--cpu-seconds", type=float, default=15.0)

@@ -2,6 +2,7 @@
 #include "internal.cuh"
 
 #include <cmath>
+#include <cstdlib>
 #include <cstring>
 #include <mutex>
 
@@ -43,6 +44,14 @@ int cuda_fail(nys_ctx* ctx, cudaError_t e, const char* what) {
     cudaGetLastError();
     return fail(ctx, e == cudaErrorMemoryAllocation ? NYS_ENOMEM : NYS_ECUDA, "%s: %s", what,
                 cudaGetErrorString(e));
+}
+
+int pdl_mode() {
+    static const int m = [] {
+        const char* e = getenv("NYS_PDL");
+        return (e && e[0] == '0') ? 0 : (e && e[0] == '2') ? 2 : 1;
+    }();
+    return m;
 }
 
 void* scratch(nys_ctx* ctx, int slot, size_t bytes, int* status) {

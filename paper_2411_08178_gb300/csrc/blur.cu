@@ -59,6 +59,7 @@ template <class TI, class TO, class TC, int TY, int TX>
 __global__ void __launch_bounds__(256) sepcorr_kernel(const TI* __restrict__ x, TO* __restrict__ y, int n1,
                                                       int n2, const TC* __restrict__ taps, int Lcp, int Lrp,
                                                       int cc, int cr) {
+    pdl_enter();
     extern __shared__ __align__(16) unsigned char smem_raw[];
     TC* s_tap = reinterpret_cast<TC*>(smem_raw);
     const int rows = TY + Lcp;          // staged input rows = intermediate rows
@@ -115,6 +116,7 @@ template <class TI, class TO, class TC, int TY, int TX>
 __global__ void __launch_bounds__(256) corr2d_kernel(const TI* __restrict__ x, TO* __restrict__ y, int n1,
                                                      int n2, const TC* __restrict__ taps, int kh, int kwp,
                                                      int ch, int cw) {
+    pdl_enter();
     extern __shared__ __align__(16) unsigned char smem_raw[];
     TC* s_tap = reinterpret_cast<TC*>(smem_raw);
     const int rows = TY + kh - 1;
@@ -154,6 +156,7 @@ __global__ void __launch_bounds__(256) corr2d_kernel(const TI* __restrict__ x, T
 template <class TI, class TO, class TC>
 __global__ void decim_fwd_kernel(const TI* __restrict__ x, TO* __restrict__ y, int n1, int n2, int d,
                                  const TC* __restrict__ h, int kh, int kw, int batch) {
+    pdl_enter();
     const int m1 = n1 / d, m2 = n2 / d;
     const int64_t total = (int64_t)batch * m1 * m2;
     for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
@@ -180,6 +183,7 @@ __global__ void decim_fwd_kernel(const TI* __restrict__ x, TO* __restrict__ y, i
 template <class TI, class TO, class TC>
 __global__ void decim_adj_kernel(const TI* __restrict__ y, TO* __restrict__ x, int n1, int n2, int d,
                                  const TC* __restrict__ h, int kh, int kw, int batch) {
+    pdl_enter();
     const int m1 = n1 / d, m2 = n2 / d;
     const int64_t total = (int64_t)batch * n1 * n2;
     const int ch = (kh - 1) / 2, cw = (kw - 1) / 2;
@@ -224,7 +228,8 @@ int launch_sep(nys_op* op, const void* x, void* y, int batch, const void* taps, 
         attr_max = (int)sm;
     }
     dim3 grid((op->n2 + T - 1) / T, (op->n1 + T - 1) / T, batch);
-    k<<<grid, 256, sm, op->ctx->stream>>>((const TI*)x, (TO*)y, op->n1, op->n2, (const TC*)taps, Lcp, Lrp, cc, cr);
+    NYS_CK(op->ctx, launch_pdl(k, grid, 256, sm, op->ctx->stream, (const TI*)x, (TO*)y, op->n1, op->n2,
+                               (const TC*)taps, Lcp, Lrp, cc, cr));
     NYS_LAUNCH_CK(op->ctx);
     return NYS_OK;
 }
@@ -241,8 +246,8 @@ int launch_c2d(nys_op* op, const void* x, void* y, int batch, const void* taps) 
         attr_max = (int)sm;
     }
     dim3 grid((op->n2 + T - 1) / T, (op->n1 + T - 1) / T, batch);
-    k<<<grid, 256, sm, op->ctx->stream>>>((const TI*)x, (TO*)y, op->n1, op->n2, (const TC*)taps, op->kh, kwp,
-                                          (op->kh - 1) / 2, (op->kw - 1) / 2);
+    NYS_CK(op->ctx, launch_pdl(k, grid, 256, sm, op->ctx->stream, (const TI*)x, (TO*)y, op->n1, op->n2,
+                               (const TC*)taps, op->kh, kwp, (op->kh - 1) / 2, (op->kw - 1) / 2));
     NYS_LAUNCH_CK(op->ctx);
     return NYS_OK;
 }
@@ -279,24 +284,24 @@ int decim_typed(nys_op* op, int which, const void* x, void* y, int batch) {
     const TC* h = (const TC*)op->taps_fwd;
     const int grid = op->ctx->sm_count * 8;
     if (which == 0) {
-        decim_fwd_kernel<TI, TO, TC><<<grid, 256, 0, s>>>((const TI*)x, (TO*)y, op->n1, op->n2, op->decim, h,
-                                                           op->kh, op->kw, batch);
+        NYS_CK(op->ctx, launch_pdl(decim_fwd_kernel<TI, TO, TC>, grid, 256, 0, s, (const TI*)x, (TO*)y, op->n1,
+                                   op->n2, op->decim, h, op->kh, op->kw, batch));
         NYS_LAUNCH_CK(op->ctx);
         return NYS_OK;
     }
     if (which == 1) {
-        decim_adj_kernel<TI, TO, TC><<<grid, 256, 0, s>>>((const TI*)x, (TO*)y, op->n1, op->n2, op->decim, h,
-                                                           op->kh, op->kw, batch);
+        NYS_CK(op->ctx, launch_pdl(decim_adj_kernel<TI, TO, TC>, grid, 256, 0, s, (const TI*)x, (TO*)y, op->n1,
+                                   op->n2, op->decim, h, op->kh, op->kw, batch));
         NYS_LAUNCH_CK(op->ctx);
         return NYS_OK;
     }
     for (int b0 = 0; b0 < batch; b0 += op->chunk) {
         const int nb = std::min(op->chunk, batch - b0);
-        decim_fwd_kernel<TI, TC, TC><<<grid, 256, 0, s>>>((const TI*)x + (size_t)b0 * op->N, (TC*)op->inter, op->n1,
-                                                           op->n2, op->decim, h, op->kh, op->kw, nb);
+        NYS_CK(op->ctx, launch_pdl(decim_fwd_kernel<TI, TC, TC>, grid, 256, 0, s, (const TI*)x + (size_t)b0 * op->N,
+                                   (TC*)op->inter, op->n1, op->n2, op->decim, h, op->kh, op->kw, nb));
         NYS_LAUNCH_CK(op->ctx);
-        decim_adj_kernel<TC, TO, TC><<<grid, 256, 0, s>>>((const TC*)op->inter, (TO*)y + (size_t)b0 * op->N, op->n1,
-                                                           op->n2, op->decim, h, op->kh, op->kw, nb);
+        NYS_CK(op->ctx, launch_pdl(decim_adj_kernel<TC, TO, TC>, grid, 256, 0, s, (const TC*)op->inter,
+                                   (TO*)y + (size_t)b0 * op->N, op->n1, op->n2, op->decim, h, op->kh, op->kw, nb));
         NYS_LAUNCH_CK(op->ctx);
     }
     return NYS_OK;

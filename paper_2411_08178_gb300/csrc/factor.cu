@@ -179,6 +179,7 @@ constexpr int VCH = 2048;    // pixels per partial-sum chunk
 template <class TU, class TZ, class TA>
 __global__ void __launch_bounds__(256) utz_vec_kernel(const TU* __restrict__ U, const TZ* __restrict__ z, int64_t N,
                                                       int ell, int jper, TA* __restrict__ part) {
+    pdl_enter();
     constexpr int V = Vec16<TU>::n;
     __shared__ __align__(16) TA zs[VCH];
     const int64_t i0 = (int64_t)blockIdx.x * VCH;
@@ -250,8 +251,8 @@ int precond_vec(nys_ctx* ctx, const nys_precond* pc, int inverse, const void* z,
     TA* wbuf = coef + (size_t)batch * ell;
     cudaStream_t s = ctx->stream;
     if (batch > 65535) return fail(ctx, NYS_EINVAL, "precond: batch above 65535");
-    utz_vec_kernel<TU, TZ, TA><<<dim3(nchunk, groups, batch), 256, 0, s>>>((const TU*)pc->U, (const TZ*)z, N, ell,
-                                                                          jper, part);
+    NYS_CK(ctx, launch_pdl(utz_vec_kernel<TU, TZ, TA>, dim3(nchunk, groups, batch), 256, 0, s, (const TU*)pc->U,
+                           (const TZ*)z, N, ell, jper, part));
     NYS_LAUNCH_CK(ctx);
     using TM = typename std::conditional<sizeof(TA) == 8, double, float>::type;
     const TM* Mp = sizeof(TA) == 8 ? (const TM*)pv->M64 : (const TM*)pv->M32;
@@ -264,11 +265,11 @@ int precond_vec(nys_ctx* ctx, const nys_precond* pc, int inverse, const void* z,
     const size_t sm = (((size_t)ell + 3) & ~size_t(3)) * sizeof(TA) + (size_t)8 * P * sizeof(TA);
     const dim3 grid((unsigned)((N + P - 1) / P), batch);
     if (pvx == 1)
-        uc_vec_kernel<TU, TZ, TA><<<grid, 256, sm, s>>>((const TU*)pc->U, (const TZ*)z, N, ell, coef,
-                                                        inverse ? TA(-1) : TA(1), (TZ*)out);
+        NYS_CK(ctx, launch_pdl(uc_vec_kernel<TU, TZ, TA>, grid, 256, sm, s, (const TU*)pc->U, (const TZ*)z, N, ell,
+                               coef, inverse ? TA(-1) : TA(1), (TZ*)out, (const TZ*)nullptr, TA(1)));
     else
-        uc_vec_kernel<TU, TZ, TA, 2, 2><<<grid, 256, sm, s>>>((const TU*)pc->U, (const TZ*)z, N, ell, coef,
-                                                              inverse ? TA(-1) : TA(1), (TZ*)out);
+        NYS_CK(ctx, launch_pdl(uc_vec_kernel<TU, TZ, TA, 2, 2>, grid, 256, sm, s, (const TU*)pc->U, (const TZ*)z, N,
+                               ell, coef, inverse ? TA(-1) : TA(1), (TZ*)out, (const TZ*)nullptr, TA(1)));
     NYS_LAUNCH_CK(ctx);
     return NYS_OK;
 }

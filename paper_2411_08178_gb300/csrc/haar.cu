@@ -19,6 +19,7 @@ namespace {
 template <class TI, class TO, class TL, class TC>
 __global__ void haar_fwd_level(const TI* __restrict__ src, TO* __restrict__ out, TL* __restrict__ ll, int n1,
                                int n2, int h, int w, int last, int batch) {
+    pdl_enter();
     const int hh = h / 2, hw = w / 2;
     const int64_t total = (int64_t)batch * hh * hw;
     for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
@@ -46,6 +47,7 @@ __global__ void haar_fwd_level(const TI* __restrict__ src, TO* __restrict__ out,
 template <class TL, class TD, class TO, class TC>
 __global__ void haar_inv_level(const TL* __restrict__ lsrc, const TD* __restrict__ dsrc, TO* __restrict__ dst,
                                int n1, int n2, int h, int w, int batch) {
+    pdl_enter();
     const int hh = h / 2, hw = w / 2;
     const int64_t total = (int64_t)batch * hh * hw;
     for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
@@ -101,9 +103,11 @@ int haar_typed(nys_op* op, const void* in, void* out, int batch, int inverse) {
         for (int lev = 0; lev < L; ++lev) {
             const int h = n1 >> lev, w = n2 >> lev, last = (lev == L - 1);
             if (src_is_in)
-                haar_fwd_level<TI, TO, TC, TC><<<grid, 256, 0, s>>>((const TI*)src, (TO*)out, cur, n1, n2, h, w, last, batch);
+                NYS_CK(ctx, launch_pdl(haar_fwd_level<TI, TO, TC, TC>, grid, 256, 0, s,
+                                       (const TI*)src, (TO*)out, cur, n1, n2, h, w, last, batch));
             else
-                haar_fwd_level<TC, TO, TC, TC><<<grid, 256, 0, s>>>((const TC*)src, (TO*)out, cur, n1, n2, h, w, last, batch);
+                NYS_CK(ctx, launch_pdl(haar_fwd_level<TC, TO, TC, TC>, grid, 256, 0, s,
+                                       (const TC*)src, (TO*)out, cur, n1, n2, h, w, last, batch));
             NYS_LAUNCH_CK(ctx);
             src = cur;
             src_is_in = false;
@@ -119,15 +123,19 @@ int haar_typed(nys_op* op, const void* in, void* out, int batch, int inverse) {
         const int h = n1 >> lev, w = n2 >> lev;
         if (lev == 0) {
             if (lev == L - 1)
-                haar_inv_level<TI, TI, TO, TC><<<grid, 256, 0, s>>>((const TI*)in, (const TI*)in, (TO*)out, n1, n2, h, w, batch);
+                NYS_CK(ctx, launch_pdl(haar_inv_level<TI, TI, TO, TC>, grid, 256, 0, s,
+                                       (const TI*)in, (const TI*)in, (TO*)out, n1, n2, h, w, batch));
             else
-                haar_inv_level<TC, TI, TO, TC><<<grid, 256, 0, s>>>(lsrc, (const TI*)in, (TO*)out, n1, n2, h, w, batch);
+                NYS_CK(ctx, launch_pdl(haar_inv_level<TC, TI, TO, TC>, grid, 256, 0, s,
+                                       lsrc, (const TI*)in, (TO*)out, n1, n2, h, w, batch));
             NYS_LAUNCH_CK(ctx);
         } else {
             if (lev == L - 1)
-                haar_inv_level<TI, TI, TC, TC><<<grid, 256, 0, s>>>((const TI*)in, (const TI*)in, cur, n1, n2, h, w, batch);
+                NYS_CK(ctx, launch_pdl(haar_inv_level<TI, TI, TC, TC>, grid, 256, 0, s,
+                                       (const TI*)in, (const TI*)in, cur, n1, n2, h, w, batch));
             else
-                haar_inv_level<TC, TI, TC, TC><<<grid, 256, 0, s>>>(lsrc, (const TI*)in, cur, n1, n2, h, w, batch);
+                NYS_CK(ctx, launch_pdl(haar_inv_level<TC, TI, TC, TC>, grid, 256, 0, s,
+                                       lsrc, (const TI*)in, cur, n1, n2, h, w, batch));
             NYS_LAUNCH_CK(ctx);
             lsrc = cur;
             cur = (cur == tA) ? tB : tA;

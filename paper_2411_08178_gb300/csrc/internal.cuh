@@ -9,6 +9,7 @@
 #include <cstdint>
 #include <cstdio>
 #include <string>
+#include <utility>
 #include <vector>
 
 #include "../../include/nys.h"
@@ -135,12 +136,60 @@ enum Slot {
     SLOT_COUNT = 11
 };
 void* scratch(nys_ctx* ctx, int slot, size_t bytes, int* status);
+// elements of SLOT_PROX the dual prox needs for G dual components over N
+// pixels: two (R, Q) buffers and two images
+inline size_t prox_work_elems(int G, int64_t N) { return (size_t)(4 * G + 2) * (size_t)N; }
 
 #define NYS_CK(ctx, call)                                              \
     do {                                                               \
         cudaError_t e_ = (call);                                       \
         if (e_ != cudaSuccess) return nys::cuda_fail((ctx), e_, #call); \
     } while (0)
+
+// ------------------------------------ programmatic dependent launch ----
+// The kernels of the iteration are short (a few µs at 512²) and run back to
+// back in one stream or graph, so the gap between two of them is a large part
+// of an iteration.  A kernel launched through launch_pdl() may be scheduled
+// while its predecessor in the stream is still running; it must then begin
+// with pdl_enter(), whose griddepcontrol.wait returns only once every grid
+// it depends on has completed and its writes are visible (a no-op for a
+// normal launch), before it touches memory.  The trigger after it lets the
+// next kernel be scheduled in turn.  Because every such kernel waits before
+// any access, completion stays transitive along the stream.
+// The attribute is set on eager launches only: replayed from a CUDA graph the
+// same kernels ran about 4% slower with it on a GB300 (the graph already
+// removes the launch gaps).  NYS_PDL in the environment: 0 = never, 2 = also
+// while a stream is being captured, otherwise eager launches only.
+__device__ __forceinline__ void pdl_enter() {
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
+int pdl_mode();   // api.cu: 0, 1 or 2 as above
+
+inline bool pdl_enabled(cudaStream_t stream) {
+    const int m = pdl_mode();
+    if (m == 0) return false;
+    if (m == 2) return true;
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    return cudaStreamIsCapturing(stream, &cs) == cudaSuccess && cs == cudaStreamCaptureStatusNone;
+}
+
+template <typename... KArgs, typename... Args>
+inline cudaError_t launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t stream,
+                              Args&&... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = stream;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = pdl_enabled(stream) ? 1 : 0;
+    return cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...);
+}
 
 #define NYS_LAUNCH_CK(ctx)                                             \
     do {                                                               \
@@ -209,7 +258,8 @@ int precond_run(nys_ctx* ctx, const nys_precond* pc, int inverse, int dtype, con
                 void* out, int batch);
 // the contexts an unrolled-solve handle launches on (unroll.cu)
 void unroll_contexts(const nys_unroll* U, nys_ctx** ctx, nys_ctx** op_ctx);
-// dual APG prox with the fused three-launch step (prox_fused.cu); returns
+// dual APG prox with the fused two-launch (TV) or three-launch (HS) step
+// (prox_fused.cu); returns
 // NYS_EINVAL without launching anything when the layout does not allow it
 int prox_dual_fused(nys_ctx* ctx, const nys_precond* pc, int reg, double lb, int n_inner, int dtype, int n1, int n2,
                     const void* s, void* out, void* Q);

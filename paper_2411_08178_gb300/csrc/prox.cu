@@ -38,6 +38,7 @@ namespace {
 template <class T, int REG>
 __global__ void lt_kernel(const T* __restrict__ Q, const T* __restrict__ base, typename Comp<T>::type lb, int n1,
                           int n2, T* __restrict__ out) {
+    pdl_enter();
     using TC = typename Comp<T>::type;
     const int64_t N = (int64_t)n1 * n2;
     for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < N; t += (int64_t)gridDim.x * blockDim.x) {
@@ -52,9 +53,26 @@ __global__ void lt_kernel(const T* __restrict__ Q, const T* __restrict__ base, t
 template <class T>
 __global__ void axpy_kernel(const T* __restrict__ s, const T* __restrict__ pg, typename Comp<T>::type lb, int64_t N,
                             T* __restrict__ x) {
+    pdl_enter();
     using TC = typename Comp<T>::type;
     for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < N; t += (int64_t)gridDim.x * blockDim.x)
         x[t] = (T)((TC)s[t] - lb * (TC)pg[t]);
+}
+
+// Plain (P = I) anisotropic-TV dual step fused with the x after it:
+// out = s - lb L^T R_new (L^T Q_new on the last step); out is not d.x
+template <class T>
+__global__ void tv_dual_x_kernel(TvDual<T> d, const T* __restrict__ s, typename Comp<T>::type lb, int n1, int n2,
+                                 T* __restrict__ out) {
+    pdl_enter();
+    using TC = typename Comp<T>::type;
+    const int64_t N = (int64_t)n1 * n2;
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < N; t += (int64_t)gridDim.x * blockDim.x) {
+        int i, j;
+        pix_ij(t, n2, i, j);
+        const TC g = tv_dual_lt<T>(d, i, j, n1, n2);
+        out[t] = (T)((TC)s[t] - lb * g);
+    }
 }
 
 template <class T, int REG>
@@ -65,49 +83,80 @@ int prox_dual_typed(nys_ctx* ctx, const nys_precond* pc, double lb, int n_inner,
     const double normL2 = REG == NYS_REG_TV ? 8.0 : 32.0;
     const int64_t N = (int64_t)n1 * n2;
     int st;
+    // no column with d_i > 0: P = I exactly
+    if (pc && pc->priv && ((const nys_precond_priv*)pc->priv)->ell_eff == 0) pc = nullptr;
     if (pc) {
-        // three launches per dual step (prox_fused.cu) where the layout allows
+        // two launches per TV dual step, three per HS one (prox_fused.cu),
+        // where the layout allows
         st = prox_dual_fused(ctx, pc, REG, lb, n_inner, sizeof(T) == 8 ? NYS_F64 : NYS_F32, n1, n2, s, out, Q);
         if (st != NYS_EINVAL) return st;
     }
-    T* work = (T*)scratch(ctx, SLOT_PROX, ((size_t)2 * G * N + 2 * N) * sizeof(T), &st);
+    T* work = (T*)scratch(ctx, SLOT_PROX, prox_work_elems(G, N) * sizeof(T), &st);
     if (st) return st;
-    T* R = work;
-    T* Qp = R + G * N;
-    T* x = Qp + G * N;
-    T* g = x + N;
     cudaStream_t sm = ctx->stream;
-    NYS_CK(ctx, cudaMemcpyAsync(R, Q, sizeof(T) * G * N, cudaMemcpyDeviceToDevice, sm));
-    NYS_CK(ctx, cudaMemcpyAsync(Qp, Q, sizeof(T) * G * N, cudaMemcpyDeviceToDevice, sm));
     const int grid = (int)std::min<int64_t>((N + 255) / 256, ctx->sm_count * 8);
     const int dt = sizeof(T) == 8 ? NYS_F64 : NYS_F32;
     const TC step = (TC)(1.0 / (lb * normL2));
     double t = 1.0;
+    if (!pc && REG == NYS_REG_TV) {
+        // one launch per dual step: x ping-pongs between X[0] and X[1], (R, Q)
+        // as in the preconditioned fused step (warm start from Q itself, the
+        // last step writes Q unless it reads it)
+        T* X[2] = {work, work + N};
+        T* RQ[2][2] = {{work + 2 * N, work + 2 * N + G * N}, {work + 2 * N + 2 * G * N, work + 2 * N + 3 * G * N}};
+        NYS_CK(ctx, launch_pdl(lt_kernel<T, REG>, grid, 256, 0, sm, Q, s, (TC)lb, n1, n2, n_inner ? X[0] : out));
+        NYS_LAUNCH_CK(ctx);
+        for (int k = 0; k < n_inner; ++k) {
+            const double tn = 0.5 * (1.0 + std::sqrt(1.0 + 4.0 * t * t));
+            const double beta = (t - 1.0) / tn;
+            t = tn;
+            const bool fin = k + 1 == n_inner;
+            TvDual<T> d;
+            d.x = X[k & 1];
+            d.Ro = k ? RQ[k & 1][0] : Q;
+            d.Qo = k ? RQ[k & 1][1] : Q;
+            d.Rn = fin ? nullptr : RQ[(k + 1) & 1][0];
+            d.Qn = (fin && k) ? Q : RQ[(k + 1) & 1][1];
+            d.step = step;
+            d.beta = (TC)beta;
+            NYS_CK(ctx, launch_pdl(tv_dual_x_kernel<T>, grid, 256, 0, sm, d, s, (TC)lb, n1, n2,
+                                   fin ? out : X[(k + 1) & 1]));
+            NYS_LAUNCH_CK(ctx);
+        }
+        if (n_inner == 1) NYS_CK(ctx, cudaMemcpyAsync(Q, RQ[1][1], sizeof(T) * G * N, cudaMemcpyDeviceToDevice, sm));
+        return NYS_OK;
+    }
+    T* R = work;
+    T* Qp = R + G * N;
+    T* x = Qp + G * N;
+    T* g = x + N;
+    NYS_CK(ctx, cudaMemcpyAsync(R, Q, sizeof(T) * G * N, cudaMemcpyDeviceToDevice, sm));
+    NYS_CK(ctx, cudaMemcpyAsync(Qp, Q, sizeof(T) * G * N, cudaMemcpyDeviceToDevice, sm));
     for (int k = 0; k < n_inner; ++k) {
         if (pc) {
-            lt_kernel<T, REG><<<grid, 256, 0, sm>>>(R, nullptr, TC(0), n1, n2, g);
+            NYS_CK(ctx, launch_pdl(lt_kernel<T, REG>, grid, 256, 0, sm, R, nullptr, TC(0), n1, n2, g));
             NYS_LAUNCH_CK(ctx);
             if ((st = precond_run(ctx, pc, 1, dt, g, g, 1))) return st;
-            axpy_kernel<T><<<grid, 256, 0, sm>>>(s, g, (TC)lb, N, x);
+            NYS_CK(ctx, launch_pdl(axpy_kernel<T>, grid, 256, 0, sm, s, g, (TC)lb, N, x));
         } else {
-            lt_kernel<T, REG><<<grid, 256, 0, sm>>>(R, s, (TC)lb, n1, n2, x);
+            NYS_CK(ctx, launch_pdl(lt_kernel<T, REG>, grid, 256, 0, sm, R, s, (TC)lb, n1, n2, x));
         }
         NYS_LAUNCH_CK(ctx);
         const double tn = 0.5 * (1.0 + std::sqrt(1.0 + 4.0 * t * t));
         const double beta = (t - 1.0) / tn;
         t = tn;
-        dual_update_kernel<T, REG><<<grid, 256, 0, sm>>>(x, R, Qp, step, (TC)beta, n1, n2);
+        NYS_CK(ctx, launch_pdl(dual_update_kernel<T, REG>, grid, 256, 0, sm, x, R, Qp, step, (TC)beta, n1, n2));
         NYS_LAUNCH_CK(ctx);
     }
     // Q_io <- last Q; out = s - lb P^{-1} L^T Q
     NYS_CK(ctx, cudaMemcpyAsync(Q, Qp, sizeof(T) * G * N, cudaMemcpyDeviceToDevice, sm));
     if (pc) {
-        lt_kernel<T, REG><<<grid, 256, 0, sm>>>(Qp, nullptr, TC(0), n1, n2, g);
+        NYS_CK(ctx, launch_pdl(lt_kernel<T, REG>, grid, 256, 0, sm, Qp, nullptr, TC(0), n1, n2, g));
         NYS_LAUNCH_CK(ctx);
         if ((st = precond_run(ctx, pc, 1, dt, g, g, 1))) return st;
-        axpy_kernel<T><<<grid, 256, 0, sm>>>(s, g, (TC)lb, N, out);
+        NYS_CK(ctx, launch_pdl(axpy_kernel<T>, grid, 256, 0, sm, s, g, (TC)lb, N, out));
     } else {
-        lt_kernel<T, REG><<<grid, 256, 0, sm>>>(Qp, s, (TC)lb, n1, n2, out);
+        NYS_CK(ctx, launch_pdl(lt_kernel<T, REG>, grid, 256, 0, sm, Qp, s, (TC)lb, n1, n2, out));
     }
     NYS_LAUNCH_CK(ctx);
     return NYS_OK;
@@ -142,6 +191,7 @@ __global__ void __launch_bounds__(256) ssn_eval_kernel(const T* __restrict__ U, 
                                                        const double* __restrict__ gtrial,
                                                        const SsnState* __restrict__ state, double* __restrict__ Fp,
                                                        double* __restrict__ Sp, float* __restrict__ Jp) {
+    pdl_enter();
     if (state->done) return;
     // dynamic shared memory: rr, ss (SCH doubles each), gs, sd (ell doubles
     // each), then the masked Ubar chunk ub (ell x (SCH + 1) floats)
@@ -204,6 +254,7 @@ __global__ void __launch_bounds__(1024) ssn_step_kernel(int nb, int ell, double 
                                                         double* __restrict__ gtrial, double* __restrict__ dir,
                                                         double* __restrict__ Fcur, double* __restrict__ Jw,
                                                         SsnState* __restrict__ st) {
+    pdl_enter();
     if (st->done) return;
     __shared__ double F[SMAXL];
     __shared__ double sh[32];
@@ -285,6 +336,7 @@ __global__ void __launch_bounds__(1024) ssn_step_kernel(int nb, int ell, double 
 template <class T>
 __global__ void ssn_final_kernel(const T* __restrict__ U, const double* __restrict__ sqd, const T* __restrict__ s,
                                  int64_t N, int ell, double tau, const double* __restrict__ gamma, T* __restrict__ out) {
+    pdl_enter();
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
         double z = (double)s[i];
         for (int j = 0; j < ell; ++j) z -= sqd[j] * (double)U[(size_t)j * N + i] * gamma[j];
@@ -294,11 +346,13 @@ __global__ void ssn_final_kernel(const T* __restrict__ U, const double* __restri
 
 template <class T>
 __global__ void soft_kernel(const T* __restrict__ s, int64_t N, double tau, T* __restrict__ out) {
+    pdl_enter();
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x)
         out[i] = (T)soft((double)s[i], tau);
 }
 
 __global__ void ssn_init_kernel(SsnState* st, const double* gamma_in, double* gamma, double* gtrial, int ell) {
+    pdl_enter();
     for (int j = threadIdx.x; j < ell; j += blockDim.x) {
         const double g = gamma_in ? gamma_in[j] : 0.0;
         gamma[j] = g;
@@ -344,7 +398,7 @@ int ssn_run(nys_ctx* ctx, const nys_precond* pc, double tau, int64_t N, const T*
     float* Jp = (float*)(Sp + (size_t)nb * ell);
     cudaStream_t sm = ctx->stream;
     const double tol = sizeof(T) == 8 ? 1e-12 : 1e-6;
-    ssn_init_kernel<<<1, 256, 0, sm>>>(state, gamma_io, gamma, gtrial, ell);
+    NYS_CK(ctx, launch_pdl(ssn_init_kernel, 1, 256, 0, sm, state, (const double*)gamma_io, gamma, gtrial, ell));
     NYS_LAUNCH_CK(ctx);
     const T* U = (const T*)pc->U;
     const size_t esm = (size_t)(2 * SCH + 2 * ell) * sizeof(double) + (size_t)ell * (SCH + 1) * sizeof(float);
@@ -357,10 +411,11 @@ int ssn_run(nys_ctx* ctx, const nys_precond* pc, double tau, int64_t N, const T*
     const int max_evals = max_newton * 12 + 1;
     while (true) {
         for (int e = 0; e < evals_per_batch; ++e) {
-            ssn_eval_kernel<T><<<nb, 256, esm, sm>>>(U, pv->sqrtd, s, N, ell, tau, gtrial, state, Fp, Sp, Jp);
+            NYS_CK(ctx, launch_pdl(ssn_eval_kernel<T>, nb, 256, esm, sm, U, (const double*)pv->sqrtd, s, N, ell, tau,
+                                   (const double*)gtrial, (const SsnState*)state, Fp, Sp, Jp));
             NYS_LAUNCH_CK(ctx);
-            ssn_step_kernel<<<1, 1024, 0, sm>>>(nb, ell, tol, max_newton, Fp, Sp, Jp, gamma, gtrial, dir, Fcur, Jw,
-                                                state);
+            NYS_CK(ctx, launch_pdl(ssn_step_kernel, 1, 1024, 0, sm, nb, ell, tol, max_newton, (const double*)Fp,
+                                   (const double*)Sp, (const float*)Jp, gamma, gtrial, dir, Fcur, Jw, state));
             NYS_LAUNCH_CK(ctx);
         }
         launched += evals_per_batch;
@@ -371,7 +426,8 @@ int ssn_run(nys_ctx* ctx, const nys_precond* pc, double tau, int64_t N, const T*
         if (h.done || launched >= max_evals) break;
     }
     const int grid = (int)std::min<int64_t>((N + 255) / 256, ctx->sm_count * 8);
-    ssn_final_kernel<T><<<grid, 256, 0, sm>>>(U, pv->sqrtd, s, N, ell, tau, gamma, out);
+    NYS_CK(ctx, launch_pdl(ssn_final_kernel<T>, grid, 256, 0, sm, U, (const double*)pv->sqrtd, s, N, ell, tau,
+                           (const double*)gamma, out));
     NYS_LAUNCH_CK(ctx);
     if (gamma_io) NYS_CK(ctx, cudaMemcpyAsync(gamma_io, gamma, ell * sizeof(double), cudaMemcpyDeviceToDevice, sm));
     if (info) {
@@ -393,7 +449,7 @@ template int ssn_run<double>(nys_ctx*, const nys_precond*, double, int64_t, cons
 template <class T>
 int soft_run(nys_ctx* ctx, double tau, int64_t N, const T* s, T* out) {
     const int grid = (int)std::min<int64_t>((N + 255) / 256, ctx->sm_count * 8);
-    soft_kernel<T><<<grid, 256, 0, ctx->stream>>>(s, N, tau, out);
+    NYS_CK(ctx, launch_pdl(soft_kernel<T>, grid, 256, 0, ctx->stream, s, N, tau, out));
     NYS_LAUNCH_CK(ctx);
     return NYS_OK;
 }

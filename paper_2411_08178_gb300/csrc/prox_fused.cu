@@ -3,14 +3,15 @@
 // columns of U (Eq. RYPreconditioner in Woodbury form).  One dual step
 //     x   = s - lb P^{-1} L^T R
 //     Q'  = Proj(R + step L x),  R <- Q' + beta (Q' - Q),  Q <- Q'
-// takes three launches instead of six:
-//   lt_utz   g = L^T R over a chunk of pixels (stencil from global R), written
-//            out and staged in shared memory, then the chunk's partial sums
-//            of U^T g (warps over the active columns, 16-byte loads of U);
-//            the last CTA to finish reduces the (column-major) partials and
-//            forms c = M w
+// takes two launches for anisotropic TV (three for HS) instead of six:
+//   lt_utz   TV: the dual update of the previous step fused in front of
+//            g = L^T R_new (stencil.cuh, tv_dual_lt; HS: g = L^T R) over a
+//            chunk of pixels, written out and staged in shared memory, then
+//            the chunk's partial sums of U^T g (warps over the active
+//            columns, 16-byte loads of U); the last CTA to finish reduces the
+//            (column-major) partials and forms c = M w
 //   uc       x = s - lb (g - U c)   (vec.cuh, 16-byte loads of U)
-//   dual     L x and the dual update (stencil.cuh)
+//   dual     HS only: L x and the dual update (stencil.cuh)
 // U is read twice per step, as in the unfused P^{-1} apply; the launches of
 // L^T R, the coefficient pass and x = s - lb (...) are folded away.
 #include "internal.cuh"
@@ -27,12 +28,17 @@ constexpr int FCH = 1024;        // pixels per partial-sum chunk (small active s
 constexpr int FCH_WIDE = 512;    // large active sets: twice the CTAs, more bytes of U in flight
 constexpr int COUNTER_PROX = 1;
 
-template <class TU, class T, class TA, class TM, int REG, bool LAST, int FCH>
+// DUAL: the stencil pass is the anisotropic-TV dual step fused with the L^T
+// after it (tv_dual_lt, inputs and outputs in `dual`, R unused); otherwise
+// it is L^T R.
+template <class TU, class T, class TA, class TM, int REG, bool LAST, int FCH, bool DUAL>
 __global__ void __launch_bounds__(256) lt_utz_kernel(const T* __restrict__ R, int n1, int n2,
                                                      const TU* __restrict__ U, int le, int ldm,
                                                      const TM* __restrict__ M, T* __restrict__ g,
                                                      TA* __restrict__ part, TA* __restrict__ coef,
-                                                     unsigned* __restrict__ counter) {
+                                                     unsigned* __restrict__ counter, TvDual<T> dual) {
+    pdl_enter();
+    static_assert(!DUAL || REG == NYS_REG_TV, "the fused dual step is for anisotropic TV");
     constexpr int V = Vec16<TU>::n;
     constexpr int PT = (FCH + 255) / 256;   // pixels per thread in the stencil pass
     __shared__ __align__(16) TA gs[FCH];
@@ -48,7 +54,7 @@ __global__ void __launch_bounds__(256) lt_utz_kernel(const T* __restrict__ R, in
         if (threadIdx.x + q * 256 < FCH && p < N) {
             int i, j;
             pix_ij(p, n2, i, j);
-            v[q] = (TA)lt_q<T, REG>(R, i, j, n1, n2);
+            v[q] = DUAL ? (TA)tv_dual_lt<T>(dual, i, j, n1, n2) : (TA)lt_q<T, REG>(R, i, j, n1, n2);
         }
     }
 #pragma unroll
@@ -114,9 +120,10 @@ int fused_typed(nys_ctx* ctx, const nys_precond* pc, double lb, int n_inner, int
                 T* Q) {
     using TM = typename std::conditional<sizeof(TA) == 8, double, float>::type;
     constexpr int V = Vec16<TU>::n;
+    constexpr bool TV = REG == NYS_REG_TV;
     const nys_precond_priv* pv = (const nys_precond_priv*)pc->priv;
-    const int G = REG == NYS_REG_TV ? 2 : 3;
-    const double normL2 = REG == NYS_REG_TV ? 8.0 : 32.0;
+    const int G = TV ? 2 : 3;
+    const double normL2 = TV ? 8.0 : 32.0;
     const int64_t N = (int64_t)n1 * n2;
     const int le = pv->ell_eff;
     // small active sets: the last CTA of lt_utz forms M w; large ones: two
@@ -126,19 +133,16 @@ int fused_typed(nys_ctx* ctx, const nys_precond* pc, double lb, int n_inner, int
     const int fch = last ? FCH : FCH_WIDE;
     const int nchunk = (int)((N + fch - 1) / fch);
     int st;
-    T* work = (T*)scratch(ctx, SLOT_PROX, ((size_t)2 * G * N + 2 * N) * sizeof(T), &st);
+    T* work = (T*)scratch(ctx, SLOT_PROX, prox_work_elems(G, N) * sizeof(T), &st);
     if (st) return st;
-    T* R = work;
-    T* Qp = R + G * N;
-    T* g = Qp + G * N;
+    T* g = work;
     T* x = g + N;
+    T* RQ[2][2] = {{x + N, x + N + G * N}, {x + N + 2 * G * N, x + N + 3 * G * N}};   // [buffer][R, Q]
     TA* part = (TA*)scratch(ctx, SLOT_PRECOND, ((size_t)nchunk * std::max(le, 1) + 2 * std::max(le, 1)) * sizeof(TA), &st);
     if (st) return st;
     TA* coef = part + (size_t)nchunk * std::max(le, 1);
     TA* wbuf = coef + std::max(le, 1);
     cudaStream_t sm = ctx->stream;
-    NYS_CK(ctx, cudaMemcpyAsync(R, Q, sizeof(T) * G * N, cudaMemcpyDeviceToDevice, sm));
-    NYS_CK(ctx, cudaMemcpyAsync(Qp, Q, sizeof(T) * G * N, cudaMemcpyDeviceToDevice, sm));
     const TM* M = sizeof(TA) == 8 ? (const TM*)pv->M64 : (const TM*)pv->M32;
     const size_t lsm = ((size_t)le + (le <= 64 ? (size_t)le * le : 0)) * sizeof(TA) + 16;
     // x pass: large active sets take two 16-byte vectors per lane and two
@@ -150,39 +154,76 @@ int fused_typed(nys_ctx* ctx, const nys_precond* pc, double lb, int n_inner, int
     const int dg = (int)std::min<int64_t>((N + 255) / 256, (int64_t)ctx->sm_count * 8);
     const TA step = (TA)(1.0 / (lb * normL2));
     unsigned* counter = ctx->counters + COUNTER_PROX;
-    // x (or out) = s - lb P^{-1} L^T Rin
-    auto xfn = [&](const T* Rin, T* dst) -> int {
+    // g = L^T Rin, or the fused TV dual step and the L^T after it (dual.x
+    // set); then x (or out) = s - lb (g - U c), c = M U^T g
+    auto xfn = [&](const T* Rin, const TvDual<T>& dual, T* dst) -> int {
         if (last) {
-            lt_utz_kernel<TU, T, TA, TM, REG, true, FCH><<<nchunk, 256, lsm, sm>>>(Rin, n1, n2, (const TU*)pc->U, le,
-                                                                                     pc->ell, M, g, part, coef, counter);
+            if (dual.x)
+                NYS_CK(ctx, launch_pdl(lt_utz_kernel<TU, T, TA, TM, REG, true, FCH, TV>, nchunk, 256, lsm, sm, Rin,
+                                       n1, n2, (const TU*)pc->U, le, pc->ell, M, g, part, coef, counter, dual));
+            else
+                NYS_CK(ctx, launch_pdl(lt_utz_kernel<TU, T, TA, TM, REG, true, FCH, false>, nchunk, 256, lsm, sm, Rin,
+                                       n1, n2, (const TU*)pc->U, le, pc->ell, M, g, part, coef, counter, dual));
             NYS_LAUNCH_CK(ctx);
         } else {
-            lt_utz_kernel<TU, T, TA, TM, REG, false, FCH_WIDE><<<nchunk, 256, 16, sm>>>(
-                Rin, n1, n2, (const TU*)pc->U, le, pc->ell, M, g, part, coef, counter);
+            if (dual.x)
+                NYS_CK(ctx, launch_pdl(lt_utz_kernel<TU, T, TA, TM, REG, false, FCH_WIDE, TV>, nchunk, 256, 16, sm,
+                                       Rin, n1, n2, (const TU*)pc->U, le, pc->ell, M, g, part, coef, counter, dual));
+            else
+                NYS_CK(ctx, launch_pdl(lt_utz_kernel<TU, T, TA, TM, REG, false, FCH_WIDE, false>, nchunk, 256, 16, sm,
+                                       Rin, n1, n2, (const TU*)pc->U, le, pc->ell, M, g, part, coef, counter, dual));
             NYS_LAUNCH_CK(ctx);
             int st2 = coef_run<TA, TM>(ctx, part, nchunk, le, pc->ell, 1, M, (const TM*)nullptr, coef, 1, wbuf);
             if (st2) return st2;
         }
         if (pvx == 1)
-            uc_vec_kernel<TU, T, TA><<<dim3(ug, 1), 256, usm, sm>>>((const TU*)pc->U, g, N, le, coef, TA(-1), dst, s,
-                                                                    (TA)(-lb));
+            NYS_CK(ctx, launch_pdl(uc_vec_kernel<TU, T, TA>, dim3(ug, 1), 256, usm, sm, (const TU*)pc->U, g, N, le,
+                                   coef, TA(-1), dst, s, (TA)(-lb)));
         else
-            uc_vec_kernel<TU, T, TA, 2, 2><<<dim3(ug, 1), 256, usm, sm>>>((const TU*)pc->U, g, N, le, coef, TA(-1), dst,
-                                                                          s, (TA)(-lb));
+            NYS_CK(ctx, launch_pdl(uc_vec_kernel<TU, T, TA, 2, 2>, dim3(ug, 1), 256, usm, sm, (const TU*)pc->U, g, N,
+                                   le, coef, TA(-1), dst, s, (TA)(-lb)));
         NYS_LAUNCH_CK(ctx);
         return NYS_OK;
     };
+    const TvDual<T> none = {};
     double t = 1.0;
+    if (TV) {
+        // warm start R = Q = Q_in; step k reads (R, Q) from RQ[k & 1] (Q_in
+        // itself for k = 0) and writes RQ[(k + 1) & 1]; the last step writes
+        // only Q, straight into Q_in when that is not its own input
+        if ((st = xfn(Q, none, n_inner ? x : out))) return st;
+        for (int k = 0; k < n_inner; ++k) {
+            const double tn = 0.5 * (1.0 + std::sqrt(1.0 + 4.0 * t * t));
+            const double beta = (t - 1.0) / tn;
+            t = tn;
+            const bool fin = k + 1 == n_inner;
+            TvDual<T> d;
+            d.x = x;
+            d.Ro = k ? RQ[k & 1][0] : Q;
+            d.Qo = k ? RQ[k & 1][1] : Q;
+            d.Rn = fin ? nullptr : RQ[(k + 1) & 1][0];
+            d.Qn = (fin && k) ? Q : RQ[(k + 1) & 1][1];
+            d.step = step;
+            d.beta = (TA)beta;
+            if ((st = xfn(nullptr, d, fin ? out : x))) return st;
+        }
+        if (n_inner == 1) NYS_CK(ctx, cudaMemcpyAsync(Q, RQ[1][1], sizeof(T) * G * N, cudaMemcpyDeviceToDevice, sm));
+        return NYS_OK;
+    }
+    T* R = RQ[0][0];
+    T* Qp = RQ[0][1];
+    NYS_CK(ctx, cudaMemcpyAsync(R, Q, sizeof(T) * G * N, cudaMemcpyDeviceToDevice, sm));
+    NYS_CK(ctx, cudaMemcpyAsync(Qp, Q, sizeof(T) * G * N, cudaMemcpyDeviceToDevice, sm));
     for (int k = 0; k < n_inner; ++k) {
-        if ((st = xfn(R, x))) return st;
+        if ((st = xfn(R, none, x))) return st;
         const double tn = 0.5 * (1.0 + std::sqrt(1.0 + 4.0 * t * t));
         const double beta = (t - 1.0) / tn;
         t = tn;
-        dual_update_kernel<T, REG><<<dg, 256, 0, sm>>>(x, R, Qp, step, (TA)beta, n1, n2);
+        NYS_CK(ctx, launch_pdl(dual_update_kernel<T, REG>, dg, 256, 0, sm, x, R, Qp, step, (TA)beta, n1, n2));
         NYS_LAUNCH_CK(ctx);
     }
     NYS_CK(ctx, cudaMemcpyAsync(Q, Qp, sizeof(T) * G * N, cudaMemcpyDeviceToDevice, sm));
-    return xfn(Qp, out);
+    return xfn(Qp, none, out);
 }
 
 }  // namespace

@@ -67,6 +67,7 @@ __device__ __forceinline__ void sample_pos(int qi, TC qf, int ri, TC rf, int& lo
 // xT[b][j][i] = x[b][i][j]
 template <class TI, class TC>
 __global__ void radon_prep_kernel(const TI* __restrict__ x, TC* __restrict__ xr, TC* __restrict__ xT, int n1, int n2) {
+    pdl_enter();
     __shared__ TC tile[32][33];
     const int b = blockIdx.z;
     const int i0 = blockIdx.y * 32, j0 = blockIdx.x * 32;
@@ -92,6 +93,7 @@ template <class TC, class TO, int IB>
 __global__ void __launch_bounds__(256) radon_fwd2_kernel(const TC* __restrict__ xr, const TC* __restrict__ xT,
                                                          TO* __restrict__ y, int n1, int n2, int n_angles,
                                                          int n_bins, int batch, RTab<TC> tab) {
+    pdl_enter();
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int k = blockIdx.x;
     const int b0 = blockIdx.y * IB;
@@ -167,6 +169,7 @@ template <class TI, class TO, class TC, int IB, int AK>
 __global__ void __launch_bounds__(256) radon_adj2_kernel(const TI* __restrict__ s, TO* __restrict__ x, int n1, int n2,
                                                          int n_angles, int n_bins, int batch, RTab<TC> tab, TC c1,
                                                          TC c2, TC cb) {
+    pdl_enter();
     extern __shared__ __align__(16) unsigned char smem_raw[];
     // per-angle scalars for every angle, staged once
     int* g_rs = reinterpret_cast<int*>(smem_raw);
@@ -391,25 +394,28 @@ int radon_fwd(nys_op* op, const void* x, void* y, int batch) {
         const TI* xb = (const TI*)x + (size_t)b0 * N;
         // the row-major source is x itself when it already has the compute type
         const bool same = std::is_same<TI, TC>::value;
-        radon_prep_kernel<TI, TC><<<dim3((op->n2 + 31) / 32, (op->n1 + 31) / 32, nb), dim3(32, 8), 0, st>>>(
-            xb, same ? nullptr : xr, xT, op->n1, op->n2);
+        NYS_CK(op->ctx, launch_pdl(radon_prep_kernel<TI, TC>, dim3((op->n2 + 31) / 32, (op->n1 + 31) / 32, nb),
+                                   dim3(32, 8), 0, st, xb, same ? nullptr : xr, xT, op->n1, op->n2));
         NYS_LAUNCH_CK(op->ctx);
         const TC* src_r = same ? (const TC*)xb : xr;
         TO* yb = (TO*)y + (size_t)b0 * op->M;
         if (nb >= 4) {
             const int full = nb / 4 * 4;
-            radon_fwd2_kernel<TC, TO, 4><<<dim3(op->n_angles, full / 4), 256, sm, st>>>(
-                src_r, xT, yb, op->n1, op->n2, op->n_angles, op->n_bins, full, tables<TC>(op));
+            NYS_CK(op->ctx, launch_pdl(radon_fwd2_kernel<TC, TO, 4>, dim3(op->n_angles, full / 4), 256, sm, st, src_r,
+                                       (const TC*)xT, yb, op->n1, op->n2, op->n_angles, op->n_bins, full,
+                                       tables<TC>(op)));
             NYS_LAUNCH_CK(op->ctx);
             if (full < nb) {
-                radon_fwd2_kernel<TC, TO, 1><<<dim3(op->n_angles, nb - full), 256, sm, st>>>(
-                    src_r + (size_t)full * N, xT + (size_t)full * N, yb + (size_t)full * op->M, op->n1, op->n2,
-                    op->n_angles, op->n_bins, nb - full, tables<TC>(op));
+                NYS_CK(op->ctx, launch_pdl(radon_fwd2_kernel<TC, TO, 1>, dim3(op->n_angles, nb - full), 256, sm, st,
+                                           src_r + (size_t)full * N, (const TC*)(xT + (size_t)full * N),
+                                           yb + (size_t)full * op->M, op->n1, op->n2, op->n_angles, op->n_bins,
+                                           nb - full, tables<TC>(op)));
                 NYS_LAUNCH_CK(op->ctx);
             }
         } else {
-            radon_fwd2_kernel<TC, TO, 1><<<dim3(op->n_angles, nb), 256, sm, st>>>(
-                src_r, xT, yb, op->n1, op->n2, op->n_angles, op->n_bins, nb, tables<TC>(op));
+            NYS_CK(op->ctx, launch_pdl(radon_fwd2_kernel<TC, TO, 1>, dim3(op->n_angles, nb), 256, sm, st, src_r,
+                                       (const TC*)xT, yb, op->n1, op->n2, op->n_angles, op->n_bins, nb,
+                                       tables<TC>(op)));
             NYS_LAUNCH_CK(op->ctx);
         }
     }
@@ -430,9 +436,10 @@ void radon_adj_launch(nys_op* op, const TI* s, TO* x, int nb) {
                                  (int)sm);
         attr = sm;
     }
-    radon_adj2_kernel<TI, TO, TC, IB, AK><<<grid, 256, sm, op->ctx->stream>>>(
-        s, x, op->n1, op->n2, op->n_angles, op->n_bins, nb, tables<TC>(op), (TC)((op->n1 - 1) / 2.0),
-        (TC)((op->n2 - 1) / 2.0), (TC)((op->n_bins - 1) / 2.0));
+    // a launch error is left for the caller's launch check (cudaGetLastError)
+    (void)launch_pdl(radon_adj2_kernel<TI, TO, TC, IB, AK>, grid, 256, sm, op->ctx->stream, s, x, op->n1, op->n2,
+                     op->n_angles, op->n_bins, nb, tables<TC>(op), (TC)((op->n1 - 1) / 2.0), (TC)((op->n2 - 1) / 2.0),
+                     (TC)((op->n_bins - 1) / 2.0));
 }
 
 template <class TI, class TO, class TC>

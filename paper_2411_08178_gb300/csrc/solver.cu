@@ -61,12 +61,14 @@ namespace {
 
 template <class T>
 __global__ void sub_kernel(T* __restrict__ a, const T* __restrict__ b, int64_t n) {
+    pdl_enter();
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
         a[i] = a[i] - b[i];
 }
 
 template <class T>
 __global__ void huber_resid_kernel(T* __restrict__ r, const T* __restrict__ y, int64_t n, double delta) {
+    pdl_enter();
     using TC = typename Comp<T>::type;
     const TC d = (TC)delta;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
@@ -77,6 +79,7 @@ __global__ void huber_resid_kernel(T* __restrict__ r, const T* __restrict__ y, i
 template <class T>
 __global__ void step_kernel(const T* __restrict__ u, const T* __restrict__ g, double alpha, int64_t n,
                             T* __restrict__ s) {
+    pdl_enter();
     using TC = typename Comp<T>::type;
     const TC a = (TC)alpha;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
@@ -88,6 +91,7 @@ __global__ void step_kernel(const T* __restrict__ u, const T* __restrict__ g, do
 template <class T>
 __global__ void momentum_kernel(const T* __restrict__ xn, const T* __restrict__ x, const double* __restrict__ t_in,
                                 double* __restrict__ t_out, int64_t n, T* __restrict__ u) {
+    pdl_enter();
     using TC = typename Comp<T>::type;
     const double t = *t_in;
     const double tn = 0.5 * (1.0 + sqrt(1.0 + 4.0 * t * t));
@@ -103,6 +107,7 @@ __global__ void momentum_kernel(const T* __restrict__ xn, const T* __restrict__ 
 // CTA sums the partials in the same order, w /= ||w|| and out[0] = ||w||
 template <class T>
 __global__ void __launch_bounds__(256) sumsq_part_kernel(const T* __restrict__ w, int64_t n, double* __restrict__ part) {
+    pdl_enter();
     __shared__ double sh[32];
     double s = 0.0;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
@@ -117,6 +122,7 @@ template <class T>
 __global__ void __launch_bounds__(256) scale_by_norm_kernel(T* __restrict__ w, int64_t n,
                                                             const double* __restrict__ part, int np,
                                                             double* __restrict__ out) {
+    pdl_enter();
     __shared__ double sh[32];
     double s = 0.0;
     for (int t = threadIdx.x; t < np; t += blockDim.x) s += part[t];
@@ -223,25 +229,27 @@ int gradient(nys_solver* S) {
         if ((st = haar_run(op, S->u, S->tN, 1, 1, dt, dt))) return st;
         if (S->d.fit == NYS_FIT_HUBER) {
             if ((st = op_run(op, 0, S->tN, S->tM, 1, dt, dt))) return st;
-            huber_resid_kernel<T><<<gM, 256, 0, ctx->stream>>>((T*)S->tM, (const T*)S->y, S->M, S->d.huber_delta);
+            NYS_CK(ctx, launch_pdl(huber_resid_kernel<T>, gM, 256, 0, ctx->stream, (T*)S->tM, (const T*)S->y, S->M,
+                               S->d.huber_delta));
             NYS_LAUNCH_CK(ctx);
             if ((st = op_run(op, 1, S->tM, S->s, 1, dt, dt))) return st;
             return haar_run(op, S->s, S->g, 1, 0, dt, dt);
         }
         if ((st = op_run(op, 2, S->tN, S->s, 1, dt, dt))) return st;
         if ((st = haar_run(op, S->s, S->g, 1, 0, dt, dt))) return st;
-        sub_kernel<T><<<gN, 256, 0, ctx->stream>>>((T*)S->g, (const T*)S->aty, S->N);
+        NYS_CK(ctx, launch_pdl(sub_kernel<T>, gN, 256, 0, ctx->stream, (T*)S->g, (const T*)S->aty, S->N));
         NYS_LAUNCH_CK(ctx);
         return NYS_OK;
     }
     if (S->d.fit == NYS_FIT_HUBER) {
         if ((st = op_run(op, 0, S->u, S->tM, 1, dt, dt))) return st;
-        huber_resid_kernel<T><<<gM, 256, 0, ctx->stream>>>((T*)S->tM, (const T*)S->y, S->M, S->d.huber_delta);
+        NYS_CK(ctx, launch_pdl(huber_resid_kernel<T>, gM, 256, 0, ctx->stream, (T*)S->tM, (const T*)S->y, S->M,
+                               S->d.huber_delta));
         NYS_LAUNCH_CK(ctx);
         return op_run(op, 1, S->tM, S->g, 1, dt, dt);
     }
     if ((st = op_run(op, 2, S->u, S->g, 1, dt, dt))) return st;
-    sub_kernel<T><<<gN, 256, 0, ctx->stream>>>((T*)S->g, (const T*)S->aty, S->N);
+    NYS_CK(ctx, launch_pdl(sub_kernel<T>, gN, 256, 0, ctx->stream, (T*)S->g, (const T*)S->aty, S->N));
     NYS_LAUNCH_CK(ctx);
     return NYS_OK;
 }
@@ -256,7 +264,8 @@ int iterate_one(nys_solver* S, int par) {
     int st;
     if ((st = gradient<T>(S))) return st;
     if (S->pc && (st = precond_run(ctx, S->pc, 1, S->dt, S->g, S->g, 1))) return st;
-    step_kernel<T><<<gN, 256, 0, ctx->stream>>>((const T*)S->u, (const T*)S->g, S->alpha, S->N, (T*)S->s);
+    NYS_CK(ctx, launch_pdl(step_kernel<T>, gN, 256, 0, ctx->stream, (const T*)S->u, (const T*)S->g, S->alpha, S->N,
+                           (T*)S->s));
     NYS_LAUNCH_CK(ctx);
     const double tau = S->alpha * S->d.lambda;
     if (S->d.reg == NYS_REG_WAVELET) {
@@ -266,8 +275,8 @@ int iterate_one(nys_solver* S, int par) {
         st = prox_dual_run(ctx, S->pc, S->d.reg, tau, S->d.n_inner, S->dt, S->op->n1, S->op->n2, S->s, xn, S->Q);
     }
     if (st) return st;
-    momentum_kernel<T><<<gN, 256, 0, ctx->stream>>>((const T*)xn, (const T*)x, S->pw + 2 + par, S->pw + 2 + (par ^ 1),
-                                                    S->N, (T*)S->u);
+    NYS_CK(ctx, launch_pdl(momentum_kernel<T>, gN, 256, 0, ctx->stream, (const T*)xn, (const T*)x, S->pw + 2 + par,
+                           S->pw + 2 + (par ^ 1), S->N, (T*)S->u));
     NYS_LAUNCH_CK(ctx);
     return NYS_OK;
 }
@@ -343,9 +352,9 @@ int estimate_alpha(nys_solver* S) {
     NYS_LAUNCH_CK(ctx);
     const int gN = grid_for(ctx, S->N);
     auto normalise = [&](T* v) -> int {
-        sumsq_part_kernel<T><<<gN, 256, 0, s>>>(v, S->N, S->npart);
+        NYS_CK(ctx, launch_pdl(sumsq_part_kernel<T>, gN, 256, 0, s, v, S->N, S->npart));
         NYS_LAUNCH_CK(ctx);
-        scale_by_norm_kernel<T><<<gN, 256, 0, s>>>(v, S->N, S->npart, gN, S->pw);
+        NYS_CK(ctx, launch_pdl(scale_by_norm_kernel<T>, gN, 256, 0, s, v, S->N, (const double*)S->npart, gN, S->pw));
         NYS_LAUNCH_CK(ctx);
         return NYS_OK;
     };
@@ -439,7 +448,7 @@ int create_typed(nys_solver* S, const void* y) {
     if ((st = reset_state<T>(S))) return st;
     // reserve the scratch that pgd_step uses, so later steps never allocate
     if (S->G) {
-        if (!scratch(ctx, SLOT_PROX, ((size_t)2 * S->G * N + 2 * N) * es, &st)) return st;
+        if (!scratch(ctx, SLOT_PROX, prox_work_elems(S->G, N) * es, &st)) return st;
     }
     if (S->pc) {
         // the largest of the P^{-1} / prox partial-sum layouts (chunks of 1024 or

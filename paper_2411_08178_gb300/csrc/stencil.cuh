@@ -94,6 +94,53 @@ __device__ __forceinline__ void dual_pixel(const typename Comp<T>::type* Lx, T* 
     }
 }
 
+// Inputs and outputs of one anisotropic-TV dual step fused with the L^T that
+// follows it: the old (R, Q) are read from Ro/Qo and the new ones written to
+// Rn/Qn (other buffers: a CTA recomputes the new values of its neighbours, so
+// nothing may be overwritten in place); Rn null = the last step, which keeps
+// only Q.
+template <class T>
+struct TvDual {
+    const T* x;
+    const T* Ro;
+    const T* Qo;
+    T* Rn;
+    T* Qn;
+    typename Comp<T>::type step, beta;
+};
+
+// Anisotropic TV: the dual step at pixel (i, j) and L^T of its result there.
+// L x is the pair of backward differences, so the new R at (i, j) needs x at
+// (i, j), (i-1, j), (i, j-1); L^T needs the new first component at (i+1, j)
+// and the new second one at (i, j+1), recomputed here from x, Ro and Qo (the
+// projection is a clip per component, so each needs only its own inputs).
+// Writes the new (R, Q) at (i, j) and returns L^T R_new (L^T Q_new on the
+// last step).  The storage type is the compute type here (float32 or
+// float64 iterates), and explicit fma keeps the recomputed neighbour values
+// bit-identical to the ones their own pixel writes.
+template <class T>
+__device__ __forceinline__ typename Comp<T>::type tv_dual_lt(const TvDual<T>& d, int i, int j, int n1, int n2) {
+    using TC = typename Comp<T>::type;
+    const size_t N = (size_t)n1 * n2;
+    const size_t r0 = (size_t)i * n2, rm = (size_t)wrap_dec(i, n1) * n2, rp = (size_t)wrap_inc(i, n1) * n2;
+    const int jm = wrap_dec(j, n2), jp = wrap_inc(j, n2);
+    const size_t t = r0 + j, td = rp + j, tr = r0 + jp;
+    const TC xc = (TC)d.x[t];
+    const TC lx1 = xc - (TC)d.x[rm + j], lx1d = (TC)d.x[td] - xc;
+    const TC lx2 = xc - (TC)d.x[r0 + jm], lx2r = (TC)d.x[tr] - xc;
+    auto proj = [&](size_t e, TC lx) { return fmin(TC(1), fmax(TC(-1), fma(d.step, lx, (TC)d.Ro[e]))); };
+    const TC q1 = proj(t, lx1), q1d = proj(td, lx1d);
+    const TC q2 = proj(N + t, lx2), q2r = proj(N + tr, lx2r);
+    d.Qn[t] = (T)q1;
+    d.Qn[N + t] = (T)q2;
+    if (!d.Rn) return q1 - q1d + q2 - q2r;
+    auto mom = [&](size_t e, TC q) { return fma(d.beta, q - (TC)d.Qo[e], q); };
+    const TC r1 = mom(t, q1), r2 = mom(N + t, q2);
+    d.Rn[t] = (T)r1;
+    d.Rn[N + t] = (T)r2;
+    return r1 - mom(td, q1d) + r2 - mom(N + tr, q2r);
+}
+
 namespace {
 
 // Q' = Proj(R + step * L x); R <- Q' + beta (Q' - Qp); Qp <- Q' over the image
@@ -101,6 +148,7 @@ namespace {
 template <class T, int REG>
 __global__ void dual_update_kernel(const T* __restrict__ x, T* __restrict__ R, T* __restrict__ Qp,
                                    typename Comp<T>::type step, typename Comp<T>::type beta, int n1, int n2) {
+    pdl_enter();
     using TC = typename Comp<T>::type;
     const int64_t N = (int64_t)n1 * n2;
     for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < N; t += (int64_t)gridDim.x * blockDim.x) {

@@ -118,6 +118,7 @@ template <class TA, class TM>
 __global__ void __launch_bounds__(256) coef_vec_kernel(const TA* __restrict__ part, int nb, int le, int ldm,
                                                        int inverse, const TM* __restrict__ M,
                                                        const TM* __restrict__ d, TA* __restrict__ coef) {
+    pdl_enter();
     extern __shared__ __align__(16) unsigned char smem_raw[];
     TA* w = reinterpret_cast<TA*>(smem_raw);
     const int b = blockIdx.y;
@@ -132,6 +133,7 @@ __global__ void __launch_bounds__(256) coef_vec_kernel(const TA* __restrict__ pa
 template <class TA>
 __global__ void __launch_bounds__(256) reduce_cols_kernel(const TA* __restrict__ part, int nb, int le,
                                                           TA* __restrict__ w) {
+    pdl_enter();
     const int j = blockIdx.x * 8 + (threadIdx.x >> 5), lane = threadIdx.x & 31, b = blockIdx.y;
     if (j >= le) return;
     const TA* p = part + ((size_t)b * le + j) * nb;
@@ -154,6 +156,7 @@ template <class TA, class TM>
 __global__ void __launch_bounds__(256) mw_kernel(const TM* __restrict__ M, int ldm, int inverse,
                                                  const TM* __restrict__ d, const TA* __restrict__ w, int le,
                                                  TA* __restrict__ coef) {
+    pdl_enter();
     extern __shared__ __align__(16) unsigned char smem_raw[];
     TA* ws = reinterpret_cast<TA*>(smem_raw);
     const int b = blockIdx.y;
@@ -169,14 +172,15 @@ int coef_run(nys_ctx* ctx, const TA* part, int nb, int le, int ldm, int inverse,
              TA* coef, int batch, TA* wbuf = nullptr) {
     cudaStream_t s = ctx->stream;
     if (le <= 64 || !wbuf) {
-        coef_vec_kernel<TA, TM><<<dim3((le + 31) / 32, batch), 256, le * sizeof(TA), s>>>(part, nb, le, ldm, inverse,
-                                                                                         M, d, coef);
+        NYS_CK(ctx, launch_pdl(coef_vec_kernel<TA, TM>, dim3((le + 31) / 32, batch), 256, le * sizeof(TA), s, part,
+                               nb, le, ldm, inverse, M, d, coef));
         NYS_LAUNCH_CK(ctx);
         return NYS_OK;
     }
-    reduce_cols_kernel<TA><<<dim3((le + 7) / 8, batch), 256, 0, s>>>(part, nb, le, wbuf);
+    NYS_CK(ctx, launch_pdl(reduce_cols_kernel<TA>, dim3((le + 7) / 8, batch), 256, 0, s, part, nb, le, wbuf));
     NYS_LAUNCH_CK(ctx);
-    mw_kernel<TA, TM><<<dim3((le + 7) / 8, batch), 256, le * sizeof(TA), s>>>(M, ldm, inverse, d, wbuf, le, coef);
+    NYS_CK(ctx, launch_pdl(mw_kernel<TA, TM>, dim3((le + 7) / 8, batch), 256, le * sizeof(TA), s, M, ldm, inverse, d,
+                           wbuf, le, coef));
     NYS_LAUNCH_CK(ctx);
     return NYS_OK;
 }
@@ -231,6 +235,7 @@ __global__ void __launch_bounds__(256) uc_vec_kernel(const TU* __restrict__ U, c
                                                      int ell, const TA* __restrict__ coef, TA sign,
                                                      TZ* __restrict__ out, const TZ* __restrict__ base = nullptr,
                                                      TA scale = TA(1)) {
+    pdl_enter();
     constexpr int V = Vec16<TU>::n;
     constexpr int P = 32 * V * PV;
     extern __shared__ __align__(16) unsigned char smem_raw[];

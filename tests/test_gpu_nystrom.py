@@ -200,7 +200,7 @@ def test_precond_degenerate_is_reported(env):
 @pytest.mark.parametrize("precond", [False, True])
 @pytest.mark.parametrize("shape", [(40, 52), (27, 31)])
 def test_prox_dual_matches_oracle(env, dt, reg, precond, shape):
-    # (40, 52): the fused three-launch dual step with partial 8 x 64 tiles;
+    # (40, 52): the fused dual step (two launches for TV, three for HS);
     # (27, 31): N not a multiple of the vector width, the unfused path
     torch, api, ctx = env
     (n1, n2), ell = shape, 10
@@ -212,8 +212,10 @@ def test_prox_dual_matches_oracle(env, dt, reg, precond, shape):
         h = gaussian_kernel(5, 1.0)
         opo = O.Operator("blur", n1, n2, kernel=h)
         ref = oracle.nystrom.nystrom(_flat_phi(opo, n1, n2), gaussian_matrix(n1 * n2, ell, 7), EPS64)
-        P = oracle.nystrom.Precond(ref["U"], ref["S_hat"])
-        pc = api.Precond(ctx, n1 * n2, ell, tdt).import_factor(ref["U"], ref["S_hat"], 0.0, True)
+        # without the sqrt heuristic: 9 of the 10 columns get d_i > 0 here
+        P = oracle.nystrom.Precond(ref["U"], ref["S_hat"], 0.0, False)
+        pc = api.Precond(ctx, n1 * n2, ell, tdt).import_factor(ref["U"], ref["S_hat"], 0.0, False)
+        assert pc.ell_active == ell - 1
     x_ref, Q_ref = oracle.prox.prox_dual(s, reg, lb, P, n_inner)
     sg = torch.from_numpy(s).to(tdt).cuda()
     fn = api.prox_tv if reg == "tv" else api.prox_hs
@@ -225,6 +227,36 @@ def test_prox_dual_matches_oracle(env, dt, reg, precond, shape):
     x2, Q2 = fn(ctx, pc, lb, n_inner, sg, Q=Q)
     x2_ref, _ = oracle.prox.prox_dual(s, reg, lb, P, n_inner, Q0=Q_ref)
     assert rel(x2.cpu(), x2_ref) < tol * 10
+
+
+@pytest.mark.parametrize("precond", [False, True, "inactive"])
+@pytest.mark.parametrize("n_inner", [0, 1, 2, 3, 7])
+def test_prox_tv_fused_dual_step_inner_counts(env, precond, n_inner):
+    # the TV dual step fused with the L^T after it keeps (R, Q) in two
+    # buffers, starts from the caller's Q and writes the last Q back into it:
+    # every inner count from 0 up, from a nonzero warm start, against the
+    # oracle; "inactive": a factor with no d_i > 0, where P = I exactly
+    torch, api, ctx = env
+    n1, n2, ell = 40, 52, 10
+    s = phantom(max(n1, n2), 6, 3, "mixed")[:n1, :n2] + 0.05 * gaussian_probe_like((n1, n2), 13)
+    Q0 = np.clip(np.random.default_rng(4).normal(0.0, 0.6, (2, n1, n2)), -1.0, 1.0)
+    lb = 0.02
+    P, pc = oracle.nystrom.Identity(), None
+    if precond:
+        h = gaussian_kernel(5, 1.0)
+        opo = O.Operator("blur", n1, n2, kernel=h)
+        ref = oracle.nystrom.nystrom(_flat_phi(opo, n1, n2), gaussian_matrix(n1 * n2, ell, 7), EPS64)
+        S_hat = ref["S_hat"] if precond is True else np.full(ell, ref["S_hat"][-1])   # all d_i = 0
+        P = oracle.nystrom.Precond(ref["U"], S_hat, 0.0, False)
+        pc = api.Precond(ctx, n1 * n2, ell, torch.float64).import_factor(ref["U"], S_hat, 0.0, False)
+        assert pc.ell_active == (ell - 1 if precond is True else 0)
+    x_ref, Q_ref = oracle.prox.prox_dual(s, "tv", lb, P, n_inner, Q0=Q0)
+    Qg = torch.from_numpy(Q0).cuda()
+    x, Q = api.prox_tv(ctx, pc, lb, n_inner, torch.from_numpy(s).cuda(), Q=Qg)
+    assert rel(x.cpu(), x_ref) < 1e-12
+    assert rel(Q.cpu(), Q_ref) < 1e-12
+    if n_inner == 0:
+        assert torch.equal(Q.cpu(), torch.from_numpy(Q0))
 
 
 @pytest.mark.parametrize("ell,reg", [(16, "tv"), (16, "hs"), (96, "tv")])
