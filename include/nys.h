@@ -122,11 +122,12 @@ int nys_op_set_kernel(nys_op* op, const double* kernel, int kh, int kw);
 
 /* Project autotuner: times the operator's launch variants on scratch data
  * of `batch` images (batch >= 1) on the ctx stream and keeps the fastest for
- * this op -- the blur output tile (32 or 64 pixels square, float32 ops) or the
- * number of angles the Radon adjoint stages per round (4, 8 or 16; at most 8
- * for float64).  *choice (may be NULL) receives the value kept.  Allocates
- * and frees scratch and synchronises; not capturable.  Results are the same
- * for every variant up to float summation order. */
+ * this op -- the blur output tile (32 or 64 pixels square, float32 ops) or,
+ * for the Radon adjoint, the number of angles per round (4, 8 or 16) and then,
+ * for batch >= 4, the images per CTA (4 or 1).  *choice (may be NULL)
+ * receives the value kept for the first knob (tile side or angles per round).
+ * Allocates and frees scratch and synchronises; not capturable.  Results are
+ * the same for every variant up to float summation order. */
 int nys_op_autotune(nys_op* op, int batch, int* choice);
 
 /* y[b] = A x[b], b < batch.  x: batch*N, y: batch*M, op dtype. */

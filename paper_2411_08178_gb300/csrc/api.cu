@@ -305,23 +305,30 @@ int nys_op_autotune(nys_op* op, int batch, int* choice) {
         cleanup();
         return cuda_fail(ctx, e, "nys_op_autotune scratch");
     }
-    // candidates: the variant knob and the operator pass it affects
-    std::vector<int> cand;
+    // stages of (knob, candidates), tuned one after the other on the operator
+    // pass they affect
+    struct Stage {
+        int* knob;
+        std::vector<int> cand;
+    };
+    std::vector<Stage> stages;
     int which = 2;
-    int* knob = nullptr;
+    int* knob = nullptr;   // the one reported through `choice`
     if (op->kind == NYS_OP_RADON) {
         knob = &op->radon_adj_ak;
-        cand = op->dtype == NYS_F64 ? std::vector<int>{4, 8} : std::vector<int>{4, 8, 16};
+        stages.push_back({&op->radon_adj_ak, {4, 8, 16}});
+        if (batch >= 4) stages.push_back({&op->radon_adj_ib, {4, 1}});
         which = 1;
     } else if (op->kind == NYS_OP_BLUR && op->dtype != NYS_F64) {
         knob = &op->blur_tile;
-        cand = {32, 64};
+        stages.push_back({&op->blur_tile, {32, 64}});
     }
-    if (knob) {
+    for (const Stage& sg : stages) {
+        if (st) break;
         float best = 1e30f;
-        int best_v = *knob;
-        for (int v : cand) {
-            *knob = v;
+        int best_v = *sg.knob;
+        for (int v : sg.cand) {
+            *sg.knob = v;
             if ((st = op_run(op, which, x, y, batch, op->dtype, op->dtype))) break;   // warm-up
             cudaEventRecord(e0, ctx->stream);
             for (int r = 0; r < 3 && !st; ++r) st = op_run(op, which, x, y, batch, op->dtype, op->dtype);
@@ -338,7 +345,7 @@ int nys_op_autotune(nys_op* op, int batch, int* choice) {
                 best_v = v;
             }
         }
-        *knob = best_v;
+        *sg.knob = best_v;
     }
     cudaStreamSynchronize(ctx->stream);
     cleanup();

@@ -104,7 +104,8 @@ struct nys_op {
     double span = 0.0;
     void* rtab = nullptr;             // per-angle tables, see radon.cu
     void* lines = nullptr;            // radon: `chunk` images as line-major copies (row-major and transposed)
-    int radon_adj_ak = 8;             // radon adjoint: angles staged per round (chosen by nys_op_autotune)
+    int radon_adj_ak = 16;            // radon adjoint: angles per round, 4, 8 or 16 (nys_op_autotune)
+    int radon_adj_ib = 4;             // radon adjoint: images per CTA for batches of 4 or more, 1 or 4
     int blur_tile = 64;               // blur: output tile side, 32 or 64 (float32; chosen by nys_op_autotune)
     // intermediate buffer for two-pass normals (M per image, `chunk` images)
     void* inter = nullptr;

@@ -21,8 +21,9 @@
 // adjoint is the exact transpose of the forward up to summation order, with
 // no atomics.
 //
-// Forward: one CTA per (angle, group of IB images), each thread three bins,
-// stepping along the lines of the angle.  The image is read "line-major":
+// Forward: one CTA per (angle, group of IB images), each warp 96 consecutive
+// bins (three per lane), stepping along the lines of the angle that the
+// warp's rays cross inside the image.  The image is read "line-major":
 // row-step angles read the row-major image, column-step angles a transposed
 // copy (made once per batch chunk), so consecutive bins of a warp read
 // consecutive addresses for both kinds of angle.  The per-line table entries
@@ -88,7 +89,7 @@ __global__ void radon_prep_kernel(const TI* __restrict__ x, TC* __restrict__ xr,
     }
 }
 
-// forward: one CTA per (angle, IB images); threads over bins, three per thread
+// forward: one CTA per (angle, IB images); warps over bins, three per lane
 template <class TC, class TO, int IB>
 __global__ void __launch_bounds__(256) radon_fwd2_kernel(const TC* __restrict__ xr, const TC* __restrict__ xT,
                                                          TO* __restrict__ y, int n1, int n2, int n_angles,
@@ -110,15 +111,39 @@ __global__ void __launch_bounds__(256) radon_fwd2_kernel(const TC* __restrict__ 
     const size_t N = (size_t)n1 * n2;
     const TC* src = (rs ? xr : xT) + (size_t)b0 * N;
     const TC wt = tab.wt[k];
-    for (int mb = threadIdx.x; mb < n_bins; mb += 3 * blockDim.x) {
+    // a warp takes 96 consecutive bins (three groups of 32, one bin of each
+    // per lane: the loads of a group stay coalesced)
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+    // u(m, l) = Q_m + R_l with R_l = -(l - c_line) t, t = oth / den: the
+    // lines where a sample of the warp's bins can land in [-1, na) form one
+    // interval (Q is monotone in m), taken with two lines of margin; outside
+    // it every sample is out of range and adds exactly zero
+    const TC tl = tab.oth[k] / tab.slope[k];
+    const TC c_line = TC(0.5) * (TC)((rs ? n1 : n2) - 1);
+    for (int mb = warp * 96 + lane; mb - lane < n_bins; mb += nw * 96) {
+        const int mf = mb - lane, ml = min(mf + 95, n_bins - 1);
+        const TC Qa = (TC)tab.qi[(size_t)k * n_bins + mf] + tab.qf[(size_t)k * n_bins + mf];
+        const TC Qb = (TC)tab.qi[(size_t)k * n_bins + ml] + tab.qf[(size_t)k * n_bins + ml];
+        const TC Qmin = fmin(Qa, Qb), Qmax = fmax(Qa, Qb);
+        int l_beg = 0, l_end = nl;
+        if (fabs(tl) > TC(1e-6)) {
+            // -1 <= Q - (l - c_line) t < na
+            const TC e1 = c_line + (Qmin - (TC)na) / tl, e2 = c_line + (Qmax + TC(1)) / tl;
+            l_beg = max(0, (int)floor(fmin(e1, e2)) - 2);
+            l_end = min(nl, (int)ceil(fmax(e1, e2)) + 3);
+        } else if (Qmax < TC(-3) || Qmin > (TC)(na + 2)) {
+            l_end = 0;
+        }
         int qi[3];
         TC qf[3];
         bool ok[3];
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
-            const int m = mb + c * blockDim.x;
+            const int m = mb + c * 32;
             ok[c] = m < n_bins;
-            qi[c] = ok[c] ? tab.qi[(size_t)k * n_bins + m] : 0;
+            // a bin past the last one gets a position far below the line, so
+            // the range tests below reject it without a separate flag
+            qi[c] = ok[c] ? tab.qi[(size_t)k * n_bins + m] : -(1 << 28);
             qf[c] = ok[c] ? tab.qf[(size_t)k * n_bins + m] : TC(0);
         }
         TC acc[3][IB];
@@ -127,7 +152,7 @@ __global__ void __launch_bounds__(256) radon_fwd2_kernel(const TC* __restrict__ 
 #pragma unroll
             for (int q = 0; q < IB; ++q) acc[c][q] = TC(0);
 #pragma unroll 4
-        for (int l = 0; l < nl; ++l) {
+        for (int l = l_beg; l < l_end; ++l) {
             const int ri = s_ri[l];
             const TC rf = s_rf[l];
             const TC* line = src + (size_t)l * na;
@@ -136,7 +161,7 @@ __global__ void __launch_bounds__(256) radon_fwd2_kernel(const TC* __restrict__ 
                 int lo;
                 TC w;
                 sample_pos<TC>(qi[c], qf[c], ri, rf, lo, w);
-                const bool in0 = ok[c] && lo >= 0 && lo < na, in1 = ok[c] && lo + 1 >= 0 && lo + 1 < na;
+                const bool in0 = (unsigned)lo < (unsigned)na, in1 = (unsigned)(lo + 1) < (unsigned)na;
 #pragma unroll
                 for (int q = 0; q < IB; ++q) {
                     const TC* lq = line + (size_t)q * N;
@@ -150,7 +175,7 @@ __global__ void __launch_bounds__(256) radon_fwd2_kernel(const TC* __restrict__ 
         }
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
-            const int m = mb + c * blockDim.x;
+            const int m = mb + c * 32;
             if (!ok[c]) continue;
 #pragma unroll
             for (int q = 0; q < IB; ++q)
@@ -159,34 +184,59 @@ __global__ void __launch_bounds__(256) radon_fwd2_kernel(const TC* __restrict__ 
     }
 }
 
-// adjoint: one CTA per (16 x 16 pixel tile, IB images), angles AK at a time.
-// For a pixel at position p on line l of angle k, the rays that sample it
-// are found from the continuous bin m* = c_b + slope (p - c - R_l) and the
-// three integer candidates around it are tested with the forward's exact test.
+// adjoint, line-scatter form: one CTA per (16 x 16 pixel tile, IB images),
+// AK angles per round.  The 256 threads are (angle a, segment g, line r) with
+// r over the tile's 16 lines (tile rows for a row-step angle, tile columns for
+// a column-step one) and AK x S = 16 (S = 16 / AK segments of the line's
+// bins).  A thread walks its bins in increasing order, evaluates the
+// forward's sample position with the same float expressions (sample_pos) and
+// adds (1 - f) s[m] at position lo and f s[m] at lo + 1 into its own row of a
+// shared buffer: no other thread writes that row, so there are no races and
+// the order of the sums is fixed.  After a barrier each pixel adds, angle by
+// angle, the S segment entries of its position and then the weighted angle
+// term -- the exact transpose of the forward, up to summation order.  The
+// global loads of the next round (staged bins, sinogram values, the line's
+// table entry) are issued into registers before the current round's scatter.
 constexpr int ATS = 16;     // tile side
-constexpr int AWIN = 48;    // staged bins per angle
+// staged bins per angle: the bins reaching a line of the tile start at most
+// 4 + 1 bins above the window start and span 17 |slope| + 15 |oth| + 2 <= 25
+// more (|slope|, |oth| <= 1 and 17^2 + 15^2 < 23^2), so 32 cover them all
+constexpr int AWIN = 32;
+constexpr int AWP = AWIN + 16;   // sinogram row pitch: the two angles of a warp 16 banks apart
+
+template <class TC>
+struct QS {   // one staged bin: integer and fractional part of Q_m
+    int qi;
+    TC qf;
+};
+
 template <class TI, class TO, class TC, int IB, int AK>
-__global__ void __launch_bounds__(256) radon_adj2_kernel(const TI* __restrict__ s, TO* __restrict__ x, int n1, int n2,
-                                                         int n_angles, int n_bins, int batch, RTab<TC> tab, TC c1,
-                                                         TC c2, TC cb) {
+__global__ void __launch_bounds__(256, IB == 1 ? 6 : 2)
+    radon_adj3_kernel(const TI* __restrict__ s, TO* __restrict__ x, int n1, int n2, int n_angles, int n_bins,
+                      int batch, RTab<TC> tab, TC c1, TC c2, TC cb) {
     pdl_enter();
+    constexpr int S = ATS / AK;            // segments per line
+    constexpr int BP = ATS + 1;            // buffer row pitch (odd: spreads the banks)
+    constexpr int U = (AK * AWIN + 255) / 256;   // staged entries per thread
+    static_assert(AK * S == ATS, "AK divides the tile side");
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    // per-angle scalars for every angle, staged once
-    int* g_rs = reinterpret_cast<int*>(smem_raw);
-    TC* g_slope = reinterpret_cast<TC*>(g_rs + ((n_angles + 3) & ~3));
+    // [buf: AK S x IB x 16 x BP][sqs: AK x AWIN][ss: AK x IB x AWP][slope, oth, wt: n_angles]
+    // [rowstep: n_angles][mlo: AK]
+    TC* buf = reinterpret_cast<TC*>(smem_raw);
+    QS<TC>* sqs = reinterpret_cast<QS<TC>*>(buf + AK * S * IB * ATS * BP);
+    TC* ss = reinterpret_cast<TC*>(sqs + AK * AWIN);
+    TC* g_slope = ss + AK * IB * AWP;
     TC* g_oth = g_slope + n_angles;
     TC* g_wt = g_oth + n_angles;
-    __shared__ int sq_i[AK][AWIN];
-    __shared__ TC sq_f[AK][AWIN];
-    __shared__ TC ss[AK][IB][AWIN];
-    __shared__ int sr_i[AK][ATS];
-    __shared__ TC sr_f[AK][ATS];
-    __shared__ int s_mlo[AK];
+    int* g_rs = reinterpret_cast<int*>(g_wt + n_angles);
+    int* s_mlo = g_rs + n_angles;
     const int i0 = blockIdx.y * ATS, j0 = blockIdx.x * ATS;
     const int b0 = blockIdx.z * IB;
     const int ti = threadIdx.x / ATS, tj = threadIdx.x % ATS;
     const int i = i0 + ti, j = j0 + tj;
     const bool valid = i < n1 && j < n2;
+    // scatter role: line r of angle a_me, segment g_me
+    const int r = threadIdx.x % ATS, a_me = (threadIdx.x / ATS) / S, g_me = (threadIdx.x / ATS) % S;
     const size_t M = (size_t)n_angles * n_bins;
     for (int k = threadIdx.x; k < n_angles; k += blockDim.x) {
         g_rs[k] = tab.rowstep[k];
@@ -195,97 +245,130 @@ __global__ void __launch_bounds__(256) radon_adj2_kernel(const TI* __restrict__ 
         g_wt[k] = tab.wt[k];
     }
     __syncthreads();
-    // window start of angle k for this tile: m* = cb + slope (p - cpos) + oth (l - cline)
-    // is affine in (p, l), so its minimum over the tile is at a corner; two
-    // bins of margin cover the float rounding of the split tables
+    // first staged bin of angle k for this tile: m* = cb + slope (p - cpos) + oth (l - cline)
+    // is affine in (p, l), so its minimum over the tile (positions one beyond
+    // each side included) is at a corner; four bins of margin cover the float
+    // rounding of the split tables
     auto window = [&](int k) -> int {
         const int rs = g_rs[k];
         const TC sl = g_slope[k], ot = g_oth[k];
         const TC pa = (TC)(rs ? j0 : i0) - (rs ? c2 : c1);
         const TC la = (TC)(rs ? i0 : j0) - (rs ? c1 : c2);
-        const TC mp = fmin(sl * pa, sl * (pa + TC(ATS - 1)));
+        const TC mp = fmin(sl * (pa - TC(1)), sl * (pa + TC(ATS)));
         const TC ml = fmin(ot * la, ot * (la + TC(ATS - 1)));
-        return (int)floor(cb + mp + ml) - 2;
+        return (int)floor(cb + mp + ml) - 4;
+    };
+    // next round's loads, held in registers through the current round
+    int pf_qi[U];
+    TC pf_qf[U];
+    TC pf_s[U][IB];
+    int pf_ri = 0;
+    TC pf_rf = TC(0);
+    auto prefetch = [&](int k0) {
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int e = threadIdx.x + 256 * u;
+            const int a = e / AWIN, w = e % AWIN;
+            const int k = k0 + a;
+            bool ok = e < AK * AWIN && k < n_angles;
+            const int m = ok ? window(k) + w : 0;
+            ok = ok && m >= 0 && m < n_bins;
+            pf_qi[u] = ok ? tab.qi[(size_t)k * n_bins + m] : 0;
+            pf_qf[u] = ok ? tab.qf[(size_t)k * n_bins + m] : TC(0);
+#pragma unroll
+            for (int q = 0; q < IB; ++q)
+                pf_s[u][q] = (ok && b0 + q < batch) ? (TC)ldf(s + (size_t)(b0 + q) * M + (size_t)k * n_bins + m) : TC(0);
+        }
+        const int k = k0 + a_me;
+        pf_ri = 0;
+        pf_rf = TC(0);
+        if (k < n_angles) {
+            const int rs = g_rs[k];
+            const int l = (rs ? i0 : j0) + r;
+            if (l < (rs ? n1 : n2)) {
+                pf_ri = tab.ri[(size_t)k * tab.nl_max + l];
+                pf_rf = tab.rf[(size_t)k * tab.nl_max + l];
+            }
+        }
     };
     TC acc[IB];
 #pragma unroll
     for (int q = 0; q < IB; ++q) acc[q] = TC(0);
+    prefetch(0);
     for (int k0 = 0; k0 < n_angles; k0 += AK) {
-        __syncthreads();   // the previous round's shared tables are consumed
+        __syncthreads();   // the previous round's buffers and tables are consumed
         if (threadIdx.x < AK) s_mlo[threadIdx.x] = (k0 + threadIdx.x < n_angles) ? window(k0 + threadIdx.x) : 0;
-        __syncthreads();
-        for (int e = threadIdx.x; e < AK * AWIN; e += blockDim.x) {
-            const int a = e / AWIN, w = e % AWIN;
-            const int k = k0 + a;
-            bool ok = k < n_angles;
-            const int m = ok ? s_mlo[a] + w : 0;
-            ok = ok && m >= 0 && m < n_bins;
-            sq_i[a][w] = ok ? tab.qi[(size_t)k * n_bins + m] : 0;
-            sq_f[a][w] = ok ? tab.qf[(size_t)k * n_bins + m] : TC(0);
 #pragma unroll
-            for (int q = 0; q < IB; ++q)
-                ss[a][q][w] = (ok && b0 + q < batch) ? (TC)ldf(s + (size_t)(b0 + q) * M + (size_t)k * n_bins + m) : TC(0);
+        for (int u = 0; u < U; ++u) {
+            const int e = threadIdx.x + 256 * u;
+            if (e < AK * AWIN) {
+                const int a = e / AWIN, w = e % AWIN;
+                sqs[e] = QS<TC>{pf_qi[u], pf_qf[u]};
+#pragma unroll
+                for (int q = 0; q < IB; ++q) ss[(a * IB + q) * AWP + w] = pf_s[u][q];
+            }
         }
-        for (int e = threadIdx.x; e < AK * ATS; e += blockDim.x) {
-            const int a = e / ATS, q = e % ATS;
-            const int k = k0 + a;
-            int ri = 0;
-            TC rf = TC(0);
-            if (k < n_angles) {
-                const int rs = g_rs[k];
-                const int l = (rs ? i0 : j0) + q;
-                if (l < (rs ? n1 : n2)) {
-                    ri = tab.ri[(size_t)k * tab.nl_max + l];
-                    rf = tab.rf[(size_t)k * tab.nl_max + l];
+        const int ri = pf_ri;
+        const TC rf = pf_rf;
+        // zero this thread's buffer rows (only it writes them)
+        TC* row = buf + (size_t)((a_me * S + g_me) * IB) * ATS * BP;
+        const int k_me = k0 + a_me;
+        const int rs = k_me < n_angles ? g_rs[k_me] : 1;
+        // row-step: line r is tile row r, position c is column c -> [r][c];
+        // column-step: line r is tile column r, position c is row c -> [c][r]
+        const int ls = rs ? BP : 1, ps = rs ? 1 : BP;
+#pragma unroll
+        for (int q = 0; q < IB; ++q)
+            for (int c = 0; c < ATS; ++c) row[q * ATS * BP + r * ls + c * ps] = TC(0);
+        __syncthreads();
+        if (k0 + AK < n_angles) prefetch(k0 + AK);
+        const int l = (rs ? i0 : j0) + r;              // line index in the image
+        if (k_me < n_angles && l < (rs ? n1 : n2)) {
+            const int p0 = rs ? j0 : i0;               // first position of the tile on the line
+            const TC cpos = rs ? c2 : c1;
+            const TC sl = g_slope[k_me];
+            // bins whose sample lands in positions p0 - 1 .. p0 + 15 (u in
+            // [p0 - 1, p0 + 16)), from the inverse m*(p) with one bin of
+            // margin; they lie inside the staged window (see AWIN)
+            const TC base = cb - sl * (cpos + ((TC)ri + rf));
+            const TC ma = base + sl * (TC)(p0 - 1), mb = base + sl * (TC)(p0 + ATS);
+            const int wlo = s_mlo[a_me];
+            const int mlo = max(max(0, wlo), (int)floor(fmin(ma, mb)) - 1);
+            const int mhi = min(min(n_bins, wlo + AWIN) - 1, (int)ceil(fmax(ma, mb)) + 1);
+            const int len = mhi - mlo + 1;
+            if (len > 0) {
+                const int w_beg = mlo - wlo + (g_me * len) / S, w_end = mlo - wlo + ((g_me + 1) * len) / S;
+                const QS<TC>* qa = sqs + a_me * AWIN;
+                const TC* sa = ss + a_me * IB * AWP;
+                TC* rl = row + r * ls;
+                for (int w = w_beg; w < w_end; ++w) {
+                    const QS<TC> e = qa[w];
+                    int lo;
+                    TC f;
+                    sample_pos<TC>(e.qi, e.qf, ri, rf, lo, f);
+                    const int c = lo - p0;
+                    if (c < -1 || c >= ATS) continue;
+#pragma unroll
+                    for (int q = 0; q < IB; ++q) {
+                        const TC sv = sa[q * AWP + w];
+                        TC* rq = rl + q * ATS * BP;
+                        if (c >= 0) rq[c * ps] = fma(TC(1) - f, sv, rq[c * ps]);
+                        if (c + 1 < ATS) rq[(c + 1) * ps] = fma(f, sv, rq[(c + 1) * ps]);
+                    }
                 }
             }
-            sr_i[a][q] = ri;
-            sr_f[a][q] = rf;
         }
         __syncthreads();
         if (!valid) continue;
         const int na = min(AK, n_angles - k0);
         for (int a = 0; a < na; ++a) {
-            const int k = k0 + a;
-            const int rs = g_rs[k];
-            const int lq = rs ? ti : tj;       // line of this pixel within the tile
-            const int p = rs ? j : i;          // position along the line
-            const TC cpos = rs ? c2 : c1;
-            const int ri = sr_i[a][lq];
-            const TC rf = sr_f[a][lq];
-            const TC mstar = cb + g_slope[k] * ((TC)p - cpos - ((TC)ri + rf));
-            // a bin m samples this pixel only if |u(m) - p| < 1, i.e. |m - m*| <
-            // |slope| <= 1: the (at most three) integers in (m* - 1, m* + 1),
-            // with a margin for the rounding of m*
-            const int m0 = (int)ceil(mstar - TC(1) - TC(1e-4));
-            const int mlo = s_mlo[a];
-            TC part[IB];
 #pragma unroll
-            for (int q = 0; q < IB; ++q) part[q] = TC(0);
+            for (int q = 0; q < IB; ++q) {
+                TC part = buf[(size_t)((a * S) * IB + q) * ATS * BP + ti * BP + tj];
 #pragma unroll
-            for (int dm = 0; dm < 3; ++dm) {
-                const int m = m0 + dm;
-                if (m < 0 || m >= n_bins) continue;
-                const int w = m - mlo;
-                const bool in = w >= 0 && w < AWIN;
-                int lo;
-                TC wf;
-                if (in) sample_pos<TC>(sq_i[a][w], sq_f[a][w], ri, rf, lo, wf);
-                else sample_pos<TC>(tab.qi[(size_t)k * n_bins + m], tab.qf[(size_t)k * n_bins + m], ri, rf, lo, wf);
-                TC wgt = TC(0);
-                if (lo == p) wgt = TC(1) - wf;
-                else if (lo + 1 == p) wgt = wf;
-                if (wgt == TC(0)) continue;
-#pragma unroll
-                for (int q = 0; q < IB; ++q) {
-                    const TC sv = in ? ss[a][q][w]
-                                     : ((b0 + q < batch) ? (TC)ldf(s + (size_t)(b0 + q) * M + (size_t)k * n_bins + m)
-                                                         : TC(0));
-                    part[q] = fma(wgt, sv, part[q]);
-                }
+                for (int g = 1; g < S; ++g) part += buf[(size_t)((a * S + g) * IB + q) * ATS * BP + ti * BP + tj];
+                acc[q] = fma(g_wt[k0 + a], part, acc[q]);
             }
-#pragma unroll
-            for (int q = 0; q < IB; ++q) acc[q] = fma(g_wt[k], part[q], acc[q]);
         }
     }
     if (!valid) return;
@@ -422,35 +505,42 @@ int radon_fwd(nys_op* op, const void* x, void* y, int batch) {
     return NYS_OK;
 }
 
+template <class TC, int IB, int AK>
+size_t adj3_smem(int n_angles) {
+    constexpr int S = ATS / AK;
+    return sizeof(TC) * ((size_t)AK * S * IB * ATS * (ATS + 1) + (size_t)AK * IB * AWP + 3 * (size_t)n_angles) +
+           sizeof(QS<TC>) * (size_t)AK * AWIN + sizeof(int) * ((size_t)n_angles + AK);
+}
+
 template <class TI, class TO, class TC, int IB, int AK>
 void radon_adj_launch(nys_op* op, const TI* s, TO* x, int nb) {
     dim3 grid((op->n2 + ATS - 1) / ATS, (op->n1 + ATS - 1) / ATS, (nb + IB - 1) / IB);
-    const size_t sm = (((size_t)op->n_angles + 3) & ~size_t(3)) * 4 + 3 * (size_t)op->n_angles * sizeof(TC);
-    // opt in to more than 48 KB of shared memory when the angle tables need it
-    static size_t attr = 0;
+    const size_t sm = adj3_smem<TC, IB, AK>(op->n_angles);
+    // opt in to more than 48 KB of shared memory when the buffers need it
+    static size_t attr = 48 * 1024;
     if (sm > attr) {
-        cudaFuncAttributes fa;
-        if (cudaFuncGetAttributes(&fa, radon_adj2_kernel<TI, TO, TC, IB, AK>) == cudaSuccess &&
-            fa.sharedSizeBytes + sm > 48 * 1024)
-            cudaFuncSetAttribute(radon_adj2_kernel<TI, TO, TC, IB, AK>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)sm);
+        cudaFuncSetAttribute(radon_adj3_kernel<TI, TO, TC, IB, AK>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)sm);
         attr = sm;
     }
     // a launch error is left for the caller's launch check (cudaGetLastError)
-    (void)launch_pdl(radon_adj2_kernel<TI, TO, TC, IB, AK>, grid, 256, sm, op->ctx->stream, s, x, op->n1, op->n2,
+    (void)launch_pdl(radon_adj3_kernel<TI, TO, TC, IB, AK>, grid, 256, sm, op->ctx->stream, s, x, op->n1, op->n2,
                      op->n_angles, op->n_bins, nb, tables<TC>(op), (TC)((op->n1 - 1) / 2.0), (TC)((op->n2 - 1) / 2.0),
                      (TC)((op->n_bins - 1) / 2.0));
 }
 
 template <class TI, class TO, class TC>
 int radon_adj(nys_op* op, const void* s, void* x, int batch) {
-    for (int b0 = 0; b0 < batch; b0 += 65535 * 4) {
-        const int nb = std::min(65535 * 4, batch - b0);
+    // images per CTA: 4 for batches of 4 or more unless nys_op_autotune chose 1;
+    // grid.z (images / ib) stays within 65535
+    const int ib = (batch >= 4 && op->radon_adj_ib == 4) ? 4 : 1;
+    for (int b0 = 0; b0 < batch; b0 += 65535 * ib) {
+        const int nb = std::min(65535 * ib, batch - b0);
         const TI* sb = (const TI*)s + (size_t)b0 * op->M;
         TO* xb = (TO*)x + (size_t)b0 * op->N;
-        // 4, 8 or 16 angles per round (nys_op_autotune); float64 stays at <= 8
-        const int ak = (sizeof(TC) == 8 && op->radon_adj_ak > 8) ? 8 : op->radon_adj_ak;
-        if (nb >= 4) {
+        // 4, 8 or 16 angles per round (nys_op_autotune)
+        const int ak = op->radon_adj_ak;
+        if (ib == 4 && nb >= 4) {
             if (ak == 4) radon_adj_launch<TI, TO, TC, 4, 4>(op, sb, xb, nb);
             else if (ak == 16) radon_adj_launch<TI, TO, TC, 4, 16>(op, sb, xb, nb);
             else radon_adj_launch<TI, TO, TC, 4, 8>(op, sb, xb, nb);
