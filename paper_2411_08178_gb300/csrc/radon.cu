@@ -341,20 +341,72 @@ __global__ void __launch_bounds__(256, IB == 1 ? 6 : 2)
                 const QS<TC>* qa = sqs + a_me * AWIN;
                 const TC* sa = ss + a_me * IB * AWP;
                 TC* rl = row + r * ls;
-                for (int w = w_beg; w < w_end; ++w) {
-                    const QS<TC> e = qa[w];
-                    int lo;
-                    TC f;
-                    sample_pos<TC>(e.qi, e.qf, ri, rf, lo, f);
-                    const int c = lo - p0;
-                    if (c < -1 || c >= ATS) continue;
-#pragma unroll
-                    for (int q = 0; q < IB; ++q) {
-                        const TC sv = sa[q * AWP + w];
-                        TC* rq = rl + q * ATS * BP;
-                        if (c >= 0) rq[c * ps] = fma(TC(1) - f, sv, rq[c * ps]);
-                        if (c + 1 < ATS) rq[(c + 1) * ps] = fma(f, sv, rq[(c + 1) * ps]);
+                if constexpr (IB == 1) {
+                    // one image: read-modify-write of the buffer row
+                    for (int w = w_beg; w < w_end; ++w) {
+                        const QS<TC> e = qa[w];
+                        int lo;
+                        TC f;
+                        sample_pos<TC>(e.qi, e.qf, ri, rf, lo, f);
+                        const int c = lo - p0;
+                        if (c < -1 || c >= ATS) continue;
+                        const TC sv = sa[w];
+                        if (c >= 0) rl[c * ps] = fma(TC(1) - f, sv, rl[c * ps]);
+                        if (c + 1 < ATS) rl[(c + 1) * ps] = fma(f, sv, rl[(c + 1) * ps]);
                     }
+                } else {
+                    // Several images: two positions are summed in registers and
+                    // each is written out once (fewer shared-memory accesses per
+                    // bin; measured faster for 4 images per CTA, slower for one).
+                    // lo is monotone in m, so a position's (at most two, three on
+                    // a rounding tie) contributions come from consecutive bins,
+                    // and a slot is complete as soon as a bin no longer touches
+                    // it.  The sums run in bin order, as the read-modify-write.
+                    int cA = -1000, cB = -1000;
+                    TC vA[IB], vB[IB];
+#pragma unroll
+                    for (int q = 0; q < IB; ++q) vA[q] = vB[q] = TC(0);
+                    auto flush = [&](int c, const TC* v) {
+                        if (c >= 0 && c < ATS) {
+#pragma unroll
+                            for (int q = 0; q < IB; ++q) rl[q * ATS * BP + c * ps] = v[q];
+                        }
+                    };
+                    for (int w = w_beg; w < w_end; ++w) {
+                        const QS<TC> e = qa[w];
+                        int lo;
+                        TC f;
+                        sample_pos<TC>(e.qi, e.qf, ri, rf, lo, f);
+                        const int c = lo - p0;
+                        if (c < -1 || c >= ATS) continue;
+                        TC sv[IB];
+#pragma unroll
+                        for (int q = 0; q < IB; ++q) sv[q] = sa[q * AWP + w];
+#pragma unroll
+                        for (int t = 0; t < 2; ++t) {          // position c (weight 1 - f), then c + 1 (f)
+                            const int ct = c + t;
+                            const TC wgt = t ? f : TC(1) - f;
+                            if (ct == cA) {
+#pragma unroll
+                                for (int q = 0; q < IB; ++q) vA[q] = fma(wgt, sv[q], vA[q]);
+                            } else if (ct == cB) {
+#pragma unroll
+                                for (int q = 0; q < IB; ++q) vB[q] = fma(wgt, sv[q], vB[q]);
+                            } else if (cA != c && cA != c + 1) {   // slot A is complete
+                                flush(cA, vA);
+                                cA = ct;
+#pragma unroll
+                                for (int q = 0; q < IB; ++q) vA[q] = fma(wgt, sv[q], TC(0));
+                            } else {                               // slot B is
+                                flush(cB, vB);
+                                cB = ct;
+#pragma unroll
+                                for (int q = 0; q < IB; ++q) vB[q] = fma(wgt, sv[q], TC(0));
+                            }
+                        }
+                    }
+                    flush(cA, vA);
+                    flush(cB, vB);
                 }
             }
         }
