@@ -20,10 +20,21 @@ TEST INFRASTRUCTURE ONLY -- see oracle/__init__.py.
       Q_k = Proj_B(R_k + L x / (lb ||L||^2))
       t_{k+1} = (1 + sqrt(1 + 4 t_k^2)) / 2
       R_{k+1} = Q_k + ((t_k - 1)/t_{k+1}) (Q_k - Q_{k-1})
-  and returns x(Q_n) and Q_n.  Projections:
-    - anisotropic TV (phi = 1): clip every component to [-1, 1];
-    - Hessian Schatten-1 (phi = 1 on 2x2 Hessians): project each symmetric
-      2x2 block onto the spectral-norm unit ball (clip its eigenvalues).
+  and returns x(Q_n) and Q_n.  The dual ball is the unit ball of the mixed
+  norm l_{inf,psi}, 1/phi + 1/psi = 1 (Eqs. dualMixedNormRep and
+  mixedUnitNormBall); its projection acts on each group (pixel) alone:
+    - anisotropic TV (phi = 1, psi = inf): clip every component to [-1, 1];
+    - isotropic TV (phi = 2, psi = 2): scale each pixel's pair to Euclidean
+      norm <= 1;
+    - Hessian Schatten-1 (HS_1: phi = 1 on the singular values of the 2x2
+      Hessian, dual ball = spectral norm <= 1): clip the eigenvalues;
+    - Hessian Schatten-2 (HS_2, Frobenius, self-dual): scale each symmetric
+      block to Frobenius norm <= 1 (the cross term counted twice, as in the
+      inner product q11 v11 + 2 q12 v12 + q22 v22);
+    - Hessian Schatten-inf (HS_inf, spectral norm; dual ball = Schatten-1
+      norm <= 1): project the eigenvalue pair onto the l1 unit ball.
+  (Appendix A gives the groups; the Hessian variants are the HS_1, HS_2 and
+  HS_inf of the supplementary CT experiments.)
 """
 from __future__ import annotations
 
@@ -94,11 +105,54 @@ def proj_spectral_2x2(q):
     return np.stack([mp + dp * cos2, dp * sin2, mp - dp * cos2], axis=-3)
 
 
+def proj_l2_pairs(q):
+    """q: (..., 2, n1, n2); each pixel's (q1, q2) scaled to Euclidean norm <= 1."""
+    nrm = np.sqrt(q[..., 0, :, :] ** 2 + q[..., 1, :, :] ** 2)
+    return q / np.maximum(1.0, nrm)[..., None, :, :]
+
+
+def proj_frobenius_2x2(q):
+    """q: (..., 3, n1, n2) holding (a, b, c) of [[a, b], [b, c]]; each block
+    scaled to Frobenius norm sqrt(a^2 + 2 b^2 + c^2) <= 1."""
+    a, b, c = q[..., 0, :, :], q[..., 1, :, :], q[..., 2, :, :]
+    nrm = np.sqrt(a * a + 2.0 * b * b + c * c)
+    return q / np.maximum(1.0, nrm)[..., None, :, :]
+
+
+def proj_l1_ball_2(l1, l2):
+    """Euclidean projection of the pairs (l1, l2) onto |l1| + |l2| <= 1:
+    soft-thresholding by the theta that brings the sum of magnitudes to 1."""
+    a1, a2 = np.abs(l1), np.abs(l2)
+    big, small = np.maximum(a1, a2), np.minimum(a1, a2)
+    theta = np.where(big - small >= 1.0, big - 1.0, 0.5 * (big + small - 1.0))
+    theta = np.where(a1 + a2 <= 1.0, 0.0, theta)
+    return np.sign(l1) * np.maximum(a1 - theta, 0.0), np.sign(l2) * np.maximum(a2 - theta, 0.0)
+
+
+def proj_nuclear_2x2(q):
+    """q: (..., 3, n1, n2) as in proj_spectral_2x2; each block projected onto
+    the Schatten-1 (nuclear) unit ball: its eigenvalue pair onto the l1 ball."""
+    a, b, c = q[..., 0, :, :], q[..., 1, :, :], q[..., 2, :, :]
+    m = 0.5 * (a + c)
+    h = 0.5 * (a - c)
+    r = np.sqrt(h * h + b * b)
+    l1, l2 = proj_l1_ball_2(m + r, m - r)
+    mp = 0.5 * (l1 + l2)
+    dp = 0.5 * (l1 - l2)
+    safe = np.where(r > 0.0, r, 1.0)
+    cos2, sin2 = np.where(r > 0.0, h / safe, 1.0), np.where(r > 0.0, b / safe, 0.0)
+    return np.stack([mp + dp * cos2, dp * sin2, mp - dp * cos2], axis=-3)
+
+
 REGULARISERS = {
     # name: (L, L^T, ||L||^2, projection onto the dual unit ball)
     "tv": (ops.grad, ops.grad_adjoint, 8.0, proj_box),
+    "isotv": (ops.grad, ops.grad_adjoint, 8.0, proj_l2_pairs),
     "hs": (ops.hess, ops.hess_adjoint, 32.0, proj_spectral_2x2),
+    "hs2": (ops.hess, ops.hess_adjoint, 32.0, proj_frobenius_2x2),
+    "hsinf": (ops.hess, ops.hess_adjoint, 32.0, proj_nuclear_2x2),
 }
+DUAL_COMPONENTS = {"tv": 2, "isotv": 2, "hs": 3, "hs2": 3, "hsinf": 3}
 
 
 def prox_dual(s: np.ndarray, reg: str, lam_bar: float, precond, n_inner: int,
@@ -110,7 +164,7 @@ def prox_dual(s: np.ndarray, reg: str, lam_bar: float, precond, n_inner: int,
     """
     L, Lt, normL2, proj = REGULARISERS[reg]
     s = np.asarray(s, dtype=np.float64)
-    G = 2 if reg == "tv" else 3
+    G = DUAL_COMPONENTS[reg]
     Q_prev = np.zeros((G,) + s.shape) if Q0 is None else np.array(Q0, dtype=np.float64)
     R = Q_prev.copy()
     t = 1.0
@@ -126,14 +180,22 @@ def prox_dual(s: np.ndarray, reg: str, lam_bar: float, precond, n_inner: int,
 
 
 def reg_value(x: np.ndarray, reg: str) -> float:
-    """g(x) = ||L x||_{1,phi}: anisotropic TV, Hessian Schatten-1 or l1 (wavelet coeffs)."""
+    """g(x) = ||L x||_{1,phi}: anisotropic or isotropic TV, Hessian Schatten-1, -2
+    or -inf, or l1 (wavelet coefficients)."""
     if reg == "tv":
         return float(np.abs(ops.grad(x)).sum())
-    if reg == "hs":
+    if reg == "isotv":
+        g = ops.grad(x)
+        return float(np.sqrt(g[0] ** 2 + g[1] ** 2).sum())
+    if reg in ("hs", "hs2", "hsinf"):
         v = ops.hess(x)
         a, b, c = v[0], v[1], v[2]
+        if reg == "hs2":
+            return float(np.sqrt(a * a + 2.0 * b * b + c * c).sum())
         m = 0.5 * (a + c)
         r = np.sqrt((0.5 * (a - c)) ** 2 + b * b)
+        if reg == "hsinf":
+            return float((np.abs(m) + r).sum())
         return float((np.abs(m + r) + np.abs(m - r)).sum())
     if reg == "wavelet":
         return float(np.abs(x).sum())
