@@ -51,7 +51,10 @@ enum {
 enum { NYS_F32 = 0, NYS_F64 = 1, NYS_BF16 = 2 };
 enum { NYS_OP_BLUR = 0, NYS_OP_BLUR_DECIM = 1, NYS_OP_RADON = 2 };
 enum { NYS_PHI_ATA = 0, NYS_PHI_W_ATA_WT = 1 };
-enum { NYS_REG_WAVELET = 0, NYS_REG_TV = 1, NYS_REG_HS = 2 };
+/* regularisers ||L x||_{1,phi} (Eq. lpl1qMixedNorm, Appendix A): Haar l1;
+ * first differences with phi = 1 (anisotropic TV) or phi = 2 (isotropic TV);
+ * the 2x2 Hessian with the Schatten-1, -2 or -inf norm (HS_1, HS_2, HS_inf) */
+enum { NYS_REG_WAVELET = 0, NYS_REG_TV = 1, NYS_REG_HS = 2, NYS_REG_ISOTV = 3, NYS_REG_HS2 = 4, NYS_REG_HSINF = 5 };
 enum { NYS_FIT_L2 = 0, NYS_FIT_HUBER = 1 };
 
 typedef struct nys_ctx nys_ctx;
@@ -251,6 +254,15 @@ int prox_tv(nys_ctx* ctx, const nys_precond* pc, double lambda_bar, int n_inner,
             int dtype, int n1, int n2, const void* s, void* out, void* Q_io);
 int prox_hs(nys_ctx* ctx, const nys_precond* pc, double lambda_bar, int n_inner,
             int dtype, int n1, int n2, const void* s, void* out, void* Q_io);
+/* The same dual APG for any mixed-norm regulariser of Eq. lpl1qMixedNorm:
+ * reg = NYS_REG_TV, NYS_REG_ISOTV (Q: 2*N) or NYS_REG_HS, NYS_REG_HS2,
+ * NYS_REG_HSINF (Q: 3*N).  The dual ball is that of l_{inf,psi},
+ * 1/phi + 1/psi = 1 (Eq. mixedUnitNormBall), projected per pixel: clip
+ * (TV), Euclidean scaling (isotropic TV), eigenvalue clip (HS_1), Frobenius
+ * scaling with the cross term counted twice (HS_2), eigenvalues onto the l1
+ * ball (HS_inf).  NYS_EINVAL for NYS_REG_WAVELET or an unknown reg. */
+int prox_mixed(nys_ctx* ctx, const nys_precond* pc, int reg, double lambda_bar, int n_inner,
+               int dtype, int n1, int n2, const void* s, void* out, void* Q_io);
 
 /* ---------------------------------------------------------- Algorithm 3 -- */
 typedef struct nys_solver_desc {

@@ -16,7 +16,7 @@ NYS_EDEGENERATE, NYS_ENONFINITE, NYS_ETIMEOUT, NYS_ENOCONV = 5, 6, 7, 8
 NYS_F32, NYS_F64, NYS_BF16 = 0, 1, 2
 NYS_OP_BLUR, NYS_OP_BLUR_DECIM, NYS_OP_RADON = 0, 1, 2
 NYS_PHI_ATA, NYS_PHI_W_ATA_WT = 0, 1
-NYS_REG_WAVELET, NYS_REG_TV, NYS_REG_HS = 0, 1, 2
+NYS_REG_WAVELET, NYS_REG_TV, NYS_REG_HS, NYS_REG_ISOTV, NYS_REG_HS2, NYS_REG_HSINF = 0, 1, 2, 3, 4, 5
 NYS_FIT_L2, NYS_FIT_HUBER = 0, 1
 
 CODE_NAMES = {0: "NYS_OK", 1: "NYS_EINVAL", 2: "NYS_ENOMEM", 3: "NYS_ECUDA", 4: "NYS_ENOTSPD",
@@ -87,6 +87,7 @@ PROTOTYPES = {
     "prox_wavelet": (i32, [vp, C.POINTER(nys_precond), f64, i32, i64, vp, vp, vp, C.POINTER(nys_prox_info)]),
     "prox_tv": (i32, [vp, C.POINTER(nys_precond), f64, i32, i32, i32, i32, vp, vp, vp]),
     "prox_hs": (i32, [vp, C.POINTER(nys_precond), f64, i32, i32, i32, i32, vp, vp, vp]),
+    "prox_mixed": (i32, [vp, C.POINTER(nys_precond), i32, f64, i32, i32, i32, i32, vp, vp, vp]),
     "nys_solver_create": (i32, [vp, vp, C.POINTER(nys_solver_desc), vp, C.POINTER(nys_precond), C.POINTER(vp)]),
     "nys_solver_destroy": (i32, [vp]),
     "pgd_step": (i32, [vp, i32]),

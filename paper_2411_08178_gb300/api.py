@@ -318,6 +318,17 @@ def prox_hs(ctx, pc, lam_bar, n_inner, s, Q=None, out=None):
     return _prox_dual(_lib().prox_hs, 3, ctx, pc, lam_bar, n_inner, s, Q, out)
 
 
+REGS = {"wavelet": A.NYS_REG_WAVELET, "tv": A.NYS_REG_TV, "hs": A.NYS_REG_HS, "isotv": A.NYS_REG_ISOTV,
+        "hs2": A.NYS_REG_HS2, "hsinf": A.NYS_REG_HSINF}
+
+
+def prox_mixed(ctx, pc, reg: str, lam_bar, n_inner, s, Q=None, out=None):
+    """Dual APG prox for any mixed-norm regulariser ("tv", "isotv", "hs", "hs2", "hsinf")."""
+    code = REGS[reg]
+    fn = lambda *a: _lib().prox_mixed(a[0], a[1], code, *a[2:])
+    return _prox_dual(fn, 2 if reg in ("tv", "isotv") else 3, ctx, pc, lam_bar, n_inner, s, Q, out)
+
+
 class Solver:
     """nys_solver: Algorithm 3 (WAPG; plain APG when pc is None)."""
 
@@ -325,7 +336,7 @@ class Solver:
                  fit: str = "l2", huber_delta: float = 0.0, alpha: float = 0.0, n_inner: int = 20,
                  power_iters: int = 50, power_seed: int = 7, use_graph: bool = True):
         d = A.nys_solver_desc()
-        d.reg = {"wavelet": A.NYS_REG_WAVELET, "tv": A.NYS_REG_TV, "hs": A.NYS_REG_HS}[reg]
+        d.reg = REGS[reg]
         d.fit = {"l2": A.NYS_FIT_L2, "huber": A.NYS_FIT_HUBER}[fit]
         d.lambda_ = lam
         d.huber_delta = huber_delta

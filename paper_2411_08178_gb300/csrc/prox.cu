@@ -79,8 +79,8 @@ template <class T, int REG>
 int prox_dual_typed(nys_ctx* ctx, const nys_precond* pc, double lb, int n_inner, int n1, int n2, const T* s, T* out,
                     T* Q) {
     using TC = typename Comp<T>::type;
-    const int G = REG == NYS_REG_TV ? 2 : 3;
-    const double normL2 = REG == NYS_REG_TV ? 8.0 : 32.0;
+    const int G = dual_components(REG);
+    const double normL2 = first_order(REG) ? 8.0 : 32.0;
     const int64_t N = (int64_t)n1 * n2;
     int st;
     // no column with d_i > 0: P = I exactly
@@ -458,17 +458,21 @@ template int soft_run<double>(nys_ctx*, double, int64_t, const double*, double*)
 
 int prox_dual_run(nys_ctx* ctx, const nys_precond* pc, int reg, double lb, int n_inner, int dtype, int n1, int n2,
                   const void* s, void* out, void* Q) {
-    if (dtype == NYS_F64) {
-        if (reg == NYS_REG_TV)
-            return prox_dual_typed<double, NYS_REG_TV>(ctx, pc, lb, n_inner, n1, n2, (const double*)s, (double*)out,
-                                                       (double*)Q);
-        return prox_dual_typed<double, NYS_REG_HS>(ctx, pc, lb, n_inner, n1, n2, (const double*)s, (double*)out,
-                                                   (double*)Q);
-    }
-    if (reg == NYS_REG_TV)
-        return prox_dual_typed<float, NYS_REG_TV>(ctx, pc, lb, n_inner, n1, n2, (const float*)s, (float*)out,
-                                                  (float*)Q);
-    return prox_dual_typed<float, NYS_REG_HS>(ctx, pc, lb, n_inner, n1, n2, (const float*)s, (float*)out, (float*)Q);
+    auto go = [&](auto* tag) -> int {
+        using T = std::remove_pointer_t<decltype(tag)>;
+        const T* sp = (const T*)s;
+        T* op = (T*)out;
+        T* qp = (T*)Q;
+        switch (reg) {
+            case NYS_REG_TV: return prox_dual_typed<T, NYS_REG_TV>(ctx, pc, lb, n_inner, n1, n2, sp, op, qp);
+            case NYS_REG_ISOTV: return prox_dual_typed<T, NYS_REG_ISOTV>(ctx, pc, lb, n_inner, n1, n2, sp, op, qp);
+            case NYS_REG_HS: return prox_dual_typed<T, NYS_REG_HS>(ctx, pc, lb, n_inner, n1, n2, sp, op, qp);
+            case NYS_REG_HS2: return prox_dual_typed<T, NYS_REG_HS2>(ctx, pc, lb, n_inner, n1, n2, sp, op, qp);
+            case NYS_REG_HSINF: return prox_dual_typed<T, NYS_REG_HSINF>(ctx, pc, lb, n_inner, n1, n2, sp, op, qp);
+        }
+        return fail(ctx, NYS_EINVAL, "prox: regulariser %d has no dual prox", reg);
+    };
+    return dtype == NYS_F64 ? go((double*)nullptr) : go((float*)nullptr);
 }
 
 }  // namespace nys
@@ -501,6 +505,16 @@ int prox_hs(nys_ctx* ctx, const nys_precond* pc, double lb, int n_inner, int dty
     if (int st = check_prox(ctx, pc, dtype, (int64_t)n1 * n2, s, out)) return st;
     if (!Q || n1 <= 0 || n2 <= 0 || n_inner < 0 || !(lb > 0.0)) return fail(ctx, NYS_EINVAL, "prox_hs: bad argument");
     return prox_dual_run(ctx, pc, NYS_REG_HS, lb, n_inner, dtype, n1, n2, s, out, Q);
+}
+
+int prox_mixed(nys_ctx* ctx, const nys_precond* pc, int reg, double lb, int n_inner, int dtype, int n1, int n2,
+               const void* s, void* out, void* Q) {
+    if (int st = check_prox(ctx, pc, dtype, (int64_t)n1 * n2, s, out)) return st;
+    if (!Q || n1 <= 0 || n2 <= 0 || n_inner < 0 || !(lb > 0.0))
+        return fail(ctx, NYS_EINVAL, "prox_mixed: bad argument");
+    if (reg != NYS_REG_TV && reg != NYS_REG_ISOTV && reg != NYS_REG_HS && reg != NYS_REG_HS2 && reg != NYS_REG_HSINF)
+        return fail(ctx, NYS_EINVAL, "prox_mixed: regulariser %d has no dual prox", reg);
+    return prox_dual_run(ctx, pc, reg, lb, n_inner, dtype, n1, n2, s, out, Q);
 }
 
 int prox_wavelet(nys_ctx* ctx, const nys_precond* pc, double tau, int dtype, int64_t N, const void* s, void* out,

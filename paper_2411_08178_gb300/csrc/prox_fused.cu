@@ -122,8 +122,8 @@ int fused_typed(nys_ctx* ctx, const nys_precond* pc, double lb, int n_inner, int
     constexpr int V = Vec16<TU>::n;
     constexpr bool TV = REG == NYS_REG_TV;
     const nys_precond_priv* pv = (const nys_precond_priv*)pc->priv;
-    const int G = TV ? 2 : 3;
-    const double normL2 = TV ? 8.0 : 32.0;
+    const int G = dual_components(REG);
+    const double normL2 = first_order(REG) ? 8.0 : 32.0;
     const int64_t N = (int64_t)n1 * n2;
     const int le = pv->ell_eff;
     // small active sets: the last CTA of lt_utz forms M w; large ones: two
@@ -242,9 +242,17 @@ int prox_dual_fused(nys_ctx* ctx, const nys_precond* pc, int reg, double lb, int
         using TU = std::remove_pointer_t<decltype(tu)>;
         using T = std::remove_pointer_t<decltype(tt)>;
         using TA = std::remove_pointer_t<decltype(ta)>;
-        if (reg == NYS_REG_TV)
-            return fused_typed<TU, T, TA, NYS_REG_TV>(ctx, pc, lb, n_inner, n1, n2, (const T*)s, (T*)out, (T*)Q);
-        return fused_typed<TU, T, TA, NYS_REG_HS>(ctx, pc, lb, n_inner, n1, n2, (const T*)s, (T*)out, (T*)Q);
+        const T* sp = (const T*)s;
+        T* op = (T*)out;
+        T* qp = (T*)Q;
+        switch (reg) {
+            case NYS_REG_TV: return fused_typed<TU, T, TA, NYS_REG_TV>(ctx, pc, lb, n_inner, n1, n2, sp, op, qp);
+            case NYS_REG_ISOTV: return fused_typed<TU, T, TA, NYS_REG_ISOTV>(ctx, pc, lb, n_inner, n1, n2, sp, op, qp);
+            case NYS_REG_HS: return fused_typed<TU, T, TA, NYS_REG_HS>(ctx, pc, lb, n_inner, n1, n2, sp, op, qp);
+            case NYS_REG_HS2: return fused_typed<TU, T, TA, NYS_REG_HS2>(ctx, pc, lb, n_inner, n1, n2, sp, op, qp);
+            case NYS_REG_HSINF: return fused_typed<TU, T, TA, NYS_REG_HSINF>(ctx, pc, lb, n_inner, n1, n2, sp, op, qp);
+        }
+        return NYS_EINVAL;
     };
     if (dtype == NYS_F64) {
         if (pc->dtype != NYS_F64) return NYS_EINVAL;

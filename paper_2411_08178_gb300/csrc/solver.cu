@@ -176,15 +176,19 @@ __global__ void objective_kernel(const T* __restrict__ r, const T* __restrict__ 
     for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < N; t += (int64_t)gridDim.x * blockDim.x) {
         const int i = (int)(t / n2), j = (int)(t - (int64_t)i * n2);
         auto X = [&](int a, int b) { return (double)x[(size_t)pmod(a, n1) * n2 + pmod(b, n2)]; };
-        if (REG == NYS_REG_TV) {
-            g += fabs(X(i, j) - X(i - 1, j)) + fabs(X(i, j) - X(i, j - 1));
-        } else if (REG == NYS_REG_HS) {
+        if (REG == NYS_REG_TV || REG == NYS_REG_ISOTV) {
+            const double g1 = X(i, j) - X(i - 1, j), g2 = X(i, j) - X(i, j - 1);
+            g += REG == NYS_REG_TV ? fabs(g1) + fabs(g2) : sqrt(g1 * g1 + g2 * g2);
+        } else if (REG == NYS_REG_HS || REG == NYS_REG_HS2 || REG == NYS_REG_HSINF) {
             const double v11 = X(i - 1, j) - 2.0 * X(i, j) + X(i + 1, j);
             const double v22 = X(i, j - 1) - 2.0 * X(i, j) + X(i, j + 1);
             const double v12 = 0.25 * (X(i + 1, j + 1) - X(i + 1, j - 1) - X(i - 1, j + 1) + X(i - 1, j - 1));
             const double m = 0.5 * (v11 + v22), h = 0.5 * (v11 - v22);
             const double rr = sqrt(h * h + v12 * v12);
-            g += fabs(m + rr) + fabs(m - rr);
+            // Schatten-1, -2 (Frobenius, cross term twice) or -inf of [[v11, v12], [v12, v22]]
+            g += REG == NYS_REG_HS ? fabs(m + rr) + fabs(m - rr)
+                 : REG == NYS_REG_HS2 ? sqrt(v11 * v11 + 2.0 * v12 * v12 + v22 * v22)
+                                      : fabs(m) + rr;
         } else {
             g += fabs((double)x[t]);
         }
@@ -476,7 +480,8 @@ extern "C" {
 int nys_solver_create(nys_ctx* ctx, nys_op* op, const nys_solver_desc* d, const void* y, const nys_precond* pc,
                       nys_solver** out) {
     if (!ctx || !op || !d || !y || !out) return fail(ctx, NYS_EINVAL, "nys_solver_create: null argument");
-    if (d->reg != NYS_REG_WAVELET && d->reg != NYS_REG_TV && d->reg != NYS_REG_HS)
+    if (d->reg != NYS_REG_WAVELET && d->reg != NYS_REG_TV && d->reg != NYS_REG_HS && d->reg != NYS_REG_ISOTV &&
+        d->reg != NYS_REG_HS2 && d->reg != NYS_REG_HSINF)
         return fail(ctx, NYS_EINVAL, "nys_solver_create: unknown regulariser");
     if (d->reg == NYS_REG_WAVELET && op->haar_levels <= 0)
         return fail(ctx, NYS_EINVAL, "nys_solver_create: the wavelet model needs haar_levels > 0");
@@ -496,7 +501,7 @@ int nys_solver_create(nys_ctx* ctx, nys_op* op, const nys_solver_desc* d, const 
     S->dt = op->dtype;
     S->N = op->N;
     S->M = op->M;
-    S->G = d->reg == NYS_REG_TV ? 2 : (d->reg == NYS_REG_HS ? 3 : 0);
+    S->G = d->reg == NYS_REG_WAVELET ? 0 : (d->reg == NYS_REG_TV || d->reg == NYS_REG_ISOTV ? 2 : 3);
     const int st = S->dt == NYS_F64 ? create_typed<double>(S, y) : create_typed<float>(S, y);
     if (st) {
         nys_solver_destroy(S);
@@ -583,15 +588,15 @@ int nys_solver_objective(nys_solver* S, double* F) {
         const T* r = (const T*)S->tM;
         const T* yy = (const T*)S->y;
         const T* xx = (const T*)x;
-        if (S->d.reg == NYS_REG_TV)
-            objective_kernel<T, NYS_REG_TV><<<nb, 256, 0, s>>>(r, yy, S->M, S->d.fit, S->d.huber_delta, xx,
-                                                               S->op->n1, S->op->n2, part);
-        else if (S->d.reg == NYS_REG_HS)
-            objective_kernel<T, NYS_REG_HS><<<nb, 256, 0, s>>>(r, yy, S->M, S->d.fit, S->d.huber_delta, xx,
-                                                               S->op->n1, S->op->n2, part);
-        else
-            objective_kernel<T, NYS_REG_WAVELET><<<nb, 256, 0, s>>>(r, yy, S->M, S->d.fit, S->d.huber_delta, xx,
-                                                                    S->op->n1, S->op->n2, part);
+        auto k = objective_kernel<T, NYS_REG_WAVELET>;
+        switch (S->d.reg) {
+            case NYS_REG_TV: k = objective_kernel<T, NYS_REG_TV>; break;
+            case NYS_REG_ISOTV: k = objective_kernel<T, NYS_REG_ISOTV>; break;
+            case NYS_REG_HS: k = objective_kernel<T, NYS_REG_HS>; break;
+            case NYS_REG_HS2: k = objective_kernel<T, NYS_REG_HS2>; break;
+            case NYS_REG_HSINF: k = objective_kernel<T, NYS_REG_HSINF>; break;
+        }
+        k<<<nb, 256, 0, s>>>(r, yy, S->M, S->d.fit, S->d.huber_delta, xx, S->op->n1, S->op->n2, part);
         NYS_LAUNCH_CK(ctx);
         return NYS_OK;
     };

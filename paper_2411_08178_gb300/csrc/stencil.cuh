@@ -21,6 +21,11 @@ __device__ __forceinline__ void pix_ij(int64_t t, int n2, int& i, int& j) {
     j = (int)(u - (unsigned)i * (unsigned)n2);
 }
 
+// first differences (anisotropic and isotropic TV) or the 2x2 Hessian
+__host__ __device__ constexpr bool first_order(int reg) { return reg == NYS_REG_TV || reg == NYS_REG_ISOTV; }
+// dual components per pixel
+__host__ __device__ constexpr int dual_components(int reg) { return first_order(reg) ? 2 : 3; }
+
 // L^T Q at pixel (i, j)
 template <class T, int REG>
 __device__ __forceinline__ typename Comp<T>::type lt_q(const T* __restrict__ Q, int i, int j, int n1, int n2) {
@@ -29,7 +34,7 @@ __device__ __forceinline__ typename Comp<T>::type lt_q(const T* __restrict__ Q, 
     const size_t r0 = (size_t)i * n2;
     const int jp = wrap_inc(j, n2);
     const size_t rp = (size_t)wrap_inc(i, n1) * n2;
-    if (REG == NYS_REG_TV) {
+    if (first_order(REG)) {
         const T* q1 = Q;
         const T* q2 = Q + N;
         return (TC)q1[r0 + j] - (TC)q1[rp + j] + (TC)q2[r0 + j] - (TC)q2[r0 + jp];
@@ -48,8 +53,12 @@ __device__ __forceinline__ typename Comp<T>::type lt_q(const T* __restrict__ Q, 
 
 // One APG step of the dual at pixel t (components at t, t + N, t + 2N) given
 // L x there (2 components for TV, (v11, v12, v22) for the Hessian):
-// Q' = Proj(R + step L x), R <- Q' + beta (Q' - Qp), Qp <- Q'.  Proj clips to
-// [-1, 1] (TV) or clips the eigenvalues of the symmetric 2 x 2 block (HS).
+// Q' = Proj(R + step L x), R <- Q' + beta (Q' - Qp), Qp <- Q'.  Proj is the
+// projection onto the pixel's dual ball (Eq. mixedUnitNormBall): clip to
+// [-1, 1] (anisotropic TV), scale to Euclidean norm <= 1 (isotropic TV), clip
+// the eigenvalues of the symmetric 2 x 2 block (HS_1), scale it to Frobenius
+// norm <= 1 (HS_2), or move its eigenvalue pair onto the l1 unit ball
+// (HS_inf).
 template <class T, int REG>
 __device__ __forceinline__ void dual_pixel(const typename Comp<T>::type* Lx, T* __restrict__ R, T* __restrict__ Qp,
                                            int64_t t, int64_t N, typename Comp<T>::type step,
@@ -64,25 +73,58 @@ __device__ __forceinline__ void dual_pixel(const typename Comp<T>::type* Lx, T* 
             R[e] = (T)(q + beta * (q - o));
             Qp[e] = (T)q;
         }
+    } else if (REG == NYS_REG_ISOTV) {
+        TC q[2];
+#pragma unroll
+        for (int c = 0; c < 2; ++c) q[c] = (TC)R[t + c * N] + step * Lx[c];
+        const TC den = fmax(TC(1), sqrt(q[0] * q[0] + q[1] * q[1]));
+#pragma unroll
+        for (int c = 0; c < 2; ++c) {
+            const int64_t e = t + c * N;
+            const TC qc = q[c] / den;
+            const TC o = (TC)Qp[e];
+            R[e] = (T)(qc + beta * (qc - o));
+            Qp[e] = (T)qc;
+        }
     } else {
         const TC a = (TC)R[t] + step * Lx[0];
         const TC b = (TC)R[t + N] + step * Lx[1];
         const TC c = (TC)R[t + 2 * N] + step * Lx[2];
-        // eigen-clip of [[a, b], [b, c]]
-        const TC m = TC(0.5) * (a + c), h = TC(0.5) * (a - c);
-        const TC r = sqrt(h * h + b * b);
-        const TC l1 = fmin(TC(1), fmax(TC(-1), m + r));
-        const TC l2 = fmin(TC(1), fmax(TC(-1), m - r));
-        const TC mp = TC(0.5) * (l1 + l2), dp = TC(0.5) * (l1 - l2);
         TC pa, pb, pc;
-        if (r > TC(0)) {
-            pa = mp + dp * (h / r);
-            pb = dp * (b / r);
-            pc = mp - dp * (h / r);
+        if (REG == NYS_REG_HS2) {
+            const TC den = fmax(TC(1), sqrt(a * a + TC(2) * b * b + c * c));
+            pa = a / den;
+            pb = b / den;
+            pc = c / den;
         } else {
-            pa = mp;
-            pb = TC(0);
-            pc = mp;
+            // eigenvalues m +- r of [[a, b], [b, c]], projected, recomposed on
+            // the same eigenvectors
+            const TC m = TC(0.5) * (a + c), h = TC(0.5) * (a - c);
+            const TC r = sqrt(h * h + b * b);
+            TC l1, l2;
+            if (REG == NYS_REG_HSINF) {
+                // onto |l1| + |l2| <= 1: soft-threshold both magnitudes by theta
+                const TC e1 = m + r, e2 = m - r;
+                const TC a1 = fabs(e1), a2 = fabs(e2);
+                const TC big = fmax(a1, a2), small = fmin(a1, a2);
+                TC th = big - small >= TC(1) ? big - TC(1) : TC(0.5) * (big + small - TC(1));
+                if (a1 + a2 <= TC(1)) th = TC(0);
+                l1 = copysign(fmax(a1 - th, TC(0)), e1);
+                l2 = copysign(fmax(a2 - th, TC(0)), e2);
+            } else {
+                l1 = fmin(TC(1), fmax(TC(-1), m + r));
+                l2 = fmin(TC(1), fmax(TC(-1), m - r));
+            }
+            const TC mp = TC(0.5) * (l1 + l2), dp = TC(0.5) * (l1 - l2);
+            if (r > TC(0)) {
+                pa = mp + dp * (h / r);
+                pb = dp * (b / r);
+                pc = mp - dp * (h / r);
+            } else {
+                pa = mp;
+                pb = TC(0);
+                pc = mp;
+            }
         }
         const TC oa = (TC)Qp[t], ob = (TC)Qp[t + N], oc = (TC)Qp[t + 2 * N];
         R[t] = (T)(pa + beta * (pa - oa));
@@ -158,7 +200,7 @@ __global__ void dual_update_kernel(const T* __restrict__ x, T* __restrict__ R, T
         const int jm = wrap_dec(j, n2);
         const TC xc = (TC)x[t];
         TC Lx[3];
-        if (REG == NYS_REG_TV) {
+        if (first_order(REG)) {
             Lx[0] = xc - (TC)x[rm + j];
             Lx[1] = xc - (TC)x[r0 + jm];
             Lx[2] = TC(0);

@@ -1,6 +1,6 @@
 """Per-call timings of the library's hot entry points, and a small target for ncu.
 
-  python -m paper_2411_08178_gb300.profile_kernels [--case all|precond|normal|sketch|prox|iter|unroll|batch]
+  python -m paper_2411_08178_gb300.profile_kernels [--case all|precond|normal|sketch|prox|prox_mixed|iter|unroll|batch]
         [--n 512] [--ell 200] [--reps 20] [--l2]
 
 Each case builds the 512 x 512 deblurring operator (25 x 25 Gaussian, sigma 4)
@@ -97,6 +97,25 @@ def main():
         out.append(dict(case="prox_tv P=I n_inner=20", ms=ms))
         ms = timed(lambda: api.prox_tv(ctx, pc, 5e-4, 20, s, Q=Q), reps=max(2, args.reps // 2))
         out.append(dict(case="prox_tv P=RNP n_inner=20", ms=ms))
+    if "prox_mixed" in cases:
+        # every mixed-norm regulariser, P = I and P = RNP, 20 dual steps; the
+        # algorithmic bytes of one dual step as the launches stream them:
+        # anisotropic TV fuses the update (x, old and new (R, Q), s, x / g),
+        # the others read R for L^T, then x, R, Q for the update
+        s = torch.rand(n, n, device=dev)
+        for reg in ("tv", "isotv", "hs", "hs2", "hsinf"):
+            G = 2 if reg in ("tv", "isotv") else 3
+            Q = torch.zeros(G, n, n, device=dev)
+            for name, p_ in (("P=I", None), ("P=RNP", pc)):
+                ms = timed(lambda: api.prox_mixed(ctx, p_, reg, 5e-4, 20, s, Q=Q), reps=max(2, args.reps // 2))
+                if p_ is None:
+                    words = 4 * G + 3 if reg == "tv" else 5 * G + 3
+                    per_step = words * N * 4
+                else:
+                    words = 4 * G + 5 if reg == "tv" else 5 * G + 5
+                    per_step = words * N * 4 + 2 * pc.ell_active * N * ub
+                out.append(dict(case=f"prox_mixed {reg} {name} n_inner=20", ms=ms, bytes=21 * per_step,
+                                GBs=21 * per_step / ms / 1e6, active_columns=pc.ell_active if p_ is not None else 0))
     if "iter" in cases:
         y = torch.rand(op.meas_shape, device=dev)
         for name, p in (("plain", None), ("precond", pc)):

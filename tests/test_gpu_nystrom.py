@@ -229,6 +229,48 @@ def test_prox_dual_matches_oracle(env, dt, reg, precond, shape):
     assert rel(x2.cpu(), x2_ref) < tol * 10
 
 
+@pytest.mark.parametrize("dt", ["f32", "f64"])
+@pytest.mark.parametrize("reg", ["isotv", "hs2", "hsinf"])
+@pytest.mark.parametrize("precond", [False, True])
+@pytest.mark.parametrize("shape", [(40, 52), (27, 31)])
+def test_prox_mixed_variants_match_oracle(env, dt, reg, precond, shape):
+    # isotropic TV, HS_2 and HS_inf through prox_mixed: the fused launches
+    # (40 x 52 with P) and the unfused ones (27 x 31, or P = I) against the
+    # oracle's dual APG, then a warm start from the returned Q
+    torch, api, ctx = env
+    (n1, n2), ell = shape, 10
+    s = phantom(max(n1, n2), 6, 3, "mixed")[:n1, :n2] + 0.05 * gaussian_probe_like((n1, n2), 13)
+    lb, n_inner = 0.02, 30
+    tdt = torch.float64 if dt == "f64" else torch.float32
+    P, pc = oracle.nystrom.Identity(), None
+    if precond:
+        h = gaussian_kernel(5, 1.0)
+        opo = O.Operator("blur", n1, n2, kernel=h)
+        ref = oracle.nystrom.nystrom(_flat_phi(opo, n1, n2), gaussian_matrix(n1 * n2, ell, 7), EPS64)
+        P = oracle.nystrom.Precond(ref["U"], ref["S_hat"], 0.0, False)
+        pc = api.Precond(ctx, n1 * n2, ell, tdt).import_factor(ref["U"], ref["S_hat"], 0.0, False)
+        assert pc.ell_active == ell - 1
+    x_ref, Q_ref = oracle.prox.prox_dual(s, reg, lb, P, n_inner)
+    sg = torch.from_numpy(s).to(tdt).cuda()
+    x, Q = api.prox_mixed(ctx, pc, reg, lb, n_inner, sg)
+    tol = TOL[dt] * (10 if dt == "f32" else 1)
+    assert rel(x.cpu(), x_ref) < tol
+    assert rel(Q.cpu(), Q_ref) < tol * 10
+    x2, _ = api.prox_mixed(ctx, pc, reg, lb, n_inner, sg, Q=Q)
+    x2_ref, _ = oracle.prox.prox_dual(s, reg, lb, P, n_inner, Q0=Q_ref)
+    assert rel(x2.cpu(), x2_ref) < tol * 10
+
+
+def test_prox_mixed_rejects_wavelet(env):
+    torch, api, ctx = env
+    from paper_2411_08178_gb300._abi import NYS_EINVAL, NYS_REG_WAVELET, NysError
+    s = torch.zeros(8, 8, dtype=torch.float64, device="cuda")
+    with pytest.raises(NysError) as e:
+        api._prox_dual(lambda *a: api._lib().prox_mixed(a[0], a[1], NYS_REG_WAVELET, *a[2:]), 2, ctx, None,
+                       0.1, 3, s)
+    assert e.value.code == NYS_EINVAL
+
+
 @pytest.mark.parametrize("precond", [False, True, "inactive"])
 @pytest.mark.parametrize("n_inner", [0, 1, 2, 3, 7])
 def test_prox_tv_fused_dual_step_inner_counts(env, precond, n_inner):

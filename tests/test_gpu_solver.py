@@ -72,6 +72,12 @@ def test_wapg_hs_huber_superres_f32(env):
     assert _run(env, "f32", "blur_decim", 64, 12, "hs", 1e-3, 15, fit="huber", delta=0.01, decim=4) < 1e-4
 
 
+@pytest.mark.parametrize("reg,dt,tol", [("isotv", "f64", 1e-10), ("isotv", "f32", 1e-4), ("hs2", "f64", 1e-10),
+                                         ("hsinf", "f64", 1e-10)])
+def test_wapg_mixed_norm_variants_blur(env, reg, dt, tol):
+    assert _run(env, dt, "blur", 64, 16, reg, 5e-3, 15) < tol
+
+
 def test_wapg_tv_radon_f32(env):
     assert _run(env, "f32", "radon", 48, 16, "tv", 2e-4, 10, na=30, nb=70) < 1e-4
 
@@ -88,7 +94,8 @@ def test_step_size_estimate_close_to_oracle(env):
 
 
 @pytest.mark.parametrize("reg,fit,dt", [("tv", "l2", "f64"), ("hs", "huber", "f64"), ("wavelet", "l2", "f64"),
-                                        ("tv", "l2", "f32")])
+                                        ("tv", "l2", "f32"), ("isotv", "l2", "f64"), ("hs2", "l2", "f64"),
+                                        ("hsinf", "huber", "f64")])
 def test_objective_matches_oracle(env, reg, fit, dt):
     torch, api, ctx = env
     n = 48
