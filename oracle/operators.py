@@ -189,6 +189,76 @@ def haar_adjoint(c: np.ndarray, levels: int) -> np.ndarray:
     return x
 
 
+# ------------------------------------------- orthonormal filter banks ---
+# A periodic two-channel orthonormal wavelet (Mallat's pyramid): one level
+# along an axis of length n maps x to
+#     lo[i] = sum_k h[k] x[(2 i + k) mod n],  hi[i] = sum_k g[k] x[(2 i + k) mod n],
+# g[k] = (-1)^k h[L-1-k] (the quadrature-mirror high-pass), stored as [lo | hi];
+# in 2-D the columns axis first, then the rows, and the next level works on
+# the low-low block.  With h = (1, 1)/sqrt 2 this is the Haar transform above.
+# Daubechies' four-tap filter (two vanishing moments, Daubechies 1988):
+#     h = (1 + sqrt 3, 3 + sqrt 3, 3 - sqrt 3, 1 - sqrt 3) / (4 sqrt 2).
+
+_S3 = math.sqrt(3.0)
+WAVELET_TAPS = {
+    "haar": np.array([1.0, 1.0]) / math.sqrt(2.0),
+    "db4": np.array([1.0 + _S3, 3.0 + _S3, 3.0 - _S3, 1.0 - _S3]) / (4.0 * math.sqrt(2.0)),
+}
+
+
+def qmf_highpass(h: np.ndarray) -> np.ndarray:
+    L = len(h)
+    return np.array([(-1) ** k * h[L - 1 - k] for k in range(L)])
+
+
+def _analysis(x, h, axis):
+    g = qmf_highpass(h)
+    n = x.shape[axis]
+    i2 = 2 * np.arange(n // 2)
+    lo = sum(h[k] * np.take(x, (i2 + k) % n, axis=axis) for k in range(len(h)))
+    hi = sum(g[k] * np.take(x, (i2 + k) % n, axis=axis) for k in range(len(h)))
+    return np.concatenate([lo, hi], axis=axis)
+
+
+def _synthesis(c, h, axis):
+    # the transpose of _analysis: x[(2 i + k) mod n] += h[k] lo[i] + g[k] hi[i]
+    g = qmf_highpass(h)
+    n = c.shape[axis]
+    lo, hi = np.split(c, 2, axis=axis)
+    x = np.zeros_like(c)
+    i2 = 2 * np.arange(n // 2)
+    for k in range(len(h)):
+        idx = (i2 + k) % n
+        contrib = h[k] * lo + g[k] * hi
+        xm = np.moveaxis(x, axis, 0)
+        np.add.at(xm, idx, np.moveaxis(contrib, axis, 0))
+    return x
+
+
+def wavelet_forward(x: np.ndarray, levels: int, kind: str = "haar") -> np.ndarray:
+    """Coefficients W x in the Mallat layout for the filter bank `kind`."""
+    h = WAVELET_TAPS[kind]
+    c = np.array(x, dtype=np.float64, copy=True)
+    hh, ww = c.shape[-2:]
+    for _ in range(levels):
+        blk = _analysis(c[..., :hh, :ww], h, axis=-1)
+        c[..., :hh, :ww] = _analysis(blk, h, axis=-2)
+        hh, ww = hh // 2, ww // 2
+    return c
+
+
+def wavelet_adjoint(c: np.ndarray, levels: int, kind: str = "haar") -> np.ndarray:
+    """W^T c (= W^{-1} c, W orthonormal), coarsest level first."""
+    h = WAVELET_TAPS[kind]
+    x = np.array(c, dtype=np.float64, copy=True)
+    n1, n2 = x.shape[-2:]
+    for lev in reversed(range(levels)):
+        hh, ww = n1 >> lev, n2 >> lev
+        blk = _synthesis(x[..., :hh, :ww], h, axis=-2)
+        x[..., :hh, :ww] = _synthesis(blk, h, axis=-1)
+    return x
+
+
 # ----------------------------------------------- finite differences --------
 
 def grad(x: np.ndarray) -> np.ndarray:

@@ -31,19 +31,29 @@ class Problem:
     """min_x f(x) + lambda g(x) for one operator, data y and regulariser."""
 
     def __init__(self, op: ops.Operator, y: np.ndarray, lam: float, reg: str,
-                 fit: str = "l2", huber_delta: float = 0.0, haar_levels: int = 3):
+                 fit: str = "l2", huber_delta: float = 0.0, haar_levels: int = 3, wavelet: str = "haar"):
         self.op, self.y, self.lam, self.reg = op, np.asarray(y, dtype=np.float64), lam, reg
-        self.fit, self.delta, self.levels = fit, huber_delta, haar_levels
+        self.fit, self.delta, self.levels, self.wavelet = fit, huber_delta, haar_levels, wavelet
         self.shape = (op.n1, op.n2)
 
     # variable <-> image
+    def _w(self, x):
+        if self.wavelet == "haar":
+            return ops.haar_forward(x, self.levels)
+        return ops.wavelet_forward(x, self.levels, self.wavelet)
+
+    def _wt(self, c):
+        if self.wavelet == "haar":
+            return ops.haar_adjoint(c, self.levels)
+        return ops.wavelet_adjoint(c, self.levels, self.wavelet)
+
     def to_image(self, v):
-        return ops.haar_adjoint(v, self.levels) if self.reg == "wavelet" else v
+        return self._wt(v) if self.reg == "wavelet" else v
 
     def phi(self, v):
         """Phi = A^T A (or W A^T A W^T) applied to a stack of variables (..., n1, n2)."""
         if self.reg == "wavelet":
-            return ops.haar_forward(self.op.normal(ops.haar_adjoint(v, self.levels)), self.levels)
+            return self._w(self.op.normal(self._wt(v)))
         return self.op.normal(v)
 
     def grad_f(self, v):
@@ -51,7 +61,7 @@ class Problem:
         if self.fit == "huber":
             r = np.clip(r, -self.delta, self.delta)
         g = self.op.adjoint(r)
-        return ops.haar_forward(g, self.levels) if self.reg == "wavelet" else g
+        return self._w(g) if self.reg == "wavelet" else g
 
     def objective(self, v) -> float:
         r = self.op.apply(self.to_image(v)) - self.y
