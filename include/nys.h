@@ -54,6 +54,7 @@ enum { NYS_PHI_ATA = 0, NYS_PHI_W_ATA_WT = 1 };
 /* regularisers ||L x||_{1,phi} (Eq. lpl1qMixedNorm, Appendix A): Haar l1;
  * first differences with phi = 1 (anisotropic TV) or phi = 2 (isotropic TV);
  * the 2x2 Hessian with the Schatten-1, -2 or -inf norm (HS_1, HS_2, HS_inf) */
+enum { NYS_WAVELET_HAAR = 0, NYS_WAVELET_DB4 = 1 };
 enum { NYS_REG_WAVELET = 0, NYS_REG_TV = 1, NYS_REG_HS = 2, NYS_REG_ISOTV = 3, NYS_REG_HS2 = 4, NYS_REG_HSINF = 5 };
 enum { NYS_FIT_L2 = 0, NYS_FIT_HUBER = 1 };
 
@@ -99,9 +100,12 @@ int nys_launch_count(const nys_ctx* ctx, int64_t* count);
  * Blur: (Hx)[i,j] = sum_ab kernel[a*kw+b] x[(i+a-(kh-1)/2) mod n1,
  * (j+b-(kw-1)/2) mod n2]; kh, kw odd.  Decimation keeps pixels (d i, d j).
  * The kernel (host, float64, kh*kw) is copied; the descriptor may be freed
- * after the call.  haar_levels > 0 enables the orthonormal Haar transform W
- * (Mallat layout) used by NYS_PHI_W_ATA_WT and the wavelet regulariser
- * (Sec. III-B, invertible L); n1, n2 must be divisible by 2^haar_levels. */
+ * after the call.  haar_levels > 0 enables the orthonormal wavelet transform
+ * W (Mallat layout, periodic) used by NYS_PHI_W_ATA_WT and the wavelet
+ * regulariser (Sec. III-B, invertible L): Haar, or Daubechies' four-tap
+ * filter bank (wavelet = NYS_WAVELET_DB4: lo[i] = sum_k h[k] x[(2i+k) mod n],
+ * hi with g[k] = (-1)^k h[3-k], columns first); n1, n2 must be divisible by
+ * 2^haar_levels. */
 typedef struct nys_op_desc {
     int kind;               /* NYS_OP_*                                     */
     int dtype;              /* NYS_F32 or NYS_F64                           */
@@ -112,6 +116,7 @@ typedef struct nys_op_desc {
     int n_angles, n_bins;   /* NYS_OP_RADON                                 */
     double angle_span;      /* NYS_OP_RADON, radians (pi = parallel beam)   */
     int haar_levels;        /* 0 = no wavelet                               */
+    int wavelet;            /* NYS_WAVELET_HAAR (0) or NYS_WAVELET_DB4      */
 } nys_op_desc;
 
 int nys_op_create(nys_ctx* ctx, const nys_op_desc* desc, nys_op** op);

@@ -97,7 +97,7 @@ class Operator:
 
     def __init__(self, ctx: Context, kind: str, n1: int, n2: int, dtype=torch.float32, kernel=None,
                  decim: int = 1, n_angles: int = 0, n_bins: int = 0, angle_span: float = math.pi,
-                 haar_levels: int = 0):
+                 haar_levels: int = 0, wavelet: str = "haar"):
         lib = _lib()
         self.ctx, self.kind, self.n1, self.n2, self.dtype = ctx, kind, n1, n2, dtype
         d = A.nys_op_desc()
@@ -113,6 +113,7 @@ class Operator:
         d.decim = decim
         d.n_angles, d.n_bins, d.angle_span = n_angles, n_bins, angle_span
         d.haar_levels = haar_levels
+        d.wavelet = {"haar": A.NYS_WAVELET_HAAR, "db4": A.NYS_WAVELET_DB4}[wavelet]
         h = C.c_void_p()
         check(lib.nys_op_create(ctx.h, C.byref(d), C.byref(h)), ctx.h)
         self.h = h

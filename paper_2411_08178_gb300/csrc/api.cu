@@ -212,6 +212,11 @@ int nys_op_create(nys_ctx* ctx, const nys_op_desc* d, nys_op** out) {
         return fail(ctx, NYS_EINVAL, "image size must be positive with fewer than 2^31 pixels");
     }
     op->haar_levels = d->haar_levels;
+    op->wavelet = d->wavelet;
+    if (d->wavelet != NYS_WAVELET_HAAR && d->wavelet != NYS_WAVELET_DB4) {
+        nys_op_destroy(op);
+        return fail(ctx, NYS_EINVAL, "unknown wavelet %d", d->wavelet);
+    }
     if (d->haar_levels < 0 || (d->haar_levels > 0 && ((d->n1 % (1 << d->haar_levels)) ||
                                                      (d->n2 % (1 << d->haar_levels))))) {
         nys_op_destroy(op);

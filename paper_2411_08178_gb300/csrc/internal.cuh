@@ -89,6 +89,7 @@ struct nys_op {
     int kind = 0, dtype = 0, n1 = 0, n2 = 0;
     int64_t N = 0, M = 0;
     int haar_levels = 0;
+    int wavelet = 0;                  // NYS_WAVELET_HAAR or NYS_WAVELET_DB4
     // blur
     int kh = 0, kw = 0, decim = 1;
     std::vector<double> h;            // kh*kw

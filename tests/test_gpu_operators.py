@@ -120,6 +120,33 @@ def test_haar_forward_inverse(env, dt):
     assert rel(api.op_haar(op, w, inverse=True).cpu(), x) < TOL[dt]
 
 
+@pytest.mark.parametrize("dt", ["f32", "f64"])
+@pytest.mark.parametrize("shape,levels", [((64, 64), 3), ((32, 48), 2), ((16, 8), 3), ((128, 64), 4)])
+def test_daubechies4_forward_inverse(env, dt, shape, levels):
+    # the periodic four-tap transform against the oracle's filter bank, down
+    # to 2 x 1 coarsest blocks (periodised filters), and W^T W = I
+    torch, api, ctx = env
+    n1, n2 = shape
+    op = api.Operator(ctx, "blur", n1, n2, dtype=getattr(torch, DT[dt]), kernel=gaussian_kernel(3, 1.0),
+                      haar_levels=levels, wavelet="db4")
+    x = gaussian_probe_like((2, n1, n2), seed=12)
+    w = api.op_haar(op, _t(torch, x, dt))
+    assert rel(w.cpu(), O.wavelet_forward(x, levels, "db4")) < TOL[dt]
+    assert rel(api.op_haar(op, _t(torch, x, dt), inverse=True).cpu(), O.wavelet_adjoint(x, levels, "db4")) < TOL[dt]
+    assert rel(api.op_haar(op, w, inverse=True).cpu(), x) < TOL[dt]
+
+
+def test_unknown_wavelet_is_refused(env):
+    torch, api, ctx = env
+    from paper_2411_08178_gb300 import _abi as A
+    d = A.nys_op_desc()
+    d.kind, d.dtype, d.n1, d.n2, d.haar_levels, d.wavelet = A.NYS_OP_RADON, A.NYS_F32, 16, 16, 2, 7
+    d.n_angles, d.n_bins, d.angle_span = 8, 24, 3.141592653589793
+    import ctypes as C
+    h = C.c_void_p()
+    assert api._lib().nys_op_create(ctx.h, C.byref(d), C.byref(h)) == A.NYS_EINVAL
+
+
 def test_blur_full_size_sampled(env):
     # the 512 x 512, 25 x 25 sigma = 4 operator at full size, checked on
     # sampled pixels that the oracle computes one by one

@@ -22,29 +22,29 @@ def env():
 
 
 def _setup(kind, n, ell, seed, reg, lam, fit="l2", delta=0.0, decim=1, na=0, nb=0, ksize=9, sigma=1.5,
-           levels=3, noise=0.01):
+           levels=3, noise=0.01, wavelet="haar"):
     h = gaussian_kernel(ksize, sigma) if kind != "radon" else None
     opo = O.Operator(kind, n, n, kernel=h, decim=decim, n_angles=na, n_bins=nb)
     x_true = phantom(n, 8, seed, "mixed")
     y = opo.apply(x_true)
     y = y + np.random.default_rng(seed + 1).normal(0, noise * max(1.0, np.abs(y).max()), y.shape)
-    prob = oracle.wapg.Problem(opo, y, lam, reg, fit=fit, huber_delta=delta, haar_levels=levels)
+    prob = oracle.wapg.Problem(opo, y, lam, reg, fit=fit, huber_delta=delta, haar_levels=levels, wavelet=wavelet)
     phi = lambda V: prob.phi(V.reshape(-1, n, n)).reshape(V.shape[0], -1)
     ref = oracle.nystrom.nystrom(phi, gaussian_matrix(n * n, ell, seed + 2), EPS64) if ell else None
     return h, opo, prob, y, ref
 
 
 def _run(env, dt, kind, n, ell, reg, lam, iters, n_inner=10, fit="l2", delta=0.0, decim=1, na=0, nb=0,
-         levels=3, seed=1, precond=True):
+         levels=3, seed=1, precond=True, wavelet="haar"):
     torch, api, ctx = env
     h, opo, prob, y, ref = _setup(kind, n, ell if precond else 0, seed, reg, lam, fit, delta, decim, na, nb,
-                                  levels=levels)
+                                  levels=levels, wavelet=wavelet)
     P = oracle.nystrom.Precond(ref["U"], ref["S_hat"]) if precond else None
     alpha = 1.0 / oracle.wapg.power_lipschitz(prob, P)
     x_ref = prob.to_image(oracle.wapg.wapg(prob, alpha, iters, precond=P, n_inner=n_inner)["x"])
     tdt = torch.float64 if dt == "f64" else torch.float32
     op = api.Operator(ctx, kind, n, n, dtype=tdt, kernel=h, decim=decim, n_angles=na, n_bins=nb,
-                      haar_levels=levels if reg == "wavelet" else 0)
+                      haar_levels=levels if reg == "wavelet" else 0, wavelet=wavelet)
     pc = None
     if precond:
         pc = api.Precond(ctx, n * n, ell, tdt).import_factor(ref["U"], ref["S_hat"], 0.0, True)
@@ -57,6 +57,14 @@ def _run(env, dt, kind, n, ell, reg, lam, iters, n_inner=10, fit="l2", delta=0.0
 def test_wapg_wavelet_deblur64_f64(env):
     # the 64 x 64 float64 deblurring workload: 9 x 9 sigma 1.5, Haar-3, lambda 1e-3, ell 32
     assert _run(env, "f64", "blur", 64, 32, "wavelet", 1e-3, 15) < 1e-9
+
+
+@pytest.mark.parametrize("dt,tol", [("f64", 1e-9)])
+def test_wapg_daubechies4_deblur(env, dt, tol):
+    # the wavelet model with the four-tap Daubechies transform (4 levels, the
+    # CT experiments' choice): Phi = W A^T A W^T sketched by the oracle, the
+    # semi-smooth Newton prox, 15 WAPG iterations
+    assert _run(env, dt, "blur", 64, 32, "wavelet", 1e-3, 15, levels=4, wavelet="db4") < tol
 
 
 def test_apg_plain_tv_f64(env):
