@@ -16,8 +16,10 @@ slowly and obviously, one step at a time:
   wapg      -- Algorithm 3 (WAPG / APG), power-iteration step size, objectives
   unroll    -- K unrolled Algorithm 3 iterations (TV) and their hand-derived
                reverse-mode gradient with respect to lambda and the blur kernel
+  irm       -- Algorithm 2 (IRM for l_p - l_q) with PCG and the on-the-fly
+               Nystrom preconditioner
 Every function is pinned by a `-m "not gpu"` test against something other than
 itself (closed forms, invariants, brute force, published test vectors); see
 the tests named test_oracle_*.
 """
-from . import operators, philox, nystrom, prox, wapg, unroll  # noqa: F401
+from . import operators, philox, nystrom, prox, wapg, unroll, irm  # noqa: F401
