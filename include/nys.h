@@ -269,6 +269,47 @@ int prox_hs(nys_ctx* ctx, const nys_precond* pc, double lambda_bar, int n_inner,
 int prox_mixed(nys_ctx* ctx, const nys_precond* pc, int reg, double lambda_bar, int n_inner,
                int dtype, int n1, int n2, const void* s, void* out, void* Q_io);
 
+/* ---------------------------------------------------------- Algorithm 2 -- */
+/* Iteratively reweighted minimisation for the l_p - l_q problem of Eq.
+ * lplqReg, min (1/p) sum |Ax - y|^p + (lambda/q) sum |(L x)_l^zeta|^q with L the
+ * first differences (each of the two components its own element).  Outer
+ * iteration k (Algorithm 2, Eqs. v:z:updating and WfWg:IRM): W_f =
+ * |A x - y|_eps^{p-2}, W_g = |L x|_eps^{q-2} (|r|_eps = sqrt(r^2 + eps)), then
+ * x solves (A^T W_f A + lambda L^T W_g L) x = A^T W_f y (Eq.
+ * lplq:sub:updateX:linearEq) by conjugate gradients from the previous x,
+ * preconditioned (ell > 0) with the Nystrom preconditioner of that matrix
+ * built on the fly (Algorithm 1 on Omega drawn with seed + k, Eq.
+ * RYPreconditioner with mu = 0).  CG stops at ||r|| <= cg_tol ||b||. */
+typedef struct nys_irm_desc {
+    double p;            /* data-term exponent, 0 < p <= 2                  */
+    double q;            /* regulariser exponent, 0 < q <= 2                */
+    double lambda;       /* >= 0                                            */
+    double eps;          /* > 0                                             */
+    int ell;             /* sketch size per outer iteration; 0 = plain CG   */
+    int store_dtype;     /* sketch storage: NYS_BF16 or NYS_F32 for float32
+                            operators, NYS_F64 for float64 ones             */
+    uint64_t seed;
+    double cg_tol;       /* > 0                                             */
+    int cg_max;          /* >= 1                                            */
+} nys_irm_desc;
+typedef struct nys_irm_info {
+    int cg_iters;        /* CG iterations of the outer iteration            */
+    double residual;     /* ||r|| / ||b|| at exit                           */
+    double rel_change;   /* ||x^k - x^{k-1}|| / ||x^k||                      */
+} nys_irm_info;
+typedef struct nys_irm nys_irm;
+/* y: device, M values of the op dtype (copied).  x starts at 0.  The handle
+ * keeps op and ctx; destroy it before the op. */
+int nys_irm_create(nys_ctx* ctx, nys_op* op, const nys_irm_desc* desc, const void* y, nys_irm** out);
+/* One outer iteration; synchronises the ctx stream once per CG iteration
+ * (the stopping test).  info (host) may be NULL. */
+int nys_irm_step(nys_irm* irm, nys_irm_info* info);
+/* x (device, N values of the op dtype). */
+int nys_irm_get_x(const nys_irm* irm, void* x);
+/* x = 0 and the outer count (and so the probe seeds) restart. */
+int nys_irm_reset(nys_irm* irm);
+int nys_irm_destroy(nys_irm* irm);
+
 /* ---------------------------------------------------------- Algorithm 3 -- */
 typedef struct nys_solver_desc {
     int reg;             /* NYS_REG_*                                       */

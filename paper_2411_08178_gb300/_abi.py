@@ -42,6 +42,16 @@ class nys_prox_info(C.Structure):
     _fields_ = [("iterations", C.c_int), ("converged", C.c_int), ("residual", C.c_double)]
 
 
+class nys_irm_desc(C.Structure):
+    _fields_ = [("p", C.c_double), ("q", C.c_double), ("lambda_", C.c_double), ("eps", C.c_double),
+                ("ell", C.c_int), ("store_dtype", C.c_int), ("seed", C.c_uint64), ("cg_tol", C.c_double),
+                ("cg_max", C.c_int)]
+
+
+class nys_irm_info(C.Structure):
+    _fields_ = [("cg_iters", C.c_int), ("residual", C.c_double), ("rel_change", C.c_double)]
+
+
 class nys_solver_desc(C.Structure):
     _fields_ = [("reg", C.c_int), ("fit", C.c_int), ("lambda_", C.c_double), ("huber_delta", C.c_double),
                 ("alpha", C.c_double), ("n_inner", C.c_int), ("power_iters", C.c_int),
@@ -90,6 +100,11 @@ PROTOTYPES = {
     "prox_hs": (i32, [vp, C.POINTER(nys_precond), f64, i32, i32, i32, i32, vp, vp, vp]),
     "prox_mixed": (i32, [vp, C.POINTER(nys_precond), i32, f64, i32, i32, i32, i32, vp, vp, vp]),
     "nys_solver_create": (i32, [vp, vp, C.POINTER(nys_solver_desc), vp, C.POINTER(nys_precond), C.POINTER(vp)]),
+    "nys_irm_create": (i32, [vp, vp, C.POINTER(nys_irm_desc), vp, C.POINTER(vp)]),
+    "nys_irm_step": (i32, [vp, C.POINTER(nys_irm_info)]),
+    "nys_irm_get_x": (i32, [vp, vp]),
+    "nys_irm_reset": (i32, [vp]),
+    "nys_irm_destroy": (i32, [vp]),
     "nys_solver_destroy": (i32, [vp]),
     "pgd_step": (i32, [vp, i32]),
     "nys_solver_reset": (i32, [vp]),

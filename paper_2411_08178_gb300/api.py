@@ -394,6 +394,49 @@ class Solver:
             pass
 
 
+class IRM:
+    """nys_irm: Algorithm 2 (IRM for l_p - l_q, L = first differences) with
+    CG, preconditioned by the on-the-fly Nystrom preconditioner when ell > 0."""
+
+    def __init__(self, ctx: Context, op: Operator, y: torch.Tensor, p: float, q: float, lam: float,
+                 eps: float = 1e-4, ell: int = 0, store_dtype=torch.bfloat16, seed: int = 0,
+                 cg_tol: float = 1e-4, cg_max: int = 1000):
+        d = A.nys_irm_desc()
+        d.p, d.q, d.lambda_, d.eps = p, q, lam, eps
+        d.ell = ell
+        d.store_dtype = _DT[torch.float64 if op.dtype == torch.float64 else store_dtype]
+        d.seed, d.cg_tol, d.cg_max = seed, cg_tol, cg_max
+        self.ctx, self.op = ctx, op
+        self._y = y.contiguous()
+        h = C.c_void_p()
+        check(_lib().nys_irm_create(ctx.h, op.h, C.byref(d), _ptr(self._y), C.byref(h)), ctx.h)
+        self.h = h
+
+    def step(self) -> dict:
+        info = A.nys_irm_info()
+        check(_lib().nys_irm_step(self.h, C.byref(info)), self.ctx.h)
+        return {"cg_iters": info.cg_iters, "residual": info.residual, "rel_change": info.rel_change}
+
+    def reset(self):
+        check(_lib().nys_irm_reset(self.h), self.ctx.h)
+
+    def x(self) -> torch.Tensor:
+        out = torch.empty((self.op.n1, self.op.n2), dtype=self.op.dtype, device=torch.device("cuda", self.ctx.device))
+        check(_lib().nys_irm_get_x(self.h, _ptr(out)), self.ctx.h)
+        return out
+
+    def close(self):
+        if getattr(self, "h", None):
+            _lib().nys_irm_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
 def pgd_step(solver: Solver, n: int = 1):
     solver.step(n)
 

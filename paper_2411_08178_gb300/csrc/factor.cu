@@ -377,6 +377,17 @@ int precond_run(nys_ctx* ctx, const nys_precond* pc, int inverse, int dtype, con
     return fail(ctx, NYS_EINVAL, "precond: f32 data needs an f32 or bf16 factor");
 }
 
+// Omega (total entries of store_dt) from the counter-based generator
+int omega_fill(nys_ctx* ctx, int store_dt, void* Omega, int64_t total, uint64_t seed) {
+    cudaStream_t s = ctx->stream;
+    const int grid = (int)std::min<int64_t>((total / 4 + 255) / 256 + 1, ctx->sm_count * 16);
+    if (store_dt == NYS_F64) omega_kernel<double, double><<<grid, 256, 0, s>>>((double*)Omega, total, seed);
+    else if (store_dt == NYS_F32) omega_kernel<float, float><<<grid, 256, 0, s>>>((float*)Omega, total, seed);
+    else omega_kernel<__nv_bfloat16, float><<<grid, 256, 0, s>>>((__nv_bfloat16*)Omega, total, seed);
+    NYS_LAUNCH_CK(ctx);
+    return NYS_OK;
+}
+
 }  // namespace nys
 
 using namespace nys;
@@ -390,13 +401,7 @@ int nys_sketch(nys_ctx* ctx, nys_op* op, int phi_kind, int ell, uint64_t seed, i
         return fail(ctx, NYS_EINVAL, "nys_sketch: store dtype does not match the operator");
     if (phi_kind == NYS_PHI_W_ATA_WT && op->haar_levels <= 0)
         return fail(ctx, NYS_EINVAL, "nys_sketch: W A^T A W^T needs an operator with haar_levels");
-    cudaStream_t s = ctx->stream;
-    const int64_t total = (int64_t)ell * op->N;
-    const int grid = (int)std::min<int64_t>((total / 4 + 255) / 256 + 1, ctx->sm_count * 16);
-    if (store_dt == NYS_F64) omega_kernel<double, double><<<grid, 256, 0, s>>>((double*)Omega, total, seed);
-    else if (store_dt == NYS_F32) omega_kernel<float, float><<<grid, 256, 0, s>>>((float*)Omega, total, seed);
-    else omega_kernel<__nv_bfloat16, float><<<grid, 256, 0, s>>>((__nv_bfloat16*)Omega, total, seed);
-    NYS_LAUNCH_CK(ctx);
+    if (int st0 = omega_fill(ctx, store_dt, Omega, (int64_t)ell * op->N, seed)) return st0;
     if (phi_kind == NYS_PHI_ATA) return op_run(op, 2, Omega, Y, ell, store_dt, store_dt);
     if (phi_kind != NYS_PHI_W_ATA_WT) return fail(ctx, NYS_EINVAL, "nys_sketch: unknown phi kind");
     // W A^T A W^T, chunked through compute-type temporaries

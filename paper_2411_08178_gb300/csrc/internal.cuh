@@ -234,6 +234,9 @@ int check_tc_timeout(nys_ctx* ctx);
 int gemm_tall(nys_ctx* ctx, int in_dt, const void* A, const void* A2, const double* alpha_dev, int64_t N,
               int k, const double* W, int q, int out_dt, void* out);
 
+// Omega for Algorithm 1 step 1: total i.i.d. N(0,1) entries (factor.cu)
+int omega_fill(nys_ctx* ctx, int store_dt, void* Omega, int64_t total, uint64_t seed);
+
 // reductions (reduce.cu)
 int norm2_diff(nys_ctx* ctx, int dtype, int64_t n, const void* a, const void* b, double** out_dev);
 

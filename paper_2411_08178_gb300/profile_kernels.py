@@ -1,6 +1,6 @@
 """Per-call timings of the library's hot entry points, and a small target for ncu.
 
-  python -m paper_2411_08178_gb300.profile_kernels [--case all|precond|normal|sketch|prox|prox_mixed|iter|unroll|batch]
+  python -m paper_2411_08178_gb300.profile_kernels [--case all|precond|normal|sketch|prox|prox_mixed|irm|iter|unroll|batch]
         [--n 512] [--ell 200] [--reps 20] [--l2]
 
 Each case builds the 512 x 512 deblurring operator (25 x 25 Gaussian, sigma 4)
@@ -31,6 +31,8 @@ def main():
     ap.add_argument("--l2", action="store_true", help="keep U resident in L2 (nys_l2_persist)")
     ap.add_argument("--batch-count", type=int, default=64)
     ap.add_argument("--batch-inner", type=int, default=20)
+    ap.add_argument("--irm-eps", type=float, default=1e-8, help="IRM smoothing |r|_eps = sqrt(r^2 + eps)")
+    ap.add_argument("--irm-lambda", type=float, default=2e-3)
     ap.add_argument("--op", choices=["blur", "radon"], default="blur",
                     help="blur: 25 x 25 Gaussian sigma 4; radon: 720 angles x 736 bins")
     args = ap.parse_args()
@@ -116,6 +118,43 @@ def main():
                     per_step = words * N * 4 + 2 * pc.ell_active * N * ub
                 out.append(dict(case=f"prox_mixed {reg} {name} n_inner=20", ms=ms, bytes=21 * per_step,
                                 GBs=21 * per_step / ms / 1e6, active_columns=pc.ell_active if p_ is not None else 0))
+    if "irm" in cases:
+        # Algorithm 2 on the impulsive-noise deblurring setting of the
+        # experiments: 512 x 512, 9 x 9 Gaussian (sigma 1.6) or uniform blur,
+        # 5% + 5% salt and pepper, q = 1, p in {1, 0.5}, PCG tolerance 1e-4,
+        # 5 outer iterations, plain CG against ell = 100 (bf16 sketch); wall
+        # time of the 5 outer iterations (sketches and factors included)
+        import numpy as np
+        rng = np.random.default_rng(51)
+        xt = torch.from_numpy(WL.phantom(n, 30, 51, "ellipse")).float().to(dev)
+        for blur_name, hk in (("gauss9 s1.6", WL.gaussian_kernel(9, 1.6)), ("uniform9", np.full((9, 9), 1.0 / 81))):
+            opi = api.Operator(ctx, "blur", n, n, dtype=torch.float32, kernel=hk)
+            yv = api.op_apply(opi, xt[None])[0].double().cpu().numpy()
+            msk = rng.uniform(size=(n, n))
+            yv = np.where(msk < 0.05, 1.0, np.where(msk > 0.95, 0.0, yv))
+            yt = torch.from_numpy(yv).float().to(dev)
+            for pp in (1.0, 0.5):
+                res = {}
+                for ell_i in (0, 100):
+                    irm = api.IRM(ctx, opi, yt, pp, 1.0, args.irm_lambda, args.irm_eps, ell=ell_i, store_dtype=sd,
+                                  seed=7, cg_tol=1e-4, cg_max=20000)
+                    irm.step()                      # warm-up (sizes scratch, loads kernels)
+                    irm.reset()
+                    torch.cuda.synchronize()
+                    a = torch.cuda.Event(enable_timing=True)
+                    b = torch.cuda.Event(enable_timing=True)
+                    a.record(stream)
+                    its = [irm.step()["cg_iters"] for _ in range(5)]
+                    b.record(stream)
+                    torch.cuda.synchronize()
+                    res[ell_i] = (a.elapsed_time(b), its)
+                    irm.close()
+                t0, t1 = res[0][0], res[100][0]
+                out.append(dict(case=f"irm {blur_name} p={pp} q=1 lambda={args.irm_lambda} eps={args.irm_eps} "
+                                     f"5 outer iterations", ms_plain=t0, ms_rnp=t1, cg_plain=res[0][1],
+                                cg_rnp=res[100][1], saved_time=(t0 - t1) / t0,
+                                saved_cg=1.0 - sum(res[100][1]) / sum(res[0][1])))
+            opi.close()
     if "iter" in cases:
         y = torch.rand(op.meas_shape, device=dev)
         for name, p in (("plain", None), ("precond", pc)):
