@@ -190,10 +190,12 @@ struct Irm {
         NYS_LAUNCH_CK(ctx);
         return NYS_OK;
     }
-    double read_rr() {
-        cudaMemcpyAsync(S->host_rr, S->sc + S_RR, sizeof(double), cudaMemcpyDeviceToHost, s);
-        cudaStreamSynchronize(s);
-        return *S->host_rr;
+    // the last mode-0 reduction, on the host (synchronises the stream)
+    int read_rr(double* out) {
+        NYS_CK(ctx, cudaMemcpyAsync(S->host_rr, S->sc + S_RR, sizeof(double), cudaMemcpyDeviceToHost, s));
+        NYS_CK(ctx, cudaStreamSynchronize(s));
+        *out = *S->host_rr;
+        return NYS_OK;
     }
     // out = Phi_k u = A^T W_f A u + lambda L^T W_g L u
     int phi(const void* u, void* out) {
@@ -252,14 +254,15 @@ struct Irm {
             if (st) return st;
         }
         NYS_CK(ctx, cudaMemcpyAsync(S->xp, S->x, N * sizeof(T), cudaMemcpyDeviceToDevice, s));
-        if ((st = dot(S->b, S->b, N, 0))) return st;
-        const double nb = std::sqrt(read_rr());
+        double v;
+        if ((st = dot(S->b, S->b, N, 0)) || (st = read_rr(&v))) return st;
+        const double nb = std::sqrt(v);
         // r = b - Phi x, z = P^{-1} r, p = z
         if ((st = phi(S->x, S->r))) return st;
         NYS_CK(ctx, launch_pdl(irm_rsub<T>, grid, 256, 0, s, (const T*)S->b, (T*)S->r, N));
         NYS_LAUNCH_CK(ctx);
-        if ((st = dot(S->r, S->r, N, 0))) return st;
-        double rn = std::sqrt(read_rr());
+        if ((st = dot(S->r, S->r, N, 0)) || (st = read_rr(&v))) return st;
+        double rn = std::sqrt(v);
         int it = 0;
         if (rn > S->d.cg_tol * nb) {
             auto precond = [&]() -> int {
@@ -277,8 +280,8 @@ struct Irm {
                 NYS_CK(ctx, launch_pdl(irm_cg_xr<T>, grid, 256, 0, s, (T*)S->x, (T*)S->r, (const T*)S->p,
                                        (const T*)S->q, N, (const double*)S->sc));
                 NYS_LAUNCH_CK(ctx);
-                if ((st = dot(S->r, S->r, N, 0))) return st;
-                rn = std::sqrt(read_rr());
+                if ((st = dot(S->r, S->r, N, 0)) || (st = read_rr(&v))) return st;
+                rn = std::sqrt(v);
                 if (!(rn > S->d.cg_tol * nb)) break;
                 if ((st = precond())) return st;
                 if ((st = dot(S->r, S->z, N, 2))) return st;
@@ -290,10 +293,10 @@ struct Irm {
         // ||x^k - x^{k-1}|| / ||x^k||
         NYS_CK(ctx, launch_pdl(irm_rsub<T>, grid, 256, 0, s, (const T*)S->x, (T*)S->xp, N));   // xp = x - xp
         NYS_LAUNCH_CK(ctx);
-        if ((st = dot(S->xp, S->xp, N, 0))) return st;
-        const double dx = std::sqrt(read_rr());
-        if ((st = dot(S->x, S->x, N, 0))) return st;
-        const double nx = std::sqrt(read_rr());
+        if ((st = dot(S->xp, S->xp, N, 0)) || (st = read_rr(&v))) return st;
+        const double dx = std::sqrt(v);
+        if ((st = dot(S->x, S->x, N, 0)) || (st = read_rr(&v))) return st;
+        const double nx = std::sqrt(v);
         S->k += 1;
         if (info) {
             info->cg_iters = it;
