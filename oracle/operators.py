@@ -149,6 +149,97 @@ def radon_adjoint(s: np.ndarray, n1: int, n2: int, span: float = math.pi) -> np.
     return out.reshape(lead + (n1, n2))
 
 
+# ---------------------------------------------------- fan-beam transform --
+# A point source on a circle of radius R about the image centre and a flat
+# detector at distance D from it (the fan-beam CT geometry): at angle theta,
+# e_s = (cos, sin), e_d = (-sin, cos), source S = R e_s, detector centre
+# S - D e_s, bin m at offset u_m = (m - (n_bins-1)/2) du along e_d; ray m runs
+# from S to its bin.  Joseph's method per ray: a ray whose direction d has
+# |d_y| >= |d_x| samples every row i at column position u = a + b i
+# (b = d_x/d_y), weight |d|/|d_y|; otherwise every column j at row position
+# u = a + b j (b = d_y/d_x), weight |d|/|d_x|; linear interpolation between
+# floor(u) and floor(u) + 1, zero outside.  Pixel (i, j) sits at
+# (j - c2, i - c1).
+
+def fanbeam_tables(n1: int, n2: int, n_angles: int, n_bins: int, R: float, D: float, du: float,
+                   span: float = 2.0 * math.pi):
+    """Per ray (n_angles, n_bins): rowstep flag, a, b, weight."""
+    c1, c2 = (n1 - 1) / 2.0, (n2 - 1) / 2.0
+    th = np.arange(n_angles, dtype=np.float64)[:, None] * (span / n_angles)
+    um = (np.arange(n_bins, dtype=np.float64)[None, :] - (n_bins - 1) / 2.0) * du
+    cs, sn = np.cos(th), np.sin(th)
+    Sx, Sy = R * cs, R * sn
+    dx = -D * cs - um * sn
+    dy = -D * sn + um * cs
+    nd = np.sqrt(dx * dx + dy * dy)
+    row = np.abs(dy) >= np.abs(dx)
+    # the major component divides (never zero: |major| >= |d| / sqrt 2)
+    major = np.where(row, dy, dx)
+    minor = np.where(row, dx, dy)
+    b = minor / major
+    # row-step: u = Sx + (i - c1 - Sy) b + c2; column-step: u = Sy + (j - c2 - Sx) b + c1
+    a = np.where(row, Sx - (c1 + Sy) * b + c2, Sy - (c2 + Sx) * b + c1)
+    w = nd / np.abs(major)
+    return row, a, b, w
+
+
+def fanbeam_apply(x: np.ndarray, n_angles: int, n_bins: int, R: float, D: float, du: float,
+                  span: float = 2.0 * math.pi) -> np.ndarray:
+    x = np.asarray(x, dtype=np.float64)
+    n1, n2 = x.shape[-2:]
+    lead = x.shape[:-2]
+    row, a, b, w = fanbeam_tables(n1, n2, n_angles, n_bins, R, D, du, span)
+    out = np.zeros(lead + (n_angles, n_bins), dtype=np.float64)
+    for k in range(n_angles):
+        for rs, nl, lim in ((True, n1, n2), (False, n2, n1)):
+            m = np.nonzero(row[k] == rs)[0]
+            if m.size == 0:
+                continue
+            l = np.arange(nl, dtype=np.float64)
+            u = a[k, m][:, None] + b[k, m][:, None] * l[None, :]        # (rays, lines)
+            lo = np.floor(u)
+            f = u - lo
+            lo = lo.astype(np.int64)
+            line = np.broadcast_to(np.arange(nl)[None, :], lo.shape)
+            acc = np.zeros(lead + (m.size,), dtype=np.float64)
+            for idx, wgt in ((lo, 1.0 - f), (lo + 1, f)):
+                ok = (idx >= 0) & (idx < lim)
+                ii = np.where(ok, idx, 0)
+                vals = x[..., line, ii] if rs else x[..., ii, line]
+                acc += np.sum(np.where(ok, wgt, 0.0) * vals, axis=-1)
+            out[..., k, m] = w[k, m] * acc
+    return out
+
+
+def fanbeam_adjoint(s: np.ndarray, n1: int, n2: int, R: float, D: float, du: float,
+                    span: float = 2.0 * math.pi) -> np.ndarray:
+    s = np.asarray(s, dtype=np.float64)
+    n_angles, n_bins = s.shape[-2:]
+    lead = s.shape[:-2]
+    flat = s.reshape((-1, n_angles, n_bins))
+    row, a, b, w = fanbeam_tables(n1, n2, n_angles, n_bins, R, D, du, span)
+    out = np.zeros((flat.shape[0], n1 * n2), dtype=np.float64)
+    for k in range(n_angles):
+        for rs, nl, lim in ((True, n1, n2), (False, n2, n1)):
+            m = np.nonzero(row[k] == rs)[0]
+            if m.size == 0:
+                continue
+            l = np.arange(nl, dtype=np.float64)
+            u = a[k, m][:, None] + b[k, m][:, None] * l[None, :]
+            lo = np.floor(u)
+            f = u - lo
+            lo = lo.astype(np.int64)
+            line = np.broadcast_to(np.arange(nl)[None, :], lo.shape)
+            for idx, wgt in ((lo, 1.0 - f), (lo + 1, f)):
+                ok = (idx >= 0) & (idx < lim)
+                pix = (line * n2 + idx) if rs else (idx * n2 + line)
+                pix = pix[ok]
+                for bb in range(flat.shape[0]):
+                    contrib = (w[k, m][:, None] * wgt * flat[bb, k, m][:, None])[ok]
+                    out[bb] += np.bincount(pix, weights=contrib, minlength=n1 * n2)
+    return out.reshape(lead + (n1, n2))
+
+
 # ------------------------------------------------------------------ Haar ---
 
 _R2 = 1.0 / math.sqrt(2.0)
@@ -305,15 +396,19 @@ class Operator:
     """A forward model A with its exact adjoint, on (..., n1, n2) images."""
 
     def __init__(self, kind: str, n1: int, n2: int, kernel=None, decim: int = 1,
-                 n_angles: int = 0, n_bins: int = 0, span: float = math.pi):
+                 n_angles: int = 0, n_bins: int = 0, span: float | None = None,
+                 src_dist: float = 0.0, det_dist: float = 0.0, det_spacing: float = 1.0):
         self.kind, self.n1, self.n2 = kind, n1, n2
         self.kernel = None if kernel is None else np.asarray(kernel, dtype=np.float64)
+        if span is None:
+            span = 2.0 * math.pi if kind == "fanbeam" else math.pi
         self.decim, self.n_angles, self.n_bins, self.span = decim, n_angles, n_bins, span
+        self.R, self.D, self.du = src_dist, det_dist, det_spacing
         if kind == "blur":
             self.meas_shape = (n1, n2)
         elif kind == "blur_decim":
             self.meas_shape = (n1 // decim, n2 // decim)
-        elif kind == "radon":
+        elif kind in ("radon", "fanbeam"):
             self.meas_shape = (n_angles, n_bins)
         else:
             raise ValueError(kind)
@@ -323,6 +418,8 @@ class Operator:
             return blur_apply(x, self.kernel)
         if self.kind == "blur_decim":
             return decim_apply(x, self.kernel, self.decim)
+        if self.kind == "fanbeam":
+            return fanbeam_apply(x, self.n_angles, self.n_bins, self.R, self.D, self.du, self.span)
         return radon_apply(x, self.n_angles, self.n_bins, self.span)
 
     def adjoint(self, y):
@@ -330,6 +427,8 @@ class Operator:
             return blur_adjoint(y, self.kernel)
         if self.kind == "blur_decim":
             return decim_adjoint(y, self.kernel, self.decim)
+        if self.kind == "fanbeam":
+            return fanbeam_adjoint(y, self.n1, self.n2, self.R, self.D, self.du, self.span)
         return radon_adjoint(y, self.n1, self.n2, self.span)
 
     def normal(self, x):
