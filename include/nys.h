@@ -49,7 +49,7 @@ enum {
 };
 
 enum { NYS_F32 = 0, NYS_F64 = 1, NYS_BF16 = 2 };
-enum { NYS_OP_BLUR = 0, NYS_OP_BLUR_DECIM = 1, NYS_OP_RADON = 2 };
+enum { NYS_OP_BLUR = 0, NYS_OP_BLUR_DECIM = 1, NYS_OP_RADON = 2, NYS_OP_FANBEAM = 3 };
 enum { NYS_PHI_ATA = 0, NYS_PHI_W_ATA_WT = 1 };
 /* regularisers ||L x||_{1,phi} (Eq. lpl1qMixedNorm, Appendix A): Haar l1;
  * first differences with phi = 1 (anisotropic TV) or phi = 2 (isotropic TV);
@@ -97,6 +97,13 @@ int nys_launch_count(const nys_ctx* ctx, int64_t* count);
  * pixels, pixel (i, j) at x = j - (n2-1)/2, y = i - (n1-1)/2; one sample per
  * row (|cos| + 1e-9 >= |sin|, weight 1/|cos|) or per column (weight 1/|sin|)
  * with linear interpolation, zero outside the image.
+ * Fan beam (NYS_OP_FANBEAM, the experiments' second CT geometry): a point
+ * source on a circle of radius src_dist about the image centre and a flat
+ * detector at det_dist from it; at angle theta_k = k * angle_span / n_angles
+ * the source sits at R (cos, sin) and bin m at offset (m - (n_bins-1)/2)
+ * det_spacing along (-sin, cos) on the detector; each ray is sampled by
+ * Joseph's method along rows (|d_y| >= |d_x|) or columns, weight |d| / |major
+ * component|.  src_dist must exceed the image half-diagonal by 2 pixels.
  * Blur: (Hx)[i,j] = sum_ab kernel[a*kw+b] x[(i+a-(kh-1)/2) mod n1,
  * (j+b-(kw-1)/2) mod n2]; kh, kw odd.  Decimation keeps pixels (d i, d j).
  * The kernel (host, float64, kh*kw) is copied; the descriptor may be freed
@@ -117,6 +124,9 @@ typedef struct nys_op_desc {
     double angle_span;      /* NYS_OP_RADON, radians (pi = parallel beam)   */
     int haar_levels;        /* 0 = no wavelet                               */
     int wavelet;            /* NYS_WAVELET_HAAR (0) or NYS_WAVELET_DB4      */
+    double src_dist;        /* NYS_OP_FANBEAM: source to image centre, R    */
+    double det_dist;        /* NYS_OP_FANBEAM: source to detector, D > R    */
+    double det_spacing;     /* NYS_OP_FANBEAM: detector bin width           */
 } nys_op_desc;
 
 int nys_op_create(nys_ctx* ctx, const nys_op_desc* desc, nys_op** op);

@@ -14,7 +14,7 @@ LIB_PATH = os.path.join(HERE, "lib", "libnys.so")
 NYS_OK, NYS_EINVAL, NYS_ENOMEM, NYS_ECUDA, NYS_ENOTSPD = 0, 1, 2, 3, 4
 NYS_EDEGENERATE, NYS_ENONFINITE, NYS_ETIMEOUT, NYS_ENOCONV = 5, 6, 7, 8
 NYS_F32, NYS_F64, NYS_BF16 = 0, 1, 2
-NYS_OP_BLUR, NYS_OP_BLUR_DECIM, NYS_OP_RADON = 0, 1, 2
+NYS_OP_BLUR, NYS_OP_BLUR_DECIM, NYS_OP_RADON, NYS_OP_FANBEAM = 0, 1, 2, 3
 NYS_PHI_ATA, NYS_PHI_W_ATA_WT = 0, 1
 NYS_REG_WAVELET, NYS_REG_TV, NYS_REG_HS, NYS_REG_ISOTV, NYS_REG_HS2, NYS_REG_HSINF = 0, 1, 2, 3, 4, 5
 NYS_WAVELET_HAAR, NYS_WAVELET_DB4 = 0, 1
@@ -28,7 +28,8 @@ class nys_op_desc(C.Structure):
     _fields_ = [("kind", C.c_int), ("dtype", C.c_int), ("n1", C.c_int), ("n2", C.c_int),
                 ("kernel", C.POINTER(C.c_double)), ("kh", C.c_int), ("kw", C.c_int), ("decim", C.c_int),
                 ("n_angles", C.c_int), ("n_bins", C.c_int), ("angle_span", C.c_double),
-                ("haar_levels", C.c_int), ("wavelet", C.c_int)]
+                ("haar_levels", C.c_int), ("wavelet", C.c_int), ("src_dist", C.c_double),
+                ("det_dist", C.c_double), ("det_spacing", C.c_double)]
 
 
 class nys_precond(C.Structure):

@@ -93,15 +93,19 @@ class Context:
 
 
 class Operator:
-    """nys_op: blur, blur + decimation or parallel-beam ray transform."""
+    """nys_op: blur, blur + decimation, parallel-beam or fan-beam ray transform."""
 
     def __init__(self, ctx: Context, kind: str, n1: int, n2: int, dtype=torch.float32, kernel=None,
-                 decim: int = 1, n_angles: int = 0, n_bins: int = 0, angle_span: float = math.pi,
-                 haar_levels: int = 0, wavelet: str = "haar"):
+                 decim: int = 1, n_angles: int = 0, n_bins: int = 0, angle_span: float | None = None,
+                 haar_levels: int = 0, wavelet: str = "haar", src_dist: float = 0.0, det_dist: float = 0.0,
+                 det_spacing: float = 1.0):
         lib = _lib()
         self.ctx, self.kind, self.n1, self.n2, self.dtype = ctx, kind, n1, n2, dtype
+        if angle_span is None:
+            angle_span = 2.0 * math.pi if kind == "fanbeam" else math.pi
         d = A.nys_op_desc()
-        d.kind = {"blur": A.NYS_OP_BLUR, "blur_decim": A.NYS_OP_BLUR_DECIM, "radon": A.NYS_OP_RADON}[kind]
+        d.kind = {"blur": A.NYS_OP_BLUR, "blur_decim": A.NYS_OP_BLUR_DECIM, "radon": A.NYS_OP_RADON,
+                  "fanbeam": A.NYS_OP_FANBEAM}[kind]
         d.dtype = _DT[dtype]
         d.n1, d.n2 = n1, n2
         self._kernel = None
@@ -114,6 +118,7 @@ class Operator:
         d.n_angles, d.n_bins, d.angle_span = n_angles, n_bins, angle_span
         d.haar_levels = haar_levels
         d.wavelet = {"haar": A.NYS_WAVELET_HAAR, "db4": A.NYS_WAVELET_DB4}[wavelet]
+        d.src_dist, d.det_dist, d.det_spacing = src_dist, det_dist, det_spacing
         h = C.c_void_p()
         check(lib.nys_op_create(ctx.h, C.byref(d), C.byref(h)), ctx.h)
         self.h = h

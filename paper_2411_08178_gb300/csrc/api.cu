@@ -87,6 +87,7 @@ int op_run(nys_op* op, int which, const void* x, void* y, int batch, int in_dt, 
         case NYS_OP_BLUR: return blur_run(op, which, x, y, batch, in_dt, out_dt);
         case NYS_OP_BLUR_DECIM: return decim_run(op, which, x, y, batch, in_dt, out_dt);
         case NYS_OP_RADON: return radon_run(op, which, x, y, batch, in_dt, out_dt);
+        case NYS_OP_FANBEAM: return fanbeam_run(op, which, x, y, batch, in_dt, out_dt);
     }
     return fail(op->ctx, NYS_EINVAL, "unknown operator kind %d", op->kind);
 }
@@ -248,6 +249,22 @@ int nys_op_create(nys_ctx* ctx, const nys_op_desc* d, nys_op** out) {
         op->span = d->angle_span;
         op->M = (int64_t)d->n_angles * d->n_bins;
         st = radon_setup(op);
+    } else if (d->kind == NYS_OP_FANBEAM) {
+        const double half_diag = 0.5 * std::sqrt((double)d->n1 * d->n1 + (double)d->n2 * d->n2);
+        if (d->n_angles <= 0 || d->n_bins <= 0 || !(d->angle_span > 0.0) || !(d->src_dist > half_diag + 2.0) ||
+            !(d->det_dist > d->src_dist) || !(d->det_spacing > 0.0)) {
+            nys_op_destroy(op);
+            return fail(ctx, NYS_EINVAL, "fan-beam geometry needs n_angles, n_bins > 0, span > 0, "
+                                         "src_dist beyond the image, det_dist > src_dist, det_spacing > 0");
+        }
+        op->n_angles = d->n_angles;
+        op->n_bins = d->n_bins;
+        op->span = d->angle_span;
+        op->src_dist = d->src_dist;
+        op->det_dist = d->det_dist;
+        op->det_spacing = d->det_spacing;
+        op->M = (int64_t)d->n_angles * d->n_bins;
+        st = fanbeam_setup(op);
     } else {
         nys_op_destroy(op);
         return fail(ctx, NYS_EINVAL, "unknown operator kind %d", d->kind);

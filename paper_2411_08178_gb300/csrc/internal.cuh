@@ -105,6 +105,7 @@ struct nys_op {
     double span = 0.0;
     void* rtab = nullptr;             // per-angle tables, see radon.cu
     void* lines = nullptr;            // radon: `chunk` images as line-major copies (row-major and transposed)
+    double src_dist = 0.0, det_dist = 0.0, det_spacing = 1.0;   // fan beam
     int radon_adj_ak = 16;            // radon adjoint: angles per round, 4, 8 or 16 (nys_op_autotune)
     int radon_adj_ib = 4;             // radon adjoint: images per CTA for batches of 4 or more, 1 or 4
     int blur_tile = 64;               // blur: output tile side, 32 or 64 (float32; chosen by nys_op_autotune)
@@ -208,6 +209,8 @@ int blur_run(nys_op* op, int which /*0 fwd,1 adj,2 normal*/, const void* x, void
 int decim_run(nys_op* op, int which, const void* x, void* y, int batch, int in_dtype, int out_dtype);
 int radon_setup(nys_op* op);
 int radon_run(nys_op* op, int which, const void* x, void* y, int batch, int in_dtype, int out_dtype);
+int fanbeam_setup(nys_op* op);
+int fanbeam_run(nys_op* op, int which, const void* x, void* y, int batch, int in_dtype, int out_dtype);
 int haar_run(nys_op* op, const void* in, void* out, int batch, int inverse, int in_dtype, int out_dtype);
 // generic: which = 0 A, 1 A^T, 2 A^T A ; dtypes may differ from op dtype (bf16 io)
 int op_run(nys_op* op, int which, const void* x, void* y, int batch, int in_dtype, int out_dtype);

@@ -33,8 +33,9 @@ def main():
     ap.add_argument("--batch-inner", type=int, default=20)
     ap.add_argument("--irm-eps", type=float, default=1e-8, help="IRM smoothing |r|_eps = sqrt(r^2 + eps)")
     ap.add_argument("--irm-lambda", type=float, default=2e-3)
-    ap.add_argument("--op", choices=["blur", "radon"], default="blur",
-                    help="blur: 25 x 25 Gaussian sigma 4; radon: 720 angles x 736 bins")
+    ap.add_argument("--op", choices=["blur", "radon", "fanbeam"], default="blur",
+                    help="blur: 25 x 25 Gaussian sigma 4; radon: 720 angles x 736 bins; fanbeam: 720 angles over "
+                         "360 deg x 1024 bins, source at 1000, detector at 2000 pixels")
     args = ap.parse_args()
     import torch
 
@@ -51,8 +52,11 @@ def main():
     N = n * n
     if args.op == "blur":
         op = api.Operator(ctx, "blur", n, n, dtype=torch.float32, kernel=WL.gaussian_kernel(25, 4.0))
-    else:
+    elif args.op == "radon":
         op = api.Operator(ctx, "radon", n, n, dtype=torch.float32, n_angles=720, n_bins=736)
+    else:
+        op = api.Operator(ctx, "fanbeam", n, n, dtype=torch.float32, n_angles=720, n_bins=1024, src_dist=1000.0,
+                          det_dist=2000.0)
     sd = torch.bfloat16 if args.u_dtype == "bf16" else torch.float32
     ub = 2 if sd == torch.bfloat16 else 4
 

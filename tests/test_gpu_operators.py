@@ -147,6 +147,38 @@ def test_unknown_wavelet_is_refused(env):
     assert api._lib().nys_op_create(ctx.h, C.byref(d), C.byref(h)) == A.NYS_EINVAL
 
 
+@pytest.mark.parametrize("dt", ["f32", "f64"])
+@pytest.mark.parametrize("n1,n2,A,B", [(24, 24, 9, 40), (20, 28, 7, 47)])
+def test_fanbeam_matches_oracle(env, dt, n1, n2, A, B):
+    # the fan-beam pair (point source at R = 30, flat detector at D = 60,
+    # unit bins, full circle) against the oracle, and its dot-product test
+    torch, api, ctx = env
+    R, D, du = 30.0, 60.0, 1.0
+    op = api.Operator(ctx, "fanbeam", n1, n2, dtype=getattr(torch, DT[dt]), n_angles=A, n_bins=B, src_dist=R,
+                      det_dist=D, det_spacing=du)
+    x = gaussian_probe_like((2, n1, n2), seed=21)
+    s = gaussian_probe_like((2, A, B), seed=22)
+    ya = api.op_apply(op, _t(torch, x, dt))
+    assert rel(ya.cpu(), O.fanbeam_apply(x, A, B, R, D, du)) < TOL[dt]
+    xa = api.op_adjoint(op, _t(torch, s, dt))
+    assert rel(xa.cpu(), O.fanbeam_adjoint(s, n1, n2, R, D, du)) < TOL[dt]
+    xn = api.op_normal(op, _t(torch, x, dt))
+    assert rel(xn.cpu(), O.fanbeam_adjoint(O.fanbeam_apply(x, A, B, R, D, du), n1, n2, R, D, du)) < TOL[dt]
+    lhs = float((ya.double().cpu() * torch.from_numpy(s)).sum())
+    rhs = float((torch.from_numpy(x) * xa.double().cpu()).sum())
+    assert lhs == pytest.approx(rhs, rel=1e-12 if dt == "f64" else 1e-5)
+
+
+def test_fanbeam_geometry_is_validated(env):
+    torch, api, ctx = env
+    from paper_2411_08178_gb300._abi import NYS_EINVAL, NysError
+    for kw in (dict(src_dist=10.0, det_dist=40.0), dict(src_dist=30.0, det_dist=20.0), dict(src_dist=30.0, det_dist=60.0,
+                                                                                            det_spacing=0.0)):
+        with pytest.raises(NysError) as e:
+            api.Operator(ctx, "fanbeam", 24, 24, n_angles=8, n_bins=30, **kw)
+        assert e.value.code == NYS_EINVAL
+
+
 def test_blur_full_size_sampled(env):
     # the 512 x 512, 25 x 25 sigma = 4 operator at full size, checked on
     # sampled pixels that the oracle computes one by one

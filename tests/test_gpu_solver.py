@@ -86,6 +86,28 @@ def test_wapg_mixed_norm_variants_blur(env, reg, dt, tol):
     assert _run(env, dt, "blur", 64, 16, reg, 5e-3, 15) < tol
 
 
+def test_wapg_tv_fanbeam_f64(env):
+    # Algorithm 3 on the fan-beam forward model (Sketch, factor and the
+    # P-metric TV prox unchanged): 10 iterations against the oracle
+    torch, api, ctx = env
+    n, A, B, R, D, ell, lam = 32, 24, 64, 40.0, 80.0, 16, 2e-3
+    opo = O.Operator("fanbeam", n, n, n_angles=A, n_bins=B, src_dist=R, det_dist=D, det_spacing=1.0)
+    x_true = phantom(n, 6, 4, "mixed")
+    y = opo.apply(x_true)
+    y = y + np.random.default_rng(5).normal(0, 0.01 * np.abs(y).max(), y.shape)
+    prob = oracle.wapg.Problem(opo, y, lam, "tv")
+    phi = lambda V: prob.phi(V.reshape(-1, n, n)).reshape(V.shape[0], -1)
+    ref = oracle.nystrom.nystrom(phi, gaussian_matrix(n * n, ell, 6), EPS64)
+    P = oracle.nystrom.Precond(ref["U"], ref["S_hat"])
+    alpha = 1.0 / oracle.wapg.power_lipschitz(prob, P)
+    x_ref = oracle.wapg.wapg(prob, alpha, 10, precond=P, n_inner=10)["x"]
+    op = api.Operator(ctx, "fanbeam", n, n, dtype=torch.float64, n_angles=A, n_bins=B, src_dist=R, det_dist=D)
+    pc = api.Precond(ctx, n * n, ell, torch.float64).import_factor(ref["U"], ref["S_hat"], 0.0, True)
+    sol = api.Solver(ctx, op, torch.from_numpy(y).cuda(), "tv", lam, pc=pc, alpha=alpha, n_inner=10)
+    sol.step(10)
+    assert rel(sol.x().cpu(), x_ref) < 1e-10
+
+
 def test_wapg_tv_radon_f32(env):
     assert _run(env, "f32", "radon", 48, 16, "tv", 2e-4, 10, na=30, nb=70) < 1e-4
 
