@@ -92,9 +92,19 @@ __global__ void __launch_bounds__(256) fan_adj_kernel(const TI* __restrict__ s, 
     TC acc = TC(0);
     for (int k = 0; k < n_angles; ++k) {
         const float* g = tab.ang + 4 * k;
+        // the rays that reach this pixel pass within one pixel of it, so their
+        // directions differ from the source-to-pixel direction v by at most
+        // asin(1/depth): away from the 45-degree split (|v_y| = |v_x|, where
+        // tan changes by 2 per radian) only one kind of ray can reach it
+        const float vx = px - g[0], vy = py - g[1];
+        const float depth = -(vx * g[2] + vy * g[3]);
+        const float tol = 8.0f / depth;
+        const bool try_row = fabsf(vy) >= fabsf(vx) * (1.0f - tol);
+        const bool try_col = fabsf(vx) >= fabsf(vy) * (1.0f - tol);
         TC part = TC(0);
 #pragma unroll
         for (int kind = 0; kind < 2; ++kind) {          // row-step rays (via row i), then column-step (via column j)
+            if (!(kind == 0 ? try_row : try_col)) continue;
             const float m1 = kind == 0 ? fan_bin(g, px - 1.0f, py, tab.D, tab.du, tab.cb)
                                        : fan_bin(g, px, py - 1.0f, tab.D, tab.du, tab.cb);
             const float m2 = kind == 0 ? fan_bin(g, px + 1.0f, py, tab.D, tab.du, tab.cb)
