@@ -134,7 +134,7 @@ def test_gradient_matches_torch_autograd():
         x, tp = xn, tk
     L = torch.mean((x - torch.from_numpy(x_true)) ** 2)
     L.backward()
-    assert float(L) == pytest.approx(loss, rel=1e-12)
+    assert float(L.detach()) == pytest.approx(loss, rel=1e-12)
     assert abs(float(lam.grad) - dlam) <= 1e-10 * abs(dlam)
     g = hh.grad.numpy()
     assert np.linalg.norm(g - dh) <= 1e-10 * np.linalg.norm(g)
