@@ -103,7 +103,9 @@ int nys_launch_count(const nys_ctx* ctx, int64_t* count);
  * the source sits at R (cos, sin) and bin m at offset (m - (n_bins-1)/2)
  * det_spacing along (-sin, cos) on the detector; each ray is sampled by
  * Joseph's method along rows (|d_y| >= |d_x|) or columns, weight |d| / |major
- * component|.  src_dist must exceed the image half-diagonal by 2 pixels.
+ * component|.  src_dist must exceed the image half-diagonal by 2 pixels,
+ * and n_angles <= 65535.  Both ray transforms need n_angles * n_bins < 2^31
+ * and N = n1 * n2 < 2^31; other sizes return NYS_EINVAL.
  * Blur: (Hx)[i,j] = sum_ab kernel[a*kw+b] x[(i+a-(kh-1)/2) mod n1,
  * (j+b-(kw-1)/2) mod n2]; kh, kw odd.  Decimation keeps pixels (d i, d j).
  * The kernel (host, float64, kh*kw) is copied; the descriptor may be freed

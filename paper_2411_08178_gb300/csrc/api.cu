@@ -240,9 +240,10 @@ int nys_op_create(nys_ctx* ctx, const nys_op_desc* d, nys_op** out) {
         op->M = (int64_t)(d->n1 / op->decim) * (d->n2 / op->decim);
         st = blur_setup(op);
     } else if (d->kind == NYS_OP_RADON) {
-        if (d->n_angles <= 0 || d->n_bins <= 0 || !(d->angle_span > 0.0)) {
+        if (d->n_angles <= 0 || d->n_bins <= 0 || !(d->angle_span > 0.0) ||
+            (int64_t)d->n_angles * d->n_bins >= (int64_t(1) << 31)) {
             nys_op_destroy(op);
-            return fail(ctx, NYS_EINVAL, "radon geometry needs n_angles, n_bins > 0 and span > 0");
+            return fail(ctx, NYS_EINVAL, "radon geometry needs n_angles, n_bins > 0, span > 0 and fewer than 2^31 bins");
         }
         op->n_angles = d->n_angles;
         op->n_bins = d->n_bins;
@@ -251,11 +252,14 @@ int nys_op_create(nys_ctx* ctx, const nys_op_desc* d, nys_op** out) {
         st = radon_setup(op);
     } else if (d->kind == NYS_OP_FANBEAM) {
         const double half_diag = 0.5 * std::sqrt((double)d->n1 * d->n1 + (double)d->n2 * d->n2);
-        if (d->n_angles <= 0 || d->n_bins <= 0 || !(d->angle_span > 0.0) || !(d->src_dist > half_diag + 2.0) ||
-            !(d->det_dist > d->src_dist) || !(d->det_spacing > 0.0)) {
+        // the kernels index rays with 32-bit ints and put the angle in grid.y
+        if (d->n_angles <= 0 || d->n_angles > 65535 || d->n_bins <= 0 ||
+            (int64_t)d->n_angles * d->n_bins >= (int64_t(1) << 31) || !(d->angle_span > 0.0) ||
+            !(d->src_dist > half_diag + 2.0) || !(d->det_dist > d->src_dist) || !(d->det_spacing > 0.0)) {
             nys_op_destroy(op);
-            return fail(ctx, NYS_EINVAL, "fan-beam geometry needs n_angles, n_bins > 0, span > 0, "
-                                         "src_dist beyond the image, det_dist > src_dist, det_spacing > 0");
+            return fail(ctx, NYS_EINVAL, "fan-beam geometry needs 0 < n_angles <= 65535, n_bins > 0, fewer than "
+                                         "2^31 bins, span > 0, src_dist beyond the image, det_dist > src_dist, "
+                                         "det_spacing > 0");
         }
         op->n_angles = d->n_angles;
         op->n_bins = d->n_bins;
