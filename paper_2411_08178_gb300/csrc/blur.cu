@@ -227,10 +227,12 @@ int launch_sep(nys_op* op, const void* x, void* y, int batch, const void* taps, 
         NYS_CK(op->ctx, cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
         attr_max = (int)sm;
     }
-    dim3 grid((op->n2 + T - 1) / T, (op->n1 + T - 1) / T, batch);
-    NYS_CK(op->ctx, launch_pdl(k, grid, 256, sm, op->ctx->stream, (const TI*)x, (TO*)y, op->n1, op->n2,
-                               (const TC*)taps, Lcp, Lrp, cc, cr));
-    NYS_LAUNCH_CK(op->ctx);
+    for (int b0 = 0; b0 < batch; b0 += 65535) {     // images in grid.z
+        dim3 grid((op->n2 + T - 1) / T, (op->n1 + T - 1) / T, std::min(65535, batch - b0));
+        NYS_CK(op->ctx, launch_pdl(k, grid, 256, sm, op->ctx->stream, (const TI*)x + (size_t)b0 * op->N,
+                                   (TO*)y + (size_t)b0 * op->N, op->n1, op->n2, (const TC*)taps, Lcp, Lrp, cc, cr));
+        NYS_LAUNCH_CK(op->ctx);
+    }
     return NYS_OK;
 }
 
@@ -245,10 +247,13 @@ int launch_c2d(nys_op* op, const void* x, void* y, int batch, const void* taps) 
         NYS_CK(op->ctx, cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
         attr_max = (int)sm;
     }
-    dim3 grid((op->n2 + T - 1) / T, (op->n1 + T - 1) / T, batch);
-    NYS_CK(op->ctx, launch_pdl(k, grid, 256, sm, op->ctx->stream, (const TI*)x, (TO*)y, op->n1, op->n2,
-                               (const TC*)taps, op->kh, kwp, (op->kh - 1) / 2, (op->kw - 1) / 2));
-    NYS_LAUNCH_CK(op->ctx);
+    for (int b0 = 0; b0 < batch; b0 += 65535) {     // images in grid.z
+        dim3 grid((op->n2 + T - 1) / T, (op->n1 + T - 1) / T, std::min(65535, batch - b0));
+        NYS_CK(op->ctx, launch_pdl(k, grid, 256, sm, op->ctx->stream, (const TI*)x + (size_t)b0 * op->N,
+                                   (TO*)y + (size_t)b0 * op->N, op->n1, op->n2, (const TC*)taps, op->kh, kwp,
+                                   (op->kh - 1) / 2, (op->kw - 1) / 2));
+        NYS_LAUNCH_CK(op->ctx);
+    }
     return NYS_OK;
 }
 
