@@ -122,8 +122,9 @@ class Workload:
     n_inner: int = 20
 
 
-# The five workload presets.  Sizes, operators, regularisers, lambda, sketch
-# size and iteration counts are the ones the reconstruction benchmark names.
+# The four single-problem presets (the batched workload is batch_instances
+# below).  Sizes, operators, regularisers, lambda, sketch size and iteration
+# counts are the ones the reconstruction benchmark names.
 DEBLUR64 = Workload(
     name="deblur64_haar_f64", n=64, op="blur", reg="wavelet", lam=1e-3, ell=32,
     iters=100, dtype="f64", blur_k=9, blur_sigma=1.5, noise="gauss",
