@@ -11,7 +11,7 @@
  * Layout.     An image is n1 x n2, row-major (pixel (i, j) = row i, column j at
  *             offset i*n2 + j).  A batch of B images is B images back to back.
  *             An N x ell matrix (Omega, Y, U) is stored as ell images back to
- *             back ("each column of Omega represents an image", Sec. III-C):
+ *             back, since every probe column is itself an image (Sec. III-C):
  *             column j starts at offset j*N.
  * Types.      dtype NYS_F64 or NYS_F32 for images; the sketch may also use
  *             NYS_BF16 storage for Omega, Y and U (FP32 accumulation).
