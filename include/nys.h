@@ -23,7 +23,9 @@
  *             before a reserve may grow it once).
  * Errors.     Every function returns NYS_OK (0) or one of the codes below and
  *             records a message readable with nys_last_error().  No C++
- *             exception crosses this boundary.
+ *             exception crosses this boundary.  A NULL handle or required
+ *             pointer gives NYS_EINVAL before any device work; the
+ *             *_destroy / *_release functions accept NULL and do nothing.
  */
 #ifndef NYS_H
 #define NYS_H

@@ -47,3 +47,33 @@ def test_version_and_error_without_gpu(lib):
     assert isinstance(lib.nys_last_error(None), bytes)
     # invalid arguments are rejected before any CUDA call
     assert lib.nys_create(None, 0, None) == 1
+
+
+def _null_args(argtypes):
+    import ctypes as C
+    ints = (C.c_int, C.c_int32, C.c_int64, C.c_uint64, C.c_uint32, C.c_size_t)
+    return [0 if a in ints else 0.0 if a in (C.c_double, C.c_float) else None for a in argtypes]
+
+
+def test_null_handles_and_pointers_are_rejected_without_a_device_call(lib):
+    # every entry point checks its handles and pointers before touching the
+    # device: destroy/release of NULL is a no-op, everything else NYS_EINVAL
+    from paper_2411_08178_gb300 import _abi
+    for name, (_, argtypes) in _abi.PROTOTYPES.items():
+        if name in ("nys_version", "nys_last_error"):
+            continue
+        r = getattr(lib, name)(*_null_args(argtypes))
+        if name.endswith(("_destroy", "_release")) or name == "nys_destroy":
+            assert r == _abi.NYS_OK, name
+        else:
+            assert r == _abi.NYS_EINVAL, (name, r)
+        assert isinstance(lib.nys_last_error(None), bytes)
+
+
+def test_binding_rejects_host_and_strided_tensors():
+    import torch
+    from paper_2411_08178_gb300 import api
+    with pytest.raises(ValueError):
+        api._ptr(torch.zeros(4))
+    with pytest.raises(ValueError):
+        api.dtype_code(torch.zeros(4, dtype=torch.int32))
