@@ -110,11 +110,6 @@ __global__ void small_gemm_kernel(const double* __restrict__ A, int ta, const do
     if (i < m && j < n) C[(size_t)i * n + j] = acc * (colscale ? colscale[j] : 1.0);
 }
 
-template <class TS, class TD>
-__global__ void convert_kernel(const TS* __restrict__ in, TD* __restrict__ out, int n) {
-    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < n; t += gridDim.x * blockDim.x) out[t] = (TD)in[t];
-}
-
 template <class T>
 __global__ void copy_pad(const double* __restrict__ G, int ell, T* __restrict__ Gw, int n) {
     for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < ell * ell; t += gridDim.x * blockDim.x) {
