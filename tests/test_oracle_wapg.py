@@ -95,3 +95,53 @@ def test_dual_prox_wapg_same_minimiser(reg):
     assert np.linalg.norm(x_plain - x_prec) <= 1e-5 * np.linalg.norm(x_plain)
     # both lower the objective below that of the data itself
     assert prob.objective(x_prec) < prob.objective(y)
+
+
+def _huber_problem(delta, n=10, seed=4):
+    rng = np.random.default_rng(seed)
+    op = ops.Operator("blur_decim", n, n, kernel=gaussian_kernel(3, 1.0), decim=2)
+    y = op.apply(phantom(n, 3, seed, "mixed")) + rng.normal(0, 0.05, (n // 2, n // 2))
+    return wp.Problem(op, y, 0.0, "tv", fit="huber", huber_delta=delta), rng
+
+
+def test_huber_gradient_is_the_derivative_of_its_objective():
+    # lambda = 0 isolates the data term; central differences along random
+    # directions, with the residuals spread across both sides of delta
+    prob, rng = _huber_problem(0.03)
+    x = rng.uniform(0, 1, prob.shape)
+    r = np.abs(prob.op.apply(x) - prob.y)
+    assert (r <= 0.03).any() and (r > 0.03).any()
+    g = prob.grad_f(x)
+    for _ in range(5):
+        d = rng.standard_normal(prob.shape)
+        h = 1e-6
+        fd = (prob.objective(x + h * d) - prob.objective(x - h * d)) / (2 * h)
+        assert np.sum(g * d) == pytest.approx(fd, rel=1e-6, abs=1e-9)
+
+
+def test_huber_limits():
+    # delta above every residual: least squares; delta -> 0: h/delta -> |r|
+    prob, rng = _huber_problem(1e6)
+    x = rng.uniform(0, 1, prob.shape)
+    ls = wp.Problem(prob.op, prob.y, 0.0, "tv")
+    assert prob.objective(x) == pytest.approx(ls.objective(x), rel=1e-14)
+    assert np.allclose(prob.grad_f(x), ls.grad_f(x), rtol=1e-14, atol=0)
+    small, _ = _huber_problem(1e-9)
+    r = small.op.apply(x) - small.y
+    assert small.objective(x) / 1e-9 == pytest.approx(np.abs(r).sum(), rel=1e-6)
+
+
+def test_huber_objective_is_the_integral_of_its_gradient():
+    # F(x1) - F(x0) = int_0^1 <grad F(x0 + t (x1 - x0)), x1 - x0> dt along a
+    # path whose residuals cross delta: a jump between the quadratic and the
+    # linear branch (a wrong constant) breaks it
+    prob, rng = _huber_problem(0.03)
+    x0, x1 = rng.uniform(0, 1, prob.shape), rng.uniform(0, 1, prob.shape)
+    d = x1 - x0
+    t = np.linspace(0.0, 1.0, 4001)
+    vals = np.array([np.sum(prob.grad_f(x0 + s * d) * d) for s in t])
+    integral = np.sum(0.5 * (vals[1:] + vals[:-1]) * np.diff(t))
+    r0 = np.abs(prob.op.apply(x0) - prob.y)
+    r1 = np.abs(prob.op.apply(x1) - prob.y)
+    assert ((r0 <= 0.03) != (r1 <= 0.03)).any()
+    assert prob.objective(x1) - prob.objective(x0) == pytest.approx(integral, rel=1e-6)
