@@ -428,6 +428,10 @@ def run_native(args, w: WL.Workload):
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = oracle_sample(w, k_p_run, seconds_hint=args.cpu_seconds)
+        cpu["threads"] = ("numpy's elementwise work (operators, prox) runs on one thread; BLAS/LAPACK calls "
+                          "(the factor, the Gram products) use up to `cores` threads")
+        one = oracle_sample_one_thread(w, k_p_run)
+        cpu["single_core"] = {k: one[k] for k in ("value", "unit", "cores", "phase_s", "error") if k in one}
     out = {
         "metric": METRIC, "value": round(ms_p, 3), "unit": "ms", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": round(ms_p, 3), "higher_is_better": False, "scaling": "weak",
@@ -523,6 +527,26 @@ def oracle_sample(w: WL.Workload, k_iters: int, seconds_hint: float = 15.0):
                        f"scaled to ell columns + 50 power steps + {k_iters} iterations"),
             "phase_s": {"col": round(t_col, 3), "factor": round(t_factor, 3), "power": round(t_pow, 3),
                         "iteration": round(t_it, 3)}}
+
+
+def oracle_sample_one_thread(w: WL.Workload, k_iters: int) -> dict:
+    """The same oracle sample in a fresh interpreter whose BLAS and OpenMP
+    pools hold one thread (the pools are sized when numpy loads, so this needs
+    its own process; the interpreter is exec'd, nothing is forked)."""
+    import dataclasses
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
+    code = ("import json, sys, bench; w = bench.WL.Workload(**json.loads(sys.argv[1])); "
+            "print(json.dumps(bench.oracle_sample(w, int(sys.argv[2]))))")
+    try:
+        r = subprocess.run([sys.executable, "-c", code, json.dumps(dataclasses.asdict(w)), str(k_iters)], cwd=ROOT,
+                           env=env, capture_output=True, text=True, timeout=900)
+    except subprocess.TimeoutExpired:
+        return {"error": "timed out after 900 s"}
+    if r.returncode != 0:
+        return {"error": (r.stderr.strip().splitlines() or ["exit %d" % r.returncode])[-1]}
+    out = json.loads(r.stdout.strip().splitlines()[-1])
+    out["cores"] = 1
+    return out
 
 
 def run_reference(args, w: WL.Workload):

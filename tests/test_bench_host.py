@@ -1,0 +1,28 @@
+"""Host-side pieces of bench.py that need no GPU: the CPU-oracle baseline on a
+small copy of the deblurring workload, with all threads and with one."""
+import json
+import os
+import sys
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+sys.path.insert(0, ROOT)
+
+import bench  # noqa: E402
+
+
+def test_oracle_sample_scales_its_phases_to_the_solve():
+    w = bench.WL.scaled(bench.WL.DEBLUR512, 48, ell=6)
+    r = bench.oracle_sample(w, 7)
+    ph = r["phase_s"]
+    total = w.ell * ph["col"] + ph["factor"] + 50 * ph["power"] + 7 * ph["iteration"]
+    assert r["kind"] == "oracle" and r["unit"] == "ms" and r["cores"] >= 1
+    # phases are rounded to the millisecond in the report
+    assert abs(r["value"] - 1e3 * total) <= 1e3 * (w.ell + 1 + 50 + 7) * 5e-4 + 0.1
+    json.dumps(r)
+
+
+def test_one_thread_sample_runs_in_its_own_interpreter():
+    w = bench.WL.scaled(bench.WL.DEBLUR512, 48, ell=6)
+    r = bench.oracle_sample_one_thread(w, 7)
+    assert "error" not in r, r
+    assert r["cores"] == 1 and r["value"] > 0 and "48x48" in r["sample"]
