@@ -67,6 +67,13 @@ def max_over_ranks(values, world: int, device="cpu"):
     return [float(v) for v in t.cpu()]
 
 
+def step_stats(times_ms) -> dict:
+    """Mean, median and best of the timed steps of this rank (ms)."""
+    t = [float(v) for v in times_ms]
+    return {"mean": round(statistics.mean(t), 3), "median": round(statistics.median(t), 3),
+            "best": round(min(t), 3), "n": len(t)}
+
+
 # ------------------------------------------------------------ clocks ------
 class ClockSampler:
     Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
@@ -439,6 +446,7 @@ def run_native(args, w: WL.Workload):
         "config": {**describe(w), "sketch_dtype": args.sketch_dtype, "target_rel_err": TARGET,
                    "l2": "flushed between timed steps (256 MB write)", "parallelism": f"replicas x{world}"},
         "plain_ms": round(ms_0, 3), "speedup_vs_plain": round(ms_0 / ms_p, 3),
+        "step_ms_rank0": {"precond": step_stats(times_p), "plain": step_stats(times_0)},
         "criterion": "objective gap (F(x^k) - F*)/|F*| <= 1e-3, F* the best of the reference runs; the iterate error "
                      "||x^k - x*||/||x*|| is reported beside it (x* is not resolved to 1e-3 within the run, see "
                      "xstar.drift_last_quarter)",

@@ -26,3 +26,8 @@ def test_one_thread_sample_runs_in_its_own_interpreter():
     r = bench.oracle_sample_one_thread(w, 7)
     assert "error" not in r, r
     assert r["cores"] == 1 and r["value"] > 0 and "48x48" in r["sample"]
+
+
+def test_step_stats():
+    s = bench.step_stats([3.0, 1.0, 2.0, 10.0])
+    assert s == {"mean": 4.0, "median": 2.5, "best": 1.0, "n": 4}
