@@ -80,10 +80,11 @@ class ClockSampler:
          "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
          "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
-    def __init__(self, device: int):
+    def __init__(self, device: int, directory: str | None = None):
+        import tempfile
         self.device = device
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_bench_{device}.csv")
+        self.path = os.path.join(directory or tempfile.gettempdir(), f"clocks_bench_{device}.csv")
 
     def start(self):
         try:
@@ -104,9 +105,15 @@ class ClockSampler:
         except Exception:
             self.proc.kill()
         self.f.close()
+        return self.summarise(self.path)
+
+    @staticmethod
+    def summarise(path: str) -> dict:
+        """Median SM clock, maximum SM clock and the throttle reasons seen
+        in an nvidia-smi CSV log of the query Q."""
         sm, mx, reasons = [], [], set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for line in open(self.path):
+        for line in open(path):
             p = [t.strip() for t in line.split(",")]
             if len(p) < 9:
                 continue
@@ -398,7 +405,7 @@ def run_native(args, w: WL.Workload):
     k_0_run = k_0 or kmax
     # sketch-only time (Algorithm 1 end to end)
     sketch_ms = statistics.median(nb.time_loop(nb.sketch_factor, max(3, args.steps), 1, "timed_sketch"))
-    clocks = ClockSampler(local)
+    clocks = ClockSampler(local, args.clocks_dir)
     clocks.start()
     l0 = nb.ctx.launches()
     if world > 1:
@@ -597,6 +604,8 @@ def main():
     ap.add_argument("--kmax", type=int, default=8000)
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--clocks-dir", default=None,
+                    help="where the nvidia-smi clock log of the timed region is written (default: the temp dir)")
     args = ap.parse_args()
     w = WL.PRESETS[args.workload]
     if args.ell:

@@ -31,3 +31,18 @@ def test_one_thread_sample_runs_in_its_own_interpreter():
 def test_step_stats():
     s = bench.step_stats([3.0, 1.0, 2.0, 10.0])
     assert s == {"mean": 4.0, "median": 2.5, "best": 1.0, "n": 4}
+
+
+def test_clock_log_summary(tmp_path):
+    p = tmp_path / "clocks.csv"
+    rows = ["0, 2070, 2070, 900.5, 0x0, Not Active, Not Active, Not Active, Not Active",
+            "0, 1980, 2070, 1300.2, 0x4, Not Active, Not Active, Not Active, Active",
+            "0, 2070, 2070, 1100.0, 0x0, Not Active, Not Active, Not Active, Not Active",
+            "garbage line"]
+    p.write_text("\n".join(rows) + "\n")
+    s = bench.ClockSampler.summarise(str(p))
+    assert s == {"sm_mhz": 2070.0, "sm_max_mhz": 2070.0, "reasons": ["sw_power_cap"], "samples": 3}
+    # without nvidia-smi (or before start) the sampler reports itself unavailable
+    c = bench.ClockSampler(0, str(tmp_path))
+    assert c.path.startswith(str(tmp_path))
+    assert c.stop()["reasons"] == ["nvidia-smi unavailable"]
