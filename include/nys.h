@@ -223,7 +223,8 @@ int nys_precond_setup(nys_ctx* ctx, nys_precond* pc, double mu, int sqrt_shift);
  * inverse = 1: out = P^{-1} z = z - U M U^T z.  This is the second line of
  * Eq. (RYPreconditioner) when U^T U = I, and the exact inverse of P for the
  * stored U otherwise (Woodbury), so P P^{-1} = I also when U is stored in
- * BF16.  z, out: batch*N of `dtype` (NYS_F32/NYS_F64); out == z allowed. */
+ * BF16.  z, out: batch*N of `dtype` (NYS_F32/NYS_F64); out == z allowed;
+ * batch <= 65535 (NYS_EINVAL above). */
 int precond_apply(nys_ctx* ctx, const nys_precond* pc, int inverse, int dtype,
                   const void* z, void* out, int batch);
 

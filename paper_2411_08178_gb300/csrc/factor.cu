@@ -244,13 +244,13 @@ int precond_vec(nys_ctx* ctx, const nys_precond* pc, int inverse, const void* z,
     int groups = std::max(1, std::min(ell, (4 * ctx->sm_count + nchunk - 1) / nchunk));
     const int jper = (ell + groups - 1) / groups;
     groups = (ell + jper - 1) / jper;
+    if (batch > 65535) return fail(ctx, NYS_EINVAL, "precond: batch above 65535");
     int st;
     TA* part = (TA*)scratch(ctx, SLOT_PRECOND, ((size_t)batch * nchunk * ell + 2 * (size_t)batch * ell) * sizeof(TA), &st);
     if (st) return st;
     TA* coef = part + (size_t)batch * nchunk * ell;
     TA* wbuf = coef + (size_t)batch * ell;
     cudaStream_t s = ctx->stream;
-    if (batch > 65535) return fail(ctx, NYS_EINVAL, "precond: batch above 65535");
     NYS_CK(ctx, launch_pdl(utz_vec_kernel<TU, TZ, TA>, dim3(nchunk, groups, batch), 256, 0, s, (const TU*)pc->U,
                            (const TZ*)z, N, ell, jper, part));
     NYS_LAUNCH_CK(ctx);
