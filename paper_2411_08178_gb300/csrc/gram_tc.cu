@@ -33,6 +33,10 @@ constexpr int TC_BM = 128;
 constexpr int TC_BK = 64;           // bf16 elements per 128-byte swizzle row
 constexpr int TC_STAGES = 4;
 constexpr uint32_t WAIT_LIMIT = 1u << 24;   // try_wait polls before giving up
+// every TMA x coordinate below is a multiple of TC_BK (k blocks, padded
+// widths) or of 64 pixels (tile origins), so with bf16 it starts on a
+// 16-byte boundary as the tiled bulk copy requires
+static_assert(TC_BK % 8 == 0 && TC_BM % 64 == 0, "TMA x coordinates must be multiples of 8 bf16 values");
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
