@@ -145,3 +145,28 @@ def test_huber_objective_is_the_integral_of_its_gradient():
     r1 = np.abs(prob.op.apply(x1) - prob.y)
     assert ((r0 <= 0.03) != (r1 <= 0.03)).any()
     assert prob.objective(x1) - prob.objective(x0) == pytest.approx(integral, rel=1e-6)
+
+
+@pytest.mark.parametrize("sqrt_shift", [None, False, True])
+def test_power_lipschitz_is_the_largest_eigenvalue_of_pinv_phi(sqrt_shift):
+    # Algorithm 3's step size needs L_f^P = lambda_max(P^{-1} Phi).  Its
+    # eigenvalues are those of the pencil Phi v = lambda P v, solved here by a
+    # dense generalised symmetric eigensolver with P assembled column by column
+    # from P.apply (no use of P.inverse): the estimate must be 1.02 times the
+    # top one.  An estimate of P Phi (apply and inverse swapped) is 8-50 times
+    # off on this problem, and a missing safety factor 2 % off.
+    import scipy.linalg
+    n = 8
+    op = ops.Operator("blur", n, n, kernel=gaussian_kernel(5, 1.0))
+    prob = wp.Problem(op, op.apply(phantom(n, 3, 2, "mixed")), 1e-3, "tv")
+    dense = lambda f: np.array([f(e.reshape(n, n)).ravel() for e in np.eye(n * n)]).T
+    Phi = dense(prob.phi)
+    if sqrt_shift is None:
+        P, Pd = None, np.eye(n * n)
+    else:
+        P, _ = _precond_for(prob, 10, seed=5, sqrt_shift=sqrt_shift)
+        assert (P.d > 0).sum() >= 5
+        Pd = dense(P.apply)
+    lam_max = scipy.linalg.eigh(Phi, Pd, eigvals_only=True)[-1]
+    assert wp.power_lipschitz(prob, P, iters=1000) == pytest.approx(1.02 * lam_max, rel=1e-12)
+    assert wp.power_lipschitz(prob, P) == pytest.approx(1.02 * lam_max, rel=1e-4)
