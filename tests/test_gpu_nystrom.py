@@ -7,7 +7,7 @@ import oracle
 from oracle import operators as O
 from oracle.philox import gaussian_matrix
 from workloads import gaussian_kernel, gaussian_probe_like, phantom
-from tests.gpu_util import TOL, rel, require_gpu
+from tests.gpu_util import TOL, close, rel, require_gpu
 
 pytestmark = pytest.mark.gpu
 EPS64 = 2.0 ** -52
@@ -178,12 +178,12 @@ def test_precond_apply_matches_oracle(env, dt, sqrt_shift, mu):
     pc = api.Precond(ctx, n * n, ell, tdt).import_factor(ref["U"], ref["S_hat"], mu, sqrt_shift)
     z = gaussian_probe_like((3, n * n), seed=12)
     zg = torch.from_numpy(z).to(tdt).cuda()
-    assert rel(api.precond_apply(ctx, pc, zg, inverse=True).cpu(), P.inverse(z)) < TOL[dt]
-    assert rel(api.precond_apply(ctx, pc, zg, inverse=False).cpu(), P.apply(z)) < TOL[dt]
+    close(api.precond_apply(ctx, pc, zg, inverse=True).cpu(), P.inverse(z), TOL[dt])
+    close(api.precond_apply(ctx, pc, zg, inverse=False).cpu(), P.apply(z), TOL[dt])
     # P P^{-1} z = z on the device, in place
     w = api.precond_apply(ctx, pc, zg, inverse=True)
     api.precond_apply(ctx, pc, w, inverse=False, out=w)
-    assert rel(w.cpu(), z) < TOL[dt]
+    close(w.cpu(), z, TOL[dt])
 
 
 def test_precond_degenerate_is_reported(env):
@@ -221,12 +221,12 @@ def test_prox_dual_matches_oracle(env, dt, reg, precond, shape):
     fn = api.prox_tv if reg == "tv" else api.prox_hs
     x, Q = fn(ctx, pc, lb, n_inner, sg)
     tol = TOL[dt] * (10 if dt == "f32" else 1)
-    assert rel(x.cpu(), x_ref) < tol
-    assert rel(Q.cpu(), Q_ref) < tol * 10
+    close(x.cpu(), x_ref, tol, 10 * tol)
+    close(Q.cpu(), Q_ref, tol * 10, 100 * tol)
     # warm start continues the same sequence of Q (restart of t)
     x2, Q2 = fn(ctx, pc, lb, n_inner, sg, Q=Q)
     x2_ref, _ = oracle.prox.prox_dual(s, reg, lb, P, n_inner, Q0=Q_ref)
-    assert rel(x2.cpu(), x2_ref) < tol * 10
+    close(x2.cpu(), x2_ref, tol * 10, 100 * tol)
 
 
 @pytest.mark.parametrize("dt", ["f32", "f64"])
@@ -254,11 +254,11 @@ def test_prox_mixed_variants_match_oracle(env, dt, reg, precond, shape):
     sg = torch.from_numpy(s).to(tdt).cuda()
     x, Q = api.prox_mixed(ctx, pc, reg, lb, n_inner, sg)
     tol = TOL[dt] * (10 if dt == "f32" else 1)
-    assert rel(x.cpu(), x_ref) < tol
-    assert rel(Q.cpu(), Q_ref) < tol * 10
+    close(x.cpu(), x_ref, tol, 10 * tol)
+    close(Q.cpu(), Q_ref, tol * 10, 100 * tol)
     x2, _ = api.prox_mixed(ctx, pc, reg, lb, n_inner, sg, Q=Q)
     x2_ref, _ = oracle.prox.prox_dual(s, reg, lb, P, n_inner, Q0=Q_ref)
-    assert rel(x2.cpu(), x2_ref) < tol * 10
+    close(x2.cpu(), x2_ref, tol * 10, 100 * tol)
 
 
 def test_prox_mixed_rejects_wavelet(env):
@@ -295,8 +295,8 @@ def test_prox_tv_fused_dual_step_inner_counts(env, precond, n_inner):
     x_ref, Q_ref = oracle.prox.prox_dual(s, "tv", lb, P, n_inner, Q0=Q0)
     Qg = torch.from_numpy(Q0).cuda()
     x, Q = api.prox_tv(ctx, pc, lb, n_inner, torch.from_numpy(s).cuda(), Q=Qg)
-    assert rel(x.cpu(), x_ref) < 1e-12
-    assert rel(Q.cpu(), Q_ref) < 1e-12
+    close(x.cpu(), x_ref, 1e-12, 1e-11)
+    close(Q.cpu(), Q_ref, 1e-12, 1e-11)
     if n_inner == 0:
         assert torch.equal(Q.cpu(), torch.from_numpy(Q0))
 

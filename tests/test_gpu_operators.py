@@ -7,7 +7,7 @@ import pytest
 
 from oracle import operators as O
 from workloads import gaussian_kernel, gaussian_probe_like, random_kernel
-from tests.gpu_util import TOL, rel, require_gpu
+from tests.gpu_util import TOL, close, require_gpu
 
 pytestmark = pytest.mark.gpu
 
@@ -37,9 +37,9 @@ def test_blur_apply_adjoint_normal(env, dt, shape, kern):
     x = gaussian_probe_like((3, n1, n2), seed=5)
     xg = _t(torch, x, dt)
     tol = TOL[dt] * (3 if dt == "f32" else 1)
-    assert rel(api.op_apply(op, xg).cpu(), O.blur_apply(x, h)) < tol
-    assert rel(api.op_adjoint(op, xg).cpu(), O.blur_adjoint(x, h)) < tol
-    assert rel(api.op_normal(op, xg).cpu(), O.blur_adjoint(O.blur_apply(x, h), h)) < tol
+    close(api.op_apply(op, xg).cpu(), O.blur_apply(x, h), tol)
+    close(api.op_adjoint(op, xg).cpu(), O.blur_adjoint(x, h), tol)
+    close(api.op_normal(op, xg).cpu(), O.blur_adjoint(O.blur_apply(x, h), h), tol)
 
 
 @pytest.mark.parametrize("dt", ["f32", "f64"])
@@ -50,9 +50,9 @@ def test_decim_apply_adjoint_normal(env, dt):
     op = api.Operator(ctx, "blur_decim", n, n, dtype=getattr(torch, DT[dt]), kernel=h, decim=d)
     x = gaussian_probe_like((2, n, n), seed=6)
     yv = gaussian_probe_like((2, n // d, n // d), seed=7)
-    assert rel(api.op_apply(op, _t(torch, x, dt)).cpu(), O.decim_apply(x, h, d)) < TOL[dt]
-    assert rel(api.op_adjoint(op, _t(torch, yv, dt)).cpu(), O.decim_adjoint(yv, h, d)) < TOL[dt]
-    assert rel(api.op_normal(op, _t(torch, x, dt)).cpu(), O.decim_adjoint(O.decim_apply(x, h, d), h, d)) < TOL[dt]
+    close(api.op_apply(op, _t(torch, x, dt)).cpu(), O.decim_apply(x, h, d), TOL[dt])
+    close(api.op_adjoint(op, _t(torch, yv, dt)).cpu(), O.decim_adjoint(yv, h, d), TOL[dt])
+    close(api.op_normal(op, _t(torch, x, dt)).cpu(), O.decim_adjoint(O.decim_apply(x, h, d), h, d), TOL[dt])
 
 
 @pytest.mark.parametrize("dt", ["f32", "f64"])
@@ -64,8 +64,8 @@ def test_radon_apply_adjoint(env, dt, geom):
     x = gaussian_probe_like((2, n1, n2), seed=8)
     s = gaussian_probe_like((2, na, nb), seed=9)
     tol = 1e-5 if dt == "f32" else 1e-12
-    assert rel(api.op_apply(op, _t(torch, x, dt)).cpu(), O.radon_apply(x, na, nb)) < tol
-    assert rel(api.op_adjoint(op, _t(torch, s, dt)).cpu(), O.radon_adjoint(s, n1, n2)) < tol
+    close(api.op_apply(op, _t(torch, x, dt)).cpu(), O.radon_apply(x, na, nb), tol)
+    close(api.op_adjoint(op, _t(torch, s, dt)).cpu(), O.radon_adjoint(s, n1, n2), tol)
     # exact transposition on the device: <A x, s> = <x, A^T s>
     Ax = api.op_apply(op, _t(torch, x, dt)).double()
     Ats = api.op_adjoint(op, _t(torch, s, dt)).double()
@@ -83,9 +83,9 @@ def test_radon_batch_groups(env, dt):
     x = gaussian_probe_like((5, n1, n2), seed=18)
     s = gaussian_probe_like((5, na, nb), seed=19)
     tol = 1e-5 if dt == "f32" else 1e-12
-    assert rel(api.op_apply(op, _t(torch, x, dt)).cpu(), O.radon_apply(x, na, nb)) < tol
-    assert rel(api.op_adjoint(op, _t(torch, s, dt)).cpu(), O.radon_adjoint(s, n1, n2)) < tol
-    assert rel(api.op_normal(op, _t(torch, x, dt)).cpu(), O.radon_adjoint(O.radon_apply(x, na, nb), n1, n2)) < tol
+    close(api.op_apply(op, _t(torch, x, dt)).cpu(), O.radon_apply(x, na, nb), tol)
+    close(api.op_adjoint(op, _t(torch, s, dt)).cpu(), O.radon_adjoint(s, n1, n2), tol)
+    close(api.op_normal(op, _t(torch, x, dt)).cpu(), O.radon_adjoint(O.radon_apply(x, na, nb), n1, n2), tol)
 
 
 def test_radon_full_size_properties(env):
@@ -107,6 +107,30 @@ def test_radon_full_size_properties(env):
     assert abs(lhs - rhs) <= 1e-5 * np.linalg.norm(Ax) * np.linalg.norm(s)
 
 
+def test_radon_full_size_matches_oracle(env):
+    # the 512 x 512, 720-angle, 736-bin projector of the CT workload against
+    # the oracle's Joseph projector and its transpose, every angle and bin, in
+    # the launch configurations the sketch (a batch of images) and the solver
+    # (one image) use
+    torch, api, ctx = env
+    n, na, nb = 512, 720, 736
+    op = api.Operator(ctx, "radon", n, n, dtype=torch.float32, n_angles=na, n_bins=nb)
+    x = gaussian_probe_like((n, n), seed=22)
+    s = gaussian_probe_like((na, nb), seed=23)
+    ref_fwd = O.radon_apply(x, na, nb)
+    ref_adj = O.radon_adjoint(s, n, n)
+    close(api.op_apply(op, _t(torch, x, "f32")).cpu(), ref_fwd, 1e-5)
+    close(api.op_adjoint(op, _t(torch, s, "f32")).cpu(), ref_adj, 1e-5)
+    # the same image among five (the 4-images-per-CTA kernels and a remainder)
+    xb = np.stack([x, -x, 0.5 * x, x, 2.0 * x])
+    sb = np.stack([s, s, -s, 0.25 * s, s])
+    fb = api.op_apply(op, _t(torch, xb, "f32")).cpu().numpy()
+    ab = api.op_adjoint(op, _t(torch, sb, "f32")).cpu().numpy()
+    for b, (cx, cs) in enumerate(zip((1.0, -1.0, 0.5, 1.0, 2.0), (1.0, 1.0, -1.0, 0.25, 1.0))):
+        close(fb[b], cx * ref_fwd, 1e-5)
+        close(ab[b], cs * ref_adj, 1e-5)
+
+
 @pytest.mark.parametrize("dt", ["f32", "f64"])
 def test_haar_forward_inverse(env, dt):
     torch, api, ctx = env
@@ -115,9 +139,9 @@ def test_haar_forward_inverse(env, dt):
                       haar_levels=3)
     x = gaussian_probe_like((3, n, n), seed=10)
     w = api.op_haar(op, _t(torch, x, dt))
-    assert rel(w.cpu(), O.haar_forward(x, 3)) < TOL[dt]
-    assert rel(api.op_haar(op, _t(torch, x, dt), inverse=True).cpu(), O.haar_adjoint(x, 3)) < TOL[dt]
-    assert rel(api.op_haar(op, w, inverse=True).cpu(), x) < TOL[dt]
+    close(w.cpu(), O.haar_forward(x, 3), TOL[dt])
+    close(api.op_haar(op, _t(torch, x, dt), inverse=True).cpu(), O.haar_adjoint(x, 3), TOL[dt])
+    close(api.op_haar(op, w, inverse=True).cpu(), x, TOL[dt])
 
 
 @pytest.mark.parametrize("dt", ["f32", "f64"])
@@ -131,9 +155,9 @@ def test_daubechies4_forward_inverse(env, dt, shape, levels):
                       haar_levels=levels, wavelet="db4")
     x = gaussian_probe_like((2, n1, n2), seed=12)
     w = api.op_haar(op, _t(torch, x, dt))
-    assert rel(w.cpu(), O.wavelet_forward(x, levels, "db4")) < TOL[dt]
-    assert rel(api.op_haar(op, _t(torch, x, dt), inverse=True).cpu(), O.wavelet_adjoint(x, levels, "db4")) < TOL[dt]
-    assert rel(api.op_haar(op, w, inverse=True).cpu(), x) < TOL[dt]
+    close(w.cpu(), O.wavelet_forward(x, levels, "db4"), TOL[dt])
+    close(api.op_haar(op, _t(torch, x, dt), inverse=True).cpu(), O.wavelet_adjoint(x, levels, "db4"), TOL[dt])
+    close(api.op_haar(op, w, inverse=True).cpu(), x, TOL[dt])
 
 
 def test_unknown_wavelet_is_refused(env):
@@ -159,11 +183,11 @@ def test_fanbeam_matches_oracle(env, dt, n1, n2, A, B):
     x = gaussian_probe_like((2, n1, n2), seed=21)
     s = gaussian_probe_like((2, A, B), seed=22)
     ya = api.op_apply(op, _t(torch, x, dt))
-    assert rel(ya.cpu(), O.fanbeam_apply(x, A, B, R, D, du)) < TOL[dt]
+    close(ya.cpu(), O.fanbeam_apply(x, A, B, R, D, du), TOL[dt])
     xa = api.op_adjoint(op, _t(torch, s, dt))
-    assert rel(xa.cpu(), O.fanbeam_adjoint(s, n1, n2, R, D, du)) < TOL[dt]
+    close(xa.cpu(), O.fanbeam_adjoint(s, n1, n2, R, D, du), TOL[dt])
     xn = api.op_normal(op, _t(torch, x, dt))
-    assert rel(xn.cpu(), O.fanbeam_adjoint(O.fanbeam_apply(x, A, B, R, D, du), n1, n2, R, D, du)) < TOL[dt]
+    close(xn.cpu(), O.fanbeam_adjoint(O.fanbeam_apply(x, A, B, R, D, du), n1, n2, R, D, du), TOL[dt])
     lhs = float((ya.double().cpu() * torch.from_numpy(s)).sum())
     rhs = float((torch.from_numpy(x) * xa.double().cpu()).sum())
     assert lhs == pytest.approx(rhs, rel=1e-12 if dt == "f64" else 1e-5)
