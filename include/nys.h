@@ -20,7 +20,11 @@
  * Memory.     op_apply / op_adjoint / op_normal, precond_apply, prox_* and
  *             pgd_step never allocate: their scratch comes from the context
  *             workspace, which nys_reserve() sizes ahead of time (calls made
- *             before a reserve may grow it once).
+ *             before a reserve may grow it once).  Growing a region frees its
+ *             old buffer: the CUDA graphs that solvers and batches capture
+ *             are captured again before their next replay, but a graph the
+ *             caller captures itself must be captured again by the caller
+ *             (or the workspace reserved before capturing).
  * Errors.     Every function returns NYS_OK (0) or one of the codes below and
  *             records a message readable with nys_last_error().  No C++
  *             exception crosses this boundary.  A NULL handle or required
@@ -224,7 +228,7 @@ int nys_precond_setup(nys_ctx* ctx, nys_precond* pc, double mu, int sqrt_shift);
  * Eq. (RYPreconditioner) when U^T U = I, and the exact inverse of P for the
  * stored U otherwise (Woodbury), so P P^{-1} = I also when U is stored in
  * BF16.  z, out: batch*N of `dtype` (NYS_F32/NYS_F64); out == z allowed;
- * batch <= 65535 (NYS_EINVAL above). */
+ * batches above 65535 images run in chunks of 65535 (scratch for one chunk). */
 int precond_apply(nys_ctx* ctx, const nys_precond* pc, int inverse, int dtype,
                   const void* z, void* out, int batch);
 
@@ -232,12 +236,15 @@ int precond_apply(nys_ctx* ctx, const nys_precond* pc, int inverse, int dtype,
  * cudaMalloc is allowed on their side: e.g. while another component captures
  * the stream into a CUDA graph, or under a fixed memory budget).  The paper
  * has no counterpart; this is a deployment variant of precond_apply with the
- * same arguments and results.  Its scratch is one fixed device array of
- * NYS_NOALLOC_SCRATCH_BYTES (2 MiB) compiled into the library, which every
- * process that loads the library keeps on each GPU it uses until exit.
- * Limit: (ceil(N/1024) * ell + ell) values of the compute type (4 bytes for
- * f32/bf16 factors, 8 for f64) must fit, e.g. N = 512*512 with ell <= 2040 in
- * f32; larger problems get NYS_EINVAL (use precond_apply).  The call
+ * same arguments and results, computed by the plain kernels of
+ * precond_apply's general path (not its vectorised ones), one image of the
+ * batch at a time, over the active columns only.  Its scratch is one fixed
+ * device array of NYS_NOALLOC_SCRATCH_BYTES (2 MiB) compiled into the
+ * library, which every process that loads the library keeps on each GPU it
+ * uses until exit.  Limit: (ceil(N/1024) * ell_active + ell_active) values of
+ * the compute type (4 bytes for f32/bf16 factors, 8 for f64) must fit, e.g.
+ * N = 512*512 with ell_active <= 2040 in f32; larger problems get NYS_EINVAL
+ * (use precond_apply).  The call
  * allocates nothing.  Its first call on a device looks up the array's device
  * address (cudaGetSymbolAddress); make that first call before any stream
  * capture.  All calls share the one array: calls whose kernels overlap on the

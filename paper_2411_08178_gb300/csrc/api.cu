@@ -4,7 +4,9 @@
 #include <cmath>
 #include <cstdlib>
 #include <cstring>
+#include <map>
 #include <mutex>
+#include <utility>
 
 namespace {
 std::mutex g_err_mu;
@@ -46,6 +48,35 @@ int cuda_fail(nys_ctx* ctx, cudaError_t e, const char* what) {
                 cudaGetErrorString(e));
 }
 
+// The dynamic shared-memory opt-in is a property of a kernel on one device:
+// remember, per (kernel, device), the largest size granted so far, under a
+// lock, so that contexts on several devices (or several host threads) each
+// get their own opt-in before their first launch.
+int smem_optin(nys_ctx* ctx, const void* func, size_t bytes) {
+    if (bytes <= 48 * 1024) return NYS_OK;
+    static std::mutex mu;
+    static std::map<std::pair<const void*, int>, size_t> granted;
+    std::lock_guard<std::mutex> g(mu);
+    size_t& have = granted[{func, ctx ? ctx->device : 0}];
+    if (have >= bytes) return NYS_OK;
+    const cudaError_t e = cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaFuncSetAttribute(MaxDynamicSharedMemorySize)");
+    have = bytes;
+    return NYS_OK;
+}
+
+int l2_keep_cols(const nys_ctx* ctx, int64_t N, size_t es, int le) {
+    static const double frac = [] {
+        const char* e = getenv("NYS_L2_KEEP");
+        const double f = e ? atof(e) : 0.5;
+        return (f >= 0.0 && f <= 1.0) ? f : 0.5;
+    }();
+    if (le <= 0 || N <= 0) return 0;
+    const double budget = frac * (double)(ctx->l2_bytes > 0 ? ctx->l2_bytes : 0);
+    const double per_col = (double)N * (double)es;
+    return (int)std::min<double>((double)le, std::floor(budget / per_col));
+}
+
 int pdl_mode() {
     static const int m = [] {
         const char* e = getenv("NYS_PDL");
@@ -70,6 +101,7 @@ void* scratch(nys_ctx* ctx, int slot, size_t bytes, int* status) {
         cudaFree(ctx->slot_ptr[slot]);
         ctx->slot_ptr[slot] = nullptr;
         ctx->slot_bytes[slot] = 0;
+        ++ctx->scratch_gen;
     }
     size_t nb = (bytes + 4095) & ~size_t(4095);
     cudaError_t e = cudaMalloc(&ctx->slot_ptr[slot], nb);
@@ -154,6 +186,11 @@ int nys_create(nys_ctx** out, int device, void* stream) {
     c->device = device;
     c->stream = (cudaStream_t)stream;
     cudaDeviceGetAttribute(&c->sm_count, cudaDevAttrMultiProcessorCount, device);
+    {
+        int l2 = 0;
+        cudaDeviceGetAttribute(&l2, cudaDevAttrL2CacheSize, device);
+        c->l2_bytes = l2;
+    }
     // completion counters of the last-CTA reductions (zero between launches)
     e = cudaMalloc(&c->counters, 64 * sizeof(unsigned));
     if (e == cudaSuccess) e = cudaMemset(c->counters, 0, 64 * sizeof(unsigned));
@@ -304,6 +341,8 @@ int nys_op_set_kernel(nys_op* op, const double* kernel, int kh, int kw) {
         if (b) cudaFree(b);
     op->taps_fwd = op->taps_adj = op->taps_nrm = op->inter = nullptr;
     op->chunk = 0;
+    // graphs that captured the old tap tables must be captured again
+    ++op->ctx->scratch_gen;
     op->h.assign(kernel, kernel + (size_t)kh * kw);
     return blur_setup(op);
 }

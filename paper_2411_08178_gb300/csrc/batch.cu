@@ -26,6 +26,7 @@ struct nys_batch {
     cudaEvent_t fork = nullptr;
     cudaGraphExec_t g_fwd = nullptr, g_bwd = nullptr;
     bool fwd_done = false;
+    uint64_t gen = 0;   // sum of the item contexts' scratch generations at capture
 };
 
 namespace nys {
@@ -70,6 +71,33 @@ int capture(nys_batch* B, bool backward, cudaGraphExec_t* out) {
     const cudaError_t ei = cudaGraphInstantiate(out, g, 0);
     cudaGraphDestroy(g);
     if (ei != cudaSuccess) return cuda_fail(B->ctx, ei, "batch graph instantiate");
+    return NYS_OK;
+}
+
+// the graphs hold the addresses of the item contexts' scratch regions
+uint64_t scratch_gens(const nys_batch* B) {
+    uint64_t g = B->ctx->scratch_gen;
+    for (nys_ctx* c : B->item_ctx) g += c->scratch_gen;
+    return g;
+}
+
+// capture both graphs again if a scratch region they use was reallocated
+int refresh(nys_batch* B) {
+    if (B->gen == scratch_gens(B)) return NYS_OK;
+    for (nys_ctx* c : B->item_ctx) NYS_CK(B->ctx, cudaStreamSynchronize(c->stream));
+    NYS_CK(B->ctx, cudaStreamSynchronize(B->ctx->stream));
+    cudaGraphExec_t f = nullptr, b = nullptr;
+    int st = capture(B, false, &f);
+    if (!st) st = capture(B, true, &b);
+    if (st) {
+        if (f) cudaGraphExecDestroy(f);
+        return st;
+    }
+    cudaGraphExecDestroy(B->g_fwd);
+    cudaGraphExecDestroy(B->g_bwd);
+    B->g_fwd = f;
+    B->g_bwd = b;
+    B->gen = scratch_gens(B);
     return NYS_OK;
 }
 
@@ -120,6 +148,7 @@ int nys_batch_create(nys_ctx* ctx, int n, nys_unroll* const* items, nys_ctx* con
         if (cudaStreamSynchronize(B->item_ctx[i]->stream) != cudaSuccess) st = cuda_fail(ctx, cudaGetLastError(), "batch warm-up");
     if (!st) st = capture(B, false, &B->g_fwd);
     if (!st) st = capture(B, true, &B->g_bwd);
+    B->gen = scratch_gens(B);
     if (st) {
         nys_batch_destroy(B);
         return st;
@@ -130,6 +159,7 @@ int nys_batch_create(nys_ctx* ctx, int n, nys_unroll* const* items, nys_ctx* con
 
 int nys_batch_forward(nys_batch* B) {
     if (!B) return fail(nullptr, NYS_EINVAL, "null batch");
+    if (int st = refresh(B)) return st;
     NYS_CK(B->ctx, cudaGraphLaunch(B->g_fwd, B->ctx->stream));
     B->fwd_done = true;
     return NYS_OK;
@@ -138,6 +168,7 @@ int nys_batch_forward(nys_batch* B) {
 int nys_batch_backward(nys_batch* B) {
     if (!B) return fail(nullptr, NYS_EINVAL, "null batch");
     if (!B->fwd_done) return fail(B->ctx, NYS_EINVAL, "nys_batch_backward before nys_batch_forward");
+    if (int st = refresh(B)) return st;
     NYS_CK(B->ctx, cudaGraphLaunch(B->g_bwd, B->ctx->stream));
     return NYS_OK;
 }

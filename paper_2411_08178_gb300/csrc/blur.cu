@@ -222,11 +222,7 @@ int launch_sep(nys_op* op, const void* x, void* y, int batch, const void* taps, 
     const size_t sm = sep_smem<TC>(T, T, Lcp, Lrp);
     auto k = sepcorr_kernel<TI, TO, TC, T, T>;
     if (sm > 227 * 1024) return fail(op->ctx, NYS_EINVAL, "blur kernel too wide for the shared-memory tile");
-    static int attr_max = 48 * 1024;   // largest opt-in already granted to this instantiation
-    if ((int)sm > attr_max) {
-        NYS_CK(op->ctx, cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
-        attr_max = (int)sm;
-    }
+    if (int st = smem_optin(op->ctx, (const void*)k, sm)) return st;
     for (int b0 = 0; b0 < batch; b0 += 65535) {     // images in grid.z
         dim3 grid((op->n2 + T - 1) / T, (op->n1 + T - 1) / T, std::min(65535, batch - b0));
         NYS_CK(op->ctx, launch_pdl(k, grid, 256, sm, op->ctx->stream, (const TI*)x + (size_t)b0 * op->N,
@@ -242,11 +238,7 @@ int launch_c2d(nys_op* op, const void* x, void* y, int batch, const void* taps) 
     const size_t sm = c2d_smem<TC>(T, T, op->kh, kwp);
     auto k = corr2d_kernel<TI, TO, TC, T, T>;
     if (sm > 227 * 1024) return fail(op->ctx, NYS_EINVAL, "blur kernel too large for the shared-memory tile");
-    static int attr_max = 48 * 1024;
-    if ((int)sm > attr_max) {
-        NYS_CK(op->ctx, cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
-        attr_max = (int)sm;
-    }
+    if (int st = smem_optin(op->ctx, (const void*)k, sm)) return st;
     for (int b0 = 0; b0 < batch; b0 += 65535) {     // images in grid.z
         dim3 grid((op->n2 + T - 1) / T, (op->n1 + T - 1) / T, std::min(65535, batch - b0));
         NYS_CK(op->ctx, launch_pdl(k, grid, 256, sm, op->ctx->stream, (const TI*)x + (size_t)b0 * op->N,

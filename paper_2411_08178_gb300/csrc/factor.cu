@@ -122,10 +122,11 @@ __global__ void __launch_bounds__(256) utz_kernel(const TU* __restrict__ U, cons
     }
 }
 
-// coef[b][r] = inverse ? sum_k M[r][k] w[k] : d[r] w[r],  w = sum over partial blocks
+// coef[b][r] = inverse ? sum_k M[r][k] w[k] : d[r] w[r],  w = sum over partial
+// blocks; M has leading dimension ldm >= ell
 template <class TA, class TM>
-__global__ void __launch_bounds__(256) coef_kernel(const TA* __restrict__ part, int nb, int ell, int inverse,
-                                                   const TM* __restrict__ M, const TM* __restrict__ d,
+__global__ void __launch_bounds__(256) coef_kernel(const TA* __restrict__ part, int nb, int ell, int ldm,
+                                                   int inverse, const TM* __restrict__ M, const TM* __restrict__ d,
                                                    TA* __restrict__ coef) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     double* w = reinterpret_cast<double*>(smem_raw);
@@ -143,7 +144,7 @@ __global__ void __launch_bounds__(256) coef_kernel(const TA* __restrict__ part, 
         double s;
         if (inverse) {
             s = 0.0;
-            for (int k = lane; k < ell; k += 32) s += (double)M[(size_t)r * ell + k] * w[k];
+            for (int k = lane; k < ell; k += 32) s += (double)M[(size_t)r * ldm + k] * w[k];
             s = warp_sum(s);
         } else {
             s = (double)d[r] * w[r];
@@ -178,8 +179,9 @@ constexpr int VCH = 2048;    // pixels per partial-sum chunk
 // (column-major per batch image: a column's chunk sums are contiguous)
 template <class TU, class TZ, class TA>
 __global__ void __launch_bounds__(256) utz_vec_kernel(const TU* __restrict__ U, const TZ* __restrict__ z, int64_t N,
-                                                      int ell, int jper, TA* __restrict__ part) {
+                                                      int ell, int jper, TA* __restrict__ part, int keep) {
     pdl_enter();
+    const L2Pol l2p = make_l2_pol();
     constexpr int V = Vec16<TU>::n;
     __shared__ __align__(16) TA zs[VCH];
     const int64_t i0 = (int64_t)blockIdx.x * VCH;
@@ -192,6 +194,7 @@ __global__ void __launch_bounds__(256) utz_vec_kernel(const TU* __restrict__ U, 
     const int cnt = (int)(N - i0 < (int64_t)VCH ? N - i0 : (int64_t)VCH);   // multiple of V
     for (int j = j0 + warp; j < j1; j += 8) {
         const TU* uj = U + (size_t)j * N + i0;
+        const uint64_t pol = j < keep ? l2p.last : l2p.first;
         TA s = TA(0);
         if (cnt == VCH) {
             // full chunk: the trip count is a compile-time constant, so all of a
@@ -202,7 +205,7 @@ __global__ void __launch_bounds__(256) utz_vec_kernel(const TU* __restrict__ U, 
             for (int t0 = 0; t0 < T; t0 += G) {
                 TA u[G][V];
 #pragma unroll
-                for (int q = 0; q < G; ++q) load_vec<TU, TA, V>(uj + ((t0 + q) * 32 + lane) * V, u[q]);
+                for (int q = 0; q < G; ++q) load_vec_pol<TU, TA, V>(uj + ((t0 + q) * 32 + lane) * V, u[q], pol);
 #pragma unroll
                 for (int q = 0; q < G; ++q) {
                     const int t = ((t0 + q) * 32 + lane) * V;
@@ -218,7 +221,7 @@ __global__ void __launch_bounds__(256) utz_vec_kernel(const TU* __restrict__ U, 
         }
         for (int t = lane * V; t < cnt; t += 32 * V) {
             TA u[V], zv[V];
-            load_vec<TU, TA, V>(uj + t, u);
+            load_vec_pol<TU, TA, V>(uj + t, u, pol);
             lds_vec<TA, V>(zs + t, zv);
 #pragma unroll
             for (int k = 0; k < V; ++k) s = fma(u[k], zv[k], s);
@@ -251,8 +254,9 @@ int precond_vec(nys_ctx* ctx, const nys_precond* pc, int inverse, const void* z,
     TA* coef = part + (size_t)batch * nchunk * ell;
     TA* wbuf = coef + (size_t)batch * ell;
     cudaStream_t s = ctx->stream;
+    const int keep = l2_keep_cols(ctx, N, sizeof(TU), ell);
     NYS_CK(ctx, launch_pdl(utz_vec_kernel<TU, TZ, TA>, dim3(nchunk, groups, batch), 256, 0, s, (const TU*)pc->U,
-                           (const TZ*)z, N, ell, jper, part));
+                           (const TZ*)z, N, ell, jper, part, keep));
     NYS_LAUNCH_CK(ctx);
     using TM = typename std::conditional<sizeof(TA) == 8, double, float>::type;
     const TM* Mp = sizeof(TA) == 8 ? (const TM*)pv->M64 : (const TM*)pv->M32;
@@ -266,10 +270,10 @@ int precond_vec(nys_ctx* ctx, const nys_precond* pc, int inverse, const void* z,
     const dim3 grid((unsigned)((N + P - 1) / P), batch);
     if (pvx == 1)
         NYS_CK(ctx, launch_pdl(uc_vec_kernel<TU, TZ, TA>, grid, 256, sm, s, (const TU*)pc->U, (const TZ*)z, N, ell,
-                               coef, inverse ? TA(-1) : TA(1), (TZ*)out, (const TZ*)nullptr, TA(1)));
+                               coef, inverse ? TA(-1) : TA(1), (TZ*)out, (const TZ*)nullptr, TA(1), keep));
     else
         NYS_CK(ctx, launch_pdl(uc_vec_kernel<TU, TZ, TA, 2, 2>, grid, 256, sm, s, (const TU*)pc->U, (const TZ*)z, N,
-                               ell, coef, inverse ? TA(-1) : TA(1), (TZ*)out, (const TZ*)nullptr, TA(1)));
+                               ell, coef, inverse ? TA(-1) : TA(1), (TZ*)out, (const TZ*)nullptr, TA(1), keep));
     NYS_LAUNCH_CK(ctx);
     return NYS_OK;
 }
@@ -286,10 +290,13 @@ int precond_typed(nys_ctx* ctx, const nys_precond* pc, int inverse, const void* 
             return precond_vec<TU, TZ, TA>(ctx, pc, inverse, z, out, batch);
     }
     const int nb = (int)((N + PCH - 1) / PCH);
+    // chunks of at most 65535 images (grid.y) run one after another on the
+    // stream and reuse the same scratch
+    const size_t bmax = (size_t)std::min(batch, 65535);
     int st;
-    TA* part = (TA*)scratch(ctx, SLOT_PRECOND, ((size_t)batch * nb * ell + (size_t)batch * ell) * sizeof(TA), &st);
+    TA* part = (TA*)scratch(ctx, SLOT_PRECOND, (bmax * nb * ell + bmax * ell) * sizeof(TA), &st);
     if (st) return st;
-    TA* coef = part + (size_t)batch * nb * ell;
+    TA* coef = part + bmax * nb * ell;
     cudaStream_t s = ctx->stream;
     for (int b0 = 0; b0 < batch; b0 += 65535) {
         const int bb = std::min(65535, batch - b0);
@@ -298,10 +305,10 @@ int precond_typed(nys_ctx* ctx, const nys_precond* pc, int inverse, const void* 
         NYS_LAUNCH_CK(ctx);
         if (sizeof(TA) == 8)
             coef_kernel<TA, double><<<dim3((ell + 31) / 32, bb), 256, ell * sizeof(double), s>>>(
-                part, nb, ell, inverse, (const double*)pv->M64, (const double*)pv->d, coef);
+                part, nb, ell, ell, inverse, (const double*)pv->M64, (const double*)pv->d, coef);
         else
             coef_kernel<TA, float><<<dim3((ell + 31) / 32, bb), 256, ell * sizeof(double), s>>>(
-                part, nb, ell, inverse, (const float*)pv->M32, (const float*)pv->d32, coef);
+                part, nb, ell, ell, inverse, (const float*)pv->M32, (const float*)pv->d32, coef);
         NYS_LAUNCH_CK(ctx);
         const int gx = (int)std::min<int64_t>((N + 255) / 256, 4096);
         uc_kernel<TU, TZ, TA><<<dim3(gx, bb), 256, ell * sizeof(TA), s>>>(
@@ -568,12 +575,15 @@ int precond_apply(nys_ctx* ctx, const nys_precond* pc, int inverse, int dtype, c
 }  // extern "C"
 
 // ------------------------------------------- allocation-free P / P^{-1} ----
-// precond_apply_noalloc runs the same three kernels as precond_apply, but its
-// scratch (the per-block partial sums of U^T z and the ell coefficients) lives
-// in one file-scope device array instead of the context workspace, so the
-// call never allocates: for callers that must not call cudaMalloc (a stream
-// that is being captured into a CUDA graph by someone else, a real-time loop
-// with a fixed memory budget, a host that hands the library only its own
+// precond_apply_noalloc computes what precond_apply computes, with the plain
+// (unvectorised) kernels of precond_apply's general path -- per-block partial
+// sums of U^T z, the coefficient pass, then z + U c -- over the active columns
+// only (those with d_i > 0; M and d vanish outside them), one image at a
+// time.  Its scratch (the partial sums and the coefficients) lives in one
+// file-scope device array instead of the context workspace, so the call
+// never allocates: for callers that must not call cudaMalloc (a stream that
+// is being captured into a CUDA graph by someone else, a real-time loop with
+// a fixed memory budget, a host that hands the library only its own
 // buffers).  Every process that loads the library keeps this array on each
 // GPU it uses until it exits.
 static __device__ __align__(256) unsigned char g_noalloc_scratch[NYS_NOALLOC_SCRATCH_BYTES];
@@ -607,13 +617,19 @@ int precond_noalloc_typed(nys_ctx* ctx, const nys_precond* pc, int inverse, cons
                           void* scratch_dev) {
     const nys_precond_priv* pv = (const nys_precond_priv*)pc->priv;
     const int64_t N = pc->N;
-    const int ell = pc->ell;
+    const int ell = pv->ell_eff;   // active columns; M's leading dimension stays pc->ell
+    const int ldm = pc->ell;
     const int nb = (int)((N + PCH - 1) / PCH);
     const size_t need = ((size_t)nb * ell + (size_t)ell) * sizeof(TA);
     if (need > NYS_NOALLOC_SCRATCH_BYTES)
         return fail(ctx, NYS_EINVAL,
-                    "precond_apply_noalloc: needs %zu scratch bytes (ceil(N/%d) * ell + ell values) but the "
-                    "fixed array holds %d; use precond_apply", need, PCH, (int)NYS_NOALLOC_SCRATCH_BYTES);
+                    "precond_apply_noalloc: needs %zu scratch bytes (ceil(N/%d) * ell_active + ell_active values) "
+                    "but the fixed array holds %d; use precond_apply", need, PCH, (int)NYS_NOALLOC_SCRATCH_BYTES);
+    if (ell == 0) {   // P = I: a device-to-device copy (no allocation)
+        if (out != z) NYS_CK(ctx, cudaMemcpyAsync(out, z, (size_t)batch * N * sizeof(TZ), cudaMemcpyDeviceToDevice,
+                                                  ctx->stream));
+        return NYS_OK;
+    }
     // every partial and coefficient is written before it is read: nothing
     // has to be cleared between calls
     TA* part = (TA*)scratch_dev;
@@ -627,10 +643,10 @@ int precond_noalloc_typed(nys_ctx* ctx, const nys_precond* pc, int inverse, cons
         NYS_LAUNCH_CK(ctx);
         if (sizeof(TA) == 8)
             coef_kernel<TA, double><<<dim3((ell + 31) / 32, 1), 256, ell * sizeof(double), s>>>(
-                part, nb, ell, inverse, (const double*)pv->M64, (const double*)pv->d, coef);
+                part, nb, ell, ldm, inverse, (const double*)pv->M64, (const double*)pv->d, coef);
         else
             coef_kernel<TA, float><<<dim3((ell + 31) / 32, 1), 256, ell * sizeof(double), s>>>(
-                part, nb, ell, inverse, (const float*)pv->M32, (const float*)pv->d32, coef);
+                part, nb, ell, ldm, inverse, (const float*)pv->M32, (const float*)pv->d32, coef);
         NYS_LAUNCH_CK(ctx);
         uc_kernel<TU, TZ, TA><<<dim3(gx, 1), 256, ell * sizeof(TA), s>>>((const TU*)pc->U, zb, N, ell, coef,
                                                                         inverse ? TA(-1) : TA(1), ob);

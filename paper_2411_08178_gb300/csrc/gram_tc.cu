@@ -275,11 +275,7 @@ int gram_AtB_tc(nys_ctx* ctx, const void* A, int p, const void* B, int q, int64_
     int* err = (int*)scratch(ctx, SLOT_TCERR, 64, &st);
     if (st) return st;
     const size_t smem = 1024 + (size_t)TC_STAGES * (TC_BM * TC_BK * 2 + (size_t)BN * TC_BK * 2) + 256;
-    static size_t attr = 0;
-    if (smem > attr) {
-        NYS_CK(ctx, cudaFuncSetAttribute(gram_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        attr = smem;
-    }
+    if ((st = smem_optin(ctx, (const void*)gram_tc_kernel, smem))) return st;
     cudaStream_t s = ctx->stream;
     NYS_CK(ctx, cudaMemsetAsync(err, 0, sizeof(int), s));
     gram_tc_kernel<<<dim3(splits, mtiles), 256, smem, s>>>(mA, mB, p, q, BN, tmem_cols, kblocks, kper, part, err);
@@ -516,21 +512,11 @@ int gemm_tall_tc(nys_ctx* ctx, const void* Y, const void* Om, const double* v_de
     const size_t smem = 1024 + (size_t)nst * stage_bytes + 256;
     const unsigned mtiles = (unsigned)((N + TC_BM - 1) / TC_BM);
     if (out_dt == NYS_BF16) {
-        static size_t attr = 0;
-        if (smem > attr) {
-            NYS_CK(ctx, cudaFuncSetAttribute(tall_tc_kernel<__nv_bfloat16>,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-            attr = smem;
-        }
+        if (int st2 = smem_optin(ctx, (const void*)tall_tc_kernel<__nv_bfloat16>, smem)) return st2;
         tall_tc_kernel<__nv_bfloat16><<<mtiles, 256, smem, s>>>(mY, mO, mW, N, q, BN, tmem_cols, L1 / TC_BK,
                                                                  Kpad, nst, (__nv_bfloat16*)out, err);
     } else {
-        static size_t attr = 0;
-        if (smem > attr) {
-            NYS_CK(ctx, cudaFuncSetAttribute(tall_tc_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)smem));
-            attr = smem;
-        }
+        if (int st2 = smem_optin(ctx, (const void*)tall_tc_kernel<float>, smem)) return st2;
         tall_tc_kernel<float><<<mtiles, 256, smem, s>>>(mY, mO, mW, N, q, BN, tmem_cols, L1 / TC_BK, Kpad, nst, (float*)out,
                                                        err);
     }

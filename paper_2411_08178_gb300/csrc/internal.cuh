@@ -70,6 +70,7 @@ struct nys_ctx {
     int device = 0;
     cudaStream_t stream = nullptr;
     int sm_count = 152;
+    int64_t l2_bytes = 0;   // device L2 size (cudaDevAttrL2CacheSize)
     int64_t launches = 0;   // kernels launched through this context
     cudaStreamAttrValue l2_window = {};   // access-policy window set by nys_l2_persist
     bool l2_window_set = false;
@@ -82,6 +83,9 @@ struct nys_ctx {
     // independent growable scratch regions (see nys::scratch)
     void* slot_ptr[12] = {nullptr};
     size_t slot_bytes[12] = {0};
+    // incremented whenever a scratch region is reallocated: a CUDA graph that
+    // captured the old address must be captured again before it is replayed
+    uint64_t scratch_gen = 0;
 };
 
 struct nys_op {
@@ -122,6 +126,15 @@ void ctx_release(nys_ctx* ctx);
 // record an error on ctx (and globally) and return `code`
 int fail(nys_ctx* ctx, int code, const char* fmt, ...);
 int cuda_fail(nys_ctx* ctx, cudaError_t e, const char* what);
+// Number of leading active columns of U (N values of es bytes each) whose
+// loads carry the L2 evict_last priority, so that they stay in L2 between the
+// many P^{-1} applications of a solve while the other columns stream past
+// with evict_first: all le columns when U fits in the L2 budget (a fraction
+// of the L2 size, NYS_L2_KEEP, default 0.5), else as many as fit.
+int l2_keep_cols(const nys_ctx* ctx, int64_t N, size_t es, int le);
+// Opt `func` in to `bytes` of dynamic shared memory on ctx's device (the
+// current device), once per kernel and device; NYS_OK or NYS_ECUDA.
+int smem_optin(nys_ctx* ctx, const void* func, size_t bytes);
 
 // Scratch regions: each slot is an independent buffer that grows on demand.
 enum Slot {

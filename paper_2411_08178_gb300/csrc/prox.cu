@@ -402,11 +402,7 @@ int ssn_run(nys_ctx* ctx, const nys_precond* pc, double tau, int64_t N, const T*
     NYS_LAUNCH_CK(ctx);
     const T* U = (const T*)pc->U;
     const size_t esm = (size_t)(2 * SCH + 2 * ell) * sizeof(double) + (size_t)ell * (SCH + 1) * sizeof(float);
-    static int attr_max = 48 * 1024;
-    if ((int)esm > attr_max) {
-        NYS_CK(ctx, cudaFuncSetAttribute(ssn_eval_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)esm));
-        attr_max = (int)esm;
-    }
+    if (int st2 = smem_optin(ctx, (const void*)ssn_eval_kernel<T>, esm)) return st2;
     int launched = 0;
     const int max_evals = max_newton * 12 + 1;
     while (true) {

@@ -36,7 +36,7 @@ __global__ void __launch_bounds__(256) lt_utz_kernel(const T* __restrict__ R, in
                                                      const TU* __restrict__ U, int le, int ldm,
                                                      const TM* __restrict__ M, T* __restrict__ g,
                                                      TA* __restrict__ part, TA* __restrict__ coef,
-                                                     unsigned* __restrict__ counter, TvDual<T> dual) {
+                                                     unsigned* __restrict__ counter, TvDual<T> dual, int keep) {
     pdl_enter();
     static_assert(!DUAL || REG == NYS_REG_TV, "the fused dual step is for anisotropic TV");
     constexpr int V = Vec16<TU>::n;
@@ -69,18 +69,21 @@ __global__ void __launch_bounds__(256) lt_utz_kernel(const T* __restrict__ R, in
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int cnt = (int)(N - i0 < (int64_t)FCH ? N - i0 : (int64_t)FCH);   // multiple of V
     constexpr int T4 = FCH / (32 * V);
+    const L2Pol l2p = make_l2_pol();
     for (int j = warp; j < le; j += 16) {
         // columns j and j + 8 together: twice the 16-byte loads in flight
         const bool two = j + 8 < le;
         const TU* u0 = U + (size_t)j * N + i0;
         const TU* u1 = U + (size_t)(two ? j + 8 : j) * N + i0;
+        const uint64_t p0 = j < keep ? l2p.last : l2p.first;
+        const uint64_t p1 = (two ? j + 8 : j) < keep ? l2p.last : l2p.first;
         TA s0 = TA(0), s1 = TA(0);
         if (cnt == FCH) {
             TA a[T4][V], b[T4][V];
 #pragma unroll
             for (int q = 0; q < T4; ++q) {
-                load_vec<TU, TA, V>(u0 + (q * 32 + lane) * V, a[q]);
-                load_vec<TU, TA, V>(u1 + (q * 32 + lane) * V, b[q]);
+                load_vec_pol<TU, TA, V>(u0 + (q * 32 + lane) * V, a[q], p0);
+                load_vec_pol<TU, TA, V>(u1 + (q * 32 + lane) * V, b[q], p1);
             }
 #pragma unroll
             for (int q = 0; q < T4; ++q) {
@@ -95,8 +98,8 @@ __global__ void __launch_bounds__(256) lt_utz_kernel(const T* __restrict__ R, in
         } else {
             for (int t = lane * V; t < cnt; t += 32 * V) {
                 TA a[V], b[V], zv[V];
-                load_vec<TU, TA, V>(u0 + t, a);
-                load_vec<TU, TA, V>(u1 + t, b);
+                load_vec_pol<TU, TA, V>(u0 + t, a, p0);
+                load_vec_pol<TU, TA, V>(u1 + t, b, p1);
                 lds_vec<TA, V>(gs + t, zv);
 #pragma unroll
                 for (int k = 0; k < V; ++k) {
@@ -154,34 +157,35 @@ int fused_typed(nys_ctx* ctx, const nys_precond* pc, double lb, int n_inner, int
     const int dg = (int)std::min<int64_t>((N + 255) / 256, (int64_t)ctx->sm_count * 8);
     const TA step = (TA)(1.0 / (lb * normL2));
     unsigned* counter = ctx->counters + COUNTER_PROX;
+    const int keep = l2_keep_cols(ctx, N, sizeof(TU), le);
     // g = L^T Rin, or the fused TV dual step and the L^T after it (dual.x
     // set); then x (or out) = s - lb (g - U c), c = M U^T g
     auto xfn = [&](const T* Rin, const TvDual<T>& dual, T* dst) -> int {
         if (last) {
             if (dual.x)
                 NYS_CK(ctx, launch_pdl(lt_utz_kernel<TU, T, TA, TM, REG, true, FCH, TV>, nchunk, 256, lsm, sm, Rin,
-                                       n1, n2, (const TU*)pc->U, le, pc->ell, M, g, part, coef, counter, dual));
+                                       n1, n2, (const TU*)pc->U, le, pc->ell, M, g, part, coef, counter, dual, keep));
             else
                 NYS_CK(ctx, launch_pdl(lt_utz_kernel<TU, T, TA, TM, REG, true, FCH, false>, nchunk, 256, lsm, sm, Rin,
-                                       n1, n2, (const TU*)pc->U, le, pc->ell, M, g, part, coef, counter, dual));
+                                       n1, n2, (const TU*)pc->U, le, pc->ell, M, g, part, coef, counter, dual, keep));
             NYS_LAUNCH_CK(ctx);
         } else {
             if (dual.x)
                 NYS_CK(ctx, launch_pdl(lt_utz_kernel<TU, T, TA, TM, REG, false, FCH_WIDE, TV>, nchunk, 256, 16, sm,
-                                       Rin, n1, n2, (const TU*)pc->U, le, pc->ell, M, g, part, coef, counter, dual));
+                                       Rin, n1, n2, (const TU*)pc->U, le, pc->ell, M, g, part, coef, counter, dual, keep));
             else
                 NYS_CK(ctx, launch_pdl(lt_utz_kernel<TU, T, TA, TM, REG, false, FCH_WIDE, false>, nchunk, 256, 16, sm,
-                                       Rin, n1, n2, (const TU*)pc->U, le, pc->ell, M, g, part, coef, counter, dual));
+                                       Rin, n1, n2, (const TU*)pc->U, le, pc->ell, M, g, part, coef, counter, dual, keep));
             NYS_LAUNCH_CK(ctx);
             int st2 = coef_run<TA, TM>(ctx, part, nchunk, le, pc->ell, 1, M, (const TM*)nullptr, coef, 1, wbuf);
             if (st2) return st2;
         }
         if (pvx == 1)
             NYS_CK(ctx, launch_pdl(uc_vec_kernel<TU, T, TA>, dim3(ug, 1), 256, usm, sm, (const TU*)pc->U, g, N, le,
-                                   coef, TA(-1), dst, s, (TA)(-lb)));
+                                   coef, TA(-1), dst, s, (TA)(-lb), keep));
         else
             NYS_CK(ctx, launch_pdl(uc_vec_kernel<TU, T, TA, 2, 2>, dim3(ug, 1), 256, usm, sm, (const TU*)pc->U, g, N,
-                                   le, coef, TA(-1), dst, s, (TA)(-lb)));
+                                   le, coef, TA(-1), dst, s, (TA)(-lb), keep));
         NYS_LAUNCH_CK(ctx);
         return NYS_OK;
     };

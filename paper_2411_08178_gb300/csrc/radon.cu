@@ -569,12 +569,7 @@ void radon_adj_launch(nys_op* op, const TI* s, TO* x, int nb) {
     dim3 grid((op->n2 + ATS - 1) / ATS, (op->n1 + ATS - 1) / ATS, (nb + IB - 1) / IB);
     const size_t sm = adj3_smem<TC, IB, AK>(op->n_angles);
     // opt in to more than 48 KB of shared memory when the buffers need it
-    static size_t attr = 48 * 1024;
-    if (sm > attr) {
-        cudaFuncSetAttribute(radon_adj3_kernel<TI, TO, TC, IB, AK>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)sm);
-        attr = sm;
-    }
+    (void)smem_optin(op->ctx, (const void*)radon_adj3_kernel<TI, TO, TC, IB, AK>, sm);
     // a launch error is left for the caller's launch check (cudaGetLastError)
     (void)launch_pdl(radon_adj3_kernel<TI, TO, TC, IB, AK>, grid, 256, sm, op->ctx->stream, s, x, op->n1, op->n2,
                      op->n_angles, op->n_bins, nb, tables<TC>(op), (TC)((op->n1 - 1) / 2.0), (TC)((op->n2 - 1) / 2.0),

@@ -693,18 +693,8 @@ int sym_eig(nys_ctx* ctx, const double* G, int ell, bool use_f32, const double* 
         // instead (decided on the device) if that Cholesky fails
         int* status_dev = sweeps_dev + 2;
         if (in_smem) {
-            static size_t attr = 48 * 1024;
-            if (smem > attr) {
-                NYS_CK(ctx, cudaFuncSetAttribute(jacobi_smem_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                 (int)smem));
-                attr = smem;
-            }
-            static size_t attr1 = 48 * 1024;
-            if (smem1 > attr1) {
-                NYS_CK(ctx, cudaFuncSetAttribute(jacobi_1s_kernel<T, false>,
-                                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem1));
-                attr1 = smem1;
-            }
+            if (int st2 = smem_optin(ctx, (const void*)jacobi_smem_kernel<T>, smem)) return st2;
+            if (int st2 = smem_optin(ctx, (const void*)jacobi_1s_kernel<T, false>, smem1)) return st2;
             jacobi_1s_kernel<T, false><<<1, 1024, smem1, s>>>(Gw, nullptr, n, ell, max_sweeps, logpq, logcs,
                                                               rounds_dev, sweeps_dev, status_dev);
             NYS_LAUNCH_CK(ctx);
@@ -727,12 +717,7 @@ int sym_eig(nys_ctx* ctx, const double* G, int ell, bool use_f32, const double* 
         const size_t per_round = (size_t)h * (2 * sizeof(T) + sizeof(int2));
         const int rch = (int)std::max<size_t>(1, std::min<size_t>(32, (96 * 1024) / per_round));
         const size_t rsm = 8 * (size_t)n * sizeof(T) + (size_t)rch * per_round;
-        static size_t rattr = 48 * 1024;
-        if (rsm > rattr) {
-            NYS_CK(ctx, cudaFuncSetAttribute(rot_apply_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)rsm));
-            rattr = rsm;
-        }
+        if (int st2 = smem_optin(ctx, (const void*)rot_apply_kernel<T>, rsm)) return st2;
         rot_apply_kernel<T><<<(n + 7) / 8, 256, rsm, s>>>(logpq, logcs, rounds_dev, n, rch, V);
         NYS_LAUNCH_CK(ctx);
         if (!in_smem) {

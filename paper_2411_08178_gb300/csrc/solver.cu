@@ -54,6 +54,7 @@ struct nys_solver {
     cudaGraphExec_t gexec[2] = {nullptr, nullptr};
     int64_t glaunch[2] = {0, 0};
     bool gvalid = false;
+    uint64_t gen = 0;   // ctx->scratch_gen when the graphs were captured
 };
 
 namespace nys {
@@ -317,6 +318,7 @@ int capture(nys_solver* S) {
         ctx->launches = l0;
     }
     S->gvalid = true;
+    S->gen = ctx->scratch_gen;
     return NYS_OK;
 }
 
@@ -332,6 +334,9 @@ int iterate(nys_solver* S, int n_steps) {
         }
         return NYS_OK;
     }
+    // the graphs hold the addresses of the context's scratch regions: if any
+    // was reallocated since (by another object on this context), capture again
+    if (S->gen != ctx->scratch_gen) S->gvalid = false;
     if (!S->gvalid && (st = capture<T>(S))) return st;
     NYS_CK(ctx, cudaEventRecord(S->ev_in, ctx->stream));
     NYS_CK(ctx, cudaStreamWaitEvent(S->gs, S->ev_in, 0));

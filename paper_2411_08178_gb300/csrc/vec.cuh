@@ -38,6 +38,44 @@ __device__ __forceinline__ void load_vec<double, double, 2>(const double* p, dou
     v[0] = r.x, v[1] = r.y;
 }
 
+// L2 eviction priorities for loads of U (PTX createpolicy + ld.L2::cache_hint):
+// evict_last for the columns meant to stay in L2 across applications,
+// evict_first for the columns that stream through.
+struct L2Pol {
+    uint64_t last, first;
+};
+__device__ __forceinline__ L2Pol make_l2_pol() {
+    L2Pol p;
+    asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(p.last));
+    asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p.first));
+    return p;
+}
+template <class TU, class TA, int V>
+__device__ __forceinline__ void load_vec_pol(const TU* p, TA (&v)[V], uint64_t pol);
+template <>
+__device__ __forceinline__ void load_vec_pol<__nv_bfloat16, float, 8>(const __nv_bfloat16* p, float (&v)[8],
+                                                                     uint64_t pol) {
+    uint32_t w[4];
+    asm volatile("ld.global.nc.L2::cache_hint.v4.u32 {%0, %1, %2, %3}, [%4], %5;"
+                 : "=r"(w[0]), "=r"(w[1]), "=r"(w[2]), "=r"(w[3])
+                 : "l"(p), "l"(pol));
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        v[2 * k] = __uint_as_float(w[k] << 16);
+        v[2 * k + 1] = __uint_as_float(w[k] & 0xffff0000u);
+    }
+}
+template <>
+__device__ __forceinline__ void load_vec_pol<float, float, 4>(const float* p, float (&v)[4], uint64_t pol) {
+    asm volatile("ld.global.nc.L2::cache_hint.v4.f32 {%0, %1, %2, %3}, [%4], %5;"
+                 : "=f"(v[0]), "=f"(v[1]), "=f"(v[2]), "=f"(v[3])
+                 : "l"(p), "l"(pol));
+}
+template <>
+__device__ __forceinline__ void load_vec_pol<double, double, 2>(const double* p, double (&v)[2], uint64_t pol) {
+    asm volatile("ld.global.nc.L2::cache_hint.v2.f64 {%0, %1}, [%2], %3;" : "=d"(v[0]), "=d"(v[1]) : "l"(p), "l"(pol));
+}
+
 // 128-bit shared-memory loads of V compute-type values (V * sizeof(TA) is a
 // multiple of 16 bytes)
 template <class TA, int V>
@@ -233,9 +271,10 @@ __device__ __forceinline__ void last_cta_coef_t(const TA* partT, int le, int ldm
 template <class TU, class TZ, class TA, int NQ = 4, int PV = 1>
 __global__ void __launch_bounds__(256) uc_vec_kernel(const TU* __restrict__ U, const TZ* __restrict__ z, int64_t N,
                                                      int ell, const TA* __restrict__ coef, TA sign,
-                                                     TZ* __restrict__ out, const TZ* __restrict__ base = nullptr,
-                                                     TA scale = TA(1)) {
+                                                     TZ* __restrict__ out, const TZ* __restrict__ base, TA scale,
+                                                     int keep) {
     pdl_enter();
+    const L2Pol pol = make_l2_pol();
     constexpr int V = Vec16<TU>::n;
     constexpr int P = 32 * V * PV;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -262,7 +301,8 @@ __global__ void __launch_bounds__(256) uc_vec_kernel(const TU* __restrict__ U, c
 #pragma unroll
             for (int v = 0; v < PV; ++v) {
                 const int64_t i = (int64_t)blockIdx.x * P + (v * 32 + lane) * V;
-                if (jq < ell && i < N) load_vec<TU, TA, V>(U + (size_t)jq * N + i, u[q][v]);
+                if (jq < ell && i < N)
+                    load_vec_pol<TU, TA, V>(U + (size_t)jq * N + i, u[q][v], jq < keep ? pol.last : pol.first);
                 else
 #pragma unroll
                     for (int k = 0; k < V; ++k) u[q][v][k] = TA(0);

@@ -182,3 +182,34 @@ def test_end_to_end_gpu_sketch_reaches_same_minimiser(env):
     a.step(3000)
     b.step(3000)
     assert rel(a.x().cpu(), b.x().cpu()) < 1e-4
+
+
+def test_solver_graph_recaptured_after_workspace_growth(env):
+    # A float32 solver replays the CUDA graph of its iteration.  A float64
+    # solver created afterwards on the same context needs larger scratch
+    # regions (its dual variables and partial sums take twice the bytes), so
+    # the context reallocates them and frees the old ones.  The first solver
+    # must capture its graph again rather than replay the freed addresses: its
+    # iterates equal those of the same solver run alone on a fresh context.
+    torch, api, ctx = env
+    n, ell, lam = 64, 16, 5e-3
+    h, opo, prob, y, ref = _setup("blur", n, ell, 3, "tv", lam)
+    P = oracle.nystrom.Precond(ref["U"], ref["S_hat"])
+    alpha = 1.0 / oracle.wapg.power_lipschitz(prob, P)
+
+    def solver(c, dtype):
+        op = api.Operator(c, "blur", n, n, dtype=dtype, kernel=h)
+        pc = api.Precond(c, n * n, ell, dtype).import_factor(ref["U"], ref["S_hat"], 0.0, True)
+        return op, pc, api.Solver(c, op, torch.from_numpy(y).to(dtype).cuda(), "tv", lam, pc=pc, alpha=alpha,
+                                  n_inner=10)
+
+    fresh = api.Context(0)
+    ctx_a = api.Context(0)
+    keep_a = solver(ctx_a, torch.float32)
+    keep_a[2].step(4)
+    keep_b = solver(ctx_a, torch.float64)      # grows the shared workspace
+    keep_b[2].step(2)
+    keep_a[2].step(4)
+    keep_c = solver(fresh, torch.float32)
+    keep_c[2].step(8)
+    assert rel(keep_a[2].x().cpu(), keep_c[2].x().cpu()) < 1e-6

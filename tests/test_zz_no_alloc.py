@@ -55,12 +55,14 @@ def test_noalloc_rejects_problems_beyond_the_fixed_array():
     from paper_2411_08178_gb300 import _abi
     lib = _abi.load()
     ctx = api.Context(0)
-    # f64: ceil(N/1024) * ell + ell = 512 * 512 + 512 doubles > 2 MiB
+    # f64 with every column active (s_i > sqrt(s_K) = sqrt 2):
+    # ceil(N/1024) * ell_active + ell_active = 512 * 512 + 512 doubles > 2 MiB
     N, ell = 512 * 1024, 512
     pc = api.Precond(ctx, N, ell, torch.float64)
     pc.U.zero_()
-    pc.S_hat.copy_(torch.linspace(2.0, 1.0, ell, dtype=torch.float64))
+    pc.S_hat.copy_(torch.linspace(4.0, 2.0, ell, dtype=torch.float64))
     assert lib.nys_precond_import(ctx.h, C.byref(pc.s), 0.0, 1) == _abi.NYS_OK
+    assert pc.ell_active == ell
     z = torch.ones(N, dtype=torch.float64, device="cuda")
     out = torch.empty_like(z)
     assert _call(lib, ctx, pc, True, _abi.NYS_F64, z, out) == _abi.NYS_EINVAL
