@@ -176,6 +176,13 @@ int op_haar(nys_op* op, const void* in, void* out, int batch, int inverse);
  * FP32 and rounds its output). */
 int nys_sketch(nys_ctx* ctx, nys_op* op, int phi_kind, int ell, uint64_t seed,
                int store_dtype, void* Omega, void* Y);
+/* Columns j0 <= j < j1 of the same Omega (the values nys_sketch draws for
+ * them) and Y = Phi Omega for those columns only, (j1 - j0) x N each: the
+ * probe columns are independent (Sec. III-C), so ranks that share a sketch
+ * each draw and apply their own slice.  0 <= j0 < j1 <= ell, else
+ * NYS_EINVAL. */
+int nys_sketch_cols(nys_ctx* ctx, nys_op* op, int phi_kind, int ell, int j0, int j1, uint64_t seed,
+                    int store_dtype, void* Omega, void* Y);
 
 /* Nystrom factor U, S_hat (Algorithm 1 steps 3-8).  Caller-owned device
  * buffers: U (N x ell, dtype `dtype`: NYS_F32, NYS_F64 or NYS_BF16) and
@@ -209,6 +216,26 @@ typedef struct nys_precond {
 int nys_factor(nys_ctx* ctx, const void* Omega, const void* Y, int in_dtype,
                int64_t N, int ell, double eps, nys_precond* out);
 int nys_precond_release(nys_precond* pc);
+/* Algorithm 1 steps 3-8 at the ell x ell level, from the Gram G2 of
+ * [Omega | Y] (device, float64, 2 ell x 2 ell, row-major; only the blocks
+ * Omega^T Omega, Omega^T Y, Y^T Y are read): the shift v = eps sqrt(trace
+ * Omega^T Omega), the shifted Cholesky C of sym(Omega^T Y) + v Omega^T Omega
+ * (retries as nys_factor), the eigen-decomposition V S^2 V^T of
+ * C^{-1} Y_v^T Y_v C^{-T} = B^T B, S_hat (device, ell doubles, descending)
+ * and W = C^{-T} V S^{-1} (device, ell x ell float64, row-major), so that
+ * U = (Y + v Omega) W.  Ranks that each hold a slice of the pixels sum their
+ * partial Grams (nys_gram) and call this on the sum; each then forms its rows
+ * of U with nys_tall_gemm.  eig_f64 = 0 runs the rotations in float32 (as
+ * nys_factor does for float32 / bf16 sketches).  v, retries (host, may be
+ * NULL) receive the shift and the retry count.  Synchronises;
+ * NYS_ENOTSPD as nys_factor. */
+int nys_factor_gram(nys_ctx* ctx, const double* G2, int ell, double eps, int eig_f64, double* W,
+                    double* S_hat, double* v, int* retries);
+/* nys_precond_import with K = U^T U given (device, ell x ell float64) rather
+ * than computed from pc->U: for a factor whose U holds only this rank's rows
+ * (pc->N = local rows), K is the sum of the ranks' partial Grams.  Apply such
+ * a factor with precond_partial / precond_finish.  Synchronises. */
+int nys_precond_import_gram(nys_ctx* ctx, nys_precond* pc, const double* K, double mu, int sqrt_shift);
 /* Adopt a factor the caller wrote into pc->U and pc->S_hat (N, ell, dtype
  * set; e.g. a preconditioner saved earlier): computes U^T U of the stored U,
  * the host copies s_first / s_last, and runs nys_precond_setup(mu,
@@ -231,6 +258,18 @@ int nys_precond_setup(nys_ctx* ctx, nys_precond* pc, double mu, int sqrt_shift);
  * batches above 65535 images run in chunks of 65535 (scratch for one chunk). */
 int precond_apply(nys_ctx* ctx, const nys_precond* pc, int inverse, int dtype,
                   const void* z, void* out, int batch);
+
+/* precond_apply split in two for a factor whose U holds only this rank's
+ * rows (pixel-sharded problems): precond_partial writes w[b] = U_r^T z_r[b]
+ * (ell_active values per image, float64 for NYS_F64 data, float32
+ * otherwise, device); the ranks sum w (an all-reduce of ell_active values per
+ * image); precond_finish then writes out[b] = z[b] - U_r M w[b] (inverse = 1)
+ * or z[b] + U_r diag(d) w[b], the rows of P^{-1} z or P z held by this rank.
+ * Rows a multiple of the 16-byte vector width (8 bf16, 4 f32, 2 f64),
+ * buffers 16-byte aligned, 1 <= batch <= 65535; NYS_EINVAL otherwise. */
+int precond_partial(nys_ctx* ctx, const nys_precond* pc, int dtype, const void* z, void* w, int batch);
+int precond_finish(nys_ctx* ctx, const nys_precond* pc, int inverse, int dtype, const void* w, const void* z,
+                   void* out, int batch);
 
 /* precond_apply for callers that cannot allocate device memory (no
  * cudaMalloc is allowed on their side: e.g. while another component captures

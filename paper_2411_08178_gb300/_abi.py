@@ -90,6 +90,11 @@ PROTOTYPES = {
     "op_normal": (i32, [vp, vp, vp, i32]),
     "op_haar": (i32, [vp, vp, vp, i32, i32]),
     "nys_sketch": (i32, [vp, vp, i32, i32, C.c_uint64, i32, vp, vp]),
+    "nys_sketch_cols": (i32, [vp, vp, i32, i32, i32, i32, C.c_uint64, i32, vp, vp]),
+    "nys_factor_gram": (i32, [vp, vp, i32, f64, i32, vp, vp, C.POINTER(f64), C.POINTER(i32)]),
+    "nys_precond_import_gram": (i32, [vp, C.POINTER(nys_precond), vp, f64, i32]),
+    "precond_partial": (i32, [vp, C.POINTER(nys_precond), i32, vp, vp, i32]),
+    "precond_finish": (i32, [vp, C.POINTER(nys_precond), i32, i32, vp, vp, vp, i32]),
     "nys_factor": (i32, [vp, vp, vp, i32, i64, i32, f64, C.POINTER(nys_precond)]),
     "nys_precond_release": (i32, [C.POINTER(nys_precond)]),
     "nys_precond_setup": (i32, [vp, C.POINTER(nys_precond), f64, i32]),

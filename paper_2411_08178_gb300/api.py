@@ -220,6 +220,34 @@ def nys_sketch(ctx: Context, op: Operator, ell: int, seed: int, phi: str = "ata"
     return Om, Y
 
 
+def nys_sketch_cols(ctx: Context, op: Operator, ell: int, j0: int, j1: int, seed: int, phi: str = "ata",
+                    store_dtype=None) -> tuple[torch.Tensor, torch.Tensor]:
+    """Columns j0..j1-1 of the ell-column Omega of nys_sketch and Y = Phi Omega
+    for them: (Omega_cols, Y_cols), each (j1 - j0, n1, n2)."""
+    sd = store_dtype or op.dtype
+    dev = torch.device("cuda", ctx.device)
+    Om = torch.empty((j1 - j0, op.n1, op.n2), dtype=sd, device=dev)
+    Y = torch.empty_like(Om)
+    kind = {"ata": A.NYS_PHI_ATA, "w_ata_wt": A.NYS_PHI_W_ATA_WT}[phi]
+    check(_lib().nys_sketch_cols(ctx.h, op.h, kind, ell, j0, j1, seed, _DT[sd], _ptr(Om), _ptr(Y)), ctx.h)
+    return Om, Y
+
+
+def nys_factor_gram(ctx: Context, G2: torch.Tensor, ell: int, eps: float, eig_f64: bool = False):
+    """Algorithm 1 steps 3-8 at the ell x ell level from the Gram of [Omega | Y]
+    (float64 (2 ell, 2 ell) device tensor): returns (W, S_hat, v, retries)
+    with U = (Y + v Omega) W."""
+    if G2.dtype != torch.float64 or G2.shape != (2 * ell, 2 * ell):
+        raise ValueError("nys_factor_gram: G2 must be float64 (2 ell, 2 ell)")
+    W = torch.empty((ell, ell), dtype=torch.float64, device=G2.device)
+    S = torch.empty((ell,), dtype=torch.float64, device=G2.device)
+    v = C.c_double()
+    r = C.c_int()
+    check(_lib().nys_factor_gram(ctx.h, _ptr(G2.contiguous()), ell, eps, int(eig_f64), _ptr(W), _ptr(S), C.byref(v),
+                                 C.byref(r)), ctx.h)
+    return W, S, v.value, r.value
+
+
 class Precond:
     """nys_precond with caller-owned U (ell, N) and S_hat (ell,) tensors."""
 
@@ -259,6 +287,15 @@ class Precond:
         check(_lib().nys_precond_import(self.ctx.h, C.byref(self.s), mu, int(sqrt_shift)), self.ctx.h)
         return self
 
+    def import_gram(self, U, S_hat, K: torch.Tensor, mu: float = 0.0, sqrt_shift: bool = True):
+        """Adopt this rank's rows U (ell, N_local) of a pixel-sharded factor, with
+        K = U^T U summed over the ranks (float64 (ell, ell) device tensor)."""
+        self.U.copy_(torch.as_tensor(U).reshape(self.U.shape).to(self.U.dtype))
+        self.S_hat.copy_(torch.as_tensor(S_hat).reshape(self.S_hat.shape).to(torch.float64))
+        check(_lib().nys_precond_import_gram(self.ctx.h, C.byref(self.s), _ptr(K.contiguous()), mu, int(sqrt_shift)),
+              self.ctx.h)
+        return self
+
     def close(self):
         if getattr(self, "s", None) is not None and self.s.priv:
             _lib().nys_precond_release(C.byref(self.s))
@@ -290,6 +327,26 @@ def precond_apply(ctx: Context, pc: Precond, z: torch.Tensor, inverse: bool = Tr
     if out is None:
         out = torch.empty_like(z)
     check(_lib().precond_apply(ctx.h, C.byref(pc.s), int(inverse), dtype_code(z), _ptr(z), _ptr(out), b), ctx.h)
+    return out
+
+
+def precond_partial(ctx: Context, pc: Precond, z: torch.Tensor) -> torch.Tensor:
+    """w = U_r^T z_r for this rank's rows (batch, ell_active); the ranks sum w."""
+    b = _batch(z, pc.s.N)
+    wdt = torch.float64 if z.dtype == torch.float64 else torch.float32
+    w = torch.empty((b, max(pc.ell_active, 1)), dtype=wdt, device=z.device)
+    check(_lib().precond_partial(ctx.h, C.byref(pc.s), dtype_code(z), _ptr(z), _ptr(w), b), ctx.h)
+    return w
+
+
+def precond_finish(ctx: Context, pc: Precond, w: torch.Tensor, z: torch.Tensor, inverse: bool = True,
+                   out: torch.Tensor | None = None) -> torch.Tensor:
+    """This rank's rows of P^{-1} z (or P z) from the summed w."""
+    b = _batch(z, pc.s.N)
+    if out is None:
+        out = torch.empty_like(z)
+    check(_lib().precond_finish(ctx.h, C.byref(pc.s), int(inverse), dtype_code(z), _ptr(w.contiguous()), _ptr(z),
+                                _ptr(out), b), ctx.h)
     return out
 
 

@@ -25,6 +25,58 @@ namespace {
 
 constexpr int RB = 8;  // register block (outputs per thread along a pass)
 
+// Stage rows x cols input values starting at (r0, c0) (periodic) into a
+// shared-memory tile of pitch `pitch`: one warp per row, lanes along the row.
+// The wrap is one conditional step when the staged extent fits in the image
+// (no integer division per element); small images take the modulo.
+template <class TI, class TC>
+__device__ __forceinline__ void stage_tile(const TI* __restrict__ xb, int n1, int n2, int r0, int c0, int rows,
+                                           int cols, TC* __restrict__ s, int pitch) {
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+    const bool step = r0 >= -n1 && r0 + rows <= 2 * n1 && c0 >= -n2 && c0 + cols <= 2 * n2;
+    constexpr int MQ = 4;   // rows of up to 128 columns: every load of two rows issued before any store
+    if (step && cols <= 32 * MQ) {
+        for (int ra = warp; ra < rows; ra += 2 * nw) {
+            TC v[2][MQ];
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const int r = ra + h * nw;
+                int gi = r0 + r;
+                gi = gi < 0 ? gi + n1 : (gi >= n1 ? gi - n1 : gi);
+                const TI* xr = xb + (size_t)gi * n2;
+#pragma unroll
+                for (int q = 0; q < MQ; ++q) {
+                    const int c = lane + 32 * q;
+                    int gj = c0 + c;
+                    gj = gj < 0 ? gj + n2 : (gj >= n2 ? gj - n2 : gj);
+                    v[h][q] = (r < rows && c < cols) ? (TC)ldf(xr + gj) : TC(0);
+                }
+            }
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const int r = ra + h * nw;
+#pragma unroll
+                for (int q = 0; q < MQ; ++q) {
+                    const int c = lane + 32 * q;
+                    if (r < rows && c < cols) s[(size_t)r * pitch + c] = v[h][q];
+                }
+            }
+        }
+        return;
+    }
+    for (int r = warp; r < rows; r += nw) {
+        int gi = r0 + r;
+        gi = step ? (gi < 0 ? gi + n1 : (gi >= n1 ? gi - n1 : gi)) : pmod(gi, n1);
+        const TI* xr = xb + (size_t)gi * n2;
+        TC* sr = s + (size_t)r * pitch;
+        for (int c = lane; c < cols; c += 32) {
+            int gj = c0 + c;
+            gj = step ? (gj < 0 ? gj + n2 : (gj >= n2 ? gj - n2 : gj)) : pmod(gj, n2);
+            sr[c] = (TC)ldf(xr + gj);
+        }
+    }
+}
+
 __host__ __device__ inline int round8(int x) { return (x + 7) & ~7; }
 __host__ __device__ inline int odd_pitch(int x) { return x | 1; }
 
@@ -73,11 +125,7 @@ __global__ void __launch_bounds__(256) sepcorr_kernel(const TI* __restrict__ x, 
     const size_t img = (size_t)blockIdx.z * n1 * n2;
     const TI* xb = x + img;
     for (int t = threadIdx.x; t < Lcp + Lrp; t += blockDim.x) s_tap[t] = taps[t];
-    for (int idx = threadIdx.x; idx < rows * wcols; idx += blockDim.x) {
-        const int r = idx / wcols, c = idx - r * wcols;
-        const int gi = pmod(i0 - cc + r, n1), gj = pmod(j0 - cr + c, n2);
-        s_in[r * pin + c] = (TC)ldf(xb + (size_t)gi * n2 + gj);
-    }
+    stage_tile<TI, TC>(xb, n1, n2, i0 - cc, j0 - cr, rows, wcols, s_in, pin);
     __syncthreads();
     // row pass: s_mid[r][c] = sum_b gr[b] s_in[r][c + b]
     const TC* gr = s_tap + Lcp;
@@ -127,11 +175,7 @@ __global__ void __launch_bounds__(256) corr2d_kernel(const TI* __restrict__ x, T
     const size_t img = (size_t)blockIdx.z * n1 * n2;
     const TI* xb = x + img;
     for (int t = threadIdx.x; t < kh * kwp; t += blockDim.x) s_tap[t] = taps[t];
-    for (int idx = threadIdx.x; idx < rows * wcols; idx += blockDim.x) {
-        const int r = idx / wcols, c = idx - r * wcols;
-        const int gi = pmod(i0 - ch + r, n1), gj = pmod(j0 - cw + c, n2);
-        s_in[r * pin + c] = (TC)ldf(xb + (size_t)gi * n2 + gj);
-    }
+    stage_tile<TI, TC>(xb, n1, n2, i0 - ch, j0 - cw, rows, wcols, s_in, pin);
     __syncthreads();
     TO* yb = y + img;
     for (int idx = threadIdx.x; idx < TY * (TX / RB); idx += blockDim.x) {

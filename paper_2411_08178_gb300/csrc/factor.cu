@@ -82,11 +82,14 @@ __device__ __forceinline__ void box_muller(uint32_t a, uint32_t b, double& z0, d
     z1 = rho * s;
 }
 
+// out[e - first] for first <= e < first + total: element e of the generator's
+// stream (Philox block e / 4, entry e mod 4)
 template <class T, class TC>
-__global__ void omega_kernel(T* __restrict__ out, int64_t total, uint64_t seed) {
-    const int64_t nblk = (total + 3) / 4;
+__global__ void omega_kernel(T* __restrict__ out, int64_t first, int64_t total, uint64_t seed) {
+    const int64_t b0 = first / 4, b1 = (first + total + 3) / 4;
     const uint32_t k0 = (uint32_t)(seed & 0xffffffffu), k1 = (uint32_t)(seed >> 32);
-    for (int64_t b = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; b < nblk; b += (int64_t)gridDim.x * blockDim.x) {
+    for (int64_t b = b0 + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; b < b1;
+         b += (int64_t)gridDim.x * blockDim.x) {
         const P4 x = philox4x32_10(P4{(uint32_t)(b & 0xffffffffu), (uint32_t)((uint64_t)b >> 32), 0u, 0u}, k0, k1);
         TC z[4];
         box_muller(x.x, x.y, z[0], z[1]);
@@ -94,7 +97,7 @@ __global__ void omega_kernel(T* __restrict__ out, int64_t total, uint64_t seed) 
         const int64_t e0 = 4 * b;
 #pragma unroll
         for (int r = 0; r < 4; ++r)
-            if (e0 + r < total) stf(out + e0 + r, z[r]);
+            if (e0 + r >= first && e0 + r < first + total) stf(out + (e0 + r - first), z[r]);
     }
 }
 
@@ -278,6 +281,64 @@ int precond_vec(nys_ctx* ctx, const nys_precond* pc, int inverse, const void* z,
     return NYS_OK;
 }
 
+// The two halves of the apply for a factor whose U holds only this rank's
+// rows of a pixel-sharded problem (the ranks sum w between them):
+//   partial:  w[b][j] = sum over the local rows of U[j][i] z[b][i]  (j < ell_active)
+//   finish:   out[b] = z[b] -/+ U coef(w[b])  (coef = M w or d .* w)
+template <class TU, class TZ, class TA>
+int precond_partial_typed(nys_ctx* ctx, const nys_precond* pc, const void* z, TA* w, int batch) {
+    const nys_precond_priv* pv = (const nys_precond_priv*)pc->priv;
+    const int64_t N = pc->N;
+    const int ell = pv->ell_eff;
+    if (ell == 0) return NYS_OK;
+    const int nchunk = (int)((N + VCH - 1) / VCH);
+    int groups = std::max(1, std::min(ell, (4 * ctx->sm_count + nchunk - 1) / nchunk));
+    const int jper = (ell + groups - 1) / groups;
+    groups = (ell + jper - 1) / jper;
+    int st;
+    TA* part = (TA*)scratch(ctx, SLOT_PRECOND, (size_t)batch * nchunk * ell * sizeof(TA), &st);
+    if (st) return st;
+    cudaStream_t s = ctx->stream;
+    const int keep = l2_keep_cols(ctx, N, sizeof(TU), ell);
+    NYS_CK(ctx, launch_pdl(utz_vec_kernel<TU, TZ, TA>, dim3(nchunk, groups, batch), 256, 0, s, (const TU*)pc->U,
+                           (const TZ*)z, N, ell, jper, part, keep));
+    NYS_LAUNCH_CK(ctx);
+    NYS_CK(ctx, launch_pdl(reduce_cols_kernel<TA>, dim3((ell + 7) / 8, batch), 256, 0, s, part, nchunk, ell, w));
+    NYS_LAUNCH_CK(ctx);
+    return NYS_OK;
+}
+
+template <class TU, class TZ, class TA>
+int precond_finish_typed(nys_ctx* ctx, const nys_precond* pc, int inverse, const TA* w, const void* z, void* out,
+                         int batch) {
+    constexpr int V = Vec16<TU>::n;
+    const nys_precond_priv* pv = (const nys_precond_priv*)pc->priv;
+    const int64_t N = pc->N;
+    const int ell = pv->ell_eff;
+    cudaStream_t s = ctx->stream;
+    if (ell == 0) {
+        if (out != z) NYS_CK(ctx, cudaMemcpyAsync(out, z, (size_t)batch * N * sizeof(TZ), cudaMemcpyDeviceToDevice, s));
+        return NYS_OK;
+    }
+    int st;
+    TA* coef = (TA*)scratch(ctx, SLOT_MISC, (size_t)batch * ell * sizeof(TA) + 64, &st);
+    if (st) return st;
+    using TM = typename std::conditional<sizeof(TA) == 8, double, float>::type;
+    const TM* Mp = sizeof(TA) == 8 ? (const TM*)pv->M64 : (const TM*)pv->M32;
+    const TM* dp = sizeof(TA) == 8 ? (const TM*)pv->d : (const TM*)pv->d32;
+    NYS_CK(ctx, launch_pdl(mw_kernel<TA, TM>, dim3((ell + 7) / 8, batch), 256, ell * sizeof(TA), s, Mp, pc->ell, inverse,
+                           dp, w, ell, coef));
+    NYS_LAUNCH_CK(ctx);
+    const int keep = l2_keep_cols(ctx, N, sizeof(TU), ell);
+    const int P = 32 * V * 2;
+    const size_t sm = (((size_t)ell + 3) & ~size_t(3)) * sizeof(TA) + (size_t)8 * P * sizeof(TA);
+    NYS_CK(ctx, launch_pdl(uc_vec_kernel<TU, TZ, TA, 2, 2>, dim3((unsigned)((N + P - 1) / P), batch), 256, sm, s,
+                           (const TU*)pc->U, (const TZ*)z, N, ell, coef, inverse ? TA(-1) : TA(1), (TZ*)out,
+                           (const TZ*)nullptr, TA(1), keep));
+    NYS_LAUNCH_CK(ctx);
+    return NYS_OK;
+}
+
 template <class TU, class TZ, class TA>
 int precond_typed(nys_ctx* ctx, const nys_precond* pc, int inverse, const void* z, void* out, int batch) {
     const nys_precond_priv* pv = (const nys_precond_priv*)pc->priv;
@@ -349,9 +410,14 @@ int precond_setup_impl(nys_ctx* ctx, nys_precond* pc, double mu, int sqrt_shift)
         // (I + Ubar^T Ubar)^{-1} on the active block only (Ubar's other columns are 0)
         form_A_kernel<<<64, 256, 0, s>>>(pv->K, ell, pv->sqrtd, eff, A);
         NYS_LAUNCH_CK(ctx);
-        chol_kernel<<<1, 1024, 0, s>>>(A, eff, info);
-        NYS_LAUNCH_CK(ctx);
-        tri_inv_kernel<<<eff, 32, 0, s>>>(A, Li, eff);
+        st = chol_cluster(ctx, A, eff, eff, 0, 0.0, 0, A, info, 3);
+        if (st == NYS_EINVAL) {
+            chol_kernel<<<1, 1024, 0, s>>>(A, eff, info);
+            NYS_LAUNCH_CK(ctx);
+        } else if (st) {
+            return st;
+        }
+        tri_inv_kernel<<<eff, 32, eff * sizeof(double), s>>>(A, Li, eff);
         NYS_LAUNCH_CK(ctx);
         // (I + Ubar^T Ubar)^{-1} = L^{-T} L^{-1}
         if ((st = launch_small_gemm(ctx, Li, 1, Li, 0, eff, eff, eff, nullptr, Ai))) return st;
@@ -384,13 +450,14 @@ int precond_run(nys_ctx* ctx, const nys_precond* pc, int inverse, int dtype, con
     return fail(ctx, NYS_EINVAL, "precond: f32 data needs an f32 or bf16 factor");
 }
 
-// Omega (total entries of store_dt) from the counter-based generator
-int omega_fill(nys_ctx* ctx, int store_dt, void* Omega, int64_t total, uint64_t seed) {
+// Omega (total entries of store_dt, starting at element `first` of the
+// generator's stream) from the counter-based generator
+int omega_fill(nys_ctx* ctx, int store_dt, void* Omega, int64_t total, uint64_t seed, int64_t first) {
     cudaStream_t s = ctx->stream;
     const int grid = (int)std::min<int64_t>((total / 4 + 255) / 256 + 1, ctx->sm_count * 16);
-    if (store_dt == NYS_F64) omega_kernel<double, double><<<grid, 256, 0, s>>>((double*)Omega, total, seed);
-    else if (store_dt == NYS_F32) omega_kernel<float, float><<<grid, 256, 0, s>>>((float*)Omega, total, seed);
-    else omega_kernel<__nv_bfloat16, float><<<grid, 256, 0, s>>>((__nv_bfloat16*)Omega, total, seed);
+    if (store_dt == NYS_F64) omega_kernel<double, double><<<grid, 256, 0, s>>>((double*)Omega, first, total, seed);
+    else if (store_dt == NYS_F32) omega_kernel<float, float><<<grid, 256, 0, s>>>((float*)Omega, first, total, seed);
+    else omega_kernel<__nv_bfloat16, float><<<grid, 256, 0, s>>>((__nv_bfloat16*)Omega, first, total, seed);
     NYS_LAUNCH_CK(ctx);
     return NYS_OK;
 }
@@ -402,13 +469,20 @@ using namespace nys;
 extern "C" {
 
 int nys_sketch(nys_ctx* ctx, nys_op* op, int phi_kind, int ell, uint64_t seed, int store_dt, void* Omega, void* Y) {
+    return nys_sketch_cols(ctx, op, phi_kind, ell, 0, ell, seed, store_dt, Omega, Y);
+}
+
+int nys_sketch_cols(nys_ctx* ctx, nys_op* op, int phi_kind, int ell_total, int j0, int j1, uint64_t seed,
+                    int store_dt, void* Omega, void* Y) {
     if (!ctx || !op || !Omega || !Y) return fail(ctx, NYS_EINVAL, "nys_sketch: null argument");
-    if (ell <= 0) return fail(ctx, NYS_EINVAL, "nys_sketch: ell must be positive");
+    if (ell_total <= 0 || j0 < 0 || j1 <= j0 || j1 > ell_total)
+        return fail(ctx, NYS_EINVAL, "nys_sketch: need 0 <= j0 < j1 <= ell");
+    const int ell = j1 - j0;
     if (op->dtype == NYS_F64 ? store_dt != NYS_F64 : (store_dt != NYS_F32 && store_dt != NYS_BF16))
         return fail(ctx, NYS_EINVAL, "nys_sketch: store dtype does not match the operator");
     if (phi_kind == NYS_PHI_W_ATA_WT && op->haar_levels <= 0)
         return fail(ctx, NYS_EINVAL, "nys_sketch: W A^T A W^T needs an operator with haar_levels");
-    if (int st0 = omega_fill(ctx, store_dt, Omega, (int64_t)ell * op->N, seed)) return st0;
+    if (int st0 = omega_fill(ctx, store_dt, Omega, (int64_t)ell * op->N, seed, (int64_t)j0 * op->N)) return st0;
     if (phi_kind == NYS_PHI_ATA) return op_run(op, 2, Omega, Y, ell, store_dt, store_dt);
     if (phi_kind != NYS_PHI_W_ATA_WT) return fail(ctx, NYS_EINVAL, "nys_sketch: unknown phi kind");
     // W A^T A W^T, chunked through compute-type temporaries
@@ -467,6 +541,58 @@ static int alloc_priv(nys_ctx* ctx, nys_precond* pc) {
     return NYS_OK;
 }
 
+// The ell x ell part of Algorithm 1 (steps 3-8) from the Gram G2 of
+// [Omega | Y] (2 ell x 2 ell, ld 2 ell, device): shift, shifted Cholesky,
+// G = C^{-1} Y_v^T Y_v C^{-T} = B^T B, its eigen-decomposition, S_hat, and
+// W = C^{-T} V S^{-1} (ell x ell, row-major, device) so that U = (Y + v Omega) W.
+// info (device, 16 doubles): [0] status (1: Cholesky failed after the
+// retries), [1] v, [2] retries.  Workspace from SLOT_FACTOR after `skip`
+// doubles (room the caller keeps for G2).
+static int factor_small(nys_ctx* ctx, const double* G2, int ell, double eps, bool eig_f32, size_t skip,
+                        double* S_hat, double** W_out, double** info_out) {
+    const size_t l2 = (size_t)ell * ell;
+    const int n = (ell + 1) & ~1;
+    int st;
+    // layout after the skipped doubles (float64 unless noted): C, H, Ci, T1,
+    // Gm, Vs, scale, info (16) + sweeps (16), then the eigen work area: 2 n^2
+    // values of the Jacobi type and ell doubles
+    const size_t need = (skip + 6 * l2 + (size_t)ell + 32) * 8 + 2 * (size_t)n * n * 8 + 8 * (size_t)n + 256;
+    double* w = (double*)scratch(ctx, SLOT_FACTOR, need, &st);
+    if (st) return st;
+    double* C = w + skip;
+    double* H = C + l2;
+    double* Ci = H + l2;
+    double* T1 = Ci + l2;
+    double* Gm = T1 + l2;
+    double* Vs = Gm + l2;
+    double* scale = Vs + l2;
+    double* info = scale + ell;           // 16 doubles
+    int* sweeps = (int*)(info + 16);
+    void* ework = (void*)(info + 32);     // eigen work (2 n^2 T + n doubles)
+    cudaStream_t s = ctx->stream;
+    NYS_CK(ctx, cudaMemsetAsync(info, 0, 16 * sizeof(double), s));
+    // shifted Cholesky (steps 4-5): on a 16-SM cluster where it fits, else one CTA
+    st = chol_cluster(ctx, G2, 2 * ell, ell, 1, eps, 8, C, info, 0);
+    if (st == NYS_EINVAL) {
+        shift_chol_kernel<<<1, 1024, 0, s>>>(G2, ell, eps, 8, C, info);
+        NYS_LAUNCH_CK(ctx);
+    } else if (st) {
+        return st;
+    }
+    form_H_kernel<<<64, 256, 0, s>>>(G2, ell, info, H);
+    NYS_LAUNCH_CK(ctx);
+    tri_inv_kernel<<<ell, 32, ell * sizeof(double), s>>>(C, Ci, ell);
+    NYS_LAUNCH_CK(ctx);
+    if ((st = launch_small_gemm(ctx, Ci, 0, H, 0, ell, ell, ell, nullptr, T1))) return st;
+    if ((st = launch_small_gemm(ctx, T1, 0, Ci, 1, ell, ell, ell, nullptr, Gm))) return st;
+    if ((st = sym_eig(ctx, Gm, ell, eig_f32, info, ework, Vs, S_hat, scale, sweeps))) return st;
+    // W = C^{-T} V S^{-1}  (into T1)
+    if ((st = launch_small_gemm(ctx, Ci, 1, Vs, 0, ell, ell, ell, scale, T1))) return st;
+    *W_out = T1;
+    *info_out = info;
+    return NYS_OK;
+}
+
 int nys_factor(nys_ctx* ctx, const void* Omega, const void* Y, int in_dt, int64_t N, int ell, double eps,
                nys_precond* pc) {
     if (!ctx || !Omega || !Y || !pc || !pc->U || !pc->S_hat) return fail(ctx, NYS_EINVAL, "nys_factor: null argument");
@@ -485,40 +611,29 @@ int nys_factor(nys_ctx* ctx, const void* Omega, const void* Y, int in_dt, int64_
     const size_t l2 = (size_t)ell * ell;
     const int n = (ell + 1) & ~1;
     int st;
-    // layout of the factor workspace (float64 unless noted)
-    // G2, C, H, Ci, T1, Gm, Vs, scale, info (16) + sweeps (16), then the eigen
-    // work area: 2 n^2 values of the Jacobi type and ell doubles
+    // G2 at the start of the factor workspace, sized for factor_small too
     const size_t need = ((size_t)L2 * L2 + 6 * l2 + (size_t)ell + 32) * 8 + 2 * (size_t)n * n * 8 + 8 * (size_t)n + 256;
-    double* w = (double*)scratch(ctx, SLOT_FACTOR, need, &st);
+    double* G2 = (double*)scratch(ctx, SLOT_FACTOR, need, &st);
     if (st) return st;
-    double* G2 = w;
-    double* C = G2 + (size_t)L2 * L2;
-    double* H = C + l2;
-    double* Ci = H + l2;
-    double* T1 = Ci + l2;
-    double* Gm = T1 + l2;
-    double* Vs = Gm + l2;
-    double* scale = Vs + l2;
-    double* info = scale + ell;           // 16 doubles
-    int* sweeps = (int*)(info + 16);
-    void* ework = (void*)(info + 32);     // eigen work (2 n^2 T + n doubles)
     cudaStream_t s = ctx->stream;
-    NYS_CK(ctx, cudaMemsetAsync(info, 0, 16 * sizeof(double), s));
-    // one Gram pass over [Omega | Y]
-    if ((st = gram_AtB(ctx, in_dt, Omega, ell, Omega, ell, N, G2, L2))) return st;
-    if ((st = gram_AtB(ctx, in_dt, Omega, ell, Y, ell, N, G2 + ell, L2))) return st;
-    if ((st = gram_AtB(ctx, in_dt, Y, ell, Y, ell, N, G2 + (size_t)ell * L2 + ell, L2))) return st;
-    shift_chol_kernel<<<1, 1024, 0, s>>>(G2, ell, eps, 8, C, info);
-    NYS_LAUNCH_CK(ctx);
-    form_H_kernel<<<64, 256, 0, s>>>(G2, ell, info, H);
-    NYS_LAUNCH_CK(ctx);
-    tri_inv_kernel<<<ell, 32, 0, s>>>(C, Ci, ell);
-    NYS_LAUNCH_CK(ctx);
-    if ((st = launch_small_gemm(ctx, Ci, 0, H, 0, ell, ell, ell, nullptr, T1))) return st;
-    if ((st = launch_small_gemm(ctx, T1, 0, Ci, 1, ell, ell, ell, nullptr, Gm))) return st;
-    if ((st = sym_eig(ctx, Gm, ell, !f64, info, ework, Vs, pc->S_hat, scale, sweeps))) return st;
-    // W = C^{-T} V S^{-1}  (into T1)
-    if ((st = launch_small_gemm(ctx, Ci, 1, Vs, 0, ell, ell, ell, scale, T1))) return st;
+    // one Gram pass over [Omega | Y]: Omega^T Omega, Omega^T Y and Y^T Y in
+    // one tensor-core launch for bf16 sketches, three passes otherwise
+    st = NYS_EINVAL;
+    if (in_dt == NYS_BF16) {
+        const void* srcs[2] = {Omega, Y};
+        const int cols[2] = {ell, ell};
+        const GramJob jobs[3] = {{0, 0, G2, L2}, {0, 1, G2 + ell, L2}, {1, 1, G2 + (size_t)ell * L2 + ell, L2}};
+        st = gram_tc_jobs(ctx, srcs, cols, 2, N, 3, jobs);
+        if (st != NYS_OK && st != NYS_EINVAL) return st;
+    }
+    if (st == NYS_EINVAL) {
+        if ((st = gram_AtB(ctx, in_dt, Omega, ell, Omega, ell, N, G2, L2))) return st;
+        if ((st = gram_AtB(ctx, in_dt, Omega, ell, Y, ell, N, G2 + ell, L2))) return st;
+        if ((st = gram_AtB(ctx, in_dt, Y, ell, Y, ell, N, G2 + (size_t)ell * L2 + ell, L2))) return st;
+    }
+    double* T1 = nullptr;
+    double* info = nullptr;
+    if ((st = factor_small(ctx, G2, ell, eps, !f64, (size_t)L2 * L2, pc->S_hat, &T1, &info))) return st;
     // U = (Y + v Omega) W
     if ((st = gemm_tall(ctx, in_dt, Y, Omega, info + 1, N, ell, T1, ell, pc->dtype, pc->U))) return st;
     // K = U^T U of the stored U
@@ -560,9 +675,81 @@ int nys_precond_import(nys_ctx* ctx, nys_precond* pc, double mu, int sqrt_shift)
     return precond_setup_impl(ctx, pc, mu, sqrt_shift ? 1 : 0);
 }
 
+int nys_factor_gram(nys_ctx* ctx, const double* G2, int ell, double eps, int eig_f64, double* W, double* S_hat,
+                    double* v, int* retries) {
+    if (!ctx || !G2 || !W || !S_hat) return fail(ctx, NYS_EINVAL, "nys_factor_gram: null argument");
+    if (ell <= 0 || ell > 1024) return fail(ctx, NYS_EINVAL, "nys_factor_gram: need 0 < ell <= 1024");
+    if (!(eps >= 0.0)) return fail(ctx, NYS_EINVAL, "nys_factor_gram: eps must be >= 0");
+    int st;
+    double* T1 = nullptr;
+    double* info = nullptr;
+    if ((st = factor_small(ctx, G2, ell, eps, eig_f64 == 0, 0, S_hat, &T1, &info))) return st;
+    cudaStream_t s = ctx->stream;
+    NYS_CK(ctx, cudaMemcpyAsync(W, T1, (size_t)ell * ell * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    double h[3];
+    NYS_CK(ctx, cudaMemcpyAsync(h, info, sizeof(h), cudaMemcpyDeviceToHost, s));
+    NYS_CK(ctx, cudaStreamSynchronize(s));
+    if (v) *v = h[1];
+    if (retries) *retries = (int)h[2];
+    if (h[0] != 0.0) return fail(ctx, NYS_ENOTSPD, "nys_factor_gram: Cholesky of the shifted core failed after %d "
+                                 "retries", (int)h[2]);
+    return NYS_OK;
+}
+
+int nys_precond_import_gram(nys_ctx* ctx, nys_precond* pc, const double* K, double mu, int sqrt_shift) {
+    if (!ctx || !pc || !pc->U || !pc->S_hat || !K) return fail(ctx, NYS_EINVAL, "nys_precond_import_gram: null argument");
+    const int ell = pc->ell;
+    if (pc->N <= 0 || ell <= 0 || ell > 1024)
+        return fail(ctx, NYS_EINVAL, "nys_precond_import_gram: need N > 0 and 0 < ell <= 1024");
+    if (pc->dtype != NYS_F32 && pc->dtype != NYS_F64 && pc->dtype != NYS_BF16)
+        return fail(ctx, NYS_EINVAL, "nys_precond_import_gram: bad dtype");
+    if (int st = alloc_priv(ctx, pc)) return st;
+    auto* pv = (nys_precond_priv*)pc->priv;
+    pc->mu = NAN;
+    cudaStream_t s = ctx->stream;
+    NYS_CK(ctx, cudaMemcpyAsync(pv->K, K, (size_t)ell * ell * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    NYS_CK(ctx, cudaMemcpyAsync(&pc->s_first, pc->S_hat, sizeof(double), cudaMemcpyDeviceToHost, s));
+    NYS_CK(ctx, cudaMemcpyAsync(&pc->s_last, pc->S_hat + ell - 1, sizeof(double), cudaMemcpyDeviceToHost, s));
+    NYS_CK(ctx, cudaStreamSynchronize(s));
+    return precond_setup_impl(ctx, pc, mu, sqrt_shift ? 1 : 0);
+}
+
 int nys_precond_setup(nys_ctx* ctx, nys_precond* pc, double mu, int sqrt_shift) {
     if (!ctx || !pc || !pc->priv) return fail(ctx, NYS_EINVAL, "nys_precond_setup: factor first");
     return precond_setup_impl(ctx, pc, mu, sqrt_shift ? 1 : 0);
+}
+
+// shared checks of the split apply: vector path only (N a multiple of the
+// 16-byte vector width, aligned operands), batch <= 65535
+static int split_check(nys_ctx* ctx, const nys_precond* pc, int dtype, const void* a, const void* b, int batch,
+                       const char* who) {
+    if (!ctx || !pc || !a || !b) return fail(ctx, NYS_EINVAL, "%s: null argument", who);
+    if (!pc->priv || !pc->U || pc->mu != pc->mu) return fail(ctx, NYS_EINVAL, "%s: preconditioner not set up", who);
+    if (batch < 1 || batch > 65535) return fail(ctx, NYS_EINVAL, "%s: batch must be in [1, 65535]", who);
+    const int V = pc->dtype == NYS_BF16 ? 8 : (pc->dtype == NYS_F32 ? 4 : 2);
+    if (pc->N % V || pc->N % 4 || (((uintptr_t)pc->U | (uintptr_t)a | (uintptr_t)b) & 15))
+        return fail(ctx, NYS_EINVAL, "%s: rows must be a multiple of %d and buffers 16-byte aligned", who, V);
+    if (dtype == NYS_F64 ? pc->dtype != NYS_F64 : (dtype != NYS_F32 || pc->dtype == NYS_F64))
+        return fail(ctx, NYS_EINVAL, "%s: data and factor dtypes do not match", who);
+    return NYS_OK;
+}
+
+int precond_partial(nys_ctx* ctx, const nys_precond* pc, int dtype, const void* z, void* w, int batch) {
+    if (int st = split_check(ctx, pc, dtype, z, w, batch, "precond_partial")) return st;
+    if (dtype == NYS_F64) return precond_partial_typed<double, double, double>(ctx, pc, z, (double*)w, batch);
+    if (pc->dtype == NYS_F32) return precond_partial_typed<float, float, float>(ctx, pc, z, (float*)w, batch);
+    return precond_partial_typed<__nv_bfloat16, float, float>(ctx, pc, z, (float*)w, batch);
+}
+
+int precond_finish(nys_ctx* ctx, const nys_precond* pc, int inverse, int dtype, const void* w, const void* z,
+                   void* out, int batch) {
+    if (int st = split_check(ctx, pc, dtype, z, out, batch, "precond_finish")) return st;
+    if (!w) return fail(ctx, NYS_EINVAL, "precond_finish: null argument");
+    if (dtype == NYS_F64)
+        return precond_finish_typed<double, double, double>(ctx, pc, inverse, (const double*)w, z, out, batch);
+    if (pc->dtype == NYS_F32)
+        return precond_finish_typed<float, float, float>(ctx, pc, inverse, (const float*)w, z, out, batch);
+    return precond_finish_typed<__nv_bfloat16, float, float>(ctx, pc, inverse, (const float*)w, z, out, batch);
 }
 
 int precond_apply(nys_ctx* ctx, const nys_precond* pc, int inverse, int dtype, const void* z, void* out, int batch) {

@@ -1,24 +1,32 @@
-// Tall-skinny Gram C = A^T B on the 5th-generation tensor cores (tcgen05).
+// Tall-skinny Gram products C = A^T B on the 5th-generation tensor cores
+// (tcgen05), several of them in one launch.
 //
-// A (N x p) and B (N x q) hold their columns as contiguous bf16 images, so as
-// MMA operands both are K-major (K = N pixels): the UMMA computes
-// D[m][n] = sum_k A[m][k] B[n][k] = (A^T B)[m][n] directly.  These are the
-// Gram products of Algorithm 1 (Omega^T Omega, Omega^T Y, Y^T Y) and the
-// U^T U of the stored factor: 2 N ell^2 flops over 4 N ell bytes, i.e. HBM
-// bound once the multiply runs on tensor cores.
+// The operands (at most two: Omega and Y, or U) hold their columns as
+// contiguous bf16 images, so as MMA operands both sides are K-major (K = N
+// pixels): the UMMA computes D[m][n] = sum_k A[m][k] B[n][k] = (A^T B)[m][n]
+// directly.  These are the Gram products of Algorithm 1 (Omega^T Omega,
+// Omega^T Y, Y^T Y: one launch, so each K range of Omega and Y is read from
+// DRAM once and served to the tiles that share it from L2) and the U^T U of
+// the stored factor: 2 N ell^2 flops over 2 N ell bytes per operand, i.e.
+// HBM bound once the multiply runs on tensor cores.
 //
-// One CTA owns a 128-row block of D (all q <= 256 columns, one TMEM
-// accumulator of BN <= 256 fp32 columns) over one split of the K range:
+// The output is cut into tiles of 128 rows x BN <= 256 columns; a product of
+// an operand with itself keeps only the tiles that reach the diagonal.  CTA
+// (tile, split) accumulates its tile over one split of the K range:
 //   warp 0      TMA producer: 64-pixel K blocks of A (128 x 64) and B (BN x 64)
-//               into a 4-stage ring, 128B swizzle, mbarrier transaction counts
+//               into a 4-stage ring, 128B swizzle, mbarrier transaction counts;
+//               rows past an operand's last column are zero-filled by TMA
 //   warp 1      MMA issuer: one elected thread, 4 x tcgen05.mma (K = 16) per
 //               stage, tcgen05.commit frees the stage / signals the result
 //   warp 2      TMEM allocation (BN columns, power of two >= 32)
 //   warps 4-7   epilogue: tcgen05.ld 32x32b.x16 of its 32-lane quarter, fp32
-//               partial tile to global; the splits are summed in float64 by
-//               the existing deterministic reduction.
-// Every mbarrier wait is bounded: on time-out the kernel records an error,
-// stops issuing, drains its own TMA copies and MMAs, frees TMEM and returns.
+//               partial tile to global, column-major within the tile (a warp
+//               store covers 32 consecutive rows); the splits are summed in
+//               float64, in a fixed order, by gram_tiles_reduce_kernel.
+// The splits are the slowest grid index, so the tiles of one K range run
+// side by side.  Every mbarrier wait is bounded: on time-out the kernel
+// records an error, stops issuing, drains its own TMA copies and MMAs, frees
+// TMEM and returns.
 #include "internal.cuh"
 
 #include <cuda.h>
@@ -88,10 +96,25 @@ __host__ __device__ constexpr uint32_t idesc_bf16(int M, int N) {
     return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
 }
 
+// tile table of one multi-product launch: x = source of A (bit 0), source
+// of B (bit 1), product index (bits 2+); y = first row; z = first column
+constexpr int GRAM_MAX_TILES = 128;
+constexpr int GRAM_MAX_JOBS = 4;
+struct GramTiles {
+    int n;
+    int4 t[GRAM_MAX_TILES];
+};
+struct GramJobs {
+    int n;
+    double* C[GRAM_MAX_JOBS];
+    int ldc[GRAM_MAX_JOBS], p[GRAM_MAX_JOBS], q[GRAM_MAX_JOBS], sym[GRAM_MAX_JOBS];
+};
+
 __global__ void __launch_bounds__(256, 1)
-    gram_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, int p, int q,
-                   int BN, int tmem_cols, int kblocks_total, int kblocks_per_split, float* __restrict__ part,
-                   int* __restrict__ err) {
+    gram_tc_kernel(const __grid_constant__ CUtensorMap tmA0, const __grid_constant__ CUtensorMap tmA1,
+                   const __grid_constant__ CUtensorMap tmB0, const __grid_constant__ CUtensorMap tmB1,
+                   const __grid_constant__ GramTiles tiles, int BN, int tmem_cols, int kblocks_total,
+                   int kblocks_per_split, float* __restrict__ part, int* __restrict__ err) {
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     unsigned char* base = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     const uint32_t a_bytes = TC_BM * TC_BK * 2;
@@ -105,8 +128,12 @@ __global__ void __launch_bounds__(256, 1)
     int* abort_flag = reinterpret_cast<int*>(tmem_slot + 1);
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int m0 = blockIdx.y * TC_BM;
-    const int split = blockIdx.x;
+    const int tile = blockIdx.x;
+    const int4 tl = tiles.t[tile];
+    const CUtensorMap* mA = (tl.x & 1) ? &tmA1 : &tmA0;
+    const CUtensorMap* mB = (tl.x & 2) ? &tmB1 : &tmB0;
+    const int m0 = tl.y, n0 = tl.z;
+    const int split = blockIdx.y;
     const int kb0 = split * kblocks_per_split;
     const int nk = max(0, min(kblocks_total, kb0 + kblocks_per_split) - kb0);
 
@@ -143,8 +170,8 @@ __global__ void __launch_bounds__(256, 1)
             }
             mbar_arrive_expect_tx(&full[s], a_bytes + b_bytes);
             const int kx = (kb0 + i) * TC_BK;
-            tma_load_2d(sA + s * a_bytes, &tmA, &full[s], kx, m0);
-            tma_load_2d(sB + s * b_bytes, &tmB, &full[s], kx, 0);
+            tma_load_2d(sA + s * a_bytes, mA, &full[s], kx, m0);
+            tma_load_2d(sB + s * b_bytes, mB, &full[s], kx, n0);
             ++issued;
         }
         // drain: every issued copy has landed before the CTA may exit
@@ -183,14 +210,14 @@ __global__ void __launch_bounds__(256, 1)
                          smem_u32(accum))
                      : "memory");
     } else if (warp >= 4) {
-        // epilogue: this warp's quarter of the 128 TMEM lanes = rows of D
+        // epilogue: this warp's quarter of the 128 TMEM lanes = rows of the tile
         const int quarter = warp & 3;
         const bool ok = mbar_wait(accum, 0);
         tc_fence_after();
         if (!ok) atomicExch(err, 1);
-        const int row = m0 + quarter * 32 + lane;
+        const int r = quarter * 32 + lane;
+        float* out = part + ((size_t)split * tiles.n + tile) * (size_t)BN * TC_BM;
         if (ok && nk > 0 && !*(volatile int*)abort_flag) {
-            float* out = part + ((size_t)split * p + row) * q;
             for (int c0 = 0; c0 < BN; c0 += 16) {
                 uint32_t v[16];
                 const uint32_t taddr = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)c0;
@@ -202,15 +229,11 @@ __global__ void __launch_bounds__(256, 1)
                       "=r"(v[15])
                     : "r"(taddr));
                 asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-                if (row < p) {
 #pragma unroll
-                    for (int j = 0; j < 16; ++j)
-                        if (c0 + j < q) out[c0 + j] = __uint_as_float(v[j]);
-                }
+                for (int j = 0; j < 16; ++j) out[(size_t)(c0 + j) * TC_BM + r] = __uint_as_float(v[j]);
             }
-        } else if (nk == 0 && row < p) {
-            float* out = part + ((size_t)split * p + row) * q;
-            for (int c = 0; c < q; ++c) out[c] = 0.0f;
+        } else if (nk == 0) {
+            for (int c = 0; c < BN; ++c) out[(size_t)c * TC_BM + r] = 0.0f;
         }
     }
     tc_fence_before();
@@ -218,6 +241,31 @@ __global__ void __launch_bounds__(256, 1)
     tc_fence_after();
     if (warp == 2)
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(tmem_cols) : "memory");
+}
+
+// C_job[m0 + r][n0 + c] = sum over splits (float64, fixed order) of the tile's
+// partials; a product of an operand with itself writes each entry on or above
+// the diagonal and its mirror.  Grid (tiles, entries / 256): one entry per
+// thread.
+__global__ void __launch_bounds__(256) gram_tiles_reduce_kernel(const float* __restrict__ part, int splits, int BN,
+                                                                const __grid_constant__ GramTiles tiles,
+                                                                const __grid_constant__ GramJobs jobs) {
+    const int tile = blockIdx.x;
+    const int4 tl = tiles.t[tile];
+    const int job = tl.x >> 2;
+    double* C = jobs.C[job];
+    const int ldc = jobs.ldc[job], p = jobs.p[job], q = jobs.q[job], sym = jobs.sym[job];
+    const size_t stride = (size_t)tiles.n * BN * TC_BM;
+    const float* base = part + (size_t)tile * BN * TC_BM;
+    for (int e = blockIdx.y * blockDim.x + threadIdx.x; e < BN * TC_BM; e += gridDim.y * blockDim.x) {
+        const int c = e / TC_BM, r = e - c * TC_BM;
+        const int i = tl.y + r, j = tl.z + c;
+        if (i >= p || j >= q || (sym && j < i)) continue;
+        double s = 0.0;
+        for (int z = 0; z < splits; ++z) s += (double)base[(size_t)z * stride + e];
+        C[(size_t)i * ldc + j] = s;
+        if (sym) C[(size_t)j * ldc + i] = s;
+    }
 }
 
 PFN_cuTensorMapEncodeTiled_v12000 encode_fn(nys_ctx* ctx) {
@@ -249,28 +297,63 @@ bool make_map(PFN_cuTensorMapEncodeTiled_v12000 enc, CUtensorMap* m, const void*
 
 }  // namespace
 
-// C (p x q, float64, ld = ldc) = A^T B for bf16 operands on tensor cores.
-// Returns NYS_EINVAL (without touching the device) when the shapes are not
-// supported, so the caller can take the CUDA-core path.
-int gram_AtB_tc(nys_ctx* ctx, const void* A, int p, const void* B, int q, int64_t N, double* C, int ldc) {
-    if (q < 1 || q > 256 || p < 1 || N < TC_BK || (N % 8) != 0 || N > (int64_t)0x7fffffff ||
-        (((uintptr_t)A | (uintptr_t)B) & 15))
+// The Gram products `jobs` of at most two bf16 operands (srcs[0], srcs[1],
+// cols[] columns of N pixels each) in one launch.  Returns NYS_EINVAL
+// (without touching the device) when the shapes are not supported, so the
+// caller can take the CUDA-core path.
+int gram_tc_jobs(nys_ctx* ctx, const void* const* srcs, const int* cols, int nsrc, int64_t N, int njobs,
+                 const GramJob* jl) {
+    if (nsrc < 1 || nsrc > 2 || njobs < 1 || njobs > GRAM_MAX_JOBS || N < TC_BK || (N % 8) != 0 ||
+        N > (int64_t)0x7fffffff)
         return NYS_EINVAL;
+    for (int s = 0; s < nsrc; ++s)
+        if (!srcs[s] || cols[s] < 1 || cols[s] > 1024 || ((uintptr_t)srcs[s] & 15)) return NYS_EINVAL;
     auto enc = encode_fn(ctx);
     if (!enc) return NYS_EINVAL;
-    const int BN = ((q + 15) / 16) * 16;
+    // one column-tile width for the launch: at most 256, balanced over the
+    // widest product's columns
+    int qmax = 1;
+    for (int k = 0; k < njobs; ++k) {
+        if (jl[k].a < 0 || jl[k].a >= nsrc || jl[k].b < 0 || jl[k].b >= nsrc) return NYS_EINVAL;
+        qmax = std::max(qmax, cols[jl[k].b]);
+    }
+    const int nct_max = (qmax + 255) / 256;
+    const int BN = ((((qmax + nct_max - 1) / nct_max) + 15) / 16) * 16;
     int tmem_cols = 32;
     while (tmem_cols < BN) tmem_cols <<= 1;
-    CUtensorMap mA, mB;
-    if (!make_map(enc, &mA, A, N, p, TC_BM) || !make_map(enc, &mB, B, N, q, BN)) return NYS_EINVAL;
-    const int mtiles = (p + TC_BM - 1) / TC_BM;
+    GramTiles tiles = {};
+    GramJobs jobs = {};
+    jobs.n = njobs;
+    for (int k = 0; k < njobs; ++k) {
+        const int p = cols[jl[k].a], q = cols[jl[k].b];
+        const bool sym = jl[k].a == jl[k].b;
+        jobs.C[k] = jl[k].C;
+        jobs.ldc[k] = jl[k].ldc;
+        jobs.p[k] = p;
+        jobs.q[k] = q;
+        jobs.sym[k] = sym ? 1 : 0;
+        for (int m0 = 0; m0 < p; m0 += TC_BM)
+            for (int n0 = 0; n0 < q; n0 += BN) {
+                // a product with itself: skip tiles entirely below the diagonal
+                if (sym && std::min(n0 + BN, q) - 1 < m0) continue;
+                if (tiles.n >= GRAM_MAX_TILES) return NYS_EINVAL;
+                tiles.t[tiles.n++] = make_int4(jl[k].a | (jl[k].b << 1) | (k << 2), m0, n0, 0);
+            }
+    }
+    CUtensorMap mA[2], mB[2];
+    for (int s = 0; s < 2; ++s) {
+        const int src = s < nsrc ? s : 0;
+        if (!make_map(enc, &mA[s], srcs[src], N, cols[src], TC_BM) || !make_map(enc, &mB[s], srcs[src], N, cols[src], BN))
+            return NYS_EINVAL;
+    }
     const int kblocks = (int)((N + TC_BK - 1) / TC_BK);
-    // about one CTA per SM (each holds ~170 KB of shared memory)
-    int splits = std::max(1, std::min(kblocks, ctx->sm_count / mtiles));
+    // about one CTA per SM (each holds up to ~200 KB of shared memory)
+    int splits = std::max(1, std::min(kblocks, ctx->sm_count / tiles.n));
     const int kper = (kblocks + splits - 1) / splits;
     splits = (kblocks + kper - 1) / kper;
+    if (splits > 65535) return NYS_EINVAL;
     int st;
-    float* part = (float*)scratch(ctx, SLOT_GRAM, (size_t)splits * p * q * sizeof(float) + 64, &st);
+    float* part = (float*)scratch(ctx, SLOT_GRAM, (size_t)splits * tiles.n * BN * TC_BM * sizeof(float) + 64, &st);
     if (st) return st;
     int* err = (int*)scratch(ctx, SLOT_TCERR, 64, &st);
     if (st) return st;
@@ -278,12 +361,27 @@ int gram_AtB_tc(nys_ctx* ctx, const void* A, int p, const void* B, int q, int64_
     if ((st = smem_optin(ctx, (const void*)gram_tc_kernel, smem))) return st;
     cudaStream_t s = ctx->stream;
     NYS_CK(ctx, cudaMemsetAsync(err, 0, sizeof(int), s));
-    gram_tc_kernel<<<dim3(splits, mtiles), 256, smem, s>>>(mA, mB, p, q, BN, tmem_cols, kblocks, kper, part, err);
+    gram_tc_kernel<<<dim3(tiles.n, splits), 256, smem, s>>>(mA[0], mA[1], mB[0], mB[1], tiles, BN, tmem_cols, kblocks,
+                                                            kper, part, err);
     NYS_LAUNCH_CK(ctx);
-    const int rb = std::min<int64_t>(1024, ((int64_t)p * q + 255) / 256);
-    gram_reduce_f32(ctx, part, splits, p, q, C, ldc, rb);
+    gram_tiles_reduce_kernel<<<dim3(tiles.n, (BN * TC_BM + 255) / 256), 256, 0, s>>>(part, splits, BN, tiles, jobs);
     NYS_LAUNCH_CK(ctx);
     return NYS_OK;
+}
+
+// C (p x q, float64, ld = ldc) = A^T B for bf16 operands on tensor cores
+// (A == B: one operand, the symmetric tiles only).
+int gram_AtB_tc(nys_ctx* ctx, const void* A, int p, const void* B, int q, int64_t N, double* C, int ldc) {
+    if (A == B && p == q) {
+        const void* srcs[1] = {A};
+        const int cols[1] = {p};
+        const GramJob j = {0, 0, C, ldc};
+        return gram_tc_jobs(ctx, srcs, cols, 1, N, 1, &j);
+    }
+    const void* srcs[2] = {A, B};
+    const int cols[2] = {p, q};
+    const GramJob j = {0, 1, C, ldc};
+    return gram_tc_jobs(ctx, srcs, cols, 2, N, 1, &j);
 }
 
 }  // namespace nys
@@ -291,7 +389,9 @@ int gram_AtB_tc(nys_ctx* ctx, const void* A, int p, const void* B, int q, int64_
 // ---------------------------------------------------------------------------
 // U = (Y + v Omega) W on tcgen05, as the plain product U = [Y | Omega] W' with
 // W' = [W; v W] (no elementwise pass over the tall data).  Per CTA one
-// 128-pixel tile of U and all q <= 256 columns:
+// 128-pixel tile of U and one block of BN <= 256 of its q <= 1024 columns
+// (the column blocks of a pixel tile are adjacent in the grid, so the tile's
+// Y and Omega rows come from L2 after the first block):
 //   A (128 pixels x 64 k) comes from Y or Omega, whose rows are images, so the
 //     operand is MN-major: two 64-pixel TMA boxes (128B swizzle) side by side,
 //     the second at LBO = 8 KB, 8-row K groups 1 KB apart (SBO)
@@ -349,7 +449,8 @@ __global__ void __launch_bounds__(256, 1)
     int* abort_flag = reinterpret_cast<int*>(tmem_slot + 1);
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int64_t m0 = (int64_t)blockIdx.x * TC_BM;
+    const int64_t m0 = (int64_t)blockIdx.y * TC_BM;
+    const int n0 = blockIdx.x * BN;
     const int nk = 2 * kb_half;
 
     if (threadIdx.x == 0) {
@@ -387,8 +488,8 @@ __global__ void __launch_bounds__(256, 1)
             const int krow = (i < kb_half ? i : i - kb_half) * TC_BK;
             tma_load_2d(sA + s * a_bytes, mx, &full[s], (int)m0, krow);
             tma_load_2d(sA + s * a_bytes + half_bytes, mx, &full[s], (int)m0 + 64, krow);
-            tma_load_2d(sB + s * b_bytes, &tmW, &full[s], i * TC_BK, 0);
-            tma_load_2d(sB + s * b_bytes + bh_bytes, &tmW, &full[s], kpad + i * TC_BK, 0);
+            tma_load_2d(sB + s * b_bytes, &tmW, &full[s], i * TC_BK, n0);
+            tma_load_2d(sB + s * b_bytes + bh_bytes, &tmW, &full[s], kpad + i * TC_BK, n0);
             ++issued;
         }
         for (int i = max(0, issued - nst); i < issued; ++i)
@@ -452,7 +553,7 @@ __global__ void __launch_bounds__(256, 1)
                 if (pix < N) {
 #pragma unroll
                     for (int j = 0; j < 16; ++j)
-                        if (c0 + j < q) stf(U + (size_t)(c0 + j) * N + pix, __uint_as_float(v[j]));
+                        if (n0 + c0 + j < q) stf(U + (size_t)(n0 + c0 + j) * N + pix, __uint_as_float(v[j]));
                 }
             }
         }
@@ -482,13 +583,16 @@ bool make_map_box(PFN_cuTensorMapEncodeTiled_v12000 enc, CUtensorMap* m, const v
 // shape is not supported (caller falls back to CUDA cores).
 int gemm_tall_tc(nys_ctx* ctx, const void* Y, const void* Om, const double* v_dev, int64_t N, int ell,
                  const double* W, int out_dt, void* out) {
-    if (ell < 1 || ell > 256 || N < 128 || (N % 8) != 0 || N > (int64_t)0x7fffffff ||
-        (((uintptr_t)Y | (uintptr_t)Om) & 15) || (out_dt != NYS_BF16 && out_dt != NYS_F32))
+    if (ell < 1 || ell > 1024 || N < 128 || (N % 8) != 0 || N > (int64_t)0x7fffffff ||
+        (N + TC_BM - 1) / TC_BM > 65535 || (((uintptr_t)Y | (uintptr_t)Om) & 15) ||
+        (out_dt != NYS_BF16 && out_dt != NYS_F32))
         return NYS_EINVAL;
     auto enc = encode_fn(ctx);
     if (!enc) return NYS_EINVAL;
     const int q = ell;
-    const int BN = ((q + 15) / 16) * 16;
+    // column blocks of at most 256, balanced
+    const int nct = (q + 255) / 256;
+    const int BN = ((((q + nct - 1) / nct) + 15) / 16) * 16;
     int tmem_cols = 32;
     while (tmem_cols < BN) tmem_cols <<= 1;
     const int L1 = ((ell + TC_BK - 1) / TC_BK) * TC_BK;
@@ -510,15 +614,15 @@ int gemm_tall_tc(nys_ctx* ctx, const void* Y, const void* Om, const double* v_de
     const int nst = (int)std::min<size_t>(TALL_STAGES, (227 * 1024 - 2048) / stage_bytes);
     if (nst < 2) return NYS_EINVAL;
     const size_t smem = 1024 + (size_t)nst * stage_bytes + 256;
-    const unsigned mtiles = (unsigned)((N + TC_BM - 1) / TC_BM);
+    const dim3 grid((unsigned)nct, (unsigned)((N + TC_BM - 1) / TC_BM));
     if (out_dt == NYS_BF16) {
         if (int st2 = smem_optin(ctx, (const void*)tall_tc_kernel<__nv_bfloat16>, smem)) return st2;
-        tall_tc_kernel<__nv_bfloat16><<<mtiles, 256, smem, s>>>(mY, mO, mW, N, q, BN, tmem_cols, L1 / TC_BK,
-                                                                 Kpad, nst, (__nv_bfloat16*)out, err);
+        tall_tc_kernel<__nv_bfloat16><<<grid, 256, smem, s>>>(mY, mO, mW, N, q, BN, tmem_cols, L1 / TC_BK, Kpad, nst,
+                                                               (__nv_bfloat16*)out, err);
     } else {
         if (int st2 = smem_optin(ctx, (const void*)tall_tc_kernel<float>, smem)) return st2;
-        tall_tc_kernel<float><<<mtiles, 256, smem, s>>>(mY, mO, mW, N, q, BN, tmem_cols, L1 / TC_BK, Kpad, nst, (float*)out,
-                                                       err);
+        tall_tc_kernel<float><<<grid, 256, smem, s>>>(mY, mO, mW, N, q, BN, tmem_cols, L1 / TC_BK, Kpad, nst,
+                                                       (float*)out, err);
     }
     NYS_LAUNCH_CK(ctx);
     return NYS_OK;

@@ -237,8 +237,19 @@ int gram_AtB_path(nys_ctx* ctx, int dtype, const void* A, int p, const void* B, 
                   int path);
 // tcgen05 Gram for bf16 operands (gram_tc.cu); NYS_EINVAL when unsupported
 int gram_AtB_tc(nys_ctx* ctx, const void* A, int p, const void* B, int q, int64_t N, double* C, int ldc);
+// one product srcs[a]^T srcs[b] into C (float64, ld = ldc) of a multi-product launch
+struct GramJob {
+    int a, b;
+    double* C;
+    int ldc;
+};
+// up to four Gram products of up to two bf16 operands (cols[s] columns of N
+// pixels, at most 1024) in one tensor-core launch (gram_tc.cu); NYS_EINVAL
+// when unsupported
+int gram_tc_jobs(nys_ctx* ctx, const void* const* srcs, const int* cols, int nsrc, int64_t N, int njobs,
+                 const GramJob* jobs);
 void gram_reduce_f32(nys_ctx* ctx, const float* part, int splits, int p, int q, double* C, int ldc, int blocks);
-// tcgen05 U = (Y + v Omega) W for bf16 Y, Omega, ell <= 256 (gram_tc.cu); NYS_EINVAL when unsupported
+// tcgen05 U = (Y + v Omega) W for bf16 Y, Omega, ell <= 1024 (gram_tc.cu); NYS_EINVAL when unsupported
 int gemm_tall_tc(nys_ctx* ctx, const void* Y, const void* Om, const double* v_dev, int64_t N, int ell,
                  const double* W, int out_dt, void* out);
 // path: 0 = tensor cores when possible, 1 = CUDA cores, 2 = tensor cores or NYS_EINVAL
@@ -250,8 +261,23 @@ int check_tc_timeout(nys_ctx* ctx);
 int gemm_tall(nys_ctx* ctx, int in_dt, const void* A, const void* A2, const double* alpha_dev, int64_t N,
               int k, const double* W, int q, int out_dt, void* out);
 
+// eigenvectors V (float32, row-major, ld = ldv) of the symmetric ell x ell
+// float64 G by one-sided Jacobi on a thread-block cluster
+// (jacobi_cluster.cu); NYS_EINVAL (nothing launched) when not applicable;
+// *status (device) = 1 if the float32 Cholesky of G fails
+int jacobi_cluster(nys_ctx* ctx, const double* G, int ell, int max_sweeps, float* V, int ldv, int* sweeps,
+                   int* status);
+
+// float64 Cholesky L (n x n, lower, row-major) on a 16-CTA cluster
+// (chol_cluster.cu): mode 0 of src (ld), status in info[slot]; mode 1 of
+// sym(Omega^T Y) + v Omega^T Omega from the Gram src = G2 with the shift and
+// its retries in info[0..2].  NYS_EINVAL (nothing launched) when n is outside
+// [48, 512] or the cluster cannot be placed.
+int chol_cluster(nys_ctx* ctx, const double* src, int ld, int n, int mode, double eps, int max_retries, double* L,
+                 double* info, int slot);
+
 // Omega for Algorithm 1 step 1: total i.i.d. N(0,1) entries (factor.cu)
-int omega_fill(nys_ctx* ctx, int store_dt, void* Omega, int64_t total, uint64_t seed);
+int omega_fill(nys_ctx* ctx, int store_dt, void* Omega, int64_t total, uint64_t seed, int64_t first = 0);
 
 // reductions (reduce.cu)
 int norm2_diff(nys_ctx* ctx, int dtype, int64_t n, const void* a, const void* b, double** out_dev);

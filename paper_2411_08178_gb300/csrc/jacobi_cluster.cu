@@ -1,0 +1,364 @@
+// Eigen-decomposition of the ell x ell Gram G = B^T B of Algorithm 1 step 7 on
+// a thread-block cluster: one-sided (Hestenes) Jacobi on the Cholesky factor
+// R (G = R^T R), float32, for 64 <= ell <= 448.
+//
+// The columns of R -- each with the matching column of V, the accumulated
+// rotation, beside it -- are cut into 2C blocks of b columns; CTA c of the
+// cluster holds two of them in shared memory (its two "seats").
+//   Cholesky   right-looking by panels (one block per panel): the panel's
+//              owner factors its b x b diagonal block, every CTA solves for
+//              the panel's rows of its own later columns, then updates its
+//              columns with the panel's rows gathered from the other CTAs
+//              (distributed shared memory); two cluster barriers per panel.
+//   sweeps     one sweep pairs every column with every other once: a CTA
+//              rotates every pair between its two blocks (b sub-rounds of b
+//              disjoint pairs, one warp per pair), and in the first block
+//              round also the pairs inside each block; then the blocks move
+//              to the next seats of a round-robin tournament over the 2C
+//              seats (seat 0 fixed, the others shift by one), copied from the
+//              neighbouring CTAs' shared memory, and the next block round
+//              starts.  2C - 1 block rounds per sweep; the sweeps stop when
+//              no pair needed a rotation (cluster-wide vote) or after
+//              max_sweeps.
+//   output     V (row-major, ld = ldv): column idx of V is the accumulated
+//              rotation of the column that started as column idx of R, so
+//              R V has orthogonal columns and V^T G V is diagonal.
+// Every CTA runs the same sequence of cluster barriers (uniform control
+// flow, no spin waits).  A non-positive Cholesky pivot sets *status_out = 1
+// and writes nothing else, so that the caller's two-sided kernel runs.
+#include "internal.cuh"
+
+#include <cooperative_groups.h>
+
+namespace cg = cooperative_groups;
+
+namespace nys {
+namespace {
+
+constexpr int JC_THREADS = 512;   // 16 warps: one per pair of a sub-round (b <= 16)
+
+template <int C>
+__global__ void __launch_bounds__(JC_THREADS, 1)
+    jacobi_cluster_kernel(const double* __restrict__ G, int nreal, int b, int max_sweeps, float* __restrict__ V,
+                          int ldv, int* __restrict__ sweeps_out, int* __restrict__ status_out) {
+    cg::cluster_group cluster = cg::this_cluster();
+    const int rank = (int)cluster.block_rank();
+    const int npad = 2 * C * b;
+    const int col_len = 2 * npad;                 // R part, then V part
+    const int slot_len = b * col_len;
+    extern __shared__ __align__(16) float jc_smem[];
+    float* buf = jc_smem;                         // [4][b][2 npad]: cur seat 0, cur seat 1, next seat 0, next seat 1
+    float* nrm = buf + 4 * (size_t)slot_len;      // [4][b]
+    int* idx = reinterpret_cast<int*>(nrm + 4 * b);   // [4][b]
+    __shared__ int bad_flag, rot_flag;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+
+    // seats: CTA c holds seats c and 2C - 1 - c; block k starts in seat k
+    int cur = 0;                                  // buffers cur, cur + 1 are the current seats
+    auto seat_buf = [&](int which) { return buf + (size_t)which * slot_len; };
+    const int blk[2] = {rank, 2 * C - 1 - rank};
+    for (int s = 0; s < 2; ++s)
+        for (int c = threadIdx.x; c < b; c += blockDim.x) idx[s * b + c] = blk[s] * b + c;
+    // load G (padded with the identity) into the R parts, columns of the two blocks
+    for (int s = 0; s < 2; ++s) {
+        float* sb = seat_buf(s);
+        for (int t = threadIdx.x; t < b * npad; t += blockDim.x) {
+            const int c = t / npad, i = t - c * npad;
+            const int j = blk[s] * b + c;
+            float g;
+            if (i < nreal && j < nreal) g = (float)G[(size_t)i * nreal + j];
+            else g = (i == j) ? 1.0f : 0.0f;
+            sb[(size_t)c * col_len + i] = g;
+        }
+    }
+    if (threadIdx.x == 0) bad_flag = 0;
+    // the next-seat buffers serve as staging during the Cholesky
+    float* stage = seat_buf(2);
+    cluster.sync();
+
+    // ---------------------------------------------------------- Cholesky --
+    for (int k = 0; k < 2 * C; ++k) {
+        const int owner = k < C ? k : 2 * C - 1 - k;
+        const int oseat = k < C ? 0 : 1;
+        const int p0 = k * b;                      // first column (and row) of the panel
+        if (rank == owner) {
+            float* pb = seat_buf(oseat);
+            for (int t = 0; t < b; ++t) {
+                const int r = p0 + t;
+                if (threadIdx.x == 0) {
+                    const float d = pb[(size_t)t * col_len + r];
+                    if (!(d > 0.0f)) bad_flag = 1;
+                    else pb[(size_t)t * col_len + r] = sqrtf(d);
+                }
+                __syncthreads();
+                if (bad_flag) break;
+                const float rtt = pb[(size_t)t * col_len + r];
+                for (int c = t + 1 + threadIdx.x; c < b; c += blockDim.x) pb[(size_t)c * col_len + r] /= rtt;
+                __syncthreads();
+                // update rows r+1.. of the later panel columns: R(i, c) -= R(r, i) R(r, c), r < i <= p0 + c
+                for (int e = threadIdx.x; e < b * b; e += blockDim.x) {
+                    const int c = e / b, i = p0 + e - (e / b) * b;
+                    if (c > t && i > r && i <= p0 + c)
+                        pb[(size_t)c * col_len + i] -= pb[(size_t)(i - p0) * col_len + r] * pb[(size_t)c * col_len + r];
+                }
+                __syncthreads();
+            }
+            // a failed pivot: tell every CTA (their own copy of the flag), so
+            // that all leave after the same barrier and no CTA reads the
+            // shared memory of one that has left
+            if (bad_flag && threadIdx.x < C) *cluster.map_shared_rank(&bad_flag, (int)threadIdx.x) = 1;
+        }
+        cluster.sync();
+        if (bad_flag) {
+            if (rank == 0 && threadIdx.x == 0) *status_out = 1;
+            return;
+        }
+        // the panel's diagonal block R_PP (b x b, upper) from its owner
+        {
+            const float* ob = cluster.map_shared_rank(seat_buf(oseat), owner);
+            for (int e = threadIdx.x; e < b * b; e += blockDim.x) {
+                const int c = e / b, i = e - c * b;
+                stage[e] = ob[(size_t)c * col_len + p0 + i];   // stage[c b + i] = R(p0 + i, p0 + c)
+            }
+        }
+        __syncthreads();
+        // rows of the panel in my later columns: solve R_PP^T x = g (forward substitution)
+        for (int s = 0; s < 2; ++s) {
+            if (blk[s] <= k) continue;
+            float* sb = seat_buf(s);
+            for (int c = threadIdx.x; c < b; c += blockDim.x) {
+                float* col = sb + (size_t)c * col_len;
+                for (int i = 0; i < b; ++i) {
+                    float v = col[p0 + i];
+                    for (int q = 0; q < i; ++q) v -= stage[i * b + q] * col[p0 + q];
+                    col[p0 + i] = v / stage[i * b + i];
+                }
+            }
+        }
+        cluster.sync();
+        // gather the panel's rows of every column after the panel: stage[i][m] = R(p0 + i, m)
+        const int m0 = p0 + b;
+        const int nm = npad - m0;
+        if (nm > 0) {
+            for (int e = threadIdx.x; e < b * nm; e += blockDim.x) {
+                const int m = m0 + e / b, i = e - (e / b) * b;
+                const int kb = m / b, c = m - kb * b;
+                const int orank = kb < C ? kb : 2 * C - 1 - kb, os = kb < C ? 0 : 1;
+                const float* ob = cluster.map_shared_rank(seat_buf(os), orank);
+                stage[(size_t)b * b + (size_t)(m - m0) * b + i] = ob[(size_t)c * col_len + p0 + i];
+            }
+            __syncthreads();
+            // trailing update of my later columns: R(i, j) -= sum_t R(p0 + t, i) R(p0 + t, j), m0 <= i <= j
+            for (int s = 0; s < 2; ++s) {
+                if (blk[s] <= k) continue;
+                float* sb = seat_buf(s);
+                const float* rows = stage + (size_t)b * b;
+                for (int e = threadIdx.x; e < b * npad; e += blockDim.x) {
+                    const int c = e / npad, i = e - c * npad;
+                    const int j = blk[s] * b + c;
+                    if (i < m0 || i > j) continue;
+                    float* col = sb + (size_t)c * col_len;
+                    float acc = 0.0f;
+                    for (int t = 0; t < b; ++t) acc += rows[(size_t)(i - m0) * b + t] * col[p0 + t];
+                    col[i] -= acc;
+                }
+            }
+        }
+        // the next panel's owner reads and writes only its own columns and
+        // rows of later panels; the others read this panel's rows, which are final
+        __syncthreads();
+    }
+    // R upper triangular (the strict lower parts still hold G); V = I
+    for (int s = 0; s < 2; ++s) {
+        float* sb = seat_buf(s);
+        for (int t = threadIdx.x; t < b * npad; t += blockDim.x) {
+            const int c = t / npad, i = t - c * npad;
+            const int j = blk[s] * b + c;
+            float* col = sb + (size_t)c * col_len;
+            if (i > j) col[i] = 0.0f;
+            col[npad + i] = (i == j) ? 1.0f : 0.0f;
+        }
+    }
+    __syncthreads();
+
+    // ------------------------------------------------------------ sweeps --
+    const float tol = 1.2e-7f * sqrtf((float)npad);
+    const int nv = npad / 4;                       // float4 vectors per R part
+    auto rotate_pair = [&](float* x, float* y, float* na, float* nb_, int ix, int iy) -> bool {
+        // one warp: c = x . y over the R parts, then the plane rotation of both parts
+        const float4* xv = reinterpret_cast<const float4*>(x);
+        const float4* yv = reinterpret_cast<const float4*>(y);
+        float c = 0.0f;
+        for (int v = lane; v < nv; v += 32) {
+            const float4 p = xv[v], q = yv[v];
+            c += p.x * q.x + p.y * q.y + p.z * q.z + p.w * q.w;
+        }
+        c = warp_sum(c);
+        const float a = *na, bb = *nb_;
+        if (ix >= nreal || iy >= nreal || c == 0.0f || !(fabsf(c) > tol * sqrtf(a * bb))) return false;
+        const float zeta = (bb - a) / (2.0f * c);
+        const float t = (zeta >= 0.0f ? 1.0f : -1.0f) / (fabsf(zeta) + sqrtf(1.0f + zeta * zeta));
+        const float cs = 1.0f / sqrtf(1.0f + t * t), sn = t * cs;
+        float4* xw = reinterpret_cast<float4*>(x);
+        float4* yw = reinterpret_cast<float4*>(y);
+        for (int v = lane; v < 2 * nv; v += 32) {
+            const float4 p = xw[v], q = yw[v];
+            xw[v] = make_float4(cs * p.x - sn * q.x, cs * p.y - sn * q.y, cs * p.z - sn * q.z, cs * p.w - sn * q.w);
+            yw[v] = make_float4(sn * p.x + cs * q.x, sn * p.y + cs * q.y, sn * p.z + cs * q.z, sn * p.w + cs * q.w);
+        }
+        __syncwarp();
+        if (lane == 0) {
+            *na = a - t * c;
+            *nb_ = bb + t * c;
+        }
+        return true;
+    };
+    int sweep = 0;
+    for (; sweep < max_sweeps; ++sweep) {
+        // column norms of the R parts, recomputed every sweep
+        for (int s = 0; s < 2; ++s) {
+            float* sb = seat_buf(cur + s);
+            for (int c = warp; c < b; c += JC_THREADS / 32) {
+                const float4* xv = reinterpret_cast<const float4*>(sb + (size_t)c * col_len);
+                float a = 0.0f;
+                for (int v = lane; v < nv; v += 32) {
+                    const float4 p = xv[v];
+                    a += p.x * p.x + p.y * p.y + p.z * p.z + p.w * p.w;
+                }
+                a = warp_sum(a);
+                if (lane == 0) nrm[(cur + s) * b + c] = a;
+            }
+        }
+        if (threadIdx.x == 0) rot_flag = 0;
+        __syncthreads();
+        bool rotated = false;
+        for (int br = 0; br < 2 * C - 1; ++br) {
+            float* X = seat_buf(cur);
+            float* Y = seat_buf(cur + 1);
+            float* nX = nrm + cur * b;
+            float* nY = nrm + (cur + 1) * b;
+            const int* iX = idx + cur * b;
+            const int* iY = idx + (cur + 1) * b;
+            if (br == 0) {
+                // pairs inside each block: round robin over b (+1 if odd) players
+                const int bp = b + (b & 1);
+                for (int r = 0; r < bp - 1; ++r) {
+                    const int half = bp / 2;
+                    if (warp < 2 * half) {
+                        const int s = warp / half, k = warp - s * half;
+                        const int u = (k == 0) ? bp - 1 : (r + k) % (bp - 1);
+                        const int v = (k == 0) ? r : (r - k + bp - 1) % (bp - 1);
+                        if (u < b && v < b) {
+                            float* S = s ? Y : X;
+                            float* nS = s ? nY : nX;
+                            const int* iS = s ? iY : iX;
+                            const int p = min(u, v), q = max(u, v);
+                            rotated |= rotate_pair(S + (size_t)p * col_len, S + (size_t)q * col_len, nS + p, nS + q,
+                                                   iS[p], iS[q]);
+                        }
+                    }
+                    __syncthreads();
+                }
+            }
+            // pairs between the two blocks: (X_i, Y_(i + r) mod b)
+            for (int r = 0; r < b; ++r) {
+                if (warp < b) {
+                    const int i = warp, j = (warp + r) % b;
+                    rotated |= rotate_pair(X + (size_t)i * col_len, Y + (size_t)j * col_len, nX + i, nY + j, iX[i],
+                                           iY[j]);
+                }
+                __syncthreads();
+            }
+            // move the blocks to the next seats (seat 0 stays, seat k -> k + 1, 2C - 1 -> 1)
+            cluster.sync();
+            const int nxt = cur ^ 2;
+            for (int s = 0; s < 2; ++s) {
+                const int seat = s == 0 ? rank : 2 * C - 1 - rank;
+                int src_seat = seat == 0 ? 0 : (seat == 1 ? 2 * C - 1 : seat - 1);
+                const int src_rank = src_seat < C ? src_seat : 2 * C - 1 - src_seat;
+                const int src_s = src_seat < C ? 0 : 1;
+                const float* sb = cluster.map_shared_rank(seat_buf(cur + src_s), src_rank);
+                const float* sn = cluster.map_shared_rank(nrm + (cur + src_s) * b, src_rank);
+                const int* si = cluster.map_shared_rank(idx + (cur + src_s) * b, src_rank);
+                float4* dst = reinterpret_cast<float4*>(seat_buf(nxt + s));
+                const float4* src = reinterpret_cast<const float4*>(sb);
+                for (int v = threadIdx.x; v < slot_len / 4; v += blockDim.x) dst[v] = src[v];
+                for (int c = threadIdx.x; c < b; c += blockDim.x) {
+                    nrm[(nxt + s) * b + c] = sn[c];
+                    idx[(nxt + s) * b + c] = si[c];
+                }
+            }
+            cluster.sync();
+            cur = nxt;
+        }
+        // cluster-wide vote: did any pair rotate in this sweep?
+        if (rotated) atomicOr(&rot_flag, 1);
+        cluster.sync();
+        int any = 0;
+        for (int r = 0; r < C; ++r) any |= *cluster.map_shared_rank(&rot_flag, r);
+        cluster.sync();
+        if (!any) {
+            ++sweep;
+            break;
+        }
+    }
+    // V columns out, at the index each column started from
+    for (int s = 0; s < 2; ++s) {
+        const float* sb = seat_buf(cur + s);
+        for (int t = threadIdx.x; t < b * nreal; t += blockDim.x) {
+            const int c = t / nreal, i = t - c * nreal;
+            const int j = idx[(cur + s) * b + c];
+            if (j < nreal) V[(size_t)i * ldv + j] = sb[(size_t)c * col_len + npad + i];
+        }
+    }
+    if (rank == 0 && threadIdx.x == 0) {
+        *sweeps_out = sweep;
+        *status_out = 0;
+    }
+}
+
+template <int C>
+int launch_jc(nys_ctx* ctx, const double* G, int ell, int b, int max_sweeps, float* V, int ldv, int* sweeps,
+              int* status) {
+    const int npad = 2 * C * b;
+    const size_t smem = (size_t)4 * b * 2 * npad * sizeof(float) + (size_t)4 * b * (sizeof(float) + sizeof(int)) + 64;
+    if (smem > 220 * 1024) return NYS_EINVAL;
+    auto k = jacobi_cluster_kernel<C>;
+    if (C > 8) NYS_CK(ctx, cudaFuncSetAttribute(k, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
+    if (int st = smem_optin(ctx, (const void*)k, smem)) return st;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(C, 1, 1);
+    cfg.blockDim = dim3(JC_THREADS, 1, 1);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = ctx->stream;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = C;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    int clusters = 0;
+    if (cudaOccupancyMaxActiveClusters(&clusters, k, &cfg) != cudaSuccess || clusters < 1) {
+        cudaGetLastError();
+        return NYS_EINVAL;
+    }
+    NYS_CK(ctx, cudaLaunchKernelEx(&cfg, k, G, ell, b, max_sweeps, V, ldv, sweeps, status));
+    ++ctx->launches;
+    return NYS_OK;
+}
+
+}  // namespace
+
+// V (row-major, ld = ldv, float32) = eigenvectors of the symmetric ell x ell
+// float64 matrix G by the cluster kernel above; NYS_EINVAL (nothing
+// launched) when ell is outside [64, 448] or the cluster cannot be placed.
+// *status = 1 on the device if the float32 Cholesky of G fails.
+int jacobi_cluster(nys_ctx* ctx, const double* G, int ell, int max_sweeps, float* V, int ldv, int* sweeps,
+                   int* status) {
+    if (ell < 64 || ell > 448) return NYS_EINVAL;
+    if (ell <= 256) return launch_jc<8>(ctx, G, ell, (ell + 15) / 16, max_sweeps, V, ldv, sweeps, status);
+    return launch_jc<16>(ctx, G, ell, (ell + 31) / 32, max_sweeps, V, ldv, sweeps, status);
+}
+
+}  // namespace nys

@@ -21,6 +21,7 @@
 #include "chol.cuh"
 
 #include <cmath>
+#include <cstdlib>
 
 namespace nys {
 
@@ -71,21 +72,23 @@ __global__ void form_H_kernel(const double* __restrict__ G2, int ell, const doub
 }
 
 // X = C^{-1} for lower-triangular C (n x n).  Block j (one warp) solves
-// C x = e_j by forward substitution.
+// C x = e_j by forward substitution, with x in shared memory (the dependent
+// chain of the substitution stays on chip) and rows of C read coalesced;
+// column j of X is written at the end.  Dynamic shared memory: n doubles.
 __global__ void tri_inv_kernel(const double* __restrict__ C, double* __restrict__ X, int n) {
+    extern __shared__ __align__(16) double tx[];
     const int j = blockIdx.x;
     const int lane = threadIdx.x;
-    double* x = X + 0;  // column j stored at X[i * n + j]
-    for (int i = lane; i < j; i += 32) x[(size_t)i * n + j] = 0.0;
-    if (lane == 0) x[(size_t)j * n + j] = 1.0 / C[(size_t)j * n + j];
+    if (lane == 0) tx[j] = 1.0 / C[(size_t)j * n + j];
     __syncwarp();
     for (int i = j + 1; i < n; ++i) {
         double s = 0.0;
-        for (int k = j + lane; k < i; k += 32) s += C[(size_t)i * n + k] * x[(size_t)k * n + j];
+        for (int k = j + lane; k < i; k += 32) s += C[(size_t)i * n + k] * tx[k];
         s = warp_sum(s);
-        if (lane == 0) x[(size_t)i * n + j] = -s / C[(size_t)i * n + i];
+        if (lane == 0) tx[i] = -s / C[(size_t)i * n + i];
         __syncwarp();
     }
+    for (int i = lane; i < n; i += 32) X[(size_t)i * n + j] = i < j ? 0.0 : tx[i];
 }
 
 // C (m x n) = op(A) op(B) * colscale[j]  (row-major; op = transpose if flag)
@@ -669,9 +672,32 @@ int sym_eig(nys_ctx* ctx, const double* G, int ell, bool use_f32, const double* 
         NYS_CK(ctx, cudaMemsetAsync(Gw, 0, sizeof(T) * n * n, s));
         copy_pad<T><<<64, 256, 0, s>>>(G, ell, Gw, n);
         NYS_LAUNCH_CK(ctx);
-        const int max_sweeps = sizeof(T) == 8 ? 30 : 15;
+        // sweep cap: 30 (float64) or 15 (float32) unless NYS_EIG_SWEEPS sets it
+        static const int env_sweeps = [] {
+            const char* e = getenv("NYS_EIG_SWEEPS");
+            const int v = e ? atoi(e) : 0;
+            return v > 0 && v <= 100 ? v : 0;
+        }();
+        const int max_sweeps = env_sweeps ? env_sweeps : (sizeof(T) == 8 ? 30 : 15);
         const double tol = sizeof(T) == 8 ? 1e-14 : 2e-7;
         const int h = n / 2;
+        int* status_dev = sweeps_dev + 2;
+        if (sizeof(T) == 4) {
+            // float32 sketches of 64..448 columns: the cluster kernel (Cholesky
+            // and one-sided Jacobi spread over 8 or 16 SMs, V formed in place);
+            // the two-sided kernel runs instead if its Cholesky fails
+            const int stc = jacobi_cluster(ctx, G, ell, max_sweeps, (float*)V, n, sweeps_dev, status_dev);
+            if (stc == NYS_OK) {
+                jacobi_kernel<T><<<1, 1024, 0, s>>>(Gw, V, n, ell, max_sweeps, tol, sweeps_dev, status_dev);
+                NYS_LAUNCH_CK(ctx);
+                rayleigh_kernel<T><<<ell, 128, 0, s>>>(G, V, ell, n, lam);
+                NYS_LAUNCH_CK(ctx);
+                sort_eig_kernel<T><<<(ell + 127) / 128, 128, 0, s>>>(lam, V, ell, n, info, Vout, S_hat, scale);
+                NYS_LAUNCH_CK(ctx);
+                return NYS_OK;
+            }
+            if (stc != NYS_EINVAL) return stc;
+        }
         const size_t smem = sizeof(T) * ((size_t)n * (n + 1) + 2 * (size_t)h) + sizeof(int) * (2 * (size_t)n + 2 * h + 4) + 64;
         const size_t smem1 = sizeof(T) * ((size_t)n * jac_pitch(n, false) + 2 * (size_t)n) + 64;
         // both kernels of the shared-memory path must fit (leaving room for
@@ -691,7 +717,6 @@ int sym_eig(nys_ctx* ctx, const double* G, int ell, bool use_f32, const double* 
         int* rounds_dev = sweeps_dev + 1;
         // one-sided Jacobi on the Cholesky factor of G; the two-sided kernel runs
         // instead (decided on the device) if that Cholesky fails
-        int* status_dev = sweeps_dev + 2;
         if (in_smem) {
             if (int st2 = smem_optin(ctx, (const void*)jacobi_smem_kernel<T>, smem)) return st2;
             if (int st2 = smem_optin(ctx, (const void*)jacobi_1s_kernel<T, false>, smem1)) return st2;

@@ -25,8 +25,10 @@ def _operands(torch, p, q, N, seed, same=False):
 
 # (p, q, N): the ell = 200 sketch at 512 x 512, ragged K (N not a multiple of
 # the 64-pixel K block), a second M tile that is mostly padding, narrow and
-# full-width outputs, a single column
-CASES = [(200, 200, 262144), (130, 48, 5000), (64, 17, 4096), (128, 256, 8192), (1, 1, 1024), (257, 96, 2048)]
+# full-width outputs, a single column, and outputs wider than one 256-column
+# tile (two and four column tiles, rows over several 128-row tiles)
+CASES = [(200, 200, 262144), (130, 48, 5000), (64, 17, 4096), (128, 256, 8192), (1, 1, 1024), (257, 96, 2048),
+         (300, 520, 8192), (400, 400, 20000), (96, 1024, 4096)]
 
 
 @pytest.mark.parametrize("p,q,N", CASES)
@@ -48,7 +50,7 @@ def test_gram_paths_agree(env, p, q, N):
 
 
 @pytest.mark.parametrize("k,N,out", [(200, 262144, "bf16"), (48, 5000, "f32"), (17, 1024, "f32"), (256, 2048, "bf16"),
-                                     (1, 128, "f32")])
+                                     (1, 128, "f32"), (400, 16384, "f32"), (600, 4096, "bf16"), (1024, 2048, "f32")])
 def test_tall_gemm_tensor_cores_match_float64(env, k, N, out):
     # U = (Y + v Omega) W: the MN-major A operand (columns are images)
     torch, api, ctx = env
@@ -67,14 +69,18 @@ def test_tall_gemm_tensor_cores_match_float64(env, k, N, out):
     assert np.linalg.norm(U - Uc) / np.linalg.norm(ref) < tol
 
 
-def test_gram_symmetric_and_fallback(env):
+@pytest.mark.parametrize("p,N", [(40, 4096), (300, 8192), (800, 4096)])
+def test_gram_symmetric_and_fallback(env, p, N):
+    # A^T A of one operand computes only the tiles that reach the diagonal and
+    # mirrors them: the full matrix must come back, exactly symmetric
     torch, api, ctx = env
-    A, _, ref = _operands(torch, 40, 40, 4096, seed=9, same=True)
-    C = api.nys_gram(ctx, A, A, path=0).cpu().numpy()
-    assert np.allclose(C, C.T, rtol=0, atol=1e-6 * np.abs(C).max())
-    # q > 256 or N not a multiple of 8: the tensor-core path declines
+    A, _, ref = _operands(torch, p, p, N, seed=9, same=True)
+    C = api.nys_gram(ctx, A, A, path=2).cpu().numpy()
+    assert np.array_equal(C, C.T)
+    assert np.linalg.norm(C - ref) / np.linalg.norm(ref) < 1e-5
+    # N not a multiple of 8 (rows not 16-byte aligned): the tensor-core path declines
     from paper_2411_08178_gb300._abi import NYS_EINVAL, NysError
-    A2, B2, ref2 = _operands(torch, 8, 300, 1024, seed=4)
+    A2, B2, ref2 = _operands(torch, 8, 300, 1020, seed=4)
     with pytest.raises(NysError) as e:
         api.nys_gram(ctx, A2, B2, path=2)
     assert e.value.code == NYS_EINVAL

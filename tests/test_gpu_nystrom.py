@@ -116,6 +116,23 @@ def test_factor_large_ell_global_jacobi(env, dt, ell):
     _check_factor(pc.U.double().cpu().numpy(), pc.S_hat.cpu().numpy(), ref, *tol)
 
 
+@pytest.mark.parametrize("ell", [300, 520])
+def test_factor_bf16_wide_sketch_matches_oracle(env, ell):
+    # bf16 sketches wider than one 256-column tensor-core tile: the single
+    # launch of Omega^T Omega, Omega^T Y, Y^T Y and the tall U = Y_v W in
+    # column blocks, then the global-memory eigensolver, against the oracle
+    # from the same Omega at the bf16 tolerance
+    torch, api, ctx = env
+    n = 64
+    h = gaussian_kernel(9, 1.5)
+    op = api.Operator(ctx, "blur", n, n, dtype=torch.float32, kernel=h)
+    opo = O.Operator("blur", n, n, kernel=h)
+    ref = oracle.nystrom.nystrom(_flat_phi(opo, n, n), gaussian_matrix(n * n, ell, 8), EPS32)
+    Ob, Yb = api.nys_sketch(ctx, op, ell, seed=8, store_dtype=torch.bfloat16)
+    pcb = api.nys_factor(ctx, Ob, Yb, EPS32, u_dtype=torch.bfloat16)
+    _check_factor(pcb.U.double().cpu().numpy(), pcb.S_hat.cpu().numpy(), ref, 3e-2, 3e-2)
+
+
 @pytest.mark.parametrize("sd,tol", [("f32", 2e-4), ("bf16", 2e-2)])
 def test_factor_full_size_properties(env, sd, tol):
     # the 512 x 512, ell = 200, 25 x 25 sigma 4 sketch in the bench's launch
@@ -160,6 +177,35 @@ def test_not_spd_core_is_reported(env):
     torch, api, ctx = env
     from paper_2411_08178_gb300._abi import NYS_ENOTSPD, NysError
     Om = torch.from_numpy(gaussian_matrix(400, 6, 1).reshape(6, 20, 20)).cuda()
+    with pytest.raises(NysError) as e:
+        api.nys_factor(ctx, Om, -Om, EPS64)
+    assert e.value.code == NYS_ENOTSPD
+
+
+@pytest.mark.parametrize("ell", [6, 64, 200])
+def test_cholesky_retries_match_oracle(env, ell):
+    # Y = -delta Omega: the core (v - delta) Omega^T Omega is SPD only once the
+    # shift v = eps ||Omega||_F, multiplied by 10 per failure, exceeds delta.
+    # delta = 10^2.5 v0 needs three retries; the count, the final shift and the
+    # factor against the oracle's Algorithm 1 with the same retry rule.  ell =
+    # 64 and 200 run the 16-SM cluster Cholesky, ell = 6 the one-CTA kernel.
+    torch, api, ctx = env
+    n = 32
+    Om = torch.from_numpy(gaussian_matrix(n * n, ell, 11).reshape(ell, n, n)).cuda()
+    v0 = EPS64 * float(torch.linalg.norm(Om.double()))
+    delta = v0 * 10.0 ** 2.5
+    pc = api.nys_factor(ctx, Om, -delta * Om, EPS64)
+    ref = oracle.nystrom.nystrom(lambda V: -delta * V, Om.reshape(ell, -1).cpu().numpy(), EPS64)
+    assert ref["retries"] == 3 and pc.chol_retries == 3
+    assert abs(pc.v - ref["v"]) <= 1e-12 * ref["v"]
+    assert np.max(np.abs(pc.S_hat.cpu().numpy() - ref["S_hat"])) <= 1e-8 * max(ref["S_hat"][0], 1e-300) + 1e-12
+
+
+@pytest.mark.parametrize("ell", [64, 200])
+def test_not_spd_core_is_reported_on_the_cluster_path(env, ell):
+    torch, api, ctx = env
+    from paper_2411_08178_gb300._abi import NYS_ENOTSPD, NysError
+    Om = torch.from_numpy(gaussian_matrix(32 * 32, ell, 2).reshape(ell, 32, 32)).cuda()
     with pytest.raises(NysError) as e:
         api.nys_factor(ctx, Om, -Om, EPS64)
     assert e.value.code == NYS_ENOTSPD
