@@ -110,7 +110,9 @@ int nys_launch_count(const nys_ctx* ctx, int64_t* count);
  * det_spacing along (-sin, cos) on the detector; each ray is sampled by
  * Joseph's method along rows (|d_y| >= |d_x|) or columns, weight |d| / |major
  * component|.  src_dist must exceed the image half-diagonal by 2 pixels,
- * and n_angles <= 65535.  Both ray transforms need n_angles * n_bins < 2^31
+ * n_angles <= 65535, and float32 fan-beam operators take images of at most
+ * 2048 rows and columns (they evaluate sample positions in float32 split
+ * into an integer and a fraction; float64 ones in float64).  Both ray transforms need n_angles * n_bins < 2^31
  * and N = n1 * n2 < 2^31; other sizes return NYS_EINVAL.
  * Blur: (Hx)[i,j] = sum_ab kernel[a*kw+b] x[(i+a-(kh-1)/2) mod n1,
  * (j+b-(kw-1)/2) mod n2]; kh, kw odd.  Decimation keeps pixels (d i, d j).

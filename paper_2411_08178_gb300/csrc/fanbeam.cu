@@ -10,9 +10,18 @@
 // weight |d|/|d_x|; linear interpolation between floor(u) and floor(u) + 1,
 // zero outside.  Pixel (i, j) sits at (j - c2, i - c1).
 //
-// The per-ray a, b are float64 (a host table), and both kernels evaluate
-// u = fma(b, l, a) in float64, so the adjoint's interpolation weights are
-// exactly the forward's.  Forward: one thread per ray, stepping its lines.
+// The per-ray a, b come from a host table.  Float64 operators evaluate
+// u = fma(b, l, a) in float64.  Float32 operators evaluate the same position
+// split into an integer and a fraction, in float32 only (GB300's float64 pipe
+// is a small fraction of its float32 one): about the middle line l0 of the
+// ray, u = ai + af + b (l - l0) with ai an integer and af in [0, 1) (from
+// float64 on the host), b = bhi + blo with bhi on a 2^-12 grid, so that
+// bhi (l - l0) is exact in float32 for images up to 2048 lines; the integer
+// part of bhi (l - l0) is split off exactly and the rest, af + frac + blo
+// (l - l0), stays below 3 in magnitude, so the fraction is good to about
+// 1e-7.  Either way both kernels evaluate the same expression, so the
+// adjoint's interpolation weights are exactly the forward's.
+// Forward: one thread per ray, stepping its lines.
 // Adjoint: one thread per pixel gathering, angle by angle, the rays whose
 // sample on the pixel's row (row-step rays) or column (column-step rays)
 // lies within one pixel of it -- bins between those of the rays through the
@@ -34,13 +43,38 @@ struct FanTab {
     const double* w;       // [n_angles][n_bins]
     const int* rs;         // [n_angles][n_bins] row-step flag
     const float* ang;      // [n_angles][4]: S_x, S_y, cos, sin
+    const float4* split;   // [n_angles][n_bins]: (ai as an integer value, af, bhi, blo) about l0
     float D, du, cb;
+    int l0r, l0c;          // middle line of row-step (n1 / 2) and column-step (n2 / 2) rays
 };
 
 __device__ __forceinline__ int floor_clamped(double u, double& f) {
     const double fl = floor(fmin(fmax(u, -1.0e9), 1.0e9));
     f = u - fl;
     return (int)fl;
+}
+
+// position of ray `ray` on line l: integer part (returned) and fraction f.
+// float64 operators: fma(b, l, a) in float64; float32 operators: the split
+// float32 evaluation described above.  The forward and the adjoint call this
+// same function, so both take the same floor and the same weights.
+template <class TC>
+__device__ __forceinline__ int fan_pos(const FanTab& tab, int ray, int rs, int l, TC& f);
+template <>
+__device__ __forceinline__ int fan_pos<double>(const FanTab& tab, int ray, int rs, int l, double& f) {
+    return floor_clamped(fma(tab.b[ray], (double)l, tab.a[ray]), f);
+}
+template <>
+__device__ __forceinline__ int fan_pos<float>(const FanTab& tab, int ray, int rs, int l, float& f) {
+    const float4 sp = tab.split[ray];
+    const float k = (float)(l - (rs ? tab.l0r : tab.l0c));
+    const float t = sp.z * k;                 // exact: bhi on a 2^-12 grid, |k| <= 1024
+    const float ft = floorf(t);
+    const float fr = fmaf(sp.w, k, sp.y + (t - ft));
+    const float ff = floorf(fr);
+    f = fr - ff;
+    const float ip = sp.x + ft + ff;          // an integer below 2^24 in magnitude: exact
+    return (int)fminf(fmaxf(ip, -1.0e9f), 1.0e9f);
 }
 
 template <class TI, class TO, class TC>
@@ -52,14 +86,15 @@ __global__ void __launch_bounds__(256) fan_fwd_kernel(const TI* __restrict__ x, 
     if (m >= n_bins) return;
     const int ray = k * n_bins + m;
     const int rs = tab.rs[ray];
-    const double a = tab.a[ray], s = tab.b[ray];
+    const double a = 0.0, s = 0.0;
     const int nl = rs ? n1 : n2, na = rs ? n2 : n1;
     const TI* xb = x + (size_t)b * n1 * n2;
     TC acc = TC(0);
+    (void)a;
+    (void)s;
     for (int l = 0; l < nl; ++l) {
-        double fd;
-        const int lo = floor_clamped(fma(s, (double)l, a), fd);
-        const TC f = (TC)fd;
+        TC f;
+        const int lo = fan_pos<TC>(tab, ray, rs, l, f);
         TC v0 = TC(0), v1 = TC(0);
         if ((unsigned)lo < (unsigned)na) v0 = (TC)ldf(xb + (rs ? (size_t)l * n2 + lo : (size_t)lo * n2 + l));
         if ((unsigned)(lo + 1) < (unsigned)na)
@@ -115,11 +150,11 @@ __global__ void __launch_bounds__(256) fan_adj_kernel(const TI* __restrict__ s, 
             for (int m = mlo; m <= mhi; ++m) {
                 const int ray = k * n_bins + m;
                 if (tab.rs[ray] != (kind == 0)) continue;
-                double fd;
-                const int lo = floor_clamped(fma(tab.b[ray], (double)l, tab.a[ray]), fd);
+                TC fd;
+                const int lo = fan_pos<TC>(tab, ray, kind == 0, l, fd);
                 TC wgt;
-                if (lo == p) wgt = TC(1) - (TC)fd;
-                else if (lo + 1 == p) wgt = (TC)fd;
+                if (lo == p) wgt = TC(1) - fd;
+                else if (lo + 1 == p) wgt = fd;
                 else continue;
                 part = fma((TC)tab.w[ray] * wgt, (TC)ldf(sb + (size_t)ray), part);
             }
@@ -127,6 +162,15 @@ __global__ void __launch_bounds__(256) fan_adj_kernel(const TI* __restrict__ s, 
         acc += part;
     }
     stf(x + (size_t)b * N + t, acc);
+}
+
+// byte offset of the float4 split table in op->rtab: after a, b, w (doubles),
+// the row-step flags and the per-angle floats, rounded up to 16 bytes
+size_t fan_split_offset(const nys_op* op) {
+    const size_t R = (size_t)op->n_angles * op->n_bins;
+    const size_t off = 3 * R * sizeof(double) + ((R + 3) & ~size_t(3)) * sizeof(int) +
+                       (((size_t)op->n_angles * 4 + 3) & ~size_t(3)) * sizeof(float);
+    return (off + 15) & ~size_t(15);
 }
 
 FanTab fan_tab(const nys_op* op) {
@@ -138,6 +182,9 @@ FanTab fan_tab(const nys_op* op) {
     t.w = t.b + R;
     t.rs = (const int*)(t.w + R);
     t.ang = (const float*)(t.rs + ((R + 3) & ~size_t(3)));
+    t.split = (const float4*)(base + fan_split_offset(op));
+    t.l0r = op->n1 / 2;
+    t.l0c = op->n2 / 2;
     t.D = (float)op->det_dist;
     t.du = (float)op->det_spacing;
     t.cb = 0.5f * (float)(op->n_bins - 1);
@@ -186,12 +233,16 @@ int fan_typed(nys_op* op, int which, const void* x, void* y, int batch) {
 
 int fanbeam_setup(nys_op* op) {
     const int A = op->n_angles, B = op->n_bins, n1 = op->n1, n2 = op->n2;
+    if (op->dtype != NYS_F64 && std::max(n1, n2) > 2048)
+        return fail(op->ctx, NYS_EINVAL, "fan beam: float32 operators take images of at most 2048 lines");
     const double c1 = (n1 - 1) / 2.0, c2 = (n2 - 1) / 2.0, cb = (B - 1) / 2.0;
     const double R = op->src_dist, D = op->det_dist, du = op->det_spacing;
     const size_t RA = (size_t)A * B;
     std::vector<double> a(RA), bb(RA), w(RA);
     std::vector<int> rs((RA + 3) & ~size_t(3), 0);
     std::vector<float> ang((size_t)A * 4);
+    std::vector<float> split(4 * RA);
+    const int l0r = n1 / 2, l0c = n2 / 2;
     for (int k = 0; k < A; ++k) {
         const double th = k * (op->span / A);
         const double cs = std::cos(th), sn = std::sin(th);
@@ -211,9 +262,18 @@ int fanbeam_setup(nys_op* op) {
             a[r] = row ? Sx - (c1 + Sy) * bb[r] + c2 : Sy - (c2 + Sx) * bb[r] + c1;
             w[r] = nd / std::fabs(major);
             rs[r] = row ? 1 : 0;
+            // float32 split about the middle line (see the header comment)
+            const double bhi = std::nearbyint(bb[r] * 4096.0) / 4096.0;
+            const double am = a[r] + bb[r] * (row ? l0r : l0c);
+            const double ai = std::floor(am);
+            split[4 * r] = (float)ai;
+            split[4 * r + 1] = (float)(am - ai);
+            split[4 * r + 2] = (float)bhi;
+            split[4 * r + 3] = (float)(bb[r] - bhi);
         }
     }
-    const size_t bytes = 3 * RA * sizeof(double) + rs.size() * sizeof(int) + ang.size() * sizeof(float);
+    const size_t split_off = fan_split_offset(op);
+    const size_t bytes = split_off + split.size() * sizeof(float);
     NYS_CK(op->ctx, cudaMalloc(&op->rtab, bytes));
     char* p = (char*)op->rtab;
     NYS_CK(op->ctx, cudaMemcpy(p, a.data(), RA * sizeof(double), cudaMemcpyHostToDevice));
@@ -223,6 +283,7 @@ int fanbeam_setup(nys_op* op) {
                                cudaMemcpyHostToDevice));
     NYS_CK(op->ctx, cudaMemcpy(p + 3 * RA * sizeof(double) + rs.size() * sizeof(int), ang.data(),
                                ang.size() * sizeof(float), cudaMemcpyHostToDevice));
+    NYS_CK(op->ctx, cudaMemcpy(p + split_off, split.data(), split.size() * sizeof(float), cudaMemcpyHostToDevice));
     op->chunk = 32;
     NYS_CK(op->ctx, cudaMalloc(&op->inter, (size_t)op->chunk * op->M * dtype_size(op->dtype)));
     return NYS_OK;

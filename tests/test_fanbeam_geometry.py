@@ -123,3 +123,39 @@ def test_fanbeam_adjoint_candidates_at_the_measured_size():
     assert worst_bin <= 0.25 * MARGIN_BINS, worst_bin
     assert worst_kind <= 0.5, worst_kind
     assert min_depth > 1.0, min_depth
+
+
+def split_positions(a, b, row, n1, n2):
+    """The float32 operators' positions, restated in numpy float32 from the
+    host's split (integer + fraction about the middle line l0, b = bhi + blo
+    with bhi on a 2^-12 grid): returns (integer part, fraction) of every ray on
+    every line l < max(n1, n2) (lines past a ray's own count are ignored)."""
+    L = max(n1, n2)
+    l0 = np.where(row, n1 // 2, n2 // 2)
+    bhi = np.round(b * 4096.0) / 4096.0
+    am = a + b * l0
+    ai = np.floor(am)
+    sp_x, sp_y = ai.astype(np.float32), (am - ai).astype(np.float32)
+    sp_z, sp_w = bhi.astype(np.float32), (b - bhi).astype(np.float32)
+    k = (np.arange(L)[None, None, :] - l0[..., None]).astype(np.float32)
+    t = sp_z[..., None] * k
+    ft = np.floor(t)
+    fr = (sp_w[..., None] * k).astype(np.float64) + (sp_y[..., None] + (t - ft)).astype(np.float64)
+    fr = fr.astype(np.float32)   # a fused multiply-add rounds once: emulate it in float64, round at the end
+    ff = np.floor(fr)
+    return (sp_x[..., None] + ft + ff).astype(np.float64), (fr - ff).astype(np.float64)
+
+
+@pytest.mark.parametrize("geom", [(24, 24, 9, 40, 30.0, 60.0, 1.0), (20, 28, 7, 47, 30.0, 60.0, 1.0),
+                                  (512, 512, 24, 1024, 1000.0, 2000.0, 1.0)])
+def test_float32_split_positions_match_float64(geom):
+    # the float32 evaluation agrees with u = a + b l to 1e-6 of a pixel, so
+    # its interpolation weights agree with the float64 (oracle) ones to 1e-6
+    n1, n2, A, B, R, D, du = geom
+    a, b, row, _ = tables(n1, n2, A, B, R, D, du)
+    ip, fr = split_positions(a, b, row, n1, n2)
+    L = max(n1, n2)
+    u = a[..., None] + b[..., None] * np.arange(L)[None, None, :]
+    err = np.abs((ip + fr) - u)
+    assert err.max() < 1e-6, err.max()
+    assert np.all((fr >= 0.0) & (fr < 1.0))
