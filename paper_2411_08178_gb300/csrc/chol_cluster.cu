@@ -84,24 +84,29 @@ __global__ void __launch_bounds__(CH_THREADS, 1)
             const int oseat = k < CC ? 0 : 1;
             const int p0 = k * b;
             if (rank == owner) {
-                for (int t = 0; t < b; ++t) {
-                    const int r = p0 + t;
-                    if (threadIdx.x == 0) {
-                        const double d = col(oseat, t)[r];
-                        if (!(d > 0.0) || !isfinite(d)) bad_flag = 1;
-                        else col(oseat, t)[r] = sqrt(d);
+                // the b x b diagonal block by one warp (b <= 16: warp barriers only)
+                const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+                if (warp == 0) {
+                    for (int t = 0; t < b; ++t) {
+                        const int r = p0 + t;
+                        if (lane == 0) {
+                            const double d = col(oseat, t)[r];
+                            if (!(d > 0.0) || !isfinite(d)) bad_flag = 1;
+                            else col(oseat, t)[r] = sqrt(d);
+                        }
+                        __syncwarp();
+                        if (bad_flag) break;
+                        const double rtt = col(oseat, t)[r];
+                        for (int c = t + 1 + lane; c < b; c += 32) col(oseat, c)[r] /= rtt;
+                        __syncwarp();
+                        for (int e = lane; e < b * b; e += 32) {
+                            const int c = e / b, i = p0 + e - c * b;
+                            if (c > t && i > r && i <= p0 + c) col(oseat, c)[i] -= col(oseat, i - p0)[r] * col(oseat, c)[r];
+                        }
+                        __syncwarp();
                     }
-                    __syncthreads();
-                    if (bad_flag) break;
-                    const double rtt = col(oseat, t)[r];
-                    for (int c = t + 1 + threadIdx.x; c < b; c += blockDim.x) col(oseat, c)[r] /= rtt;
-                    __syncthreads();
-                    for (int e = threadIdx.x; e < b * b; e += blockDim.x) {
-                        const int c = e / b, i = p0 + e - c * b;
-                        if (c > t && i > r && i <= p0 + c) col(oseat, c)[i] -= col(oseat, i - p0)[r] * col(oseat, c)[r];
-                    }
-                    __syncthreads();
                 }
+                __syncthreads();
                 if (bad_flag && threadIdx.x < CC) *cluster.map_shared_rank(&bad_flag, (int)threadIdx.x) = 1;
             }
             cluster.sync();
@@ -117,14 +122,18 @@ __global__ void __launch_bounds__(CH_THREADS, 1)
                 }
             }
             __syncthreads();
-            for (int s = 0; s < 2; ++s) {
-                if (blk[s] <= k) continue;
-                for (int c = threadIdx.x; c < b; c += blockDim.x) {
+            {
+                // forward substitution, one warp per column, lanes over the b <= 16 terms
+                const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+                for (int q2 = warp; q2 < 2 * b; q2 += CH_THREADS / 32) {
+                    const int s = q2 / b, c = q2 - s * b;
+                    if (blk[s] <= k) continue;
                     double* cc = col(s, c);
                     for (int i = 0; i < b; ++i) {
-                        double x = cc[p0 + i];
-                        for (int q = 0; q < i; ++q) x -= stage[i * b + q] * cc[p0 + q];
-                        cc[p0 + i] = x / stage[i * b + i];
+                        double x = lane < i ? stage[i * b + lane] * cc[p0 + lane] : 0.0;
+                        x = warp_sum(x);
+                        if (lane == 0) cc[p0 + i] = (cc[p0 + i] - x) / stage[i * b + i];
+                        __syncwarp();
                     }
                 }
             }

@@ -261,8 +261,14 @@ __global__ void __launch_bounds__(256) gram_tiles_reduce_kernel(const float* __r
         const int c = e / TC_BM, r = e - c * TC_BM;
         const int i = tl.y + r, j = tl.z + c;
         if (i >= p || j >= q || (sym && j < i)) continue;
-        double s = 0.0;
-        for (int z = 0; z < splits; ++z) s += (double)base[(size_t)z * stride + e];
+        // four independent partial sums (loads in flight), combined in a fixed order
+        double s4[4] = {0.0, 0.0, 0.0, 0.0};
+        int z = 0;
+        for (; z + 4 <= splits; z += 4)
+#pragma unroll
+            for (int u = 0; u < 4; ++u) s4[u] += (double)base[(size_t)(z + u) * stride + e];
+        for (; z < splits; ++z) s4[0] += (double)base[(size_t)z * stride + e];
+        const double s = (s4[0] + s4[1]) + (s4[2] + s4[3]);
         C[(size_t)i * ldc + j] = s;
         if (sym) C[(size_t)j * ldc + i] = s;
     }

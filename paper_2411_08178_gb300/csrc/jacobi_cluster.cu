@@ -82,27 +82,31 @@ __global__ void __launch_bounds__(JC_THREADS, 1)
         const int oseat = k < C ? 0 : 1;
         const int p0 = k * b;                      // first column (and row) of the panel
         if (rank == owner) {
-            float* pb = seat_buf(oseat);
-            for (int t = 0; t < b; ++t) {
-                const int r = p0 + t;
-                if (threadIdx.x == 0) {
-                    const float d = pb[(size_t)t * col_len + r];
-                    if (!(d > 0.0f)) bad_flag = 1;
-                    else pb[(size_t)t * col_len + r] = sqrtf(d);
+            // the b x b diagonal block by one warp (b <= 16: warp barriers only)
+            if (warp == 0) {
+                float* pb = seat_buf(oseat);
+                for (int t = 0; t < b; ++t) {
+                    const int r = p0 + t;
+                    if (lane == 0) {
+                        const float d = pb[(size_t)t * col_len + r];
+                        if (!(d > 0.0f)) bad_flag = 1;
+                        else pb[(size_t)t * col_len + r] = sqrtf(d);
+                    }
+                    __syncwarp();
+                    if (bad_flag) break;
+                    const float rtt = pb[(size_t)t * col_len + r];
+                    for (int c = t + 1 + lane; c < b; c += 32) pb[(size_t)c * col_len + r] /= rtt;
+                    __syncwarp();
+                    // rows r+1.. of the later panel columns: R(i, c) -= R(r, i) R(r, c), r < i <= p0 + c
+                    for (int e = lane; e < b * b; e += 32) {
+                        const int c = e / b, i = p0 + e - (e / b) * b;
+                        if (c > t && i > r && i <= p0 + c)
+                            pb[(size_t)c * col_len + i] -= pb[(size_t)(i - p0) * col_len + r] * pb[(size_t)c * col_len + r];
+                    }
+                    __syncwarp();
                 }
-                __syncthreads();
-                if (bad_flag) break;
-                const float rtt = pb[(size_t)t * col_len + r];
-                for (int c = t + 1 + threadIdx.x; c < b; c += blockDim.x) pb[(size_t)c * col_len + r] /= rtt;
-                __syncthreads();
-                // update rows r+1.. of the later panel columns: R(i, c) -= R(r, i) R(r, c), r < i <= p0 + c
-                for (int e = threadIdx.x; e < b * b; e += blockDim.x) {
-                    const int c = e / b, i = p0 + e - (e / b) * b;
-                    if (c > t && i > r && i <= p0 + c)
-                        pb[(size_t)c * col_len + i] -= pb[(size_t)(i - p0) * col_len + r] * pb[(size_t)c * col_len + r];
-                }
-                __syncthreads();
             }
+            __syncthreads();
             // a failed pivot: tell every CTA (their own copy of the flag), so
             // that all leave after the same barrier and no CTA reads the
             // shared memory of one that has left
@@ -122,17 +126,17 @@ __global__ void __launch_bounds__(JC_THREADS, 1)
             }
         }
         __syncthreads();
-        // rows of the panel in my later columns: solve R_PP^T x = g (forward substitution)
-        for (int s = 0; s < 2; ++s) {
+        // rows of the panel in my later columns: solve R_PP^T x = g (forward
+        // substitution), one warp per column, lanes over the b <= 16 terms
+        for (int cc = warp; cc < 2 * b; cc += JC_THREADS / 32) {
+            const int s = cc / b, c = cc - s * b;
             if (blk[s] <= k) continue;
-            float* sb = seat_buf(s);
-            for (int c = threadIdx.x; c < b; c += blockDim.x) {
-                float* col = sb + (size_t)c * col_len;
-                for (int i = 0; i < b; ++i) {
-                    float v = col[p0 + i];
-                    for (int q = 0; q < i; ++q) v -= stage[i * b + q] * col[p0 + q];
-                    col[p0 + i] = v / stage[i * b + i];
-                }
+            float* col = seat_buf(s) + (size_t)c * col_len;
+            for (int i = 0; i < b; ++i) {
+                float v = lane < i ? stage[i * b + lane] * col[p0 + lane] : 0.0f;
+                v = warp_sum(v);
+                if (lane == 0) col[p0 + i] = (col[p0 + i] - v) / stage[i * b + i];
+                __syncwarp();
             }
         }
         cluster.sync();
