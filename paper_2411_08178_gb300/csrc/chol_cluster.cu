@@ -122,19 +122,16 @@ __global__ void __launch_bounds__(CH_THREADS, 1)
                 }
             }
             __syncthreads();
-            {
-                // forward substitution, one warp per column, lanes over the b <= 16 terms
-                const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-                for (int q2 = warp; q2 < 2 * b; q2 += CH_THREADS / 32) {
-                    const int s = q2 / b, c = q2 - s * b;
-                    if (blk[s] <= k) continue;
-                    double* cc = col(s, c);
-                    for (int i = 0; i < b; ++i) {
-                        double x = lane < i ? stage[i * b + lane] * cc[p0 + lane] : 0.0;
-                        x = warp_sum(x);
-                        if (lane == 0) cc[p0 + i] = (cc[p0 + i] - x) / stage[i * b + i];
-                        __syncwarp();
-                    }
+            // forward substitution, one thread per column (a chain of b^2 / 2
+            // FMAs is shorter than b rounds of float64 warp reductions)
+            for (int q2 = threadIdx.x; q2 < 2 * b; q2 += blockDim.x) {
+                const int s = q2 / b, c = q2 - s * b;
+                if (blk[s] <= k) continue;
+                double* cc = col(s, c);
+                for (int i = 0; i < b; ++i) {
+                    double x = cc[p0 + i];
+                    for (int q = 0; q < i; ++q) x -= stage[i * b + q] * cc[p0 + q];
+                    cc[p0 + i] = x / stage[i * b + i];
                 }
             }
             cluster.sync();

@@ -127,16 +127,16 @@ __global__ void __launch_bounds__(JC_THREADS, 1)
         }
         __syncthreads();
         // rows of the panel in my later columns: solve R_PP^T x = g (forward
-        // substitution), one warp per column, lanes over the b <= 16 terms
-        for (int cc = warp; cc < 2 * b; cc += JC_THREADS / 32) {
+        // substitution), one thread per column (a chain of b^2 / 2 FMAs is
+        // shorter than b rounds of warp reductions)
+        for (int cc = threadIdx.x; cc < 2 * b; cc += blockDim.x) {
             const int s = cc / b, c = cc - s * b;
             if (blk[s] <= k) continue;
             float* col = seat_buf(s) + (size_t)c * col_len;
             for (int i = 0; i < b; ++i) {
-                float v = lane < i ? stage[i * b + lane] * col[p0 + lane] : 0.0f;
-                v = warp_sum(v);
-                if (lane == 0) col[p0 + i] = (col[p0 + i] - v) / stage[i * b + i];
-                __syncwarp();
+                float v = col[p0 + i];
+                for (int q = 0; q < i; ++q) v -= stage[i * b + q] * col[p0 + q];
+                col[p0 + i] = v / stage[i * b + i];
             }
         }
         cluster.sync();
@@ -188,27 +188,48 @@ __global__ void __launch_bounds__(JC_THREADS, 1)
     // ------------------------------------------------------------ sweeps --
     const float tol = 1.2e-7f * sqrtf((float)npad);
     const int nv = npad / 4;                       // float4 vectors per R part
+    // one warp rotates columns x and y: c = x . y over the R parts, then the
+    // plane rotation of both parts.  Every lane holds its share of both
+    // columns (R and V parts, at most NVL 16-byte vectors of each) in
+    // registers from the first load to the store, so the chain is one
+    // load, the dot product, the rotation's parameters and one store.
+    constexpr int NVL = C / 4;   // npad = 2 C b <= 32 C floats per part: 8 C vectors over 32 lanes
     auto rotate_pair = [&](float* x, float* y, float* na, float* nb_, int ix, int iy) -> bool {
-        // one warp: c = x . y over the R parts, then the plane rotation of both parts
-        const float4* xv = reinterpret_cast<const float4*>(x);
-        const float4* yv = reinterpret_cast<const float4*>(y);
-        float c = 0.0f;
-        for (int v = lane; v < nv; v += 32) {
-            const float4 p = xv[v], q = yv[v];
-            c += p.x * q.x + p.y * q.y + p.z * q.z + p.w * q.w;
-        }
-        c = warp_sum(c);
-        const float a = *na, bb = *nb_;
-        if (ix >= nreal || iy >= nreal || c == 0.0f || !(fabsf(c) > tol * sqrtf(a * bb))) return false;
-        const float zeta = (bb - a) / (2.0f * c);
-        const float t = (zeta >= 0.0f ? 1.0f : -1.0f) / (fabsf(zeta) + sqrtf(1.0f + zeta * zeta));
-        const float cs = 1.0f / sqrtf(1.0f + t * t), sn = t * cs;
         float4* xw = reinterpret_cast<float4*>(x);
         float4* yw = reinterpret_cast<float4*>(y);
-        for (int v = lane; v < 2 * nv; v += 32) {
-            const float4 p = xw[v], q = yw[v];
-            xw[v] = make_float4(cs * p.x - sn * q.x, cs * p.y - sn * q.y, cs * p.z - sn * q.z, cs * p.w - sn * q.w);
-            yw[v] = make_float4(sn * p.x + cs * q.x, sn * p.y + cs * q.y, sn * p.z + cs * q.z, sn * p.w + cs * q.w);
+        const float a = *na, bb = *nb_;
+        float4 px[NVL], qy[NVL], vx[NVL], vy[NVL];
+        float c = 0.0f;
+#pragma unroll
+        for (int u = 0; u < NVL; ++u) {
+            const int v = lane + 32 * u;
+            if (v < nv) {
+                px[u] = xw[v], qy[u] = yw[v], vx[u] = xw[nv + v], vy[u] = yw[nv + v];
+            } else {
+                px[u] = qy[u] = vx[u] = vy[u] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+            }
+            c += px[u].x * qy[u].x + px[u].y * qy[u].y + px[u].z * qy[u].z + px[u].w * qy[u].w;
+        }
+        c = warp_sum(c);
+        if (ix >= nreal || iy >= nreal || c == 0.0f || !(fabsf(c) > tol * sqrtf(a * bb))) return false;
+        // t = sign(zeta) / (|zeta| + sqrt(1 + zeta^2)), the smaller root of t^2 + 2 zeta t - 1 = 0
+        const float zeta = __fdividef(bb - a, 2.0f * c);
+        const float t = __fdividef(zeta >= 0.0f ? 1.0f : -1.0f, fabsf(zeta) + sqrtf(fmaf(zeta, zeta, 1.0f)));
+        const float cs = rsqrtf(fmaf(t, t, 1.0f)), sn = t * cs;
+        auto rot = [&](const float4& p, const float4& q, float4& o1, float4& o2) {
+            o1 = make_float4(cs * p.x - sn * q.x, cs * p.y - sn * q.y, cs * p.z - sn * q.z, cs * p.w - sn * q.w);
+            o2 = make_float4(sn * p.x + cs * q.x, sn * p.y + cs * q.y, sn * p.z + cs * q.z, sn * p.w + cs * q.w);
+        };
+#pragma unroll
+        for (int u = 0; u < NVL; ++u) {
+            const int v = lane + 32 * u;
+            if (v < nv) {
+                float4 o1, o2;
+                rot(px[u], qy[u], o1, o2);
+                xw[v] = o1, yw[v] = o2;
+                rot(vx[u], vy[u], o1, o2);
+                xw[nv + v] = o1, yw[nv + v] = o2;
+            }
         }
         __syncwarp();
         if (lane == 0) {
@@ -286,7 +307,21 @@ __global__ void __launch_bounds__(JC_THREADS, 1)
                 const int* si = cluster.map_shared_rank(idx + (cur + src_s) * b, src_rank);
                 float4* dst = reinterpret_cast<float4*>(seat_buf(nxt + s));
                 const float4* src = reinterpret_cast<const float4*>(sb);
-                for (int v = threadIdx.x; v < slot_len / 4; v += blockDim.x) dst[v] = src[v];
+                // four remote loads in flight per thread before the stores
+                const int nvec = slot_len / 4;
+                for (int v0 = threadIdx.x; v0 < nvec; v0 += 4 * JC_THREADS) {
+                    float4 t4[4];
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) {
+                        const int v = v0 + u * JC_THREADS;
+                        if (v < nvec) t4[u] = src[v];
+                    }
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) {
+                        const int v = v0 + u * JC_THREADS;
+                        if (v < nvec) dst[v] = t4[u];
+                    }
+                }
                 for (int c = threadIdx.x; c < b; c += blockDim.x) {
                     nrm[(nxt + s) * b + c] = sn[c];
                     idx[(nxt + s) * b + c] = si[c];
