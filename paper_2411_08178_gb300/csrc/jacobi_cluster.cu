@@ -187,6 +187,7 @@ __global__ void __launch_bounds__(JC_THREADS, 1)
 
     // ------------------------------------------------------------ sweeps --
     const float tol = 1.2e-7f * sqrtf((float)npad);
+    const float tol2 = tol * tol;
     const int nv = npad / 4;                       // float4 vectors per R part
     // one warp rotates columns x and y: c = x . y over the R parts, then the
     // plane rotation of both parts.  Every lane holds its share of both
@@ -211,10 +212,12 @@ __global__ void __launch_bounds__(JC_THREADS, 1)
             c += px[u].x * qy[u].x + px[u].y * qy[u].y + px[u].z * qy[u].z + px[u].w * qy[u].w;
         }
         c = warp_sum(c);
-        if (ix >= nreal || iy >= nreal || c == 0.0f || !(fabsf(c) > tol * sqrtf(a * bb))) return false;
-        // t = sign(zeta) / (|zeta| + sqrt(1 + zeta^2)), the smaller root of t^2 + 2 zeta t - 1 = 0
-        const float zeta = __fdividef(bb - a, 2.0f * c);
-        const float t = __fdividef(zeta >= 0.0f ? 1.0f : -1.0f, fabsf(zeta) + sqrtf(fmaf(zeta, zeta, 1.0f)));
+        if (ix >= nreal || iy >= nreal || c == 0.0f || !(c * c > tol2 * (a * bb))) return false;
+        // t = sign(zeta) / (|zeta| + sqrt(1 + zeta^2)) with zeta = (bb - a) / (2c), the
+        // smaller root of t^2 + 2 zeta t - 1 = 0, written as 2c sign(d) / (|d| + sqrt(d^2 + 4c^2)),
+        // d = bb - a: three dependent special-function operations instead of four
+        const float d = bb - a;
+        const float t = __fdividef(d >= 0.0f ? 2.0f * c : -2.0f * c, fabsf(d) + sqrtf(fmaf(d, d, 4.0f * c * c)));
         const float cs = rsqrtf(fmaf(t, t, 1.0f)), sn = t * cs;
         auto rot = [&](const float4& p, const float4& q, float4& o1, float4& o2) {
             o1 = make_float4(cs * p.x - sn * q.x, cs * p.y - sn * q.y, cs * p.z - sn * q.z, cs * p.w - sn * q.w);
@@ -288,7 +291,7 @@ __global__ void __launch_bounds__(JC_THREADS, 1)
             // pairs between the two blocks: (X_i, Y_(i + r) mod b)
             for (int r = 0; r < b; ++r) {
                 if (warp < b) {
-                    const int i = warp, j = (warp + r) % b;
+                    const int i = warp, j = warp + r < b ? warp + r : warp + r - b;
                     rotated |= rotate_pair(X + (size_t)i * col_len, Y + (size_t)j * col_len, nX + i, nY + j, iX[i],
                                            iY[j]);
                 }
