@@ -292,6 +292,62 @@ class Native:
             del Om, Y
         return out
 
+    def ell_rule(self, ells, k_plain=None):
+        """A sketch-size rule from one sketch (the paper fixes K by hand after
+        a study of L_f^P ||x^1 - x*||_P^2 against K, Sec. IV-C).
+
+        One sketch at the largest candidate gives every smaller sketch too
+        (the first ell columns of Omega and Y are the ell-column sketch: the
+        probe generator is indexed by column).  For each candidate: the
+        factor of the first ell columns, the step-size estimate L(ell) = 1 /
+        alpha (50 power steps on P^{-1} A^T A) and the measured time of one
+        WAPG iteration t(ell).  With the distance term of the accelerated
+        rate held fixed, the iterations to a given accuracy scale like
+        sqrt(L); the rule picks the ell with the least sqrt(L(ell)/L(0)) t(ell),
+        the time per unit of progress (plain APG: ell = 0).  It needs no x*
+        and no solve; `k_pred` is the plain count k_plain scaled by the same
+        ratio, for comparison with the measured counts."""
+        torch, api, w = self.torch, self.api, self.w
+        ells = sorted(set(int(e) for e in ells))
+        stream = torch.cuda.current_stream(self.dev)
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        Om = torch.empty((ells[-1], w.n, w.n), dtype=self.sd, device=self.dev)
+        Y = torch.empty_like(Om)
+        api.nys_sketch(self.ctx, self.op, ells[-1], w.seed_omega, store_dtype=self.sd, out=(Om, Y))
+        b.record(stream)
+        torch.cuda.synchronize(self.dev)
+        sketch_ms = a.elapsed_time(b)
+
+        def per_iter(sol, n=20):
+            sol.restart(False)
+            sol.step(3)
+            return self._events_ms(lambda: sol.step(n), 1) / n
+
+        L0 = 1.0 / self.solver_0.alpha
+        t0 = per_iter(self.solver_0)
+        rows = [{"ell": 0, "L": L0, "rate_ratio": 1.0, "ms_per_iter": round(t0, 4), "score": round(t0, 4),
+                 "k_pred": k_plain}]
+        for ell in ells:
+            pc = api.Precond(self.ctx, w.n * w.n, ell, self.sd)
+            api.nys_factor(self.ctx, Om[:ell], Y[:ell], EPS32, pc=pc)
+            if not self.sqrt_shift:
+                pc.setup(0.0, False)
+            sol = api.Solver(self.ctx, self.op, self.y, w.reg, w.lam, pc=pc, **self.kw)
+            L = 1.0 / sol.alpha
+            t = per_iter(sol)
+            r = math.sqrt(L / L0)
+            rows.append({"ell": ell, "active_columns": pc.ell_active, "L": L, "rate_ratio": round(r, 4),
+                         "ms_per_iter": round(t, 4), "score": round(r * t, 4),
+                         "k_pred": round(k_plain * r) if k_plain else None})
+            sol.close()
+            pc.close()
+        del Om, Y
+        best = min(rows, key=lambda q: q["score"])
+        return {"rule": "argmin over ell of sqrt(L(ell) / L(0)) x (ms per WAPG iteration); ell = 0 is plain APG",
+                "sketch_ms_at_largest": round(sketch_ms, 3), "candidates": rows, "chosen_ell": best["ell"]}
+
     def time_loop(self, fn, steps, warmup, tag="timed"):
         torch = self.torch
         stream = torch.cuda.current_stream(self.dev)
@@ -488,8 +544,12 @@ def run_native(args, w: WL.Workload):
              "what": "C = L ||x^1 - x*||_P^2 (x^1 = 0, L = 1/alpha); F(x^k) - F* <= 2C/(k+1)^2 reaches the target at "
                      "k_bound"}
     sweep = None
+    rule = None
     if args.ell_sweep:
         sweep = nb.ell_sweep([int(e) for e in args.ell_sweep.split(",")], xstar, Fstar, kmax, args.sweep_steps, 1)
+        rule = nb.ell_rule([int(e) for e in args.ell_sweep.split(",")] + [w.ell], k_0)
+        measured = [(w.ell, ms_p)] + [(q["ell"], q["ms"]) for q in sweep] + [(0, ms_0)]
+        rule["measured_best_ell"] = min(measured, key=lambda m: m[1])[0]
     others = {}
     if not args.no_others:
         nb.close()
@@ -545,6 +605,7 @@ def run_native(args, w: WL.Workload):
     }
     if sweep is not None:
         out["ell_sweep"] = sweep
+        out["ell_rule"] = rule
     if others:
         out["other_workloads"] = others
     if rank == 0:
