@@ -51,8 +51,7 @@ TARGET = 1e-3
 # ncu capture of the kernels of that evaluation, keyed by (workload, active
 # columns, sketch dtype); the value applies to that configuration and kernel
 # version only
-DUAL_STEP_TRAFFIC = {("deblur512_tv_f32", 22, "bf16"): 30.22e6,
-                     # warm L2 (the columns kept with evict_last stay resident
+DUAL_STEP_TRAFFIC = {# warm L2 (the columns kept with evict_last stay resident
                      # across x evaluations, as in the solve)
                      ("ct512_parallel_tv_f32", 400, "bf16"): 291.0e6}
 SECONDARY = ("deblur512_tv_f32", "superres4x_hs_huber_f32")
@@ -440,7 +439,13 @@ class Native:
         ms = self._graph_ms(lambda: fn(self.ctx, self.pc, lb, w.n_inner, s, Q=Q, out=out), reps)
         uc = le * N * ub + 2 * N * f + N * f                 # U, g and s in, x out
         lt_utz = G * N * f + le * N * ub + N * f             # R (or Q) in, U, g out
-        if w.reg == "tv":
+        if w.reg == "tv" and le <= 64:
+            # one launch per dual step, x staged per chunk from U: U twice
+            # (U c for x, U^T g), s and g in, (R, Q) old in and new out, g out
+            # (the last step writes no R); then the final x
+            step = 2 * le * N * ub + 3 * N * f + 4 * G * N * f
+            total = lt_utz + w.n_inner * step - G * N * f + uc
+        elif w.reg == "tv":
             # x, (R, Q) old in, (R, Q) new out, g out, U (the last step writes no R)
             fused = N * f + 4 * G * N * f + N * f + le * N * ub
             total = lt_utz + uc + w.n_inner * (fused + uc) - G * N * f
@@ -449,10 +454,15 @@ class Native:
             copies = 3 * 2 * (G * N * f)                     # the warm start in and out
             total = w.n_inner * (lt_utz + uc + dual) + lt_utz + uc + copies
         steps = w.n_inner + 1
-        desc = (f"P-metric {w.reg.upper()} x evaluation, graph replay ("
-                + ("lt_utz_kernel with the fused dual update, "
-                   + ("last-CTA M w" if le <= 64 else "reduce_cols + mw") + ", uc_vec_kernel)" if w.reg == "tv"
-                   else "lt_utz_kernel + uc_vec_kernel + dual_update_kernel)"))
+        if w.reg == "tv" and le <= 64:
+            desc = ("P-metric TV x evaluation, graph replay (one lt_utz_kernel per dual step: x staged from U per "
+                    "chunk, dual update, L^T, U^T g partials, last-CTA M w)")
+        elif w.reg == "tv":
+            desc = ("P-metric TV x evaluation, graph replay (lt_utz_kernel with the fused dual update, reduce_cols + "
+                    "mw, uc_vec_kernel)")
+        else:
+            desc = (f"P-metric {w.reg.upper()} x evaluation, graph replay (lt_utz_kernel + uc_vec_kernel + "
+                    "dual_update_kernel)")
         return ms / steps, total / steps, desc
 
     def normal_ms(self, reps: int = 20):

@@ -28,24 +28,76 @@ constexpr int FCH = 1024;        // pixels per partial-sum chunk (small active s
 constexpr int FCH_WIDE = 512;    // large active sets: twice the CTAs, more bytes of U in flight
 constexpr int COUNTER_PROX = 1;
 
+// The x of the previous dual step, x = s - lb (g - U c), for a step that
+// stages it in shared memory instead of reading a stored x (c: le <= 64)
+template <class T, class TA>
+struct XStage {
+    const T* s;
+    const T* g;
+    const TA* c;
+    TA lb;
+};
+
 // DUAL: the stencil pass is the anisotropic-TV dual step fused with the L^T
 // after it (tv_dual_lt, inputs and outputs in `dual`, R unused); otherwise
-// it is L^T R.
-template <class TU, class T, class TA, class TM, int REG, bool LAST, int FCH, bool DUAL>
+// it is L^T R.  XR (with DUAL, small active sets): the CTA first computes x
+// on its chunk and one image row either side (U c from 16-byte loads of the
+// L2-resident U, one chain of FMAs over the columns per pixel, so a pixel
+// staged by two CTAs gets the same float in both) into shared memory, and
+// the stencil reads it there: one launch per dual step, no stored x.
+// Dynamic shared memory: XR: FCH + 2 n2 + 64 values, then the last CTA's.
+template <class TU, class T, class TA, class TM, int REG, bool LAST, int FCH, bool DUAL, bool XR = false>
 __global__ void __launch_bounds__(256) lt_utz_kernel(const T* __restrict__ R, int n1, int n2,
                                                      const TU* __restrict__ U, int le, int ldm,
                                                      const TM* __restrict__ M, T* __restrict__ g,
                                                      TA* __restrict__ part, TA* __restrict__ coef,
-                                                     unsigned* __restrict__ counter, TvDual<T> dual, int keep) {
+                                                     unsigned* __restrict__ counter, TvDual<T> dual, int keep,
+                                                     XStage<T, TA> xr) {
     pdl_enter();
     static_assert(!DUAL || REG == NYS_REG_TV, "the fused dual step is for anisotropic TV");
+    static_assert(!XR || DUAL, "x is staged only for the fused dual step");
     constexpr int V = Vec16<TU>::n;
     constexpr int PT = (FCH + 255) / 256;   // pixels per thread in the stencil pass
     __shared__ __align__(16) TA gs[FCH];
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    TA* sm = reinterpret_cast<TA*>(smem_raw);   // last CTA: w and (le <= 64) M
     const int64_t N = (int64_t)n1 * n2;
     const int64_t i0 = (int64_t)blockIdx.x * FCH;
+    const int nst = XR ? FCH + 2 * n2 : 0;          // staged x values
+    TA* xs = reinterpret_cast<TA*>(smem_raw);
+    TA* cs = xs + nst;
+    TA* sm = XR ? cs + 64 : xs;   // last CTA: w and (le <= 64) M
+    const int64_t base = XR ? (i0 - n2 + N) % N : 0;   // first staged pixel
+    if constexpr (XR) {
+        for (int k = threadIdx.x; k < le; k += blockDim.x) cs[k] = xr.c[k];
+        __syncthreads();
+        // V consecutive pixels per thread and round (base, N and n2 are
+        // multiples of V, so a vector never wraps)
+        for (int v0 = threadIdx.x * V; v0 < nst; v0 += blockDim.x * V) {
+            const int64_t q0 = (base + v0) % N;
+            TA acc[V];
+#pragma unroll
+            for (int e = 0; e < V; ++e) acc[e] = TA(0);
+            for (int k = 0; k < le; ++k) {
+                TA u[V];
+                load_vec<TU, TA, V>(U + (size_t)k * N + q0, u);
+                const TA ck = cs[k];
+#pragma unroll
+                for (int e = 0; e < V; ++e) acc[e] = fma(u[e], ck, acc[e]);
+            }
+#pragma unroll
+            for (int e = 0; e < V; ++e) {
+                const TA v = (TA)xr.g[q0 + e] + TA(-1) * acc[e];
+                xs[v0 + e] = (TA)xr.s[q0 + e] + (-xr.lb) * v;
+            }
+        }
+        __syncthreads();
+    }
+    using TC = typename Comp<T>::type;
+    auto xf = [&](size_t q) -> TC {
+        int64_t o = (int64_t)q - base;
+        if (o < 0) o += N;
+        return (TC)xs[o];
+    };
     TA v[PT];
 #pragma unroll
     for (int q = 0; q < PT; ++q) {
@@ -54,7 +106,10 @@ __global__ void __launch_bounds__(256) lt_utz_kernel(const T* __restrict__ R, in
         if (threadIdx.x + q * 256 < FCH && p < N) {
             int i, j;
             pix_ij(p, n2, i, j);
-            v[q] = DUAL ? (TA)tv_dual_lt<T>(dual, i, j, n1, n2) : (TA)lt_q<T, REG>(R, i, j, n1, n2);
+            if constexpr (XR)
+                v[q] = (TA)tv_dual_lt_f<T>(dual, xf, i, j, n1, n2);
+            else
+                v[q] = DUAL ? (TA)tv_dual_lt<T>(dual, i, j, n1, n2) : (TA)lt_q<T, REG>(R, i, j, n1, n2);
         }
     }
 #pragma unroll
@@ -158,24 +213,25 @@ int fused_typed(nys_ctx* ctx, const nys_precond* pc, double lb, int n_inner, int
     const TA step = (TA)(1.0 / (lb * normL2));
     unsigned* counter = ctx->counters + COUNTER_PROX;
     const int keep = l2_keep_cols(ctx, N, sizeof(TU), le);
+    const XStage<T, TA> xr0 = {};
     // g = L^T Rin, or the fused TV dual step and the L^T after it (dual.x
     // set); then x (or out) = s - lb (g - U c), c = M U^T g
     auto xfn = [&](const T* Rin, const TvDual<T>& dual, T* dst) -> int {
         if (last) {
             if (dual.x)
                 NYS_CK(ctx, launch_pdl(lt_utz_kernel<TU, T, TA, TM, REG, true, FCH, TV>, nchunk, 256, lsm, sm, Rin,
-                                       n1, n2, (const TU*)pc->U, le, pc->ell, M, g, part, coef, counter, dual, keep));
+                                       n1, n2, (const TU*)pc->U, le, pc->ell, M, g, part, coef, counter, dual, keep, xr0));
             else
                 NYS_CK(ctx, launch_pdl(lt_utz_kernel<TU, T, TA, TM, REG, true, FCH, false>, nchunk, 256, lsm, sm, Rin,
-                                       n1, n2, (const TU*)pc->U, le, pc->ell, M, g, part, coef, counter, dual, keep));
+                                       n1, n2, (const TU*)pc->U, le, pc->ell, M, g, part, coef, counter, dual, keep, xr0));
             NYS_LAUNCH_CK(ctx);
         } else {
             if (dual.x)
                 NYS_CK(ctx, launch_pdl(lt_utz_kernel<TU, T, TA, TM, REG, false, FCH_WIDE, TV>, nchunk, 256, 16, sm,
-                                       Rin, n1, n2, (const TU*)pc->U, le, pc->ell, M, g, part, coef, counter, dual, keep));
+                                       Rin, n1, n2, (const TU*)pc->U, le, pc->ell, M, g, part, coef, counter, dual, keep, xr0));
             else
                 NYS_CK(ctx, launch_pdl(lt_utz_kernel<TU, T, TA, TM, REG, false, FCH_WIDE, false>, nchunk, 256, 16, sm,
-                                       Rin, n1, n2, (const TU*)pc->U, le, pc->ell, M, g, part, coef, counter, dual, keep));
+                                       Rin, n1, n2, (const TU*)pc->U, le, pc->ell, M, g, part, coef, counter, dual, keep, xr0));
             NYS_LAUNCH_CK(ctx);
             int st2 = coef_run<TA, TM>(ctx, part, nchunk, le, pc->ell, 1, M, (const TM*)nullptr, coef, 1, wbuf);
             if (st2) return st2;
@@ -191,6 +247,41 @@ int fused_typed(nys_ctx* ctx, const nys_precond* pc, double lb, int n_inner, int
     };
     const TvDual<T> none = {};
     double t = 1.0;
+    const size_t xsm = ((size_t)FCH + 2 * (size_t)n2 + 64) * sizeof(TA) + lsm;
+    if (TV && last && n_inner >= 1 && n2 % V == 0 && N >= (int64_t)FCH + 2 * n2 && xsm <= 48 * 1024) {
+        // small active sets: one launch per dual step, x staged per chunk from
+        // U (L2-resident), c, s and g (XR above); g and c alternate between
+        // two buffers; the final x is one pass of U c
+        T* gb[2] = {g, x};
+        TA* cb[2] = {coef, wbuf};
+        NYS_CK(ctx, launch_pdl(lt_utz_kernel<TU, T, TA, TM, REG, true, FCH, false>, nchunk, 256, lsm, sm, Q, n1, n2,
+                               (const TU*)pc->U, le, pc->ell, M, gb[0], part, cb[0], counter, none, keep, xr0));
+        NYS_LAUNCH_CK(ctx);
+        for (int k = 0; k < n_inner; ++k) {
+            const double tn = 0.5 * (1.0 + std::sqrt(1.0 + 4.0 * t * t));
+            const double beta = (t - 1.0) / tn;
+            t = tn;
+            const bool fin = k + 1 == n_inner;
+            TvDual<T> d;
+            d.x = nullptr;
+            d.Ro = k ? RQ[k & 1][0] : Q;
+            d.Qo = k ? RQ[k & 1][1] : Q;
+            d.Rn = fin ? nullptr : RQ[(k + 1) & 1][0];
+            d.Qn = (fin && k) ? Q : RQ[(k + 1) & 1][1];
+            d.step = step;
+            d.beta = (TA)beta;
+            const XStage<T, TA> xr = {s, gb[k & 1], cb[k & 1], (TA)lb};
+            NYS_CK(ctx, launch_pdl(lt_utz_kernel<TU, T, TA, TM, REG, true, FCH, TV, TV>, nchunk, 256, xsm, sm,
+                                   (const T*)nullptr, n1, n2, (const TU*)pc->U, le, pc->ell, M, gb[(k + 1) & 1], part,
+                                   cb[(k + 1) & 1], counter, d, keep, xr));
+            NYS_LAUNCH_CK(ctx);
+        }
+        NYS_CK(ctx, launch_pdl(uc_vec_kernel<TU, T, TA>, dim3(ug, 1), 256, usm, sm, (const TU*)pc->U, gb[n_inner & 1],
+                               N, le, cb[n_inner & 1], TA(-1), out, s, (TA)(-lb), keep));
+        NYS_LAUNCH_CK(ctx);
+        if (n_inner == 1) NYS_CK(ctx, cudaMemcpyAsync(Q, RQ[1][1], sizeof(T) * G * N, cudaMemcpyDeviceToDevice, sm));
+        return NYS_OK;
+    }
     if (TV) {
         // warm start R = Q = Q_in; step k reads (R, Q) from RQ[k & 1] (Q_in
         // itself for k = 0) and writes RQ[(k + 1) & 1]; the last step writes

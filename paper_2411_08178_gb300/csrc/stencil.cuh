@@ -160,16 +160,18 @@ struct TvDual {
 // last step).  The storage type is the compute type here (float32 or
 // float64 iterates), and explicit fma keeps the recomputed neighbour values
 // bit-identical to the ones their own pixel writes.
-template <class T>
-__device__ __forceinline__ typename Comp<T>::type tv_dual_lt(const TvDual<T>& d, int i, int j, int n1, int n2) {
+// xf(q) gives x at flat index q (from memory, or from a staged copy).
+template <class T, class XF>
+__device__ __forceinline__ typename Comp<T>::type tv_dual_lt_f(const TvDual<T>& d, XF xf, int i, int j, int n1,
+                                                               int n2) {
     using TC = typename Comp<T>::type;
     const size_t N = (size_t)n1 * n2;
     const size_t r0 = (size_t)i * n2, rm = (size_t)wrap_dec(i, n1) * n2, rp = (size_t)wrap_inc(i, n1) * n2;
     const int jm = wrap_dec(j, n2), jp = wrap_inc(j, n2);
     const size_t t = r0 + j, td = rp + j, tr = r0 + jp;
-    const TC xc = (TC)d.x[t];
-    const TC lx1 = xc - (TC)d.x[rm + j], lx1d = (TC)d.x[td] - xc;
-    const TC lx2 = xc - (TC)d.x[r0 + jm], lx2r = (TC)d.x[tr] - xc;
+    const TC xc = xf(t);
+    const TC lx1 = xc - xf(rm + j), lx1d = xf(td) - xc;
+    const TC lx2 = xc - xf(r0 + jm), lx2r = xf(tr) - xc;
     auto proj = [&](size_t e, TC lx) { return fmin(TC(1), fmax(TC(-1), fma(d.step, lx, (TC)d.Ro[e]))); };
     const TC q1 = proj(t, lx1), q1d = proj(td, lx1d);
     const TC q2 = proj(N + t, lx2), q2r = proj(N + tr, lx2r);
@@ -181,6 +183,11 @@ __device__ __forceinline__ typename Comp<T>::type tv_dual_lt(const TvDual<T>& d,
     d.Rn[t] = (T)r1;
     d.Rn[N + t] = (T)r2;
     return r1 - mom(td, q1d) + r2 - mom(N + tr, q2r);
+}
+template <class T>
+__device__ __forceinline__ typename Comp<T>::type tv_dual_lt(const TvDual<T>& d, int i, int j, int n1, int n2) {
+    using TC = typename Comp<T>::type;
+    return tv_dual_lt_f<T>(d, [&](size_t q) { return (TC)d.x[q]; }, i, j, n1, n2);
 }
 
 namespace {
