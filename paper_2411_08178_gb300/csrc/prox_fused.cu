@@ -248,7 +248,9 @@ int fused_typed(nys_ctx* ctx, const nys_precond* pc, double lb, int n_inner, int
     const TvDual<T> none = {};
     double t = 1.0;
     const size_t xsm = ((size_t)FCH + 2 * (size_t)n2 + 64) * sizeof(TA) + lsm;
-    if (TV && last && n_inner >= 1 && n2 % V == 0 && N >= (int64_t)FCH + 2 * n2 && xsm <= 48 * 1024) {
+    // (48 KB: static gs[FCH] plus this dynamic part, no opt-in needed)
+    if (TV && last && n_inner >= 1 && n2 % V == 0 && N >= (int64_t)FCH + 2 * n2 &&
+        xsm + (size_t)FCH * sizeof(TA) <= 48 * 1024) {
         // small active sets: one launch per dual step, x staged per chunk from
         // U (L2-resident), c, s and g (XR above); g and c alternate between
         // two buffers; the final x is one pass of U c
