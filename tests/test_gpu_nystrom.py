@@ -116,12 +116,13 @@ def test_factor_large_ell_global_jacobi(env, dt, ell):
     _check_factor(pc.U.double().cpu().numpy(), pc.S_hat.cpu().numpy(), ref, *tol)
 
 
-@pytest.mark.parametrize("ell", [300, 520])
+@pytest.mark.parametrize("ell", [256, 257, 300, 448, 520])
 def test_factor_bf16_wide_sketch_matches_oracle(env, ell):
-    # bf16 sketches wider than one 256-column tensor-core tile: the single
+    # bf16 sketches at and past one 256-column tensor-core tile: the single
     # launch of Omega^T Omega, Omega^T Y, Y^T Y and the tall U = Y_v W in
-    # column blocks, then the global-memory eigensolver, against the oracle
-    # from the same Omega at the bf16 tolerance
+    # column blocks; the cluster eigensolver on 8 CTAs (256), on 16 (257 ..
+    # 448, its upper end) and the global-memory one beyond (520); against the
+    # oracle from the same Omega at the bf16 tolerance
     torch, api, ctx = env
     n = 64
     h = gaussian_kernel(9, 1.5)
@@ -182,15 +183,16 @@ def test_not_spd_core_is_reported(env):
     assert e.value.code == NYS_ENOTSPD
 
 
-@pytest.mark.parametrize("ell", [6, 64, 200])
+@pytest.mark.parametrize("ell", [6, 47, 48, 64, 200, 512, 513])
 def test_cholesky_retries_match_oracle(env, ell):
     # Y = -delta Omega: the core (v - delta) Omega^T Omega is SPD only once the
     # shift v = eps ||Omega||_F, multiplied by 10 per failure, exceeds delta.
     # delta = 10^2.5 v0 needs three retries; the count, the final shift and the
     # factor against the oracle's Algorithm 1 with the same retry rule.  ell =
-    # 64 and 200 run the 16-SM cluster Cholesky, ell = 6 the one-CTA kernel.
+    # 48 .. 512 run the 16-SM cluster Cholesky (both ends of its range), 6, 47
+    # and 513 the one-CTA kernel.
     torch, api, ctx = env
-    n = 32
+    n = 32 if ell <= 512 else 24
     Om = torch.from_numpy(gaussian_matrix(n * n, ell, 11).reshape(ell, n, n)).cuda()
     v0 = EPS64 * float(torch.linalg.norm(Om.double()))
     delta = v0 * 10.0 ** 2.5
