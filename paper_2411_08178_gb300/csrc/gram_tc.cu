@@ -28,6 +28,7 @@
 // records an error, stops issuing, drains its own TMA copies and MMAs, frees
 // TMEM and returns.
 #include "internal.cuh"
+#include "tma.cuh"
 
 #include <cuda.h>
 #include <cudaTypedefs.h>
@@ -40,38 +41,11 @@ namespace {
 constexpr int TC_BM = 128;
 constexpr int TC_BK = 64;           // bf16 elements per 128-byte swizzle row
 constexpr int TC_STAGES = 4;
-constexpr uint32_t WAIT_LIMIT = 1u << 24;   // try_wait polls before giving up
 // every TMA x coordinate below is a multiple of TC_BK (k blocks, padded
 // widths) or of 64 pixels (tile origins), so with bf16 it starts on a
 // 16-byte boundary as the tiled bulk copy requires
 static_assert(TC_BK % 8 == 0 && TC_BM % 64 == 0, "TMA x coordinates must be multiples of 8 bf16 values");
 
-__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
-
-__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
-}
-__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t bytes) {
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
-                 : "memory");
-}
-__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
-    uint32_t ok;
-    asm volatile(
-        "{\n\t.reg .pred p;\n\t"
-        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-        "selp.u32 %0, 1, 0, p;\n}\n"
-        : "=r"(ok)
-        : "r"(smem_u32(bar)), "r"(parity)
-        : "memory");
-    return ok != 0;
-}
-// bounded wait; false on time-out
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
-    for (uint32_t i = 0; i < WAIT_LIMIT; ++i)
-        if (mbar_try_wait(bar, parity)) return true;
-    return false;
-}
 __device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, uint64_t* bar, int x, int y) {
     asm volatile(
         "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], "
