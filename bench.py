@@ -504,6 +504,11 @@ def secondary_workload(w: WL.Workload, device: int, sketch_dtype: str, ref_iters
             "k_precond": k_p, "k_precond_settled": k_ps, "ms": round(ms_p, 3), "sketch_ms": round(sk, 3),
             "active_columns": nb.pc.ell_active,
             "iterate_err_at_k": e_p, "speedup_vs_plain": round(out["plain"]["ms"] / ms_p, 3)}
+        if sqrt_shift:
+            # the sketch-size rule between plain APG and the configured sketch
+            rule = nb.ell_rule([w.ell], out["plain"]["k"])
+            rule["measured_best_ell"] = w.ell if ms_p < out["plain"]["ms"] else 0
+            out["ell_rule"] = rule
         nb.close()
     return out
 
@@ -609,6 +614,9 @@ def run_native(args, w: WL.Workload):
                      "achieved": round(achieved, 1), "peak": peaks["hbm_gbs"], "peak_source": peaks["src"],
                      "unit": "GB/s", "frac": round(achieved / peaks["hbm_gbs"], 4),
                      "traffic": traffic, "bytes_per_step": step_bytes, "ms_per_step": round(step_ms, 5),
+                     # DRAM bytes of the ncu capture over the live time: the rate the kernels draw from HBM
+                     # (the rest of the algorithmic bytes come from L2)
+                     "dram_gbs": round(traffic / (step_ms * 1e-3) / 1e9, 1) if traffic else None,
                      "active_columns": nb.pc.ell_active,
                      "p_inverse_apply": {"achieved": round(achieved_pinv, 1), "bytes": pre_bytes,
                                          "ms": round(pre_ms, 5),

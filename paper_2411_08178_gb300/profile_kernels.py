@@ -159,6 +159,41 @@ def main():
                                 cg_rnp=res[100][1], saved_time=(t0 - t1) / t0,
                                 saved_cg=1.0 - sum(res[100][1]) / sum(res[0][1])))
             opi.close()
+    if "read_ceiling" in cases:
+        # DRAM bandwidth of a read-only stream against a read + write copy,
+        # over U's size (ell bf16 images): torch's sum and clone, CUDA events,
+        # a 256 MB write between repetitions so that every byte comes from DRAM
+        big = torch.zeros(ell * N, dtype=torch.bfloat16, device=dev)
+        acc = torch.empty(ell * N // 4096, dtype=torch.float32, device=dev)
+        dst = torch.empty_like(big)
+        flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)
+
+        def flushed(fn, reps=args.reps):
+            ts = []
+            for r in range(reps + 3):
+                flush.fill_(float(r))
+                a = torch.cuda.Event(enable_timing=True)
+                b = torch.cuda.Event(enable_timing=True)
+                a.record(stream)
+                fn()
+                b.record(stream)
+                torch.cuda.synchronize()
+                if r >= 3:
+                    ts.append(a.elapsed_time(b))
+            return sum(ts) / len(ts)
+        nb = ell * N * 2
+        ms = flushed(lambda: torch.sum(big.view(-1, 4096), dim=1, dtype=torch.float32, out=acc))
+        out.append(dict(case=f"read-only stream (row sums of {nb / 1e6:.0f} MB bf16, rows of 4096)", ms=ms, bytes=nb,
+                        GBs=nb / ms / 1e6))
+        # the library matrix-vector product over the same bytes: U^T z with U
+        # as an ell x N bf16 matrix (what the U^T g pass computes)
+        zv = torch.zeros(N, dtype=torch.bfloat16, device=dev)
+        yv = torch.empty(ell, dtype=torch.bfloat16, device=dev)
+        ms = flushed(lambda: torch.mv(big.view(ell, N), zv, out=yv))
+        out.append(dict(case=f"read-only stream (torch.mv, {ell} x {N} bf16)", ms=ms, bytes=nb, GBs=nb / ms / 1e6))
+        ms = flushed(lambda: dst.copy_(big))
+        out.append(dict(case=f"copy (read + write {nb / 1e6:.0f} MB each)", ms=ms, bytes=2 * nb, GBs=2 * nb / ms / 1e6))
+        del big, dst, flush
     if "iter" in cases:
         y = torch.rand(op.meas_shape, device=dev)
         for name, p in (("plain", None), ("precond", pc)):
