@@ -82,6 +82,37 @@ def test_factor_f64_matches_algorithm1(env):
     assert np.max(np.abs(U @ U.T - np.eye(ell))) < 1e-9
 
 
+@pytest.mark.parametrize("dt", ["f64", "f32", "bf16"])
+@pytest.mark.parametrize("ell", [1, 2, 3])
+def test_tiny_sketches_end_to_end(env, dt, ell):
+    # the smallest sketches: Algorithm 1 (a 1 x 1 core has one eigenvalue),
+    # the preconditioner (the square-root heuristic; the unit-sum blur has
+    # S_hat <= 1, so d_ell = sqrt(s_ell) - 1 <= 0 and ell = 1 leaves no
+    # active column: P = I exactly) and the P-metric TV prox
+    torch, api, ctx = env
+    n = 24
+    h = gaussian_kernel(5, 1.0)
+    idt = torch.float64 if dt == "f64" else torch.float32
+    sd = {"f64": torch.float64, "f32": torch.float32, "bf16": torch.bfloat16}[dt]
+    op = api.Operator(ctx, "blur", n, n, dtype=idt, kernel=h)
+    opo = O.Operator("blur", n, n, kernel=h)
+    eps = EPS64 if dt == "f64" else EPS32
+    Om, Y = api.nys_sketch(ctx, op, ell, seed=5, store_dtype=sd)
+    pc = api.nys_factor(ctx, Om, Y, eps, u_dtype=sd)
+    ref = oracle.nystrom.nystrom(_flat_phi(opo, n, n), gaussian_matrix(n * n, ell, 5), eps)
+    tol = {"f64": (1e-10, 1e-9), "f32": (1e-4, 1e-3), "bf16": (3e-2, 3e-2)}[dt]
+    _check_factor(pc.U.double().cpu().numpy(), pc.S_hat.cpu().numpy(), ref, *tol)
+    d = oracle.nystrom.precond_weights(pc.S_hat.cpu().numpy(), 0.0, True)
+    assert pc.ell_active == int(np.sum(d > 0)) and d[-1] == 0.0
+    Ul = pc.U.double().cpu().numpy().reshape(ell, -1)
+    P = oracle.nystrom.Precond(Ul, pc.S_hat.cpu().numpy(), 0.0, True)
+    s = gaussian_probe_like((n, n), 6)
+    x_ref, _ = oracle.prox.prox_dual(s, "tv", 0.05, P, 5)
+    x, _ = api.prox_tv(ctx, pc, 0.05, 5, torch.from_numpy(s).to(idt).cuda())
+    ptol = 1e-10 if dt == "f64" else 1e-4
+    close(x, x_ref, ptol, 10 * ptol)
+
+
 def test_factor_f32_and_bf16_stated_accuracy(env):
     torch, api, ctx = env
     n, ell = 128, 48
