@@ -22,6 +22,7 @@
 //           info[1] = v, info[2] = retries (as the one-CTA kernel)
 // Output: L (n x n, row-major, ld n), lower triangular with zeros above.
 #include "internal.cuh"
+#include "chol_panel.cuh"
 
 #include <cooperative_groups.h>
 
@@ -84,27 +85,10 @@ __global__ void __launch_bounds__(CH_THREADS, 1)
             const int oseat = k < CC ? 0 : 1;
             const int p0 = k * b;
             if (rank == owner) {
-                // the b x b diagonal block by one warp (b <= 16: warp barriers only)
-                const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-                if (warp == 0) {
-                    for (int t = 0; t < b; ++t) {
-                        const int r = p0 + t;
-                        if (lane == 0) {
-                            const double d = col(oseat, t)[r];
-                            if (!(d > 0.0) || !isfinite(d)) bad_flag = 1;
-                            else col(oseat, t)[r] = sqrt(d);
-                        }
-                        __syncwarp();
-                        if (bad_flag) break;
-                        const double rtt = col(oseat, t)[r];
-                        for (int c = t + 1 + lane; c < b; c += 32) col(oseat, c)[r] /= rtt;
-                        __syncwarp();
-                        for (int e = lane; e < b * b; e += 32) {
-                            const int c = e / b, i = p0 + e - c * b;
-                            if (c > t && i > r && i <= p0 + c) col(oseat, c)[i] -= col(oseat, i - p0)[r] * col(oseat, c)[r];
-                        }
-                        __syncwarp();
-                    }
+                // the b x b diagonal block by one warp (b <= 16, registers and shuffles)
+                if ((threadIdx.x >> 5) == 0) {
+                    const bool okb = warp_chol_block<double>([&](int c) { return col(oseat, c); }, p0, b);
+                    if (!okb && (threadIdx.x & 31) == 0) bad_flag = 1;
                 }
                 __syncthreads();
                 if (bad_flag && threadIdx.x < CC) *cluster.map_shared_rank(&bad_flag, (int)threadIdx.x) = 1;
@@ -127,12 +111,7 @@ __global__ void __launch_bounds__(CH_THREADS, 1)
             for (int q2 = threadIdx.x; q2 < 2 * b; q2 += blockDim.x) {
                 const int s = q2 / b, c = q2 - s * b;
                 if (blk[s] <= k) continue;
-                double* cc = col(s, c);
-                for (int i = 0; i < b; ++i) {
-                    double x = cc[p0 + i];
-                    for (int q = 0; q < i; ++q) x -= stage[i * b + q] * cc[p0 + q];
-                    cc[p0 + i] = x / stage[i * b + i];
-                }
+                panel_forward_subst(col(s, c), stage, p0, b);
             }
             cluster.sync();
             const int m0 = p0 + b;

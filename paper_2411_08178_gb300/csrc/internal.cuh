@@ -263,10 +263,11 @@ int gemm_tall(nys_ctx* ctx, int in_dt, const void* A, const void* A2, const doub
 
 // eigenvectors V (float32, row-major, ld = ldv) of the symmetric ell x ell
 // float64 G by one-sided Jacobi on a thread-block cluster
-// (jacobi_cluster.cu); NYS_EINVAL (nothing launched) when not applicable;
-// *status (device) = 1 if the float32 Cholesky of G fails
-int jacobi_cluster(nys_ctx* ctx, const double* G, int ell, int max_sweeps, float* V, int ldv, int* sweeps,
-                   int* status);
+// (jacobi_cluster.cu), Rsave = ell * ell floats of workspace; NYS_EINVAL
+// (nothing launched) when not applicable; *status (device) = 1 if the
+// float32 Cholesky of G fails
+int jacobi_cluster(nys_ctx* ctx, const double* G, int ell, int max_sweeps, float* V, int ldv, float* Rsave,
+                   int* sweeps, int* status);
 
 // float64 Cholesky L (n x n, lower, row-major) on a 16-CTA cluster
 // (chol_cluster.cu): mode 0 of src (ld), status in info[slot]; mode 1 of

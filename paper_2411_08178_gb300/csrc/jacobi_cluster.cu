@@ -2,9 +2,12 @@
 // a thread-block cluster: one-sided (Hestenes) Jacobi on the Cholesky factor
 // R (G = R^T R), float32, for 64 <= ell <= 448.
 //
-// The columns of R -- each with the matching column of V, the accumulated
-// rotation, beside it -- are cut into 2C blocks of b columns; CTA c of the
-// cluster holds two of them in shared memory (its two "seats").
+// The columns of R are cut into 2C blocks of b columns; CTA c of the
+// cluster holds two of them in shared memory (its two "seats").  The
+// rotations are not accumulated: the sweeps turn R into R V (orthogonal
+// columns) and V = R^{-1} (R V) is recovered afterwards by back substitution
+// against a copy of R saved before the sweeps, so that a sub-round and a
+// move between CTAs carry one float per row instead of two.
 //   Cholesky   right-looking by panels (one block per panel): the panel's
 //              owner factors its b x b diagonal block, every CTA solves for
 //              the panel's rows of its own later columns, then updates its
@@ -20,13 +23,14 @@
 //              starts.  2C - 1 block rounds per sweep; the sweeps stop when
 //              no pair needed a rotation (cluster-wide vote) or after
 //              max_sweeps.
-//   output     V (row-major, ld = ldv): column idx of V is the accumulated
-//              rotation of the column that started as column idx of R, so
-//              R V has orthogonal columns and V^T G V is diagonal.
+//   output     R V (row-major, ld = ldv): column idx is the rotated column
+//              that started as column idx of R; jc_backsolve_kernel turns it
+//              into V (unit columns), V^T G V diagonal.
 // Every CTA runs the same sequence of cluster barriers (uniform control
 // flow, no spin waits).  A non-positive Cholesky pivot sets *status_out = 1
 // and writes nothing else, so that the caller's two-sided kernel runs.
 #include "internal.cuh"
+#include "chol_panel.cuh"
 
 #include <cooperative_groups.h>
 
@@ -40,14 +44,15 @@ constexpr int JC_THREADS = 512;   // 16 warps: one per pair of a sub-round (b <=
 template <int C>
 __global__ void __launch_bounds__(JC_THREADS, 1)
     jacobi_cluster_kernel(const double* __restrict__ G, int nreal, int b, int max_sweeps, float* __restrict__ V,
-                          int ldv, int* __restrict__ sweeps_out, int* __restrict__ status_out) {
+                          int ldv, float* __restrict__ Rsave, int* __restrict__ sweeps_out,
+                          int* __restrict__ status_out) {
     cg::cluster_group cluster = cg::this_cluster();
     const int rank = (int)cluster.block_rank();
     const int npad = 2 * C * b;
-    const int col_len = 2 * npad;                 // R part, then V part
+    const int col_len = npad;
     const int slot_len = b * col_len;
     extern __shared__ __align__(16) float jc_smem[];
-    float* buf = jc_smem;                         // [4][b][2 npad]: cur seat 0, cur seat 1, next seat 0, next seat 1
+    float* buf = jc_smem;                         // [4][b][npad]: cur seat 0, cur seat 1, next seat 0, next seat 1
     float* nrm = buf + 4 * (size_t)slot_len;      // [4][b]
     int* idx = reinterpret_cast<int*>(nrm + 4 * b);   // [4][b]
     __shared__ int bad_flag, rot_flag;
@@ -59,7 +64,7 @@ __global__ void __launch_bounds__(JC_THREADS, 1)
     const int blk[2] = {rank, 2 * C - 1 - rank};
     for (int s = 0; s < 2; ++s)
         for (int c = threadIdx.x; c < b; c += blockDim.x) idx[s * b + c] = blk[s] * b + c;
-    // load G (padded with the identity) into the R parts, columns of the two blocks
+    // load G (padded with the identity), columns of the two blocks
     for (int s = 0; s < 2; ++s) {
         float* sb = seat_buf(s);
         for (int t = threadIdx.x; t < b * npad; t += blockDim.x) {
@@ -82,29 +87,11 @@ __global__ void __launch_bounds__(JC_THREADS, 1)
         const int oseat = k < C ? 0 : 1;
         const int p0 = k * b;                      // first column (and row) of the panel
         if (rank == owner) {
-            // the b x b diagonal block by one warp (b <= 16: warp barriers only)
+            // the b x b diagonal block by one warp (b <= 16, registers and shuffles)
             if (warp == 0) {
                 float* pb = seat_buf(oseat);
-                for (int t = 0; t < b; ++t) {
-                    const int r = p0 + t;
-                    if (lane == 0) {
-                        const float d = pb[(size_t)t * col_len + r];
-                        if (!(d > 0.0f)) bad_flag = 1;
-                        else pb[(size_t)t * col_len + r] = sqrtf(d);
-                    }
-                    __syncwarp();
-                    if (bad_flag) break;
-                    const float rtt = pb[(size_t)t * col_len + r];
-                    for (int c = t + 1 + lane; c < b; c += 32) pb[(size_t)c * col_len + r] /= rtt;
-                    __syncwarp();
-                    // rows r+1.. of the later panel columns: R(i, c) -= R(r, i) R(r, c), r < i <= p0 + c
-                    for (int e = lane; e < b * b; e += 32) {
-                        const int c = e / b, i = p0 + e - (e / b) * b;
-                        if (c > t && i > r && i <= p0 + c)
-                            pb[(size_t)c * col_len + i] -= pb[(size_t)(i - p0) * col_len + r] * pb[(size_t)c * col_len + r];
-                    }
-                    __syncwarp();
-                }
+                const bool ok = warp_chol_block<float>([&](int c) { return pb + (size_t)c * col_len; }, p0, b);
+                if (!ok && lane == 0) bad_flag = 1;
             }
             __syncthreads();
             // a failed pivot: tell every CTA (their own copy of the flag), so
@@ -132,12 +119,7 @@ __global__ void __launch_bounds__(JC_THREADS, 1)
         for (int cc = threadIdx.x; cc < 2 * b; cc += blockDim.x) {
             const int s = cc / b, c = cc - s * b;
             if (blk[s] <= k) continue;
-            float* col = seat_buf(s) + (size_t)c * col_len;
-            for (int i = 0; i < b; ++i) {
-                float v = col[p0 + i];
-                for (int q = 0; q < i; ++q) v -= stage[i * b + q] * col[p0 + q];
-                col[p0 + i] = v / stage[i * b + i];
-            }
+            panel_forward_subst(seat_buf(s) + (size_t)c * col_len, stage, p0, b);
         }
         cluster.sync();
         // gather the panel's rows of every column after the panel: stage[i][m] = R(p0 + i, m)
@@ -172,7 +154,8 @@ __global__ void __launch_bounds__(JC_THREADS, 1)
         // rows of later panels; the others read this panel's rows, which are final
         __syncthreads();
     }
-    // R upper triangular (the strict lower parts still hold G); V = I
+    // R upper triangular (the strict lower parts still hold G); a copy of its
+    // nreal x nreal part (column-major, ld nreal) for the back substitution
     for (int s = 0; s < 2; ++s) {
         float* sb = seat_buf(s);
         for (int t = threadIdx.x; t < b * npad; t += blockDim.x) {
@@ -180,7 +163,7 @@ __global__ void __launch_bounds__(JC_THREADS, 1)
             const int j = blk[s] * b + c;
             float* col = sb + (size_t)c * col_len;
             if (i > j) col[i] = 0.0f;
-            col[npad + i] = (i == j) ? 1.0f : 0.0f;
+            if (i < nreal && j < nreal) Rsave[(size_t)j * nreal + i] = i > j ? 0.0f : col[i];
         }
     }
     __syncthreads();
@@ -188,62 +171,69 @@ __global__ void __launch_bounds__(JC_THREADS, 1)
     // ------------------------------------------------------------ sweeps --
     const float tol = 1.2e-7f * sqrtf((float)npad);
     const float tol2 = tol * tol;
-    const int nv = npad / 4;                       // float4 vectors per R part
-    // one warp rotates columns x and y: c = x . y over the R parts, then the
-    // plane rotation of both parts.  Every lane holds its share of both
-    // columns (R and V parts, at most NVL 16-byte vectors of each) in
-    // registers from the first load to the store, so the chain is one
-    // load, the dot product, the rotation's parameters and one store.
-    constexpr int NVL = C / 4;   // npad = 2 C b <= 32 C floats per part: 8 C vectors over 32 lanes
+    const int nv = npad / 4;                       // float4 vectors per column
+    // one warp rotates columns x and y: c = x . y, then the plane rotation.
+    // Every lane holds its share of both columns (at most NVL 16-byte
+    // vectors of each) in registers from the first load to the store, so
+    // the chain is one load, the dot product, the rotation's parameters and
+    // one store.
+    constexpr int NVL = C / 4;   // npad = 2 C b <= 32 C floats: 8 C vectors over 32 lanes
+    // the rotation that zeroes x . y = c for squared norms a (x) and bb (y):
+    // t = sign(zeta) / (|zeta| + sqrt(1 + zeta^2)) with zeta = (bb - a) / (2c), the
+    // smaller root of t^2 + 2 zeta t - 1 = 0, written as 2c sign(d) / (|d| + sqrt(d^2 + 4c^2)),
+    // d = bb - a: three dependent special-function operations instead of four.
+    // The squared norms move by -t c (x) and +t c (y).
+    auto rot_params = [](float c, float a, float bb, float& cs, float& sn, float& tc) {
+        const float d = bb - a;
+        const float t = __fdividef(d >= 0.0f ? 2.0f * c : -2.0f * c, fabsf(d) + sqrtf(fmaf(d, d, 4.0f * c * c)));
+        cs = rsqrtf(fmaf(t, t, 1.0f));
+        sn = t * cs;
+        tc = t * c;
+    };
+    auto rot4 = [](const float4& p, const float4& q, float cs, float sn, float4& o1, float4& o2) {
+        const float4 r1 = make_float4(cs * p.x - sn * q.x, cs * p.y - sn * q.y, cs * p.z - sn * q.z, cs * p.w - sn * q.w);
+        o2 = make_float4(sn * p.x + cs * q.x, sn * p.y + cs * q.y, sn * p.z + cs * q.z, sn * p.w + cs * q.w);
+        o1 = r1;
+    };
     auto rotate_pair = [&](float* x, float* y, float* na, float* nb_, int ix, int iy) -> bool {
         float4* xw = reinterpret_cast<float4*>(x);
         float4* yw = reinterpret_cast<float4*>(y);
         const float a = *na, bb = *nb_;
-        float4 px[NVL], qy[NVL], vx[NVL], vy[NVL];
+        float4 px[NVL], qy[NVL];
         float c = 0.0f;
 #pragma unroll
         for (int u = 0; u < NVL; ++u) {
             const int v = lane + 32 * u;
             if (v < nv) {
-                px[u] = xw[v], qy[u] = yw[v], vx[u] = xw[nv + v], vy[u] = yw[nv + v];
+                px[u] = xw[v], qy[u] = yw[v];
             } else {
-                px[u] = qy[u] = vx[u] = vy[u] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+                px[u] = qy[u] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
             }
             c += px[u].x * qy[u].x + px[u].y * qy[u].y + px[u].z * qy[u].z + px[u].w * qy[u].w;
         }
         c = warp_sum(c);
         if (ix >= nreal || iy >= nreal || c == 0.0f || !(c * c > tol2 * (a * bb))) return false;
-        // t = sign(zeta) / (|zeta| + sqrt(1 + zeta^2)) with zeta = (bb - a) / (2c), the
-        // smaller root of t^2 + 2 zeta t - 1 = 0, written as 2c sign(d) / (|d| + sqrt(d^2 + 4c^2)),
-        // d = bb - a: three dependent special-function operations instead of four
-        const float d = bb - a;
-        const float t = __fdividef(d >= 0.0f ? 2.0f * c : -2.0f * c, fabsf(d) + sqrtf(fmaf(d, d, 4.0f * c * c)));
-        const float cs = rsqrtf(fmaf(t, t, 1.0f)), sn = t * cs;
-        auto rot = [&](const float4& p, const float4& q, float4& o1, float4& o2) {
-            o1 = make_float4(cs * p.x - sn * q.x, cs * p.y - sn * q.y, cs * p.z - sn * q.z, cs * p.w - sn * q.w);
-            o2 = make_float4(sn * p.x + cs * q.x, sn * p.y + cs * q.y, sn * p.z + cs * q.z, sn * p.w + cs * q.w);
-        };
+        float cs, sn, tc;
+        rot_params(c, a, bb, cs, sn, tc);
 #pragma unroll
         for (int u = 0; u < NVL; ++u) {
             const int v = lane + 32 * u;
             if (v < nv) {
                 float4 o1, o2;
-                rot(px[u], qy[u], o1, o2);
+                rot4(px[u], qy[u], cs, sn, o1, o2);
                 xw[v] = o1, yw[v] = o2;
-                rot(vx[u], vy[u], o1, o2);
-                xw[nv + v] = o1, yw[nv + v] = o2;
             }
         }
         __syncwarp();
         if (lane == 0) {
-            *na = a - t * c;
-            *nb_ = bb + t * c;
+            *na = a - tc;
+            *nb_ = bb + tc;
         }
         return true;
     };
     int sweep = 0;
     for (; sweep < max_sweeps; ++sweep) {
-        // column norms of the R parts, recomputed every sweep
+        // column norms, recomputed every sweep
         for (int s = 0; s < 2; ++s) {
             float* sb = seat_buf(cur + s);
             for (int c = warp; c < b; c += JC_THREADS / 32) {
@@ -288,12 +278,63 @@ __global__ void __launch_bounds__(JC_THREADS, 1)
                     __syncthreads();
                 }
             }
-            // pairs between the two blocks: (X_i, Y_(i + r) mod b)
-            for (int r = 0; r < b; ++r) {
+            // pairs between the two blocks: (X_i, Y_(i + r) mod b).  Warp i
+            // keeps X_i and its norm in registers for the b
+            // sub-rounds; only the Y columns pass through shared memory.
+            {
+                float4 px[NVL];
+                float a = 0.0f;
+                int ix = 0;
                 if (warp < b) {
-                    const int i = warp, j = warp + r < b ? warp + r : warp + r - b;
-                    rotated |= rotate_pair(X + (size_t)i * col_len, Y + (size_t)j * col_len, nX + i, nY + j, iX[i],
-                                           iY[j]);
+                    const float4* xw = reinterpret_cast<const float4*>(X + (size_t)warp * col_len);
+#pragma unroll
+                    for (int u = 0; u < NVL; ++u) {
+                        const int v = lane + 32 * u;
+                        px[u] = v < nv ? xw[v] : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+                    }
+                    a = nX[warp];
+                    ix = iX[warp];
+                }
+                bool xdirty = false;
+                for (int r = 0; r < b; ++r) {
+                    if (warp < b) {
+                        const int j = warp + r < b ? warp + r : warp + r - b;
+                        float4* yw = reinterpret_cast<float4*>(Y + (size_t)j * col_len);
+                        float4 qy[NVL];
+                        const float bb = nY[j];
+                        float c = 0.0f;
+#pragma unroll
+                        for (int u = 0; u < NVL; ++u) {
+                            const int v = lane + 32 * u;
+                            qy[u] = v < nv ? yw[v] : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+                            c += px[u].x * qy[u].x + px[u].y * qy[u].y + px[u].z * qy[u].z + px[u].w * qy[u].w;
+                        }
+                        c = warp_sum(c);
+                        if (ix < nreal && iY[j] < nreal && c != 0.0f && c * c > tol2 * (a * bb)) {
+                            float cs, sn, tc;
+                            rot_params(c, a, bb, cs, sn, tc);
+#pragma unroll
+                            for (int u = 0; u < NVL; ++u) {
+                                const int v = lane + 32 * u;
+                                float4 o;
+                                rot4(px[u], qy[u], cs, sn, px[u], o);
+                                if (v < nv) yw[v] = o;
+                            }
+                            a -= tc;
+                            if (lane == 0) nY[j] = bb + tc;
+                            rotated = xdirty = true;
+                        }
+                    }
+                    __syncthreads();
+                }
+                if (warp < b && xdirty) {
+                    float4* xw = reinterpret_cast<float4*>(X + (size_t)warp * col_len);
+#pragma unroll
+                    for (int u = 0; u < NVL; ++u) {
+                        const int v = lane + 32 * u;
+                        if (v < nv) xw[v] = px[u];
+                    }
+                    if (lane == 0) nX[warp] = a;
                 }
                 __syncthreads();
             }
@@ -344,13 +385,13 @@ __global__ void __launch_bounds__(JC_THREADS, 1)
             break;
         }
     }
-    // V columns out, at the index each column started from
+    // the columns of R V out, at the index each column started from
     for (int s = 0; s < 2; ++s) {
         const float* sb = seat_buf(cur + s);
         for (int t = threadIdx.x; t < b * nreal; t += blockDim.x) {
             const int c = t / nreal, i = t - c * nreal;
             const int j = idx[(cur + s) * b + c];
-            if (j < nreal) V[(size_t)i * ldv + j] = sb[(size_t)c * col_len + npad + i];
+            if (j < nreal) V[(size_t)i * ldv + j] = sb[(size_t)c * col_len + i];
         }
     }
     if (rank == 0 && threadIdx.x == 0) {
@@ -359,11 +400,67 @@ __global__ void __launch_bounds__(JC_THREADS, 1)
     }
 }
 
+// V := R^{-1} V column by column, then each column scaled to unit length:
+// R upper triangular (nreal x nreal, column-major, ld nreal, as the cluster
+// kernel saved it), V row-major with ld ldv.  One CTA per column; rows in
+// blocks of 32 from the bottom: one warp solves the block's triangle (its
+// 32 x 32 part of R in registers, the solution broadcast by shuffles), then
+// every thread removes the block from the rows above.  Nothing is done when
+// *status != 0 (the cluster kernel's Cholesky failed and the two-sided
+// kernel writes V instead).
+__global__ void __launch_bounds__(256) jc_backsolve_kernel(const float* __restrict__ R, float* __restrict__ V,
+                                                           int ldv, int nreal, const int* __restrict__ status) {
+    if (*status != 0) return;
+    extern __shared__ float y[];   // nreal
+    __shared__ float red[8];
+    const int j = blockIdx.x;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    for (int i = threadIdx.x; i < nreal; i += blockDim.x) y[i] = V[(size_t)i * ldv + j];
+    __syncthreads();
+    for (int i1 = nreal; i1 > 0; i1 -= 32) {
+        const int i0 = i1 > 32 ? i1 - 32 : 0, m = i1 - i0;
+        if (warp == 0) {
+            // lane l: row i0 + l; rt[t] = R(i0 + l, i0 + t) for l <= t < m
+            float rt[32];
+#pragma unroll
+            for (int t = 0; t < 32; ++t)
+                rt[t] = (t < m && lane <= t) ? R[(size_t)(i0 + t) * nreal + i0 + lane] : 0.0f;
+            float yl = lane < m ? y[i0 + lane] : 0.0f;
+#pragma unroll
+            for (int t = 31; t >= 0; --t) {
+                if (t < m) {
+                    const float xt = __shfl_sync(0xffffffffu, lane == t ? yl / rt[t] : 0.0f, t);
+                    if (lane == t) yl = xt;
+                    else if (lane < t) yl = fmaf(-rt[t], xt, yl);
+                }
+            }
+            if (lane < m) y[i0 + lane] = yl;
+        }
+        __syncthreads();
+        for (int k = threadIdx.x; k < i0; k += blockDim.x) {
+            float acc = 0.0f;
+            for (int t = 0; t < m; ++t) acc = fmaf(R[(size_t)(i0 + t) * nreal + k], y[i0 + t], acc);
+            y[k] -= acc;
+        }
+        __syncthreads();
+    }
+    float ss = 0.0f;
+    for (int i = threadIdx.x; i < nreal; i += blockDim.x) ss = fmaf(y[i], y[i], ss);
+    ss = warp_sum(ss);
+    if (lane == 0) red[warp] = ss;
+    __syncthreads();
+    float tot = 0.0f;
+#pragma unroll
+    for (int w = 0; w < 8; ++w) tot += red[w];
+    const float sc = tot > 0.0f ? rsqrtf(tot) : 0.0f;
+    for (int i = threadIdx.x; i < nreal; i += blockDim.x) V[(size_t)i * ldv + j] = y[i] * sc;
+}
+
 template <int C>
-int launch_jc(nys_ctx* ctx, const double* G, int ell, int b, int max_sweeps, float* V, int ldv, int* sweeps,
-              int* status) {
+int launch_jc(nys_ctx* ctx, const double* G, int ell, int b, int max_sweeps, float* V, int ldv, float* Rsave,
+              int* sweeps, int* status) {
     const int npad = 2 * C * b;
-    const size_t smem = (size_t)4 * b * 2 * npad * sizeof(float) + (size_t)4 * b * (sizeof(float) + sizeof(int)) + 64;
+    const size_t smem = (size_t)4 * b * npad * sizeof(float) + (size_t)4 * b * (sizeof(float) + sizeof(int)) + 64;
     if (smem > 220 * 1024) return NYS_EINVAL;
     auto k = jacobi_cluster_kernel<C>;
     if (C > 8) NYS_CK(ctx, cudaFuncSetAttribute(k, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
@@ -385,22 +482,26 @@ int launch_jc(nys_ctx* ctx, const double* G, int ell, int b, int max_sweeps, flo
         cudaGetLastError();
         return NYS_EINVAL;
     }
-    NYS_CK(ctx, cudaLaunchKernelEx(&cfg, k, G, ell, b, max_sweeps, V, ldv, sweeps, status));
+    NYS_CK(ctx, cudaLaunchKernelEx(&cfg, k, G, ell, b, max_sweeps, V, ldv, Rsave, sweeps, status));
     ++ctx->launches;
+    jc_backsolve_kernel<<<ell, 256, (size_t)ell * sizeof(float), ctx->stream>>>(Rsave, V, ldv, ell, status);
+    NYS_LAUNCH_CK(ctx);
     return NYS_OK;
 }
 
 }  // namespace
 
 // V (row-major, ld = ldv, float32) = eigenvectors of the symmetric ell x ell
-// float64 matrix G by the cluster kernel above; NYS_EINVAL (nothing
+// float64 matrix G by the cluster kernel and the back substitution above;
+// Rsave: ell * ell floats of device workspace.  NYS_EINVAL (nothing
 // launched) when ell is outside [64, 448] or the cluster cannot be placed.
-// *status = 1 on the device if the float32 Cholesky of G fails.
-int jacobi_cluster(nys_ctx* ctx, const double* G, int ell, int max_sweeps, float* V, int ldv, int* sweeps,
-                   int* status) {
+// *status = 1 on the device if the float32 Cholesky of G fails (V is then
+// not written).
+int jacobi_cluster(nys_ctx* ctx, const double* G, int ell, int max_sweeps, float* V, int ldv, float* Rsave,
+                   int* sweeps, int* status) {
     if (ell < 64 || ell > 448) return NYS_EINVAL;
-    if (ell <= 256) return launch_jc<8>(ctx, G, ell, (ell + 15) / 16, max_sweeps, V, ldv, sweeps, status);
-    return launch_jc<16>(ctx, G, ell, (ell + 31) / 32, max_sweeps, V, ldv, sweeps, status);
+    if (ell <= 256) return launch_jc<8>(ctx, G, ell, (ell + 15) / 16, max_sweeps, V, ldv, Rsave, sweeps, status);
+    return launch_jc<16>(ctx, G, ell, (ell + 31) / 32, max_sweeps, V, ldv, Rsave, sweeps, status);
 }
 
 }  // namespace nys

@@ -657,7 +657,9 @@ int launch_small_gemm(nys_ctx* ctx, const double* A, int ta, const double* B, in
 
 // Eigen-decomposition of the symmetric ell x ell float64 matrix G:
 // Vout (ell x ell, columns sorted by descending eigenvalue), S_hat, scale.
-// `work` provides n*n*2 T + ell doubles.  `use_f32` picks the Jacobi type.
+// `work` provides 2 n^2 + n doubles (the float path: n^2 floats each for the
+// padded copy, V and the cluster kernel's R, and n doubles).  `use_f32` picks
+// the Jacobi type.
 int sym_eig(nys_ctx* ctx, const double* G, int ell, bool use_f32, const double* info, void* work, double* Vout,
             double* S_hat, double* scale, int* sweeps_dev) {
     const int n = (ell + 1) & ~1;
@@ -686,7 +688,10 @@ int sym_eig(nys_ctx* ctx, const double* G, int ell, bool use_f32, const double* 
             // float32 sketches of 64..448 columns: the cluster kernel (Cholesky
             // and one-sided Jacobi spread over 8 or 16 SMs, V formed in place);
             // the two-sided kernel runs instead if its Cholesky fails
-            const int stc = jacobi_cluster(ctx, G, ell, max_sweeps, (float*)V, n, sweeps_dev, status_dev);
+            // R's copy for the back substitution after lam: the work area holds
+            // 2 n^2 doubles + n, the float path uses n^2 + n^2 floats + n doubles
+            float* Rsave = (float*)(lam + n);
+            const int stc = jacobi_cluster(ctx, G, ell, max_sweeps, (float*)V, n, Rsave, sweeps_dev, status_dev);
             if (stc == NYS_OK) {
                 jacobi_kernel<T><<<1, 1024, 0, s>>>(Gw, V, n, ell, max_sweeps, tol, sweeps_dev, status_dev);
                 NYS_LAUNCH_CK(ctx);
