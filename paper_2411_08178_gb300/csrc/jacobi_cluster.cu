@@ -21,7 +21,8 @@
 //              seats (seat 0 fixed, the others shift by one), copied from the
 //              neighbouring CTAs' shared memory, and the next block round
 //              starts.  2C - 1 block rounds per sweep; the sweeps stop when
-//              no pair needed a rotation (cluster-wide vote) or after
+//              no pair needed a rotation or every pair's |x . y| / (|x| |y|)
+//              was below stop2^(1/2) (cluster-wide vote), or after
 //              max_sweeps.
 //   output     R V (row-major, ld = ldv): column idx is the rotated column
 //              that started as column idx of R; jc_backsolve_kernel turns it
@@ -44,7 +45,7 @@ constexpr int JC_THREADS = 512;   // 16 warps: one per pair of a sub-round (b <=
 template <int C>
 __global__ void __launch_bounds__(JC_THREADS, 1)
     jacobi_cluster_kernel(const double* __restrict__ G, int nreal, int b, int max_sweeps, float* __restrict__ V,
-                          int ldv, float* __restrict__ Rsave, int* __restrict__ sweeps_out,
+                          int ldv, float* __restrict__ Rsave, float stop2, int* __restrict__ sweeps_out,
                           int* __restrict__ status_out) {
     cg::cluster_group cluster = cg::this_cluster();
     const int rank = (int)cluster.block_rank();
@@ -55,7 +56,7 @@ __global__ void __launch_bounds__(JC_THREADS, 1)
     float* buf = jc_smem;                         // [4][b][npad]: cur seat 0, cur seat 1, next seat 0, next seat 1
     float* nrm = buf + 4 * (size_t)slot_len;      // [4][b]
     int* idx = reinterpret_cast<int*>(nrm + 4 * b);   // [4][b]
-    __shared__ int bad_flag, rot_flag;
+    __shared__ int bad_flag, rot_flag, rmax_bits;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 
     // seats: CTA c holds seats c and 2C - 1 - c; block k starts in seat k
@@ -181,11 +182,14 @@ __global__ void __launch_bounds__(JC_THREADS, 1)
     // the rotation that zeroes x . y = c for squared norms a (x) and bb (y):
     // t = sign(zeta) / (|zeta| + sqrt(1 + zeta^2)) with zeta = (bb - a) / (2c), the
     // smaller root of t^2 + 2 zeta t - 1 = 0, written as 2c sign(d) / (|d| + sqrt(d^2 + 4c^2)),
-    // d = bb - a: three dependent special-function operations instead of four.
-    // The squared norms move by -t c (x) and +t c (y).
+    // d = bb - a: three dependent special-function operations instead of four
+    // (the square root as h rsqrt(h), h > 0 since c != 0: the same few-ulp
+    // accuracy as the rsqrt that gives cs).  The squared norms move by -t c
+    // (x) and +t c (y).
     auto rot_params = [](float c, float a, float bb, float& cs, float& sn, float& tc) {
         const float d = bb - a;
-        const float t = __fdividef(d >= 0.0f ? 2.0f * c : -2.0f * c, fabsf(d) + sqrtf(fmaf(d, d, 4.0f * c * c)));
+        const float h = fmaf(d, d, 4.0f * c * c);
+        const float t = __fdividef(d >= 0.0f ? 2.0f * c : -2.0f * c, fabsf(d) + h * rsqrtf(h));
         cs = rsqrtf(fmaf(t, t, 1.0f));
         sn = t * cs;
         tc = t * c;
@@ -195,6 +199,8 @@ __global__ void __launch_bounds__(JC_THREADS, 1)
         o2 = make_float4(sn * p.x + cs * q.x, sn * p.y + cs * q.y, sn * p.z + cs * q.z, sn * p.w + cs * q.w);
         o1 = r1;
     };
+    // the largest (x . y)^2 / (|x|^2 |y|^2) this thread's warp met in the sweep
+    float rmax2 = 0.0f;
     auto rotate_pair = [&](float* x, float* y, float* na, float* nb_, int ix, int iy) -> bool {
         float4* xw = reinterpret_cast<float4*>(x);
         float4* yw = reinterpret_cast<float4*>(y);
@@ -212,7 +218,9 @@ __global__ void __launch_bounds__(JC_THREADS, 1)
             c += px[u].x * qy[u].x + px[u].y * qy[u].y + px[u].z * qy[u].z + px[u].w * qy[u].w;
         }
         c = warp_sum(c);
-        if (ix >= nreal || iy >= nreal || c == 0.0f || !(c * c > tol2 * (a * bb))) return false;
+        if (ix >= nreal || iy >= nreal) return false;
+        rmax2 = fmaxf(rmax2, __fdividef(c * c, a * bb));
+        if (c == 0.0f || !(c * c > tol2 * (a * bb))) return false;
         float cs, sn, tc;
         rot_params(c, a, bb, cs, sn, tc);
 #pragma unroll
@@ -247,7 +255,8 @@ __global__ void __launch_bounds__(JC_THREADS, 1)
                 if (lane == 0) nrm[(cur + s) * b + c] = a;
             }
         }
-        if (threadIdx.x == 0) rot_flag = 0;
+        if (threadIdx.x == 0) rot_flag = 0, rmax_bits = 0;
+        rmax2 = 0.0f;
         __syncthreads();
         bool rotated = false;
         for (int br = 0; br < 2 * C - 1; ++br) {
@@ -310,7 +319,9 @@ __global__ void __launch_bounds__(JC_THREADS, 1)
                             c += px[u].x * qy[u].x + px[u].y * qy[u].y + px[u].z * qy[u].z + px[u].w * qy[u].w;
                         }
                         c = warp_sum(c);
-                        if (ix < nreal && iY[j] < nreal && c != 0.0f && c * c > tol2 * (a * bb)) {
+                        const bool real = ix < nreal && iY[j] < nreal;
+                        if (real) rmax2 = fmaxf(rmax2, __fdividef(c * c, a * bb));
+                        if (real && c != 0.0f && c * c > tol2 * (a * bb)) {
                             float cs, sn, tc;
                             rot_params(c, a, bb, cs, sn, tc);
 #pragma unroll
@@ -371,16 +382,27 @@ __global__ void __launch_bounds__(JC_THREADS, 1)
                     idx[(nxt + s) * b + c] = si[c];
                 }
             }
-            cluster.sync();
+            // a block barrier suffices here: the buffers just read in other
+            // CTAs (their current seats) are next written by the copy of the
+            // following move, after its cluster barrier, which every CTA
+            // reaches only once this copy is done
+            __syncthreads();
             cur = nxt;
         }
         // cluster-wide vote: did any pair rotate in this sweep?
         if (rotated) atomicOr(&rot_flag, 1);
+        // non-negative floats order as their bit patterns
+        if (lane == 0) atomicMax(&rmax_bits, __float_as_int(rmax2));
         cluster.sync();
         int any = 0;
-        for (int r = 0; r < C; ++r) any |= *cluster.map_shared_rank(&rot_flag, r);
+        float cmax2 = 0.0f;
+#pragma unroll 1
+        for (int r = 0; r < C; ++r) {
+            any |= *cluster.map_shared_rank(&rot_flag, r);
+            cmax2 = fmaxf(cmax2, __int_as_float(*cluster.map_shared_rank(&rmax_bits, r)));
+        }
         cluster.sync();
-        if (!any) {
+        if (!any || cmax2 < stop2) {
             ++sweep;
             break;
         }
@@ -482,7 +504,11 @@ int launch_jc(nys_ctx* ctx, const double* G, int ell, int b, int max_sweeps, flo
         cudaGetLastError();
         return NYS_EINVAL;
     }
-    NYS_CK(ctx, cudaLaunchKernelEx(&cfg, k, G, ell, b, max_sweeps, V, ldv, Rsave, sweeps, status));
+    // stop after a sweep whose largest |x . y| / (|x| |y|) was below 1e-3: its
+    // rotations leave off-diagonal terms of the order of its square, at the
+    // float32 floor of the test (quadratic convergence), so the sweep that
+    // would only confirm it is skipped
+    NYS_CK(ctx, cudaLaunchKernelEx(&cfg, k, G, ell, b, max_sweeps, V, ldv, Rsave, 1e-6f, sweeps, status));
     ++ctx->launches;
     jc_backsolve_kernel<<<ell, 256, (size_t)ell * sizeof(float), ctx->stream>>>(Rsave, V, ldv, ell, status);
     NYS_LAUNCH_CK(ctx);
