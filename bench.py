@@ -441,7 +441,13 @@ class Native:
         lb = 0.9 * w.lam
         fn = self.api.prox_hs if w.reg == "hs" else self.api.prox_tv
         le, ub, f = self.pc.ell_active, (2 if self.sd == torch.bfloat16 else 4), 4
-        ms = self._graph_ms(lambda: fn(self.ctx, self.pc, lb, w.n_inner, s, Q=Q, out=out), reps)
+        # every dual step runs here (the early stop off): the figure is the
+        # cost of one step, and the replays warm-start from their own Q
+        self.ctx.set_dual_stop(False)
+        try:
+            ms = self._graph_ms(lambda: fn(self.ctx, self.pc, lb, w.n_inner, s, Q=Q, out=out), reps)
+        finally:
+            self.ctx.set_dual_stop(True)
         uc = le * N * ub + 2 * N * f + N * f                 # U, g and s in, x out
         lt_utz = G * N * f + le * N * ub + N * f             # R (or Q) in, U, g out
         if w.reg == "tv" and le <= 64:
@@ -495,14 +501,19 @@ def secondary_workload(w: WL.Workload, device: int, sketch_dtype: str, ref_iters
             xstar, Fstar, info = nb.reference_solution(ref_iters)
             out["reference_solution"] = info
             k_0, e_0, k_0s = nb.iterations_to(nb.solver_0, xstar, Fstar, kmax)
+            a = nb.ctx.dual_steps_skipped()
             ms_0 = statistics.mean(nb.time_loop(lambda: nb.solve_plain(k_0 or kmax), steps, 2, "other_plain"))
-            out["plain"] = {"k": k_0, "k_settled": k_0s, "ms": round(ms_0, 3), "iterate_err_at_k": e_0}
+            sk_0 = (nb.ctx.dual_steps_skipped() - a) / (steps + 2)
+            out["plain"] = {"k": k_0, "k_settled": k_0s, "ms": round(ms_0, 3), "iterate_err_at_k": e_0,
+                            "dual_steps_skipped_per_solve": sk_0}
         k_p, e_p, k_ps = nb.iterations_to(nb.solver_p, xstar, Fstar, kmax)
+        a = nb.ctx.dual_steps_skipped()
         ms_p = statistics.mean(nb.time_loop(lambda: nb.solve_precond(k_p or kmax), steps, 2, "other_precond"))
+        sk_p = (nb.ctx.dual_steps_skipped() - a) / (steps + 2)
         sk = statistics.median(nb.time_loop(nb.sketch_factor, steps, 1, "other_sketch"))
         out["sqrt_shift_on" if sqrt_shift else "sqrt_shift_off"] = {
             "k_precond": k_p, "k_precond_settled": k_ps, "ms": round(ms_p, 3), "sketch_ms": round(sk, 3),
-            "active_columns": nb.pc.ell_active,
+            "active_columns": nb.pc.ell_active, "dual_steps_skipped_per_solve": sk_p,
             "iterate_err_at_k": e_p, "speedup_vs_plain": round(out["plain"]["ms"] / ms_p, 3)}
         if sqrt_shift:
             # the sketch-size rule between plain APG and the configured sketch
@@ -539,9 +550,12 @@ def run_native(args, w: WL.Workload):
     l0 = nb.ctx.launches()
     if world > 1:
         torch.distributed.barrier()
+    s0 = nb.ctx.dual_steps_skipped()
     times_p = nb.time_loop(lambda: nb.solve_precond(k_p_run), args.steps, args.warmup, "timed_precond")
     l1 = nb.ctx.launches()
+    s1 = nb.ctx.dual_steps_skipped()
     times_0 = nb.time_loop(lambda: nb.solve_plain(k_0_run), plain_steps, min(args.warmup, 2), "timed_plain")
+    s2 = nb.ctx.dual_steps_skipped()
     clk = clocks.stop()
     if world > 1:
         torch.distributed.barrier()
@@ -605,6 +619,8 @@ def run_native(args, w: WL.Workload):
                                "iterations after the first hit (Algorithm 3 is not monotone); k_precond and "
                                "k_plain are the first hits, the counts the timed solves run")},
         "iterate_err": {"precond_at_k": err_p, "plain_at_k": err_0},
+        "dual_stop": dual_stop_info(w, (s1 - s0) / (args.steps + args.warmup), k_p_run,
+                                    (s2 - s1) / (plain_steps + min(args.warmup, 2)), k_0_run),
         "reference_solution": {"F_star": Fstar, **ref_info},
         "e2e": {"value": round(ms_e, 3), "unit": "ms", "steps": plain_steps, "h2d_bytes_per_step": int(nb.y.numel() * 4),
                 "d2h_bytes_per_step": int(N * 4)},
@@ -635,6 +651,20 @@ def run_native(args, w: WL.Workload):
         print(json.dumps(out))
     if world > 1:
         torch.distributed.destroy_process_group()
+
+
+def dual_stop_info(w: WL.Workload, skipped_p, k_p, skipped_0, k_0) -> dict:
+    """Dual steps the exact early stop skipped per timed solve (bit-identical
+    results: a step is skipped only after one that changed nothing)."""
+    if w.reg != "tv":
+        return {"applies": False, "what": "the exact early stop serves the anisotropic-TV prox only"}
+    return {"applies": True,
+            "precond": {"skipped_per_solve": skipped_p, "of": k_p * w.n_inner,
+                        "fraction": round(skipped_p / max(1, k_p * w.n_inner), 4)},
+            "plain": {"skipped_per_solve": skipped_0, "of": k_0 * w.n_inner,
+                      "fraction": round(skipped_0 / max(1, k_0 * w.n_inner), 4)},
+            "what": ("dual steps skipped once a step left the dual iterate and its extrapolation unchanged "
+                     "(results bit-identical to running all n_inner steps); the roofline figures run every step")}
 
 
 def load_peaks():

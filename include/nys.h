@@ -94,6 +94,18 @@ const char* nys_version(void);
 int nys_l2_persist(nys_ctx* ctx, const void* ptr, size_t bytes, double hit_ratio);
 /* Number of kernels launched through this context since it was created. */
 int nys_launch_count(const nys_ctx* ctx, int64_t* count);
+/* Exact early stop of the dual APG of the anisotropic-TV prox (Sec. III-B,
+ * the dual problem solved by APG), on by default: once a dual step j >= 1
+ * leaves every component of the dual iterate and of its extrapolation
+ * unchanged, every later step would reproduce it (a step is a deterministic
+ * function of that pair), so the remaining steps of the call are skipped on
+ * the device and the result is bit-identical to running all n_inner steps.
+ * on = 0 runs every step.  Takes effect for prox calls issued, and solver
+ * iterations captured, after the call; NYS_EINVAL for a null context. */
+int nys_set_dual_stop(nys_ctx* ctx, int on);
+/* Dual steps skipped by the early stop on this context so far (a 32-bit
+ * device counter, wraps); synchronises the context's stream. */
+int nys_dual_steps_skipped(nys_ctx* ctx, int64_t* count);
 
 /* ------------------------------------------------------------ operators -- */
 /* Forward models of Sec. IV: periodic blur (IV-A), blur + decimation

@@ -79,6 +79,8 @@ PROTOTYPES = {
     "nys_reserve": (i32, [vp, C.c_size_t]),
     "nys_version": (C.c_char_p, []),
     "nys_launch_count": (i32, [vp, C.POINTER(i64)]),
+    "nys_set_dual_stop": (i32, [vp, i32]),
+    "nys_dual_steps_skipped": (i32, [vp, C.POINTER(i64)]),
     "nys_l2_persist": (i32, [vp, vp, C.c_size_t, f64]),
     "nys_op_create": (i32, [vp, C.POINTER(nys_op_desc), C.POINTER(vp)]),
     "nys_op_destroy": (i32, [vp]),

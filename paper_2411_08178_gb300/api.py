@@ -77,6 +77,15 @@ class Context:
         check(_lib().nys_launch_count(self.h, C.byref(n)), self.h)
         return n.value
 
+    def set_dual_stop(self, on: bool = True):
+        """Exact early stop of the TV dual iteration (bit-identical results)."""
+        check(_lib().nys_set_dual_stop(self.h, int(bool(on))), self.h)
+
+    def dual_steps_skipped(self) -> int:
+        n = C.c_int64()
+        check(_lib().nys_dual_steps_skipped(self.h, C.byref(n)), self.h)
+        return n.value
+
     def last_error(self) -> str:
         return _lib().nys_last_error(self.h).decode()
 

@@ -166,6 +166,22 @@ int nys_launch_count(const nys_ctx* ctx, int64_t* count) {
     return NYS_OK;
 }
 
+int nys_set_dual_stop(nys_ctx* ctx, int on) {
+    if (!ctx) return fail(nullptr, NYS_EINVAL, "nys_set_dual_stop: null context");
+    ctx->dual_stop = on != 0;
+    return NYS_OK;
+}
+
+int nys_dual_steps_skipped(nys_ctx* ctx, int64_t* count) {
+    if (!ctx || !count) return fail(ctx, NYS_EINVAL, "nys_dual_steps_skipped: null argument");
+    unsigned v = 0;
+    NYS_CK(ctx, cudaMemcpyAsync(&v, ctx->counters + nys::COUNTER_DUAL_SKIPPED, sizeof(unsigned),
+                                cudaMemcpyDeviceToHost, ctx->stream));
+    NYS_CK(ctx, cudaStreamSynchronize(ctx->stream));
+    *count = v;
+    return NYS_OK;
+}
+
 const char* nys_last_error(const nys_ctx* ctx) {
     if (ctx) return ctx->err.c_str();
     std::lock_guard<std::mutex> g(g_err_mu);

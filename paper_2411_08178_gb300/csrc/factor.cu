@@ -273,10 +273,12 @@ int precond_vec(nys_ctx* ctx, const nys_precond* pc, int inverse, const void* z,
     const dim3 grid((unsigned)((N + P - 1) / P), batch);
     if (pvx == 1)
         NYS_CK(ctx, launch_pdl(uc_vec_kernel<TU, TZ, TA>, grid, 256, sm, s, (const TU*)pc->U, (const TZ*)z, N, ell,
-                               coef, inverse ? TA(-1) : TA(1), (TZ*)out, (const TZ*)nullptr, TA(1), keep));
+                               coef, inverse ? TA(-1) : TA(1), (TZ*)out, (const TZ*)nullptr, TA(1), keep,
+                               DualStop{}));
     else
         NYS_CK(ctx, launch_pdl(uc_vec_kernel<TU, TZ, TA, 2, 2>, grid, 256, sm, s, (const TU*)pc->U, (const TZ*)z, N,
-                               ell, coef, inverse ? TA(-1) : TA(1), (TZ*)out, (const TZ*)nullptr, TA(1), keep));
+                               ell, coef, inverse ? TA(-1) : TA(1), (TZ*)out, (const TZ*)nullptr, TA(1), keep,
+                               DualStop{}));
     NYS_LAUNCH_CK(ctx);
     return NYS_OK;
 }
@@ -303,7 +305,8 @@ int precond_partial_typed(nys_ctx* ctx, const nys_precond* pc, const void* z, TA
     NYS_CK(ctx, launch_pdl(utz_vec_kernel<TU, TZ, TA>, dim3(nchunk, groups, batch), 256, 0, s, (const TU*)pc->U,
                            (const TZ*)z, N, ell, jper, part, keep));
     NYS_LAUNCH_CK(ctx);
-    NYS_CK(ctx, launch_pdl(reduce_cols_kernel<TA>, dim3((ell + 7) / 8, batch), 256, 0, s, part, nchunk, ell, w));
+    NYS_CK(ctx, launch_pdl(reduce_cols_kernel<TA>, dim3((ell + 7) / 8, batch), 256, 0, s, part, nchunk, ell, w,
+                           DualStop{}));
     NYS_LAUNCH_CK(ctx);
     return NYS_OK;
 }
@@ -327,14 +330,14 @@ int precond_finish_typed(nys_ctx* ctx, const nys_precond* pc, int inverse, const
     const TM* Mp = sizeof(TA) == 8 ? (const TM*)pv->M64 : (const TM*)pv->M32;
     const TM* dp = sizeof(TA) == 8 ? (const TM*)pv->d : (const TM*)pv->d32;
     NYS_CK(ctx, launch_pdl(mw_kernel<TA, TM>, dim3((ell + 7) / 8, batch), 256, ell * sizeof(TA), s, Mp, pc->ell, inverse,
-                           dp, w, ell, coef));
+                           dp, w, ell, coef, DualStop{}));
     NYS_LAUNCH_CK(ctx);
     const int keep = l2_keep_cols(ctx, N, sizeof(TU), ell);
     const int P = 32 * V * 2;
     const size_t sm = (((size_t)ell + 3) & ~size_t(3)) * sizeof(TA) + (size_t)8 * P * sizeof(TA);
     NYS_CK(ctx, launch_pdl(uc_vec_kernel<TU, TZ, TA, 2, 2>, dim3((unsigned)((N + P - 1) / P), batch), 256, sm, s,
                            (const TU*)pc->U, (const TZ*)z, N, ell, coef, inverse ? TA(-1) : TA(1), (TZ*)out,
-                           (const TZ*)nullptr, TA(1), keep));
+                           (const TZ*)nullptr, TA(1), keep, DualStop{}));
     NYS_LAUNCH_CK(ctx);
     return NYS_OK;
 }

@@ -76,6 +76,9 @@ struct nys_ctx {
     bool l2_window_set = false;
     std::string err;
     unsigned* counters = nullptr;   // device, 64 completion counters (see vec.cuh)
+    // exact early stop of the anisotropic-TV dual iteration (DualStop below),
+    // on unless nys_set_dual_stop turned it off
+    bool dual_stop = true;
     // the context is freed when its owner (nys_destroy) and every object
     // created on it (operators, solvers, unrolled solves, batches) are gone,
     // in whatever order they are destroyed
@@ -182,6 +185,42 @@ __device__ __forceinline__ void pdl_enter() {
 }
 
 int pdl_mode();   // api.cu: 0, 1 or 2 as above
+
+// Exact early stop of the dual APG of the anisotropic-TV prox.  A dual step
+// maps (R, Q) to (R', Q') by a fixed deterministic function of (R, Q) and of
+// beta, and beta only multiplies Q' - Q.  If a step leaves every component
+// unchanged (Q' = R = Q), every later step reproduces it exactly, so once a
+// step j >= 1 has changed nothing, steps j + 2 ... may be skipped: both
+// ping-pong buffers already hold the fixed point (step j's inputs and
+// outputs), and the result is bit-identical to running them.  (Step 0's
+// input g comes from a differently ordered L^T, so it does not count.)
+// Three flags in ctx->counters: step k sets flags[k % 3] when any component
+// changed and clears flags[(k + 1) % 3] for step k + 1; step k >= 2 is
+// skipped when flags[(k - 1) % 3] is clear.  A skipped last step still
+// writes Q (and, without a preconditioner, the output x) out.
+constexpr int COUNTER_DUAL_STOP = 8;      // flags at counters[8 .. 10]
+constexpr int COUNTER_DUAL_SKIPPED = 11;  // dual steps skipped (wraps)
+struct DualStop {
+    unsigned* flags = nullptr;   // nullptr: this launch never skips
+    int k = 0;                   // the dual step of this launch
+};
+__device__ __forceinline__ bool dual_skip(const DualStop& s) {
+    return s.flags && s.k >= 2 && *(volatile const unsigned*)(s.flags + (s.k + 2) % 3) == 0u;
+}
+// the step's own bookkeeping, by one thread of the grid: clear the next
+// step's flag and count a skip
+__device__ __forceinline__ void dual_stop_enter(const DualStop& s, bool skip) {
+    if (s.flags && blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0) {
+        s.flags[(s.k + 1) % 3] = 0u;
+        if (skip) atomicAdd(s.flags + (COUNTER_DUAL_SKIPPED - COUNTER_DUAL_STOP), 1u);
+    }
+}
+// a step that computed: set its flag when any thread of the block saw a change
+// (every thread of the block calls this)
+__device__ __forceinline__ void dual_stop_report(const DualStop& s, bool changed) {
+    const int any = __syncthreads_or(changed ? 1 : 0);
+    if (s.flags && any && threadIdx.x == 0) s.flags[s.k % 3] = 1u;
+}
 
 inline bool pdl_enabled(cudaStream_t stream) {
     const int m = pdl_mode();

@@ -60,19 +60,35 @@ __global__ void axpy_kernel(const T* __restrict__ s, const T* __restrict__ pg, t
 }
 
 // Plain (P = I) anisotropic-TV dual step fused with the x after it:
-// out = s - lb L^T R_new (L^T Q_new on the last step); out is not d.x
+// out = s - lb L^T R_new (L^T Q_new on the last step); out is not d.x.
+// With the exact early stop (internal.cuh) a skipped step does nothing, a
+// skipped last step writes Q and out = x (at the fixed point R = Q, so the
+// two L^T agree bit for bit).
 template <class T>
 __global__ void tv_dual_x_kernel(TvDual<T> d, const T* __restrict__ s, typename Comp<T>::type lb, int n1, int n2,
-                                 T* __restrict__ out) {
+                                 T* __restrict__ out, DualStop stop) {
     pdl_enter();
     using TC = typename Comp<T>::type;
     const int64_t N = (int64_t)n1 * n2;
+    const bool skip = dual_skip(stop);
+    dual_stop_enter(stop, skip);
+    if (skip) {
+        if (!d.Rn)
+            for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < N;
+                 t += (int64_t)gridDim.x * blockDim.x) {
+                tv_dual_copy_q<T>(d, (size_t)t, (size_t)N);
+                out[t] = d.x[t];
+            }
+        return;
+    }
+    bool chg = false;
     for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < N; t += (int64_t)gridDim.x * blockDim.x) {
         int i, j;
         pix_ij(t, n2, i, j);
-        const TC g = tv_dual_lt<T>(d, i, j, n1, n2);
+        const TC g = tv_dual_lt<T>(d, i, j, n1, n2, &chg);
         out[t] = (T)((TC)s[t] - lb * g);
     }
+    dual_stop_report(stop, chg);
 }
 
 template <class T, int REG>
@@ -119,8 +135,11 @@ int prox_dual_typed(nys_ctx* ctx, const nys_precond* pc, double lb, int n_inner,
             d.Qn = (fin && k) ? Q : RQ[(k + 1) & 1][1];
             d.step = step;
             d.beta = (TC)beta;
+            DualStop ds;
+            if (ctx->dual_stop) ds.flags = ctx->counters + COUNTER_DUAL_STOP;
+            ds.k = k;
             NYS_CK(ctx, launch_pdl(tv_dual_x_kernel<T>, grid, 256, 0, sm, d, s, (TC)lb, n1, n2,
-                                   fin ? out : X[(k + 1) & 1]));
+                                   fin ? out : X[(k + 1) & 1], ds));
             NYS_LAUNCH_CK(ctx);
         }
         if (n_inner == 1) NYS_CK(ctx, cudaMemcpyAsync(Q, RQ[1][1], sizeof(T) * G * N, cudaMemcpyDeviceToDevice, sm));

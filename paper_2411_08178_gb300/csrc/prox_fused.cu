@@ -52,7 +52,7 @@ __global__ void __launch_bounds__(256) lt_utz_kernel(const T* __restrict__ R, in
                                                      const TM* __restrict__ M, T* __restrict__ g,
                                                      TA* __restrict__ part, TA* __restrict__ coef,
                                                      unsigned* __restrict__ counter, TvDual<T> dual, int keep,
-                                                     XStage<T, TA> xr) {
+                                                     XStage<T, TA> xr, DualStop stop) {
     pdl_enter();
     static_assert(!DUAL || REG == NYS_REG_TV, "the fused dual step is for anisotropic TV");
     static_assert(!XR || DUAL, "x is staged only for the fused dual step");
@@ -67,6 +67,18 @@ __global__ void __launch_bounds__(256) lt_utz_kernel(const T* __restrict__ R, in
     TA* cs = xs + nst;
     TA* sm = XR ? cs + 64 : xs;   // last CTA: w and (le <= 64) M
     const int64_t base = XR ? (i0 - n2 + N) % N : 0;   // first staged pixel
+    if constexpr (DUAL) {
+        // the exact early stop (internal.cuh): a skipped step writes nothing
+        // (the last one only Q)
+        const bool skip = dual_skip(stop);
+        dual_stop_enter(stop, skip);
+        if (skip) {
+            if (!dual.Rn)
+                for (int q = threadIdx.x; q < FCH && i0 + q < N; q += blockDim.x)
+                    tv_dual_copy_q<T>(dual, (size_t)(i0 + q), (size_t)N);
+            return;
+        }
+    }
     if constexpr (XR) {
         for (int k = threadIdx.x; k < le; k += blockDim.x) cs[k] = xr.c[k];
         __syncthreads();
@@ -99,6 +111,7 @@ __global__ void __launch_bounds__(256) lt_utz_kernel(const T* __restrict__ R, in
         return (TC)xs[o];
     };
     TA v[PT];
+    bool chg = false;
 #pragma unroll
     for (int q = 0; q < PT; ++q) {
         const int64_t p = i0 + threadIdx.x + q * 256;
@@ -107,9 +120,9 @@ __global__ void __launch_bounds__(256) lt_utz_kernel(const T* __restrict__ R, in
             int i, j;
             pix_ij(p, n2, i, j);
             if constexpr (XR)
-                v[q] = (TA)tv_dual_lt_f<T>(dual, xf, i, j, n1, n2);
+                v[q] = (TA)tv_dual_lt_f<T>(dual, xf, i, j, n1, n2, &chg);
             else
-                v[q] = DUAL ? (TA)tv_dual_lt<T>(dual, i, j, n1, n2) : (TA)lt_q<T, REG>(R, i, j, n1, n2);
+                v[q] = DUAL ? (TA)tv_dual_lt<T>(dual, i, j, n1, n2, &chg) : (TA)lt_q<T, REG>(R, i, j, n1, n2);
         }
     }
 #pragma unroll
@@ -119,7 +132,8 @@ __global__ void __launch_bounds__(256) lt_utz_kernel(const T* __restrict__ R, in
         if (p < N) g[p] = (T)v[q];
         gs[threadIdx.x + q * 256] = v[q];
     }
-    __syncthreads();
+    if constexpr (DUAL) dual_stop_report(stop, chg);   // (a block barrier)
+    else __syncthreads();
     if (le == 0) return;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int cnt = (int)(N - i0 < (int64_t)FCH ? N - i0 : (int64_t)FCH);   // multiple of V
@@ -214,34 +228,44 @@ int fused_typed(nys_ctx* ctx, const nys_precond* pc, double lb, int n_inner, int
     unsigned* counter = ctx->counters + COUNTER_PROX;
     const int keep = l2_keep_cols(ctx, N, sizeof(TU), le);
     const XStage<T, TA> xr0 = {};
+    const DualStop nostop{};
+    // the exact early stop of the TV dual iteration for step k (internal.cuh)
+    auto stop_at = [&](int k) {
+        DualStop ds;
+        if (ctx->dual_stop) ds.flags = ctx->counters + COUNTER_DUAL_STOP;
+        ds.k = k;
+        return ds;
+    };
     // g = L^T Rin, or the fused TV dual step and the L^T after it (dual.x
-    // set); then x (or out) = s - lb (g - U c), c = M U^T g
-    auto xfn = [&](const T* Rin, const TvDual<T>& dual, T* dst) -> int {
+    // set); then x (or out) = s - lb (g - U c), c = M U^T g.  ds: the dual
+    // step's early stop (the x pass of the last step always runs)
+    auto xfn = [&](const T* Rin, const TvDual<T>& dual, T* dst, DualStop ds) -> int {
+        const DualStop ucs = dual.Rn ? ds : nostop;
         if (last) {
             if (dual.x)
                 NYS_CK(ctx, launch_pdl(lt_utz_kernel<TU, T, TA, TM, REG, true, FCH, TV>, nchunk, 256, lsm, sm, Rin,
-                                       n1, n2, (const TU*)pc->U, le, pc->ell, M, g, part, coef, counter, dual, keep, xr0));
+                                       n1, n2, (const TU*)pc->U, le, pc->ell, M, g, part, coef, counter, dual, keep, xr0, ds));
             else
                 NYS_CK(ctx, launch_pdl(lt_utz_kernel<TU, T, TA, TM, REG, true, FCH, false>, nchunk, 256, lsm, sm, Rin,
-                                       n1, n2, (const TU*)pc->U, le, pc->ell, M, g, part, coef, counter, dual, keep, xr0));
+                                       n1, n2, (const TU*)pc->U, le, pc->ell, M, g, part, coef, counter, dual, keep, xr0, ds));
             NYS_LAUNCH_CK(ctx);
         } else {
             if (dual.x)
                 NYS_CK(ctx, launch_pdl(lt_utz_kernel<TU, T, TA, TM, REG, false, FCH_WIDE, TV>, nchunk, 256, 16, sm,
-                                       Rin, n1, n2, (const TU*)pc->U, le, pc->ell, M, g, part, coef, counter, dual, keep, xr0));
+                                       Rin, n1, n2, (const TU*)pc->U, le, pc->ell, M, g, part, coef, counter, dual, keep, xr0, ds));
             else
                 NYS_CK(ctx, launch_pdl(lt_utz_kernel<TU, T, TA, TM, REG, false, FCH_WIDE, false>, nchunk, 256, 16, sm,
-                                       Rin, n1, n2, (const TU*)pc->U, le, pc->ell, M, g, part, coef, counter, dual, keep, xr0));
+                                       Rin, n1, n2, (const TU*)pc->U, le, pc->ell, M, g, part, coef, counter, dual, keep, xr0, ds));
             NYS_LAUNCH_CK(ctx);
-            int st2 = coef_run<TA, TM>(ctx, part, nchunk, le, pc->ell, 1, M, (const TM*)nullptr, coef, 1, wbuf);
+            int st2 = coef_run<TA, TM>(ctx, part, nchunk, le, pc->ell, 1, M, (const TM*)nullptr, coef, 1, wbuf, ds);
             if (st2) return st2;
         }
         if (pvx == 1)
             NYS_CK(ctx, launch_pdl(uc_vec_kernel<TU, T, TA>, dim3(ug, 1), 256, usm, sm, (const TU*)pc->U, g, N, le,
-                                   coef, TA(-1), dst, s, (TA)(-lb), keep));
+                                   coef, TA(-1), dst, s, (TA)(-lb), keep, ucs));
         else
             NYS_CK(ctx, launch_pdl(uc_vec_kernel<TU, T, TA, 2, 2>, dim3(ug, 1), 256, usm, sm, (const TU*)pc->U, g, N,
-                                   le, coef, TA(-1), dst, s, (TA)(-lb), keep));
+                                   le, coef, TA(-1), dst, s, (TA)(-lb), keep, ucs));
         NYS_LAUNCH_CK(ctx);
         return NYS_OK;
     };
@@ -257,7 +281,8 @@ int fused_typed(nys_ctx* ctx, const nys_precond* pc, double lb, int n_inner, int
         T* gb[2] = {g, x};
         TA* cb[2] = {coef, wbuf};
         NYS_CK(ctx, launch_pdl(lt_utz_kernel<TU, T, TA, TM, REG, true, FCH, false>, nchunk, 256, lsm, sm, Q, n1, n2,
-                               (const TU*)pc->U, le, pc->ell, M, gb[0], part, cb[0], counter, none, keep, xr0));
+                               (const TU*)pc->U, le, pc->ell, M, gb[0], part, cb[0], counter, none, keep, xr0,
+                               nostop));
         NYS_LAUNCH_CK(ctx);
         for (int k = 0; k < n_inner; ++k) {
             const double tn = 0.5 * (1.0 + std::sqrt(1.0 + 4.0 * t * t));
@@ -275,11 +300,11 @@ int fused_typed(nys_ctx* ctx, const nys_precond* pc, double lb, int n_inner, int
             const XStage<T, TA> xr = {s, gb[k & 1], cb[k & 1], (TA)lb};
             NYS_CK(ctx, launch_pdl(lt_utz_kernel<TU, T, TA, TM, REG, true, FCH, TV, TV>, nchunk, 256, xsm, sm,
                                    (const T*)nullptr, n1, n2, (const TU*)pc->U, le, pc->ell, M, gb[(k + 1) & 1], part,
-                                   cb[(k + 1) & 1], counter, d, keep, xr));
+                                   cb[(k + 1) & 1], counter, d, keep, xr, stop_at(k)));
             NYS_LAUNCH_CK(ctx);
         }
         NYS_CK(ctx, launch_pdl(uc_vec_kernel<TU, T, TA>, dim3(ug, 1), 256, usm, sm, (const TU*)pc->U, gb[n_inner & 1],
-                               N, le, cb[n_inner & 1], TA(-1), out, s, (TA)(-lb), keep));
+                               N, le, cb[n_inner & 1], TA(-1), out, s, (TA)(-lb), keep, nostop));
         NYS_LAUNCH_CK(ctx);
         if (n_inner == 1) NYS_CK(ctx, cudaMemcpyAsync(Q, RQ[1][1], sizeof(T) * G * N, cudaMemcpyDeviceToDevice, sm));
         return NYS_OK;
@@ -288,7 +313,7 @@ int fused_typed(nys_ctx* ctx, const nys_precond* pc, double lb, int n_inner, int
         // warm start R = Q = Q_in; step k reads (R, Q) from RQ[k & 1] (Q_in
         // itself for k = 0) and writes RQ[(k + 1) & 1]; the last step writes
         // only Q, straight into Q_in when that is not its own input
-        if ((st = xfn(Q, none, n_inner ? x : out))) return st;
+        if ((st = xfn(Q, none, n_inner ? x : out, nostop))) return st;
         for (int k = 0; k < n_inner; ++k) {
             const double tn = 0.5 * (1.0 + std::sqrt(1.0 + 4.0 * t * t));
             const double beta = (t - 1.0) / tn;
@@ -302,7 +327,7 @@ int fused_typed(nys_ctx* ctx, const nys_precond* pc, double lb, int n_inner, int
             d.Qn = (fin && k) ? Q : RQ[(k + 1) & 1][1];
             d.step = step;
             d.beta = (TA)beta;
-            if ((st = xfn(nullptr, d, fin ? out : x))) return st;
+            if ((st = xfn(nullptr, d, fin ? out : x, stop_at(k)))) return st;
         }
         if (n_inner == 1) NYS_CK(ctx, cudaMemcpyAsync(Q, RQ[1][1], sizeof(T) * G * N, cudaMemcpyDeviceToDevice, sm));
         return NYS_OK;
@@ -312,7 +337,7 @@ int fused_typed(nys_ctx* ctx, const nys_precond* pc, double lb, int n_inner, int
     NYS_CK(ctx, cudaMemcpyAsync(R, Q, sizeof(T) * G * N, cudaMemcpyDeviceToDevice, sm));
     NYS_CK(ctx, cudaMemcpyAsync(Qp, Q, sizeof(T) * G * N, cudaMemcpyDeviceToDevice, sm));
     for (int k = 0; k < n_inner; ++k) {
-        if ((st = xfn(R, none, x))) return st;
+        if ((st = xfn(R, none, x, nostop))) return st;
         const double tn = 0.5 * (1.0 + std::sqrt(1.0 + 4.0 * t * t));
         const double beta = (t - 1.0) / tn;
         t = tn;
@@ -320,7 +345,7 @@ int fused_typed(nys_ctx* ctx, const nys_precond* pc, double lb, int n_inner, int
         NYS_LAUNCH_CK(ctx);
     }
     NYS_CK(ctx, cudaMemcpyAsync(Q, Qp, sizeof(T) * G * N, cudaMemcpyDeviceToDevice, sm));
-    return xfn(Qp, none, out);
+    return xfn(Qp, none, out, nostop);
 }
 
 }  // namespace

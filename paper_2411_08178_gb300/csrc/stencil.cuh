@@ -161,9 +161,11 @@ struct TvDual {
 // float64 iterates), and explicit fma keeps the recomputed neighbour values
 // bit-identical to the ones their own pixel writes.
 // xf(q) gives x at flat index q (from memory, or from a staged copy).
+// chg (not on the last step): set when the new (R, Q) at (i, j) differs
+// from the old one (the test of the exact early stop, internal.cuh).
 template <class T, class XF>
 __device__ __forceinline__ typename Comp<T>::type tv_dual_lt_f(const TvDual<T>& d, XF xf, int i, int j, int n1,
-                                                               int n2) {
+                                                               int n2, bool* chg = nullptr) {
     using TC = typename Comp<T>::type;
     const size_t N = (size_t)n1 * n2;
     const size_t r0 = (size_t)i * n2, rm = (size_t)wrap_dec(i, n1) * n2, rp = (size_t)wrap_inc(i, n1) * n2;
@@ -182,12 +184,22 @@ __device__ __forceinline__ typename Comp<T>::type tv_dual_lt_f(const TvDual<T>& 
     const TC r1 = mom(t, q1), r2 = mom(N + t, q2);
     d.Rn[t] = (T)r1;
     d.Rn[N + t] = (T)r2;
+    if (chg && !(q1 == (TC)d.Ro[t] && q1 == (TC)d.Qo[t] && q2 == (TC)d.Ro[N + t] && q2 == (TC)d.Qo[N + t]))
+        *chg = true;
     return r1 - mom(td, q1d) + r2 - mom(N + tr, q2r);
 }
 template <class T>
-__device__ __forceinline__ typename Comp<T>::type tv_dual_lt(const TvDual<T>& d, int i, int j, int n1, int n2) {
+__device__ __forceinline__ typename Comp<T>::type tv_dual_lt(const TvDual<T>& d, int i, int j, int n1, int n2,
+                                                             bool* chg = nullptr) {
     using TC = typename Comp<T>::type;
-    return tv_dual_lt_f<T>(d, [&](size_t q) { return (TC)d.x[q]; }, i, j, n1, n2);
+    return tv_dual_lt_f<T>(d, [&](size_t q) { return (TC)d.x[q]; }, i, j, n1, n2, chg);
+}
+
+// A skipped last dual step: the fixed point's Q out (both components)
+template <class T>
+__device__ __forceinline__ void tv_dual_copy_q(const TvDual<T>& d, size_t t, size_t N) {
+    d.Qn[t] = d.Qo[t];
+    d.Qn[N + t] = d.Qo[N + t];
 }
 
 namespace {

@@ -168,10 +168,12 @@ __global__ void __launch_bounds__(256) coef_vec_kernel(const TA* __restrict__ pa
 // Large le, two passes spread over many CTAs.  reduce_cols: w[b][j] =
 // sum_c part[b][j][c], one warp per column (8 per CTA); mw: coef[b][r] =
 // inverse ? sum_k M[r][k] w[b][k] : d[r] w[b][r], one warp per row.
+// (stop: inside the dual iteration of the prox, a skipped step does nothing)
 template <class TA>
 __global__ void __launch_bounds__(256) reduce_cols_kernel(const TA* __restrict__ part, int nb, int le,
-                                                          TA* __restrict__ w) {
+                                                          TA* __restrict__ w, DualStop stop) {
     pdl_enter();
+    if (dual_skip(stop)) return;
     const int j = blockIdx.x * 8 + (threadIdx.x >> 5), lane = threadIdx.x & 31, b = blockIdx.y;
     if (j >= le) return;
     const TA* p = part + ((size_t)b * le + j) * nb;
@@ -193,8 +195,9 @@ __global__ void __launch_bounds__(256) reduce_cols_kernel(const TA* __restrict__
 template <class TA, class TM>
 __global__ void __launch_bounds__(256) mw_kernel(const TM* __restrict__ M, int ldm, int inverse,
                                                  const TM* __restrict__ d, const TA* __restrict__ w, int le,
-                                                 TA* __restrict__ coef) {
+                                                 TA* __restrict__ coef, DualStop stop) {
     pdl_enter();
+    if (dual_skip(stop)) return;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     TA* ws = reinterpret_cast<TA*>(smem_raw);
     const int b = blockIdx.y;
@@ -207,7 +210,7 @@ __global__ void __launch_bounds__(256) mw_kernel(const TM* __restrict__ M, int l
 // path for small le and the two-kernel path otherwise
 template <class TA, class TM>
 int coef_run(nys_ctx* ctx, const TA* part, int nb, int le, int ldm, int inverse, const TM* M, const TM* d,
-             TA* coef, int batch, TA* wbuf = nullptr) {
+             TA* coef, int batch, TA* wbuf = nullptr, DualStop stop = {}) {
     cudaStream_t s = ctx->stream;
     if (le <= 64 || !wbuf) {
         NYS_CK(ctx, launch_pdl(coef_vec_kernel<TA, TM>, dim3((le + 31) / 32, batch), 256, le * sizeof(TA), s, part,
@@ -215,10 +218,10 @@ int coef_run(nys_ctx* ctx, const TA* part, int nb, int le, int ldm, int inverse,
         NYS_LAUNCH_CK(ctx);
         return NYS_OK;
     }
-    NYS_CK(ctx, launch_pdl(reduce_cols_kernel<TA>, dim3((le + 7) / 8, batch), 256, 0, s, part, nb, le, wbuf));
+    NYS_CK(ctx, launch_pdl(reduce_cols_kernel<TA>, dim3((le + 7) / 8, batch), 256, 0, s, part, nb, le, wbuf, stop));
     NYS_LAUNCH_CK(ctx);
     NYS_CK(ctx, launch_pdl(mw_kernel<TA, TM>, dim3((le + 7) / 8, batch), 256, le * sizeof(TA), s, M, ldm, inverse, d,
-                           wbuf, le, coef));
+                           wbuf, le, coef, stop));
     NYS_LAUNCH_CK(ctx);
     return NYS_OK;
 }
@@ -272,8 +275,9 @@ template <class TU, class TZ, class TA, int NQ = 4, int PV = 1>
 __global__ void __launch_bounds__(256) uc_vec_kernel(const TU* __restrict__ U, const TZ* __restrict__ z, int64_t N,
                                                      int ell, const TA* __restrict__ coef, TA sign,
                                                      TZ* __restrict__ out, const TZ* __restrict__ base, TA scale,
-                                                     int keep) {
+                                                     int keep, DualStop stop) {
     pdl_enter();
+    if (dual_skip(stop)) return;
     const L2Pol pol = make_l2_pol();
     constexpr int V = Vec16<TU>::n;
     constexpr int P = 32 * V * PV;
