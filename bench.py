@@ -656,8 +656,6 @@ def run_native(args, w: WL.Workload):
 def dual_stop_info(w: WL.Workload, skipped_p, k_p, skipped_0, k_0) -> dict:
     """Dual steps the exact early stop skipped per timed solve (bit-identical
     results: a step is skipped only after one that changed nothing)."""
-    if w.reg != "tv":
-        return {"applies": False, "what": "the exact early stop serves the anisotropic-TV prox only"}
     return {"applies": True,
             "precond": {"skipped_per_solve": skipped_p, "of": k_p * w.n_inner,
                         "fraction": round(skipped_p / max(1, k_p * w.n_inner), 4)},

@@ -94,8 +94,9 @@ const char* nys_version(void);
 int nys_l2_persist(nys_ctx* ctx, const void* ptr, size_t bytes, double hit_ratio);
 /* Number of kernels launched through this context since it was created. */
 int nys_launch_count(const nys_ctx* ctx, int64_t* count);
-/* Exact early stop of the dual APG of the anisotropic-TV prox (Sec. III-B,
- * the dual problem solved by APG), on by default: once a dual step j >= 1
+/* Exact early stop of the dual APG of the mixed-norm proxes (prox_tv,
+ * prox_hs, prox_mixed; Sec. III-B, the dual problem solved by APG), on by
+ * default: once a dual step j >= 1
  * leaves every component of the dual iterate and of its extrapolation
  * unchanged, every later step would reproduce it (a step is a deterministic
  * function of that pair), so the remaining steps of the call are skipped on

@@ -78,7 +78,7 @@ class Context:
         return n.value
 
     def set_dual_stop(self, on: bool = True):
-        """Exact early stop of the TV dual iteration (bit-identical results)."""
+        """Exact early stop of the mixed-norm dual iteration (bit-identical results)."""
         check(_lib().nys_set_dual_stop(self.h, int(bool(on))), self.h)
 
     def dual_steps_skipped(self) -> int:

@@ -186,14 +186,15 @@ __device__ __forceinline__ void pdl_enter() {
 
 int pdl_mode();   // api.cu: 0, 1 or 2 as above
 
-// Exact early stop of the dual APG of the anisotropic-TV prox.  A dual step
-// maps (R, Q) to (R', Q') by a fixed deterministic function of (R, Q) and of
-// beta, and beta only multiplies Q' - Q.  If a step leaves every component
-// unchanged (Q' = R = Q), every later step reproduces it exactly, so once a
-// step j >= 1 has changed nothing, steps j + 2 ... may be skipped: both
-// ping-pong buffers already hold the fixed point (step j's inputs and
-// outputs), and the result is bit-identical to running them.  (Step 0's
-// input g comes from a differently ordered L^T, so it does not count.)
+// Exact early stop of the dual APG of the mixed-norm proxes (TV, isotropic
+// TV, HS_1, HS_2, HS_inf).  A dual step maps (R, Q) to (R', Q') by a fixed
+// deterministic function of (R, Q) and of beta, and beta only multiplies
+// Q' - Q.  If a step leaves every component unchanged (Q' = R = Q), every
+// later step reproduces it exactly, so once a step j >= 1 has changed
+// nothing, steps j + 2 ... may be skipped: the buffers (ping-pong or updated
+// in place) already hold the fixed point, and the result is bit-identical to
+// running them.  (In the fused anisotropic-TV step, step 0's input g comes
+// from a differently ordered L^T, so step 0 does not count.)
 // Three flags in ctx->counters: step k sets flags[k % 3] when any component
 // changed and clears flags[(k + 1) % 3] for step k + 1; step k >= 2 is
 // skipped when flags[(k - 1) % 3] is clear.  A skipped last step still

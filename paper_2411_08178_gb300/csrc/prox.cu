@@ -34,11 +34,13 @@ namespace nys {
 
 namespace {
 
-// out = base - lb * L^T Q   (base may be null -> out = L^T Q, lb ignored)
+// out = base - lb * L^T Q   (base may be null -> out = L^T Q, lb ignored);
+// nothing inside a dual step that the exact early stop skips
 template <class T, int REG>
 __global__ void lt_kernel(const T* __restrict__ Q, const T* __restrict__ base, typename Comp<T>::type lb, int n1,
-                          int n2, T* __restrict__ out) {
+                          int n2, T* __restrict__ out, DualStop stop) {
     pdl_enter();
+    if (dual_skip(stop)) return;
     using TC = typename Comp<T>::type;
     const int64_t N = (int64_t)n1 * n2;
     for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < N; t += (int64_t)gridDim.x * blockDim.x) {
@@ -120,7 +122,8 @@ int prox_dual_typed(nys_ctx* ctx, const nys_precond* pc, double lb, int n_inner,
         // last step writes Q unless it reads it)
         T* X[2] = {work, work + N};
         T* RQ[2][2] = {{work + 2 * N, work + 2 * N + G * N}, {work + 2 * N + 2 * G * N, work + 2 * N + 3 * G * N}};
-        NYS_CK(ctx, launch_pdl(lt_kernel<T, REG>, grid, 256, 0, sm, Q, s, (TC)lb, n1, n2, n_inner ? X[0] : out));
+        NYS_CK(ctx, launch_pdl(lt_kernel<T, REG>, grid, 256, 0, sm, Q, s, (TC)lb, n1, n2, n_inner ? X[0] : out,
+                               DualStop{}));
         NYS_LAUNCH_CK(ctx);
         for (int k = 0; k < n_inner; ++k) {
             const double tn = 0.5 * (1.0 + std::sqrt(1.0 + 4.0 * t * t));
@@ -152,30 +155,35 @@ int prox_dual_typed(nys_ctx* ctx, const nys_precond* pc, double lb, int n_inner,
     NYS_CK(ctx, cudaMemcpyAsync(R, Q, sizeof(T) * G * N, cudaMemcpyDeviceToDevice, sm));
     NYS_CK(ctx, cudaMemcpyAsync(Qp, Q, sizeof(T) * G * N, cudaMemcpyDeviceToDevice, sm));
     for (int k = 0; k < n_inner; ++k) {
+        // the exact early stop (internal.cuh): dual_update keeps the flags;
+        // the x of a skipped step is not recomputed (P = I)
+        DualStop ds;
+        if (ctx->dual_stop) ds.flags = ctx->counters + COUNTER_DUAL_STOP;
+        ds.k = k;
         if (pc) {
-            NYS_CK(ctx, launch_pdl(lt_kernel<T, REG>, grid, 256, 0, sm, R, nullptr, TC(0), n1, n2, g));
+            NYS_CK(ctx, launch_pdl(lt_kernel<T, REG>, grid, 256, 0, sm, R, nullptr, TC(0), n1, n2, g, DualStop{}));
             NYS_LAUNCH_CK(ctx);
             if ((st = precond_run(ctx, pc, 1, dt, g, g, 1))) return st;
             NYS_CK(ctx, launch_pdl(axpy_kernel<T>, grid, 256, 0, sm, s, g, (TC)lb, N, x));
         } else {
-            NYS_CK(ctx, launch_pdl(lt_kernel<T, REG>, grid, 256, 0, sm, R, s, (TC)lb, n1, n2, x));
+            NYS_CK(ctx, launch_pdl(lt_kernel<T, REG>, grid, 256, 0, sm, R, s, (TC)lb, n1, n2, x, ds));
         }
         NYS_LAUNCH_CK(ctx);
         const double tn = 0.5 * (1.0 + std::sqrt(1.0 + 4.0 * t * t));
         const double beta = (t - 1.0) / tn;
         t = tn;
-        NYS_CK(ctx, launch_pdl(dual_update_kernel<T, REG>, grid, 256, 0, sm, x, R, Qp, step, (TC)beta, n1, n2));
+        NYS_CK(ctx, launch_pdl(dual_update_kernel<T, REG>, grid, 256, 0, sm, x, R, Qp, step, (TC)beta, n1, n2, ds));
         NYS_LAUNCH_CK(ctx);
     }
     // Q_io <- last Q; out = s - lb P^{-1} L^T Q
     NYS_CK(ctx, cudaMemcpyAsync(Q, Qp, sizeof(T) * G * N, cudaMemcpyDeviceToDevice, sm));
     if (pc) {
-        NYS_CK(ctx, launch_pdl(lt_kernel<T, REG>, grid, 256, 0, sm, Qp, nullptr, TC(0), n1, n2, g));
+        NYS_CK(ctx, launch_pdl(lt_kernel<T, REG>, grid, 256, 0, sm, Qp, nullptr, TC(0), n1, n2, g, DualStop{}));
         NYS_LAUNCH_CK(ctx);
         if ((st = precond_run(ctx, pc, 1, dt, g, g, 1))) return st;
         NYS_CK(ctx, launch_pdl(axpy_kernel<T>, grid, 256, 0, sm, s, g, (TC)lb, N, out));
     } else {
-        NYS_CK(ctx, launch_pdl(lt_kernel<T, REG>, grid, 256, 0, sm, Qp, s, (TC)lb, n1, n2, out));
+        NYS_CK(ctx, launch_pdl(lt_kernel<T, REG>, grid, 256, 0, sm, Qp, s, (TC)lb, n1, n2, out, DualStop{}));
     }
     NYS_LAUNCH_CK(ctx);
     return NYS_OK;

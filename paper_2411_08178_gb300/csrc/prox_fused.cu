@@ -78,6 +78,9 @@ __global__ void __launch_bounds__(256) lt_utz_kernel(const T* __restrict__ R, in
                     tv_dual_copy_q<T>(dual, (size_t)(i0 + q), (size_t)N);
             return;
         }
+    } else {
+        // L^T R of an unfused dual step (the dual update keeps the flags)
+        if (dual_skip(stop)) return;
     }
     if constexpr (XR) {
         for (int k = threadIdx.x; k < le; k += blockDim.x) cs[k] = xr.c[k];
@@ -240,7 +243,7 @@ int fused_typed(nys_ctx* ctx, const nys_precond* pc, double lb, int n_inner, int
     // set); then x (or out) = s - lb (g - U c), c = M U^T g.  ds: the dual
     // step's early stop (the x pass of the last step always runs)
     auto xfn = [&](const T* Rin, const TvDual<T>& dual, T* dst, DualStop ds) -> int {
-        const DualStop ucs = dual.Rn ? ds : nostop;
+        const DualStop ucs = (dual.x && !dual.Rn) ? nostop : ds;
         if (last) {
             if (dual.x)
                 NYS_CK(ctx, launch_pdl(lt_utz_kernel<TU, T, TA, TM, REG, true, FCH, TV>, nchunk, 256, lsm, sm, Rin,
@@ -337,11 +340,15 @@ int fused_typed(nys_ctx* ctx, const nys_precond* pc, double lb, int n_inner, int
     NYS_CK(ctx, cudaMemcpyAsync(R, Q, sizeof(T) * G * N, cudaMemcpyDeviceToDevice, sm));
     NYS_CK(ctx, cudaMemcpyAsync(Qp, Q, sizeof(T) * G * N, cudaMemcpyDeviceToDevice, sm));
     for (int k = 0; k < n_inner; ++k) {
-        if ((st = xfn(R, none, x, nostop))) return st;
+        // the exact early stop: the dual update keeps the flags, the x pass
+        // of a skipped step does nothing (x, R and Q already hold the fixed
+        // point)
+        if ((st = xfn(R, none, x, stop_at(k)))) return st;
         const double tn = 0.5 * (1.0 + std::sqrt(1.0 + 4.0 * t * t));
         const double beta = (t - 1.0) / tn;
         t = tn;
-        NYS_CK(ctx, launch_pdl(dual_update_kernel<T, REG>, dg, 256, 0, sm, x, R, Qp, step, (TA)beta, n1, n2));
+        NYS_CK(ctx, launch_pdl(dual_update_kernel<T, REG>, dg, 256, 0, sm, x, R, Qp, step, (TA)beta, n1, n2,
+                               stop_at(k)));
         NYS_LAUNCH_CK(ctx);
     }
     NYS_CK(ctx, cudaMemcpyAsync(Q, Qp, sizeof(T) * G * N, cudaMemcpyDeviceToDevice, sm));

@@ -58,38 +58,49 @@ __device__ __forceinline__ typename Comp<T>::type lt_q(const T* __restrict__ Q, 
 // [-1, 1] (anisotropic TV), scale to Euclidean norm <= 1 (isotropic TV), clip
 // the eigenvalues of the symmetric 2 x 2 block (HS_1), scale it to Frobenius
 // norm <= 1 (HS_2), or move its eigenvalue pair onto the l1 unit ball
-// (HS_inf).
+// (HS_inf).  chg: set when the new Q at the pixel differs from the old R or
+// Q there (the test of the exact early stop, internal.cuh).
 template <class T, int REG>
 __device__ __forceinline__ void dual_pixel(const typename Comp<T>::type* Lx, T* __restrict__ R, T* __restrict__ Qp,
                                            int64_t t, int64_t N, typename Comp<T>::type step,
-                                           typename Comp<T>::type beta) {
+                                           typename Comp<T>::type beta, bool* chg = nullptr) {
     using TC = typename Comp<T>::type;
+    auto note = [&](TC q, TC r, TC o) {
+        if (chg && !(q == r && q == o)) *chg = true;
+    };
     if (REG == NYS_REG_TV) {
 #pragma unroll
         for (int c = 0; c < 2; ++c) {
             const int64_t e = t + c * N;
-            const TC q = fmin(TC(1), fmax(TC(-1), (TC)R[e] + step * Lx[c]));
+            const TC r = (TC)R[e];
+            const TC q = fmin(TC(1), fmax(TC(-1), r + step * Lx[c]));
             const TC o = (TC)Qp[e];
+            note(q, r, o);
             R[e] = (T)(q + beta * (q - o));
             Qp[e] = (T)q;
         }
     } else if (REG == NYS_REG_ISOTV) {
-        TC q[2];
+        TC q[2], r[2];
 #pragma unroll
-        for (int c = 0; c < 2; ++c) q[c] = (TC)R[t + c * N] + step * Lx[c];
+        for (int c = 0; c < 2; ++c) {
+            r[c] = (TC)R[t + c * N];
+            q[c] = r[c] + step * Lx[c];
+        }
         const TC den = fmax(TC(1), sqrt(q[0] * q[0] + q[1] * q[1]));
 #pragma unroll
         for (int c = 0; c < 2; ++c) {
             const int64_t e = t + c * N;
             const TC qc = q[c] / den;
             const TC o = (TC)Qp[e];
+            note(qc, r[c], o);
             R[e] = (T)(qc + beta * (qc - o));
             Qp[e] = (T)qc;
         }
     } else {
-        const TC a = (TC)R[t] + step * Lx[0];
-        const TC b = (TC)R[t + N] + step * Lx[1];
-        const TC c = (TC)R[t + 2 * N] + step * Lx[2];
+        const TC ra = (TC)R[t], rb = (TC)R[t + N], rc = (TC)R[t + 2 * N];
+        const TC a = ra + step * Lx[0];
+        const TC b = rb + step * Lx[1];
+        const TC c = rc + step * Lx[2];
         TC pa, pb, pc;
         if (REG == NYS_REG_HS2) {
             const TC den = fmax(TC(1), sqrt(a * a + TC(2) * b * b + c * c));
@@ -127,6 +138,9 @@ __device__ __forceinline__ void dual_pixel(const typename Comp<T>::type* Lx, T* 
             }
         }
         const TC oa = (TC)Qp[t], ob = (TC)Qp[t + N], oc = (TC)Qp[t + 2 * N];
+        note(pa, ra, oa);
+        note(pb, rb, ob);
+        note(pc, rc, oc);
         R[t] = (T)(pa + beta * (pa - oa));
         R[t + N] = (T)(pb + beta * (pb - ob));
         R[t + 2 * N] = (T)(pc + beta * (pc - oc));
@@ -206,12 +220,20 @@ namespace {
 
 // Q' = Proj(R + step * L x); R <- Q' + beta (Q' - Qp); Qp <- Q' over the image
 // (x read from global memory with its periodic neighbours)
+// With the exact early stop (internal.cuh) this kernel keeps the step's
+// flags; a skipped step does nothing (R and Q are updated in place, so they
+// already hold the fixed point).
 template <class T, int REG>
 __global__ void dual_update_kernel(const T* __restrict__ x, T* __restrict__ R, T* __restrict__ Qp,
-                                   typename Comp<T>::type step, typename Comp<T>::type beta, int n1, int n2) {
+                                   typename Comp<T>::type step, typename Comp<T>::type beta, int n1, int n2,
+                                   DualStop stop) {
     pdl_enter();
     using TC = typename Comp<T>::type;
     const int64_t N = (int64_t)n1 * n2;
+    const bool skip = dual_skip(stop);
+    dual_stop_enter(stop, skip);
+    if (skip) return;
+    bool chg = false;
     for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < N; t += (int64_t)gridDim.x * blockDim.x) {
         int i, j;
         pix_ij(t, n2, i, j);
@@ -230,8 +252,9 @@ __global__ void dual_update_kernel(const T* __restrict__ x, T* __restrict__ R, T
             Lx[2] = (TC)x[r0 + jm] - TC(2) * xc + (TC)x[r0 + jp];
             Lx[1] = TC(0.25) * ((TC)x[rp + jp] - (TC)x[rp + jm] - (TC)x[rm + jp] + (TC)x[rm + jm]);
         }
-        dual_pixel<T, REG>(Lx, R, Qp, t, N, step, beta);
+        dual_pixel<T, REG>(Lx, R, Qp, t, N, step, beta, &chg);
     }
+    dual_stop_report(stop, chg);
 }
 
 }  // namespace

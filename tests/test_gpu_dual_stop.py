@@ -102,3 +102,36 @@ def test_dual_stop_solver_bit_identical(env, precond):
         ctx.set_dual_stop(True)
     assert skips[0] == 0 and skips[1] > 0
     assert torch.equal(xs[0], xs[1])
+
+
+@pytest.mark.parametrize("reg", ["isotv", "hs", "hs2", "hsinf"])
+@pytest.mark.parametrize("ell,udt,dt", [(0, None, "f32"), (0, None, "f64"), (10, "f32", "f32"), (96, "f32", "f32"),
+                                        (96, "f64", "f64")])
+def test_dual_stop_mixed_norms_bit_identical(env, reg, ell, udt, dt):
+    # the unfused dual steps (L^T, the P^{-1} passes, then the dual update):
+    # stop on and off agree bit for bit; a prox weight small enough to
+    # saturate the dual gives the stop something to skip
+    torch, api, ctx = env
+    n, lb = 64, 1e-6
+    G = 2 if reg == "isotv" else 3
+    tdt = torch.float64 if dt == "f64" else torch.float32
+    pc = None
+    if ell:
+        ud = {"f32": torch.float32, "f64": torch.float64}[udt]
+        pc = api.Precond(ctx, n * n, ell, ud).import_factor(_orthonormal(n * n, ell, 3), np.linspace(2.0, 1.0, ell),
+                                                            0.0, False)
+    s = torch.from_numpy(phantom(n, 6, 3, "mixed") + 0.05 * gaussian_probe_like((n, n), 9)).to(tdt).cuda()
+    Q0 = torch.zeros((G, n, n), dtype=tdt, device="cuda")
+    out = {}
+    try:
+        for on in (False, True):
+            ctx.set_dual_stop(on)
+            before = ctx.dual_steps_skipped()
+            x, Q = api.prox_mixed(ctx, pc, reg, lb, 20, s, Q=Q0.clone())
+            torch.cuda.synchronize()
+            out[on] = (x.clone(), Q.clone(), ctx.dual_steps_skipped() - before)
+    finally:
+        ctx.set_dual_stop(True)
+    print(f"{reg} active {max(ell - 1, 0)} {dt}: {out[True][2]} of 20 dual steps skipped")
+    assert out[False][2] == 0
+    assert torch.equal(out[True][0], out[False][0]) and torch.equal(out[True][1], out[False][1])
