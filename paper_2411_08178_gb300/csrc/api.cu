@@ -208,8 +208,8 @@ int nys_create(nys_ctx** out, int device, void* stream) {
         c->l2_bytes = l2;
     }
     // completion counters of the last-CTA reductions (zero between launches)
-    e = cudaMalloc(&c->counters, 64 * sizeof(unsigned));
-    if (e == cudaSuccess) e = cudaMemset(c->counters, 0, 64 * sizeof(unsigned));
+    e = cudaMalloc(&c->counters, COUNTER_WORDS * sizeof(unsigned));
+    if (e == cudaSuccess) e = cudaMemset(c->counters, 0, COUNTER_WORDS * sizeof(unsigned));
     if (e != cudaSuccess) {
         if (c->counters) cudaFree(c->counters);
         delete c;

@@ -75,7 +75,7 @@ struct nys_ctx {
     cudaStreamAttrValue l2_window = {};   // access-policy window set by nys_l2_persist
     bool l2_window_set = false;
     std::string err;
-    unsigned* counters = nullptr;   // device, 64 completion counters (see vec.cuh)
+    unsigned* counters = nullptr;   // device, COUNTER_WORDS words: completion counters (vec.cuh), dual-stop flags
     // exact early stop of the anisotropic-TV dual iteration (DualStop below),
     // on unless nys_set_dual_stop turned it off
     bool dual_stop = true;
@@ -195,32 +195,44 @@ int pdl_mode();   // api.cu: 0, 1 or 2 as above
 // in place) already hold the fixed point, and the result is bit-identical to
 // running them.  (In the fused anisotropic-TV step, step 0's input g comes
 // from a differently ordered L^T, so step 0 does not count.)
-// Three flags in ctx->counters: step k sets flags[k % 3] when any component
-// changed and clears flags[(k + 1) % 3] for step k + 1; step k >= 2 is
-// skipped when flags[(k - 1) % 3] is clear.  A skipped last step still
-// writes Q (and, without a preconditioner, the output x) out.
-constexpr int COUNTER_DUAL_STOP = 8;      // flags at counters[8 .. 10]
-constexpr int COUNTER_DUAL_SKIPPED = 11;  // dual steps skipped (wraps)
+// Three flags in ctx->counters: step k sets flag k % 3 when any component
+// changed and clears flag (k + 1) % 3 for step k + 1; step k >= 2 is skipped
+// when flag (k - 1) % 3 is clear.  A skipped last step still writes Q (and,
+// without a preconditioner, the output x) out.  Each flag is spread over
+// DUAL_STOP_SLOTS words (block b sets word b % DUAL_STOP_SLOTS): a thousand
+// blocks storing to one word serialise for tens of microseconds.
+constexpr int COUNTER_DUAL_SKIPPED = 8;     // dual steps skipped (wraps)
+constexpr int DUAL_STOP_SLOTS = 128;
+constexpr int COUNTER_DUAL_STOP = 512;      // 3 x DUAL_STOP_SLOTS flag words
+constexpr int COUNTER_WORDS = COUNTER_DUAL_STOP + 3 * DUAL_STOP_SLOTS;   // ctx->counters size
 struct DualStop {
     unsigned* flags = nullptr;   // nullptr: this launch never skips
     int k = 0;                   // the dual step of this launch
 };
+// Whether this launch's step is skipped, the same answer in every thread of
+// the block: every thread calls it (a block barrier), blockDim.x >=
+// DUAL_STOP_SLOTS
 __device__ __forceinline__ bool dual_skip(const DualStop& s) {
-    return s.flags && s.k >= 2 && *(volatile const unsigned*)(s.flags + (s.k + 2) % 3) == 0u;
+    const bool armed = s.flags && s.k >= 2;
+    int set = 0;
+    if (armed && threadIdx.x < DUAL_STOP_SLOTS)
+        set = *(volatile const unsigned*)(s.flags + ((s.k + 2) % 3) * DUAL_STOP_SLOTS + threadIdx.x) != 0u;
+    const int any = __syncthreads_or(set);
+    return armed && !any;
 }
-// the step's own bookkeeping, by one thread of the grid: clear the next
-// step's flag and count a skip
+// the step's own bookkeeping, by block 0: clear the next step's flag and
+// count a skip
 __device__ __forceinline__ void dual_stop_enter(const DualStop& s, bool skip) {
-    if (s.flags && blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0) {
-        s.flags[(s.k + 1) % 3] = 0u;
-        if (skip) atomicAdd(s.flags + (COUNTER_DUAL_SKIPPED - COUNTER_DUAL_STOP), 1u);
+    if (s.flags && blockIdx.x == 0 && blockIdx.y == 0) {
+        if (threadIdx.x < DUAL_STOP_SLOTS) s.flags[((s.k + 1) % 3) * DUAL_STOP_SLOTS + threadIdx.x] = 0u;
+        if (skip && threadIdx.x == 0) atomicAdd(s.flags + (COUNTER_DUAL_SKIPPED - COUNTER_DUAL_STOP), 1u);
     }
 }
 // a step that computed: set its flag when any thread of the block saw a change
-// (every thread of the block calls this)
+// (every thread of the block calls this; a block barrier)
 __device__ __forceinline__ void dual_stop_report(const DualStop& s, bool changed) {
     const int any = __syncthreads_or(changed ? 1 : 0);
-    if (s.flags && any && threadIdx.x == 0) s.flags[s.k % 3] = 1u;
+    if (s.flags && any && threadIdx.x == 0) s.flags[(s.k % 3) * DUAL_STOP_SLOTS + blockIdx.x % DUAL_STOP_SLOTS] = 1u;
 }
 
 inline bool pdl_enabled(cudaStream_t stream) {
