@@ -210,15 +210,14 @@ struct DualStop {
     int k = 0;                   // the dual step of this launch
 };
 // Whether this launch's step is skipped, the same answer in every thread of
-// the block: every thread calls it (a block barrier), blockDim.x >=
-// DUAL_STOP_SLOTS
+// the block: every thread calls it (a block barrier when armed), blockDim.x
+// >= DUAL_STOP_SLOTS
 __device__ __forceinline__ bool dual_skip(const DualStop& s) {
-    const bool armed = s.flags && s.k >= 2;
+    if (!s.flags || s.k < 2) return false;   // a kernel parameter: the same in every thread
     int set = 0;
-    if (armed && threadIdx.x < DUAL_STOP_SLOTS)
+    if (threadIdx.x < DUAL_STOP_SLOTS)
         set = *(volatile const unsigned*)(s.flags + ((s.k + 2) % 3) * DUAL_STOP_SLOTS + threadIdx.x) != 0u;
-    const int any = __syncthreads_or(set);
-    return armed && !any;
+    return !__syncthreads_or(set);
 }
 // the step's own bookkeeping, by block 0: clear the next step's flag and
 // count a skip
@@ -231,6 +230,10 @@ __device__ __forceinline__ void dual_stop_enter(const DualStop& s, bool skip) {
 // a step that computed: set its flag when any thread of the block saw a change
 // (every thread of the block calls this; a block barrier)
 __device__ __forceinline__ void dual_stop_report(const DualStop& s, bool changed) {
+    if (!s.flags) {
+        __syncthreads();
+        return;
+    }
     const int any = __syncthreads_or(changed ? 1 : 0);
     if (s.flags && any && threadIdx.x == 0) s.flags[(s.k % 3) * DUAL_STOP_SLOTS + blockIdx.x % DUAL_STOP_SLOTS] = 1u;
 }

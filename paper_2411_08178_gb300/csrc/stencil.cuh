@@ -188,19 +188,28 @@ __device__ __forceinline__ typename Comp<T>::type tv_dual_lt_f(const TvDual<T>& 
     const TC xc = xf(t);
     const TC lx1 = xc - xf(rm + j), lx1d = xf(td) - xc;
     const TC lx2 = xc - xf(r0 + jm), lx2r = xf(tr) - xc;
-    auto proj = [&](size_t e, TC lx) { return fmin(TC(1), fmax(TC(-1), fma(d.step, lx, (TC)d.Ro[e]))); };
-    const TC q1 = proj(t, lx1), q1d = proj(td, lx1d);
-    const TC q2 = proj(N + t, lx2), q2r = proj(N + tr, lx2r);
+    // the old (R, Q) at the pixel, read once before any store (the pointers
+    // may alias as far as the compiler knows)
+    const TC ro1 = (TC)d.Ro[t], ro2 = (TC)d.Ro[N + t];
+    const TC qo1 = d.Rn ? (TC)d.Qo[t] : TC(0), qo2 = d.Rn ? (TC)d.Qo[N + t] : TC(0);
+    auto clip = [&](TC lx, TC r) { return fmin(TC(1), fmax(TC(-1), fma(d.step, lx, r))); };
+    auto proj = [&](size_t e, TC lx) { return clip(lx, (TC)d.Ro[e]); };
+    const TC q1 = clip(lx1, ro1), q1d = proj(td, lx1d);
+    const TC q2 = clip(lx2, ro2), q2r = proj(N + tr, lx2r);
+    TC mq1d = TC(0), mq2r = TC(0);
+    if (d.Rn) {
+        auto mom = [&](size_t e, TC q) { return fma(d.beta, q - (TC)d.Qo[e], q); };
+        mq1d = mom(td, q1d);
+        mq2r = mom(N + tr, q2r);
+    }
     d.Qn[t] = (T)q1;
     d.Qn[N + t] = (T)q2;
     if (!d.Rn) return q1 - q1d + q2 - q2r;
-    auto mom = [&](size_t e, TC q) { return fma(d.beta, q - (TC)d.Qo[e], q); };
-    const TC r1 = mom(t, q1), r2 = mom(N + t, q2);
+    const TC r1 = fma(d.beta, q1 - qo1, q1), r2 = fma(d.beta, q2 - qo2, q2);
     d.Rn[t] = (T)r1;
     d.Rn[N + t] = (T)r2;
-    if (chg && !(q1 == (TC)d.Ro[t] && q1 == (TC)d.Qo[t] && q2 == (TC)d.Ro[N + t] && q2 == (TC)d.Qo[N + t]))
-        *chg = true;
-    return r1 - mom(td, q1d) + r2 - mom(N + tr, q2r);
+    if (chg && !(q1 == ro1 && q1 == qo1 && q2 == ro2 && q2 == qo2)) *chg = true;
+    return r1 - mq1d + r2 - mq2r;
 }
 template <class T>
 __device__ __forceinline__ typename Comp<T>::type tv_dual_lt(const TvDual<T>& d, int i, int j, int n1, int n2,
