@@ -1,13 +1,15 @@
 """Per-call timings of the library's hot entry points, and a small target for ncu.
 
   python -m paper_2411_08178_gb300.profile_kernels [--case all|precond|normal|sketch|prox|prox_mixed|irm|iter|unroll|batch]
-        [--n 512] [--ell 200] [--reps 20] [--l2]
+        [--n 512] [--ell 200] [--reps 20] [--l2] [--dual-stop off|on]
 
 Each case builds the 512 x 512 deblurring operator (25 x 25 Gaussian, sigma 4)
 and times one library call with CUDA events on the calling stream (warm-up
 first, mean over --reps), then prints one JSON line per case with the time
 and the algorithmic bytes or flops of the call.  With few repetitions it is
-also the workload for `ncu -k regex:<kernel> -c <n>` captures.
+also the workload for `ncu -k regex:<kernel> -c <n>` captures.  The exact
+early stop of the dual iterations is off unless --dual-stop on: the prox
+cases then time every dual step (their cost per step), whatever the input.
 """
 from __future__ import annotations
 
@@ -29,6 +31,8 @@ def main():
     ap.add_argument("--reps", type=int, default=20)
     ap.add_argument("--u-dtype", choices=["bf16", "f32"], default="bf16")
     ap.add_argument("--l2", action="store_true", help="keep U resident in L2 (nys_l2_persist)")
+    ap.add_argument("--dual-stop", choices=["off", "on"], default="off",
+                    help="the exact early stop of the dual iterations (off: every dual step runs)")
     ap.add_argument("--batch-count", type=int, default=64)
     ap.add_argument("--batch-inner", type=int, default=20)
     ap.add_argument("--irm-eps", type=float, default=1e-8, help="IRM smoothing |r|_eps = sqrt(r^2 + eps)")
@@ -48,6 +52,7 @@ def main():
     stream = torch.cuda.Stream(dev)
     torch.cuda.set_stream(stream)
     ctx = api.Context(0, stream)
+    ctx.set_dual_stop(args.dual_stop == "on")
     n, ell = args.n, args.ell
     N = n * n
     if args.op == "blur":
