@@ -208,6 +208,9 @@ constexpr int COUNTER_WORDS = COUNTER_DUAL_STOP + 3 * DUAL_STOP_SLOTS;   // ctx-
 struct DualStop {
     unsigned* flags = nullptr;   // nullptr: this launch never skips
     int k = 0;                   // the dual step of this launch
+    // the x pass of a skipped last step: where the fixed point's x already is
+    // (the pass copies it to its output instead of streaming U again)
+    const void* copy = nullptr;
 };
 // Whether this launch's step is skipped, the same answer in every thread of
 // the block: every thread calls it (a block barrier when armed), blockDim.x

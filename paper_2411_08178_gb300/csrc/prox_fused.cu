@@ -243,7 +243,11 @@ int fused_typed(nys_ctx* ctx, const nys_precond* pc, double lb, int n_inner, int
     // set); then x (or out) = s - lb (g - U c), c = M U^T g.  ds: the dual
     // step's early stop (the x pass of the last step always runs)
     auto xfn = [&](const T* Rin, const TvDual<T>& dual, T* dst, DualStop ds) -> int {
-        const DualStop ucs = (dual.x && !dual.Rn) ? nostop : ds;
+        // the last dual step's x pass: if that step is skipped, x already holds
+        // its output (the last step that ran computed it from the same g and
+        // c; at the fixed point the two L^T agree bit for bit)
+        DualStop ucs = ds;
+        if (dual.x && !dual.Rn) ucs.copy = dual.x;
         if (last) {
             if (dual.x)
                 NYS_CK(ctx, launch_pdl(lt_utz_kernel<TU, T, TA, TM, REG, true, FCH, TV>, nchunk, 256, lsm, sm, Rin,

@@ -277,10 +277,20 @@ __global__ void __launch_bounds__(256) uc_vec_kernel(const TU* __restrict__ U, c
                                                      TZ* __restrict__ out, const TZ* __restrict__ base, TA scale,
                                                      int keep, DualStop stop) {
     pdl_enter();
-    if (dual_skip(stop)) return;
-    const L2Pol pol = make_l2_pol();
     constexpr int V = Vec16<TU>::n;
     constexpr int P = 32 * V * PV;
+    if (dual_skip(stop)) {
+        if (stop.copy)
+            for (int p = threadIdx.x; p < P; p += blockDim.x) {
+                const int64_t ii = (int64_t)blockIdx.x * P + p;
+                if (ii < N) {
+                    const size_t o = (size_t)blockIdx.y * N + ii;
+                    out[o] = reinterpret_cast<const TZ*>(stop.copy)[o];
+                }
+            }
+        return;
+    }
+    const L2Pol pol = make_l2_pol();
     extern __shared__ __align__(16) unsigned char smem_raw[];
     TA* c = reinterpret_cast<TA*>(smem_raw);
     TA* red = c + ((ell + 3) & ~3);            // [8][P]
