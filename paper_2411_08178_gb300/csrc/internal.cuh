@@ -191,7 +191,7 @@ int pdl_mode();   // api.cu: 0, 1 or 2 as above
 // deterministic function of (R, Q) and of beta, and beta only multiplies
 // Q' - Q.  If a step leaves every component unchanged (Q' = R = Q), every
 // later step reproduces it exactly, so once a step j >= 1 has changed
-// nothing, steps j + 2 ... may be skipped: the buffers (ping-pong or updated
+// nothing, steps j + 1 ... may be skipped: the buffers (ping-pong or updated
 // in place) already hold the fixed point, and the result is bit-identical to
 // running them.  (In the fused anisotropic-TV step, step 0's input g comes
 // from a differently ordered L^T, so step 0 does not count.)
