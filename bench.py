@@ -243,6 +243,29 @@ class Native:
         solver.x(buf)
         return None, self.api.nys_rel_err(self.ctx, buf, xstar), None
 
+    def stop_bitwise_check(self, k_p, k_0):
+        """Untimed: the iterate after the timed solves' iteration counts with
+        the exact early stop of the dual iteration on and off, preconditioned
+        and plain, compared bit for bit (fresh solvers, so each captures its
+        iteration with the setting)."""
+        torch, api, w = self.torch, self.api, self.w
+        out = {}
+        try:
+            for name, k, pc in (("precond", k_p, self.pc), ("plain", k_0, None)):
+                xs = []
+                for on in (True, False):
+                    self.ctx.set_dual_stop(on)
+                    sol = api.Solver(self.ctx, self.op, self.y, w.reg, w.lam, pc=pc, **self.kw)
+                    sol.step(k)
+                    xs.append(sol.x().clone())
+                    sol.close()
+                out[name] = bool(torch.equal(xs[0], xs[1]))
+        finally:
+            self.ctx.set_dual_stop(True)
+        out["what"] = ("x^k after the timed iteration counts with the dual early stop on and off, compared bit for bit "
+                       "(untimed)")
+        return out
+
     def solve_precond(self, k):
         self.sketch_factor()
         self.solver_p.restart(True)
@@ -561,6 +584,7 @@ def run_native(args, w: WL.Workload):
         torch.distributed.barrier()
     nb.x_host = torch.empty((w.n, w.n), dtype=torch.float32).pin_memory()
     times_e2e = nb.time_loop(lambda: nb.e2e_step(k_p_run), plain_steps, 1, "timed_e2e")
+    stop_check = nb.stop_bitwise_check(k_p_run, k_0_run)
     pre_ms, pre_bytes = nb.precond_roofline()
     step_ms, step_bytes, step_desc = nb.dual_step_roofline()
     normal_ms = nb.normal_ms()
@@ -619,8 +643,9 @@ def run_native(args, w: WL.Workload):
                                "iterations after the first hit (Algorithm 3 is not monotone); k_precond and "
                                "k_plain are the first hits, the counts the timed solves run")},
         "iterate_err": {"precond_at_k": err_p, "plain_at_k": err_0},
-        "dual_stop": dual_stop_info(w, (s1 - s0) / (args.steps + args.warmup), k_p_run,
-                                    (s2 - s1) / (plain_steps + min(args.warmup, 2)), k_0_run),
+        "dual_stop": {**dual_stop_info(w, (s1 - s0) / (args.steps + args.warmup), k_p_run,
+                                       (s2 - s1) / (plain_steps + min(args.warmup, 2)), k_0_run),
+                      "bitwise_equal_to_stop_off": stop_check},
         "reference_solution": {"F_star": Fstar, **ref_info},
         "e2e": {"value": round(ms_e, 3), "unit": "ms", "steps": plain_steps, "h2d_bytes_per_step": int(nb.y.numel() * 4),
                 "d2h_bytes_per_step": int(N * 4)},
