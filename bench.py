@@ -53,7 +53,7 @@ TARGET = 1e-3
 # version only
 DUAL_STEP_TRAFFIC = {# warm L2 (the columns kept with evict_last stay resident
                      # across x evaluations, as in the solve)
-                     ("ct512_parallel_tv_f32", 400, "bf16"): 288.0e6}
+                     ("ct512_parallel_tv_f32", 400, "bf16"): 291.5e6}
 SECONDARY = ("deblur512_tv_f32", "superres4x_hs_huber_f32")
 # Iterations the preconditioned solve takes to the target on each workload
 # (the native arm's first-hit count on a GB300, bench.py's k_precond): the
