@@ -46,3 +46,14 @@ def test_clock_log_summary(tmp_path):
     c = bench.ClockSampler(0, str(tmp_path))
     assert c.path.startswith(str(tmp_path))
     assert c.stop()["reasons"] == ["nvidia-smi unavailable"]
+
+
+def test_dual_stop_report():
+    # skipped steps per timed solve against the steps the solve issues
+    # (n_inner per WAPG iteration)
+    w = bench.WL.PRESETS["ct512_parallel_tv_f32"]
+    r = bench.dual_stop_info(w, 31850.0, 1774, 81067.0, 4504)
+    assert r["precond"]["of"] == 1774 * w.n_inner and r["plain"]["of"] == 4504 * w.n_inner
+    assert r["precond"]["fraction"] == round(31850.0 / (1774 * w.n_inner), 4)
+    assert 0.0 <= r["plain"]["fraction"] <= 1.0
+    json.dumps(r)
